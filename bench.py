@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Throughput of the tangent-point energy + gradient on one GB300.
+
+Default workload: icosphere level 7 (327,680 triangles, 163,842 vertices)
+deformed by seeded spherical-harmonic modes l <= 12 with amplitudes
+N(0, (0.05/l)^2), seed 2; q = 6, p = 12; direct all-pairs form, FP32 pair
+terms with FP64 accumulation.  One step = one pass of the hot path: the
+positions are re-uploaded (device to device), the per-triangle data is
+recomputed, all admitted pairs are evaluated, the per-triangle derivatives
+are pulled back to the vertices and the energy is reduced.
+
+Metric: ordered pair interactions per second (nt (nt-1) minus the ordered
+pairs of triangles sharing a vertex, per evaluation) and ms per evaluation.
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
+same workload on the host cores.  Under torchrun every rank runs an
+independent replica (the evaluation does not shard); ``value`` is the total
+over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TP energy+grad ms/eval & pair-interactions/s at 327k tris; rel err vs FP64"
+UNIT = "pair-interactions/s"
+# Algorithmic FP32 work per unordered admitted pair of the energy+gradient
+# pair function (both orderings, shared subexpressions once), counted from
+# its expression DAG with an FMA as 2 flops: 25 FMA + 25 other = 75 flops.
+FLOPS_PER_UNORDERED_PAIR = 75
+FP32_LANES_PER_SM = 128
+# DRAM bytes per launch of the dominant kernel from the committed ncu
+# capture (profiles/); None until a capture of the current kernel exists.
+NCU_TRAFFIC_BYTES = None
+
+WORKLOADS = {
+    "sh_l7": "icosphere level 7 (327,680 triangles) with seeded SH deformation l<=12, a_lm~N(0,(0.05/l)^2), seed 2",
+    "dish_l5": "icosphere level 5 (20,480 triangles) mapped to a double-walled dish, gap 0.02, jitter N(0,0.002^2)",
+    "folds_l8": "icosphere level 8 (1,310,720 triangles) with 40 seeded radial folds of depth 0.1",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sh_l7", choices=sorted(WORKLOADS))
+    ap.add_argument("--mode", default="direct", choices=["direct", "bh"])
+    ap.add_argument("--theta", type=float, default=0.25)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"tp_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower() in ("active", "1", "yes"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def run_cpu_baseline(V, F, seconds):
+    """The FP64 oracle as it stands, on a bounded sample of target triangles."""
+    import oracle
+
+    oracle.build()
+    nt = F.shape[0]
+    nth = oracle.nthreads_default()
+    rng = np.random.default_rng(123)
+    x, nu, w = oracle.tri_data(V, F)
+    cal = rng.choice(nt, max(nth, 8), replace=False)
+    t0 = time.perf_counter()
+    oracle.tri_accum(V, F, cal, soa=(x, nu, w), nthreads=nth)
+    dt = time.perf_counter() - t0
+    per = dt / len(cal)
+    m = int(max(len(cal), min(nt, seconds / max(per, 1e-9))))
+    m = max(nth, (m // nth) * nth)
+    tris = rng.choice(nt, m, replace=False)
+    t0 = time.perf_counter()
+    oracle.tri_accum(V, F, tris, soa=(x, nu, w), nthreads=nth)
+    dt = time.perf_counter() - t0
+    val = m * (nt - 1) / dt
+    return {"value": val, "unit": UNIT, "cores": nth, "kind": "oracle",
+            "sample": f"dPhi/d(w,nu,x) of {m} random target triangles against all {nt - 1} others "
+                      f"(both orderings, FP64), {dt:.1f} s; rate = targets*(nt-1)/s"}
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    from paper_2509_22110_gb300 import meshgen
+    import oracle
+
+    V, F = meshgen.workload(args.workload)
+    nt = F.shape[0]
+    oracle.build()
+    nth = oracle.nthreads_default()
+    rng = np.random.default_rng(7)
+    x, nu, w = oracle.tri_data(V, F)
+    # size one step at ~per-step seconds so warmup + steps stay within a few minutes
+    per_step = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    cal = rng.choice(nt, nth, replace=False)
+    t0 = time.perf_counter()
+    oracle.tri_accum(V, F, cal, soa=(x, nu, w), nthreads=nth)
+    per = (time.perf_counter() - t0) / nth
+    m = max(nth, int(per_step / max(per, 1e-9)) // nth * nth)
+    times = []
+    for s in range(args.warmup + args.steps):
+        tris = rng.choice(nt, m, replace=False)
+        t0 = time.perf_counter()
+        oracle.tri_accum(V, F, tris, soa=(x, nu, w), nthreads=nth)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    val = args.steps * m * (nt - 1) / tot
+    full_ms = (nt / m) * (tot / args.steps) * 1e3
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": full_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded mesh)", "impl": "reference",
+            "config": {"workload": WORKLOADS[args.workload], "mode": args.mode, "q": 6, "p": 12,
+                       "step": f"{m} sampled targets per step; ms_per_step extrapolated to all {nt} targets"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": nth, "kind": "oracle",
+                             "sample": f"{m} random target triangles x {nt - 1} sources per step"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    import torch.distributed as tdist
+
+    ws, rank, local = dist_info()
+    if ws > 1:
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2509_22110_gb300 import build as _b
+
+    if rank == 0:
+        _b.build()
+    if ws > 1:
+        tdist.barrier()
+    import paper_2509_22110_gb300 as tp
+    from paper_2509_22110_gb300 import _tp, meshgen
+
+    V, F = meshgen.workload(args.workload)
+    nt, nv = F.shape[0], V.shape[0]
+    stream = torch.cuda.Stream(dev)
+    ctx = tp.tp_create(local, stream.cuda_stream)
+    mode = tp.TP_DIRECT if args.mode == "direct" else tp.TP_BH
+    prm = tp.tp_params_default(mode=mode, theta=args.theta)
+    with torch.cuda.stream(stream):
+        Vd = torch.tensor(V, device=dev)
+        Fd = torch.tensor(F, device=dev)
+        gd = torch.zeros_like(Vd)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+    stream.synchronize()
+    tp.tp_mesh_upload(ctx, Vd, Fd)
+    up_stats = tp.tp_get_stats(ctx)
+
+    launches = [0]
+    kern_ms = []
+
+    def step():
+        tp.tp_mesh_upload(ctx, Vd, None, flags=_tp.TP_POSITIONS_ONLY)
+        launches[0] += tp.tp_get_stats(ctx)["kernel_launches"]
+        if mode != tp.TP_DIRECT:
+            tp.tp_tree_build(ctx, 16, 30)
+            launches[0] += tp.tp_get_stats(ctx)["kernel_launches"]
+        e = tp.tp_gradient(ctx, gd, prm)
+        st = tp.tp_get_stats(ctx)
+        launches[0] += st["kernel_launches"]
+        kern_ms.append(st["ms_kernel"])
+        return e, st
+
+    for _ in range(args.warmup):
+        step()
+    launches[0] = 0
+    kern_ms.clear()
+    n_ex = nt * (nt - 1) - step()[1]["pairs_exact"]
+    launches[0] = 0
+    kern_ms.clear()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if ws > 1:
+        tdist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    stats = None
+    energy = None
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))  # evict the previous step's working set from L2
+        starts[k].record(stream)
+        energy, stats = step()
+        ends[k].record(stream)
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        tdist.barrier()
+    clk = clocks.stop()
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    t_local = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        tdist.all_reduce(t_local, op=tdist.ReduceOp.MAX)
+    total_ms = float(t_local.item())
+    ms_step = total_ms / args.steps
+    pairs = stats["pairs_exact"] + stats["far_pairs"]
+    value = ws * args.steps * pairs / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (unmasked direct pair kernel)
+    roof = None
+    if mode == tp.TP_DIRECT:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        pk = measured_peaks()
+        max_mhz = float(pk.get("sm_max_mhz", 2070.0))
+        peak_tflops = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+        n_items = stats["tile_pairs"] - stats["tile_pairs_masked"]
+        upairs = n_items * 1024 * 1024  # unordered pairs in the unmasked launch (nt is a multiple of 1024 here)
+        kms = statistics.mean(kern_ms) if kern_ms else float("nan")
+        achieved = FLOPS_PER_UNORDERED_PAIR * upairs / (kms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": NCU_TRAFFIC_BYTES,
+                "kernel": "k_pairs_grad<6,false>", "kernel_ms": kms,
+                "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz (max SM clock)",
+                "flops_per_unordered_pair": FLOPS_PER_UNORDERED_PAIR, "unordered_pairs_per_launch": upairs}
+        if clk and clk.get("sm_mhz"):
+            roof["frac_at_sampled_clock"] = achieved / (sms * FP32_LANES_PER_SM * 2 * clk["sm_mhz"] * 1e6 / 1e12)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded mesh)",
+            "config": {"workload": WORKLOADS[args.workload], "nt": nt, "nv": nv, "mode": args.mode,
+                       "theta": args.theta if mode != tp.TP_DIRECT else None, "q": 6, "p": 12,
+                       "accumulation": "f64", "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "energy": energy, "gpu_launches": launches[0], "clocks": clk, "roofline": roof,
+            "ordered_pairs_per_eval": pairs}
+
+    if rank == 0 and not args.no_accuracy and mode == tp.TP_DIRECT:
+        # FP64 reference on the GPU (the FP64 kernel is pinned to the oracle by the tests)
+        g64 = torch.zeros_like(Vd)
+        e64 = tp.tp_gradient(ctx, g64, tp.tp_params_default(prec=tp.TP_F64))
+        line["accuracy"] = {"energy_rel_err_vs_f64": abs(energy - e64) / abs(e64),
+                            "grad_rel_l2_vs_f64": float(torch.linalg.norm(gd - g64) / torch.linalg.norm(g64)),
+                            "reference": "same mesh, FP64 pair terms and accumulation (TP_F64)"}
+
+    if not args.no_e2e:
+        # end to end through the public API with pinned host buffers
+        Vh = torch.tensor(V).pin_memory()
+        gh = torch.zeros(V.shape, dtype=torch.float64).pin_memory()
+        for _ in range(2):
+            tp.tp_mesh_upload(ctx, Vh, None, flags=_tp.TP_POSITIONS_ONLY)
+            tp.tp_gradient(ctx, gh, prm)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            tp.tp_mesh_upload(ctx, Vh, None, flags=_tp.TP_POSITIONS_ONLY)
+            if mode != tp.TP_DIRECT:
+                tp.tp_tree_build(ctx, 16, 30)
+            tp.tp_gradient(ctx, gh, prm)
+        torch.cuda.synchronize(dev)
+        t_e2e = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
+        if ws > 1:
+            tdist.all_reduce(t_e2e, op=tdist.ReduceOp.MAX)
+        line["e2e"] = {"value": ws * args.steps * pairs / float(t_e2e.item()), "unit": UNIT,
+                       "h2d_bytes_per_step": int(Vh.numel() * 8), "d2h_bytes_per_step": int(gh.numel() * 8 + 8)}
+
+    tp.tp_destroy(ctx)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = run_cpu_baseline(V, F, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        tdist.barrier()
+        tdist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

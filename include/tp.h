@@ -1,0 +1,156 @@
+/*
+ * tp.h - C ABI of the GB300 tangent-point energy library (libtp.so).
+ *
+ * The library evaluates the discrete tangent-point energy of a closed
+ * triangulated surface and its gradient with respect to the vertex
+ * positions (Porrmann, Bartels, Voigt, "Self-avoiding fluid deformable
+ * surfaces"):
+ *
+ *   Phi(X) = scale * sum_{(T,S) ordered, T != S, T and S share no vertex}
+ *                  w_T w_S |<nu_T, x_T - x_S>|^q / |x_T - x_S|^p
+ *
+ * x_T the centroid, nu_T the unit normal and w_T the area of flat triangle T.
+ * This is Eq. (TP) of Sec. 2.2.2 with alpha = q, 2 alpha = p (the paper uses
+ * alpha = 6, rho = 1e-4, i.e. scale = rho/alpha), discretised with one
+ * quadrature point per triangle.  The gradient is the exact derivative of
+ * this sum (the discrete counterpart of Eq. (dTP), Sec. 3.2).  The
+ * Barnes-Hut mode clusters the inner sum only (Sec. 3.2).
+ *
+ * Conventions for every call:
+ *  - Status codes are the only error channel; a failing call leaves the
+ *    context usable and stores a message readable with tp_last_error().
+ *  - All work is ordered on the CUDA stream given to tp_create().  Calls that
+ *    return a host scalar synchronise that stream.
+ *  - The library copies its inputs.  The caller owns every output buffer.
+ *  - Pointers flagged TP_DEVICE_PTR are device addresses on the context's
+ *    device; otherwise they are host addresses.
+ *  - A context is not thread-safe; use one per host thread.
+ */
+#ifndef TP_H
+#define TP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tp_ctx tp_ctx;
+
+typedef enum {
+    TP_OK = 0,
+    TP_E_ARG = 1,       /* invalid argument (null pointer, bad size, unsupported q/p ...) */
+    TP_E_CUDA = 2,      /* a CUDA runtime call failed                                    */
+    TP_E_STATE = 3,     /* no mesh uploaded, BH without a tree, LEARNED without a model  */
+    TP_E_NONFINITE = 4, /* degenerate triangle, non-finite vertex or coincident admitted
+                           centroids: the energy is +inf (finite only if embedded,
+                           Sec. 2.2.2)                                                   */
+    TP_E_TIMEOUT = 5,   /* a device-side bounded wait gave up                            */
+    TP_E_OOM = 6,       /* device allocation failed                                      */
+    TP_E_MODEL = 7      /* malformed far-field model file                                */
+} tp_status;
+
+typedef enum { TP_DIRECT = 0, TP_BH = 1, TP_LEARNED = 2 } tp_mode;
+typedef enum { TP_F32_F64ACC = 0, TP_F32_KAHAN = 1, TP_F64 = 2 } tp_prec;
+enum { TP_DTYPE_F32 = 0, TP_DTYPE_F64 = 1 };
+
+/* flags of tp_mesh_upload / tp_gradient */
+#define TP_DEVICE_PTR 0x1u      /* pointers are device addresses                       */
+#define TP_POSITIONS_ONLY 0x2u  /* re-upload V only; keep faces and derived topology   */
+/* flags of tp_params */
+#define TP_EXCLUDE_EDGE 0x4u    /* exclude only pairs sharing an edge (default: a vertex) */
+
+typedef struct {
+    int32_t q, p;   /* exponents: q even, p even; supported (6,12) and (8,16)       */
+    double scale;   /* prefactor c (rho/alpha in Eq. TP); 1.0 for the bare sum      */
+    int32_t mode;   /* tp_mode                                                      */
+    double theta;   /* opening parameter of TP_BH / TP_LEARNED (Sec. 3.2)           */
+    int32_t prec;   /* tp_prec                                                      */
+    uint32_t flags; /* TP_EXCLUDE_EDGE                                              */
+} tp_params;
+
+/* Fill *p with the defaults: q=6, p=12, scale=1, DIRECT, theta=0.25, F32_F64ACC. */
+void tp_params_default(tp_params* p);
+
+/* Create a context on `device` whose work is ordered on `cuda_stream`
+ * (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream; NULL is the
+ * legacy default stream).  *out receives the context; free with tp_destroy. */
+tp_status tp_create(tp_ctx** out, int device, void* cuda_stream);
+void tp_destroy(tp_ctx* ctx);
+
+/* Message of the last failing call on ctx (owned by ctx, valid until the next call). */
+const char* tp_last_error(const tp_ctx* ctx);
+
+/* Upload a mesh.  V: nv*3 coordinates (v_dtype TP_DTYPE_F32 or _F64, row-major
+ * [nv][3]); F: nt*3 int32 vertex indices, counter-clockwise seen from outside.
+ * Flags: TP_DEVICE_PTR (V and F are device pointers), TP_POSITIONS_ONLY (F
+ * is ignored and the previous connectivity is kept; nv must match).
+ * Computes the per-triangle data (centroids, normals, areas; Sec. 3.2: the
+ * data every quadrature point needs is cached contiguously) and orders the
+ * triangles along a Morton curve.  Degenerate triangles or non-finite
+ * coordinates give TP_E_NONFINITE.  Indices outside [0, nv) give TP_E_ARG. */
+tp_status tp_mesh_upload(tp_ctx* ctx, const void* V, int64_t nv, int v_dtype, const int32_t* F, int64_t nt,
+                         uint32_t flags);
+
+/* Build the cluster tree used by TP_BH and TP_LEARNED from the current
+ * positions: 30-bit Morton codes of the FP64 centroids (morton_bits must be
+ * a multiple of 3, at most 30), radix tree of the sorted (code, index) keys,
+ * cluster leaves of at most leaf_size triangles (1..32) and FP64 cluster
+ * moments (area, area-weighted centroid, first and second normal moments,
+ * vertex bounding box) - the "precomputed averages over a patch" of Sec. 3.2. */
+tp_status tp_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits);
+
+/* Energy Phi of the uploaded mesh; *energy_out (host) receives it. */
+tp_status tp_energy(tp_ctx* ctx, const tp_params* params, double* energy_out);
+
+/* Energy (optional: energy_out may be NULL) and gradient dPhi/dV.  grad_out
+ * receives nv*3 values of type g_dtype (TP_DTYPE_F32 / _F64), row-major like
+ * V; it is a device pointer when flags has TP_DEVICE_PTR, else host memory. */
+tp_status tp_gradient(tp_ctx* ctx, const tp_params* params, double* energy_out, void* grad_out, int g_dtype,
+                      uint32_t flags);
+
+/* Load the far-field network used by TP_LEARNED from a file written by
+ * tp_far_model_save (versioned header, then weights). */
+tp_status tp_far_model_load(tp_ctx* ctx, const char* path);
+
+/* ------------------------------------------------------------------ */
+/* Inspection entry points (host outputs, for tests and benchmarks)   */
+
+typedef struct {
+    int64_t nt, nv;
+    int64_t pairs_exact;   /* ordered pairs evaluated exactly in the last call        */
+    int64_t far_terms;     /* (target, cluster) far-field terms in the last call      */
+    int64_t far_pairs;     /* ordered pairs represented by those far terms            */
+    int64_t learned_terms; /* far terms evaluated by the network                       */
+    int64_t tile_pairs, tile_pairs_masked, tile_pairs_precise;
+    float ms_kernel;       /* device time of the dominant kernel of the last call      */
+    float ms_total;        /* device time of the whole last call                       */
+    int64_t kernel_launches; /* library kernels launched by the last call (CUDA library
+                                calls such as the radix sort are not counted)        */
+} tp_stats;
+
+tp_status tp_get_stats(const tp_ctx* ctx, tp_stats* out);
+
+/* Per-triangle data in the library's (Morton) order: perm[nt] original index,
+ * x[nt*3] f64 centroids, nu[nt*3] f64 normals, w[nt] f64 areas.  Any pointer may be NULL. */
+tp_status tp_debug_tri_data(tp_ctx* ctx, int32_t* perm, double* x, double* nu, double* w);
+
+/* Per-triangle derivatives of the last tp_gradient call, in ORIGINAL triangle
+ * order (without scale): gw[nt] = dPhi/dw_T, gnu[nt*3], gx[nt*3]. */
+tp_status tp_debug_accum(tp_ctx* ctx, double* gw, double* gnu, double* gx);
+
+/* The tree of the last tp_tree_build: codes[nt] (by original index),
+ * perm[nt], left/right[nt-1], first/last[2nt-1], leaves[*nleaves] (capacity nt),
+ * mom[(2nt-1)*13], box[(2nt-1)*6].  Any pointer may be NULL. */
+tp_status tp_debug_tree(tp_ctx* ctx, uint32_t* codes, int32_t* perm, int32_t* left, int32_t* right,
+                        int32_t* first, int32_t* last, int32_t* leaves, int64_t* nleaves, double* mom,
+                        double* box);
+
+/* Library version string. */
+const char* tp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TP_H */

@@ -1,0 +1,149 @@
+"""GB300 (sm_103a) tangent-point energy of closed triangle meshes.
+
+Phi(X) = c * sum over ordered pairs (T, S) of triangles sharing no vertex of
+w_T w_S |<nu_T, x_T - x_S>|^q / |x_T - x_S|^p  (Eq. TP, Sec. 2.2.2 of
+Porrmann, Bartels, Voigt, "Self-avoiding fluid deformable surfaces"), with its
+exact vertex gradient, evaluated by hand-written CUDA kernels behind the C ABI
+of ``include/tp.h``.
+
+``_tp`` is the ctypes binding (same names as the C entry points);
+:class:`TPEnergy` is the ``torch.autograd.Function`` whose backward calls
+``tp_gradient`` (which recomputes the pair geometry; nothing per pair is
+stored); :class:`TangentPointEnergy` owns a context for one mesh topology.
+``meshgen`` builds the seeded synthetic meshes.
+"""
+
+from __future__ import annotations
+
+from . import _tp
+from ._tp import (  # noqa: F401
+    TP_BH,
+    TP_DIRECT,
+    TP_F32_F64ACC,
+    TP_F64,
+    TP_LEARNED,
+    TPError,
+    tp_create,
+    tp_debug_accum,
+    tp_debug_tree,
+    tp_debug_tri_data,
+    tp_destroy,
+    tp_energy,
+    tp_far_model_load,
+    tp_get_stats,
+    tp_gradient,
+    tp_last_error,
+    tp_mesh_upload,
+    tp_params_default,
+    tp_tree_build,
+    tp_version,
+)
+
+__all__ = [
+    "TPEnergy",
+    "TangentPointEnergy",
+    "tp_create",
+    "tp_destroy",
+    "tp_mesh_upload",
+    "tp_tree_build",
+    "tp_energy",
+    "tp_gradient",
+    "tp_far_model_load",
+    "tp_get_stats",
+    "tp_params_default",
+]
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+class TangentPointEnergy:
+    """A library context bound to one mesh topology on one CUDA device.
+
+    ``params`` keyword arguments set the ``tp_params`` fields (q, p, scale,
+    mode, theta, prec, flags).  Positions are re-uploaded on every call; the
+    faces only when they change.
+    """
+
+    def __init__(self, F, device=0, stream=None, **params):
+        torch = _torch()
+        self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+        self.ctx = tp_create(self.device.index or 0, stream)
+        self.F = torch.as_tensor(F, dtype=torch.int32).to(self.device).contiguous()
+        self.params = tp_params_default(**params)
+        self._uploaded = False
+        self._tree = None
+
+    def close(self):
+        if self.ctx:
+            tp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def upload(self, V):
+        V = V.detach().contiguous()
+        if not self._uploaded:
+            tp_mesh_upload(self.ctx, V, self.F)
+            self._uploaded = True
+        else:
+            tp_mesh_upload(self.ctx, V, None, flags=_tp.TP_POSITIONS_ONLY)
+        if self.params.mode != TP_DIRECT:
+            tp_tree_build(self.ctx, 16, 30)
+
+    def energy(self, V):
+        self.upload(V)
+        return tp_energy(self.ctx, self.params)
+
+    def gradient(self, V, out=None):
+        self.upload(V)
+        torch = _torch()
+        g = out if out is not None else torch.empty_like(V)
+        e = tp_gradient(self.ctx, g, self.params)
+        return e, g
+
+    def __call__(self, V):
+        return TPEnergy.apply(V, self)
+
+
+def _make_function():
+    torch = _torch()
+
+    class _TPEnergy(torch.autograd.Function):
+        """Phi(V) with backward dPhi/dV from the hand-written adjoint kernel."""
+
+        @staticmethod
+        def forward(ctx, V, tpe):
+            e = tpe.energy(V)
+            ctx.tpe = tpe
+            ctx.save_for_backward(V)
+            return V.new_tensor(e)
+
+        @staticmethod
+        def backward(ctx, g):
+            (V,) = ctx.saved_tensors
+            _, grad = ctx.tpe.gradient(V)
+            return grad * g, None
+
+    return _TPEnergy
+
+
+class _LazyFunction:
+    _fn = None
+
+    def __getattr__(self, name):
+        if _LazyFunction._fn is None:
+            _LazyFunction._fn = _make_function()
+        return getattr(_LazyFunction._fn, name)
+
+
+TPEnergy = _LazyFunction()

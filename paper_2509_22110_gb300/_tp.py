@@ -1,0 +1,228 @@
+"""ctypes binding of ``libtp.so`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls (see
+``include/tp.h``) and does nothing but convert arguments: all arithmetic
+runs in the library's CUDA kernels.  A missing library is an error, never a
+fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtp.so")
+_lib = None
+
+TP_OK, TP_E_ARG, TP_E_CUDA, TP_E_STATE, TP_E_NONFINITE, TP_E_TIMEOUT, TP_E_OOM, TP_E_MODEL = range(8)
+TP_DIRECT, TP_BH, TP_LEARNED = 0, 1, 2
+TP_F32_F64ACC, TP_F32_KAHAN, TP_F64 = 0, 1, 2
+TP_DTYPE_F32, TP_DTYPE_F64 = 0, 1
+TP_DEVICE_PTR = 0x1
+TP_POSITIONS_ONLY = 0x2
+TP_EXCLUDE_EDGE = 0x4
+
+STATUS_NAMES = {
+    0: "TP_OK", 1: "TP_E_ARG", 2: "TP_E_CUDA", 3: "TP_E_STATE", 4: "TP_E_NONFINITE",
+    5: "TP_E_TIMEOUT", 6: "TP_E_OOM", 7: "TP_E_MODEL",
+}
+
+
+class TPError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class tp_params(C.Structure):
+    _fields_ = [("q", C.c_int32), ("p", C.c_int32), ("scale", C.c_double), ("mode", C.c_int32),
+                ("theta", C.c_double), ("prec", C.c_int32), ("flags", C.c_uint32)]
+
+
+class tp_stats(C.Structure):
+    _fields_ = [("nt", C.c_int64), ("nv", C.c_int64), ("pairs_exact", C.c_int64), ("far_terms", C.c_int64),
+                ("far_pairs", C.c_int64), ("learned_terms", C.c_int64), ("tile_pairs", C.c_int64),
+                ("tile_pairs_masked", C.c_int64), ("tile_pairs_precise", C.c_int64), ("ms_kernel", C.c_float),
+                ("ms_total", C.c_float), ("kernel_launches", C.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def lib():
+    """Load ``libtp.so``; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2509_22110_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i64, i32, u32 = C.c_void_p, C.c_int64, C.c_int, C.c_uint32
+    L.tp_params_default.argtypes = [C.POINTER(tp_params)]
+    L.tp_version.restype = C.c_char_p
+    L.tp_create.argtypes = [C.POINTER(vp), i32, vp]
+    L.tp_create.restype = i32
+    L.tp_destroy.argtypes = [vp]
+    L.tp_last_error.argtypes = [vp]
+    L.tp_last_error.restype = C.c_char_p
+    L.tp_mesh_upload.argtypes = [vp, vp, i64, i32, vp, i64, u32]
+    L.tp_mesh_upload.restype = i32
+    L.tp_tree_build.argtypes = [vp, i32, i32]
+    L.tp_tree_build.restype = i32
+    L.tp_energy.argtypes = [vp, C.POINTER(tp_params), C.POINTER(C.c_double)]
+    L.tp_energy.restype = i32
+    L.tp_gradient.argtypes = [vp, C.POINTER(tp_params), C.POINTER(C.c_double), vp, i32, u32]
+    L.tp_gradient.restype = i32
+    L.tp_far_model_load.argtypes = [vp, C.c_char_p]
+    L.tp_far_model_load.restype = i32
+    L.tp_get_stats.argtypes = [vp, C.POINTER(tp_stats)]
+    L.tp_get_stats.restype = i32
+    L.tp_debug_tri_data.argtypes = [vp, vp, vp, vp, vp]
+    L.tp_debug_tri_data.restype = i32
+    L.tp_debug_accum.argtypes = [vp, vp, vp, vp]
+    L.tp_debug_accum.restype = i32
+    L.tp_debug_tree.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, C.POINTER(C.c_int64), vp, vp]
+    L.tp_debug_tree.restype = i32
+    _lib = L
+    return L
+
+
+def _check(ctx, st):
+    if st != TP_OK:
+        msg = lib().tp_last_error(ctx)
+        raise TPError(st, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """(address, is_device) of a numpy array or torch tensor (contiguous)."""
+    if a is None:
+        return None, False
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, False
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), a.is_cuda
+    raise TypeError(type(a))
+
+
+def tp_version():
+    return lib().tp_version().decode()
+
+
+def tp_params_default(**kw):
+    p = tp_params()
+    lib().tp_params_default(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def tp_create(device=0, stream=None):
+    """Context handle on ``device`` ordered on ``stream`` (a cudaStream_t integer or None)."""
+    h = C.c_void_p()
+    st = lib().tp_create(C.byref(h), int(device), C.c_void_p(stream or 0))
+    if st != TP_OK:
+        raise TPError(st, "tp_create failed")
+    return h
+
+
+def tp_destroy(ctx):
+    if ctx:
+        lib().tp_destroy(ctx)
+
+
+def tp_last_error(ctx):
+    return lib().tp_last_error(ctx).decode()
+
+
+def tp_mesh_upload(ctx, V, F, flags=0):
+    """V [nv,3] float32/float64, F [nt,3] int32; numpy (host) or CUDA tensors (device)."""
+    pv, dv = _ptr(V)
+    pf, df = _ptr(F) if F is not None else (None, dv)
+    dtype = str(V.dtype)
+    if dtype.endswith("float64"):
+        vd = TP_DTYPE_F64
+    elif dtype.endswith("float32"):
+        vd = TP_DTYPE_F32
+    else:
+        raise TypeError(f"V must be float32 or float64, got {V.dtype}")
+    if F is not None and not str(F.dtype).endswith("int32"):
+        raise TypeError("F must be int32")
+    if F is not None and dv != df:
+        raise ValueError("V and F must both be host or both be device")
+    if dv:
+        flags |= TP_DEVICE_PTR
+    nv = V.shape[0]
+    nt = F.shape[0] if F is not None else 0
+    _check(ctx, lib().tp_mesh_upload(ctx, pv, nv, vd, pf, nt, flags))
+
+
+def tp_tree_build(ctx, leaf_size=16, morton_bits=30):
+    _check(ctx, lib().tp_tree_build(ctx, leaf_size, morton_bits))
+
+
+def tp_energy(ctx, params=None):
+    p = params or tp_params_default()
+    e = C.c_double(0.0)
+    _check(ctx, lib().tp_energy(ctx, C.byref(p), C.byref(e)))
+    return e.value
+
+
+def tp_gradient(ctx, grad_out, params=None, want_energy=True):
+    """Fill ``grad_out`` ([nv,3] float32/float64, host numpy or CUDA tensor); return the energy."""
+    p = params or tp_params_default()
+    pg, dg = _ptr(grad_out)
+    gd = TP_DTYPE_F64 if str(grad_out.dtype).endswith("float64") else TP_DTYPE_F32
+    e = C.c_double(0.0)
+    _check(ctx, lib().tp_gradient(ctx, C.byref(p), C.byref(e) if want_energy else None, pg, gd,
+                                  TP_DEVICE_PTR if dg else 0))
+    return e.value if want_energy else None
+
+
+def tp_far_model_load(ctx, path):
+    _check(ctx, lib().tp_far_model_load(ctx, os.fsencode(path)))
+
+
+def tp_get_stats(ctx):
+    s = tp_stats()
+    _check(ctx, lib().tp_get_stats(ctx, C.byref(s)))
+    return s.as_dict()
+
+
+def tp_debug_tri_data(ctx, nt):
+    perm = np.zeros(nt, dtype=np.int32)
+    x = np.zeros((nt, 3))
+    nu = np.zeros((nt, 3))
+    w = np.zeros(nt)
+    _check(ctx, lib().tp_debug_tri_data(ctx, perm.ctypes.data, x.ctypes.data, nu.ctypes.data, w.ctypes.data))
+    return perm, x, nu, w
+
+
+def tp_debug_accum(ctx, nt):
+    gw = np.zeros(nt)
+    gnu = np.zeros((nt, 3))
+    gx = np.zeros((nt, 3))
+    _check(ctx, lib().tp_debug_accum(ctx, gw.ctypes.data, gnu.ctypes.data, gx.ctypes.data))
+    return gw, gnu, gx
+
+
+def tp_debug_tree(ctx, nt):
+    nn = 2 * nt - 1
+    out = dict(codes=np.zeros(nt, np.uint32), perm=np.zeros(nt, np.int32), left=np.zeros(max(nt - 1, 1), np.int32),
+               right=np.zeros(max(nt - 1, 1), np.int32), first=np.zeros(nn, np.int32), last=np.zeros(nn, np.int32),
+               leaves=np.zeros(nt, np.int32), mom=np.zeros((nn, 13)), box=np.zeros((nn, 6)))
+    nl = C.c_int64(0)
+    _check(ctx, lib().tp_debug_tree(ctx, out["codes"].ctypes.data, out["perm"].ctypes.data, out["left"].ctypes.data,
+                                    out["right"].ctypes.data, out["first"].ctypes.data, out["last"].ctypes.data,
+                                    out["leaves"].ctypes.data, C.byref(nl), out["mom"].ctypes.data,
+                                    out["box"].ctypes.data))
+    out["leaves"] = out["leaves"][: nl.value]
+    out["left"] = out["left"][: nt - 1]
+    out["right"] = out["right"][: nt - 1]
+    return out

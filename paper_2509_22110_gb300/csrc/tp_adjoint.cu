@@ -1,0 +1,152 @@
+// tp_adjoint.cu - pull-back of the per-triangle derivatives to the vertices
+// and the FP64 reductions.
+//
+// The pair kernels leave, per triangle (library order), the accumulators
+// Ew, U, Gn[3], Gx[3] (each carrying the factor p/q) from which
+//     dPhi/dw_T  = Ew / ((p/q) w_T)
+//     dPhi/dnu_T = q Gn / (p/q)
+//     dPhi/dx_T  = q (Gx + U nu_T) / (p/q)
+// (without the prefactor c).  The map (v0, v1, v2) -> (x_T, nu_T, w_T) has
+//     x_T = (v0+v1+v2)/3,  N = e1 x e2 (e1 = v1-v0, e2 = v2-v0),
+//     w_T = |N|/2,  nu_T = N/|N|,
+// so with G = dPhi/dN = dPhi/dw nu/2 + (I - nu nu^T) dPhi/dnu / |N|:
+//     dPhi/dv1 = e2 x G + dPhi/dx/3,  dPhi/dv2 = G x e1 + dPhi/dx/3,
+//     dPhi/dv0 = -(e2 x G + G x e1) + dPhi/dx/3.
+// This is the discrete counterpart of Eq. (dTP), Sec. 3.2 (the variation
+// of the area element and of the normal under a vertex displacement).
+// One thread per vertex gathers its incident triangles from the CSR list
+// in a fixed order: deterministic, no atomics.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tp_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ void cross3(const double* a, const double* b, double* c) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+template <typename OutT>
+__global__ void k_adjoint(const double* __restrict__ V, const int32_t* __restrict__ F,
+                          const int32_t* __restrict__ off, const int32_t* __restrict__ v2t,
+                          const int32_t* __restrict__ iperm, const double* __restrict__ nu64,
+                          const double* __restrict__ w64, const double* __restrict__ acc, int64_t nv, int64_t nt,
+                          int64_t ntp, double q, double pq, double scale, OutT* __restrict__ grad) {
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    double g[3] = {0.0, 0.0, 0.0};
+    for (int32_t e = off[v]; e < off[v + 1]; ++e) {
+        const int32_t ent = v2t[e];
+        const int64_t T = ent >> 2;
+        const int corner = ent & 3;
+        const int64_t k = iperm[T];
+        const double w = w64[T];
+        double nu[3], gn[3], gx[3];
+        for (int a = 0; a < 3; ++a) nu[a] = nu64[a * nt + T];
+        const double Ew = acc[0 * ntp + k], U = acc[1 * ntp + k];
+        const double gw = Ew / (pq * w);
+        for (int a = 0; a < 3; ++a) {
+            gn[a] = q * acc[(2 + a) * ntp + k] / pq;
+            gx[a] = q * (acc[(5 + a) * ntp + k] + U * nu[a]) / pq;
+        }
+        const double* a0 = V + 3 * (int64_t)F[3 * T];
+        const double* a1 = V + 3 * (int64_t)F[3 * T + 1];
+        const double* a2 = V + 3 * (int64_t)F[3 * T + 2];
+        double e1[3], e2[3];
+        for (int a = 0; a < 3; ++a) {
+            e1[a] = a1[a] - a0[a];
+            e2[a] = a2[a] - a0[a];
+        }
+        const double len = 2.0 * w;
+        const double ndg = nu[0] * gn[0] + nu[1] * gn[1] + nu[2] * gn[2];
+        double G[3];
+        for (int a = 0; a < 3; ++a) G[a] = 0.5 * gw * nu[a] + (gn[a] - nu[a] * ndg) / len;
+        double c1[3], c2[3];
+        cross3(e2, G, c1);  // dPhi/de1
+        cross3(G, e1, c2);  // dPhi/de2
+        for (int a = 0; a < 3; ++a) {
+            double t = gx[a] / 3.0;
+            if (corner == 0) t -= c1[a] + c2[a];
+            else if (corner == 1) t += c1[a];
+            else t += c2[a];
+            g[a] += t;
+        }
+    }
+    for (int a = 0; a < 3; ++a) grad[3 * v + a] = (OutT)(scale * g[a]);
+}
+
+// deterministic two-pass sum of n doubles: fixed per-thread strides, fixed tree
+__global__ void k_sum_partial(const double* __restrict__ in, int64_t n, int64_t stride, double* __restrict__ part) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += in[i * stride];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_sum_final(const double* __restrict__ part, int nb, double mul, double* __restrict__ out) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = mul * sh[0];
+}
+
+}  // namespace
+
+tp_status tp_launch_adjoint(tp_ctx* ctx, const tp_params* prm, void* grad, int g_dtype) {
+    const int64_t nv = ctx->nv;
+    unsigned blocks = (unsigned)((nv + 255) / 256);
+    const double q = prm->q, pq = (double)prm->p / prm->q;
+    if (g_dtype == TP_DTYPE_F64)
+        k_adjoint<double><<<blocks, 256, 0, ctx->stream>>>(ctx->V64, ctx->F, ctx->v2t_off, ctx->v2t, ctx->iperm,
+                                                           ctx->nu64, ctx->w64, ctx->acc, nv, ctx->nt, ctx->ntp, q,
+                                                           pq, prm->scale, static_cast<double*>(grad));
+    else
+        k_adjoint<float><<<blocks, 256, 0, ctx->stream>>>(ctx->V64, ctx->F, ctx->v2t_off, ctx->v2t, ctx->iperm,
+                                                          ctx->nu64, ctx->w64, ctx->acc, nv, ctx->nt, ctx->ntp, q,
+                                                          pq, prm->scale, static_cast<float*>(grad));
+    ++ctx->nlaunch;
+    TP_CU(cudaGetLastError());
+    return TP_OK;
+}
+
+static tp_status reduce_strided(tp_ctx* ctx, const double* in, int64_t n, int64_t stride, double mul, double* d_out) {
+    const int nb = 512;
+    double* part = ctx->red + (ctx->red_cap - nb);
+    k_sum_partial<<<nb, 256, 0, ctx->stream>>>(in, n, stride, part);
+    ++ctx->nlaunch;
+    k_sum_final<<<1, 256, 0, ctx->stream>>>(part, nb, mul, d_out);
+    ++ctx->nlaunch;
+    TP_CU(cudaGetLastError());
+    return TP_OK;
+}
+
+// Phi = c * sum_T Ew_T / (2 p/q): every unordered pair adds (p/q)(e_TS + e_ST) to both ends.
+tp_status tp_launch_energy_from_acc(tp_ctx* ctx, const tp_params* prm, double* d_out) {
+    const double pq = (double)prm->p / prm->q;
+    return reduce_strided(ctx, ctx->acc, ctx->ntp, 1, prm->scale / (2.0 * pq), d_out);
+}
+
+tp_status tp_launch_reduce_sum(tp_ctx* ctx, const double* in, int64_t n, double* d_out) {
+    return reduce_strided(ctx, in, n, 1, 1.0, d_out);
+}
+
+tp_status tp_launch_check_finite(tp_ctx* ctx) {
+    (void)ctx;
+    return TP_OK;
+}

@@ -1,0 +1,564 @@
+// tp_capi.cu - the C ABI declared in include/tp.h and the host orchestration
+// behind it (buffers, kernel sequencing, error status).
+//
+// The calls follow the paper's statement of the problem: given the surface
+// (a parametrisation X, here the vertex positions of a flat triangle mesh)
+// return Phi(X) (Eq. TP, Sec. 2.2.2) and the variation dPhi/dX (Eq. dTP,
+// Sec. 3.2), either by the full double sum ("full integration", Sec. 3.2) or
+// with the inner integral clustered (Barnes-Hut, Sec. 3.2).
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+#include <vector>
+
+#include "tp_internal.cuh"
+
+#define TP_VERSION_STR "tpgpu 0.1 (sm_103a)"
+
+tp_status tp_set_err(tp_ctx* c, tp_status s, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+tp_status tp_cuda_check(tp_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return tp_set_err(c, TP_E_OOM, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return tp_set_err(c, TP_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+tp_status tp_alloc(tp_ctx* ctx, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return tp_set_err(ctx, TP_E_OOM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    ctx->allocs.push_back(*p);
+    return TP_OK;
+}
+
+void tp_free(tp_ctx* ctx, void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < ctx->allocs.size(); ++i)
+        if (ctx->allocs[i] == p) {
+            ctx->allocs[i] = ctx->allocs.back();
+            ctx->allocs.pop_back();
+            break;
+        }
+    cudaFree(p);
+}
+
+namespace {
+
+template <typename T>
+void free_ptr(tp_ctx* ctx, T*& p) {
+    tp_free(ctx, (void*)p);
+    p = nullptr;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+__global__ void k_f32_to_f64(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (double)a[i];
+}
+
+__global__ void k_check_finite_v(const double* __restrict__ V, int64_t n, unsigned* derr) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n && !isfinite(V[i])) tp_dev_error(derr, TP_DERR_NONFINITE);
+}
+
+tp_status check_params(tp_ctx* ctx, const tp_params* prm) {
+    if (!prm) return tp_set_err(ctx, TP_E_ARG, "params is NULL");
+    if (!((prm->q == 6 && prm->p == 12) || (prm->q == 8 && prm->p == 16)))
+        return tp_set_err(ctx, TP_E_ARG, "unsupported exponents q=%d p=%d (supported: 6/12, 8/16)", prm->q, prm->p);
+    if (prm->mode < TP_DIRECT || prm->mode > TP_LEARNED) return tp_set_err(ctx, TP_E_ARG, "bad mode %d", prm->mode);
+    if (prm->prec < TP_F32_F64ACC || prm->prec > TP_F64) return tp_set_err(ctx, TP_E_ARG, "bad prec %d", prm->prec);
+    if (!std::isfinite(prm->scale)) return tp_set_err(ctx, TP_E_ARG, "scale is not finite");
+    if (prm->mode != TP_DIRECT && !(prm->theta >= 0.0 && std::isfinite(prm->theta)))
+        return tp_set_err(ctx, TP_E_ARG, "theta must be finite and >= 0");
+    if (!ctx->have_mesh) return tp_set_err(ctx, TP_E_STATE, "no mesh uploaded");
+    if (prm->mode != TP_DIRECT && !ctx->tree.valid && ctx->nt > 0)
+        return tp_set_err(ctx, TP_E_STATE, "mode %d needs tp_tree_build first", prm->mode);
+    if (prm->mode == TP_LEARNED && !ctx->mlp) return tp_set_err(ctx, TP_E_STATE, "TP_LEARNED needs tp_far_model_load");
+    return TP_OK;
+}
+
+// read and clear the device error word; map to a status
+tp_status take_device_error(tp_ctx* ctx, const char* where) {
+    unsigned h = 0;
+    TP_CU(cudaMemcpyAsync(&h, ctx->derr, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+    TP_CU(cudaStreamSynchronize(ctx->stream));
+    if (!h) return TP_OK;
+    TP_CU(cudaMemsetAsync(ctx->derr, 0, sizeof(unsigned), ctx->stream));
+    if (h & TP_DERR_TIMEOUT) return tp_set_err(ctx, TP_E_TIMEOUT, "%s: a device-side wait timed out", where);
+    if (h & TP_DERR_INDEX) return tp_set_err(ctx, TP_E_ARG, "%s: face index outside [0, nv)", where);
+    if (h & TP_DERR_STACK) return tp_set_err(ctx, TP_E_CUDA, "%s: traversal stack overflow", where);
+    if (h & TP_DERR_NONFINITE)
+        return tp_set_err(ctx, TP_E_NONFINITE, "%s: degenerate triangle or non-finite coordinate", where);
+    return tp_set_err(ctx, TP_E_CUDA, "%s: device error 0x%x", where, h);
+}
+
+void release_mesh(tp_ctx* ctx) {
+    free_ptr(ctx, ctx->V64);
+    free_ptr(ctx, ctx->F);
+    free_ptr(ctx, ctx->v2t_off);
+    free_ptr(ctx, ctx->v2t);
+    free_ptr(ctx, ctx->x64);
+    free_ptr(ctx, ctx->nu64);
+    free_ptr(ctx, ctx->w64);
+    free_ptr(ctx, ctx->perm);
+    free_ptr(ctx, ctx->iperm);
+    free_ptr(ctx, ctx->codes);
+    free_ptr(ctx, ctx->codes_sorted);
+    free_ptr(ctx, ctx->idx_tmp);
+    free_ptr(ctx, ctx->soa);
+    free_ptr(ctx, ctx->src);
+    free_ptr(ctx, ctx->Fs);
+    free_ptr(ctx, ctx->acc);
+    free_ptr(ctx, ctx->red);
+    free_ptr(ctx, ctx->flagged);
+    free_ptr(ctx, ctx->mlist);
+    free_ptr(ctx, ctx->gradbuf);
+    free_ptr(ctx, ctx->vtmp);
+    tp_tree& t = ctx->tree;
+    free_ptr(ctx, t.codes);
+    free_ptr(ctx, t.left);
+    free_ptr(ctx, t.right);
+    free_ptr(ctx, t.parent);
+    free_ptr(ctx, t.first);
+    free_ptr(ctx, t.last);
+    free_ptr(ctx, t.leaves);
+    free_ptr(ctx, t.counter);
+    free_ptr(ctx, t.mom);
+    free_ptr(ctx, t.box);
+    free_ptr(ctx, t.nodef);
+    t.valid = false;
+    t.cap = 0;
+    ctx->cap_nv = ctx->cap_nt = 0;
+    ctx->have_mesh = false;
+}
+
+tp_status ensure_buffers(tp_ctx* ctx, int64_t nv, int64_t nt) {
+    const int64_t ntp = ((nt + TP_SUPER - 1) / TP_SUPER) * TP_SUPER;
+    const int64_t nsup = ntp / TP_SUPER;
+    if (nv <= ctx->cap_nv && nt <= ctx->cap_nt && ntp <= ctx->cap_ntp) {
+        ctx->ntp = ntp;
+        ctx->nsup = nsup;
+        return TP_OK;
+    }
+    release_mesh(ctx);
+    TP_TRY(tp_alloc_t(ctx, &ctx->V64, 3 * nv));
+    TP_TRY(tp_alloc_t(ctx, &ctx->vtmp, 3 * nv));
+    TP_TRY(tp_alloc_t(ctx, &ctx->gradbuf, 3 * nv));
+    TP_TRY(tp_alloc_t(ctx, &ctx->F, 3 * nt));
+    TP_TRY(tp_alloc_t(ctx, &ctx->v2t_off, nv + 1));
+    TP_TRY(tp_alloc_t(ctx, &ctx->v2t, 3 * nt));
+    TP_TRY(tp_alloc_t(ctx, &ctx->x64, 3 * nt));
+    TP_TRY(tp_alloc_t(ctx, &ctx->nu64, 3 * nt));
+    TP_TRY(tp_alloc_t(ctx, &ctx->w64, nt));
+    TP_TRY(tp_alloc_t(ctx, &ctx->perm, nt));
+    TP_TRY(tp_alloc_t(ctx, &ctx->iperm, nt));
+    TP_TRY(tp_alloc_t(ctx, &ctx->codes, nt));
+    TP_TRY(tp_alloc_t(ctx, &ctx->codes_sorted, nt));
+    TP_TRY(tp_alloc_t(ctx, &ctx->idx_tmp, std::max(nt, nv) + 1));
+    TP_TRY(tp_alloc_t(ctx, &ctx->soa, 10 * ntp));
+    TP_TRY(tp_alloc_t(ctx, &ctx->src, (int64_t)TP_SRCW * ntp));
+    TP_TRY(tp_alloc_t(ctx, &ctx->Fs, 3 * ntp));
+    TP_TRY(tp_alloc_t(ctx, &ctx->acc, (int64_t)TP_NACC * ntp));
+    ctx->red_cap = std::max<int64_t>(nt, 6 * 1024) + 4096;
+    TP_TRY(tp_alloc_t(ctx, &ctx->red, ctx->red_cap));
+    const int64_t nbits = nsup * nsup;
+    TP_TRY(tp_alloc_t(ctx, &ctx->flagged, (nbits + 31) / 32));
+    TP_TRY(tp_alloc_t(ctx, &ctx->mlist, nsup * (nsup + 1) / 2 + 1));
+    ctx->cap_nv = nv;
+    ctx->cap_nt = nt;
+    ctx->cap_ntp = ntp;
+    ctx->ntp = ntp;
+    ctx->nsup = nsup;
+    return TP_OK;
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.f;
+    }
+    return ms;
+}
+
+int64_t n_direct_pairs(const tp_ctx* ctx) {
+    // ordered pairs: nt (nt - 1) minus the excluded ones (computed on upload)
+    return ctx->nt * (ctx->nt - 1) - ctx->n_excluded_ordered;
+}
+
+}  // namespace
+
+extern "C" {
+
+void tp_params_default(tp_params* p) {
+    if (!p) return;
+    p->q = 6;
+    p->p = 12;
+    p->scale = 1.0;
+    p->mode = TP_DIRECT;
+    p->theta = 0.25;
+    p->prec = TP_F32_F64ACC;
+    p->flags = 0u;
+}
+
+const char* tp_version(void) { return TP_VERSION_STR; }
+
+tp_status tp_create(tp_ctx** out, int device, void* cuda_stream) {
+    if (!out) return TP_E_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return TP_E_CUDA;
+    }
+    if (device < 0 || device >= ndev) return TP_E_ARG;
+    DeviceGuard g(device);
+    tp_ctx* ctx = new tp_ctx();
+    ctx->device = device;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete ctx;
+        return TP_E_CUDA;
+    }
+    if (prop.major < 10) {
+        delete ctx;
+        return TP_E_CUDA;  // built for sm_103a only
+    }
+    ctx->num_sms = prop.multiProcessorCount;
+    for (int i = 0; i < 4; ++i) cudaEventCreate(&ctx->ev[i]);
+    if (tp_alloc_t(ctx, &ctx->derr, 4) != TP_OK || tp_alloc_t(ctx, &ctx->scalar, 8) != TP_OK ||
+        tp_alloc_t(ctx, &ctx->center, 3) != TP_OK || tp_alloc_t(ctx, &ctx->bounds, 6) != TP_OK ||
+        tp_alloc_t(ctx, &ctx->mcount, 4) != TP_OK) {
+        tp_destroy(ctx);
+        return TP_E_OOM;
+    }
+    cudaMemsetAsync(ctx->derr, 0, 4 * sizeof(unsigned), ctx->stream);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        tp_destroy(ctx);
+        return TP_E_CUDA;
+    }
+    *out = ctx;
+    return TP_OK;
+}
+
+void tp_destroy(tp_ctx* ctx) {
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    tp_mlp_release(ctx);
+    for (void* p : ctx->allocs) cudaFree(p);
+    ctx->allocs.clear();
+    for (int i = 0; i < 4; ++i)
+        if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    delete ctx;
+}
+
+const char* tp_last_error(const tp_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+tp_status tp_mesh_upload(tp_ctx* ctx, const void* V, int64_t nv, int v_dtype, const int32_t* F, int64_t nt,
+                         uint32_t flags) {
+    if (!ctx) return TP_E_ARG;
+    DeviceGuard g(ctx->device);
+    ctx->err.clear();
+    ctx->nlaunch = 0;
+    const bool dev = flags & TP_DEVICE_PTR;
+    const bool posonly = flags & TP_POSITIONS_ONLY;
+    if (v_dtype != TP_DTYPE_F32 && v_dtype != TP_DTYPE_F64) return tp_set_err(ctx, TP_E_ARG, "bad v_dtype %d", v_dtype);
+    if (nv < 0 || nt < 0) return tp_set_err(ctx, TP_E_ARG, "negative size");
+    if (nt >= (int64_t)1 << 30 || nv >= (int64_t)1 << 30) return tp_set_err(ctx, TP_E_ARG, "mesh too large");
+    if (posonly) {
+        if (!ctx->have_mesh) return tp_set_err(ctx, TP_E_STATE, "TP_POSITIONS_ONLY before a full upload");
+        if (nv != ctx->nv) return tp_set_err(ctx, TP_E_ARG, "TP_POSITIONS_ONLY with nv=%lld != %lld", (long long)nv,
+                                             (long long)ctx->nv);
+        nt = ctx->nt;
+    }
+    if (nv > 0 && !V) return tp_set_err(ctx, TP_E_ARG, "V is NULL");
+    if (!posonly && nt > 0 && !F) return tp_set_err(ctx, TP_E_ARG, "F is NULL");
+    if (!posonly) {
+        TP_TRY(ensure_buffers(ctx, std::max<int64_t>(nv, 1), std::max<int64_t>(nt, 1)));
+        ctx->nv = nv;
+        ctx->nt = nt;
+        ctx->ntp = ((nt + TP_SUPER - 1) / TP_SUPER) * TP_SUPER;
+        ctx->nsup = ctx->ntp / TP_SUPER;
+        ctx->tree.valid = false;
+        ctx->have_mesh = false;
+    }
+    cudaEventRecord(ctx->ev[2], ctx->stream);
+    // positions
+    const size_t vbytes = (size_t)(3 * nv) * (v_dtype == TP_DTYPE_F64 ? 8 : 4);
+    if (nv > 0) {
+        if (v_dtype == TP_DTYPE_F64) {
+            TP_CU(cudaMemcpyAsync(ctx->V64, V, vbytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  ctx->stream));
+        } else {
+            TP_CU(cudaMemcpyAsync(ctx->vtmp, V, vbytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  ctx->stream));
+            k_f32_to_f64<<<(unsigned)((3 * nv + 255) / 256), 256, 0, ctx->stream>>>(ctx->vtmp, ctx->V64, 3 * nv);
+            ++ctx->nlaunch;
+        }
+        k_check_finite_v<<<(unsigned)((3 * nv + 255) / 256), 256, 0, ctx->stream>>>(ctx->V64, 3 * nv, ctx->derr);
+        ++ctx->nlaunch;
+    }
+    if (!posonly && nt > 0)
+        TP_CU(cudaMemcpyAsync(ctx->F, F, (size_t)(3 * nt) * 4, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              ctx->stream));
+    if (nt > 0) {
+        TP_TRY(tp_launch_tri_data(ctx));
+        if (!posonly) {
+            TP_TRY(take_device_error(ctx, "tp_mesh_upload"));
+            TP_TRY(tp_build_v2t(ctx));
+            TP_TRY(tp_launch_morton_order(ctx, 30));
+        }
+        TP_TRY(tp_launch_sorted_soa(ctx));
+        if (!posonly) {
+            TP_TRY(tp_launch_flagged(ctx));
+            TP_TRY(tp_count_excluded(ctx));
+        }
+    }
+    cudaEventRecord(ctx->ev[3], ctx->stream);
+    TP_TRY(take_device_error(ctx, "tp_mesh_upload"));
+    ctx->have_mesh = true;
+    ctx->stats = tp_stats{};
+    ctx->stats.nt = nt;
+    ctx->stats.nv = nv;
+    ctx->stats.ms_total = elapsed(ctx->ev[2], ctx->ev[3]);
+    ctx->stats.kernel_launches = ctx->nlaunch;
+    return TP_OK;
+}
+
+tp_status tp_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits) {
+    if (!ctx) return TP_E_ARG;
+    DeviceGuard g(ctx->device);
+    ctx->err.clear();
+    if (!ctx->have_mesh) return tp_set_err(ctx, TP_E_STATE, "no mesh uploaded");
+    if (leaf_size < 1 || leaf_size > 32) return tp_set_err(ctx, TP_E_ARG, "leaf_size must be in [1, 32]");
+    if (morton_bits < 3 || morton_bits > 30 || morton_bits % 3) return tp_set_err(ctx, TP_E_ARG, "bad morton_bits");
+    if (ctx->nt == 0) {
+        ctx->tree.valid = true;
+        return TP_OK;
+    }
+    ctx->nlaunch = 0;
+    cudaEventRecord(ctx->ev[2], ctx->stream);
+    TP_TRY(tp_launch_tree_build(ctx, leaf_size, morton_bits));
+    cudaEventRecord(ctx->ev[3], ctx->stream);
+    TP_TRY(take_device_error(ctx, "tp_tree_build"));
+    ctx->tree.valid = true;
+    ctx->stats.ms_total = elapsed(ctx->ev[2], ctx->ev[3]);
+    ctx->stats.kernel_launches = ctx->nlaunch;
+    return TP_OK;
+}
+
+static tp_status run_eval(tp_ctx* ctx, const tp_params* prm, bool want_grad, void* grad_out, int g_dtype,
+                          uint32_t flags, double* energy_out) {
+    TP_TRY(check_params(ctx, prm));
+    const int64_t nt = ctx->nt, nv = ctx->nv;
+    ctx->stats = tp_stats{};
+    ctx->stats.nt = nt;
+    ctx->stats.nv = nv;
+    ctx->nlaunch = 0;
+    ctx->last_q = prm->q;
+    ctx->last_pq = (double)prm->p / prm->q;
+    const bool dev = flags & TP_DEVICE_PTR;
+    if (want_grad && g_dtype != TP_DTYPE_F32 && g_dtype != TP_DTYPE_F64)
+        return tp_set_err(ctx, TP_E_ARG, "bad g_dtype %d", g_dtype);
+    if (want_grad && nv > 0 && !grad_out) return tp_set_err(ctx, TP_E_ARG, "grad_out is NULL");
+    const size_t gbytes = (size_t)(3 * nv) * (g_dtype == TP_DTYPE_F64 ? 8 : 4);
+    if (nt == 0) {
+        if (energy_out) *energy_out = 0.0;
+        if (want_grad && nv > 0) {
+            if (dev) TP_CU(cudaMemsetAsync(grad_out, 0, gbytes, ctx->stream));
+            else memset(grad_out, 0, gbytes);
+            TP_CU(cudaStreamSynchronize(ctx->stream));
+        }
+        return TP_OK;
+    }
+    cudaEventRecord(ctx->ev[2], ctx->stream);
+    bool energy_from_acc = true;
+    if (prm->mode == TP_DIRECT) {
+        if (prm->prec == TP_F64) {
+            TP_TRY(tp_launch_direct_f64(ctx, prm, want_grad));
+            if (!want_grad) {
+                energy_from_acc = false;
+                TP_TRY(tp_launch_reduce_sum(ctx, ctx->red, nt, ctx->scalar + 1));
+            }
+        } else if (want_grad) {
+            TP_TRY(tp_launch_direct_grad(ctx, prm));
+        } else {
+            int nparts = 0;
+            TP_TRY(tp_launch_direct_energy(ctx, prm, ctx->red, &nparts));
+            TP_TRY(tp_launch_reduce_sum(ctx, ctx->red, nparts, ctx->scalar + 1));
+            energy_from_acc = false;
+        }
+        ctx->stats.pairs_exact = n_direct_pairs(ctx);
+        ctx->stats.tile_pairs = ctx->nsup * (ctx->nsup + 1) / 2;
+        ctx->stats.tile_pairs_masked = ctx->n_masked;
+    } else {
+        TP_TRY(tp_launch_bh(ctx, prm, prm->mode == TP_LEARNED));
+    }
+    double pq = (double)prm->p / prm->q;
+    if (energy_from_acc) {
+        TP_TRY(tp_launch_energy_from_acc(ctx, prm, ctx->scalar));
+    }
+    void* gdst = nullptr;
+    if (want_grad) {
+        gdst = dev ? grad_out : (void*)ctx->gradbuf;
+        TP_TRY(tp_launch_adjoint(ctx, prm, gdst, g_dtype));
+    }
+    cudaEventRecord(ctx->ev[3], ctx->stream);
+    double e = 0.0;
+    if (energy_from_acc) {
+        TP_CU(cudaMemcpyAsync(&e, ctx->scalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    } else {
+        TP_CU(cudaMemcpyAsync(&e, ctx->scalar + 1, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    if (want_grad && !dev && nv > 0)
+        TP_CU(cudaMemcpyAsync(grad_out, ctx->gradbuf, gbytes, cudaMemcpyDeviceToHost, ctx->stream));
+    TP_CU(cudaStreamSynchronize(ctx->stream));
+    TP_TRY(take_device_error(ctx, want_grad ? "tp_gradient" : "tp_energy"));
+    if (!energy_from_acc && prm->mode == TP_DIRECT) {
+        if (prm->prec == TP_F64) e = prm->scale * e;
+        else e = prm->scale * e / pq;
+    }
+    ctx->stats.ms_kernel = elapsed(ctx->ev[0], ctx->ev[1]);
+    ctx->stats.ms_total = elapsed(ctx->ev[2], ctx->ev[3]);
+    ctx->stats.kernel_launches = ctx->nlaunch;
+    if (energy_out) *energy_out = e;
+    if (!std::isfinite(e)) {
+        if (energy_out) *energy_out = INFINITY;
+        return tp_set_err(ctx, TP_E_NONFINITE,
+                          "energy is not finite: two admitted triangles have coincident centroids (not embedded)");
+    }
+    return TP_OK;
+}
+
+tp_status tp_energy(tp_ctx* ctx, const tp_params* params, double* energy_out) {
+    if (!ctx) return TP_E_ARG;
+    DeviceGuard g(ctx->device);
+    ctx->err.clear();
+    if (!energy_out) return tp_set_err(ctx, TP_E_ARG, "energy_out is NULL");
+    return run_eval(ctx, params, false, nullptr, TP_DTYPE_F64, 0u, energy_out);
+}
+
+tp_status tp_gradient(tp_ctx* ctx, const tp_params* params, double* energy_out, void* grad_out, int g_dtype,
+                      uint32_t flags) {
+    if (!ctx) return TP_E_ARG;
+    DeviceGuard g(ctx->device);
+    ctx->err.clear();
+    return run_eval(ctx, params, true, grad_out, g_dtype, flags, energy_out);
+}
+
+tp_status tp_get_stats(const tp_ctx* ctx, tp_stats* out) {
+    if (!ctx || !out) return TP_E_ARG;
+    *out = ctx->stats;
+    return TP_OK;
+}
+
+tp_status tp_debug_tri_data(tp_ctx* ctx, int32_t* perm, double* x, double* nu, double* w) {
+    if (!ctx) return TP_E_ARG;
+    DeviceGuard g(ctx->device);
+    if (!ctx->have_mesh) return tp_set_err(ctx, TP_E_STATE, "no mesh uploaded");
+    const int64_t nt = ctx->nt;
+    if (nt == 0) return TP_OK;
+    std::vector<int32_t> hp(nt);
+    std::vector<double> hx(3 * nt), hn(3 * nt), hw(nt);
+    TP_CU(cudaMemcpyAsync(hp.data(), ctx->perm, 4 * nt, cudaMemcpyDeviceToHost, ctx->stream));
+    TP_CU(cudaMemcpyAsync(hx.data(), ctx->x64, 24 * nt, cudaMemcpyDeviceToHost, ctx->stream));
+    TP_CU(cudaMemcpyAsync(hn.data(), ctx->nu64, 24 * nt, cudaMemcpyDeviceToHost, ctx->stream));
+    TP_CU(cudaMemcpyAsync(hw.data(), ctx->w64, 8 * nt, cudaMemcpyDeviceToHost, ctx->stream));
+    TP_CU(cudaStreamSynchronize(ctx->stream));
+    for (int64_t k = 0; k < nt; ++k) {
+        if (perm) perm[k] = hp[k];
+        int64_t T = hp[k];
+        for (int a = 0; a < 3; ++a) {
+            if (x) x[3 * k + a] = hx[a * nt + T];
+            if (nu) nu[3 * k + a] = hn[a * nt + T];
+        }
+        if (w) w[k] = hw[T];
+    }
+    return TP_OK;
+}
+
+tp_status tp_debug_accum(tp_ctx* ctx, double* gw, double* gnu, double* gx) {
+    if (!ctx) return TP_E_ARG;
+    DeviceGuard g(ctx->device);
+    if (!ctx->have_mesh) return tp_set_err(ctx, TP_E_STATE, "no mesh uploaded");
+    const int64_t nt = ctx->nt, ntp = ctx->ntp;
+    if (nt == 0) return TP_OK;
+    std::vector<double> acc((size_t)TP_NACC * ntp), hn(3 * nt), hw(nt);
+    std::vector<int32_t> ip(nt);
+    TP_CU(cudaMemcpyAsync(acc.data(), ctx->acc, 8 * TP_NACC * ntp, cudaMemcpyDeviceToHost, ctx->stream));
+    TP_CU(cudaMemcpyAsync(ip.data(), ctx->iperm, 4 * nt, cudaMemcpyDeviceToHost, ctx->stream));
+    TP_CU(cudaMemcpyAsync(hn.data(), ctx->nu64, 24 * nt, cudaMemcpyDeviceToHost, ctx->stream));
+    TP_CU(cudaMemcpyAsync(hw.data(), ctx->w64, 8 * nt, cudaMemcpyDeviceToHost, ctx->stream));
+    TP_CU(cudaStreamSynchronize(ctx->stream));
+    const double q = ctx->last_q, pq = ctx->last_pq;
+    for (int64_t T = 0; T < nt; ++T) {
+        int64_t k = ip[T];
+        if (gw) gw[T] = acc[k] / (pq * hw[T]);
+        for (int a = 0; a < 3; ++a) {
+            if (gnu) gnu[3 * T + a] = q * acc[(2 + a) * ntp + k] / pq;
+            if (gx) gx[3 * T + a] = q * (acc[(5 + a) * ntp + k] + acc[ntp + k] * hn[a * nt + T]) / pq;
+        }
+    }
+    return TP_OK;
+}
+
+tp_status tp_debug_tree(tp_ctx* ctx, uint32_t* codes, int32_t* perm, int32_t* left, int32_t* right, int32_t* first,
+                        int32_t* last, int32_t* leaves, int64_t* nleaves, double* mom, double* box) {
+    if (!ctx) return TP_E_ARG;
+    DeviceGuard g(ctx->device);
+    if (!ctx->tree.valid) return tp_set_err(ctx, TP_E_STATE, "no tree built");
+    const int64_t n = ctx->nt;
+    if (n == 0) return TP_OK;
+    const int64_t nn = 2 * n - 1;
+    tp_tree& t = ctx->tree;
+    if (codes) TP_CU(cudaMemcpyAsync(codes, ctx->codes, 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    if (perm) TP_CU(cudaMemcpyAsync(perm, ctx->perm, 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    if (left && n > 1) TP_CU(cudaMemcpyAsync(left, t.left, 4 * (n - 1), cudaMemcpyDeviceToHost, ctx->stream));
+    if (right && n > 1) TP_CU(cudaMemcpyAsync(right, t.right, 4 * (n - 1), cudaMemcpyDeviceToHost, ctx->stream));
+    if (first) TP_CU(cudaMemcpyAsync(first, t.first, 4 * nn, cudaMemcpyDeviceToHost, ctx->stream));
+    if (last) TP_CU(cudaMemcpyAsync(last, t.last, 4 * nn, cudaMemcpyDeviceToHost, ctx->stream));
+    if (leaves) TP_CU(cudaMemcpyAsync(leaves, t.leaves, 4 * t.nleaves, cudaMemcpyDeviceToHost, ctx->stream));
+    if (mom) TP_CU(cudaMemcpyAsync(mom, t.mom, 8 * 13 * nn, cudaMemcpyDeviceToHost, ctx->stream));
+    if (box) TP_CU(cudaMemcpyAsync(box, t.box, 8 * 6 * nn, cudaMemcpyDeviceToHost, ctx->stream));
+    TP_CU(cudaStreamSynchronize(ctx->stream));
+    if (nleaves) *nleaves = t.nleaves;
+    return TP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,842 @@
+// tp_direct.cu - direct all-pairs tangent-point energy and its per-triangle
+// derivatives (Eq. TP, Sec. 2.2.2; the "full integration" scheme of Sec. 3.2
+// with one centroid point per flat triangle).
+//
+// Symmetric scheme.  Each unordered pair {T,S} of admitted triangles is
+// evaluated once; both orderings are formed from the shared geometry
+//     d = x_T - x_S,  r2 = |d|^2,  inv = 1/r2,  a = nu_T.d,  b = nu_S.d,
+//     al = a*inv, be = b*inv   (so al^6 = a^6/r^12: no overflow of r^-12)
+//     s6 = al^6 + be^6,  wts = w~_T w~_S  (w~ = sqrt(p/q) w, p = 2q)
+//     E = wts s6 = (p/q)(e_TS + e_ST),  A5 = wts inv al^5,  B5 = wts inv be^5,
+//     k = wts inv s6
+// and added to per-triangle accumulators (all carrying the factor p/q):
+//     T: Ew += E, U += A5, Gn += A5 d, Gx += B5 nu_S - k d
+//     S: Ew += E, U -= B5, Gn += B5 d, Gx += -A5 nu_T + k d
+// from which dPhi/dw = Ew/((p/q) w), dPhi/dnu = q Gn/(p/q),
+// dPhi/dx = q (Gx + U nu)/(p/q) (exact chain rule of the discrete sum; the
+// two-sided accumulation is the discrete counterpart of the reordered
+// variation Eq. (dTP_reordered), Sec. 3.2).  Written for q = 6, p = 12 and
+// q = 8, p = 16.
+//
+// Work decomposition.  Triangles are in Morton order, padded to super-tiles
+// of 1024.  A work item is a super-tile pair (I <= J).  A persistent block
+// (8 warps, one per SM) keeps the 1024 targets of I in registers (each lane
+// 2 packed pairs of consecutive targets, FP32x2 arithmetic) and streams the
+// 1024 sources of J through shared memory in chunks of 128 with
+// cp.async.bulk (TMA bulk copies, completion on an mbarrier, bounded
+// waits).  Per source every lane adds its 4 pair contributions to packed
+// target accumulators; the source contributions of the warp are reduced by
+// a butterfly transpose (8 values over 32 lanes in 9 shuffles) and written
+// once per warp; per chunk the block sums its 8 warps and promotes to FP64
+// with one global atomic add per source and accumulator.  Target partials
+// (FP32 over one super-tile) are promoted to FP64 in shared memory and
+// flushed when the block moves to another target row.
+//
+// Pairs of super-tiles that contain a pair of triangles sharing a vertex
+// (and all diagonal items) are "masked" items, processed by the MASKED
+// instantiation, which tests adjacency per pair.  All other items are
+// branch-free.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tp_internal.cuh"
+
+namespace {
+
+constexpr int WARPS = 8;
+constexpr int THREADS = WARPS * 32;
+constexpr int NCHUNK = TP_SUPER / TP_CHUNK;  // chunks per super-tile
+constexpr int SMEM_TACC = TP_NACC * TP_SUPER * 8;        // 64 KB
+constexpr int SMEM_SACC = WARPS * TP_CHUNK * TP_NACC * 4;  // 32 KB
+constexpr int CHUNK_BYTES = TP_CHUNK * TP_SRCW * 4;        // 10 KB
+constexpr int SMEM_GRAD = SMEM_TACC + SMEM_SACC + 2 * CHUNK_BYTES + 64;
+constexpr int SMEM_ENERGY = 2 * CHUNK_BYTES + 64 + WARPS * 8;
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ------------------------------------------------------------ TMA bulk + mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: true when the phase completed, false after TP_SPIN_LIMIT polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < TP_SPIN_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+struct DirectArgs {
+    const float* soa;     // 10 planes of ntp: x_hi[3], x_lo[3], nu[3], w~
+    const float* src;     // [ntp][TP_SRCW]
+    const int32_t* Fs;    // [ntp][3]
+    double* acc;          // [TP_NACC][ntp]
+    const unsigned* flagged;  // bitmap nsup*nsup
+    const int32_t* mlist; // masked items (I << 16 | J)
+    int64_t nmasked;
+    int64_t ntp;
+    int nsup;
+    int edge_only;
+    unsigned* derr;
+    double* partial;      // per-block energy partials (energy kernel)
+};
+
+// item index <-> (I, J), I <= J, row-major over I
+struct ItemIter {
+    int I, J, n;
+    __device__ void set(int64_t idx, int nsup) {
+        n = nsup;
+        int i = 0;
+        int64_t off = 0;
+        // rows have n-i items; a short loop (nsup is at most a few thousand)
+        while (off + (n - i) <= idx) {
+            off += n - i;
+            ++i;
+        }
+        I = i;
+        J = i + (int)(idx - off);
+    }
+    __device__ void next() {
+        if (++J >= n) {
+            ++I;
+            J = I;
+        }
+    }
+};
+
+__device__ __forceinline__ bool item_flagged(const unsigned* bm, int nsup, int I, int J) {
+    int64_t bit = (int64_t)I * nsup + J;
+    return (bm[bit >> 5] >> (bit & 31)) & 1u;
+}
+
+struct SrcRec {
+    float2 h[3], l[3], n[3], w;
+};
+
+__device__ __forceinline__ void load_src(const float* rec, SrcRec& s) {
+    const float4* r = reinterpret_cast<const float4*>(rec);
+    float4 a = r[0], b = r[1], c = r[2], d = r[3], e = r[4];
+    s.h[0] = make_float2(a.x, a.y);
+    s.h[1] = make_float2(a.z, a.w);
+    s.h[2] = make_float2(b.x, b.y);
+    s.l[0] = make_float2(b.z, b.w);
+    s.l[1] = make_float2(c.x, c.y);
+    s.l[2] = make_float2(c.z, c.w);
+    s.n[0] = make_float2(d.x, d.y);
+    s.n[1] = make_float2(d.z, d.w);
+    s.n[2] = make_float2(e.x, e.y);
+    s.w = make_float2(e.z, e.w);
+}
+
+struct TgtPair {
+    float2 h[3], l[3], n[3], w;
+};
+
+__device__ __forceinline__ void load_tgt(const float* soa, int64_t ntp, int64_t t0, TgtPair& t) {
+    // t0 even: (t0, t0+1) from each plane as one float2
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        t.h[k] = *reinterpret_cast<const float2*>(soa + (0 + k) * ntp + t0);
+        t.l[k] = *reinterpret_cast<const float2*>(soa + (3 + k) * ntp + t0);
+        t.n[k] = *reinterpret_cast<const float2*>(soa + (6 + k) * ntp + t0);
+    }
+    t.w = *reinterpret_cast<const float2*>(soa + 9 * ntp + t0);
+}
+
+struct Acc8 {
+    float2 v[TP_NACC];  // Ew, U, Gn[3], Gx[3]
+};
+
+template <int Q>
+__device__ __forceinline__ float2 powq_m1(float2 x, float2& xq) {
+    // returns x^(Q-1), sets xq = x^Q (Q even: 6 or 8)
+    float2 x2 = mul2(x, x);
+    float2 x4 = mul2(x2, x2);
+    if (Q == 6) {
+        xq = mul2(x4, x2);
+        return mul2(x4, x);
+    } else {
+        float2 x8 = mul2(x4, x4);
+        xq = x8;
+        return mul2(mul2(x4, x2), x);
+    }
+}
+
+// One packed evaluation: target pair t against one source s (both halves share s).
+// valid_mask: per half, 1.0 admitted, 0.0 excluded (MASKED only).
+template <int Q, bool MASKED>
+__device__ __forceinline__ void pair_grad(const TgtPair& t, const SrcRec& s, Acc8& at, Acc8& as, float2 valid) {
+    float2 d[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = add2(add2(t.h[k], neg2(s.h[k])), add2(t.l[k], neg2(s.l[k])));
+    float2 r2 = mul2(d[0], d[0]);
+    r2 = fma2(d[1], d[1], r2);
+    r2 = fma2(d[2], d[2], r2);
+    float2 inv = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+    float2 wts = mul2(t.w, s.w);
+    if (MASKED) {
+        inv = make_float2(valid.x != 0.f ? inv.x : 0.f, valid.y != 0.f ? inv.y : 0.f);
+        wts = mul2(wts, valid);
+    }
+    float2 a = mul2(t.n[0], d[0]);
+    a = fma2(t.n[1], d[1], a);
+    a = fma2(t.n[2], d[2], a);
+    float2 b = mul2(s.n[0], d[0]);
+    b = fma2(s.n[1], d[1], b);
+    b = fma2(s.n[2], d[2], b);
+    float2 al = mul2(a, inv), be = mul2(b, inv);
+    float2 alq, beq;
+    float2 al5 = powq_m1<Q>(al, alq);
+    float2 be5 = powq_m1<Q>(be, beq);
+    float2 s6 = add2(alq, beq);
+    float2 E = mul2(wts, s6);
+    float2 wi = mul2(wts, inv);
+    float2 A5 = mul2(wi, al5);
+    float2 B5 = mul2(wi, be5);
+    float2 nk = neg2(mul2(wi, s6));
+    // target side
+    at.v[0] = add2(at.v[0], E);
+    at.v[1] = add2(at.v[1], A5);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        at.v[2 + k] = fma2(A5, d[k], at.v[2 + k]);
+        at.v[5 + k] = fma2(nk, d[k], fma2(B5, s.n[k], at.v[5 + k]));
+    }
+    // source side
+    as.v[0] = add2(as.v[0], E);
+    as.v[1] = add2(as.v[1], neg2(B5));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        as.v[2 + k] = fma2(B5, d[k], as.v[2 + k]);
+        as.v[5 + k] = fma2(neg2(nk), d[k], fma2(neg2(A5), t.n[k], as.v[5 + k]));
+    }
+}
+
+// Energy only: returns w~_S * s6 per half (the caller multiplies by w~_T at the end).
+template <int Q, bool MASKED>
+__device__ __forceinline__ float2 pair_energy(const TgtPair& t, const SrcRec& s, float2 valid) {
+    float2 d[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = add2(add2(t.h[k], neg2(s.h[k])), add2(t.l[k], neg2(s.l[k])));
+    float2 r2 = mul2(d[0], d[0]);
+    r2 = fma2(d[1], d[1], r2);
+    r2 = fma2(d[2], d[2], r2);
+    float2 inv = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+    float2 ws = s.w;
+    if (MASKED) {
+        inv = make_float2(valid.x != 0.f ? inv.x : 0.f, valid.y != 0.f ? inv.y : 0.f);
+        ws = mul2(ws, valid);
+    }
+    float2 a = mul2(t.n[0], d[0]);
+    a = fma2(t.n[1], d[1], a);
+    a = fma2(t.n[2], d[2], a);
+    float2 b = mul2(s.n[0], d[0]);
+    b = fma2(s.n[1], d[1], b);
+    b = fma2(s.n[2], d[2], b);
+    float2 al = mul2(a, inv), be = mul2(b, inv);
+    float2 alq, beq;
+    powq_m1<Q>(al, alq);
+    powq_m1<Q>(be, beq);
+    return mul2(ws, add2(alq, beq));
+}
+
+// Butterfly transpose-reduction of 8 per-lane values over the warp.  On
+// return every lane holds the warp total of component ((lane >> 2) & 7).
+__device__ __forceinline__ float warp_transpose_reduce8(float v[8], int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    float u[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float send = b4 ? v[i] : v[i + 4];
+        float keep = b4 ? v[i + 4] : v[i];
+        u[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float w2[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        float send = b3 ? u[i] : u[i + 2];
+        float keep = b3 ? u[i + 2] : u[i];
+        w2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float send = b2 ? w2[0] : w2[1];
+    float keep = b2 ? w2[1] : w2[0];
+    float r = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    r += __shfl_xor_sync(0xffffffffu, r, 2);
+    r += __shfl_xor_sync(0xffffffffu, r, 1);
+    return r;
+}
+
+__device__ __forceinline__ bool share_vertex(int3 a, int3 b, int edge_only) {
+    int k = (a.x == b.x) + (a.x == b.y) + (a.x == b.z) + (a.y == b.x) + (a.y == b.y) + (a.y == b.z) +
+            (a.z == b.x) + (a.z == b.y) + (a.z == b.z);
+    return edge_only ? (k >= 2) : (k >= 1);
+}
+
+__device__ __forceinline__ int3 load_face(const int32_t* Fs, int64_t k) {
+    return make_int3(Fs[3 * k], Fs[3 * k + 1], Fs[3 * k + 2]);
+}
+
+// ------------------------------------------------------------ gradient kernel
+template <int Q, bool MASKED>
+__global__ void __launch_bounds__(THREADS, 1) k_pairs_grad(DirectArgs A, int64_t item_lo, int64_t item_hi_total) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    double* tacc = reinterpret_cast<double*>(smem);                           // [8][1024]
+    float* sacc = reinterpret_cast<float*>(smem + SMEM_TACC);                 // [WARPS][CHUNK][8]
+    float* chunk = reinterpret_cast<float*>(smem + SMEM_TACC + SMEM_SACC);    // [2][CHUNK][SRCW]
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + SMEM_TACC + SMEM_SACC + 2 * CHUNK_BYTES);
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t ntp = A.ntp;
+
+    // static split of this kernel's item range over the blocks
+    const int64_t total = item_hi_total;
+    const int64_t lo = item_lo + (total * blockIdx.x) / gridDim.x;
+    const int64_t hi = item_lo + (total * (blockIdx.x + 1)) / gridDim.x;
+    if (lo >= hi) return;
+
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        mbar_fence_init();
+        s_abort = 0;
+    }
+    for (int i = tid; i < TP_NACC * TP_SUPER; i += THREADS) tacc[i] = 0.0;
+    __syncthreads();
+
+    // item sequence of this block: masked list entries, or triangular indices
+    // with flagged items skipped
+    auto item_at = [&](int64_t idx, int& I, int& J) {
+        int32_t e = A.mlist[idx];
+        I = e >> 16;
+        J = e & 0xffff;
+    };
+    ItemIter it;
+    int64_t idx = lo;
+    int curI = -1, curJ = -1;
+    // find first valid item
+    if (MASKED) {
+        item_at(idx, curI, curJ);
+    } else {
+        it.set(idx, A.nsup);
+        while (idx < hi && item_flagged(A.flagged, A.nsup, it.I, it.J)) {
+            ++idx;
+            it.next();
+        }
+        if (idx >= hi) return;  // uniform across the block
+        curI = it.I;
+        curJ = it.J;
+    }
+
+    // producer state (thread 0 issues loads; every thread tracks phases)
+    uint32_t phase[2] = {0u, 0u};
+    int64_t g = 0;  // global chunk counter of this block
+    // the next chunk to load: (item idx, I, J, chunk c)
+    int64_t nidx = idx;
+    int nI = curI, nJ = curJ, nc = 0;
+    ItemIter nit = it;
+    auto advance_next = [&]() {
+        if (++nc >= NCHUNK) {
+            nc = 0;
+            if (MASKED) {
+                ++nidx;
+                if (nidx < hi) item_at(nidx, nI, nJ);
+            } else {
+                ++nidx;
+                nit.next();
+                while (nidx < hi && item_flagged(A.flagged, A.nsup, nit.I, nit.J)) {
+                    ++nidx;
+                    nit.next();
+                }
+                nI = nit.I;
+                nJ = nit.J;
+            }
+        }
+    };
+    auto issue = [&](int buf) {
+        if (nidx < hi) {
+            const float* srcp = A.src + ((int64_t)nJ * TP_SUPER + (int64_t)nc * TP_CHUNK) * TP_SRCW;
+            mbar_expect_tx(&mbar[buf], CHUNK_BYTES);
+            tma_load_1d(chunk + buf * TP_CHUNK * TP_SRCW, srcp, CHUNK_BYTES, &mbar[buf]);
+        }
+    };
+    if (tid == 0) issue(0);
+    advance_next();
+
+    // targets of the current row
+    TgtPair tp[2];
+    int rowI = -1;
+    const int pbase = warp * 64 + lane;  // pair index within the super-tile: pbase, pbase+32
+
+    while (idx < hi) {
+        const int I = curI, J = curJ;
+        if (I != rowI) {
+            // flush FP64 target accumulators of the previous row
+            if (rowI >= 0) {
+                __syncthreads();
+                for (int i = tid; i < TP_NACC * TP_SUPER; i += THREADS) {
+                    int c = i / TP_SUPER, t = i % TP_SUPER;
+                    double v = tacc[i];
+                    if (v != 0.0) atomicAdd(&A.acc[c * ntp + (int64_t)rowI * TP_SUPER + t], v);
+                    tacc[i] = 0.0;
+                }
+                __syncthreads();
+            }
+            rowI = I;
+#pragma unroll
+            for (int P = 0; P < 2; ++P) load_tgt(A.soa, ntp, (int64_t)I * TP_SUPER + 2 * (pbase + 32 * P), tp[P]);
+        }
+        int3 tf[2][2];
+        int64_t tg[2][2];
+        if (MASKED) {
+#pragma unroll
+            for (int P = 0; P < 2; ++P)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    tg[P][h] = (int64_t)I * TP_SUPER + 2 * (pbase + 32 * P) + h;
+                    tf[P][h] = load_face(A.Fs, tg[P][h]);
+                }
+        }
+        Acc8 at[2];
+#pragma unroll
+        for (int P = 0; P < 2; ++P)
+#pragma unroll
+            for (int c = 0; c < TP_NACC; ++c) at[P].v[c] = make_float2(0.f, 0.f);
+
+        for (int c = 0; c < NCHUNK; ++c, ++g) {
+            const int buf = (int)(g & 1);
+            bool ok = mbar_wait_bounded(&mbar[buf], phase[buf]);
+            phase[buf] ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) tp_dev_error(A.derr, TP_DERR_TIMEOUT);
+                return;
+            }
+            if (tid == 0) issue(buf ^ 1);
+            advance_next();
+            const float* cb = chunk + buf * TP_CHUNK * TP_SRCW;
+            const int64_t sbase = (int64_t)J * TP_SUPER + (int64_t)c * TP_CHUNK;
+#pragma unroll 1
+            for (int s = 0; s < TP_CHUNK; ++s) {
+                SrcRec sr;
+                load_src(cb + s * TP_SRCW, sr);
+                Acc8 as;
+#pragma unroll
+                for (int k = 0; k < TP_NACC; ++k) as.v[k] = make_float2(0.f, 0.f);
+                float2 valid[2] = {make_float2(1.f, 1.f), make_float2(1.f, 1.f)};
+                if (MASKED) {
+                    const int64_t sg = sbase + s;
+                    int3 sf = load_face(A.Fs, sg);
+#pragma unroll
+                    for (int P = 0; P < 2; ++P) {
+                        float v0 = ((I != J || sg > tg[P][0]) && !share_vertex(tf[P][0], sf, A.edge_only)) ? 1.f : 0.f;
+                        float v1 = ((I != J || sg > tg[P][1]) && !share_vertex(tf[P][1], sf, A.edge_only)) ? 1.f : 0.f;
+                        valid[P] = make_float2(v0, v1);
+                    }
+                }
+#pragma unroll
+                for (int P = 0; P < 2; ++P) pair_grad<Q, MASKED>(tp[P], sr, at[P], as, valid[P]);
+                float v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v[k] = as.v[k].x + as.v[k].y;
+                float r = warp_transpose_reduce8(v, lane);
+                if ((lane & 3) == 0) sacc[(warp * TP_CHUNK + s) * TP_NACC + ((lane >> 2) & 7)] = r;
+            }
+            __syncthreads();
+            // sum the warps' source partials of this chunk and promote to FP64
+            for (int i = tid; i < TP_CHUNK * TP_NACC; i += THREADS) {
+                float ssum = 0.f;
+#pragma unroll
+                for (int w = 0; w < WARPS; ++w) ssum += sacc[w * TP_CHUNK * TP_NACC + i];
+                int s = i / TP_NACC, comp = i % TP_NACC;
+                if (ssum != 0.f) atomicAdd(&A.acc[comp * ntp + sbase + s], (double)ssum);
+            }
+            __syncthreads();
+        }
+        // promote the row's FP32 target partials of this item to FP64
+#pragma unroll
+        for (int P = 0; P < 2; ++P) {
+            const int t0 = 2 * (pbase + 32 * P);
+#pragma unroll
+            for (int k = 0; k < TP_NACC; ++k) {
+                tacc[k * TP_SUPER + t0] += (double)at[P].v[k].x;
+                tacc[k * TP_SUPER + t0 + 1] += (double)at[P].v[k].y;
+            }
+        }
+        // next item
+        ++idx;
+        if (MASKED) {
+            if (idx < hi) item_at(idx, curI, curJ);
+        } else {
+            it.next();
+            while (idx < hi && item_flagged(A.flagged, A.nsup, it.I, it.J)) {
+                ++idx;
+                it.next();
+            }
+            curI = it.I;
+            curJ = it.J;
+        }
+    }
+    __syncthreads();
+    if (rowI >= 0) {
+        for (int i = tid; i < TP_NACC * TP_SUPER; i += THREADS) {
+            int c = i / TP_SUPER, t = i % TP_SUPER;
+            double v = tacc[i];
+            if (v != 0.0) atomicAdd(&A.acc[c * ntp + (int64_t)rowI * TP_SUPER + t], v);
+        }
+    }
+}
+
+// ------------------------------------------------------------ energy kernel
+// Same item decomposition; every lane accumulates sum_S w~_S s6 for its 4
+// targets in FP32 per item, promoted to FP64 per item; the block writes one
+// FP64 partial (deterministic final reduction on the host side of the call).
+template <int Q, bool MASKED>
+__global__ void __launch_bounds__(THREADS, 1) k_pairs_energy(DirectArgs A, int64_t item_lo, int64_t item_hi_total,
+                                                             int partial_off) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    float* chunk = reinterpret_cast<float*>(smem);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * CHUNK_BYTES);
+    double* wsum = reinterpret_cast<double*>(smem + 2 * CHUNK_BYTES + 64);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t ntp = A.ntp;
+    const int64_t total = item_hi_total;
+    const int64_t lo = item_lo + (total * blockIdx.x) / gridDim.x;
+    const int64_t hi = item_lo + (total * (blockIdx.x + 1)) / gridDim.x;
+    double esum = 0.0;
+
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    auto item_at = [&](int64_t idx, int& I, int& J) {
+        int32_t e = A.mlist[idx];
+        I = e >> 16;
+        J = e & 0xffff;
+    };
+    ItemIter it;
+    int64_t idx = lo;
+    int curI = -1, curJ = -1;
+    bool any = lo < hi;
+    if (any) {
+        if (MASKED) {
+            item_at(idx, curI, curJ);
+        } else {
+            it.set(idx, A.nsup);
+            while (idx < hi && item_flagged(A.flagged, A.nsup, it.I, it.J)) {
+                ++idx;
+                it.next();
+            }
+            curI = it.I;
+            curJ = it.J;
+        }
+    }
+    uint32_t phase[2] = {0u, 0u};
+    int64_t g = 0;
+    int64_t nidx = idx;
+    int nI = curI, nJ = curJ, nc = 0;
+    ItemIter nit = it;
+    auto advance_next = [&]() {
+        if (++nc >= NCHUNK) {
+            nc = 0;
+            ++nidx;
+            if (MASKED) {
+                if (nidx < hi) item_at(nidx, nI, nJ);
+            } else {
+                nit.next();
+                while (nidx < hi && item_flagged(A.flagged, A.nsup, nit.I, nit.J)) {
+                    ++nidx;
+                    nit.next();
+                }
+                nI = nit.I;
+                nJ = nit.J;
+            }
+        }
+    };
+    auto issue = [&](int buf) {
+        if (nidx < hi) {
+            const float* srcp = A.src + ((int64_t)nJ * TP_SUPER + (int64_t)nc * TP_CHUNK) * TP_SRCW;
+            mbar_expect_tx(&mbar[buf], CHUNK_BYTES);
+            tma_load_1d(chunk + buf * TP_CHUNK * TP_SRCW, srcp, CHUNK_BYTES, &mbar[buf]);
+        }
+    };
+    if (idx < hi) {
+        if (tid == 0) issue(0);
+        advance_next();
+    }
+    const int pbase = warp * 64 + lane;
+    bool aborted = false;
+    while (idx < hi) {
+        const int I = curI, J = curJ;
+        TgtPair tp[2];
+        int3 tf[2][2];
+        int64_t tg[2][2];
+#pragma unroll
+        for (int P = 0; P < 2; ++P) {
+            load_tgt(A.soa, ntp, (int64_t)I * TP_SUPER + 2 * (pbase + 32 * P), tp[P]);
+            if (MASKED) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    tg[P][h] = (int64_t)I * TP_SUPER + 2 * (pbase + 32 * P) + h;
+                    tf[P][h] = load_face(A.Fs, tg[P][h]);
+                }
+            }
+        }
+        float2 ea[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        for (int c = 0; c < NCHUNK; ++c, ++g) {
+            const int buf = (int)(g & 1);
+            bool ok = mbar_wait_bounded(&mbar[buf], phase[buf]);
+            phase[buf] ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) tp_dev_error(A.derr, TP_DERR_TIMEOUT);
+                aborted = true;
+                break;
+            }
+            if (tid == 0) issue(buf ^ 1);
+            advance_next();
+            const float* cb = chunk + buf * TP_CHUNK * TP_SRCW;
+            const int64_t sbase = (int64_t)J * TP_SUPER + (int64_t)c * TP_CHUNK;
+#pragma unroll 2
+            for (int s = 0; s < TP_CHUNK; ++s) {
+                SrcRec sr;
+                load_src(cb + s * TP_SRCW, sr);
+                float2 valid[2] = {make_float2(1.f, 1.f), make_float2(1.f, 1.f)};
+                if (MASKED) {
+                    const int64_t sgi = sbase + s;
+                    int3 sf = load_face(A.Fs, sgi);
+#pragma unroll
+                    for (int P = 0; P < 2; ++P) {
+                        float v0 = ((I != J || sgi > tg[P][0]) && !share_vertex(tf[P][0], sf, A.edge_only)) ? 1.f : 0.f;
+                        float v1 = ((I != J || sgi > tg[P][1]) && !share_vertex(tf[P][1], sf, A.edge_only)) ? 1.f : 0.f;
+                        valid[P] = make_float2(v0, v1);
+                    }
+                }
+#pragma unroll
+                for (int P = 0; P < 2; ++P) ea[P] = add2(ea[P], pair_energy<Q, MASKED>(tp[P], sr, valid[P]));
+            }
+            __syncthreads();
+        }
+        if (aborted) break;
+#pragma unroll
+        for (int P = 0; P < 2; ++P) esum += (double)(tp[P].w.x * ea[P].x) + (double)(tp[P].w.y * ea[P].y);
+        ++idx;
+        if (MASKED) {
+            if (idx < hi) item_at(idx, curI, curJ);
+        } else {
+            it.next();
+            while (idx < hi && item_flagged(A.flagged, A.nsup, it.I, it.J)) {
+                ++idx;
+                it.next();
+            }
+            curI = it.I;
+            curJ = it.J;
+        }
+    }
+    // deterministic block reduction
+    for (int o = 16; o > 0; o >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, o);
+    if (lane == 0) wsum[warp] = esum;
+    __syncthreads();
+    if (tid == 0) {
+        double b = 0.0;
+        for (int w = 0; w < WARPS; ++w) b += wsum[w];
+        A.partial[partial_off + blockIdx.x] = b;
+    }
+}
+
+// ------------------------------------------------------------ FP64 reference kernel (TP_F64)
+// One thread per target, gather over every source (both orderings), FP64
+// arithmetic throughout; writes the same accumulator convention.
+template <int Q>
+__global__ void k_pairs_f64(const double* x64, const double* nu64, const double* w64, const int32_t* F,
+                            const int32_t* perm, int64_t nt, int64_t ntp, int edge_only, double* acc,
+                            double* eper) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= nt) return;
+    const double pq = 2.0;
+    int64_t T = perm[k];
+    double xt[3], nt3[3];
+    for (int a = 0; a < 3; ++a) {
+        xt[a] = x64[a * nt + T];
+        nt3[a] = nu64[a * nt + T];
+    }
+    double wt = w64[T];
+    int3 ft = make_int3(F[3 * T], F[3 * T + 1], F[3 * T + 2]);
+    double Ew = 0, U = 0, Gn[3] = {0, 0, 0}, Gx[3] = {0, 0, 0}, es = 0;
+    for (int64_t S = 0; S < nt; ++S) {
+        if (S == T) continue;
+        int3 fs = make_int3(F[3 * S], F[3 * S + 1], F[3 * S + 2]);
+        if (share_vertex(ft, fs, edge_only)) continue;
+        double d[3], r2 = 0, a = 0, b = 0;
+        for (int c = 0; c < 3; ++c) {
+            d[c] = xt[c] - x64[c * nt + S];
+            r2 += d[c] * d[c];
+        }
+        for (int c = 0; c < 3; ++c) {
+            a += nt3[c] * d[c];
+            b += nu64[c * nt + S] * d[c];
+        }
+        double inv = 1.0 / r2, al = a * inv, be = b * inv;
+        double al2 = al * al, be2 = be * be;
+        double alq, beq, al5, be5;
+        if (Q == 6) {
+            alq = al2 * al2 * al2;
+            beq = be2 * be2 * be2;
+            al5 = al2 * al2 * al;
+            be5 = be2 * be2 * be;
+        } else {
+            alq = al2 * al2 * al2 * al2;
+            beq = be2 * be2 * be2 * be2;
+            al5 = al2 * al2 * al2 * al;
+            be5 = be2 * be2 * be2 * be;
+        }
+        double wts = pq * wt * w64[S];
+        double s6 = alq + beq, E = wts * s6, wi = wts * inv, A5 = wi * al5, B5 = wi * be5, kk = wi * s6;
+        Ew += E;
+        U += A5;
+        es += wt * w64[S] * alq;
+        for (int c = 0; c < 3; ++c) {
+            Gn[c] += A5 * d[c];
+            Gx[c] += B5 * nu64[c * nt + S] - kk * d[c];
+        }
+    }
+    acc[0 * ntp + k] = Ew;
+    acc[1 * ntp + k] = U;
+    for (int c = 0; c < 3; ++c) {
+        acc[(2 + c) * ntp + k] = Gn[c];
+        acc[(5 + c) * ntp + k] = Gx[c];
+    }
+    eper[k] = es;
+}
+
+template <int Q>
+tp_status launch_grad_q(tp_ctx* ctx, DirectArgs& A) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_pairs_grad<Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_GRAD);
+        cudaFuncSetAttribute(k_pairs_grad<Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_GRAD);
+        attr = true;
+    }
+    const int64_t nitems = (int64_t)ctx->nsup * (ctx->nsup + 1) / 2;
+    const int64_t nfree = nitems - ctx->n_masked;
+    if (nfree > 0) {
+        int grid = (int)std::min<int64_t>(ctx->num_sms, nfree);
+        cudaEventRecord(ctx->ev[0], ctx->stream);
+        k_pairs_grad<Q, false><<<grid, THREADS, SMEM_GRAD, ctx->stream>>>(A, 0, nitems);
+        ++ctx->nlaunch;
+        cudaEventRecord(ctx->ev[1], ctx->stream);
+    }
+    if (ctx->n_masked > 0) {
+        int grid = (int)std::min<int64_t>(ctx->num_sms, ctx->n_masked);
+        k_pairs_grad<Q, true><<<grid, THREADS, SMEM_GRAD, ctx->stream>>>(A, 0, ctx->n_masked);
+        ++ctx->nlaunch;
+    }
+    TP_CU(cudaGetLastError());
+    return TP_OK;
+}
+
+template <int Q>
+tp_status launch_energy_q(tp_ctx* ctx, DirectArgs& A, int* nparts) {
+    const int64_t nitems = (int64_t)ctx->nsup * (ctx->nsup + 1) / 2;
+    const int64_t nfree = nitems - ctx->n_masked;
+    int g1 = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, nfree));
+    int g2 = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, ctx->n_masked));
+    cudaEventRecord(ctx->ev[0], ctx->stream);
+    k_pairs_energy<Q, false><<<g1, THREADS, SMEM_ENERGY, ctx->stream>>>(A, 0, nfree > 0 ? nitems : 0, 0);
+    ++ctx->nlaunch;
+    cudaEventRecord(ctx->ev[1], ctx->stream);
+    k_pairs_energy<Q, true><<<g2, THREADS, SMEM_ENERGY, ctx->stream>>>(A, 0, ctx->n_masked, g1);
+    ++ctx->nlaunch;
+    TP_CU(cudaGetLastError());
+    *nparts = g1 + g2;
+    return TP_OK;
+}
+
+DirectArgs make_args(tp_ctx* ctx, const tp_params* prm) {
+    DirectArgs A;
+    A.soa = ctx->soa;
+    A.src = ctx->src;
+    A.Fs = ctx->Fs;
+    A.acc = ctx->acc;
+    A.flagged = ctx->flagged;
+    A.mlist = ctx->mlist;
+    A.nmasked = ctx->n_masked;
+    A.ntp = ctx->ntp;
+    A.nsup = (int)ctx->nsup;
+    A.edge_only = (prm->flags & TP_EXCLUDE_EDGE) ? 1 : 0;
+    A.derr = ctx->derr;
+    A.partial = ctx->red;
+    return A;
+}
+
+}  // namespace
+
+tp_status tp_launch_direct_grad(tp_ctx* ctx, const tp_params* prm) {
+    TP_CU(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * TP_NACC * ctx->ntp, ctx->stream));
+    DirectArgs A = make_args(ctx, prm);
+    if (prm->q == 6) return launch_grad_q<6>(ctx, A);
+    return launch_grad_q<8>(ctx, A);
+}
+
+tp_status tp_launch_direct_energy(tp_ctx* ctx, const tp_params* prm, double* partials, int* nparts) {
+    DirectArgs A = make_args(ctx, prm);
+    A.partial = partials;
+    if (prm->q == 6) return launch_energy_q<6>(ctx, A, nparts);
+    return launch_energy_q<8>(ctx, A, nparts);
+}
+
+tp_status tp_launch_direct_f64(tp_ctx* ctx, const tp_params* prm, bool grad) {
+    (void)grad;
+    TP_CU(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * TP_NACC * ctx->ntp, ctx->stream));
+    const int edge = (prm->flags & TP_EXCLUDE_EDGE) ? 1 : 0;
+    int blocks = (int)((ctx->nt + 127) / 128);
+    cudaEventRecord(ctx->ev[0], ctx->stream);
+    if (prm->q == 6)
+        k_pairs_f64<6><<<blocks, 128, 0, ctx->stream>>>(ctx->x64, ctx->nu64, ctx->w64, ctx->F, ctx->perm, ctx->nt,
+                                                        ctx->ntp, edge, ctx->acc, ctx->red);
+    else
+        k_pairs_f64<8><<<blocks, 128, 0, ctx->stream>>>(ctx->x64, ctx->nu64, ctx->w64, ctx->F, ctx->perm, ctx->nt,
+                                                        ctx->ntp, edge, ctx->acc, ctx->red);
+    ++ctx->nlaunch;
+    cudaEventRecord(ctx->ev[1], ctx->stream);
+    TP_CU(cudaGetLastError());
+    return TP_OK;
+}

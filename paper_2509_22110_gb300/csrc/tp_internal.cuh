@@ -1,0 +1,162 @@
+// tp_internal.cuh - context, device buffers and launch helpers of libtp.
+//
+// Data layout in HBM (all device memory owned by the context):
+//   V64[nv][3]            f64  vertex positions (input copy)
+//   F[nt][3]              i32  faces in the caller's order
+//   v2t_off[nv+1], v2t[3nt]    vertex -> (triangle*4 + corner) incidence (CSR)
+//   x64/nu64[3][nt], w64[nt]   f64 triangle data in the caller's order
+//   perm[nt], iperm[nt]        library order (Morton) <-> caller's order
+//   soa: 10 planes of ntp f32  (x_hi[3], x_lo[3], nu[3], sqrt(2) w) in
+//        library order, padded to a multiple of TP_SUPER with zero-area
+//        triangles placed far away
+//   src[ntp][20] f32           the same 10 values, each stored twice, one
+//                              80-byte record per triangle: the unit the
+//                              pair kernel stages into shared memory
+//   Fs[ntp][3] i32             faces in library order (padding: unique negatives)
+//   acc[8][ntp] f64            per-triangle accumulators of the pair kernels
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/tp.h"
+
+#define TP_SUPER 1024      // triangles per super-tile (one block's target set)
+#define TP_CHUNK 128       // sources staged per shared-memory chunk
+#define TP_SRCW 20         // floats per staged source record
+#define TP_NACC 8          // accumulators per triangle
+#define TP_SPIN_LIMIT (1u << 26)
+
+// device error bits
+#define TP_DERR_TIMEOUT 0x1u
+#define TP_DERR_STACK 0x2u
+#define TP_DERR_INDEX 0x4u
+#define TP_DERR_NONFINITE 0x8u
+
+struct tp_tree {
+    bool valid = false;
+    int leaf_size = 16, morton_bits = 30;
+    int64_t nleaves = 0;
+    uint32_t* codes = nullptr;   // [nt] by caller's index
+    int32_t* left = nullptr;     // [nt-1]
+    int32_t* right = nullptr;    // [nt-1]
+    int32_t* parent = nullptr;   // [2nt-1]
+    int32_t* first = nullptr;    // [2nt-1]
+    int32_t* last = nullptr;     // [2nt-1]
+    int32_t* leaves = nullptr;   // [nt]
+    int32_t* counter = nullptr;  // [nt-1] visit counters of the bottom-up pass
+    double* mom = nullptr;       // [2nt-1][13]
+    double* box = nullptr;       // [2nt-1][6]
+    float* nodef = nullptr;      // [2nt-1][16] f32 node summary used by the traversal
+    int32_t* nleaves_d = nullptr;
+    int64_t cap = 0;
+};
+
+struct tp_mlp_model;
+
+struct tp_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+
+    int64_t nv = 0, nt = 0, ntp = 0, nsup = 0;
+    bool have_mesh = false;
+
+    // mesh
+    double* V64 = nullptr;
+    int32_t* F = nullptr;
+    int32_t* v2t_off = nullptr;
+    int32_t* v2t = nullptr;
+    double* x64 = nullptr;
+    double* nu64 = nullptr;
+    double* w64 = nullptr;
+    int32_t* perm = nullptr;
+    int32_t* iperm = nullptr;
+    uint32_t* codes = nullptr;      // Morton codes by caller's index
+    uint32_t* codes_sorted = nullptr;
+    int32_t* idx_tmp = nullptr;
+    float* soa = nullptr;           // 10 planes of ntp
+    float* src = nullptr;           // [ntp][TP_SRCW]
+    int32_t* Fs = nullptr;          // [ntp][3]
+    double* acc = nullptr;          // [TP_NACC][ntp]
+    double* center = nullptr;       // [3] f64 centre subtracted before the f32 split
+    double* bounds = nullptr;       // [6] min/max of centroids
+    double* red = nullptr;          // reduction scratch
+    double* scalar = nullptr;       // [4] device scalars (energy ...)
+    unsigned* derr = nullptr;       // device error word
+    unsigned* flagged = nullptr;    // bitmap nsup*nsup of super-tile pairs needing masks
+    int32_t* mlist = nullptr;       // compact list of masked super-tile pairs (I,J)
+    int32_t* mcount = nullptr;
+    void* sort_tmp = nullptr;
+    size_t sort_tmp_bytes = 0;
+    double* host_pinned = nullptr;  // small pinned staging
+
+    int64_t n_masked = 0;
+    int64_t n_excluded_ordered = 0;  // ordered pairs T != S sharing a vertex
+    int64_t cap_nv = 0, cap_nt = 0, cap_ntp = 0, red_cap = 0;
+    double* gradbuf = nullptr;      // [3nv] device staging of host gradients
+    float* vtmp = nullptr;          // [3nv] f32 staging of f32 positions
+    double last_q = 6.0, last_pq = 2.0;
+    int64_t nlaunch = 0;            // library kernels launched in the current call
+    tp_tree tree;
+    tp_mlp_model* mlp = nullptr;
+
+    tp_stats stats{};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+
+    // allocation bookkeeping
+    std::vector<void*> allocs;
+};
+
+// ---------------------------------------------------------------- host helpers
+tp_status tp_set_err(tp_ctx* c, tp_status s, const char* fmt, ...);
+tp_status tp_cuda_check(tp_ctx* c, cudaError_t e, const char* what);
+#define TP_CU(call)                                                   \
+    do {                                                              \
+        cudaError_t _e = (call);                                      \
+        if (_e != cudaSuccess) return tp_cuda_check(ctx, _e, #call);  \
+    } while (0)
+#define TP_TRY(call)                        \
+    do {                                    \
+        tp_status _s = (call);              \
+        if (_s != TP_OK) return _s;         \
+    } while (0)
+
+tp_status tp_alloc(tp_ctx* ctx, void** p, size_t bytes);
+void tp_free(tp_ctx* ctx, void* p);
+template <typename T>
+inline tp_status tp_alloc_t(tp_ctx* ctx, T** p, size_t n) {
+    return tp_alloc(ctx, reinterpret_cast<void**>(p), n * sizeof(T) + 16);
+}
+
+// ---------------------------------------------------------------- launchers (per .cu file)
+// tp_tri.cu
+tp_status tp_launch_tri_data(tp_ctx* ctx);
+tp_status tp_launch_morton_order(tp_ctx* ctx, int morton_bits);
+tp_status tp_launch_sorted_soa(tp_ctx* ctx);
+tp_status tp_launch_flagged(tp_ctx* ctx);
+tp_status tp_build_v2t(tp_ctx* ctx);
+tp_status tp_count_excluded(tp_ctx* ctx);
+// tp_direct.cu
+tp_status tp_launch_direct_grad(tp_ctx* ctx, const tp_params* prm);
+tp_status tp_launch_direct_energy(tp_ctx* ctx, const tp_params* prm, double* partials, int* nparts);
+tp_status tp_launch_direct_f64(tp_ctx* ctx, const tp_params* prm, bool grad);
+// tp_adjoint.cu
+tp_status tp_launch_adjoint(tp_ctx* ctx, const tp_params* prm, void* grad, int g_dtype);
+tp_status tp_launch_energy_from_acc(tp_ctx* ctx, const tp_params* prm, double* d_out);
+tp_status tp_launch_reduce_sum(tp_ctx* ctx, const double* in, int64_t n, double* d_out);
+tp_status tp_launch_check_finite(tp_ctx* ctx);
+// tp_lbvh.cu
+tp_status tp_launch_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits);
+// tp_bh.cu
+tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned);
+// tp_mlp.cu
+void tp_mlp_release(tp_ctx* ctx);
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ void tp_dev_error(unsigned* derr, unsigned bit) { atomicOr(derr, bit); }

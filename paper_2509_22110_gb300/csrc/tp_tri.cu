@@ -1,0 +1,381 @@
+// tp_tri.cu - per-triangle data (centroid, unit normal, area), Morton order,
+// the library-order SoA staged by the pair kernels, vertex->triangle
+// incidence and the masks of super-tile pairs.
+//
+// Sec. 3.2 caches positions, area elements and normals at every quadrature
+// point contiguously and iterates them in memory order; here the cache is a
+// structure of arrays in Morton order (one point per triangle).
+//
+// The FP64 triangle data is computed with separately rounded operations in
+// a fixed association order - x = ((v0 + v1) + v2) / 3, N = e1 x e2 with
+// products then differences, |N| = sqrt((Nx^2 + Ny^2) + Nz^2), w = |N|/2,
+// nu = N/|N| - so the Morton codes and cluster moments built from it are
+// reproducible bit for bit.
+#include <cub/cub.cuh>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tp_internal.cuh"
+
+namespace {
+
+__global__ void k_tri_data(const double* __restrict__ V, const int32_t* __restrict__ F, int64_t nt, int64_t nv,
+                           double* __restrict__ x64, double* __restrict__ nu64, double* __restrict__ w64,
+                           unsigned* derr) {
+    int64_t T = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (T >= nt) return;
+    int32_t i0 = F[3 * T], i1 = F[3 * T + 1], i2 = F[3 * T + 2];
+    if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= nv || i1 >= nv || i2 >= nv) {
+        tp_dev_error(derr, TP_DERR_INDEX);
+        for (int a = 0; a < 3; ++a) {
+            x64[a * nt + T] = 0.0;
+            nu64[a * nt + T] = 0.0;
+        }
+        w64[T] = 0.0;
+        return;
+    }
+    const double* a = V + 3 * (int64_t)i0;
+    const double* b = V + 3 * (int64_t)i1;
+    const double* c = V + 3 * (int64_t)i2;
+    double e1[3], e2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        x64[k * nt + T] = __ddiv_rn(__dadd_rn(__dadd_rn(a[k], b[k]), c[k]), 3.0);
+        e1[k] = __dsub_rn(b[k], a[k]);
+        e2[k] = __dsub_rn(c[k], a[k]);
+    }
+    double N0 = __dsub_rn(__dmul_rn(e1[1], e2[2]), __dmul_rn(e1[2], e2[1]));
+    double N1 = __dsub_rn(__dmul_rn(e1[2], e2[0]), __dmul_rn(e1[0], e2[2]));
+    double N2 = __dsub_rn(__dmul_rn(e1[0], e2[1]), __dmul_rn(e1[1], e2[0]));
+    double len = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(N0, N0), __dmul_rn(N1, N1)), __dmul_rn(N2, N2)));
+    if (!(len > 0.0) || !isfinite(len)) tp_dev_error(derr, TP_DERR_NONFINITE);
+    w64[T] = __dmul_rn(0.5, len);
+    nu64[0 * nt + T] = __ddiv_rn(N0, len);
+    nu64[1 * nt + T] = __ddiv_rn(N1, len);
+    nu64[2 * nt + T] = __ddiv_rn(N2, len);
+}
+
+// per-block min/max of the centroids (6 values), then a final single-block pass
+__global__ void k_bounds_partial(const double* __restrict__ x64, int64_t nt, double* __restrict__ part) {
+    __shared__ double smin[3][256], smax[3][256];
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t T = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; T < nt; T += (int64_t)gridDim.x * blockDim.x)
+        for (int a = 0; a < 3; ++a) {
+            double v = x64[a * nt + T];
+            mn[a] = fmin(mn[a], v);
+            mx[a] = fmax(mx[a], v);
+        }
+    for (int a = 0; a < 3; ++a) {
+        smin[a][threadIdx.x] = mn[a];
+        smax[a][threadIdx.x] = mx[a];
+    }
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int a = 0; a < 3; ++a) {
+                smin[a][threadIdx.x] = fmin(smin[a][threadIdx.x], smin[a][threadIdx.x + s]);
+                smax[a][threadIdx.x] = fmax(smax[a][threadIdx.x], smax[a][threadIdx.x + s]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int a = 0; a < 3; ++a) {
+            part[6 * blockIdx.x + a] = smin[a][0];
+            part[6 * blockIdx.x + 3 + a] = smax[a][0];
+        }
+}
+
+__global__ void k_bounds_final(const double* __restrict__ part, int nb, double* __restrict__ bounds,
+                               double* __restrict__ center) {
+    if (threadIdx.x != 0) return;
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = 0; b < nb; ++b)
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = fmin(mn[a], part[6 * b + a]);
+            mx[a] = fmax(mx[a], part[6 * b + 3 + a]);
+        }
+    for (int a = 0; a < 3; ++a) {
+        bounds[a] = mn[a];
+        bounds[3 + a] = mx[a];
+        center[a] = 0.5 * (mn[a] + mx[a]);
+    }
+}
+
+__device__ __forceinline__ uint32_t spread3(uint32_t v, int bits) {
+    uint32_t r = 0;
+    for (int i = 0; i < bits; ++i) r |= ((v >> i) & 1u) << (3 * i);
+    return r;
+}
+
+// Morton code: q_a = min(2^b - 1, floor((x_a - lo_a) * (2^b / (hi_a - lo_a)))), FP64 RN,
+// interleaved with x the most significant bit of each triplet.
+__global__ void k_morton(const double* __restrict__ x64, int64_t nt, const double* __restrict__ bounds, int bits,
+                         uint32_t* __restrict__ codes, int32_t* __restrict__ idx) {
+    int64_t T = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (T >= nt) return;
+    const uint32_t Q = 1u << bits;
+    uint32_t q[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double lo = bounds[a], hi = bounds[3 + a];
+        double s = hi > lo ? __ddiv_rn((double)Q, __dsub_rn(hi, lo)) : 0.0;
+        double t = __dmul_rn(__dsub_rn(x64[a * nt + T], lo), s);
+        double f = floor(t);
+        q[a] = f >= (double)(Q - 1) ? Q - 1 : (uint32_t)f;
+    }
+    codes[T] = (spread3(q[0], bits) << 2) | (spread3(q[1], bits) << 1) | spread3(q[2], bits);
+    idx[T] = (int32_t)T;
+}
+
+// library-order SoA, staged source records and sorted faces
+__global__ void k_sorted_soa(const double* __restrict__ x64, const double* __restrict__ nu64,
+                             const double* __restrict__ w64, const int32_t* __restrict__ F,
+                             const int32_t* __restrict__ perm, const double* __restrict__ center, int64_t nt,
+                             int64_t ntp, int32_t* __restrict__ iperm, float* __restrict__ soa,
+                             float* __restrict__ src, int32_t* __restrict__ Fs) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= ntp) return;
+    float v[10];
+    int3 f;
+    if (k < nt) {
+        int64_t T = perm[k];
+        iperm[T] = (int32_t)k;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double xc = x64[a * nt + T] - center[a];
+            float hi = (float)xc;
+            float lo = (float)(xc - (double)hi);
+            v[a] = hi;
+            v[3 + a] = lo;
+            v[6 + a] = (float)nu64[a * nt + T];
+        }
+        v[9] = (float)(1.4142135623730951 * w64[T]);  // sqrt(p/q) w with p = 2q
+        f = make_int3(F[3 * T], F[3 * T + 1], F[3 * T + 2]);
+    } else {
+        // zero-area padding placed far apart so no padding pair coincides
+        v[0] = 4096.0f + 8.0f * (float)(k - nt);
+        v[1] = 4096.0f;
+        v[2] = 4096.0f;
+        for (int a = 3; a < 10; ++a) v[a] = 0.0f;
+        f = make_int3(-1, -1, -1);
+    }
+#pragma unroll
+    for (int a = 0; a < 10; ++a) {
+        soa[a * ntp + k] = v[a];
+        src[k * TP_SRCW + 2 * a] = v[a];
+        src[k * TP_SRCW + 2 * a + 1] = v[a];
+    }
+    Fs[3 * k] = f.x;
+    Fs[3 * k + 1] = f.y;
+    Fs[3 * k + 2] = f.z;
+}
+
+// vertex -> triangle incidence (CSR), entries triangle*4 + corner
+__global__ void k_v2t_count(const int32_t* __restrict__ F, int64_t nt, int64_t nv, int32_t* __restrict__ cnt,
+                            unsigned* derr) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= 3 * nt) return;
+    int32_t v = F[i];
+    if (v < 0 || v >= nv) {
+        tp_dev_error(derr, TP_DERR_INDEX);
+        return;
+    }
+    atomicAdd(&cnt[v], 1);
+}
+
+__global__ void k_v2t_fill(const int32_t* __restrict__ F, int64_t nt, int64_t nv, const int32_t* __restrict__ off,
+                           int32_t* __restrict__ fillc, int32_t* __restrict__ v2t) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= 3 * nt) return;
+    int32_t v = F[i];
+    if (v < 0 || v >= nv) return;
+    int32_t slot = atomicAdd(&fillc[v], 1);
+    v2t[off[v] + slot] = (int32_t)((i / 3) * 4 + (i % 3));
+}
+
+// sort each vertex's short list so later sums over it are deterministic
+__global__ void k_v2t_sort(const int32_t* __restrict__ off, int64_t nv, int32_t* __restrict__ v2t) {
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    int32_t b = off[v], e = off[v + 1];
+    for (int32_t i = b + 1; i < e; ++i) {
+        int32_t key = v2t[i];
+        int32_t j = i - 1;
+        while (j >= b && v2t[j] > key) {
+            v2t[j + 1] = v2t[j];
+            --j;
+        }
+        v2t[j + 1] = key;
+    }
+}
+
+// super-tile pairs containing a pair of triangles that share a vertex
+__global__ void k_flag_pairs(const int32_t* __restrict__ F, const int32_t* __restrict__ perm,
+                             const int32_t* __restrict__ iperm, const int32_t* __restrict__ off,
+                             const int32_t* __restrict__ v2t, int64_t nt, int nsup, unsigned* __restrict__ bm) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= nt) return;
+    int64_t T = perm[k];
+    int I = (int)(k / TP_SUPER);
+    for (int c = 0; c < 3; ++c) {
+        int32_t v = F[3 * T + c];
+        for (int32_t e = off[v]; e < off[v + 1]; ++e) {
+            int64_t S = v2t[e] >> 2;
+            int J = iperm[S] / TP_SUPER;
+            int a = min(I, J), b = max(I, J);
+            int64_t bit = (int64_t)a * nsup + b;
+            atomicOr(&bm[bit >> 5], 1u << (bit & 31));
+        }
+    }
+}
+
+__global__ void k_flag_diag(int nsup, unsigned* __restrict__ bm) {
+    int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nsup) return;
+    int64_t bit = (int64_t)I * nsup + I;
+    atomicOr(&bm[bit >> 5], 1u << (bit & 31));
+}
+
+__global__ void k_flag_compact(const unsigned* __restrict__ bm, int nsup, int32_t* __restrict__ list,
+                               int32_t* __restrict__ count) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t n = (int64_t)nsup * nsup;
+    if (i >= n) return;
+    if ((bm[i >> 5] >> (i & 31)) & 1u) {
+        int I = (int)(i / nsup), J = (int)(i % nsup);
+        int32_t slot = atomicAdd(count, 1);
+        list[slot] = (I << 16) | J;
+    }
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+tp_status tp_launch_tri_data(tp_ctx* ctx) {
+    const int64_t nt = ctx->nt;
+    k_tri_data<<<blocks_for(nt, 256), 256, 0, ctx->stream>>>(ctx->V64, ctx->F, nt, ctx->nv, ctx->x64, ctx->nu64,
+                                                             ctx->w64, ctx->derr);
+    ++ctx->nlaunch;
+    int nb = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (nt + 255) / 256));
+    k_bounds_partial<<<nb, 256, 0, ctx->stream>>>(ctx->x64, nt, ctx->red);
+    ++ctx->nlaunch;
+    k_bounds_final<<<1, 32, 0, ctx->stream>>>(ctx->red, nb, ctx->bounds, ctx->center);
+    ++ctx->nlaunch;
+    TP_CU(cudaGetLastError());
+    return TP_OK;
+}
+
+tp_status tp_launch_morton_order(tp_ctx* ctx, int morton_bits) {
+    const int64_t nt = ctx->nt;
+    k_morton<<<blocks_for(nt, 256), 256, 0, ctx->stream>>>(ctx->x64, nt, ctx->bounds, morton_bits / 3, ctx->codes,
+                                                           ctx->idx_tmp);
+    ++ctx->nlaunch;
+    size_t need = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, need, ctx->codes, ctx->codes_sorted, ctx->idx_tmp, ctx->perm, (int)nt, 0,
+                                    morton_bits, ctx->stream);
+    if (need > ctx->sort_tmp_bytes) {
+        tp_free(ctx, ctx->sort_tmp);
+        ctx->sort_tmp = nullptr;
+        TP_TRY(tp_alloc(ctx, &ctx->sort_tmp, need));
+        ctx->sort_tmp_bytes = need;
+    }
+    size_t have = ctx->sort_tmp_bytes;
+    TP_CU(cub::DeviceRadixSort::SortPairs(ctx->sort_tmp, have, ctx->codes, ctx->codes_sorted, ctx->idx_tmp, ctx->perm,
+                                          (int)nt, 0, morton_bits, ctx->stream));
+    TP_CU(cudaGetLastError());
+    return TP_OK;
+}
+
+tp_status tp_launch_sorted_soa(tp_ctx* ctx) {
+    k_sorted_soa<<<blocks_for(ctx->ntp, 256), 256, 0, ctx->stream>>>(
+        ctx->x64, ctx->nu64, ctx->w64, ctx->F, ctx->perm, ctx->center, ctx->nt, ctx->ntp, ctx->iperm, ctx->soa,
+        ctx->src, ctx->Fs);
+    ++ctx->nlaunch;
+    TP_CU(cudaGetLastError());
+    return TP_OK;
+}
+
+tp_status tp_build_v2t(tp_ctx* ctx) {
+    const int64_t nt = ctx->nt, nv = ctx->nv;
+    int32_t* cnt = ctx->idx_tmp;  // reuse as counter scratch (nt >= nv/2 for closed meshes; sized max)
+    TP_CU(cudaMemsetAsync(ctx->v2t_off, 0, sizeof(int32_t) * (nv + 1), ctx->stream));
+    k_v2t_count<<<blocks_for(3 * nt, 256), 256, 0, ctx->stream>>>(ctx->F, nt, nv, ctx->v2t_off + 1, ctx->derr);
+    ++ctx->nlaunch;
+    size_t need = 0;
+    cub::DeviceScan::InclusiveSum(nullptr, need, ctx->v2t_off + 1, ctx->v2t_off + 1, (int)nv, ctx->stream);
+    if (need > ctx->sort_tmp_bytes) {
+        tp_free(ctx, ctx->sort_tmp);
+        ctx->sort_tmp = nullptr;
+        TP_TRY(tp_alloc(ctx, &ctx->sort_tmp, need));
+        ctx->sort_tmp_bytes = need;
+    }
+    size_t have = ctx->sort_tmp_bytes;
+    TP_CU(cub::DeviceScan::InclusiveSum(ctx->sort_tmp, have, ctx->v2t_off + 1, ctx->v2t_off + 1, (int)nv,
+                                        ctx->stream));
+    TP_CU(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nv, ctx->stream));
+    k_v2t_fill<<<blocks_for(3 * nt, 256), 256, 0, ctx->stream>>>(ctx->F, nt, nv, ctx->v2t_off, cnt, ctx->v2t);
+    ++ctx->nlaunch;
+    k_v2t_sort<<<blocks_for(nv, 256), 256, 0, ctx->stream>>>(ctx->v2t_off, nv, ctx->v2t);
+    ++ctx->nlaunch;
+    TP_CU(cudaGetLastError());
+    return TP_OK;
+}
+
+tp_status tp_launch_flagged(tp_ctx* ctx) {
+    const int nsup = (int)ctx->nsup;
+    const int64_t nbits = (int64_t)nsup * nsup;
+    TP_CU(cudaMemsetAsync(ctx->flagged, 0, sizeof(unsigned) * ((nbits + 31) / 32), ctx->stream));
+    TP_CU(cudaMemsetAsync(ctx->mcount, 0, sizeof(int32_t), ctx->stream));
+    k_flag_pairs<<<blocks_for(ctx->nt, 256), 256, 0, ctx->stream>>>(ctx->F, ctx->perm, ctx->iperm, ctx->v2t_off,
+                                                                    ctx->v2t, ctx->nt, nsup, ctx->flagged);
+    ++ctx->nlaunch;
+    k_flag_diag<<<blocks_for(nsup, 256), 256, 0, ctx->stream>>>(nsup, ctx->flagged);
+    ++ctx->nlaunch;
+    k_flag_compact<<<blocks_for(nbits, 256), 256, 0, ctx->stream>>>(ctx->flagged, nsup, ctx->mlist, ctx->mcount);
+    ++ctx->nlaunch;
+    int32_t h = 0;
+    TP_CU(cudaMemcpyAsync(&h, ctx->mcount, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    TP_CU(cudaStreamSynchronize(ctx->stream));
+    ctx->n_masked = h;
+    return TP_OK;
+}
+
+namespace {
+// number of distinct S != T sharing a vertex with T (ordered excluded pairs)
+__global__ void k_count_excluded(const int32_t* __restrict__ F, const int32_t* __restrict__ off,
+                                 const int32_t* __restrict__ v2t, int64_t nt, unsigned long long* __restrict__ out) {
+    int64_t T = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    unsigned long long cnt = 0;
+    if (T < nt) {
+        for (int c = 0; c < 3; ++c) {
+            int32_t v = F[3 * T + c];
+            for (int32_t e = off[v]; e < off[v + 1]; ++e) {
+                int64_t S = v2t[e] >> 2;
+                if (S == T) continue;
+                // count S once: only at the first corner of T whose vertex S touches
+                bool seen = false;
+                for (int c2 = 0; c2 < c && !seen; ++c2) {
+                    int32_t v2 = F[3 * T + c2];
+                    seen = (F[3 * S] == v2) || (F[3 * S + 1] == v2) || (F[3 * S + 2] == v2);
+                }
+                if (!seen) ++cnt;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, cnt);
+}
+}  // namespace
+
+tp_status tp_count_excluded(tp_ctx* ctx) {
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(ctx->scalar + 6);
+    TP_CU(cudaMemsetAsync(d, 0, 8, ctx->stream));
+    k_count_excluded<<<blocks_for(ctx->nt, 256), 256, 0, ctx->stream>>>(ctx->F, ctx->v2t_off, ctx->v2t, ctx->nt, d);
+    ++ctx->nlaunch;
+    unsigned long long h = 0;
+    TP_CU(cudaMemcpyAsync(&h, d, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    TP_CU(cudaStreamSynchronize(ctx->stream));
+    ctx->n_excluded_ordered = (int64_t)h;
+    return TP_OK;
+}

@@ -1,0 +1,61 @@
+"""CPU-only checks of the boundary: the library builds, loads and exports every
+entry point declared in include/tp.h, and the Python binding exposes the same
+names.  No compute call is made (there is no GPU here)."""
+
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "tp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tp_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2509_22110_gb300 import build
+
+    try:
+        return build.build()
+    except RuntimeError as e:  # pragma: no cover
+        pytest.skip(f"nvcc unavailable: {e}")
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("tp_create", "tp_destroy", "tp_mesh_upload", "tp_tree_build", "tp_energy", "tp_gradient",
+              "tp_far_model_load", "tp_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (tp_[a-z_0-9]+)$", out, flags=re.M))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_binding_names_match(libpath):
+    import ctypes
+
+    lib = ctypes.CDLL(libpath)
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+    from paper_2509_22110_gb300 import _tp
+
+    for n in declared_functions():
+        assert hasattr(_tp, n), f"binding lacks {n}"
+    assert _tp.tp_version().startswith("tpgpu")
+
+
+def test_oracle_library_loads(oracle_mod):
+    import ctypes
+
+    lib = ctypes.CDLL(oracle_mod._SO)
+    assert hasattr(lib, "or_energy")
