@@ -8,7 +8,7 @@
 //     al = a*inv, be = b*inv   (so al^6 = a^6/r^12: no overflow of r^-12)
 //     s6 = al^6 + be^6,  wts = w~_T w~_S  (w~ = sqrt(p/q) w, p = 2q)
 //     E = wts s6 = (p/q)(e_TS + e_ST),  A5 = wts inv al^5,  B5 = wts inv be^5,
-//     k = wts inv s6
+//     k = (p/q) wts inv s6
 // and added to per-triangle accumulators (all carrying the factor p/q):
 //     T: Ew += E, U += A5, Gn += A5 d, Gx += B5 nu_S - k d
 //     S: Ew += E, U -= B5, Gn += B5 d, Gx += -A5 nu_T + k d
@@ -229,7 +229,7 @@ __device__ __forceinline__ void pair_grad(const TgtPair& t, const SrcRec& s, Acc
     float2 wi = mul2(wts, inv);
     float2 A5 = mul2(wi, al5);
     float2 B5 = mul2(wi, be5);
-    float2 nk = neg2(mul2(wi, s6));
+    float2 nk = mul2(mul2(wi, s6), f2(-2.0f));  // -(p/q) wts inv s6, p = 2q
     // target side
     at.v[0] = add2(at.v[0], E);
     at.v[1] = add2(at.v[1], A5);
@@ -729,7 +729,7 @@ __global__ void k_pairs_f64(const double* x64, const double* nu64, const double*
             be5 = be2 * be2 * be2 * be;
         }
         double wts = pq * wt * w64[S];
-        double s6 = alq + beq, E = wts * s6, wi = wts * inv, A5 = wi * al5, B5 = wi * be5, kk = wi * s6;
+        double s6 = alq + beq, E = wts * s6, wi = wts * inv, A5 = wi * al5, B5 = wi * be5, kk = pq * wi * s6;
         Ew += E;
         U += A5;
         es += wt * w64[S] * alq;
