@@ -142,7 +142,8 @@ def run_cpu_baseline(V, F, seconds):
     nth = oracle.nthreads_default()
     rng = np.random.default_rng(123)
     x, nu, w = oracle.tri_data(V, F)
-    cal = rng.choice(nt, max(nth, 8), replace=False)
+    oracle.tri_accum(V, F, rng.choice(nt, nth, replace=False), soa=(x, nu, w), nthreads=nth)  # warm the pool
+    cal = rng.choice(nt, 4 * nth, replace=False)
     t0 = time.perf_counter()
     oracle.tri_accum(V, F, cal, soa=(x, nu, w), nthreads=nth)
     dt = time.perf_counter() - t0
