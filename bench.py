@@ -37,8 +37,9 @@ METRIC = "TP energy+grad ms/eval & pair-interactions/s at 327k tris; rel err vs 
 UNIT = "pair-interactions/s"
 # Algorithmic FP32 work per unordered admitted pair of the energy+gradient
 # pair function (both orderings, shared subexpressions once), counted from
-# its expression DAG with an FMA as 2 flops: 25 FMA + 25 other = 75 flops.
-FLOPS_PER_UNORDERED_PAIR = 75
+# its expression DAG with an FMA as 2 flops: 24 FMA + 28 FMUL/FADD = 76 flops
+# (the hi/lo cancellation correction and the reduction overhead not counted).
+FLOPS_PER_UNORDERED_PAIR = 76
 FP32_LANES_PER_SM = 128
 # DRAM bytes per launch of the dominant kernel from the committed ncu
 # capture (profiles/); None until a capture of the current kernel exists.
