@@ -147,6 +147,29 @@ tp_status tp_debug_tree(tp_ctx* ctx, uint32_t* codes, int32_t* perm, int32_t* le
                         int32_t* first, int32_t* last, int32_t* leaves, int64_t* nleaves, double* mom,
                         double* box);
 
+/* Energy and gradient of the direct form for callers that cannot allocate
+ * device memory - code recording a CUDA graph (allocation is not allowed
+ * while a stream is being captured), plug-ins whose host application owns
+ * all device memory through its own pool, loops that forbid allocation once
+ * running.  The paper has no counterpart: this is a deployment variant of
+ * tp_gradient in TP_DIRECT mode with the same arithmetic (FP32 pair terms,
+ * FP64 accumulation).
+ *   V [nv][3] f64, F [nt][3] i32: device inputs on the current device.
+ *   energy_out (1 f64) and grad_out ([nv][3] f64): device outputs, caller-owned.
+ *   params: q/p as tp_gradient, mode must be TP_DIRECT; scale and
+ *   TP_EXCLUDE_EDGE are honoured.  cuda_stream orders the work; the call
+ *   does not synchronise.  errbuf (may be NULL) receives a message on failure.
+ * All scratch is one fixed __device__ array sized for at most 65536
+ * triangles (about 7 MB, kept by every GPU that loads the library until the
+ * process exits); larger meshes give TP_E_ARG.  The first call on a device
+ * looks up that array's address and should be made before any stream
+ * capture.  Calls share the array: calls that overlap on the GPU race.
+ * Non-finite results (coincident admitted centroids) show as inf/NaN in the
+ * outputs instead of a status. */
+tp_status tp_gradient_direct_noalloc(const double* V, int64_t nv, const int32_t* F, int64_t nt,
+                                     const tp_params* params, double* energy_out, double* grad_out,
+                                     void* cuda_stream, char* errbuf, int64_t errbuf_len);
+
 /* Library version string. */
 const char* tp_version(void);
 

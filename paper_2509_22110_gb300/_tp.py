@@ -86,6 +86,8 @@ def lib():
     L.tp_debug_accum.restype = i32
     L.tp_debug_tree.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, C.POINTER(C.c_int64), vp, vp]
     L.tp_debug_tree.restype = i32
+    L.tp_gradient_direct_noalloc.argtypes = [vp, i64, vp, i64, C.POINTER(tp_params), vp, vp, vp, C.c_char_p, i64]
+    L.tp_gradient_direct_noalloc.restype = i32
     _lib = L
     return L
 
@@ -226,3 +228,19 @@ def tp_debug_tree(ctx, nt):
     out["left"] = out["left"][: nt - 1]
     out["right"] = out["right"][: nt - 1]
     return out
+
+
+def tp_gradient_direct_noalloc(V, F, energy_out, grad_out, params=None, stream=None):
+    """Allocation-free direct energy + gradient: V [nv,3] f64, F [nt,3] int32,
+    energy_out [1] f64 and grad_out [nv,3] f64, all CUDA tensors on the
+    current device; ``stream`` a cudaStream_t integer (None: legacy default)."""
+    p = params or tp_params_default()
+    for a in (V, F, energy_out, grad_out):
+        if not (hasattr(a, "is_cuda") and a.is_cuda and a.is_contiguous()):
+            raise ValueError("all arguments must be contiguous CUDA tensors")
+    buf = C.create_string_buffer(256)
+    st = lib().tp_gradient_direct_noalloc(V.data_ptr(), V.shape[0], F.data_ptr(), F.shape[0], C.byref(p),
+                                          energy_out.data_ptr(), grad_out.data_ptr(), C.c_void_p(stream or 0),
+                                          buf, 256)
+    if st != TP_OK:
+        raise TPError(st, buf.value.decode())
