@@ -48,6 +48,7 @@ NCU_TRAFFIC_BYTES = None
 WORKLOADS = {
     "sh_l7": "icosphere level 7 (327,680 triangles) with seeded SH deformation l<=12, a_lm~N(0,(0.05/l)^2), seed 2",
     "dish_l5": "icosphere level 5 (20,480 triangles) mapped to a double-walled dish, gap 0.02, jitter N(0,0.002^2)",
+    "sh_l6_s2": "icosphere level 6 (81,920 triangles) with seeded SH deformation l<=12, a_lm~N(0,(0.05/l)^2), seed 2",
     "folds_l8": "icosphere level 8 (1,310,720 triangles) with 40 seeded radial folds of depth 0.1",
 }
 
