@@ -1,5 +1,265 @@
-// tp_lbvh.cu - cluster tree (placeholder until the LBVH kernels land)
+// tp_lbvh.cu - cluster tree for the Barnes-Hut form: linear BVH over Morton
+// codes, cluster leaves and FP64 cluster moments.
+//
+// Sec. 3.2 clusters the inner integral with "precomputed averages over a
+// patch of mesh elements" and an admissibility condition after Yu et al.;
+// the paper does not name its tree.  This file builds a linear BVH:
+//   1. Morton codes of the FP64 centroids (tp_tri.cu, k_morton) sorted as
+//      (code, triangle index) keys;
+//   2. the binary radix tree of the sorted keys, one thread per internal
+//      node: node i covers a key range with i at one end; the direction of
+//      the range follows the longer common prefix with a neighbour, its
+//      extent is found by exponential then binary search on the common
+//      prefix length, and its split is the last position sharing more than
+//      the node's common prefix with key i (Karras 2012 numbering: the
+//      children of a node split at g are node g, or primitive g when the
+//      range [first, g] has one key, and node g+1, or primitive g+1);
+//   3. cluster leaves: nodes with at most leaf_size triangles whose parent
+//      has more, listed in ascending order of their first triangle;
+//   4. moments bottom-up: a primitive holds w, w x (3), w nu (3),
+//      (w nu_a) nu_b (6) and its vertex box; an internal node holds
+//      left + right (left first), added by the second thread to reach it
+//      (atomic visit counter, no waiting).  Every FP64 operation is
+//      separately rounded in a fixed order, so the moments are bit-exact
+//      with the oracle.
+#include <cub/cub.cuh>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
 #include "tp_internal.cuh"
-tp_status tp_launch_tree_build(tp_ctx* ctx, int, int) {
-    return tp_set_err(ctx, TP_E_STATE, "tree build not available in this build");
+
+namespace {
+
+__device__ __forceinline__ uint64_t key_at(const uint32_t* __restrict__ codes_sorted,
+                                           const int32_t* __restrict__ perm, int64_t i) {
+    return ((uint64_t)codes_sorted[i] << 32) | (uint32_t)perm[i];
+}
+
+// common prefix length of keys i and j, -1 outside [0, n)
+__device__ __forceinline__ int prefix(const uint32_t* __restrict__ cs, const int32_t* __restrict__ perm, int64_t n,
+                                      int64_t i, int64_t j) {
+    if (j < 0 || j >= n) return -1;
+    return __clzll(key_at(cs, perm, i) ^ key_at(cs, perm, j));
+}
+
+__global__ void k_radix_tree(const uint32_t* __restrict__ cs, const int32_t* __restrict__ perm, int64_t n,
+                             int32_t* __restrict__ left, int32_t* __restrict__ right, int32_t* __restrict__ parent,
+                             int32_t* __restrict__ first, int32_t* __restrict__ last) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int d = (prefix(cs, perm, n, i, i + 1) - prefix(cs, perm, n, i, i - 1)) > 0 ? 1 : -1;
+    const int dmin = prefix(cs, perm, n, i, i - d);
+    int64_t lmax = 2;
+    while (prefix(cs, perm, n, i, i + lmax * d) > dmin) lmax *= 2;
+    int64_t l = 0;
+    for (int64_t t = lmax / 2; t >= 1; t /= 2)
+        if (prefix(cs, perm, n, i, i + (l + t) * d) > dmin) l += t;
+    const int64_t j = i + l * d;
+    const int dnode = prefix(cs, perm, n, i, j);
+    int64_t s = 0;
+    int64_t t = l;
+    do {
+        t = (t + 1) / 2;
+        if (prefix(cs, perm, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    const int64_t g = i + s * d + (d < 0 ? -1 : 0);
+    const int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+    const int64_t lc = (lo == g) ? (n - 1 + g) : g;
+    const int64_t rc = (hi == g + 1) ? (n - 1 + g + 1) : (g + 1);
+    left[i] = (int32_t)lc;
+    right[i] = (int32_t)rc;
+    parent[lc] = (int32_t)i;
+    parent[rc] = (int32_t)i;
+    first[i] = (int32_t)lo;
+    last[i] = (int32_t)hi;
+}
+
+__global__ void k_prim_ranges(int64_t n, int32_t* __restrict__ first, int32_t* __restrict__ last,
+                              int32_t* __restrict__ parent) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    first[n - 1 + k] = (int32_t)k;
+    last[n - 1 + k] = (int32_t)k;
+    if (n == 1) parent[0] = -1;
+}
+
+__global__ void k_root_parent(int32_t* parent) { parent[0] = -1; }
+
+// start_node[first[v]] = v for every cluster leaf v
+__global__ void k_mark_leaves(int64_t n, int leaf_size, const int32_t* __restrict__ first,
+                              const int32_t* __restrict__ last, const int32_t* __restrict__ parent,
+                              int32_t* __restrict__ start_node) {
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= 2 * n - 1) return;
+    const int64_t cnt = (int64_t)last[v] - first[v] + 1;
+    if (cnt > leaf_size) return;
+    const int32_t p = (v == 0) ? -1 : parent[v];
+    if (p >= 0 && (int64_t)last[p] - first[p] + 1 <= leaf_size) return;
+    start_node[first[v]] = (int32_t)v;
+}
+
+struct NonNeg {
+    __device__ __forceinline__ bool operator()(const int32_t& a) const { return a >= 0; }
+};
+
+// primitive moments and the bottom-up pass
+__global__ void k_moments(const double* __restrict__ V, const int32_t* __restrict__ F,
+                          const double* __restrict__ x64, const double* __restrict__ nu64,
+                          const double* __restrict__ w64, const int32_t* __restrict__ perm,
+                          const int32_t* __restrict__ left, const int32_t* __restrict__ right,
+                          const int32_t* __restrict__ parent, int64_t n, int32_t* __restrict__ counter,
+                          double* __restrict__ mom, double* __restrict__ box) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t T = perm[k];
+    int64_t v = n - 1 + k;
+    {
+        double* m = mom + 13 * v;
+        const double w = w64[T];
+        double nu[3];
+        for (int a = 0; a < 3; ++a) nu[a] = nu64[a * n + T];
+        m[0] = w;
+        for (int a = 0; a < 3; ++a) m[1 + a] = __dmul_rn(w, x64[a * n + T]);
+        for (int a = 0; a < 3; ++a) m[4 + a] = __dmul_rn(w, nu[a]);
+        int o = 7;
+        for (int a = 0; a < 3; ++a)
+            for (int c = a; c < 3; ++c) m[o++] = __dmul_rn(__dmul_rn(w, nu[a]), nu[c]);
+        double* b = box + 6 * v;
+        for (int a = 0; a < 3; ++a) {
+            double p0 = V[3 * (int64_t)F[3 * T] + a], p1 = V[3 * (int64_t)F[3 * T + 1] + a],
+                   p2 = V[3 * (int64_t)F[3 * T + 2] + a];
+            double lo = p0, hi = p0;
+            if (p1 < lo) lo = p1;
+            if (p1 > hi) hi = p1;
+            if (p2 < lo) lo = p2;
+            if (p2 > hi) hi = p2;
+            b[a] = lo;
+            b[3 + a] = hi;
+        }
+    }
+    if (n == 1) return;
+    // climb: the second thread to reach a node adds its children
+    while (true) {
+        const int64_t p = parent[v];
+        if (p < 0) break;
+        __threadfence();
+        if (atomicAdd(&counter[p], 1) == 0) break;
+        __threadfence();
+        const int64_t l = left[p], r = right[p];
+        const double* ml = mom + 13 * l;
+        const double* mr = mom + 13 * r;
+        double* m = mom + 13 * p;
+        for (int c = 0; c < 13; ++c) m[c] = __dadd_rn(__ldcg(ml + c), __ldcg(mr + c));
+        const double* bl = box + 6 * l;
+        const double* br = box + 6 * r;
+        double* b = box + 6 * p;
+        for (int a = 0; a < 3; ++a) {
+            double l0 = __ldcg(bl + a), r0 = __ldcg(br + a), l1 = __ldcg(bl + 3 + a), r1 = __ldcg(br + 3 + a);
+            b[a] = l0 < r0 ? l0 : r0;
+            b[3 + a] = l1 > r1 ? l1 : r1;
+        }
+        v = p;
+    }
+}
+
+// f32 node record for the far-field evaluation: X - centre split hi/lo (6),
+// nubar = sum(w nu)/A (3), sqrt(p/q) A (1)
+__global__ void k_node_records(const double* __restrict__ mom, const double* __restrict__ center, int64_t nn,
+                               float* __restrict__ rec) {
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= nn) return;
+    const double* m = mom + 13 * v;
+    float* r = rec + 16 * v;
+    for (int a = 0; a < 3; ++a) {
+        double X = m[1 + a] / m[0] - center[a];
+        float hi = (float)X;
+        r[a] = hi;
+        r[3 + a] = (float)(X - (double)hi);
+        r[6 + a] = (float)(m[4 + a] / m[0]);
+    }
+    r[9] = (float)(1.4142135623730951 * m[0]);
+    for (int a = 10; a < 16; ++a) r[a] = 0.0f;
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+tp_status tp_launch_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits) {
+    const int64_t n = ctx->nt;
+    const int64_t nn = 2 * n - 1;
+    tp_tree& t = ctx->tree;
+    if (t.cap < n) {
+        tp_free(ctx, t.left);
+        tp_free(ctx, t.right);
+        tp_free(ctx, t.parent);
+        tp_free(ctx, t.first);
+        tp_free(ctx, t.last);
+        tp_free(ctx, t.leaves);
+        tp_free(ctx, t.counter);
+        tp_free(ctx, t.mom);
+        tp_free(ctx, t.box);
+        tp_free(ctx, t.nodef);
+        tp_free(ctx, t.nleaves_d);
+        t.left = t.right = t.parent = t.first = t.last = t.leaves = t.counter = t.nleaves_d = nullptr;
+        t.mom = t.box = nullptr;
+        t.nodef = nullptr;
+        TP_TRY(tp_alloc_t(ctx, &t.left, n));
+        TP_TRY(tp_alloc_t(ctx, &t.right, n));
+        TP_TRY(tp_alloc_t(ctx, &t.parent, nn));
+        TP_TRY(tp_alloc_t(ctx, &t.first, nn));
+        TP_TRY(tp_alloc_t(ctx, &t.last, nn));
+        TP_TRY(tp_alloc_t(ctx, &t.leaves, n));
+        TP_TRY(tp_alloc_t(ctx, &t.counter, n));
+        TP_TRY(tp_alloc_t(ctx, &t.mom, 13 * nn));
+        TP_TRY(tp_alloc_t(ctx, &t.box, 6 * nn));
+        TP_TRY(tp_alloc_t(ctx, &t.nodef, 16 * nn));
+        TP_TRY(tp_alloc_t(ctx, &t.nleaves_d, 4));
+        t.cap = n;
+    }
+    t.leaf_size = leaf_size;
+    t.morton_bits = morton_bits;
+    // 1. Morton order of the current centroids; refresh the library-order data
+    TP_TRY(tp_launch_morton_order(ctx, morton_bits));
+    TP_TRY(tp_launch_sorted_soa(ctx));
+    TP_TRY(tp_launch_flagged(ctx));
+    // 2. radix tree
+    if (n > 1) {
+        k_radix_tree<<<nblk(n - 1, 256), 256, 0, ctx->stream>>>(ctx->codes_sorted, ctx->perm, n, t.left, t.right,
+                                                               t.parent, t.first, t.last);
+        ++ctx->nlaunch;
+        k_root_parent<<<1, 1, 0, ctx->stream>>>(t.parent);
+        ++ctx->nlaunch;
+    }
+    k_prim_ranges<<<nblk(n, 256), 256, 0, ctx->stream>>>(n, t.first, t.last, t.parent);
+    ++ctx->nlaunch;
+    // 3. cluster leaves in ascending order of their first triangle
+    int32_t* start_node = ctx->idx_tmp;
+    TP_CU(cudaMemsetAsync(start_node, 0xff, sizeof(int32_t) * n, ctx->stream));
+    k_mark_leaves<<<nblk(nn, 256), 256, 0, ctx->stream>>>(n, leaf_size, t.first, t.last, t.parent, start_node);
+    ++ctx->nlaunch;
+    size_t need = 0;
+    cub::DeviceSelect::If(nullptr, need, start_node, t.leaves, t.nleaves_d, (int)n, NonNeg(), ctx->stream);
+    if (need > ctx->sort_tmp_bytes) {
+        tp_free(ctx, ctx->sort_tmp);
+        ctx->sort_tmp = nullptr;
+        TP_TRY(tp_alloc(ctx, &ctx->sort_tmp, need));
+        ctx->sort_tmp_bytes = need;
+    }
+    size_t have = ctx->sort_tmp_bytes;
+    TP_CU(cub::DeviceSelect::If(ctx->sort_tmp, have, start_node, t.leaves, t.nleaves_d, (int)n, NonNeg(),
+                                ctx->stream));
+    // 4. moments
+    if (n > 1) TP_CU(cudaMemsetAsync(t.counter, 0, sizeof(int32_t) * (n - 1), ctx->stream));
+    k_moments<<<nblk(n, 256), 256, 0, ctx->stream>>>(ctx->V64, ctx->F, ctx->x64, ctx->nu64, ctx->w64, ctx->perm,
+                                                     t.left, t.right, t.parent, n, t.counter, t.mom, t.box);
+    ++ctx->nlaunch;
+    k_node_records<<<nblk(nn, 256), 256, 0, ctx->stream>>>(t.mom, ctx->center, nn, t.nodef);
+    ++ctx->nlaunch;
+    int32_t h = 0;
+    TP_CU(cudaMemcpyAsync(&h, t.nleaves_d, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    TP_CU(cudaStreamSynchronize(ctx->stream));
+    TP_CU(cudaGetLastError());
+    t.nleaves = h;
+    return TP_OK;
 }
