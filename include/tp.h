@@ -128,6 +128,9 @@ typedef struct {
     float ms_total;        /* device time of the whole last call                       */
     int64_t kernel_launches; /* library kernels launched by the last call (CUDA library
                                 calls such as the radix sort are not counted)        */
+    int64_t kernel_pairs;    /* unordered triangle pairs evaluated by the dominant kernel
+                                launch of the last call (direct mode: the far-apart
+                                super-tile pairs), for throughput accounting          */
 } tp_stats;
 
 tp_status tp_get_stats(const tp_ctx* ctx, tp_stats* out);

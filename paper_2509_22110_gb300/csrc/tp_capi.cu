@@ -144,7 +144,10 @@ void release_mesh(tp_ctx* ctx) {
     free_ptr(ctx, ctx->acc);
     free_ptr(ctx, ctx->red);
     free_ptr(ctx, ctx->flagged);
+    free_ptr(ctx, ctx->adjbm);
     free_ptr(ctx, ctx->mlist);
+    free_ptr(ctx, ctx->plist);
+    free_ptr(ctx, ctx->tbox);
     free_ptr(ctx, ctx->gradbuf);
     free_ptr(ctx, ctx->vtmp);
     tp_tree& t = ctx->tree;
@@ -196,7 +199,10 @@ tp_status ensure_buffers(tp_ctx* ctx, int64_t nv, int64_t nt) {
     TP_TRY(tp_alloc_t(ctx, &ctx->red, ctx->red_cap));
     const int64_t nbits = nsup * nsup;
     TP_TRY(tp_alloc_t(ctx, &ctx->flagged, (nbits + 31) / 32));
+    TP_TRY(tp_alloc_t(ctx, &ctx->adjbm, (nbits + 31) / 32));
     TP_TRY(tp_alloc_t(ctx, &ctx->mlist, nsup * (nsup + 1) / 2 + 1));
+    TP_TRY(tp_alloc_t(ctx, &ctx->plist, nsup * (nsup + 1) / 2 + 1));
+    TP_TRY(tp_alloc_t(ctx, &ctx->tbox, 6 * nsup));
     ctx->cap_nv = nv;
     ctx->cap_nt = nt;
     ctx->cap_ntp = ntp;
@@ -262,7 +268,7 @@ tp_status tp_create(tp_ctx** out, int device, void* cuda_stream) {
     for (int i = 0; i < 4; ++i) cudaEventCreate(&ctx->ev[i]);
     if (tp_alloc_t(ctx, &ctx->derr, 4) != TP_OK || tp_alloc_t(ctx, &ctx->scalar, 8) != TP_OK ||
         tp_alloc_t(ctx, &ctx->center, 3) != TP_OK || tp_alloc_t(ctx, &ctx->bounds, 6) != TP_OK ||
-        tp_alloc_t(ctx, &ctx->mcount, 4) != TP_OK) {
+        tp_alloc_t(ctx, &ctx->mcount, 16) != TP_OK) {
         tp_destroy(ctx);
         return TP_E_OOM;
     }
@@ -345,10 +351,8 @@ tp_status tp_mesh_upload(tp_ctx* ctx, const void* V, int64_t nv, int v_dtype, co
             TP_TRY(tp_launch_morton_order(ctx, 30));
         }
         TP_TRY(tp_launch_sorted_soa(ctx));
-        if (!posonly) {
-            TP_TRY(tp_launch_flagged(ctx));
-            TP_TRY(tp_count_excluded(ctx));
-        }
+        TP_TRY(tp_launch_flagged(ctx, !posonly));
+        if (!posonly) TP_TRY(tp_count_excluded(ctx));
     }
     cudaEventRecord(ctx->ev[3], ctx->stream);
     TP_TRY(take_device_error(ctx, "tp_mesh_upload"));
@@ -427,6 +431,8 @@ static tp_status run_eval(tp_ctx* ctx, const tp_params* prm, bool want_grad, voi
         ctx->stats.pairs_exact = n_direct_pairs(ctx);
         ctx->stats.tile_pairs = ctx->nsup * (ctx->nsup + 1) / 2;
         ctx->stats.tile_pairs_masked = ctx->n_masked;
+        ctx->stats.tile_pairs_precise = ctx->n_precise;
+        ctx->stats.kernel_pairs = ctx->pairs_fast;
     } else {
         TP_TRY(tp_launch_bh(ctx, prm, prm->mode == TP_LEARNED));
     }

@@ -19,23 +19,26 @@
 // q = 8, p = 16.
 //
 // Work decomposition.  Triangles are in Morton order, padded to super-tiles
-// of 1024.  A work item is a super-tile pair (I <= J).  A persistent block
-// (8 warps, one per SM) keeps the 1024 targets of I in registers (each lane
+// of 1536.  A work item is a super-tile pair (I <= J).  A persistent block
+// (12 warps, one per SM) keeps the 1536 targets of I in registers (each lane
 // 2 packed pairs of consecutive targets, FP32x2 arithmetic) and streams the
-// 1024 sources of J through shared memory in chunks of 128 with
+// 1536 sources of J through shared memory in chunks of 128 with
 // cp.async.bulk (TMA bulk copies, completion on an mbarrier, bounded
 // waits).  Per source every lane adds its 4 pair contributions to packed
 // target accumulators; the source contributions of the warp are reduced by
 // a butterfly transpose (8 values over 32 lanes in 9 shuffles) and written
-// once per warp; per chunk the block sums its 8 warps and promotes to FP64
+// once per warp; per chunk the block sums its 12 warps and promotes to FP64
 // with one global atomic add per source and accumulator.  Target partials
-// (FP32 over one super-tile) are promoted to FP64 in shared memory and
-// flushed when the block moves to another target row.
+// (FP32 over one super-tile) are promoted to FP64 with one global atomic add
+// per target and accumulator per item.
 //
-// Pairs of super-tiles that contain a pair of triangles sharing a vertex
-// (and all diagonal items) are "masked" items, processed by the MASKED
-// instantiation, which tests adjacency per pair.  All other items are
-// branch-free.
+// Three kinds of items, three instantiations:
+//   FAST    - super-tiles far apart: d = x_hi,T - x_hi,S (FP32 centroids);
+//   PRECISE - super-tiles closer than a fraction of the mesh size:
+//             d = (hi_T - hi_S) + (lo_T - lo_S), which removes the FP32
+//             cancellation of nearby centroids;
+//   MASKED  - a pair of triangles sharing a vertex inside (and all diagonal
+//             items): hi/lo differences plus a per-pair exclusion test.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -43,14 +46,16 @@
 
 namespace {
 
-constexpr int WARPS = 8;
+constexpr int WARPS = 12;
 constexpr int THREADS = WARPS * 32;
-constexpr int NCHUNK = TP_SUPER / TP_CHUNK;  // chunks per super-tile
-constexpr int SMEM_TACC = TP_NACC * TP_SUPER * 8;        // 64 KB
-constexpr int SMEM_SACC = WARPS * TP_CHUNK * TP_NACC * 4;  // 32 KB
+constexpr int NCHUNK = TP_SUPER / TP_CHUNK;                // chunks per super-tile
+constexpr int SMEM_SACC = WARPS * TP_CHUNK * TP_NACC * 4;  // 48 KB
 constexpr int CHUNK_BYTES = TP_CHUNK * TP_SRCW * 4;        // 10 KB
-constexpr int SMEM_GRAD = SMEM_TACC + SMEM_SACC + 2 * CHUNK_BYTES + 64;
+constexpr int SMEM_GRAD = SMEM_SACC + 2 * CHUNK_BYTES + 64;
 constexpr int SMEM_ENERGY = 2 * CHUNK_BYTES + 64 + WARPS * 8;
+static_assert(TP_SUPER == WARPS * 128, "a warp owns 128 targets of the super-tile");
+
+enum { K_FAST = 0, K_PRECISE = 1, K_MASKED = 2 };
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
@@ -103,18 +108,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 struct DirectArgs {
-    const float* soa;     // 10 planes of ntp: x_hi[3], x_lo[3], nu[3], w~
-    const float* src;     // [ntp][TP_SRCW]
-    const int32_t* Fs;    // [ntp][3]
-    double* acc;          // [TP_NACC][ntp]
-    const unsigned* flagged;  // bitmap nsup*nsup
-    const int32_t* mlist; // masked items (I << 16 | J)
-    int64_t nmasked;
+    const float* soa;         // 10 planes of ntp: x_hi[3], x_lo[3], nu[3], w~
+    const float* src;         // [ntp][TP_SRCW]
+    const int32_t* Fs;        // [ntp][3]
+    double* acc;              // [TP_NACC][ntp]
+    const unsigned* flagged;  // bitmap nsup*nsup: items not for the FAST kernel
+    const int32_t* list;      // PRECISE / MASKED items (I << 16 | J)
     int64_t ntp;
     int nsup;
     int edge_only;
     unsigned* derr;
-    double* partial;      // per-block energy partials (energy kernel)
+    double* partial;          // per-block energy partials (energy kernel)
 };
 
 // item index <-> (I, J), I <= J, row-major over I
@@ -124,7 +128,6 @@ struct ItemIter {
         n = nsup;
         int i = 0;
         int64_t off = 0;
-        // rows have n-i items; a short loop (nsup is at most a few thousand)
         while (off + (n - i) <= idx) {
             off += n - i;
             ++i;
@@ -145,19 +148,64 @@ __device__ __forceinline__ bool item_flagged(const unsigned* bm, int nsup, int I
     return (bm[bit >> 5] >> (bit & 31)) & 1u;
 }
 
+// The sequence of items of one block: a contiguous slice of the triangular
+// index space with flagged items skipped (FAST), or a slice of a list.
+template <int KIND>
+struct ItemSeq {
+    const unsigned* flagged;
+    const int32_t* list;
+    int nsup;
+    int64_t idx, hi;
+    ItemIter it;
+    int I, J;
+    __device__ void load() {
+        if (KIND == K_FAST) {
+            while (idx < hi && item_flagged(flagged, nsup, it.I, it.J)) {
+                ++idx;
+                it.next();
+            }
+            I = it.I;
+            J = it.J;
+        } else if (idx < hi) {
+            const int32_t e = list[idx];
+            I = e >> 16;
+            J = e & 0xffff;
+        }
+    }
+    __device__ void start(const DirectArgs& a, int64_t lo, int64_t h) {
+        flagged = a.flagged;
+        list = a.list;
+        nsup = a.nsup;
+        idx = lo;
+        hi = h;
+        if (KIND == K_FAST && lo < h) it.set(lo, nsup);
+        load();
+    }
+    __device__ bool valid() const { return idx < hi; }
+    __device__ void next() {
+        ++idx;
+        if (KIND == K_FAST) it.next();
+        load();
+    }
+};
+
 struct SrcRec {
     float2 h[3], l[3], n[3], w;
 };
 
+template <bool LO>
 __device__ __forceinline__ void load_src(const float* rec, SrcRec& s) {
     const float4* r = reinterpret_cast<const float4*>(rec);
-    float4 a = r[0], b = r[1], c = r[2], d = r[3], e = r[4];
+    float4 a = r[0], b = r[1], d = r[3], e = r[4];
     s.h[0] = make_float2(a.x, a.y);
     s.h[1] = make_float2(a.z, a.w);
     s.h[2] = make_float2(b.x, b.y);
-    s.l[0] = make_float2(b.z, b.w);
-    s.l[1] = make_float2(c.x, c.y);
-    s.l[2] = make_float2(c.z, c.w);
+    if (LO) {
+        float4 c = r[2];
+        s.l[0] = make_float2(b.z, b.w);
+        s.l[1] = make_float2(c.x, c.y);
+        s.l[2] = make_float2(c.z, c.w);
+    }
     s.n[0] = make_float2(d.x, d.y);
     s.n[1] = make_float2(d.z, d.w);
     s.n[2] = make_float2(e.x, e.y);
@@ -168,12 +216,13 @@ struct TgtPair {
     float2 h[3], l[3], n[3], w;
 };
 
+template <bool LO>
 __device__ __forceinline__ void load_tgt(const float* soa, int64_t ntp, int64_t t0, TgtPair& t) {
     // t0 even: (t0, t0+1) from each plane as one float2
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         t.h[k] = *reinterpret_cast<const float2*>(soa + (0 + k) * ntp + t0);
-        t.l[k] = *reinterpret_cast<const float2*>(soa + (3 + k) * ntp + t0);
+        if (LO) t.l[k] = *reinterpret_cast<const float2*>(soa + (3 + k) * ntp + t0);
         t.n[k] = *reinterpret_cast<const float2*>(soa + (6 + k) * ntp + t0);
     }
     t.w = *reinterpret_cast<const float2*>(soa + 9 * ntp + t0);
@@ -198,19 +247,27 @@ __device__ __forceinline__ float2 powq_m1(float2 x, float2& xq) {
     }
 }
 
+template <bool LO>
+__device__ __forceinline__ void pair_diff(const TgtPair& t, const SrcRec& s, float2 d[3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (LO) d[k] = add2(add2(t.h[k], neg2(s.h[k])), add2(t.l[k], neg2(s.l[k])));
+        else d[k] = add2(t.h[k], neg2(s.h[k]));
+    }
+}
+
 // One packed evaluation: target pair t against one source s (both halves share s).
-// valid_mask: per half, 1.0 admitted, 0.0 excluded (MASKED only).
-template <int Q, bool MASKED>
+// valid: per half 1 admitted, 0 excluded (MASKED only).
+template <int Q, int KIND>
 __device__ __forceinline__ void pair_grad(const TgtPair& t, const SrcRec& s, Acc8& at, Acc8& as, float2 valid) {
     float2 d[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) d[k] = add2(add2(t.h[k], neg2(s.h[k])), add2(t.l[k], neg2(s.l[k])));
+    pair_diff<KIND != K_FAST>(t, s, d);
     float2 r2 = mul2(d[0], d[0]);
     r2 = fma2(d[1], d[1], r2);
     r2 = fma2(d[2], d[2], r2);
     float2 inv = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
     float2 wts = mul2(t.w, s.w);
-    if (MASKED) {
+    if (KIND == K_MASKED) {
         inv = make_float2(valid.x != 0.f ? inv.x : 0.f, valid.y != 0.f ? inv.y : 0.f);
         wts = mul2(wts, valid);
     }
@@ -249,17 +306,16 @@ __device__ __forceinline__ void pair_grad(const TgtPair& t, const SrcRec& s, Acc
 }
 
 // Energy only: returns w~_S * s6 per half (the caller multiplies by w~_T at the end).
-template <int Q, bool MASKED>
+template <int Q, int KIND>
 __device__ __forceinline__ float2 pair_energy(const TgtPair& t, const SrcRec& s, float2 valid) {
     float2 d[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) d[k] = add2(add2(t.h[k], neg2(s.h[k])), add2(t.l[k], neg2(s.l[k])));
+    pair_diff<KIND != K_FAST>(t, s, d);
     float2 r2 = mul2(d[0], d[0]);
     r2 = fma2(d[1], d[1], r2);
     r2 = fma2(d[2], d[2], r2);
     float2 inv = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
     float2 ws = s.w;
-    if (MASKED) {
+    if (KIND == K_MASKED) {
         inv = make_float2(valid.x != 0.f ? inv.x : 0.f, valid.y != 0.f ? inv.y : 0.f);
         ws = mul2(ws, valid);
     }
@@ -312,125 +368,101 @@ __device__ __forceinline__ int3 load_face(const int32_t* Fs, int64_t k) {
     return make_int3(Fs[3 * k], Fs[3 * k + 1], Fs[3 * k + 2]);
 }
 
+// Double-buffered TMA staging of the source chunks of a block's item sequence.
+template <int KIND>
+struct ChunkPipe {
+    float* chunk;
+    uint64_t* mbar;
+    uint32_t phases;       // bit b: parity of the next completion of buffer b
+    int64_t g;             // chunks consumed so far
+    ItemSeq<KIND> nseq;    // the item of the next chunk to load
+    int nc;                // its chunk index
+    __device__ void init(float* c, uint64_t* m, const ItemSeq<KIND>& seq) {
+        chunk = c;
+        mbar = m;
+        phases = 0u;
+        g = 0;
+        nseq = seq;
+        nc = 0;
+    }
+    __device__ void issue(const DirectArgs& A, int buf) {
+        if (nseq.valid()) {
+            const float* srcp = A.src + ((int64_t)nseq.J * TP_SUPER + (int64_t)nc * TP_CHUNK) * TP_SRCW;
+            mbar_expect_tx(&mbar[buf], CHUNK_BYTES);
+            tma_load_1d(chunk + buf * TP_CHUNK * TP_SRCW, srcp, CHUNK_BYTES, &mbar[buf]);
+        }
+    }
+    __device__ void advance() {
+        if (++nc >= NCHUNK) {
+            nc = 0;
+            nseq.next();
+        }
+    }
+    // wait for chunk g, then queue chunk g+1 into the other buffer; false on timeout
+    __device__ bool acquire(const DirectArgs& A, const float*& cb) {
+        const int buf = (int)(g & 1);
+        bool ok = mbar_wait_bounded(&mbar[buf], (phases >> buf) & 1u);
+        phases ^= 1u << buf;
+        if (__syncthreads_or(!ok)) return false;
+        if (threadIdx.x == 0) issue(A, buf ^ 1);
+        advance();
+        cb = chunk + buf * TP_CHUNK * TP_SRCW;
+        ++g;
+        return true;
+    }
+};
+
 // ------------------------------------------------------------ gradient kernel
-template <int Q, bool MASKED>
-__global__ void __launch_bounds__(THREADS, 1) k_pairs_grad(DirectArgs A, int64_t item_lo, int64_t item_hi_total) {
+template <int Q, int KIND>
+__global__ void __launch_bounds__(THREADS, 1) k_pairs_grad(DirectArgs A, int64_t nitems) {
     extern __shared__ __align__(128) unsigned char smem[];
-    double* tacc = reinterpret_cast<double*>(smem);                           // [8][1024]
-    float* sacc = reinterpret_cast<float*>(smem + SMEM_TACC);                 // [WARPS][CHUNK][8]
-    float* chunk = reinterpret_cast<float*>(smem + SMEM_TACC + SMEM_SACC);    // [2][CHUNK][SRCW]
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + SMEM_TACC + SMEM_SACC + 2 * CHUNK_BYTES);
-    __shared__ int s_abort;
+    float* sacc = reinterpret_cast<float*>(smem);                                 // [WARPS][CHUNK][8]
+    float* chunk = reinterpret_cast<float*>(smem + SMEM_SACC);                    // [2][CHUNK][SRCW]
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + SMEM_SACC + 2 * CHUNK_BYTES);
+    constexpr bool LO = KIND != K_FAST;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t ntp = A.ntp;
-
-    // static split of this kernel's item range over the blocks
-    const int64_t total = item_hi_total;
-    const int64_t lo = item_lo + (total * blockIdx.x) / gridDim.x;
-    const int64_t hi = item_lo + (total * (blockIdx.x + 1)) / gridDim.x;
+    const int64_t lo = (nitems * blockIdx.x) / gridDim.x;
+    const int64_t hi = (nitems * (blockIdx.x + 1)) / gridDim.x;
     if (lo >= hi) return;
+
+    ItemSeq<KIND> seq;
+    seq.start(A, lo, hi);
+    if (!seq.valid()) return;  // uniform across the block
 
     if (tid == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
         mbar_fence_init();
-        s_abort = 0;
     }
-    for (int i = tid; i < TP_NACC * TP_SUPER; i += THREADS) tacc[i] = 0.0;
     __syncthreads();
+    ChunkPipe<KIND> pipe;
+    pipe.init(chunk, mbar, seq);
+    if (tid == 0) pipe.issue(A, 0);
+    pipe.advance();
 
-    // item sequence of this block: masked list entries, or triangular indices
-    // with flagged items skipped
-    auto item_at = [&](int64_t idx, int& I, int& J) {
-        int32_t e = A.mlist[idx];
-        I = e >> 16;
-        J = e & 0xffff;
-    };
-    ItemIter it;
-    int64_t idx = lo;
-    int curI = -1, curJ = -1;
-    // find first valid item
-    if (MASKED) {
-        item_at(idx, curI, curJ);
-    } else {
-        it.set(idx, A.nsup);
-        while (idx < hi && item_flagged(A.flagged, A.nsup, it.I, it.J)) {
-            ++idx;
-            it.next();
-        }
-        if (idx >= hi) return;  // uniform across the block
-        curI = it.I;
-        curJ = it.J;
-    }
-
-    // producer state (thread 0 issues loads; every thread tracks phases)
-    uint32_t phase[2] = {0u, 0u};
-    int64_t g = 0;  // global chunk counter of this block
-    // the next chunk to load: (item idx, I, J, chunk c)
-    int64_t nidx = idx;
-    int nI = curI, nJ = curJ, nc = 0;
-    ItemIter nit = it;
-    auto advance_next = [&]() {
-        if (++nc >= NCHUNK) {
-            nc = 0;
-            if (MASKED) {
-                ++nidx;
-                if (nidx < hi) item_at(nidx, nI, nJ);
-            } else {
-                ++nidx;
-                nit.next();
-                while (nidx < hi && item_flagged(A.flagged, A.nsup, nit.I, nit.J)) {
-                    ++nidx;
-                    nit.next();
-                }
-                nI = nit.I;
-                nJ = nit.J;
-            }
-        }
-    };
-    auto issue = [&](int buf) {
-        if (nidx < hi) {
-            const float* srcp = A.src + ((int64_t)nJ * TP_SUPER + (int64_t)nc * TP_CHUNK) * TP_SRCW;
-            mbar_expect_tx(&mbar[buf], CHUNK_BYTES);
-            tma_load_1d(chunk + buf * TP_CHUNK * TP_SRCW, srcp, CHUNK_BYTES, &mbar[buf]);
-        }
-    };
-    if (tid == 0) issue(0);
-    advance_next();
-
-    // targets of the current row
     TgtPair tp[2];
     int rowI = -1;
     const int pbase = warp * 64 + lane;  // pair index within the super-tile: pbase, pbase+32
 
-    while (idx < hi) {
-        const int I = curI, J = curJ;
+    while (seq.valid()) {
+        const int I = seq.I, J = seq.J;
         if (I != rowI) {
-            // flush FP64 target accumulators of the previous row
-            if (rowI >= 0) {
-                __syncthreads();
-                for (int i = tid; i < TP_NACC * TP_SUPER; i += THREADS) {
-                    int c = i / TP_SUPER, t = i % TP_SUPER;
-                    double v = tacc[i];
-                    if (v != 0.0) atomicAdd(&A.acc[c * ntp + (int64_t)rowI * TP_SUPER + t], v);
-                    tacc[i] = 0.0;
-                }
-                __syncthreads();
-            }
             rowI = I;
 #pragma unroll
-            for (int P = 0; P < 2; ++P) load_tgt(A.soa, ntp, (int64_t)I * TP_SUPER + 2 * (pbase + 32 * P), tp[P]);
+            for (int P = 0; P < 2; ++P)
+                load_tgt<LO>(A.soa, ntp, (int64_t)I * TP_SUPER + 2 * (pbase + 32 * P), tp[P]);
         }
         int3 tf[2][2];
-        int64_t tg[2][2];
-        if (MASKED) {
+        int tl[2][2];  // target positions within the super-tile
+        if (KIND == K_MASKED) {
 #pragma unroll
             for (int P = 0; P < 2; ++P)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    tg[P][h] = (int64_t)I * TP_SUPER + 2 * (pbase + 32 * P) + h;
-                    tf[P][h] = load_face(A.Fs, tg[P][h]);
+                    tl[P][h] = 2 * (pbase + 32 * P) + h;
+                    tf[P][h] = load_face(A.Fs, (int64_t)I * TP_SUPER + tl[P][h]);
                 }
         }
         Acc8 at[2];
@@ -439,43 +471,44 @@ __global__ void __launch_bounds__(THREADS, 1) k_pairs_grad(DirectArgs A, int64_t
 #pragma unroll
             for (int c = 0; c < TP_NACC; ++c) at[P].v[c] = make_float2(0.f, 0.f);
 
-        for (int c = 0; c < NCHUNK; ++c, ++g) {
-            const int buf = (int)(g & 1);
-            bool ok = mbar_wait_bounded(&mbar[buf], phase[buf]);
-            phase[buf] ^= 1u;
-            if (__syncthreads_or(!ok)) {
+        for (int c = 0; c < NCHUNK; ++c) {
+            const float* cb;
+            if (!pipe.acquire(A, cb)) {
                 if (tid == 0) tp_dev_error(A.derr, TP_DERR_TIMEOUT);
                 return;
             }
-            if (tid == 0) issue(buf ^ 1);
-            advance_next();
-            const float* cb = chunk + buf * TP_CHUNK * TP_SRCW;
             const int64_t sbase = (int64_t)J * TP_SUPER + (int64_t)c * TP_CHUNK;
+            // on a diagonal item a warp whose 128 targets all lie above this chunk has no pair in it
+            const bool skip = (KIND == K_MASKED) && (I == J) && (c < warp);
+            if (!skip) {
 #pragma unroll 1
-            for (int s = 0; s < TP_CHUNK; ++s) {
-                SrcRec sr;
-                load_src(cb + s * TP_SRCW, sr);
-                Acc8 as;
+                for (int s = 0; s < TP_CHUNK; ++s) {
+                    SrcRec sr;
+                    load_src<LO>(cb + s * TP_SRCW, sr);
+                    Acc8 as;
 #pragma unroll
-                for (int k = 0; k < TP_NACC; ++k) as.v[k] = make_float2(0.f, 0.f);
-                float2 valid[2] = {make_float2(1.f, 1.f), make_float2(1.f, 1.f)};
-                if (MASKED) {
-                    const int64_t sg = sbase + s;
-                    int3 sf = load_face(A.Fs, sg);
+                    for (int k = 0; k < TP_NACC; ++k) as.v[k] = make_float2(0.f, 0.f);
+                    float2 valid[2] = {make_float2(1.f, 1.f), make_float2(1.f, 1.f)};
+                    if (KIND == K_MASKED) {
+                        const int sl = c * TP_CHUNK + s;
+                        const int3 sf = load_face(A.Fs, sbase + s);
 #pragma unroll
-                    for (int P = 0; P < 2; ++P) {
-                        float v0 = ((I != J || sg > tg[P][0]) && !share_vertex(tf[P][0], sf, A.edge_only)) ? 1.f : 0.f;
-                        float v1 = ((I != J || sg > tg[P][1]) && !share_vertex(tf[P][1], sf, A.edge_only)) ? 1.f : 0.f;
-                        valid[P] = make_float2(v0, v1);
+                        for (int P = 0; P < 2; ++P) {
+                            float v0 = ((I != J || sl > tl[P][0]) && !share_vertex(tf[P][0], sf, A.edge_only)) ? 1.f : 0.f;
+                            float v1 = ((I != J || sl > tl[P][1]) && !share_vertex(tf[P][1], sf, A.edge_only)) ? 1.f : 0.f;
+                            valid[P] = make_float2(v0, v1);
+                        }
                     }
+#pragma unroll
+                    for (int P = 0; P < 2; ++P) pair_grad<Q, KIND>(tp[P], sr, at[P], as, valid[P]);
+                    float v[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) v[k] = as.v[k].x + as.v[k].y;
+                    float r = warp_transpose_reduce8(v, lane);
+                    if ((lane & 3) == 0) sacc[(warp * TP_CHUNK + s) * TP_NACC + ((lane >> 2) & 7)] = r;
                 }
-#pragma unroll
-                for (int P = 0; P < 2; ++P) pair_grad<Q, MASKED>(tp[P], sr, at[P], as, valid[P]);
-                float v[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) v[k] = as.v[k].x + as.v[k].y;
-                float r = warp_transpose_reduce8(v, lane);
-                if ((lane & 3) == 0) sacc[(warp * TP_CHUNK + s) * TP_NACC + ((lane >> 2) & 7)] = r;
+            } else {
+                for (int i = lane; i < TP_CHUNK * TP_NACC; i += 32) sacc[warp * TP_CHUNK * TP_NACC + i] = 0.f;
             }
             __syncthreads();
             // sum the warps' source partials of this chunk and promote to FP64
@@ -483,62 +516,41 @@ __global__ void __launch_bounds__(THREADS, 1) k_pairs_grad(DirectArgs A, int64_t
                 float ssum = 0.f;
 #pragma unroll
                 for (int w = 0; w < WARPS; ++w) ssum += sacc[w * TP_CHUNK * TP_NACC + i];
-                int s = i / TP_NACC, comp = i % TP_NACC;
+                const int s = i / TP_NACC, comp = i % TP_NACC;
                 if (ssum != 0.f) atomicAdd(&A.acc[comp * ntp + sbase + s], (double)ssum);
             }
             __syncthreads();
         }
-        // promote the row's FP32 target partials of this item to FP64
+        // promote the item's FP32 target partials to FP64
 #pragma unroll
         for (int P = 0; P < 2; ++P) {
-            const int t0 = 2 * (pbase + 32 * P);
+            const int64_t t0 = (int64_t)I * TP_SUPER + 2 * (pbase + 32 * P);
 #pragma unroll
             for (int k = 0; k < TP_NACC; ++k) {
-                tacc[k * TP_SUPER + t0] += (double)at[P].v[k].x;
-                tacc[k * TP_SUPER + t0 + 1] += (double)at[P].v[k].y;
+                if (at[P].v[k].x != 0.f) atomicAdd(&A.acc[k * ntp + t0], (double)at[P].v[k].x);
+                if (at[P].v[k].y != 0.f) atomicAdd(&A.acc[k * ntp + t0 + 1], (double)at[P].v[k].y);
             }
         }
-        // next item
-        ++idx;
-        if (MASKED) {
-            if (idx < hi) item_at(idx, curI, curJ);
-        } else {
-            it.next();
-            while (idx < hi && item_flagged(A.flagged, A.nsup, it.I, it.J)) {
-                ++idx;
-                it.next();
-            }
-            curI = it.I;
-            curJ = it.J;
-        }
-    }
-    __syncthreads();
-    if (rowI >= 0) {
-        for (int i = tid; i < TP_NACC * TP_SUPER; i += THREADS) {
-            int c = i / TP_SUPER, t = i % TP_SUPER;
-            double v = tacc[i];
-            if (v != 0.0) atomicAdd(&A.acc[c * ntp + (int64_t)rowI * TP_SUPER + t], v);
-        }
+        seq.next();
     }
 }
 
 // ------------------------------------------------------------ energy kernel
 // Same item decomposition; every lane accumulates sum_S w~_S s6 for its 4
 // targets in FP32 per item, promoted to FP64 per item; the block writes one
-// FP64 partial (deterministic final reduction on the host side of the call).
-template <int Q, bool MASKED>
-__global__ void __launch_bounds__(THREADS, 1) k_pairs_energy(DirectArgs A, int64_t item_lo, int64_t item_hi_total,
-                                                             int partial_off) {
+// FP64 partial, summed by a deterministic reduction.
+template <int Q, int KIND>
+__global__ void __launch_bounds__(THREADS, 1) k_pairs_energy(DirectArgs A, int64_t nitems, int partial_off) {
     extern __shared__ __align__(128) unsigned char smem[];
     float* chunk = reinterpret_cast<float*>(smem);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * CHUNK_BYTES);
     double* wsum = reinterpret_cast<double*>(smem + 2 * CHUNK_BYTES + 64);
+    constexpr bool LO = KIND != K_FAST;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t ntp = A.ntp;
-    const int64_t total = item_hi_total;
-    const int64_t lo = item_lo + (total * blockIdx.x) / gridDim.x;
-    const int64_t hi = item_lo + (total * (blockIdx.x + 1)) / gridDim.x;
+    const int64_t lo = (nitems * blockIdx.x) / gridDim.x;
+    const int64_t hi = (nitems * (blockIdx.x + 1)) / gridDim.x;
     double esum = 0.0;
 
     if (tid == 0) {
@@ -547,129 +559,68 @@ __global__ void __launch_bounds__(THREADS, 1) k_pairs_energy(DirectArgs A, int64
         mbar_fence_init();
     }
     __syncthreads();
-
-    auto item_at = [&](int64_t idx, int& I, int& J) {
-        int32_t e = A.mlist[idx];
-        I = e >> 16;
-        J = e & 0xffff;
-    };
-    ItemIter it;
-    int64_t idx = lo;
-    int curI = -1, curJ = -1;
-    bool any = lo < hi;
-    if (any) {
-        if (MASKED) {
-            item_at(idx, curI, curJ);
-        } else {
-            it.set(idx, A.nsup);
-            while (idx < hi && item_flagged(A.flagged, A.nsup, it.I, it.J)) {
-                ++idx;
-                it.next();
-            }
-            curI = it.I;
-            curJ = it.J;
-        }
-    }
-    uint32_t phase[2] = {0u, 0u};
-    int64_t g = 0;
-    int64_t nidx = idx;
-    int nI = curI, nJ = curJ, nc = 0;
-    ItemIter nit = it;
-    auto advance_next = [&]() {
-        if (++nc >= NCHUNK) {
-            nc = 0;
-            ++nidx;
-            if (MASKED) {
-                if (nidx < hi) item_at(nidx, nI, nJ);
-            } else {
-                nit.next();
-                while (nidx < hi && item_flagged(A.flagged, A.nsup, nit.I, nit.J)) {
-                    ++nidx;
-                    nit.next();
-                }
-                nI = nit.I;
-                nJ = nit.J;
-            }
-        }
-    };
-    auto issue = [&](int buf) {
-        if (nidx < hi) {
-            const float* srcp = A.src + ((int64_t)nJ * TP_SUPER + (int64_t)nc * TP_CHUNK) * TP_SRCW;
-            mbar_expect_tx(&mbar[buf], CHUNK_BYTES);
-            tma_load_1d(chunk + buf * TP_CHUNK * TP_SRCW, srcp, CHUNK_BYTES, &mbar[buf]);
-        }
-    };
-    if (idx < hi) {
-        if (tid == 0) issue(0);
-        advance_next();
+    ItemSeq<KIND> seq;
+    seq.start(A, lo, hi);
+    ChunkPipe<KIND> pipe;
+    pipe.init(chunk, mbar, seq);
+    if (seq.valid()) {
+        if (tid == 0) pipe.issue(A, 0);
+        pipe.advance();
     }
     const int pbase = warp * 64 + lane;
     bool aborted = false;
-    while (idx < hi) {
-        const int I = curI, J = curJ;
+    while (seq.valid() && !aborted) {
+        const int I = seq.I, J = seq.J;
         TgtPair tp[2];
         int3 tf[2][2];
-        int64_t tg[2][2];
+        int tl[2][2];
 #pragma unroll
         for (int P = 0; P < 2; ++P) {
-            load_tgt(A.soa, ntp, (int64_t)I * TP_SUPER + 2 * (pbase + 32 * P), tp[P]);
-            if (MASKED) {
+            load_tgt<LO>(A.soa, ntp, (int64_t)I * TP_SUPER + 2 * (pbase + 32 * P), tp[P]);
+            if (KIND == K_MASKED) {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    tg[P][h] = (int64_t)I * TP_SUPER + 2 * (pbase + 32 * P) + h;
-                    tf[P][h] = load_face(A.Fs, tg[P][h]);
+                    tl[P][h] = 2 * (pbase + 32 * P) + h;
+                    tf[P][h] = load_face(A.Fs, (int64_t)I * TP_SUPER + tl[P][h]);
                 }
             }
         }
         float2 ea[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-        for (int c = 0; c < NCHUNK; ++c, ++g) {
-            const int buf = (int)(g & 1);
-            bool ok = mbar_wait_bounded(&mbar[buf], phase[buf]);
-            phase[buf] ^= 1u;
-            if (__syncthreads_or(!ok)) {
+        for (int c = 0; c < NCHUNK; ++c) {
+            const float* cb;
+            if (!pipe.acquire(A, cb)) {
                 if (tid == 0) tp_dev_error(A.derr, TP_DERR_TIMEOUT);
                 aborted = true;
                 break;
             }
-            if (tid == 0) issue(buf ^ 1);
-            advance_next();
-            const float* cb = chunk + buf * TP_CHUNK * TP_SRCW;
             const int64_t sbase = (int64_t)J * TP_SUPER + (int64_t)c * TP_CHUNK;
+            const bool skip = (KIND == K_MASKED) && (I == J) && (c < warp);
+            if (!skip) {
 #pragma unroll 2
-            for (int s = 0; s < TP_CHUNK; ++s) {
-                SrcRec sr;
-                load_src(cb + s * TP_SRCW, sr);
-                float2 valid[2] = {make_float2(1.f, 1.f), make_float2(1.f, 1.f)};
-                if (MASKED) {
-                    const int64_t sgi = sbase + s;
-                    int3 sf = load_face(A.Fs, sgi);
+                for (int s = 0; s < TP_CHUNK; ++s) {
+                    SrcRec sr;
+                    load_src<LO>(cb + s * TP_SRCW, sr);
+                    float2 valid[2] = {make_float2(1.f, 1.f), make_float2(1.f, 1.f)};
+                    if (KIND == K_MASKED) {
+                        const int sl = c * TP_CHUNK + s;
+                        const int3 sf = load_face(A.Fs, sbase + s);
 #pragma unroll
-                    for (int P = 0; P < 2; ++P) {
-                        float v0 = ((I != J || sgi > tg[P][0]) && !share_vertex(tf[P][0], sf, A.edge_only)) ? 1.f : 0.f;
-                        float v1 = ((I != J || sgi > tg[P][1]) && !share_vertex(tf[P][1], sf, A.edge_only)) ? 1.f : 0.f;
-                        valid[P] = make_float2(v0, v1);
+                        for (int P = 0; P < 2; ++P) {
+                            float v0 = ((I != J || sl > tl[P][0]) && !share_vertex(tf[P][0], sf, A.edge_only)) ? 1.f : 0.f;
+                            float v1 = ((I != J || sl > tl[P][1]) && !share_vertex(tf[P][1], sf, A.edge_only)) ? 1.f : 0.f;
+                            valid[P] = make_float2(v0, v1);
+                        }
                     }
-                }
 #pragma unroll
-                for (int P = 0; P < 2; ++P) ea[P] = add2(ea[P], pair_energy<Q, MASKED>(tp[P], sr, valid[P]));
+                    for (int P = 0; P < 2; ++P) ea[P] = add2(ea[P], pair_energy<Q, KIND>(tp[P], sr, valid[P]));
+                }
             }
             __syncthreads();
         }
         if (aborted) break;
 #pragma unroll
         for (int P = 0; P < 2; ++P) esum += (double)(tp[P].w.x * ea[P].x) + (double)(tp[P].w.y * ea[P].y);
-        ++idx;
-        if (MASKED) {
-            if (idx < hi) item_at(idx, curI, curJ);
-        } else {
-            it.next();
-            while (idx < hi && item_flagged(A.flagged, A.nsup, it.I, it.J)) {
-                ++idx;
-                it.next();
-            }
-            curI = it.I;
-            curJ = it.J;
-        }
+        seq.next();
     }
     // deterministic block reduction
     for (int o = 16; o > 0; o >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, o);
@@ -748,25 +699,33 @@ __global__ void k_pairs_f64(const double* x64, const double* nu64, const double*
 }
 
 template <int Q>
-tp_status launch_grad_q(tp_ctx* ctx, DirectArgs& A) {
+tp_status launch_grad_q(tp_ctx* ctx, DirectArgs A) {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_pairs_grad<Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_GRAD);
-        cudaFuncSetAttribute(k_pairs_grad<Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_GRAD);
+        cudaFuncSetAttribute(k_pairs_grad<Q, K_FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_GRAD);
+        cudaFuncSetAttribute(k_pairs_grad<Q, K_PRECISE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_GRAD);
+        cudaFuncSetAttribute(k_pairs_grad<Q, K_MASKED>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_GRAD);
         attr = true;
     }
     const int64_t nitems = (int64_t)ctx->nsup * (ctx->nsup + 1) / 2;
-    const int64_t nfree = nitems - ctx->n_masked;
-    if (nfree > 0) {
-        int grid = (int)std::min<int64_t>(ctx->num_sms, nfree);
-        cudaEventRecord(ctx->ev[0], ctx->stream);
-        k_pairs_grad<Q, false><<<grid, THREADS, SMEM_GRAD, ctx->stream>>>(A, 0, nitems);
+    const int64_t nfast = nitems - ctx->n_masked - ctx->n_precise;
+    cudaEventRecord(ctx->ev[0], ctx->stream);
+    if (nfast > 0) {
+        const int grid = (int)std::min<int64_t>(ctx->num_sms, nfast);
+        k_pairs_grad<Q, K_FAST><<<grid, THREADS, SMEM_GRAD, ctx->stream>>>(A, nitems);
         ++ctx->nlaunch;
-        cudaEventRecord(ctx->ev[1], ctx->stream);
+    }
+    cudaEventRecord(ctx->ev[1], ctx->stream);
+    if (ctx->n_precise > 0) {
+        A.list = ctx->plist;
+        const int grid = (int)std::min<int64_t>(ctx->num_sms, ctx->n_precise);
+        k_pairs_grad<Q, K_PRECISE><<<grid, THREADS, SMEM_GRAD, ctx->stream>>>(A, ctx->n_precise);
+        ++ctx->nlaunch;
     }
     if (ctx->n_masked > 0) {
-        int grid = (int)std::min<int64_t>(ctx->num_sms, ctx->n_masked);
-        k_pairs_grad<Q, true><<<grid, THREADS, SMEM_GRAD, ctx->stream>>>(A, 0, ctx->n_masked);
+        A.list = ctx->mlist;
+        const int grid = (int)std::min<int64_t>(ctx->num_sms, ctx->n_masked);
+        k_pairs_grad<Q, K_MASKED><<<grid, THREADS, SMEM_GRAD, ctx->stream>>>(A, ctx->n_masked);
         ++ctx->nlaunch;
     }
     TP_CU(cudaGetLastError());
@@ -774,19 +733,24 @@ tp_status launch_grad_q(tp_ctx* ctx, DirectArgs& A) {
 }
 
 template <int Q>
-tp_status launch_energy_q(tp_ctx* ctx, DirectArgs& A, int* nparts) {
+tp_status launch_energy_q(tp_ctx* ctx, DirectArgs A, int* nparts) {
     const int64_t nitems = (int64_t)ctx->nsup * (ctx->nsup + 1) / 2;
-    const int64_t nfree = nitems - ctx->n_masked;
-    int g1 = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, nfree));
-    int g2 = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, ctx->n_masked));
+    const int64_t nfast = nitems - ctx->n_masked - ctx->n_precise;
+    const int g1 = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, nfast));
+    const int g2 = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, ctx->n_precise));
+    const int g3 = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, ctx->n_masked));
     cudaEventRecord(ctx->ev[0], ctx->stream);
-    k_pairs_energy<Q, false><<<g1, THREADS, SMEM_ENERGY, ctx->stream>>>(A, 0, nfree > 0 ? nitems : 0, 0);
+    k_pairs_energy<Q, K_FAST><<<g1, THREADS, SMEM_ENERGY, ctx->stream>>>(A, nfast > 0 ? nitems : 0, 0);
     ++ctx->nlaunch;
     cudaEventRecord(ctx->ev[1], ctx->stream);
-    k_pairs_energy<Q, true><<<g2, THREADS, SMEM_ENERGY, ctx->stream>>>(A, 0, ctx->n_masked, g1);
+    A.list = ctx->plist;
+    k_pairs_energy<Q, K_PRECISE><<<g2, THREADS, SMEM_ENERGY, ctx->stream>>>(A, ctx->n_precise, g1);
+    ++ctx->nlaunch;
+    A.list = ctx->mlist;
+    k_pairs_energy<Q, K_MASKED><<<g3, THREADS, SMEM_ENERGY, ctx->stream>>>(A, ctx->n_masked, g1 + g2);
     ++ctx->nlaunch;
     TP_CU(cudaGetLastError());
-    *nparts = g1 + g2;
+    *nparts = g1 + g2 + g3;
     return TP_OK;
 }
 
@@ -797,8 +761,7 @@ DirectArgs make_args(tp_ctx* ctx, const tp_params* prm) {
     A.Fs = ctx->Fs;
     A.acc = ctx->acc;
     A.flagged = ctx->flagged;
-    A.mlist = ctx->mlist;
-    A.nmasked = ctx->n_masked;
+    A.list = ctx->mlist;
     A.ntp = ctx->ntp;
     A.nsup = (int)ctx->nsup;
     A.edge_only = (prm->flags & TP_EXCLUDE_EDGE) ? 1 : 0;

@@ -7,7 +7,7 @@
 //   x64/nu64[3][nt], w64[nt]   f64 triangle data in the caller's order
 //   perm[nt], iperm[nt]        library order (Morton) <-> caller's order
 //   soa: 10 planes of ntp f32  (x_hi[3], x_lo[3], nu[3], sqrt(2) w) in
-//        library order, padded to a multiple of TP_SUPER with zero-area
+//        library order, padded to a multiple of TP_SUPER (1536) with zero-area
 //        triangles placed far away
 //   src[ntp][20] f32           the same 10 values, each stored twice, one
 //                              80-byte record per triangle: the unit the
@@ -25,11 +25,14 @@
 
 #include "../../include/tp.h"
 
-#define TP_SUPER 1024      // triangles per super-tile (one block's target set)
+#define TP_SUPER 1536      // triangles per super-tile (one block's target set)
 #define TP_CHUNK 128       // sources staged per shared-memory chunk
 #define TP_SRCW 20         // floats per staged source record
 #define TP_NACC 8          // accumulators per triangle
 #define TP_SPIN_LIMIT (1u << 26)
+// super-tile pairs whose centroid boxes are closer than this fraction of the
+// mesh's centroid-box diagonal form centroid differences from hi + lo parts
+#define TP_PRECISE_GAP_REL 0.02f
 
 // device error bits
 #define TP_DERR_TIMEOUT 0x1u
@@ -89,14 +92,19 @@ struct tp_ctx {
     double* red = nullptr;          // reduction scratch
     double* scalar = nullptr;       // [4] device scalars (energy ...)
     unsigned* derr = nullptr;       // device error word
-    unsigned* flagged = nullptr;    // bitmap nsup*nsup of super-tile pairs needing masks
-    int32_t* mlist = nullptr;       // compact list of masked super-tile pairs (I,J)
-    int32_t* mcount = nullptr;
+    unsigned* adjbm = nullptr;      // bitmap nsup*nsup: super-tile pairs holding a vertex-sharing pair (or I == J)
+    unsigned* flagged = nullptr;    // bitmap nsup*nsup: super-tile pairs not handled by the fast kernel
+    int32_t* mlist = nullptr;       // compact list of masked super-tile pairs (I,J): a vertex-sharing pair inside
+    int32_t* plist = nullptr;       // compact list of unmasked pairs of nearby super-tiles (hi/lo centroids)
+    int32_t* mcount = nullptr;      // [8]: counts of mlist, plist, then 3 u64 pair counts (fast, precise, masked)
+    float* tbox = nullptr;          // [nsup][6] f32 centroid boxes of the super-tiles
     void* sort_tmp = nullptr;
     size_t sort_tmp_bytes = 0;
     double* host_pinned = nullptr;  // small pinned staging
 
     int64_t n_masked = 0;
+    int64_t n_precise = 0;
+    int64_t pairs_fast = 0, pairs_precise = 0, pairs_masked_items = 0;  // unordered real pairs per item kind
     int64_t n_excluded_ordered = 0;  // ordered pairs T != S sharing a vertex
     int64_t cap_nv = 0, cap_nt = 0, cap_ntp = 0, red_cap = 0;
     double* gradbuf = nullptr;      // [3nv] device staging of host gradients
@@ -139,7 +147,7 @@ inline tp_status tp_alloc_t(tp_ctx* ctx, T** p, size_t n) {
 tp_status tp_launch_tri_data(tp_ctx* ctx);
 tp_status tp_launch_morton_order(tp_ctx* ctx, int morton_bits);
 tp_status tp_launch_sorted_soa(tp_ctx* ctx);
-tp_status tp_launch_flagged(tp_ctx* ctx);
+tp_status tp_launch_flagged(tp_ctx* ctx, bool topology);
 tp_status tp_build_v2t(tp_ctx* ctx);
 tp_status tp_count_excluded(tp_ctx* ctx);
 // tp_direct.cu

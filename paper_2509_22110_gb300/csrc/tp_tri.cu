@@ -14,6 +14,7 @@
 #include <cub/cub.cuh>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "tp_internal.cuh"
 
@@ -236,15 +237,77 @@ __global__ void k_flag_diag(int nsup, unsigned* __restrict__ bm) {
     atomicOr(&bm[bit >> 5], 1u << (bit & 31));
 }
 
-__global__ void k_flag_compact(const unsigned* __restrict__ bm, int nsup, int32_t* __restrict__ list,
-                               int32_t* __restrict__ count) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t n = (int64_t)nsup * nsup;
+// centroid box of every super-tile (f32 hi parts, library order)
+__global__ void k_tile_boxes(const float* __restrict__ soa, int64_t ntp, int64_t nt, float* __restrict__ tbox) {
+    __shared__ float red[6][256];
+    const int64_t I = blockIdx.x;
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int t = threadIdx.x; t < TP_SUPER; t += blockDim.x) {
+        const int64_t k = I * TP_SUPER + t;
+        if (k >= nt) break;
+        for (int a = 0; a < 3; ++a) {
+            const float v = soa[a * ntp + k];
+            mn[a] = fminf(mn[a], v);
+            mx[a] = fmaxf(mx[a], v);
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        red[a][threadIdx.x] = mn[a];
+        red[3 + a][threadIdx.x] = mx[a];
+    }
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int a = 0; a < 3; ++a) {
+                red[a][threadIdx.x] = fminf(red[a][threadIdx.x], red[a][threadIdx.x + o]);
+                red[3 + a][threadIdx.x] = fmaxf(red[3 + a][threadIdx.x], red[3 + a][threadIdx.x + o]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) tbox[6 * I + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// Sort the super-tile pairs (I <= J) into: masked (a vertex-sharing pair
+// inside, or I == J), precise (unmasked but the two centroid boxes lie
+// closer than delta: centroid differences there need the hi/lo split), and
+// fast (everything else; the bitmap bit stays clear).
+__global__ void k_flag_classify(const unsigned* __restrict__ adj, unsigned* __restrict__ bm, int nsup, int64_t nt,
+                                const float* __restrict__ tbox,
+                                const double* __restrict__ bounds, float delta_rel, int32_t* __restrict__ mlist,
+                                int32_t* __restrict__ plist, int32_t* __restrict__ count,
+                                unsigned long long* __restrict__ npairs) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t n = (int64_t)nsup * nsup;
     if (i >= n) return;
-    if ((bm[i >> 5] >> (i & 31)) & 1u) {
-        int I = (int)(i / nsup), J = (int)(i % nsup);
-        int32_t slot = atomicAdd(count, 1);
-        list[slot] = (I << 16) | J;
+    const int I = (int)(i / nsup), J = (int)(i % nsup);
+    if (J < I) return;
+    // unordered pairs of real (non-padding) triangles in this item
+    const int64_t rI = (nt - (int64_t)I * TP_SUPER) < TP_SUPER ? nt - (int64_t)I * TP_SUPER : TP_SUPER;
+    const int64_t rJ = (nt - (int64_t)J * TP_SUPER) < TP_SUPER ? nt - (int64_t)J * TP_SUPER : TP_SUPER;
+    const unsigned long long pairs = (unsigned long long)(I == J ? rI * (rI - 1) / 2 : rI * rJ);
+    if ((adj[i >> 5] >> (i & 31)) & 1u) {
+        mlist[atomicAdd(&count[0], 1)] = (I << 16) | J;
+        atomicOr(&bm[i >> 5], 1u << (i & 31));
+        atomicAdd(&npairs[2], pairs);
+        return;
+    }
+    double d2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double e = bounds[3 + a] - bounds[a];
+        d2 += e * e;
+    }
+    const float delta = delta_rel * (float)sqrt(d2);
+    float g2 = 0.f;
+    for (int a = 0; a < 3; ++a) {
+        const float gap = fmaxf(0.f, fmaxf(tbox[6 * J + a] - tbox[6 * I + 3 + a], tbox[6 * I + a] - tbox[6 * J + 3 + a]));
+        g2 += gap * gap;
+    }
+    if (g2 < delta * delta) {
+        plist[atomicAdd(&count[1], 1)] = (I << 16) | J;
+        atomicOr(&bm[i >> 5], 1u << (i & 31));
+        atomicAdd(&npairs[1], pairs);
+    } else {
+        atomicAdd(&npairs[0], pairs);
     }
 }
 
@@ -322,22 +385,36 @@ tp_status tp_build_v2t(tp_ctx* ctx) {
     return TP_OK;
 }
 
-tp_status tp_launch_flagged(tp_ctx* ctx) {
+tp_status tp_launch_flagged(tp_ctx* ctx, bool topology) {
     const int nsup = (int)ctx->nsup;
     const int64_t nbits = (int64_t)nsup * nsup;
+    if (topology) {
+        TP_CU(cudaMemsetAsync(ctx->adjbm, 0, sizeof(unsigned) * ((nbits + 31) / 32), ctx->stream));
+        k_flag_pairs<<<blocks_for(ctx->nt, 256), 256, 0, ctx->stream>>>(ctx->F, ctx->perm, ctx->iperm, ctx->v2t_off,
+                                                                        ctx->v2t, ctx->nt, nsup, ctx->adjbm);
+        ++ctx->nlaunch;
+        k_flag_diag<<<blocks_for(nsup, 256), 256, 0, ctx->stream>>>(nsup, ctx->adjbm);
+        ++ctx->nlaunch;
+    }
     TP_CU(cudaMemsetAsync(ctx->flagged, 0, sizeof(unsigned) * ((nbits + 31) / 32), ctx->stream));
-    TP_CU(cudaMemsetAsync(ctx->mcount, 0, sizeof(int32_t), ctx->stream));
-    k_flag_pairs<<<blocks_for(ctx->nt, 256), 256, 0, ctx->stream>>>(ctx->F, ctx->perm, ctx->iperm, ctx->v2t_off,
-                                                                    ctx->v2t, ctx->nt, nsup, ctx->flagged);
+    TP_CU(cudaMemsetAsync(ctx->mcount, 0, 8 * sizeof(int32_t), ctx->stream));
+    k_tile_boxes<<<nsup, 256, 0, ctx->stream>>>(ctx->soa, ctx->ntp, ctx->nt, ctx->tbox);
     ++ctx->nlaunch;
-    k_flag_diag<<<blocks_for(nsup, 256), 256, 0, ctx->stream>>>(nsup, ctx->flagged);
+    unsigned long long* npairs = reinterpret_cast<unsigned long long*>(ctx->mcount + 2);
+    k_flag_classify<<<blocks_for(nbits, 256), 256, 0, ctx->stream>>>(ctx->adjbm, ctx->flagged, nsup, ctx->nt, ctx->tbox,
+                                                                     ctx->bounds, TP_PRECISE_GAP_REL, ctx->mlist,
+                                                                     ctx->plist, ctx->mcount, npairs);
     ++ctx->nlaunch;
-    k_flag_compact<<<blocks_for(nbits, 256), 256, 0, ctx->stream>>>(ctx->flagged, nsup, ctx->mlist, ctx->mcount);
-    ++ctx->nlaunch;
-    int32_t h = 0;
-    TP_CU(cudaMemcpyAsync(&h, ctx->mcount, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    int32_t h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    TP_CU(cudaMemcpyAsync(h, ctx->mcount, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
     TP_CU(cudaStreamSynchronize(ctx->stream));
-    ctx->n_masked = h;
+    ctx->n_masked = h[0];
+    ctx->n_precise = h[1];
+    unsigned long long p3[3];
+    memcpy(p3, h + 2, sizeof(p3));
+    ctx->pairs_fast = (int64_t)p3[0];
+    ctx->pairs_precise = (int64_t)p3[1];
+    ctx->pairs_masked_items = (int64_t)p3[2];
     return TP_OK;
 }
 
