@@ -52,6 +52,8 @@ struct BHArgs {
     const double* mom;
     const double* box;
     const float* nodef;
+    const double* adm64;
+    const float* adm32;
     double theta;
     int leaf_size;
     int edge_only;
@@ -108,27 +110,78 @@ __device__ __forceinline__ void gather_pair(const Tgt& t, const float* sh, const
     }
 }
 
-__device__ __forceinline__ bool admissible(const double* bl, const double* bc, const double* mc, double theta) {
-    bool disjoint = false;
+// Target-leaf constants of the admissibility test.
+struct LeafAdm {
+    double bl[6];      // FP64 vertex box
+    double cl[3];      // box centre (bl_min + bl_max) * 0.5
+    double dl;         // box diagonal
+    float out[6], in[6], cl32[3], dl32;
+};
+
+__device__ __forceinline__ void leaf_adm(const double* box, LeafAdm& L) {
+    double dl2 = 0.0;
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-        if (bl[3 + a] < bc[a] || bc[3 + a] < bl[a]) disjoint = true;
-    if (!disjoint) return false;
-    double dl2 = 0.0, dc2 = 0.0, r2 = 0.0;
+    for (int a = 0; a < 6; ++a) L.bl[a] = box[a];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        double el = __dsub_rn(bl[3 + a], bl[a]);
-        double ec = __dsub_rn(bc[3 + a], bc[a]);
-        double cl = __dmul_rn(__dadd_rn(bl[a], bl[3 + a]), 0.5);
-        double X = __ddiv_rn(mc[1 + a], mc[0]);
-        double t = __dsub_rn(X, cl);
+        const double el = __dsub_rn(L.bl[3 + a], L.bl[a]);
         dl2 = __dadd_rn(dl2, __dmul_rn(el, el));
-        dc2 = __dadd_rn(dc2, __dmul_rn(ec, ec));
+        L.cl[a] = __dmul_rn(__dadd_rn(L.bl[a], L.bl[3 + a]), 0.5);
+        L.out[a] = __double2float_rd(L.bl[a]);
+        L.out[3 + a] = __double2float_ru(L.bl[3 + a]);
+        L.in[a] = __double2float_ru(L.bl[a]);
+        L.in[3 + a] = __double2float_rd(L.bl[3 + a]);
+        L.cl32[a] = (float)L.cl[a];
+    }
+    L.dl = __dsqrt_rn(dl2);
+    L.dl32 = (float)L.dl;
+}
+
+// Admissibility of cluster C for target leaf L:
+//   boxes strictly disjoint along some axis, and
+//   diag(C) < theta * (|X_C - c_L| - diag(L)/2),
+// with every quantity in FP64, separately rounded, in a fixed order.  An FP32
+// pre-test settles the decision whenever its error bound allows (outward and
+// inward rounded boxes for the strict comparisons; a 1e-5 relative margin for
+// the size test, far above FP32 rounding); otherwise the FP64 test decides.
+__device__ __forceinline__ bool admissible(const LeafAdm& L, const float* c32, const double* bc,
+                                           const double* c64, double theta, float theta32) {
+    bool sure = false, amb = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (L.out[3 + a] < c32[a] || c32[3 + a] < L.out[a]) sure = true;
+        else if (!(L.in[3 + a] >= c32[6 + a] && c32[9 + a] >= L.in[a])) amb = true;
+    }
+    if (!sure) {
+        if (!amb) return false;
+        bool disjoint = false;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (L.bl[3 + a] < bc[a] || bc[3 + a] < L.bl[a]) disjoint = true;
+        if (!disjoint) return false;
+    }
+    float r2f = 0.f, M = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float t = c32[12 + a] - L.cl32[a];
+        r2f = fmaf(t, t, r2f);
+        M += fabsf(c32[12 + a]) + fabsf(L.cl32[a]);
+    }
+    const float distf = sqrtf(r2f);
+    const float rhsf = theta32 * (distf - 0.5f * L.dl32);
+    const float lhsf = c32[15];
+    const float margin = 1e-5f * (lhsf + theta32 * (distf + L.dl32 + M));
+    if (lhsf < rhsf - margin) return true;
+    if (lhsf > rhsf + margin) return false;
+    double r2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double t = __dsub_rn(c64[a], L.cl[a]);
         r2 = __dadd_rn(r2, __dmul_rn(t, t));
     }
-    double diag_l = __dsqrt_rn(dl2), diag_c = __dsqrt_rn(dc2), dist = __dsqrt_rn(r2);
-    double rhs = __dmul_rn(theta, __dsub_rn(dist, __dmul_rn(0.5, diag_l)));
-    return diag_c < rhs;
+    const double dist = __dsqrt_rn(r2);
+    const double rhs = __dmul_rn(theta, __dsub_rn(dist, __dmul_rn(0.5, L.dl)));
+    return c64[3] < rhs;
 }
 
 __device__ __forceinline__ bool adjacent(int3 a, int3 b, int edge_only) {
@@ -142,18 +195,24 @@ __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
     __shared__ int32_t s_stack[BH_WARPS][BH_STACK];
     __shared__ int32_t s_far[BH_WARPS][BH_FAR];
     __shared__ int32_t s_near[BH_WARPS][BH_NEAR];
+    __shared__ __align__(16) float s_stg[BH_WARPS][32 * 16];
+    __shared__ int32_t s_stg_cnt[BH_WARPS][32];
+    __shared__ int4 s_stg_f[BH_WARPS][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t li = (int64_t)blockIdx.x * BH_WARPS + warp;
     if (li >= A.nleaves) return;
     int32_t* st = s_stack[warp];
     int32_t* far = s_far[warp];
     int32_t* nearl = s_near[warp];
+    float* stg = s_stg[warp];
+    int32_t* stg_cnt = s_stg_cnt[warp];
+    int4* stg_f = s_stg_f[warp];
     const int64_t L = A.leaves[li];
     const int64_t fL = A.first[L];
     const int cnt = A.last[L] - A.first[L] + 1;
-    double bl[6];
-#pragma unroll
-    for (int a = 0; a < 6; ++a) bl[a] = A.box[6 * L + a];
+    LeafAdm la;
+    leaf_adm(A.box + 6 * L, la);
+    const float theta32 = (float)A.theta;
     const int t = lane & 15, half = lane >> 4;
     const int64_t k = fL + t;
     const bool active = t < cnt;
@@ -177,41 +236,77 @@ __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
     unsigned long long n_near = 0, n_far = 0, n_farp = 0;
     const unsigned lt = (1u << lane) - 1u;
 
+    // far list: stage 32 node records at a time in shared memory, then every
+    // half-warp sweeps them (half h takes records h, h+2, ...)
     auto flush_far = [&](int nf) {
         float a32[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int i = half; i < nf; i += 2) {
-            const float* r = A.nodef + 16 * (int64_t)far[i];
-            float sh[3] = {r[0], r[1], r[2]}, sl[3] = {r[3], r[4], r[5]}, sn[3] = {r[6], r[7], r[8]};
-            if (active) gather_pair<Q>(tg, sh, sl, sn, r[9], a32);
-            if (active) {
-                n_far += 1;
-                n_farp += (unsigned long long)(A.last[far[i]] - A.first[far[i]] + 1);
+        for (int b0 = 0; b0 < nf; b0 += 32) {
+            const int nb = nf - b0 < 32 ? nf - b0 : 32;
+            __syncwarp();
+            if (lane < nb) {
+                const int32_t C = far[b0 + lane];
+                const float4* r = reinterpret_cast<const float4*>(A.nodef + 16 * (int64_t)C);
+                float4* d = reinterpret_cast<float4*>(stg + lane * 16);
+                d[0] = r[0];
+                d[1] = r[1];
+                d[2] = r[2];
+                stg_cnt[lane] = A.last[C] - A.first[C] + 1;
+            }
+            __syncwarp();
+            for (int i = half; i < nb; i += 2) {
+                const float* r = stg + i * 16;
+                if (active) {
+                    gather_pair<Q>(tg, r, r + 3, r + 6, r[9], a32);
+                    n_far += 1;
+                    n_farp += (unsigned long long)stg_cnt[i];
+                }
             }
         }
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[c] += (double)a32[c];
     };
+    // near list: stage the members of up to 32 sources at a time (whole near
+    // nodes) in shared memory, then every half-warp sweeps them
     auto flush_near = [&](int nn) {
         float a32[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int i = 0; i < nn; ++i) {
-            const int64_t C = nearl[i];
-            const int64_t f = A.first[C], m = A.last[C] - A.first[C] + 1;
-            for (int64_t j = half; j < m; j += 2) {
-                const int64_t s = f + j;
-                float sh[3], sl[3], sn[3];
+        int i = 0;
+        while (i < nn) {
+            // take whole nodes while they fit in 32 slots
+            int nsrc = 0, i1 = i;
+            while (i1 < nn) {
+                const int m = A.last[nearl[i1]] - A.first[nearl[i1]] + 1;
+                if (nsrc + m > 32) break;
+                nsrc += m;
+                ++i1;
+            }
+            __syncwarp();
+            // lane -> (node, member) by walking the taken nodes
+            {
+                int base = 0;
+                for (int j = i; j < i1; ++j) {
+                    const int64_t C = nearl[j];
+                    const int64_t f = A.first[C];
+                    const int m = A.last[C] - A.first[C] + 1;
+                    if (lane >= base && lane < base + m) {
+                        const int64_t s = f + (lane - base);
+                        float* d = stg + lane * 16;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    sh[c] = A.soa[c * A.ntp + s];
-                    sl[c] = A.soa[(3 + c) * A.ntp + s];
-                    sn[c] = A.soa[(6 + c) * A.ntp + s];
+                        for (int c = 0; c < 10; ++c) d[c] = A.soa[c * A.ntp + s];
+                        stg_f[lane] = make_int4(A.Fs[3 * s], A.Fs[3 * s + 1], A.Fs[3 * s + 2], (int)s);
+                    }
+                    base += m;
                 }
-                const float sw = A.soa[9 * A.ntp + s];
-                const int3 sf = make_int3(A.Fs[3 * s], A.Fs[3 * s + 1], A.Fs[3 * s + 2]);
-                if (active && s != k && !adjacent(tf, sf, A.edge_only)) {
-                    gather_pair<Q>(tg, sh, sl, sn, sw, a32);
+            }
+            __syncwarp();
+            for (int j = half; j < nsrc; j += 2) {
+                const float* r = stg + j * 16;
+                const int4 sf = stg_f[j];
+                if (active && sf.w != (int)k && !adjacent(tf, make_int3(sf.x, sf.y, sf.z), A.edge_only)) {
+                    gather_pair<Q>(tg, r, r + 3, r + 6, r[9], a32);
                     n_near += 1;
                 }
             }
+            i = i1;
         }
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[c] += (double)a32[c];
@@ -229,7 +324,9 @@ __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
         bool is_far = false, is_near = false, is_open = false;
         if (node >= 0) {
             const int cntc = A.last[node] - A.first[node] + 1;
-            if (admissible(bl, A.box + 6 * (int64_t)node, A.mom + 13 * (int64_t)node, A.theta)) is_far = true;
+            if (admissible(la, A.adm32 + 16 * (int64_t)node, A.box + 6 * (int64_t)node, A.adm64 + 4 * (int64_t)node,
+                           A.theta, theta32))
+                is_far = true;
             else if (cntc <= A.leaf_size || node >= A.n - 1) is_near = true;
             else is_open = true;
         }
@@ -308,6 +405,8 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
     A.mom = t.mom;
     A.box = t.box;
     A.nodef = t.nodef;
+    A.adm64 = t.adm64;
+    A.adm32 = t.adm32;
     A.theta = prm->theta;
     A.leaf_size = t.leaf_size;
     A.edge_only = (prm->flags & TP_EXCLUDE_EDGE) ? 1 : 0;

@@ -147,6 +147,7 @@ void release_mesh(tp_ctx* ctx) {
     free_ptr(ctx, ctx->adjbm);
     free_ptr(ctx, ctx->mlist);
     free_ptr(ctx, ctx->plist);
+    free_ptr(ctx, ctx->flist);
     free_ptr(ctx, ctx->tbox);
     free_ptr(ctx, ctx->gradbuf);
     free_ptr(ctx, ctx->vtmp);
@@ -162,6 +163,8 @@ void release_mesh(tp_ctx* ctx) {
     free_ptr(ctx, t.mom);
     free_ptr(ctx, t.box);
     free_ptr(ctx, t.nodef);
+    free_ptr(ctx, t.adm64);
+    free_ptr(ctx, t.adm32);
     t.valid = false;
     t.cap = 0;
     ctx->cap_nv = ctx->cap_nt = 0;
@@ -202,6 +205,7 @@ tp_status ensure_buffers(tp_ctx* ctx, int64_t nv, int64_t nt) {
     TP_TRY(tp_alloc_t(ctx, &ctx->adjbm, (nbits + 31) / 32));
     TP_TRY(tp_alloc_t(ctx, &ctx->mlist, nsup * (nsup + 1) / 2 + 1));
     TP_TRY(tp_alloc_t(ctx, &ctx->plist, nsup * (nsup + 1) / 2 + 1));
+    TP_TRY(tp_alloc_t(ctx, &ctx->flist, nsup * (nsup + 1) / 2 + 1));
     TP_TRY(tp_alloc_t(ctx, &ctx->tbox, 6 * nsup));
     ctx->cap_nv = nv;
     ctx->cap_nt = nt;
@@ -268,7 +272,7 @@ tp_status tp_create(tp_ctx** out, int device, void* cuda_stream) {
     for (int i = 0; i < 4; ++i) cudaEventCreate(&ctx->ev[i]);
     if (tp_alloc_t(ctx, &ctx->derr, 4) != TP_OK || tp_alloc_t(ctx, &ctx->scalar, 8) != TP_OK ||
         tp_alloc_t(ctx, &ctx->center, 3) != TP_OK || tp_alloc_t(ctx, &ctx->bounds, 6) != TP_OK ||
-        tp_alloc_t(ctx, &ctx->mcount, 16) != TP_OK) {
+        tp_alloc_t(ctx, &ctx->mcount, 16) != TP_OK || tp_alloc_t(ctx, &ctx->work, 4) != TP_OK) {
         tp_destroy(ctx);
         return TP_E_OOM;
     }
@@ -432,7 +436,7 @@ static tp_status run_eval(tp_ctx* ctx, const tp_params* prm, bool want_grad, voi
         ctx->stats.tile_pairs = ctx->nsup * (ctx->nsup + 1) / 2;
         ctx->stats.tile_pairs_masked = ctx->n_masked;
         ctx->stats.tile_pairs_precise = ctx->n_precise;
-        ctx->stats.kernel_pairs = ctx->pairs_fast;
+        ctx->stats.kernel_pairs = ctx->pairs_fast + ctx->pairs_precise + ctx->pairs_masked_items;
     } else {
         TP_TRY(tp_launch_bh(ctx, prm, prm->mode == TP_LEARNED));
     }

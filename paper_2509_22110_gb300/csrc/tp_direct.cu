@@ -52,7 +52,7 @@ constexpr int NCHUNK = TP_SUPER / TP_CHUNK;                // chunks per super-t
 constexpr int SMEM_SACC = WARPS * TP_CHUNK * TP_NACC * 4;  // 48 KB
 constexpr int CHUNK_BYTES = TP_CHUNK * TP_SRCW * 4;        // 10 KB
 constexpr int SMEM_GRAD = SMEM_SACC + 2 * CHUNK_BYTES + 64;
-constexpr int SMEM_ENERGY = 2 * CHUNK_BYTES + 64 + WARPS * 8;
+constexpr int SMEM_ENERGY = 2 * CHUNK_BYTES + 64 + WARPS * 8;  // chunks, mbarriers + item slot, warp sums
 static_assert(TP_SUPER == WARPS * 128, "a warp owns 128 targets of the super-tile");
 
 enum { K_FAST = 0, K_PRECISE = 1, K_MASKED = 2 };
@@ -112,81 +112,15 @@ struct DirectArgs {
     const float* src;         // [ntp][TP_SRCW]
     const int32_t* Fs;        // [ntp][3]
     double* acc;              // [TP_NACC][ntp]
-    const unsigned* flagged;  // bitmap nsup*nsup: items not for the FAST kernel
-    const int32_t* list;      // PRECISE / MASKED items (I << 16 | J)
+    const int32_t* mlist;     // MASKED items (I << 16 | J)
+    const int32_t* plist;     // PRECISE items
+    const int32_t* flist;     // FAST items
+    int nm, np, nf;           // their counts; the work queue is mlist, plist, flist in that order
+    unsigned* work;           // dynamic work counter (zeroed before the launch)
     int64_t ntp;
-    int nsup;
     int edge_only;
     unsigned* derr;
     double* partial;          // per-block energy partials (energy kernel)
-};
-
-// item index <-> (I, J), I <= J, row-major over I
-struct ItemIter {
-    int I, J, n;
-    __device__ void set(int64_t idx, int nsup) {
-        n = nsup;
-        int i = 0;
-        int64_t off = 0;
-        while (off + (n - i) <= idx) {
-            off += n - i;
-            ++i;
-        }
-        I = i;
-        J = i + (int)(idx - off);
-    }
-    __device__ void next() {
-        if (++J >= n) {
-            ++I;
-            J = I;
-        }
-    }
-};
-
-__device__ __forceinline__ bool item_flagged(const unsigned* bm, int nsup, int I, int J) {
-    int64_t bit = (int64_t)I * nsup + J;
-    return (bm[bit >> 5] >> (bit & 31)) & 1u;
-}
-
-// The sequence of items of one block: a contiguous slice of the triangular
-// index space with flagged items skipped (FAST), or a slice of a list.
-template <int KIND>
-struct ItemSeq {
-    const unsigned* flagged;
-    const int32_t* list;
-    int nsup;
-    int64_t idx, hi;
-    ItemIter it;
-    int I, J;
-    __device__ void load() {
-        if (KIND == K_FAST) {
-            while (idx < hi && item_flagged(flagged, nsup, it.I, it.J)) {
-                ++idx;
-                it.next();
-            }
-            I = it.I;
-            J = it.J;
-        } else if (idx < hi) {
-            const int32_t e = list[idx];
-            I = e >> 16;
-            J = e & 0xffff;
-        }
-    }
-    __device__ void start(const DirectArgs& a, int64_t lo, int64_t h) {
-        flagged = a.flagged;
-        list = a.list;
-        nsup = a.nsup;
-        idx = lo;
-        hi = h;
-        if (KIND == K_FAST && lo < h) it.set(lo, nsup);
-        load();
-    }
-    __device__ bool valid() const { return idx < hi; }
-    __device__ void next() {
-        ++idx;
-        if (KIND == K_FAST) it.next();
-        load();
-    }
 };
 
 struct SrcRec {
@@ -256,6 +190,20 @@ __device__ __forceinline__ void pair_diff(const TgtPair& t, const SrcRec& s, flo
     }
 }
 
+// x^(Q-1) into xm1 and x^Q + addend into sum (the last product fused with the add)
+template <int Q>
+__device__ __forceinline__ void powq_m1_fma(float2 x, float2 addend, float2& xm1, float2& sum) {
+    float2 x2 = mul2(x, x);
+    float2 x4 = mul2(x2, x2);
+    if (Q == 6) {
+        sum = fma2(x4, x2, addend);
+        xm1 = mul2(x4, x);
+    } else {
+        sum = fma2(x4, x4, addend);
+        xm1 = mul2(mul2(x4, x2), x);
+    }
+}
+
 // One packed evaluation: target pair t against one source s (both halves share s).
 // valid: per half 1 admitted, 0 excluded (MASKED only).
 template <int Q, int KIND>
@@ -278,10 +226,10 @@ __device__ __forceinline__ void pair_grad(const TgtPair& t, const SrcRec& s, Acc
     b = fma2(s.n[1], d[1], b);
     b = fma2(s.n[2], d[2], b);
     float2 al = mul2(a, inv), be = mul2(b, inv);
-    float2 alq, beq;
+    float2 alq;
     float2 al5 = powq_m1<Q>(al, alq);
-    float2 be5 = powq_m1<Q>(be, beq);
-    float2 s6 = add2(alq, beq);
+    float2 be5, s6;
+    powq_m1_fma<Q>(be, alq, be5, s6);  // be^(q-1), and s6 = be^q + al^q with one fused op
     float2 E = mul2(wts, s6);
     float2 wi = mul2(wts, inv);
     float2 A5 = mul2(wi, al5);
@@ -368,268 +316,305 @@ __device__ __forceinline__ int3 load_face(const int32_t* Fs, int64_t k) {
     return make_int3(Fs[3 * k], Fs[3 * k + 1], Fs[3 * k + 2]);
 }
 
-// Double-buffered TMA staging of the source chunks of a block's item sequence.
-template <int KIND>
+// Work item fetched from the dynamic queue: kind and super-tile pair.
+struct Item {
+    int kind, I, J;
+};
+
+__device__ __forceinline__ Item decode_item(const DirectArgs& A, unsigned w) {
+    Item it;
+    int32_t e;
+    if (w < (unsigned)A.nm) {
+        it.kind = K_MASKED;
+        e = A.mlist[w];
+    } else if (w < (unsigned)(A.nm + A.np)) {
+        it.kind = K_PRECISE;
+        e = A.plist[w - A.nm];
+    } else if (w < (unsigned)(A.nm + A.np + A.nf)) {
+        it.kind = K_FAST;
+        e = A.flist[w - A.nm - A.np];
+    } else {
+        it.kind = -1;
+        e = 0;
+    }
+    it.I = e >> 16;
+    it.J = e & 0xffff;
+    return it;
+}
+
+// Double-buffered TMA staging of the 12 source chunks of one item.
 struct ChunkPipe {
     float* chunk;
     uint64_t* mbar;
-    uint32_t phases;       // bit b: parity of the next completion of buffer b
-    int64_t g;             // chunks consumed so far
-    ItemSeq<KIND> nseq;    // the item of the next chunk to load
-    int nc;                // its chunk index
-    __device__ void init(float* c, uint64_t* m, const ItemSeq<KIND>& seq) {
-        chunk = c;
-        mbar = m;
-        phases = 0u;
-        g = 0;
-        nseq = seq;
-        nc = 0;
+    uint32_t phases;  // bit b: parity of the next completion of buffer b
+    __device__ void issue(const DirectArgs& A, int J, int c, int buf) {
+        const float* srcp = A.src + ((int64_t)J * TP_SUPER + (int64_t)c * TP_CHUNK) * TP_SRCW;
+        mbar_expect_tx(&mbar[buf], CHUNK_BYTES);
+        tma_load_1d(chunk + buf * TP_CHUNK * TP_SRCW, srcp, CHUNK_BYTES, &mbar[buf]);
     }
-    __device__ void issue(const DirectArgs& A, int buf) {
-        if (nseq.valid()) {
-            const float* srcp = A.src + ((int64_t)nseq.J * TP_SUPER + (int64_t)nc * TP_CHUNK) * TP_SRCW;
-            mbar_expect_tx(&mbar[buf], CHUNK_BYTES);
-            tma_load_1d(chunk + buf * TP_CHUNK * TP_SRCW, srcp, CHUNK_BYTES, &mbar[buf]);
-        }
-    }
-    __device__ void advance() {
-        if (++nc >= NCHUNK) {
-            nc = 0;
-            nseq.next();
-        }
-    }
-    // wait for chunk g, then queue chunk g+1 into the other buffer; false on timeout
-    __device__ bool acquire(const DirectArgs& A, const float*& cb) {
-        const int buf = (int)(g & 1);
-        bool ok = mbar_wait_bounded(&mbar[buf], (phases >> buf) & 1u);
+    // wait for chunk c (buffer c & 1), then queue chunk c + 1; false on timeout
+    __device__ bool acquire(const DirectArgs& A, int J, int c, const float*& cb) {
+        const int buf = c & 1;
+        const bool ok = mbar_wait_bounded(&mbar[buf], (phases >> buf) & 1u);
         phases ^= 1u << buf;
         if (__syncthreads_or(!ok)) return false;
-        if (threadIdx.x == 0) issue(A, buf ^ 1);
-        advance();
+        if (threadIdx.x == 0 && c + 1 < NCHUNK) issue(A, J, c + 1, buf ^ 1);
         cb = chunk + buf * TP_CHUNK * TP_SRCW;
-        ++g;
         return true;
     }
 };
 
-// ------------------------------------------------------------ gradient kernel
+// block-wide fetch of the next item (thread 0 takes it from the queue)
+__device__ __forceinline__ Item fetch_item(const DirectArgs& A, int* s_item) {
+    if (threadIdx.x == 0) {
+        const unsigned w = atomicAdd(A.work, 1u);
+        const Item it = decode_item(A, w);
+        s_item[0] = it.kind;
+        s_item[1] = it.I;
+        s_item[2] = it.J;
+    }
+    __syncthreads();
+    Item it;
+    it.kind = s_item[0];
+    it.I = s_item[1];
+    it.J = s_item[2];
+    __syncthreads();  // s_item may be overwritten by the next fetch
+    return it;
+}
+
+// The 12 chunks of one item for one item kind; target partials in `at`.
 template <int Q, int KIND>
-__global__ void __launch_bounds__(THREADS, 1) k_pairs_grad(DirectArgs A, int64_t nitems) {
+__device__ __forceinline__ bool grad_item(const DirectArgs& A, ChunkPipe& pipe, float* sacc, int I, int J,
+                                          const TgtPair (&tp)[2], Acc8 (&at)[2], int warp, int lane, int pbase) {
+    constexpr bool LO = KIND != K_FAST;
+    const int64_t ntp = A.ntp;
+    int3 tf[2][2];
+    int tl[2][2];  // target positions within the super-tile
+    if (KIND == K_MASKED) {
+#pragma unroll
+        for (int P = 0; P < 2; ++P)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                tl[P][h] = 2 * (pbase + 32 * P) + h;
+                tf[P][h] = load_face(A.Fs, (int64_t)I * TP_SUPER + tl[P][h]);
+            }
+    }
+    for (int c = 0; c < NCHUNK; ++c) {
+        const float* cb;
+        if (!pipe.acquire(A, J, c, cb)) return false;
+        const int64_t sbase = (int64_t)J * TP_SUPER + (int64_t)c * TP_CHUNK;
+        // on a diagonal item a warp whose 128 targets all lie above this chunk has no pair in it
+        const bool skip = (KIND == K_MASKED) && (I == J) && (c < warp);
+        if (!skip) {
+#pragma unroll 1
+            for (int s = 0; s < TP_CHUNK; ++s) {
+                SrcRec sr;
+                load_src<LO>(cb + s * TP_SRCW, sr);
+                Acc8 as;
+#pragma unroll
+                for (int k = 0; k < TP_NACC; ++k) as.v[k] = make_float2(0.f, 0.f);
+                float2 valid[2] = {make_float2(1.f, 1.f), make_float2(1.f, 1.f)};
+                if (KIND == K_MASKED) {
+                    const int sl = c * TP_CHUNK + s;
+                    const int3 sf = load_face(A.Fs, sbase + s);
+#pragma unroll
+                    for (int P = 0; P < 2; ++P) {
+                        float v0 = ((I != J || sl > tl[P][0]) && !share_vertex(tf[P][0], sf, A.edge_only)) ? 1.f : 0.f;
+                        float v1 = ((I != J || sl > tl[P][1]) && !share_vertex(tf[P][1], sf, A.edge_only)) ? 1.f : 0.f;
+                        valid[P] = make_float2(v0, v1);
+                    }
+                }
+#pragma unroll
+                for (int P = 0; P < 2; ++P) pair_grad<Q, KIND>(tp[P], sr, at[P], as, valid[P]);
+                float v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v[k] = as.v[k].x + as.v[k].y;
+                const float r = warp_transpose_reduce8(v, lane);
+                if ((lane & 3) == 0) sacc[(warp * TP_CHUNK + s) * TP_NACC + ((lane >> 2) & 7)] = r;
+            }
+        } else {
+            for (int i = lane; i < TP_CHUNK * TP_NACC; i += 32) sacc[warp * TP_CHUNK * TP_NACC + i] = 0.f;
+        }
+        __syncthreads();
+        // sum the warps' source partials of this chunk and promote to FP64
+        for (int i = threadIdx.x; i < TP_CHUNK * TP_NACC; i += THREADS) {
+            float ssum = 0.f;
+#pragma unroll
+            for (int w = 0; w < WARPS; ++w) ssum += sacc[w * TP_CHUNK * TP_NACC + i];
+            const int s = i / TP_NACC, comp = i % TP_NACC;
+            if (ssum != 0.f) atomicAdd(&A.acc[comp * ntp + sbase + s], (double)ssum);
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+// ------------------------------------------------------------ gradient kernel
+// Persistent: every block takes items from the queue (masked, then precise,
+// then fast) until it is empty.
+template <int Q>
+__global__ void __launch_bounds__(THREADS, 1) k_pairs_grad(DirectArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     float* sacc = reinterpret_cast<float*>(smem);                                 // [WARPS][CHUNK][8]
     float* chunk = reinterpret_cast<float*>(smem + SMEM_SACC);                    // [2][CHUNK][SRCW]
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + SMEM_SACC + 2 * CHUNK_BYTES);
-    constexpr bool LO = KIND != K_FAST;
+    int* s_item = reinterpret_cast<int*>(smem + SMEM_SACC + 2 * CHUNK_BYTES + 16);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t ntp = A.ntp;
-    const int64_t lo = (nitems * blockIdx.x) / gridDim.x;
-    const int64_t hi = (nitems * (blockIdx.x + 1)) / gridDim.x;
-    if (lo >= hi) return;
-
-    ItemSeq<KIND> seq;
-    seq.start(A, lo, hi);
-    if (!seq.valid()) return;  // uniform across the block
-
     if (tid == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
         mbar_fence_init();
     }
     __syncthreads();
-    ChunkPipe<KIND> pipe;
-    pipe.init(chunk, mbar, seq);
-    if (tid == 0) pipe.issue(A, 0);
-    pipe.advance();
+    ChunkPipe pipe;
+    pipe.chunk = chunk;
+    pipe.mbar = mbar;
+    pipe.phases = 0u;
 
     TgtPair tp[2];
     int rowI = -1;
     const int pbase = warp * 64 + lane;  // pair index within the super-tile: pbase, pbase+32
-
-    while (seq.valid()) {
-        const int I = seq.I, J = seq.J;
-        if (I != rowI) {
-            rowI = I;
+    while (true) {
+        const Item it = fetch_item(A, s_item);
+        if (it.kind < 0) break;
+        if (tid == 0) pipe.issue(A, it.J, 0, 0);
+        if (it.I != rowI) {
+            rowI = it.I;
 #pragma unroll
             for (int P = 0; P < 2; ++P)
-                load_tgt<LO>(A.soa, ntp, (int64_t)I * TP_SUPER + 2 * (pbase + 32 * P), tp[P]);
-        }
-        int3 tf[2][2];
-        int tl[2][2];  // target positions within the super-tile
-        if (KIND == K_MASKED) {
-#pragma unroll
-            for (int P = 0; P < 2; ++P)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    tl[P][h] = 2 * (pbase + 32 * P) + h;
-                    tf[P][h] = load_face(A.Fs, (int64_t)I * TP_SUPER + tl[P][h]);
-                }
+                load_tgt<true>(A.soa, ntp, (int64_t)it.I * TP_SUPER + 2 * (pbase + 32 * P), tp[P]);
         }
         Acc8 at[2];
 #pragma unroll
         for (int P = 0; P < 2; ++P)
 #pragma unroll
             for (int c = 0; c < TP_NACC; ++c) at[P].v[c] = make_float2(0.f, 0.f);
-
-        for (int c = 0; c < NCHUNK; ++c) {
-            const float* cb;
-            if (!pipe.acquire(A, cb)) {
-                if (tid == 0) tp_dev_error(A.derr, TP_DERR_TIMEOUT);
-                return;
-            }
-            const int64_t sbase = (int64_t)J * TP_SUPER + (int64_t)c * TP_CHUNK;
-            // on a diagonal item a warp whose 128 targets all lie above this chunk has no pair in it
-            const bool skip = (KIND == K_MASKED) && (I == J) && (c < warp);
-            if (!skip) {
-#pragma unroll 1
-                for (int s = 0; s < TP_CHUNK; ++s) {
-                    SrcRec sr;
-                    load_src<LO>(cb + s * TP_SRCW, sr);
-                    Acc8 as;
-#pragma unroll
-                    for (int k = 0; k < TP_NACC; ++k) as.v[k] = make_float2(0.f, 0.f);
-                    float2 valid[2] = {make_float2(1.f, 1.f), make_float2(1.f, 1.f)};
-                    if (KIND == K_MASKED) {
-                        const int sl = c * TP_CHUNK + s;
-                        const int3 sf = load_face(A.Fs, sbase + s);
-#pragma unroll
-                        for (int P = 0; P < 2; ++P) {
-                            float v0 = ((I != J || sl > tl[P][0]) && !share_vertex(tf[P][0], sf, A.edge_only)) ? 1.f : 0.f;
-                            float v1 = ((I != J || sl > tl[P][1]) && !share_vertex(tf[P][1], sf, A.edge_only)) ? 1.f : 0.f;
-                            valid[P] = make_float2(v0, v1);
-                        }
-                    }
-#pragma unroll
-                    for (int P = 0; P < 2; ++P) pair_grad<Q, KIND>(tp[P], sr, at[P], as, valid[P]);
-                    float v[8];
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) v[k] = as.v[k].x + as.v[k].y;
-                    float r = warp_transpose_reduce8(v, lane);
-                    if ((lane & 3) == 0) sacc[(warp * TP_CHUNK + s) * TP_NACC + ((lane >> 2) & 7)] = r;
-                }
-            } else {
-                for (int i = lane; i < TP_CHUNK * TP_NACC; i += 32) sacc[warp * TP_CHUNK * TP_NACC + i] = 0.f;
-            }
-            __syncthreads();
-            // sum the warps' source partials of this chunk and promote to FP64
-            for (int i = tid; i < TP_CHUNK * TP_NACC; i += THREADS) {
-                float ssum = 0.f;
-#pragma unroll
-                for (int w = 0; w < WARPS; ++w) ssum += sacc[w * TP_CHUNK * TP_NACC + i];
-                const int s = i / TP_NACC, comp = i % TP_NACC;
-                if (ssum != 0.f) atomicAdd(&A.acc[comp * ntp + sbase + s], (double)ssum);
-            }
-            __syncthreads();
+        bool ok;
+        if (it.kind == K_FAST) ok = grad_item<Q, K_FAST>(A, pipe, sacc, it.I, it.J, tp, at, warp, lane, pbase);
+        else if (it.kind == K_PRECISE) ok = grad_item<Q, K_PRECISE>(A, pipe, sacc, it.I, it.J, tp, at, warp, lane, pbase);
+        else ok = grad_item<Q, K_MASKED>(A, pipe, sacc, it.I, it.J, tp, at, warp, lane, pbase);
+        if (!ok) {
+            if (tid == 0) tp_dev_error(A.derr, TP_DERR_TIMEOUT);
+            return;
         }
         // promote the item's FP32 target partials to FP64
 #pragma unroll
         for (int P = 0; P < 2; ++P) {
-            const int64_t t0 = (int64_t)I * TP_SUPER + 2 * (pbase + 32 * P);
+            const int64_t t0 = (int64_t)it.I * TP_SUPER + 2 * (pbase + 32 * P);
 #pragma unroll
             for (int k = 0; k < TP_NACC; ++k) {
                 if (at[P].v[k].x != 0.f) atomicAdd(&A.acc[k * ntp + t0], (double)at[P].v[k].x);
                 if (at[P].v[k].y != 0.f) atomicAdd(&A.acc[k * ntp + t0 + 1], (double)at[P].v[k].y);
             }
         }
-        seq.next();
     }
 }
 
 // ------------------------------------------------------------ energy kernel
-// Same item decomposition; every lane accumulates sum_S w~_S s6 for its 4
-// targets in FP32 per item, promoted to FP64 per item; the block writes one
-// FP64 partial, summed by a deterministic reduction.
 template <int Q, int KIND>
-__global__ void __launch_bounds__(THREADS, 1) k_pairs_energy(DirectArgs A, int64_t nitems, int partial_off) {
+__device__ __forceinline__ bool energy_item(const DirectArgs& A, ChunkPipe& pipe, int I, int J,
+                                            const TgtPair (&tp)[2], float2 (&ea)[2], int warp, int pbase) {
+    constexpr bool LO = KIND != K_FAST;
+    int3 tf[2][2];
+    int tl[2][2];
+    if (KIND == K_MASKED) {
+#pragma unroll
+        for (int P = 0; P < 2; ++P)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                tl[P][h] = 2 * (pbase + 32 * P) + h;
+                tf[P][h] = load_face(A.Fs, (int64_t)I * TP_SUPER + tl[P][h]);
+            }
+    }
+    for (int c = 0; c < NCHUNK; ++c) {
+        const float* cb;
+        if (!pipe.acquire(A, J, c, cb)) return false;
+        const int64_t sbase = (int64_t)J * TP_SUPER + (int64_t)c * TP_CHUNK;
+        const bool skip = (KIND == K_MASKED) && (I == J) && (c < warp);
+        if (!skip) {
+#pragma unroll 2
+            for (int s = 0; s < TP_CHUNK; ++s) {
+                SrcRec sr;
+                load_src<LO>(cb + s * TP_SRCW, sr);
+                float2 valid[2] = {make_float2(1.f, 1.f), make_float2(1.f, 1.f)};
+                if (KIND == K_MASKED) {
+                    const int sl = c * TP_CHUNK + s;
+                    const int3 sf = load_face(A.Fs, sbase + s);
+#pragma unroll
+                    for (int P = 0; P < 2; ++P) {
+                        float v0 = ((I != J || sl > tl[P][0]) && !share_vertex(tf[P][0], sf, A.edge_only)) ? 1.f : 0.f;
+                        float v1 = ((I != J || sl > tl[P][1]) && !share_vertex(tf[P][1], sf, A.edge_only)) ? 1.f : 0.f;
+                        valid[P] = make_float2(v0, v1);
+                    }
+                }
+#pragma unroll
+                for (int P = 0; P < 2; ++P) ea[P] = add2(ea[P], pair_energy<Q, KIND>(tp[P], sr, valid[P]));
+            }
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+// Every lane accumulates sum_S w~_S s6 for its 4 targets in FP32 per item,
+// promoted to FP64 per item; the block writes one FP64 partial, summed by a
+// deterministic reduction.
+template <int Q>
+__global__ void __launch_bounds__(THREADS, 1) k_pairs_energy(DirectArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     float* chunk = reinterpret_cast<float*>(smem);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * CHUNK_BYTES);
+    int* s_item = reinterpret_cast<int*>(smem + 2 * CHUNK_BYTES + 16);
     double* wsum = reinterpret_cast<double*>(smem + 2 * CHUNK_BYTES + 64);
-    constexpr bool LO = KIND != K_FAST;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t ntp = A.ntp;
-    const int64_t lo = (nitems * blockIdx.x) / gridDim.x;
-    const int64_t hi = (nitems * (blockIdx.x + 1)) / gridDim.x;
     double esum = 0.0;
-
     if (tid == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
         mbar_fence_init();
     }
     __syncthreads();
-    ItemSeq<KIND> seq;
-    seq.start(A, lo, hi);
-    ChunkPipe<KIND> pipe;
-    pipe.init(chunk, mbar, seq);
-    if (seq.valid()) {
-        if (tid == 0) pipe.issue(A, 0);
-        pipe.advance();
-    }
+    ChunkPipe pipe;
+    pipe.chunk = chunk;
+    pipe.mbar = mbar;
+    pipe.phases = 0u;
     const int pbase = warp * 64 + lane;
-    bool aborted = false;
-    while (seq.valid() && !aborted) {
-        const int I = seq.I, J = seq.J;
-        TgtPair tp[2];
-        int3 tf[2][2];
-        int tl[2][2];
+    TgtPair tp[2];
+    int rowI = -1;
+    while (true) {
+        const Item it = fetch_item(A, s_item);
+        if (it.kind < 0) break;
+        if (tid == 0) pipe.issue(A, it.J, 0, 0);
+        if (it.I != rowI) {
+            rowI = it.I;
 #pragma unroll
-        for (int P = 0; P < 2; ++P) {
-            load_tgt<LO>(A.soa, ntp, (int64_t)I * TP_SUPER + 2 * (pbase + 32 * P), tp[P]);
-            if (KIND == K_MASKED) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    tl[P][h] = 2 * (pbase + 32 * P) + h;
-                    tf[P][h] = load_face(A.Fs, (int64_t)I * TP_SUPER + tl[P][h]);
-                }
-            }
+            for (int P = 0; P < 2; ++P)
+                load_tgt<true>(A.soa, ntp, (int64_t)it.I * TP_SUPER + 2 * (pbase + 32 * P), tp[P]);
         }
         float2 ea[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-        for (int c = 0; c < NCHUNK; ++c) {
-            const float* cb;
-            if (!pipe.acquire(A, cb)) {
-                if (tid == 0) tp_dev_error(A.derr, TP_DERR_TIMEOUT);
-                aborted = true;
-                break;
-            }
-            const int64_t sbase = (int64_t)J * TP_SUPER + (int64_t)c * TP_CHUNK;
-            const bool skip = (KIND == K_MASKED) && (I == J) && (c < warp);
-            if (!skip) {
-#pragma unroll 2
-                for (int s = 0; s < TP_CHUNK; ++s) {
-                    SrcRec sr;
-                    load_src<LO>(cb + s * TP_SRCW, sr);
-                    float2 valid[2] = {make_float2(1.f, 1.f), make_float2(1.f, 1.f)};
-                    if (KIND == K_MASKED) {
-                        const int sl = c * TP_CHUNK + s;
-                        const int3 sf = load_face(A.Fs, sbase + s);
-#pragma unroll
-                        for (int P = 0; P < 2; ++P) {
-                            float v0 = ((I != J || sl > tl[P][0]) && !share_vertex(tf[P][0], sf, A.edge_only)) ? 1.f : 0.f;
-                            float v1 = ((I != J || sl > tl[P][1]) && !share_vertex(tf[P][1], sf, A.edge_only)) ? 1.f : 0.f;
-                            valid[P] = make_float2(v0, v1);
-                        }
-                    }
-#pragma unroll
-                    for (int P = 0; P < 2; ++P) ea[P] = add2(ea[P], pair_energy<Q, KIND>(tp[P], sr, valid[P]));
-                }
-            }
-            __syncthreads();
+        bool ok;
+        if (it.kind == K_FAST) ok = energy_item<Q, K_FAST>(A, pipe, it.I, it.J, tp, ea, warp, pbase);
+        else if (it.kind == K_PRECISE) ok = energy_item<Q, K_PRECISE>(A, pipe, it.I, it.J, tp, ea, warp, pbase);
+        else ok = energy_item<Q, K_MASKED>(A, pipe, it.I, it.J, tp, ea, warp, pbase);
+        if (!ok) {
+            if (tid == 0) tp_dev_error(A.derr, TP_DERR_TIMEOUT);
+            break;
         }
-        if (aborted) break;
 #pragma unroll
         for (int P = 0; P < 2; ++P) esum += (double)(tp[P].w.x * ea[P].x) + (double)(tp[P].w.y * ea[P].y);
-        seq.next();
     }
-    // deterministic block reduction
+    // deterministic block reduction (the block's item set itself depends on the queue order)
     for (int o = 16; o > 0; o >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, o);
     if (lane == 0) wsum[warp] = esum;
     __syncthreads();
     if (tid == 0) {
         double b = 0.0;
         for (int w = 0; w < WARPS; ++w) b += wsum[w];
-        A.partial[partial_off + blockIdx.x] = b;
+        A.partial[blockIdx.x] = b;
     }
 }
 
@@ -702,55 +687,31 @@ template <int Q>
 tp_status launch_grad_q(tp_ctx* ctx, DirectArgs A) {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_pairs_grad<Q, K_FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_GRAD);
-        cudaFuncSetAttribute(k_pairs_grad<Q, K_PRECISE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_GRAD);
-        cudaFuncSetAttribute(k_pairs_grad<Q, K_MASKED>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_GRAD);
+        cudaFuncSetAttribute(k_pairs_grad<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_GRAD);
         attr = true;
     }
-    const int64_t nitems = (int64_t)ctx->nsup * (ctx->nsup + 1) / 2;
-    const int64_t nfast = nitems - ctx->n_masked - ctx->n_precise;
+    const int64_t nitems = ctx->n_masked + ctx->n_precise + ctx->n_fast;
+    TP_CU(cudaMemsetAsync(ctx->work, 0, sizeof(unsigned), ctx->stream));
     cudaEventRecord(ctx->ev[0], ctx->stream);
-    if (nfast > 0) {
-        const int grid = (int)std::min<int64_t>(ctx->num_sms, nfast);
-        k_pairs_grad<Q, K_FAST><<<grid, THREADS, SMEM_GRAD, ctx->stream>>>(A, nitems);
-        ++ctx->nlaunch;
-    }
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, nitems));
+    k_pairs_grad<Q><<<grid, THREADS, SMEM_GRAD, ctx->stream>>>(A);
+    ++ctx->nlaunch;
     cudaEventRecord(ctx->ev[1], ctx->stream);
-    if (ctx->n_precise > 0) {
-        A.list = ctx->plist;
-        const int grid = (int)std::min<int64_t>(ctx->num_sms, ctx->n_precise);
-        k_pairs_grad<Q, K_PRECISE><<<grid, THREADS, SMEM_GRAD, ctx->stream>>>(A, ctx->n_precise);
-        ++ctx->nlaunch;
-    }
-    if (ctx->n_masked > 0) {
-        A.list = ctx->mlist;
-        const int grid = (int)std::min<int64_t>(ctx->num_sms, ctx->n_masked);
-        k_pairs_grad<Q, K_MASKED><<<grid, THREADS, SMEM_GRAD, ctx->stream>>>(A, ctx->n_masked);
-        ++ctx->nlaunch;
-    }
     TP_CU(cudaGetLastError());
     return TP_OK;
 }
 
 template <int Q>
 tp_status launch_energy_q(tp_ctx* ctx, DirectArgs A, int* nparts) {
-    const int64_t nitems = (int64_t)ctx->nsup * (ctx->nsup + 1) / 2;
-    const int64_t nfast = nitems - ctx->n_masked - ctx->n_precise;
-    const int g1 = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, nfast));
-    const int g2 = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, ctx->n_precise));
-    const int g3 = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, ctx->n_masked));
+    const int64_t nitems = ctx->n_masked + ctx->n_precise + ctx->n_fast;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, nitems));
+    TP_CU(cudaMemsetAsync(ctx->work, 0, sizeof(unsigned), ctx->stream));
     cudaEventRecord(ctx->ev[0], ctx->stream);
-    k_pairs_energy<Q, K_FAST><<<g1, THREADS, SMEM_ENERGY, ctx->stream>>>(A, nfast > 0 ? nitems : 0, 0);
+    k_pairs_energy<Q><<<grid, THREADS, SMEM_ENERGY, ctx->stream>>>(A);
     ++ctx->nlaunch;
     cudaEventRecord(ctx->ev[1], ctx->stream);
-    A.list = ctx->plist;
-    k_pairs_energy<Q, K_PRECISE><<<g2, THREADS, SMEM_ENERGY, ctx->stream>>>(A, ctx->n_precise, g1);
-    ++ctx->nlaunch;
-    A.list = ctx->mlist;
-    k_pairs_energy<Q, K_MASKED><<<g3, THREADS, SMEM_ENERGY, ctx->stream>>>(A, ctx->n_masked, g1 + g2);
-    ++ctx->nlaunch;
     TP_CU(cudaGetLastError());
-    *nparts = g1 + g2 + g3;
+    *nparts = grid;
     return TP_OK;
 }
 
@@ -760,10 +721,14 @@ DirectArgs make_args(tp_ctx* ctx, const tp_params* prm) {
     A.src = ctx->src;
     A.Fs = ctx->Fs;
     A.acc = ctx->acc;
-    A.flagged = ctx->flagged;
-    A.list = ctx->mlist;
+    A.mlist = ctx->mlist;
+    A.plist = ctx->plist;
+    A.flist = ctx->flist;
+    A.nm = (int)ctx->n_masked;
+    A.np = (int)ctx->n_precise;
+    A.nf = (int)ctx->n_fast;
+    A.work = ctx->work;
     A.ntp = ctx->ntp;
-    A.nsup = (int)ctx->nsup;
     A.edge_only = (prm->flags & TP_EXCLUDE_EDGE) ? 1 : 0;
     A.derr = ctx->derr;
     A.partial = ctx->red;

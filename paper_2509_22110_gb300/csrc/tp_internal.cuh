@@ -54,7 +54,9 @@ struct tp_tree {
     int32_t* counter = nullptr;  // [nt-1] visit counters of the bottom-up pass
     double* mom = nullptr;       // [2nt-1][13]
     double* box = nullptr;       // [2nt-1][6]
-    float* nodef = nullptr;      // [2nt-1][16] f32 node summary used by the traversal
+    float* nodef = nullptr;      // [2nt-1][16] f32 node summary used by the far-field terms
+    double* adm64 = nullptr;     // [2nt-1][4] f64 X_C, diag_C of the admissibility test
+    float* adm32 = nullptr;      // [2nt-1][16] f32 outward/inward boxes, X_C, diag_C (pre-test)
     int32_t* nleaves_d = nullptr;
     int64_t cap = 0;
 };
@@ -96,7 +98,9 @@ struct tp_ctx {
     unsigned* flagged = nullptr;    // bitmap nsup*nsup: super-tile pairs not handled by the fast kernel
     int32_t* mlist = nullptr;       // compact list of masked super-tile pairs (I,J): a vertex-sharing pair inside
     int32_t* plist = nullptr;       // compact list of unmasked pairs of nearby super-tiles (hi/lo centroids)
-    int32_t* mcount = nullptr;      // [8]: counts of mlist, plist, then 3 u64 pair counts (fast, precise, masked)
+    int32_t* flist = nullptr;       // compact list of the remaining (fast) super-tile pairs
+    int32_t* mcount = nullptr;      // [10]: counts of mlist, plist, 3 u64 pair counts (fast, precise, masked), count of flist
+    unsigned* work = nullptr;       // [2] dynamic work counters of the persistent pair kernels
     float* tbox = nullptr;          // [nsup][6] f32 centroid boxes of the super-tiles
     void* sort_tmp = nullptr;
     size_t sort_tmp_bytes = 0;
@@ -104,6 +108,7 @@ struct tp_ctx {
 
     int64_t n_masked = 0;
     int64_t n_precise = 0;
+    int64_t n_fast = 0;
     int64_t pairs_fast = 0, pairs_precise = 0, pairs_masked_items = 0;  // unordered real pairs per item kind
     int64_t n_excluded_ordered = 0;  // ordered pairs T != S sharing a vertex
     int64_t cap_nv = 0, cap_nt = 0, cap_ntp = 0, red_cap = 0;

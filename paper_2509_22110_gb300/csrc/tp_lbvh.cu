@@ -181,6 +181,39 @@ __global__ void k_node_records(const double* __restrict__ mom, const double* __r
     for (int a = 10; a < 16; ++a) r[a] = 0.0f;
 }
 
+// Per-node constants of the admissibility test (Barnes-Hut, tp_bh.cu):
+//   adm64[v] = (X_C[3] = sum(w x)/A, diag_C = |box extent|) in FP64, computed
+//              with exactly the operations and order of the oracle's test;
+//   adm32[v] = box rounded outward (min down, max up) [6], box rounded inward
+//              (min up, max down) [6], X_C [3], diag_C [1] in FP32 for the
+//              pre-test that settles all but borderline cases.
+__global__ void k_node_adm(const double* __restrict__ mom, const double* __restrict__ box, int64_t nn,
+                           double* __restrict__ adm64, float* __restrict__ adm32) {
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= nn) return;
+    const double* m = mom + 13 * v;
+    const double* b = box + 6 * v;
+    double dc2 = 0.0;
+    double X[3];
+    for (int a = 0; a < 3; ++a) {
+        const double ec = __dsub_rn(b[3 + a], b[a]);
+        dc2 = __dadd_rn(dc2, __dmul_rn(ec, ec));
+        X[a] = __ddiv_rn(m[1 + a], m[0]);
+        adm64[4 * v + a] = X[a];
+    }
+    const double dc = __dsqrt_rn(dc2);
+    adm64[4 * v + 3] = dc;
+    float* r = adm32 + 16 * v;
+    for (int a = 0; a < 3; ++a) {
+        r[a] = __double2float_rd(b[a]);
+        r[3 + a] = __double2float_ru(b[3 + a]);
+        r[6 + a] = __double2float_ru(b[a]);
+        r[9 + a] = __double2float_rd(b[3 + a]);
+        r[12 + a] = (float)X[a];
+    }
+    r[15] = (float)dc;
+}
+
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -201,9 +234,11 @@ tp_status tp_launch_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits) {
         tp_free(ctx, t.box);
         tp_free(ctx, t.nodef);
         tp_free(ctx, t.nleaves_d);
+        tp_free(ctx, t.adm64);
+        tp_free(ctx, t.adm32);
         t.left = t.right = t.parent = t.first = t.last = t.leaves = t.counter = t.nleaves_d = nullptr;
-        t.mom = t.box = nullptr;
-        t.nodef = nullptr;
+        t.mom = t.box = t.adm64 = nullptr;
+        t.nodef = t.adm32 = nullptr;
         TP_TRY(tp_alloc_t(ctx, &t.left, n));
         TP_TRY(tp_alloc_t(ctx, &t.right, n));
         TP_TRY(tp_alloc_t(ctx, &t.parent, nn));
@@ -215,6 +250,8 @@ tp_status tp_launch_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits) {
         TP_TRY(tp_alloc_t(ctx, &t.box, 6 * nn));
         TP_TRY(tp_alloc_t(ctx, &t.nodef, 16 * nn));
         TP_TRY(tp_alloc_t(ctx, &t.nleaves_d, 4));
+        TP_TRY(tp_alloc_t(ctx, &t.adm64, 4 * nn));
+        TP_TRY(tp_alloc_t(ctx, &t.adm32, 16 * nn));
         t.cap = n;
     }
     t.leaf_size = leaf_size;
@@ -255,6 +292,8 @@ tp_status tp_launch_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits) {
                                                      t.left, t.right, t.parent, n, t.counter, t.mom, t.box);
     ++ctx->nlaunch;
     k_node_records<<<nblk(nn, 256), 256, 0, ctx->stream>>>(t.mom, ctx->center, nn, t.nodef);
+    ++ctx->nlaunch;
+    k_node_adm<<<nblk(nn, 256), 256, 0, ctx->stream>>>(t.mom, t.box, nn, t.adm64, t.adm32);
     ++ctx->nlaunch;
     int32_t h = 0;
     TP_CU(cudaMemcpyAsync(&h, t.nleaves_d, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));

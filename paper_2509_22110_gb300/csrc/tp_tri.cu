@@ -274,7 +274,7 @@ __global__ void k_tile_boxes(const float* __restrict__ soa, int64_t ntp, int64_t
 __global__ void k_flag_classify(const unsigned* __restrict__ adj, unsigned* __restrict__ bm, int nsup, int64_t nt,
                                 const float* __restrict__ tbox,
                                 const double* __restrict__ bounds, float delta_rel, int32_t* __restrict__ mlist,
-                                int32_t* __restrict__ plist, int32_t* __restrict__ count,
+                                int32_t* __restrict__ plist, int32_t* __restrict__ flist, int32_t* __restrict__ count,
                                 unsigned long long* __restrict__ npairs) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t n = (int64_t)nsup * nsup;
@@ -307,6 +307,7 @@ __global__ void k_flag_classify(const unsigned* __restrict__ adj, unsigned* __re
         atomicOr(&bm[i >> 5], 1u << (i & 31));
         atomicAdd(&npairs[1], pairs);
     } else {
+        flist[atomicAdd(&count[8], 1)] = (I << 16) | J;
         atomicAdd(&npairs[0], pairs);
     }
 }
@@ -397,19 +398,20 @@ tp_status tp_launch_flagged(tp_ctx* ctx, bool topology) {
         ++ctx->nlaunch;
     }
     TP_CU(cudaMemsetAsync(ctx->flagged, 0, sizeof(unsigned) * ((nbits + 31) / 32), ctx->stream));
-    TP_CU(cudaMemsetAsync(ctx->mcount, 0, 8 * sizeof(int32_t), ctx->stream));
+    TP_CU(cudaMemsetAsync(ctx->mcount, 0, 10 * sizeof(int32_t), ctx->stream));
     k_tile_boxes<<<nsup, 256, 0, ctx->stream>>>(ctx->soa, ctx->ntp, ctx->nt, ctx->tbox);
     ++ctx->nlaunch;
     unsigned long long* npairs = reinterpret_cast<unsigned long long*>(ctx->mcount + 2);
     k_flag_classify<<<blocks_for(nbits, 256), 256, 0, ctx->stream>>>(ctx->adjbm, ctx->flagged, nsup, ctx->nt, ctx->tbox,
                                                                      ctx->bounds, TP_PRECISE_GAP_REL, ctx->mlist,
-                                                                     ctx->plist, ctx->mcount, npairs);
+                                                                     ctx->plist, ctx->flist, ctx->mcount, npairs);
     ++ctx->nlaunch;
-    int32_t h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    TP_CU(cudaMemcpyAsync(h, ctx->mcount, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    int32_t h[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    TP_CU(cudaMemcpyAsync(h, ctx->mcount, 10 * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
     TP_CU(cudaStreamSynchronize(ctx->stream));
     ctx->n_masked = h[0];
     ctx->n_precise = h[1];
+    ctx->n_fast = h[8];
     unsigned long long p3[3];
     memcpy(p3, h + 2, sizeof(p3));
     ctx->pairs_fast = (int64_t)p3[0];
