@@ -70,9 +70,14 @@ def _load():
 
 def _bind_mlp(lib):
     i64, i32, dbl = C.c_int64, C.c_int, C.c_double
-    lib.or_mlp_forward.argtypes = [_d, i64, _d, _d, _d]
-    lib.or_mlp_backward.argtypes = [_d, i64, _d, _d, _d, _d, _d]
+    lib.or_mlp_nparam.restype = i64
+    lib.or_mlp_forward.argtypes = [_d, i64, _d, _d]
+    lib.or_mlp_backward.argtypes = [_d, i64, _d, _d, _d]
+    lib.or_mlp_loss.argtypes = [i64, _d, _d, _d, C.c_void_p]
+    lib.or_mlp_loss.restype = dbl
     lib.or_adamw_step.argtypes = [_d, _d, _d, _d, i64, dbl, dbl, dbl, dbl, dbl, i32]
+    lib.or_far_features.argtypes = [_d, _d, _d, _d, _d]
+    lib.or_far_channels.argtypes = [_d, _d, _d, _i64, i64, _i64, i64, _d, dbl, dbl, _d, _d]
 
 
 def nthreads_default() -> int:
@@ -255,3 +260,65 @@ def bh_gradient(V, F, theta, q=6.0, p=12.0, c=1.0, adj=0, morton_bits=30, leaf_s
     E = 0.5 * c * float(np.sum(w * gw))
     grad = adjoint(V, F, gw, gnu, gx, c)
     return E, grad, dict(near_pairs=nn, far_terms=nf, tree=tree, mom=mom, box=box, gw=gw, gnu=gnu, gx=gx)
+
+
+# ---------------------------------------------------------------- learned far field
+MLP_NI, MLP_NH, MLP_NO = 24, 64, 7
+
+
+def mlp_nparam():
+    return int(_load().or_mlp_nparam())
+
+
+def mlp_forward(params, X):
+    """Network outputs [n,7] for normalised inputs X [n,24] (FP64)."""
+    lib = _load()
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    Y = np.zeros((X.shape[0], MLP_NO))
+    lib.or_mlp_forward(P, X.shape[0], X, Y)
+    return Y
+
+
+def mlp_loss_grad(params, X, T, M):
+    """(loss, dL/dparams) of the masked mean-square loss."""
+    lib = _load()
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    Y = mlp_forward(P, X)
+    dY = np.zeros_like(Y)
+    L = lib.or_mlp_loss(X.shape[0], Y, T, M, dY.ctypes.data_as(C.c_void_p))
+    dP = np.zeros_like(P)
+    lib.or_mlp_backward(P, X.shape[0], X, dY, dP)
+    return L, dP
+
+
+def adamw_step(w, m, v, g, lr, b1=0.9, b2=0.999, eps=1e-8, wd=0.0, t=1):
+    """In-place AdamW step on FP64 arrays."""
+    lib = _load()
+    for a in (w, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    lib.or_adamw_step(w, m, v, g, w.size, lr, b1, b2, eps, wd, t)
+
+
+def far_features(momL, boxL, momC, boxC):
+    lib = _load()
+    f = np.zeros(MLP_NI)
+    lib.or_far_features(*(np.ascontiguousarray(a, dtype=np.float64) for a in (momL, boxL, momC, boxC)), f)
+    return f
+
+
+def far_channels(x, nu, w, targets, members, momC, q=6.0, p=12.0):
+    """(monopole[7], exact[7]) channel sums of one (leaf, cluster) pair."""
+    lib = _load()
+    tl = np.ascontiguousarray(targets, dtype=np.int64)
+    sc = np.ascontiguousarray(members, dtype=np.int64)
+    mono = np.zeros(7)
+    exact = np.zeros(7)
+    lib.or_far_channels(np.ascontiguousarray(x, dtype=np.float64), np.ascontiguousarray(nu, dtype=np.float64),
+                        np.ascontiguousarray(w, dtype=np.float64), tl, tl.size, sc, sc.size,
+                        np.ascontiguousarray(momC, dtype=np.float64), q, p, mono, exact)
+    return mono, exact
