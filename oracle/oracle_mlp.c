@@ -9,7 +9,8 @@
  * over the patch).  Everything is the plain definition:
  *
  *   network   24 -> 64 -> 64 -> 64 -> 7, y = W4 g(W3 g(W2 g(W1 x + b1) + b2) + b3) + b4,
- *             g(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2 (GELU)
+ *             g(z) = z (1 + tanh(c (z + 0.044715 z^3))) / 2, c = sqrt(2/pi)
+ *             (the tanh form of GELU, Hendrycks and Gimpel 2016)
  *   loss      L = sum_i sum_c m_ic (y_ic - t_ic)^2 / sum_i sum_c m_ic
  *   AdamW     m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
  *             w -= lr (m/(1-b1^t)) / (sqrt(v/(1-b2^t)) + eps) + lr wd w
@@ -39,10 +40,13 @@
 #define OFF_B4 (OFF_W4 + NO * NH)
 #define NPARAM (OFF_B4 + NO)
 
-static double gelu(double z) { return 0.5 * z * (1.0 + erf(z / sqrt(2.0))); }
-/* d/dz z Phi(z) = Phi(z) + z phi(z) */
+#define GELU_C 0.79788456080286535588 /* sqrt(2/pi) */
+#define GELU_A 0.044715
+static double gelu(double z) { return 0.5 * z * (1.0 + tanh(GELU_C * (z + GELU_A * z * z * z))); }
+/* d/dz of the above: (1 + t)/2 + z (1 - t^2) c (1 + 3 a z^2) / 2 */
 static double dgelu(double z) {
-    return 0.5 * (1.0 + erf(z / sqrt(2.0))) + z * exp(-0.5 * z * z) / sqrt(2.0 * 3.14159265358979323846);
+    const double t = tanh(GELU_C * (z + GELU_A * z * z * z));
+    return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * GELU_C * (1.0 + 3.0 * GELU_A * z * z);
 }
 
 int64_t or_mlp_nparam(void) { return NPARAM; }

@@ -46,7 +46,7 @@ def test_backward_matches_finite_differences(orc):
 
 def test_gelu_closed_form_through_the_network(orc):
     """W1..W3 = 0 makes every hidden unit g(b); with b3 = 1 and one output
-    reading one unit, y = g(1) = Phi(1) = 0.8413447460685429."""
+    reading one unit, y = g(1) = (1 + tanh(sqrt(2/pi) 1.044715)) / 2."""
     n = orc.mlp_nparam()
     P = np.zeros(n)
     off_b3 = 64 * 24 + 64 + 64 * 64 + 64 + 64 * 64
@@ -57,7 +57,8 @@ def test_gelu_closed_form_through_the_network(orc):
     off_b4 = off_w4 + 7 * 64
     P[off_b4 + 6] = 0.25
     y = orc.mlp_forward(P, np.random.default_rng(1).standard_normal((3, 24)))
-    phi1 = 0.5 * (1 + math.erf(1 / math.sqrt(2)))
+    phi1 = 0.5 * (1 + math.tanh(math.sqrt(2 / math.pi) * 1.044715))
+    assert abs(phi1 - 0.8411919906082768) < 1e-15
     np.testing.assert_allclose(y[:, 0], phi1, rtol=1e-15)
     np.testing.assert_allclose(y[:, 3], -2 * phi1, rtol=1e-15)
     np.testing.assert_allclose(y[:, 6], 0.25, rtol=1e-15)
