@@ -111,8 +111,51 @@ tp_status tp_gradient(tp_ctx* ctx, const tp_params* params, double* energy_out, 
                       uint32_t flags);
 
 /* Load the far-field network used by TP_LEARNED from a file written by
- * tp_far_model_save (versioned header, then weights). */
+ * tp_far_model_save: header {"TPFM", version 1, 24, 64, 7, nparam, theta,
+ * q, p, step}, then the feature mean/std/min/max [4][24] f32 and the FP32
+ * master parameters.  Malformed files give TP_E_MODEL. */
 tp_status tp_far_model_load(tp_ctx* ctx, const char* path);
+
+/* ------------------------------------------------------------------ */
+/* Learned far field: a network 24 -> 64 -> 64 -> 64 -> 7 (tanh-form GELU,
+ * BF16 weights on the tensor cores, FP32 accumulation) predicts, for an
+ * admissible (target leaf, cluster) pair, log-factors correcting the
+ * channels of the Barnes-Hut monopole far term (the paper has no network:
+ * its clustered inner integral uses plain averages over the patch, Sec. 3.2).
+ * Parameters: FP32, packed W1[64][24] b1 W2[64][64] b2 W3[64][64] b3 W4[7][64]
+ * b4 (10,375 numbers).  All pointers below are host pointers. */
+
+/* Fresh network with Xavier-uniform weights from a counter-based generator. */
+tp_status tp_far_model_init(tp_ctx* ctx, uint64_t seed);
+tp_status tp_far_model_save(tp_ctx* ctx, const char* path);
+/* Set / read the FP32 parameters and (optional) feature normalisation [4][24]. */
+tp_status tp_far_set_params(tp_ctx* ctx, const float* params, const float* norm);
+tp_status tp_far_get_params(tp_ctx* ctx, float* params, float* norm);
+/* Training set: sampled admissible pairs of the current tree with features
+ * [24], labels [8] (7 used: log(exact member sum / monopole) per channel) and
+ * masks [8]; the labels come from direct sums over the members.  Each
+ * admissible pair at opening angle theta is kept with probability `keep`
+ * (counter-based hash of the pair and seed), at most max_pairs are added;
+ * max_pairs = 0 only counts the kept pairs into *n_added. */
+tp_status tp_far_dataset_reset(tp_ctx* ctx);
+tp_status tp_far_dataset_size(tp_ctx* ctx, int64_t* n);
+tp_status tp_far_sample_pairs(tp_ctx* ctx, double theta, double keep, uint64_t seed, int64_t max_pairs,
+                              int64_t* n_added);
+tp_status tp_far_dataset_get(tp_ctx* ctx, int64_t i0, int64_t n, float* feat, float* lab, float* mask,
+                             int32_t* pairs);
+/* Feature mean/std and in-distribution ranges from the training set. */
+tp_status tp_far_fit_normalisation(tp_ctx* ctx);
+/* `steps` AdamW steps (b1 0.9, b2 0.999, eps 1e-8, decoupled decay wd) on
+ * batches of `batch` rows; *last_loss: masked mean-square loss of the last batch. */
+tp_status tp_far_train(tp_ctx* ctx, int64_t steps, int64_t batch, double lr, double wd, uint64_t seed,
+                       double* last_loss);
+/* Network on given rows X[n][24] (raw, or normalised if normalised != 0):
+ * outputs Y[n][7]; with targets/masks [n][8] also the loss and the parameter
+ * gradient grad[10375] (each output may be NULL).  For tests. */
+tp_status tp_far_eval(tp_ctx* ctx, const float* X, int64_t n, int normalised, const float* tgt, const float* mask,
+                      float* Y, float* grad, double* loss);
+/* One AdamW step with the given gradient [10375].  For tests. */
+tp_status tp_far_adamw_step(tp_ctx* ctx, const float* grad, double lr, double wd);
 
 /* ------------------------------------------------------------------ */
 /* Inspection entry points (host outputs, for tests and benchmarks)   */

@@ -87,6 +87,22 @@ def lib():
     L.tp_debug_accum.restype = i32
     L.tp_debug_tree.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, C.POINTER(C.c_int64), vp, vp]
     L.tp_debug_tree.restype = i32
+    L.tp_far_model_init.argtypes = [vp, C.c_uint64]
+    L.tp_far_model_save.argtypes = [vp, C.c_char_p]
+    L.tp_far_set_params.argtypes = [vp, vp, vp]
+    L.tp_far_get_params.argtypes = [vp, vp, vp]
+    L.tp_far_dataset_reset.argtypes = [vp]
+    L.tp_far_dataset_size.argtypes = [vp, C.POINTER(C.c_int64)]
+    L.tp_far_sample_pairs.argtypes = [vp, C.c_double, C.c_double, C.c_uint64, i64, C.POINTER(C.c_int64)]
+    L.tp_far_dataset_get.argtypes = [vp, i64, i64, vp, vp, vp, vp]
+    L.tp_far_fit_normalisation.argtypes = [vp]
+    L.tp_far_train.argtypes = [vp, i64, i64, C.c_double, C.c_double, C.c_uint64, C.POINTER(C.c_double)]
+    L.tp_far_eval.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, C.POINTER(C.c_double)]
+    L.tp_far_adamw_step.argtypes = [vp, vp, C.c_double, C.c_double]
+    for n in ("tp_far_model_init", "tp_far_model_save", "tp_far_set_params", "tp_far_get_params",
+              "tp_far_dataset_reset", "tp_far_dataset_size", "tp_far_sample_pairs", "tp_far_dataset_get",
+              "tp_far_fit_normalisation", "tp_far_train", "tp_far_eval", "tp_far_adamw_step"):
+        getattr(L, n).restype = i32
     L.tp_gradient_direct_noalloc.argtypes = [vp, i64, vp, i64, C.POINTER(tp_params), vp, vp, vp, C.c_char_p, i64]
     L.tp_gradient_direct_noalloc.restype = i32
     _lib = L
@@ -245,3 +261,89 @@ def tp_gradient_direct_noalloc(V, F, energy_out, grad_out, params=None, stream=N
                                           buf, 256)
     if st != TP_OK:
         raise TPError(st, buf.value.decode())
+
+
+# ---------------------------------------------------------------- learned far field
+FAR_NPARAM = 10375
+
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def tp_far_model_init(ctx, seed=0):
+    _check(ctx, lib().tp_far_model_init(ctx, seed))
+
+
+def tp_far_model_save(ctx, path):
+    _check(ctx, lib().tp_far_model_save(ctx, os.fsencode(path)))
+
+
+def tp_far_set_params(ctx, params, norm=None):
+    p = _f32(params, (FAR_NPARAM,))
+    n = _f32(norm, (4, 24)) if norm is not None else None
+    _check(ctx, lib().tp_far_set_params(ctx, p.ctypes.data, n.ctypes.data if n is not None else None))
+
+
+def tp_far_get_params(ctx):
+    p = np.zeros(FAR_NPARAM, np.float32)
+    n = np.zeros((4, 24), np.float32)
+    _check(ctx, lib().tp_far_get_params(ctx, p.ctypes.data, n.ctypes.data))
+    return p, n
+
+
+def tp_far_dataset_reset(ctx):
+    _check(ctx, lib().tp_far_dataset_reset(ctx))
+
+
+def tp_far_dataset_size(ctx):
+    n = C.c_int64(0)
+    _check(ctx, lib().tp_far_dataset_size(ctx, C.byref(n)))
+    return n.value
+
+
+def tp_far_sample_pairs(ctx, theta, keep, seed, max_pairs):
+    n = C.c_int64(0)
+    _check(ctx, lib().tp_far_sample_pairs(ctx, theta, keep, seed, max_pairs, C.byref(n)))
+    return n.value
+
+
+def tp_far_dataset_get(ctx, i0, n):
+    f = np.zeros((n, 24), np.float32)
+    lab = np.zeros((n, 8), np.float32)
+    m = np.zeros((n, 8), np.float32)
+    pr = np.zeros((n, 2), np.int32)
+    _check(ctx, lib().tp_far_dataset_get(ctx, i0, n, f.ctypes.data, lab.ctypes.data, m.ctypes.data, pr.ctypes.data))
+    return f, lab, m, pr
+
+
+def tp_far_fit_normalisation(ctx):
+    _check(ctx, lib().tp_far_fit_normalisation(ctx))
+
+
+def tp_far_train(ctx, steps, batch, lr, wd=0.0, seed=0):
+    loss = C.c_double(0.0)
+    _check(ctx, lib().tp_far_train(ctx, steps, batch, lr, wd, seed, C.byref(loss)))
+    return loss.value
+
+
+def tp_far_eval(ctx, X, normalised=False, tgt=None, mask=None):
+    X = _f32(X)
+    n = X.shape[0]
+    Y = np.zeros((n, 7), np.float32)
+    g = np.zeros(FAR_NPARAM, np.float32)
+    t = _f32(tgt) if tgt is not None else None
+    m = _f32(mask) if mask is not None else None
+    loss = C.c_double(0.0)
+    _check(ctx, lib().tp_far_eval(ctx, X.ctypes.data, n, int(bool(normalised)), t.ctypes.data if t is not None else None,
+                                  m.ctypes.data if m is not None else None, Y.ctypes.data, g.ctypes.data,
+                                  C.byref(loss)))
+    return Y, g, loss.value
+
+
+def tp_far_adamw_step(ctx, grad, lr, wd=0.0):
+    g = _f32(grad, (FAR_NPARAM,))
+    _check(ctx, lib().tp_far_adamw_step(ctx, g.ctypes.data, lr, wd))

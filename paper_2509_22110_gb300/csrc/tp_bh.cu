@@ -28,8 +28,10 @@
 // direct kernels (see tp_direct.cu), and the same adjoint applies.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "tp_internal.cuh"
+#include "tp_mlp_dev.cuh"
 
 namespace {
 
@@ -59,8 +61,25 @@ struct BHArgs {
     int edge_only;
     double* acc;
     unsigned* derr;
-    unsigned long long* counts;  // [0] near pairs, [1] far terms, [2] far pairs
+    unsigned long long* counts;  // [0] near pairs, [1] far terms, [2] far pairs, [3] learned terms
+    // learned far field
+    const float* nodeft;         // [nn][16] f32 feature records
+    const __nv_bfloat16* wb;     // network weights (BF16 block)
+    const float* mbias;          // network biases
+    const float* mnorm;          // [4][24] feature mean, std, lo, hi
+    // sampling of far pairs (RECORD mode)
+    uint32_t keep_u;
+    uint64_t seed;
+    int2* rec_out;
+    int64_t rec_cap;
+    int32_t* rec_count;
 };
+
+enum { M_BH = 0, M_LEARNED = 1, M_RECORD = 2 };
+constexpr int LW_X = 32 * MLP_NIP;       // per-warp BF16 input rows
+constexpr int LW_H = 32 * MLP_NH;        // per-warp BF16 hidden rows (two buffers)
+constexpr size_t LEARN_WARP_BYTES = (size_t)(LW_X + 2 * LW_H) * 2 + 32 * MLP_NOP * 4 + 32 * 8 * 4 + 32 * 4;
+constexpr size_t LEARN_SMEM = (size_t)MLPB_N * 2 + MLPF_N * 4 + 4 * MLP_NI * 4 + 4 * LEARN_WARP_BYTES;
 
 __device__ __forceinline__ float bh_rcp(float x) {
     float y;
@@ -144,6 +163,52 @@ __device__ __forceinline__ void leaf_adm(const double* box, LeafAdm& L) {
 // pre-test settles the decision whenever its error bound allows (outward and
 // inward rounded boxes for the strict comparisons; a 1e-5 relative margin for
 // the size test, far above FP32 rounding); otherwise the FP64 test decides.
+// The same far term with the network's per-channel factors (kf[0..6]):
+// E = wts (kf0 al^q + kf1 be^q), U: kf2 A5, Gn: kf3 A5 d, Gx: kf4 B5 nubar - k d,
+// k = (p/q) wts inv (kf5 al^q + kf6 be^q).
+template <int Q>
+__device__ __forceinline__ void gather_pair_learned(const Tgt& t, const float* sh, const float* sl, const float* sn,
+                                                    float sw, const float* kf, float acc[8]) {
+    float d[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = (t.h[k] - sh[k]) + (t.l[k] - sl[k]);
+    float inv = bh_rcp(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    float a = t.n[0] * d[0] + t.n[1] * d[1] + t.n[2] * d[2];
+    float b = sn[0] * d[0] + sn[1] * d[1] + sn[2] * d[2];
+    float al = a * inv, be = b * inv;
+    float al2 = al * al, be2 = be * be, al4 = al2 * al2, be4 = be2 * be2;
+    float alq, beq, al5, be5;
+    if (Q == 6) {
+        alq = al4 * al2;
+        beq = be4 * be2;
+        al5 = al4 * al;
+        be5 = be4 * be;
+    } else {
+        alq = al4 * al4;
+        beq = be4 * be4;
+        al5 = al4 * al2 * al;
+        be5 = be4 * be2 * be;
+    }
+    float wts = t.w * sw;
+    float wi = wts * inv;
+    float A5 = wi * al5, B5 = wi * be5;
+    float k = 2.0f * wi * (kf[5] * alq + kf[6] * beq);  // (p/q) = 2
+    acc[0] += wts * (kf[0] * alq + kf[1] * beq);
+    acc[1] += kf[2] * A5;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc[2 + c] += kf[3] * A5 * d[c];
+        acc[5 + c] += kf[4] * B5 * sn[c] - k * d[c];
+    }
+}
+
+__device__ __forceinline__ uint64_t bh_mix(uint64_t x) {
+    x += 0x9e3779b97f4a7c15ull;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+
 __device__ __forceinline__ bool admissible(const LeafAdm& L, const float* c32, const double* bc,
                                            const double* c64, double theta, float theta32) {
     bool sure = false, amb = false;
@@ -190,8 +255,9 @@ __device__ __forceinline__ bool adjacent(int3 a, int3 b, int edge_only) {
     return edge_only ? k >= 2 : k >= 1;
 }
 
-template <int Q>
+template <int Q, int MODE>
 __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
+    extern __shared__ __align__(16) unsigned char lsm[];  // LEARNED: network and per-warp scratch
     __shared__ int32_t s_stack[BH_WARPS][BH_STACK];
     __shared__ int32_t s_far[BH_WARPS][BH_FAR];
     __shared__ int32_t s_near[BH_WARPS][BH_NEAR];
@@ -200,6 +266,16 @@ __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
     __shared__ int4 s_stg_f[BH_WARPS][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t li = (int64_t)blockIdx.x * BH_WARPS + warp;
+    __nv_bfloat16* s_wb = reinterpret_cast<__nv_bfloat16*>(lsm);
+    float* s_bias = reinterpret_cast<float*>(lsm + MLPB_N * 2);
+    float* s_norm = s_bias + MLPF_N;
+    unsigned char* wscr = lsm + MLPB_N * 2 + MLPF_N * 4 + 4 * MLP_NI * 4 + warp * LEARN_WARP_BYTES;
+    if (MODE == M_LEARNED) {
+        for (int i = threadIdx.x; i < MLPB_N; i += blockDim.x) s_wb[i] = A.wb[i];
+        for (int i = threadIdx.x; i < MLPF_N; i += blockDim.x) s_bias[i] = A.mbias[i];
+        for (int i = threadIdx.x; i < 4 * MLP_NI; i += blockDim.x) s_norm[i] = A.mnorm[i];
+        __syncthreads();
+    }
     if (li >= A.nleaves) return;
     int32_t* st = s_stack[warp];
     int32_t* far = s_far[warp];
@@ -233,7 +309,7 @@ __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
         tg.w = 0.f;
     }
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    unsigned long long n_near = 0, n_far = 0, n_farp = 0;
+    unsigned long long n_near = 0, n_far = 0, n_farp = 0, n_learn = 0;
     const unsigned lt = (1u << lane) - 1u;
 
     // far list: stage 32 node records at a time in shared memory, then every
@@ -253,12 +329,60 @@ __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
                 stg_cnt[lane] = A.last[C] - A.first[C] + 1;
             }
             __syncwarp();
-            for (int i = half; i < nb; i += 2) {
-                const float* r = stg + i * 16;
-                if (active) {
-                    gather_pair<Q>(tg, r, r + 3, r + 6, r[9], a32);
-                    n_far += 1;
-                    n_farp += (unsigned long long)stg_cnt[i];
+            if (MODE == M_LEARNED) {
+                // features of (L, C) for this lane's node, the network on the 32 rows, factors
+                __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(wscr);
+                __nv_bfloat16* ha = X + LW_X;
+                __nv_bfloat16* hb = ha + LW_H;
+                float* y = reinterpret_cast<float*>(hb + LW_H);
+                float* kf = y + 32 * MLP_NOP;
+                int* ind = reinterpret_cast<int*>(kf + 32 * 8);
+                int in_dist = 0;
+                if (lane < nb) {
+                    float f[MLP_NI];
+                    far_features(A.nodeft + 16 * L, A.nodeft + 16 * (int64_t)far[b0 + lane], f);
+                    in_dist = 1;
+#pragma unroll
+                    for (int c = 0; c < MLP_NI; ++c) {
+                        const float lo = s_norm[2 * MLP_NI + c], hi = s_norm[3 * MLP_NI + c];
+                        const float pad = 0.05f * (hi - lo);
+                        if (!(f[c] >= lo - pad && f[c] <= hi + pad)) in_dist = 0;
+                        X[lane * MLP_NIP + c] = __float2bfloat16_rn((f[c] - s_norm[c]) / s_norm[MLP_NI + c]);
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < MLP_NI; ++c) X[lane * MLP_NIP + c] = __float2bfloat16_rn(0.f);
+                }
+#pragma unroll
+                for (int c = MLP_NI; c < MLP_NIP; ++c) X[lane * MLP_NIP + c] = __float2bfloat16_rn(0.f);
+                ind[lane] = in_dist;
+                __syncwarp();
+                warp_mlp_forward(s_wb, s_bias, X, ha, hb, ha, nullptr, nullptr, nullptr, y, 0);
+                warp_mlp_forward(s_wb, s_bias, X, ha, hb, ha, nullptr, nullptr, nullptr, y, 16);
+                if (lane < nb) {
+#pragma unroll
+                    for (int c = 0; c < MLP_NO; ++c)
+                        kf[lane * 8 + c] = ind[lane] ? __expf(fminf(4.f, fmaxf(-4.f, y[lane * MLP_NOP + c]))) : 1.f;
+                }
+                __syncwarp();
+                for (int i = half; i < nb; i += 2) {
+                    const float* r = stg + i * 16;
+                    if (active) {
+                        gather_pair_learned<Q>(tg, r, r + 3, r + 6, r[9], kf + i * 8, a32);
+                        n_far += 1;
+                        n_farp += (unsigned long long)stg_cnt[i];
+                        n_learn += (unsigned long long)ind[i];
+                    }
+                }
+                __syncwarp();
+            } else {
+                for (int i = half; i < nb; i += 2) {
+                    const float* r = stg + i * 16;
+                    if (active) {
+                        gather_pair<Q>(tg, r, r + 3, r + 6, r[9], a32);
+                        n_far += 1;
+                        n_farp += (unsigned long long)stg_cnt[i];
+                    }
                 }
             }
         }
@@ -337,15 +461,27 @@ __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
             overflow = true;
             break;
         }
-        if (is_far) far[nf + __popc(bf & lt)] = node;
-        if (is_near) nearl[nn + __popc(bn & lt)] = node;
+        if (MODE == M_RECORD) {
+            if (is_far) {
+                const uint64_t h = bh_mix(A.seed ^ (((uint64_t)li << 32) | (uint32_t)node));
+                if ((uint32_t)(h >> 32) < A.keep_u || A.keep_u == 0xffffffffu) {
+                    const int32_t pos = atomicAdd(A.rec_count, 1);
+                    if (pos < A.rec_cap) A.rec_out[pos] = make_int2((int)li, node);
+                }
+            }
+        } else {
+            if (is_far) far[nf + __popc(bf & lt)] = node;
+            if (is_near) nearl[nn + __popc(bn & lt)] = node;
+        }
         if (is_open) {
             const int pos = sp + 2 * __popc(bo & lt);
             st[pos] = A.right[node];
             st[pos + 1] = A.left[node];
         }
-        nf += __popc(bf);
-        nn += __popc(bn);
+        if (MODE != M_RECORD) {
+            nf += __popc(bf);
+            nn += __popc(bn);
+        }
         sp += 2 * __popc(bo);
         __syncwarp();
         if (nf > BH_FAR - 32) {
@@ -362,6 +498,7 @@ __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
         if (lane == 0) tp_dev_error(A.derr, TP_DERR_STACK);
         return;
     }
+    if (MODE == M_RECORD) return;
     flush_far(nf);
     flush_near(nn);
 #pragma unroll
@@ -374,24 +511,20 @@ __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
         n_near += __shfl_xor_sync(0xffffffffu, n_near, o);
         n_far += __shfl_xor_sync(0xffffffffu, n_far, o);
         n_farp += __shfl_xor_sync(0xffffffffu, n_farp, o);
+        n_learn += __shfl_xor_sync(0xffffffffu, n_learn, o);
     }
     if (lane == 0) {
         atomicAdd(&A.counts[0], n_near);
         atomicAdd(&A.counts[1], n_far);
         atomicAdd(&A.counts[2], n_farp);
+        atomicAdd(&A.counts[3], n_learn);
     }
 }
 
-}  // namespace
-
-tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
-    if (learned) return tp_set_err(ctx, TP_E_STATE, "TP_LEARNED is not available in this build");
+BHArgs make_bh_args(tp_ctx* ctx, double theta, int edge_only) {
     tp_tree& t = ctx->tree;
-    if (t.leaf_size > 32) return tp_set_err(ctx, TP_E_ARG, "leaf_size above 32");
-    TP_CU(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * TP_NACC * ctx->ntp, ctx->stream));
-    unsigned long long* counts = reinterpret_cast<unsigned long long*>(ctx->scalar + 2);
-    TP_CU(cudaMemsetAsync(counts, 0, 3 * sizeof(unsigned long long), ctx->stream));
     BHArgs A;
+    memset(&A, 0, sizeof(A));
     A.soa = ctx->soa;
     A.ntp = ctx->ntp;
     A.Fs = ctx->Fs;
@@ -407,26 +540,72 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
     A.nodef = t.nodef;
     A.adm64 = t.adm64;
     A.adm32 = t.adm32;
-    A.theta = prm->theta;
+    A.nodeft = t.nodeft;
+    A.theta = theta;
     A.leaf_size = t.leaf_size;
-    A.edge_only = (prm->flags & TP_EXCLUDE_EDGE) ? 1 : 0;
+    A.edge_only = edge_only;
     A.acc = ctx->acc;
     A.derr = ctx->derr;
+    return A;
+}
+
+}  // namespace
+
+tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
+    tp_tree& t = ctx->tree;
+    if (t.leaf_size > 32) return tp_set_err(ctx, TP_E_ARG, "leaf_size above 32");
+    TP_CU(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * TP_NACC * ctx->ntp, ctx->stream));
+    unsigned long long* counts = reinterpret_cast<unsigned long long*>(ctx->scalar + 2);
+    TP_CU(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), ctx->stream));
+    BHArgs A = make_bh_args(ctx, prm->theta, (prm->flags & TP_EXCLUDE_EDGE) ? 1 : 0);
     A.counts = counts;
     const unsigned blocks = (unsigned)((t.nleaves + BH_WARPS - 1) / BH_WARPS);
     cudaEventRecord(ctx->ev[0], ctx->stream);
-    if (prm->q == 6)
-        k_bh<6><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
-    else
-        k_bh<8><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
+    if (learned) {
+        A.wb = static_cast<const __nv_bfloat16*>(tp_mlp_weights(ctx));
+        A.mbias = tp_mlp_bias(ctx);
+        A.mnorm = tp_mlp_norm(ctx);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_bh<6, M_LEARNED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LEARN_SMEM);
+            cudaFuncSetAttribute(k_bh<8, M_LEARNED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LEARN_SMEM);
+            attr = true;
+        }
+        if (prm->q == 6)
+            k_bh<6, M_LEARNED><<<blocks, BH_WARPS * 32, LEARN_SMEM, ctx->stream>>>(A);
+        else
+            k_bh<8, M_LEARNED><<<blocks, BH_WARPS * 32, LEARN_SMEM, ctx->stream>>>(A);
+    } else {
+        if (prm->q == 6)
+            k_bh<6, M_BH><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
+        else
+            k_bh<8, M_BH><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
+    }
     ++ctx->nlaunch;
     cudaEventRecord(ctx->ev[1], ctx->stream);
     TP_CU(cudaGetLastError());
-    unsigned long long h[3] = {0, 0, 0};
+    unsigned long long h[4] = {0, 0, 0, 0};
     TP_CU(cudaMemcpyAsync(h, counts, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
     TP_CU(cudaStreamSynchronize(ctx->stream));
     ctx->stats.pairs_exact = (int64_t)h[0];
     ctx->stats.far_terms = (int64_t)h[1];
     ctx->stats.far_pairs = (int64_t)h[2];
+    ctx->stats.learned_terms = (int64_t)h[3];
+    return TP_OK;
+}
+
+tp_status tp_launch_bh_sample(tp_ctx* ctx, double theta, uint32_t keep_u, uint64_t seed, int2* out, int64_t cap,
+                              int32_t* counter) {
+    tp_tree& t = ctx->tree;
+    BHArgs A = make_bh_args(ctx, theta, 0);
+    A.keep_u = keep_u;
+    A.seed = seed;
+    A.rec_out = out;
+    A.rec_cap = cap;
+    A.rec_count = counter;
+    const unsigned blocks = (unsigned)((t.nleaves + BH_WARPS - 1) / BH_WARPS);
+    k_bh<6, M_RECORD><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
+    ++ctx->nlaunch;
+    TP_CU(cudaGetLastError());
     return TP_OK;
 }

@@ -106,7 +106,8 @@ tp_status check_params(tp_ctx* ctx, const tp_params* prm) {
     if (!ctx->have_mesh) return tp_set_err(ctx, TP_E_STATE, "no mesh uploaded");
     if (prm->mode != TP_DIRECT && !ctx->tree.valid && ctx->nt > 0)
         return tp_set_err(ctx, TP_E_STATE, "mode %d needs tp_tree_build first", prm->mode);
-    if (prm->mode == TP_LEARNED && !ctx->mlp) return tp_set_err(ctx, TP_E_STATE, "TP_LEARNED needs tp_far_model_load");
+    if (prm->mode == TP_LEARNED && !tp_mlp_ready(ctx))
+        return tp_set_err(ctx, TP_E_STATE, "TP_LEARNED needs a far-field model (tp_far_model_load)");
     return TP_OK;
 }
 
@@ -165,6 +166,7 @@ void release_mesh(tp_ctx* ctx) {
     free_ptr(ctx, t.nodef);
     free_ptr(ctx, t.adm64);
     free_ptr(ctx, t.adm32);
+    free_ptr(ctx, t.nodeft);
     t.valid = false;
     t.cap = 0;
     ctx->cap_nv = ctx->cap_nt = 0;

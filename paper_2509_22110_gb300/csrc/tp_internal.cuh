@@ -57,6 +57,7 @@ struct tp_tree {
     float* nodef = nullptr;      // [2nt-1][16] f32 node summary used by the far-field terms
     double* adm64 = nullptr;     // [2nt-1][4] f64 X_C, diag_C of the admissibility test
     float* adm32 = nullptr;      // [2nt-1][16] f32 outward/inward boxes, X_C, diag_C (pre-test)
+    float* nodeft = nullptr;     // [2nt-1][16] f32 feature record (A, X, nubar, M2/A, diag) of the network
     int32_t* nleaves_d = nullptr;
     int64_t cap = 0;
 };
@@ -168,8 +169,15 @@ tp_status tp_launch_check_finite(tp_ctx* ctx);
 tp_status tp_launch_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits);
 // tp_bh.cu
 tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned);
+tp_status tp_launch_bh_sample(tp_ctx* ctx, double theta, uint32_t keep_u, uint64_t seed, int2* out, int64_t cap,
+                              int32_t* counter);
 // tp_mlp.cu
 void tp_mlp_release(tp_ctx* ctx);
+tp_status tp_mlp_node_features(tp_ctx* ctx);
+bool tp_mlp_ready(const tp_ctx* ctx);
+const void* tp_mlp_weights(const tp_ctx* ctx);
+const float* tp_mlp_bias(const tp_ctx* ctx);
+const float* tp_mlp_norm(const tp_ctx* ctx);
 
 // ---------------------------------------------------------------- device helpers
 __device__ __forceinline__ void tp_dev_error(unsigned* derr, unsigned bit) { atomicOr(derr, bit); }

@@ -236,9 +236,10 @@ tp_status tp_launch_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits) {
         tp_free(ctx, t.nleaves_d);
         tp_free(ctx, t.adm64);
         tp_free(ctx, t.adm32);
+        tp_free(ctx, t.nodeft);
         t.left = t.right = t.parent = t.first = t.last = t.leaves = t.counter = t.nleaves_d = nullptr;
         t.mom = t.box = t.adm64 = nullptr;
-        t.nodef = t.adm32 = nullptr;
+        t.nodef = t.adm32 = t.nodeft = nullptr;
         TP_TRY(tp_alloc_t(ctx, &t.left, n));
         TP_TRY(tp_alloc_t(ctx, &t.right, n));
         TP_TRY(tp_alloc_t(ctx, &t.parent, nn));
@@ -252,6 +253,7 @@ tp_status tp_launch_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits) {
         TP_TRY(tp_alloc_t(ctx, &t.nleaves_d, 4));
         TP_TRY(tp_alloc_t(ctx, &t.adm64, 4 * nn));
         TP_TRY(tp_alloc_t(ctx, &t.adm32, 16 * nn));
+        TP_TRY(tp_alloc_t(ctx, &t.nodeft, 16 * nn));
         t.cap = n;
     }
     t.leaf_size = leaf_size;
@@ -295,6 +297,7 @@ tp_status tp_launch_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits) {
     ++ctx->nlaunch;
     k_node_adm<<<nblk(nn, 256), 256, 0, ctx->stream>>>(t.mom, t.box, nn, t.adm64, t.adm32);
     ++ctx->nlaunch;
+    TP_TRY(tp_mlp_node_features(ctx));
     int32_t h = 0;
     TP_CU(cudaMemcpyAsync(&h, t.nleaves_d, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
     TP_CU(cudaStreamSynchronize(ctx->stream));

@@ -1,0 +1,194 @@
+"""The learned far field against the FP64 oracle, and what it gains (needs a GPU).
+
+Bars: network outputs within 1e-2 and parameter gradients within 3e-2
+(relative L2) of the FP64 oracle evaluated with the same BF16-rounded
+weights and inputs (the GPU also rounds hidden activations to BF16); AdamW
+within 1e-5 of the FP64 step; features within 1e-4 and labels within 1e-3
+of the oracle's FP64 channel sums; a trained network lowers the Barnes-Hut
+energy error on a held-out mesh.
+"""
+
+import numpy as np
+import pytest
+
+from paper_2509_22110_gb300 import meshgen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tp():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_22110_gb300 import build
+
+    build.build()
+    import paper_2509_22110_gb300 as tpm
+
+    return tpm
+
+
+@pytest.fixture()
+def ctx(tp):
+    import torch
+
+    c = tp.tp_create(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    tp.tp_destroy(c)
+
+
+def bf16(a):
+    """Round to the nearest BF16 (ties to even), returned as float64."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def bf16_params(P):
+    """BF16-round the weight matrices (biases stay FP32) of a packed parameter vector."""
+    Q = np.asarray(P, dtype=np.float32).astype(np.float64).copy()
+    offs = [(0, 64 * 24), (64 * 24 + 64, 64 * 64), (64 * 24 + 64 + 64 * 64 + 64, 64 * 64),
+            (64 * 24 + 64 + 2 * (64 * 64 + 64), 7 * 64)]
+    for o, n in offs:
+        Q[o:o + n] = bf16(Q[o:o + n])
+    return Q
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+def test_forward_and_gradient_parity(tp, ctx, oracle_mod):
+    _tp = tp._tp
+    rng = np.random.default_rng(0)
+    _tp.tp_far_model_init(ctx, 7)
+    P, _ = _tp.tp_far_get_params(ctx)
+    P = P + rng.standard_normal(P.size).astype(np.float32) * 0.05  # non-trivial output layer
+    _tp.tp_far_set_params(ctx, P)
+    n = 200
+    X = rng.standard_normal((n, 24)).astype(np.float32)
+    T = rng.standard_normal((n, 8)).astype(np.float32) * 0.3
+    M = (rng.uniform(size=(n, 8)) > 0.2).astype(np.float32)
+    M[:, 7] = 0
+    Y, g, loss = _tp.tp_far_eval(ctx, X, normalised=True, tgt=T, mask=M)
+    Pq = bf16_params(P)
+    Xq = bf16(X)
+    Yo = oracle_mod.mlp_forward(Pq, Xq)
+    assert rel(Y, Yo) <= 1e-2, rel(Y, Yo)
+    Lo, go = oracle_mod.mlp_loss_grad(Pq, Xq, T[:, :7].astype(np.float64), M[:, :7].astype(np.float64))
+    assert abs(loss - Lo) <= 2e-2 * Lo
+    assert rel(g, go) <= 3e-2, rel(g, go)
+    # per layer as well (weights of each layer)
+    bounds = [0, 64 * 24, 64 * 24 + 64, 64 * 24 + 64 + 4096, 64 * 24 + 128 + 4096, 64 * 24 + 128 + 8192,
+              64 * 24 + 192 + 8192, 64 * 24 + 192 + 8192 + 448, 10375]
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        assert rel(g[a:b], go[a:b]) <= 5e-2, (a, b, rel(g[a:b], go[a:b]))
+
+
+def test_adamw_parity(tp, ctx, oracle_mod):
+    _tp = tp._tp
+    rng = np.random.default_rng(1)
+    _tp.tp_far_model_init(ctx, 3)
+    P0, _ = _tp.tp_far_get_params(ctx)
+    w = P0.astype(np.float64).copy()
+    m = np.zeros_like(w)
+    v = np.zeros_like(w)
+    for t in range(1, 4):
+        g = rng.standard_normal(w.size).astype(np.float32)
+        _tp.tp_far_adamw_step(ctx, g, 1e-3, 1e-2)
+        oracle_mod.adamw_step(w, m, v, g.astype(np.float64), 1e-3, 0.9, 0.999, 1e-8, 1e-2, t)
+    P1, _ = _tp.tp_far_get_params(ctx)
+    assert np.max(np.abs(P1 - w)) <= 1e-5 * max(1.0, np.max(np.abs(w)))
+
+
+def test_features_and_labels_parity(tp, ctx, oracle_mod):
+    _tp = tp._tp
+    V, F = meshgen.sh_deformed_sphere(4, 12, 0.05, 5)
+    tp.tp_mesh_upload(ctx, V, F)
+    tp.tp_tree_build(ctx, 16, 30)
+    _tp.tp_far_dataset_reset(ctx)
+    n = _tp.tp_far_sample_pairs(ctx, 0.5, 0.2, 11, 400)
+    assert n > 50
+    feat, lab, msk, pairs = _tp.tp_far_dataset_get(ctx, 0, n)
+    x, nu, w = oracle_mod.tri_data(V, F)
+    t = oracle_mod.lbvh(x, 30, 16)
+    mom, box = oracle_mod.moments(V, F, t, soa=(x, nu, w))
+    for i in range(0, n, max(1, n // 60)):
+        li, C = int(pairs[i, 0]), int(pairs[i, 1])
+        L = int(t["leaves"][li])
+        fo = oracle_mod.far_features(mom[L], box[L], mom[C], box[C])
+        np.testing.assert_allclose(feat[i], fo, rtol=1e-4, atol=1e-4)
+        targets = t["perm"][t["first"][L]: t["last"][L] + 1]
+        members = t["perm"][t["first"][C]: t["last"][C] + 1]
+        mono, exact = oracle_mod.far_channels(x, nu, w, targets, members, mom[C])
+        for c in range(7):
+            r = exact[c] / mono[c] if mono[c] != 0 else -1.0
+            if r > 0 and np.isfinite(r) and abs(np.log(r)) < 3.9:
+                assert msk[i, c] == 1.0
+                assert abs(lab[i, c] - np.log(r)) <= 1e-3, (i, c, lab[i, c], np.log(r))
+
+
+def test_training_lowers_the_far_field_error(tp, ctx, tmp_path):
+    """Train on a few level-5 meshes at theta = 0.5 and compare plain
+    Barnes-Hut with the learned correction on a held-out mesh."""
+    import torch
+
+    from paper_2509_22110_gb300 import far_train
+
+    _tp = tp._tp
+    _tp.tp_far_model_init(ctx, 1234)
+    _tp.tp_far_dataset_reset(ctx)
+    far_train.sample_meshes(ctx, range(1000, 1008), 5, 0.5, 20000, log=None)
+    _tp.tp_far_fit_normalisation(ctx)
+    hist = far_train.train(ctx, 800, 2048, 2e-3, log=None)
+    assert hist[-1][1] < 0.5 * hist[0][1], hist[:3] + hist[-3:]
+    path = str(tmp_path / "m.bin")
+    _tp.tp_far_model_save(ctx, path)
+    V, F = meshgen.sh_deformed_sphere(5, 12, 0.05, 2000)
+    ctx2 = tp.tp_create(0, torch.cuda.current_stream().cuda_stream)
+    try:
+        tp.tp_far_model_load(ctx2, path)
+        tp.tp_mesh_upload(ctx2, V, F)
+        gd = np.zeros_like(V)
+        ed = tp.tp_gradient(ctx2, gd, tp.tp_params_default(prec=tp.TP_F64))
+        tp.tp_tree_build(ctx2, 16, 30)
+        gb = np.zeros_like(V)
+        eb = tp.tp_gradient(ctx2, gb, tp.tp_params_default(mode=tp.TP_BH, theta=0.5))
+        gl = np.zeros_like(V)
+        el = tp.tp_gradient(ctx2, gl, tp.tp_params_default(mode=tp.TP_LEARNED, theta=0.5))
+        st = tp.tp_get_stats(ctx2)
+        assert st["learned_terms"] > 0.5 * st["far_terms"]
+        err_b, err_l = abs(eb - ed) / ed, abs(el - ed) / ed
+        gerr_b, gerr_l = rel(gb, gd), rel(gl, gd)
+        print(f"energy error BH {err_b:.3e} learned {err_l:.3e}; gradient error BH {gerr_b:.3e} learned {gerr_l:.3e}")
+        assert err_l < 0.5 * err_b
+        assert gerr_l < 1.1 * gerr_b
+    finally:
+        tp.tp_destroy(ctx2)
+
+
+def test_model_file_roundtrip_and_errors(tp, ctx, tmp_path):
+    _tp = tp._tp
+    _tp.tp_far_model_init(ctx, 5)
+    with pytest.raises(tp.TPError):  # no normalisation yet: nothing to save
+        _tp.tp_far_model_save(ctx, str(tmp_path / "x.bin"))
+    P, _ = _tp.tp_far_get_params(ctx)
+    norm = np.stack([np.zeros(24), np.ones(24), -np.ones(24), np.ones(24)]).astype(np.float32)
+    _tp.tp_far_set_params(ctx, P, norm)
+    path = str(tmp_path / "m.bin")
+    _tp.tp_far_model_save(ctx, path)
+    import torch
+
+    c2 = tp.tp_create(0, torch.cuda.current_stream().cuda_stream)
+    try:
+        tp.tp_far_model_load(c2, path)
+        P2, n2 = _tp.tp_far_get_params(c2)
+        assert np.array_equal(P2, P) and np.array_equal(n2, norm)
+        bad = tmp_path / "bad.bin"
+        bad.write_bytes(b"TPFX" + bytes(100))
+        with pytest.raises(tp.TPError) as ei:
+            tp.tp_far_model_load(c2, str(bad))
+        assert ei.value.status == tp._tp.TP_E_MODEL
+    finally:
+        tp.tp_destroy(c2)
