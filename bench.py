@@ -60,7 +60,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sh_l7", choices=sorted(WORKLOADS))
-    ap.add_argument("--mode", default="direct", choices=["direct", "bh"])
+    ap.add_argument("--mode", default="direct", choices=["direct", "bh", "learned"])
+    ap.add_argument("--far-model", default=None, help="trained far-field model (learned mode)")
     ap.add_argument("--theta", type=float, default=0.25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
@@ -230,7 +231,11 @@ def main():
     nt, nv = F.shape[0], V.shape[0]
     stream = torch.cuda.Stream(dev)
     ctx = tp.tp_create(local, stream.cuda_stream)
-    mode = tp.TP_DIRECT if args.mode == "direct" else tp.TP_BH
+    mode = {"direct": tp.TP_DIRECT, "bh": tp.TP_BH, "learned": tp.TP_LEARNED}[args.mode]
+    if mode == tp.TP_LEARNED:
+        if not args.far_model:
+            raise SystemExit("--mode learned needs --far-model (python -m paper_2509_22110_gb300.far_train)")
+        tp.tp_far_model_load(ctx, args.far_model)
     prm = tp.tp_params_default(mode=mode, theta=args.theta)
     with torch.cuda.stream(stream):
         Vd = torch.tensor(V, device=dev)
@@ -321,7 +326,7 @@ def main():
             "ordered_pairs_per_eval": pairs}
     if mode != tp.TP_DIRECT:
         line["bh"] = {"near_pairs": stats["pairs_exact"], "far_terms": stats["far_terms"],
-                      "far_pairs_represented": stats["far_pairs"],
+                      "far_pairs_represented": stats["far_pairs"], "learned_terms": stats["learned_terms"],
                       "energy_rel_err_vs_direct_f32": abs(energy - e_direct) / abs(e_direct),
                       "note": "value counts direct-equivalent pairs (the admitted ordered pairs of the full sum)"}
 

@@ -15,6 +15,7 @@ defaults to the full configuration: 50 level-7 SH-deformed spheres (seeds
 from __future__ import annotations
 
 import argparse
+import json
 import math
 import time
 
@@ -59,6 +60,40 @@ def train(ctx, steps, batch=4096, lr=2e-3, lr_min=1e-4, wd=1e-4, seed=0, chunk=5
     return hist
 
 
+def evaluate(ctx, seeds, level, thetas, log=print):
+    """Energy and gradient errors of plain Barnes-Hut and of the learned
+    correction against the direct sum (FP32 pair terms, FP64 accumulation),
+    with the device time of each evaluation, on held-out meshes."""
+    import torch
+
+    rows = []
+    for s in seeds:
+        V, F = meshgen.sh_deformed_sphere(level, 12, 0.05, int(s))
+        Vd = torch.tensor(V, device="cuda")
+        Fd = torch.tensor(F, device="cuda")
+        _tp.tp_mesh_upload(ctx, Vd, Fd)
+        gd = torch.zeros_like(Vd)
+        ed = _tp.tp_gradient(ctx, gd, _tp.tp_params_default())
+        td = _tp.tp_get_stats(ctx)["ms_total"]
+        _tp.tp_tree_build(ctx, 16, 30)
+        tb_ms = _tp.tp_get_stats(ctx)["ms_total"]
+        for th in thetas:
+            for mode in (_tp.TP_BH, _tp.TP_LEARNED):
+                g = torch.zeros_like(Vd)
+                e = _tp.tp_gradient(ctx, g, _tp.tp_params_default(mode=mode, theta=th))
+                st = _tp.tp_get_stats(ctx)
+                rows.append(dict(seed=int(s), theta=th, mode="bh" if mode == _tp.TP_BH else "learned",
+                                 energy_err=abs(e - ed) / abs(ed),
+                                 grad_err=float(torch.linalg.norm(g - gd) / torch.linalg.norm(gd)),
+                                 ms_eval=st["ms_total"] + tb_ms, ms_direct=td,
+                                 far_terms=st["far_terms"], learned_terms=st["learned_terms"]))
+                if log:
+                    r = rows[-1]
+                    log(f"seed {s} theta {th} {r['mode']:8s}: energy err {r['energy_err']:.3e} grad err "
+                        f"{r['grad_err']:.3e} {r['ms_eval']:.2f} ms (direct {td:.2f} ms)")
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default="far_model.bin")
@@ -69,6 +104,9 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--eval-seeds", type=int, nargs=2, default=None)
+    ap.add_argument("--eval-thetas", type=float, nargs="+", default=[0.25, 0.5])
+    ap.add_argument("--summary", default=None, help="write the evaluation rows as JSON here")
     args = ap.parse_args()
     import torch
 
@@ -84,6 +122,20 @@ def main():
     _tp.tp_far_model_save(ctx, args.out)
     print(f"{n} pairs in {t1 - t0:.1f} s; {args.steps} steps in {t2 - t1:.1f} s; final loss {hist[-1][1]:.5f}; "
           f"saved {args.out}")
+    if args.eval_seeds:
+        rows = evaluate(ctx, range(*args.eval_seeds), args.level, args.eval_thetas)
+        summ = {}
+        for th in args.eval_thetas:
+            for mode in ("bh", "learned"):
+                rs = [r for r in rows if r["theta"] == th and r["mode"] == mode]
+                summ[f"{mode}@{th}"] = {k: float(np.mean([r[k] for r in rs])) for k in
+                                        ("energy_err", "grad_err", "ms_eval", "ms_direct")}
+        print(json.dumps(summ))
+        if args.summary:
+            with open(args.summary, "w") as f:
+                json.dump({"train": {"pairs": n, "steps": args.steps, "final_loss": hist[-1][1],
+                                     "level": args.level, "seeds": args.seeds, "theta": args.theta},
+                           "eval": summ, "rows": rows}, f, indent=1)
     _tp.tp_destroy(ctx)
 
 
