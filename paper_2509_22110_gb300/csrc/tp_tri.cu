@@ -88,18 +88,32 @@ __global__ void k_bounds_partial(const double* __restrict__ x64, int64_t nt, dou
 
 __global__ void k_bounds_final(const double* __restrict__ part, int nb, double* __restrict__ bounds,
                                double* __restrict__ center) {
-    if (threadIdx.x != 0) return;
+    __shared__ double smin[3][256], smax[3][256];
     double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int b = 0; b < nb; ++b)
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
         for (int a = 0; a < 3; ++a) {
             mn[a] = fmin(mn[a], part[6 * b + a]);
             mx[a] = fmax(mx[a], part[6 * b + 3 + a]);
         }
     for (int a = 0; a < 3; ++a) {
-        bounds[a] = mn[a];
-        bounds[3 + a] = mx[a];
-        center[a] = 0.5 * (mn[a] + mx[a]);
+        smin[a][threadIdx.x] = mn[a];
+        smax[a][threadIdx.x] = mx[a];
     }
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int a = 0; a < 3; ++a) {
+                smin[a][threadIdx.x] = fmin(smin[a][threadIdx.x], smin[a][threadIdx.x + o]);
+                smax[a][threadIdx.x] = fmax(smax[a][threadIdx.x], smax[a][threadIdx.x + o]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int a = 0; a < 3; ++a) {
+            bounds[a] = smin[a][0];
+            bounds[3 + a] = smax[a][0];
+            center[a] = 0.5 * (smin[a][0] + smax[a][0]);
+        }
 }
 
 __device__ __forceinline__ uint32_t spread3(uint32_t v, int bits) {
@@ -324,7 +338,7 @@ tp_status tp_launch_tri_data(tp_ctx* ctx) {
     int nb = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (nt + 255) / 256));
     k_bounds_partial<<<nb, 256, 0, ctx->stream>>>(ctx->x64, nt, ctx->red);
     ++ctx->nlaunch;
-    k_bounds_final<<<1, 32, 0, ctx->stream>>>(ctx->red, nb, ctx->bounds, ctx->center);
+    k_bounds_final<<<1, 256, 0, ctx->stream>>>(ctx->red, nb, ctx->bounds, ctx->center);
     ++ctx->nlaunch;
     TP_CU(cudaGetLastError());
     return TP_OK;
