@@ -438,7 +438,7 @@ static tp_status run_eval(tp_ctx* ctx, const tp_params* prm, bool want_grad, voi
         ctx->stats.tile_pairs = ctx->nsup * (ctx->nsup + 1) / 2;
         ctx->stats.tile_pairs_masked = ctx->n_masked;
         ctx->stats.tile_pairs_precise = ctx->n_precise;
-        ctx->stats.kernel_pairs = ctx->pairs_fast + ctx->pairs_precise + ctx->pairs_masked_items;
+        ctx->stats.kernel_pairs = ctx->pairs_fast + ctx->pairs_precise;  // the timed (non-masked) launch
     } else {
         TP_TRY(tp_launch_bh(ctx, prm, prm->mode == TP_LEARNED));
     }

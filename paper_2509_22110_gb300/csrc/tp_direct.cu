@@ -405,7 +405,8 @@ __device__ __forceinline__ bool grad_item(const DirectArgs& A, ChunkPipe& pipe, 
         const int64_t sbase = (int64_t)J * TP_SUPER + (int64_t)c * TP_CHUNK;
         // on a diagonal item a warp whose 128 targets all lie above this chunk has no pair in it
         const bool skip = (KIND == K_MASKED) && (I == J) && (c < warp);
-        if (!skip) {
+        if (!skip && KIND == K_MASKED) {
+            // masked items: per-pair exclusion test (no software pipeline: register budget)
 #pragma unroll 1
             for (int s = 0; s < TP_CHUNK; ++s) {
                 SrcRec sr;
@@ -413,16 +414,14 @@ __device__ __forceinline__ bool grad_item(const DirectArgs& A, ChunkPipe& pipe, 
                 Acc8 as;
 #pragma unroll
                 for (int k = 0; k < TP_NACC; ++k) as.v[k] = make_float2(0.f, 0.f);
-                float2 valid[2] = {make_float2(1.f, 1.f), make_float2(1.f, 1.f)};
-                if (KIND == K_MASKED) {
-                    const int sl = c * TP_CHUNK + s;
-                    const int3 sf = load_face(A.Fs, sbase + s);
+                float2 valid[2];
+                const int sl = c * TP_CHUNK + s;
+                const int3 sf = load_face(A.Fs, sbase + s);
 #pragma unroll
-                    for (int P = 0; P < 2; ++P) {
-                        float v0 = ((I != J || sl > tl[P][0]) && !share_vertex(tf[P][0], sf, A.edge_only)) ? 1.f : 0.f;
-                        float v1 = ((I != J || sl > tl[P][1]) && !share_vertex(tf[P][1], sf, A.edge_only)) ? 1.f : 0.f;
-                        valid[P] = make_float2(v0, v1);
-                    }
+                for (int P = 0; P < 2; ++P) {
+                    float v0 = ((I != J || sl > tl[P][0]) && !share_vertex(tf[P][0], sf, A.edge_only)) ? 1.f : 0.f;
+                    float v1 = ((I != J || sl > tl[P][1]) && !share_vertex(tf[P][1], sf, A.edge_only)) ? 1.f : 0.f;
+                    valid[P] = make_float2(v0, v1);
                 }
 #pragma unroll
                 for (int P = 0; P < 2; ++P) pair_grad<Q, KIND>(tp[P], sr, at[P], as, valid[P]);
@@ -431,6 +430,31 @@ __device__ __forceinline__ bool grad_item(const DirectArgs& A, ChunkPipe& pipe, 
                 for (int k = 0; k < 8; ++k) v[k] = as.v[k].x + as.v[k].y;
                 const float r = warp_transpose_reduce8(v, lane);
                 if ((lane & 3) == 0) sacc[(warp * TP_CHUNK + s) * TP_NACC + ((lane >> 2) & 7)] = r;
+            }
+        } else if (!skip) {
+            // software pipeline: the warp reduction of source s-1 runs beside the
+            // arithmetic of source s (independent instruction streams)
+            float vprev[8];
+#pragma unroll 1
+            for (int s = 0; s <= TP_CHUNK; ++s) {
+                Acc8 as;
+                if (s < TP_CHUNK) {
+                    SrcRec sr;
+                    load_src<LO>(cb + s * TP_SRCW, sr);
+#pragma unroll
+                    for (int k = 0; k < TP_NACC; ++k) as.v[k] = make_float2(0.f, 0.f);
+                    const float2 one = make_float2(1.f, 1.f);
+#pragma unroll
+                    for (int P = 0; P < 2; ++P) pair_grad<Q, KIND>(tp[P], sr, at[P], as, one);
+                }
+                if (s > 0) {
+                    const float r = warp_transpose_reduce8(vprev, lane);
+                    if ((lane & 3) == 0) sacc[(warp * TP_CHUNK + s - 1) * TP_NACC + ((lane >> 2) & 7)] = r;
+                }
+                if (s < TP_CHUNK) {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) vprev[k] = as.v[k].x + as.v[k].y;
+                }
             }
         } else {
             for (int i = lane; i < TP_CHUNK * TP_NACC; i += 32) sacc[warp * TP_CHUNK * TP_NACC + i] = 0.f;
@@ -450,9 +474,11 @@ __device__ __forceinline__ bool grad_item(const DirectArgs& A, ChunkPipe& pipe, 
 }
 
 // ------------------------------------------------------------ gradient kernel
-// Persistent: every block takes items from the queue (masked, then precise,
-// then fast) until it is empty.
-template <int Q>
+// Persistent: every block takes items from the queue until it is empty.  Two
+// instantiations: MASKQ = true serves the masked items (per-pair exclusion
+// test), MASKQ = false the precise and fast items (each has its own register
+// budget).
+template <int Q, bool MASKQ>
 __global__ void __launch_bounds__(THREADS, 1) k_pairs_grad(DirectArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     float* sacc = reinterpret_cast<float*>(smem);                                 // [WARPS][CHUNK][8]
@@ -492,9 +518,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_pairs_grad(DirectArgs A) {
 #pragma unroll
             for (int c = 0; c < TP_NACC; ++c) at[P].v[c] = make_float2(0.f, 0.f);
         bool ok;
-        if (it.kind == K_FAST) ok = grad_item<Q, K_FAST>(A, pipe, sacc, it.I, it.J, tp, at, warp, lane, pbase);
-        else if (it.kind == K_PRECISE) ok = grad_item<Q, K_PRECISE>(A, pipe, sacc, it.I, it.J, tp, at, warp, lane, pbase);
-        else ok = grad_item<Q, K_MASKED>(A, pipe, sacc, it.I, it.J, tp, at, warp, lane, pbase);
+        if (MASKQ) ok = grad_item<Q, K_MASKED>(A, pipe, sacc, it.I, it.J, tp, at, warp, lane, pbase);
+        else if (it.kind == K_FAST) ok = grad_item<Q, K_FAST>(A, pipe, sacc, it.I, it.J, tp, at, warp, lane, pbase);
+        else ok = grad_item<Q, K_PRECISE>(A, pipe, sacc, it.I, it.J, tp, at, warp, lane, pbase);
         if (!ok) {
             if (tid == 0) tp_dev_error(A.derr, TP_DERR_TIMEOUT);
             return;
@@ -687,15 +713,29 @@ template <int Q>
 tp_status launch_grad_q(tp_ctx* ctx, DirectArgs A) {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_pairs_grad<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_GRAD);
+        cudaFuncSetAttribute(k_pairs_grad<Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_GRAD);
+        cudaFuncSetAttribute(k_pairs_grad<Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_GRAD);
         attr = true;
     }
-    const int64_t nitems = ctx->n_masked + ctx->n_precise + ctx->n_fast;
-    TP_CU(cudaMemsetAsync(ctx->work, 0, sizeof(unsigned), ctx->stream));
+    TP_CU(cudaMemsetAsync(ctx->work, 0, 2 * sizeof(unsigned), ctx->stream));
+    // masked items first (their own queue), then the precise and fast items
+    if (ctx->n_masked > 0) {
+        DirectArgs M = A;
+        M.np = M.nf = 0;
+        M.work = ctx->work + 1;
+        const int grid = (int)std::min<int64_t>(ctx->num_sms, ctx->n_masked);
+        k_pairs_grad<Q, true><<<grid, THREADS, SMEM_GRAD, ctx->stream>>>(M);
+        ++ctx->nlaunch;
+    }
+    const int64_t nrest = ctx->n_precise + ctx->n_fast;
     cudaEventRecord(ctx->ev[0], ctx->stream);
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, nitems));
-    k_pairs_grad<Q><<<grid, THREADS, SMEM_GRAD, ctx->stream>>>(A);
-    ++ctx->nlaunch;
+    if (nrest > 0) {
+        DirectArgs R = A;
+        R.nm = 0;
+        const int grid = (int)std::min<int64_t>(ctx->num_sms, nrest);
+        k_pairs_grad<Q, false><<<grid, THREADS, SMEM_GRAD, ctx->stream>>>(R);
+        ++ctx->nlaunch;
+    }
     cudaEventRecord(ctx->ev[1], ctx->stream);
     TP_CU(cudaGetLastError());
     return TP_OK;

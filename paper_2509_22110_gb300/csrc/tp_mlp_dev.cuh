@@ -93,6 +93,24 @@ __device__ __forceinline__ void load_b(const __nv_bfloat16* base, int ks, int ns
 __device__ __forceinline__ int frag_row(int v) { return ((threadIdx.x & 31) >> 2) + (v >= 2 ? 8 : 0); }
 __device__ __forceinline__ int frag_col(int v) { return ((threadIdx.x & 31) & 3) * 2 + (v & 1); }
 
+// Contiguous-layout fragment loads (32-bit shared-memory reads): A row-major
+// with leading dimension lda (k contiguous), B stored as W[n][K] (k contiguous).
+__device__ __forceinline__ void load_a_rm(const __nv_bfloat16* base, int lda, int m0, int k0, uint32_t a[4]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = (lane & 3) * 2;
+    const __nv_bfloat16* p0 = base + (m0 + g) * lda + k0 + t;
+    const __nv_bfloat16* p1 = p0 + 8 * lda;
+    a[0] = *reinterpret_cast<const uint32_t*>(p0);
+    a[1] = *reinterpret_cast<const uint32_t*>(p1);
+    a[2] = *reinterpret_cast<const uint32_t*>(p0 + 8);
+    a[3] = *reinterpret_cast<const uint32_t*>(p1 + 8);
+}
+__device__ __forceinline__ void load_b_nk(const __nv_bfloat16* W, int K, int k0, int n0, uint32_t b[2]) {
+    const int lane = threadIdx.x & 31;
+    const __nv_bfloat16* p = W + (n0 + (lane >> 2)) * K + k0 + (lane & 3) * 2;
+    b[0] = *reinterpret_cast<const uint32_t*>(p);
+    b[1] = *reinterpret_cast<const uint32_t*>(p + 8);
+}
+
 // One dense layer for a warp: out[16 x N] = in[16 x K] W^T + b over rows m0..m0+15.
 // in: BF16 [rows][ld_in]; W: BF16 row-major [N][K] (element (k, n) = W[n * K + k]);
 // the raw FP32 result z goes to zout[r * ld_z + c] (may be null) and act(z) as BF16
@@ -101,15 +119,17 @@ template <int K, int N>
 __device__ __forceinline__ void warp_dense(const __nv_bfloat16* in, int ld_in, const __nv_bfloat16* W,
                                            const float* bias, int m0, float* zout, int ld_z, __nv_bfloat16* hout,
                                            int ld_h, int act) {
+    uint32_t af[K / 16][4];
+#pragma unroll
+    for (int k0 = 0; k0 < K; k0 += 16) load_a_rm(in, ld_in, m0, k0, af[k0 / 16]);
 #pragma unroll
     for (int n0 = 0; n0 < N; n0 += 8) {
         float d[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int k0 = 0; k0 < K; k0 += 16) {
-            uint32_t a[4], b[2];
-            load_a(in, ld_in, 1, m0, k0, a);
-            load_b(W, 1, K, k0, n0, b);
-            mma_bf16(d, a, b);
+            uint32_t b[2];
+            load_b_nk(W, K, k0, n0, b);
+            mma_bf16(d, af[k0 / 16], b);
         }
 #pragma unroll
         for (int v = 0; v < 4; ++v) {

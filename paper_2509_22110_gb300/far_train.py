@@ -60,6 +60,18 @@ def train(ctx, steps, batch=4096, lr=2e-3, lr_min=1e-4, wd=1e-4, seed=0, chunk=5
     return hist
 
 
+def keep_channels(ctx, channels):
+    """Zero the output rows of the channels not listed, so their factor is exp(0) = 1."""
+    P, N = _tp.tp_far_get_params(ctx)
+    w4 = 64 * 24 + 64 + 2 * (64 * 64 + 64)
+    b4 = w4 + 7 * 64
+    for c in range(7):
+        if c not in channels:
+            P[w4 + c * 64: w4 + (c + 1) * 64] = 0.0
+            P[b4 + c] = 0.0
+    _tp.tp_far_set_params(ctx, P, N)
+
+
 def evaluate(ctx, seeds, level, thetas, log=print):
     """Energy and gradient errors of plain Barnes-Hut and of the learned
     correction against the direct sum (FP32 pair terms, FP64 accumulation),
@@ -100,7 +112,10 @@ def main():
     ap.add_argument("--level", type=int, default=7)
     ap.add_argument("--seeds", type=int, nargs=2, default=[1000, 1050])
     ap.add_argument("--pairs-per-mesh", type=int, default=40000)
-    ap.add_argument("--theta", type=float, default=0.25)
+    ap.add_argument("--theta", type=float, nargs="+", default=[0.25],
+                    help="opening angles to sample training pairs at (pairs-per-mesh each)")
+    ap.add_argument("--channels", type=int, nargs="+", default=list(range(7)),
+                    help="output channels kept in the saved model (others predict factor 1)")
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--lr", type=float, default=2e-3)
@@ -114,11 +129,15 @@ def main():
     t0 = time.time()
     _tp.tp_far_model_init(ctx, 1234)
     _tp.tp_far_dataset_reset(ctx)
-    n = sample_meshes(ctx, range(*args.seeds), args.level, args.theta, args.pairs_per_mesh)
+    n = 0
+    for th in args.theta:
+        n += sample_meshes(ctx, range(*args.seeds), args.level, th, args.pairs_per_mesh, seed=int(th * 1000))
     t1 = time.time()
     _tp.tp_far_fit_normalisation(ctx)
     hist = train(ctx, args.steps, args.batch, args.lr)
     t2 = time.time()
+    if sorted(args.channels) != list(range(7)):
+        keep_channels(ctx, args.channels)
     _tp.tp_far_model_save(ctx, args.out)
     print(f"{n} pairs in {t1 - t0:.1f} s; {args.steps} steps in {t2 - t1:.1f} s; final loss {hist[-1][1]:.5f}; "
           f"saved {args.out}")
@@ -134,7 +153,8 @@ def main():
         if args.summary:
             with open(args.summary, "w") as f:
                 json.dump({"train": {"pairs": n, "steps": args.steps, "final_loss": hist[-1][1],
-                                     "level": args.level, "seeds": args.seeds, "theta": args.theta},
+                                     "level": args.level, "seeds": args.seeds, "theta": args.theta,
+                                     "channels": args.channels},
                            "eval": summ, "rows": rows}, f, indent=1)
     _tp.tp_destroy(ctx)
 
