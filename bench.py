@@ -309,13 +309,16 @@ def main():
 
     launches = [0]
     kern_ms = []
+    tree_ms = []
 
     def step():
         tp.tp_mesh_upload(ctx, Vd, None, flags=_tp.TP_POSITIONS_ONLY)
         launches[0] += tp.tp_get_stats(ctx)["kernel_launches"]
         if mode != tp.TP_DIRECT:
             tp.tp_tree_build(ctx, 16, 30)
-            launches[0] += tp.tp_get_stats(ctx)["kernel_launches"]
+            tst = tp.tp_get_stats(ctx)
+            launches[0] += tst["kernel_launches"]
+            tree_ms.append(tst["ms_total"])
         e = tp.tp_gradient(ctx, gd, prm)
         st = tp.tp_get_stats(ctx)
         launches[0] += st["kernel_launches"]
@@ -329,6 +332,7 @@ def main():
     direct_pairs = tp.tp_get_stats(ctx)["pairs_exact"]
     launches[0] = 0
     kern_ms.clear()
+    tree_ms.clear()
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -370,11 +374,19 @@ def main():
         achieved = FLOPS_PER_UNORDERED_PAIR * upairs / (kms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": NCU_TRAFFIC_BYTES,
-                "kernel": "k_pairs_grad<6,FAST>", "kernel_ms": kms,
+                "kernel": "k_pairs_grad<6,false> (PRECISE and FAST items)", "kernel_ms": kms,
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz (max SM clock)",
                 "flops_per_unordered_pair": FLOPS_PER_UNORDERED_PAIR, "unordered_pairs_per_launch": upairs}
         if clk and clk.get("sm_mhz"):
             roof["frac_at_sampled_clock"] = achieved / (sms * FP32_LANES_PER_SM * 2 * clk["sm_mhz"] * 1e6 / 1e12)
+        # measured FP32 FMA throughput (after the timed region): full occupancy, and the pair
+        # kernel's own occupancy (12 warps per SM) with 2 and 4 independent packed chains per thread
+        probe = {}
+        for key, packed, wps, ch in (("ffma2_64warps_8chains", 1, 64, 8), ("ffma_64warps_16chains", 0, 64, 16),
+                                     ("ffma2_12warps_2chains", 1, 12, 2), ("ffma2_12warps_4chains", 1, 12, 4)):
+            probe[key] = _tp.tp_measure_fp32_peak(local, stream.cuda_stream, packed, wps, ch)
+        best = max(probe["ffma2_64warps_8chains"], probe["ffma_64warps_16chains"])
+        roof["peak_measured"] = {"tflops": probe, "frac_of_best": achieved / best if best > 0 else None}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -386,7 +398,8 @@ def main():
             "energy": energy, "gpu_launches": launches[0], "clocks": clk, "roofline": roof,
             "ordered_pairs_per_eval": pairs}
     if mode != tp.TP_DIRECT:
-        line["bh"] = {"near_pairs": stats["pairs_exact"], "far_terms": stats["far_terms"],
+        line["bh"] = {"tree_build_ms": statistics.median(tree_ms) if tree_ms else None,
+                      "near_pairs": stats["pairs_exact"], "far_terms": stats["far_terms"],
                       "far_pairs_represented": stats["far_pairs"], "learned_terms": stats["learned_terms"],
                       "energy_rel_err_vs_direct_f32": abs(energy - e_direct) / abs(e_direct),
                       "note": "value counts direct-equivalent pairs (the admitted ordered pairs of the full sum)"}

@@ -219,6 +219,20 @@ tp_status tp_gradient_direct_noalloc(const double* V, int64_t nv, const int32_t*
 /* Library version string. */
 const char* tp_version(void);
 
+/*
+ * Measured FP32 throughput of this GPU: independent chains of FMAs, scalar
+ * (packed = 0, FFMA) or FP32x2 (packed = 1, FFMA2), on every SM with
+ * `warps_per_sm` resident warps (1..64) and `chains` (2, 4, 8 or 16)
+ * independent accumulators per thread.  Writes the best of three timed
+ * launches (after one warm-up) in TFLOP/s to *tflops_out (an FMA counts as
+ * 2 flops).  It is the measured counterpart of the FP32 peak the pair kernels
+ * are compared with (SMs x 128 lanes x 2 x clock).  Runs on `cuda_stream`
+ * (NULL: the legacy default stream) and synchronises it; allocates and frees a
+ * small output buffer.  TP_E_ARG on bad arguments, TP_E_CUDA on a CUDA error.
+ */
+tp_status tp_measure_fp32_peak(int device, void* cuda_stream, int packed, int warps_per_sm, int chains,
+                               double* tflops_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -105,6 +105,8 @@ def lib():
         getattr(L, n).restype = i32
     L.tp_gradient_direct_noalloc.argtypes = [vp, i64, vp, i64, C.POINTER(tp_params), vp, vp, vp, C.c_char_p, i64]
     L.tp_gradient_direct_noalloc.restype = i32
+    L.tp_measure_fp32_peak.argtypes = [i32, vp, i32, i32, i32, C.POINTER(C.c_double)]
+    L.tp_measure_fp32_peak.restype = i32
     _lib = L
     return L
 
@@ -132,6 +134,16 @@ def _ptr(a):
 
 def tp_version():
     return lib().tp_version().decode()
+
+
+def tp_measure_fp32_peak(device=0, stream=None, packed=True, warps_per_sm=64, chains=8):
+    """Measured FP32 FMA throughput in TFLOP/s (see ``tp_measure_fp32_peak`` in tp.h)."""
+    out = C.c_double(0.0)
+    st = lib().tp_measure_fp32_peak(int(device), stream, int(bool(packed)), int(warps_per_sm), int(chains),
+                                    C.byref(out))
+    if st != TP_OK:
+        raise TPError(st, "tp_measure_fp32_peak failed")
+    return out.value
 
 
 def tp_params_default(**kw):
