@@ -146,6 +146,7 @@ void release_mesh(tp_ctx* ctx) {
     free_ptr(ctx, ctx->red);
     free_ptr(ctx, ctx->flagged);
     free_ptr(ctx, ctx->adjbm);
+    free_ptr(ctx, ctx->bmask);
     free_ptr(ctx, ctx->mlist);
     free_ptr(ctx, ctx->plist);
     free_ptr(ctx, ctx->flist);
@@ -205,6 +206,7 @@ tp_status ensure_buffers(tp_ctx* ctx, int64_t nv, int64_t nt) {
     const int64_t nbits = nsup * nsup;
     TP_TRY(tp_alloc_t(ctx, &ctx->flagged, (nbits + 31) / 32));
     TP_TRY(tp_alloc_t(ctx, &ctx->adjbm, (nbits + 31) / 32));
+    TP_TRY(tp_alloc_t(ctx, &ctx->bmask, nbits * TP_BMASK_WORDS));
     TP_TRY(tp_alloc_t(ctx, &ctx->mlist, nsup * (nsup + 1) / 2 + 1));
     TP_TRY(tp_alloc_t(ctx, &ctx->plist, nsup * (nsup + 1) / 2 + 1));
     TP_TRY(tp_alloc_t(ctx, &ctx->flist, nsup * (nsup + 1) / 2 + 1));

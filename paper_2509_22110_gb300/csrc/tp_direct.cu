@@ -20,25 +20,31 @@
 //
 // Work decomposition.  Triangles are in Morton order, padded to super-tiles
 // of 1536.  A work item is a super-tile pair (I <= J).  A persistent block
-// (12 warps, one per SM) keeps the 1536 targets of I in registers (each lane
-// 2 packed pairs of consecutive targets, FP32x2 arithmetic) and streams the
-// 1536 sources of J through shared memory in chunks of 128 with
-// cp.async.bulk (TMA bulk copies, completion on an mbarrier, bounded
-// waits).  Per source every lane adds its 4 pair contributions to packed
-// target accumulators; the source contributions of the warp are reduced by
-// a butterfly transpose (8 values over 32 lanes in 9 shuffles) and written
-// once per warp; per chunk the block sums its 12 warps and promotes to FP64
-// with one global atomic add per source and accumulator.  Target partials
-// (FP32 over one super-tile) are promoted to FP64 with one global atomic add
-// per target and accumulator per item.
+// (one per SM) keeps the 1536 targets of I in registers (each lane NP packed
+// pairs of consecutive targets, FP32x2 arithmetic) and streams the 1536
+// sources of J through shared memory in chunks of 128 with cp.async.bulk
+// (TMA bulk copies, completion on an mbarrier, bounded waits).  Per source
+// every lane adds its 2 NP pair contributions to packed target
+// accumulators; the source contributions of the warp are reduced by a
+// butterfly transpose (8 values over 32 lanes in 9 shuffles), software-
+// pipelined beside the next source's arithmetic, and written once per warp;
+// per chunk the block sums its warps and promotes to FP64 with one global
+// atomic add per source and accumulator.  Target partials (FP32 over one
+// item) are promoted to FP64 with one global atomic add per target and
+// accumulator per item.
 //
-// Three kinds of items, three instantiations:
+// Three kinds of items, two launches:
 //   FAST    - super-tiles far apart: d = x_hi,T - x_hi,S (FP32 centroids);
 //   PRECISE - super-tiles closer than a fraction of the mesh size:
 //             d = (hi_T - hi_S) + (lo_T - lo_S), which removes the FP32
 //             cancellation of nearby centroids;
 //   MASKED  - a pair of triangles sharing a vertex inside (and all diagonal
-//             items): hi/lo differences plus a per-pair exclusion test.
+//             items): the 128 x 128 blocks that hold a vertex-sharing pair
+//             (and the diagonal blocks) take a per-pair exclusion test,
+//             the other blocks the PRECISE arithmetic.
+// FAST and PRECISE items run 8 warps x 3 pairs per lane (a prefetched
+// source record in registers); MASKED items 12 warps x 2 pairs per lane
+// (face indices in registers for the exclusion test).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -46,12 +52,10 @@
 
 namespace {
 
-constexpr int WARPS = 12;
+constexpr int WARPS = 12;  // energy kernel: 12 warps, each lane 2 packed target pairs
 constexpr int THREADS = WARPS * 32;
 constexpr int NCHUNK = TP_SUPER / TP_CHUNK;                // chunks per super-tile
-constexpr int SMEM_SACC = WARPS * TP_CHUNK * TP_NACC * 4;  // 48 KB
 constexpr int CHUNK_BYTES = TP_CHUNK * TP_SRCW * 4;        // 10 KB
-constexpr int SMEM_GRAD = SMEM_SACC + 2 * CHUNK_BYTES + 64;
 constexpr int SMEM_ENERGY = 2 * CHUNK_BYTES + 64 + WARPS * 8;  // chunks, mbarriers + item slot, warp sums
 static_assert(TP_SUPER == WARPS * 128, "a warp owns 128 targets of the super-tile");
 
@@ -115,6 +119,8 @@ struct DirectArgs {
     const int32_t* mlist;     // MASKED items (I << 16 | J)
     const int32_t* plist;     // PRECISE items
     const int32_t* flist;     // FAST items
+    const unsigned* bmask;    // per super-tile pair: 128 x 128 blocks holding a vertex-sharing pair
+    int nsup;                 // super-tiles
     int nm, np, nf;           // their counts; the work queue is mlist, plist, flist in that order
     unsigned* work;           // dynamic work counter (zeroed before the launch)
     int64_t ntp;
@@ -204,16 +210,35 @@ __device__ __forceinline__ void powq_m1_fma(float2 x, float2 addend, float2& xm1
     }
 }
 
-// One packed evaluation: target pair t against one source s (both halves share s).
-// valid: per half 1 admitted, 0 excluded (MASKED only).
-template <int Q, int KIND>
-__device__ __forceinline__ void pair_grad(const TgtPair& t, const SrcRec& s, Acc8& at, Acc8& as, float2 valid) {
+// Geometry of one packed evaluation that does not depend on the normals:
+// d = x_T - x_S and inv = 1/|d|^2 (computed one source ahead in the
+// pipelined loop, so the reciprocal's latency overlaps other work).
+struct PairPre {
     float2 d[3];
-    pair_diff<KIND != K_FAST>(t, s, d);
-    float2 r2 = mul2(d[0], d[0]);
-    r2 = fma2(d[1], d[1], r2);
-    r2 = fma2(d[2], d[2], r2);
-    float2 inv = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+    float2 inv;
+};
+
+template <int KIND>
+__device__ __forceinline__ void pair_pre(const TgtPair& t, const SrcRec& s, PairPre& p) {
+    pair_diff<KIND != K_FAST>(t, s, p.d);
+    float2 r2 = mul2(p.d[0], p.d[0]);
+    r2 = fma2(p.d[1], p.d[1], r2);
+    r2 = fma2(p.d[2], p.d[2], r2);
+    p.inv = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+}
+
+// The rest of one packed evaluation: target pair t against one source s (both
+// halves share s).  valid: per half 1 admitted, 0 excluded (MASKED only).
+// FIRST: the source partials `as` are initialised by this call instead of
+// accumulated.  Source-side sign convention: `as` carries +B5 in slot 1 and
+// +(A5 nu_T + nk d) in slots 5..7, i.e. the negatives of the U and Gx
+// contributions to S; the chunk epilogue flips their sign (no per-pair
+// negations).
+template <int Q, int KIND, bool FIRST>
+__device__ __forceinline__ void pair_post(const TgtPair& t, const SrcRec& s, const PairPre& p, Acc8& at, Acc8& as,
+                                          float2 valid) {
+    const float2* d = p.d;
+    float2 inv = p.inv;
     float2 wts = mul2(t.w, s.w);
     if (KIND == K_MASKED) {
         inv = make_float2(valid.x != 0.f ? inv.x : 0.f, valid.y != 0.f ? inv.y : 0.f);
@@ -230,27 +255,43 @@ __device__ __forceinline__ void pair_grad(const TgtPair& t, const SrcRec& s, Acc
     float2 al5 = powq_m1<Q>(al, alq);
     float2 be5, s6;
     powq_m1_fma<Q>(be, alq, be5, s6);  // be^(q-1), and s6 = be^q + al^q with one fused op
-    float2 E = mul2(wts, s6);
     float2 wi = mul2(wts, inv);
     float2 A5 = mul2(wi, al5);
     float2 B5 = mul2(wi, be5);
     float2 nk = mul2(mul2(wi, s6), f2(-2.0f));  // -(p/q) wts inv s6, p = 2q
-    // target side
-    at.v[0] = add2(at.v[0], E);
+    // target side (E = wts s6 is fused into both energy accumulations)
+    at.v[0] = fma2(wts, s6, at.v[0]);
     at.v[1] = add2(at.v[1], A5);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         at.v[2 + k] = fma2(A5, d[k], at.v[2 + k]);
         at.v[5 + k] = fma2(nk, d[k], fma2(B5, s.n[k], at.v[5 + k]));
     }
-    // source side
-    as.v[0] = add2(as.v[0], E);
-    as.v[1] = add2(as.v[1], neg2(B5));
+    // source side (slots 1 and 5..7 negated, see above)
+    if (FIRST) {
+        as.v[0] = mul2(wts, s6);
+        as.v[1] = B5;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        as.v[2 + k] = fma2(B5, d[k], as.v[2 + k]);
-        as.v[5 + k] = fma2(neg2(nk), d[k], fma2(neg2(A5), t.n[k], as.v[5 + k]));
+        for (int k = 0; k < 3; ++k) {
+            as.v[2 + k] = mul2(B5, d[k]);
+            as.v[5 + k] = fma2(nk, d[k], mul2(A5, t.n[k]));
+        }
+    } else {
+        as.v[0] = fma2(wts, s6, as.v[0]);
+        as.v[1] = add2(as.v[1], B5);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            as.v[2 + k] = fma2(B5, d[k], as.v[2 + k]);
+            as.v[5 + k] = fma2(nk, d[k], fma2(A5, t.n[k], as.v[5 + k]));
+        }
     }
+}
+
+template <int Q, int KIND, bool FIRST>
+__device__ __forceinline__ void pair_grad(const TgtPair& t, const SrcRec& s, Acc8& at, Acc8& as, float2 valid) {
+    PairPre p;
+    pair_pre<KIND>(t, s, p);
+    pair_post<Q, KIND, FIRST>(t, s, p, at, as, valid);
 }
 
 // Energy only: returns w~_S * s6 per half (the caller multiplies by w~_T at the end).
@@ -382,17 +423,87 @@ __device__ __forceinline__ Item fetch_item(const DirectArgs& A, int* s_item) {
     return it;
 }
 
+// Block shape of the gradient kernels: W warps, each lane NP packed target
+// pairs, W * 32 * NP * 2 = TP_SUPER targets per block.  The masked items
+// (per-pair exclusion test, face indices in registers) use 12 warps x 2
+// pairs; the precise and fast items 8 warps x 3 pairs, whose larger
+// register budget holds a prefetched source record and amortises the
+// per-source warp reduction over 6 targets per lane.
+#ifndef TP_GRAD_W
+#define TP_GRAD_W 8  // warps of the precise/fast gradient kernel (8 or 12)
+#endif
+#ifndef TP_GRAD_PREFETCH
+#define TP_GRAD_PREFETCH 1  // 1: prefetch the next source record; 2: also its geometry
+#endif
+template <bool MASKQ>
+struct GradShape {
+    static constexpr int W = MASKQ ? 12 : TP_GRAD_W;
+    static constexpr int NP = TP_SUPER / (64 * W);
+    static constexpr int PF = MASKQ ? 1 : TP_GRAD_PREFETCH;  // source pipeline depth (register budget)
+    static constexpr int THREADS = 32 * W;
+    static constexpr int SMEM = W * TP_CHUNK * TP_NACC * 4 + 2 * CHUNK_BYTES + 64;
+    static_assert(W * 32 * NP * 2 == TP_SUPER, "a block owns one super-tile of targets");
+};
+
+// One source of a precise/fast item: prefetch the next source record, the NP
+// packed evaluations, then the warp reduction of the previous source (its
+// shuffle chain overlaps this source's arithmetic).
+template <int Q, int KIND, int NP>
+__device__ __forceinline__ void src_step(const TgtPair (&tp)[NP], Acc8 (&at)[NP], const SrcRec& cur, SrcRec& nxt,
+                                         const float* nrec, bool has_next, bool has_prev, float (&vprev)[8],
+                                         float* sacc_prev, int lane) {
+    constexpr bool LO = KIND != K_FAST;
+    if (has_next) load_src<LO>(nrec, nxt);
+    const float2 one = make_float2(1.f, 1.f);
+    Acc8 as;
+    pair_grad<Q, KIND, true>(tp[0], cur, at[0], as, one);
+#pragma unroll
+    for (int P = 1; P < NP; ++P) pair_grad<Q, KIND, false>(tp[P], cur, at[P], as, one);
+    if (has_prev) {
+        const float r = warp_transpose_reduce8(vprev, lane);
+        if ((lane & 3) == 0) sacc_prev[(lane >> 2) & 7] = r;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) vprev[k] = as.v[k].x + as.v[k].y;
+}
+
+// Pipelined variant of src_step: the normal-independent geometry of the next
+// source (pn) is formed while the current source (geometry pc) is finished.
+template <int Q, int KIND, int NP>
+__device__ __forceinline__ void src_step_pp(const TgtPair (&tp)[NP], Acc8 (&at)[NP], const SrcRec& cur,
+                                            const PairPre (&pc)[NP], SrcRec& nxt, PairPre (&pn)[NP],
+                                            const float* nrec, bool has_next, bool has_prev, float (&vprev)[8],
+                                            float* sacc_prev, int lane) {
+    constexpr bool LO = KIND != K_FAST;
+    if (has_next) {
+        load_src<LO>(nrec, nxt);
+#pragma unroll
+        for (int P = 0; P < NP; ++P) pair_pre<KIND>(tp[P], nxt, pn[P]);
+    }
+    const float2 one = make_float2(1.f, 1.f);
+    Acc8 as;
+    pair_post<Q, KIND, true>(tp[0], cur, pc[0], at[0], as, one);
+#pragma unroll
+    for (int P = 1; P < NP; ++P) pair_post<Q, KIND, false>(tp[P], cur, pc[P], at[P], as, one);
+    if (has_prev) {
+        const float r = warp_transpose_reduce8(vprev, lane);
+        if ((lane & 3) == 0) sacc_prev[(lane >> 2) & 7] = r;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) vprev[k] = as.v[k].x + as.v[k].y;
+}
+
 // The 12 chunks of one item for one item kind; target partials in `at`.
-template <int Q, int KIND>
+template <int Q, int KIND, int W, int NP, int PF>
 __device__ __forceinline__ bool grad_item(const DirectArgs& A, ChunkPipe& pipe, float* sacc, int I, int J,
-                                          const TgtPair (&tp)[2], Acc8 (&at)[2], int warp, int lane, int pbase) {
+                                          const TgtPair (&tp)[NP], Acc8 (&at)[NP], int warp, int lane, int pbase) {
     constexpr bool LO = KIND != K_FAST;
     const int64_t ntp = A.ntp;
-    int3 tf[2][2];
-    int tl[2][2];  // target positions within the super-tile
+    int3 tf[NP][2];
+    int tl[NP][2];  // target positions within the super-tile
     if (KIND == K_MASKED) {
 #pragma unroll
-        for (int P = 0; P < 2; ++P)
+        for (int P = 0; P < NP; ++P)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 tl[P][h] = 2 * (pbase + 32 * P) + h;
@@ -403,69 +514,99 @@ __device__ __forceinline__ bool grad_item(const DirectArgs& A, ChunkPipe& pipe, 
         const float* cb;
         if (!pipe.acquire(A, J, c, cb)) return false;
         const int64_t sbase = (int64_t)J * TP_SUPER + (int64_t)c * TP_CHUNK;
-        // on a diagonal item a warp whose 128 targets all lie above this chunk has no pair in it
-        const bool skip = (KIND == K_MASKED) && (I == J) && (c < warp);
-        if (!skip && KIND == K_MASKED) {
+        // Masked items (one 128-target block per warp): on the diagonal, a chunk below
+        // the warp's block has no admitted pair (admitted: source index > target index)
+        // and the chunk level with it needs the per-pair test; elsewhere only blocks
+        // that hold a vertex-sharing pair need it, the others take the unmasked path.
+        static_assert(KIND != K_MASKED || 64 * NP == TP_CHUNK, "masked items need one 128-target block per warp");
+        bool skip = false, masked = false;
+        if (KIND == K_MASKED) {
+            if (I == J && c < warp) {
+                skip = true;
+            } else if (I == J && c == warp) {
+                masked = true;
+            } else {
+                const int blk = warp * TP_NBLK + c;
+                const unsigned wd = __ldg(&A.bmask[((int64_t)I * A.nsup + J) * TP_BMASK_WORDS + (blk >> 5)]);
+                masked = (wd >> (blk & 31)) & 1u;
+            }
+        }
+        float* wacc = sacc + warp * TP_CHUNK * TP_NACC;
+        if (masked) {
             // masked items: per-pair exclusion test (no software pipeline: register budget)
 #pragma unroll 1
             for (int s = 0; s < TP_CHUNK; ++s) {
                 SrcRec sr;
                 load_src<LO>(cb + s * TP_SRCW, sr);
                 Acc8 as;
-#pragma unroll
-                for (int k = 0; k < TP_NACC; ++k) as.v[k] = make_float2(0.f, 0.f);
-                float2 valid[2];
+                float2 valid[NP];
                 const int sl = c * TP_CHUNK + s;
                 const int3 sf = load_face(A.Fs, sbase + s);
 #pragma unroll
-                for (int P = 0; P < 2; ++P) {
+                for (int P = 0; P < NP; ++P) {
                     float v0 = ((I != J || sl > tl[P][0]) && !share_vertex(tf[P][0], sf, A.edge_only)) ? 1.f : 0.f;
                     float v1 = ((I != J || sl > tl[P][1]) && !share_vertex(tf[P][1], sf, A.edge_only)) ? 1.f : 0.f;
                     valid[P] = make_float2(v0, v1);
                 }
+                pair_grad<Q, KIND, true>(tp[0], sr, at[0], as, valid[0]);
 #pragma unroll
-                for (int P = 0; P < 2; ++P) pair_grad<Q, KIND>(tp[P], sr, at[P], as, valid[P]);
+                for (int P = 1; P < NP; ++P) pair_grad<Q, KIND, false>(tp[P], sr, at[P], as, valid[P]);
                 float v[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) v[k] = as.v[k].x + as.v[k].y;
                 const float r = warp_transpose_reduce8(v, lane);
-                if ((lane & 3) == 0) sacc[(warp * TP_CHUNK + s) * TP_NACC + ((lane >> 2) & 7)] = r;
+                if ((lane & 3) == 0) wacc[s * TP_NACC + ((lane >> 2) & 7)] = r;
             }
         } else if (!skip) {
-            // software pipeline: the warp reduction of source s-1 runs beside the
-            // arithmetic of source s (independent instruction streams)
+            // two sources per trip with alternating record registers: the next
+            // source's record is loaded while the current one is evaluated
+            constexpr int KU = KIND == K_MASKED ? K_PRECISE : KIND;  // unmasked blocks of masked items
+            constexpr bool LOU = KU != K_FAST;
             float vprev[8];
+            SrcRec ra, rb;
+            if constexpr (PF == 2) {
+            PairPre pa[NP], pb[NP];
+            load_src<LOU>(cb, ra);
+#pragma unroll
+            for (int P = 0; P < NP; ++P) pair_pre<KU>(tp[P], ra, pa[P]);
 #pragma unroll 1
-            for (int s = 0; s <= TP_CHUNK; ++s) {
-                Acc8 as;
-                if (s < TP_CHUNK) {
-                    SrcRec sr;
-                    load_src<LO>(cb + s * TP_SRCW, sr);
-#pragma unroll
-                    for (int k = 0; k < TP_NACC; ++k) as.v[k] = make_float2(0.f, 0.f);
-                    const float2 one = make_float2(1.f, 1.f);
-#pragma unroll
-                    for (int P = 0; P < 2; ++P) pair_grad<Q, KIND>(tp[P], sr, at[P], as, one);
-                }
-                if (s > 0) {
-                    const float r = warp_transpose_reduce8(vprev, lane);
-                    if ((lane & 3) == 0) sacc[(warp * TP_CHUNK + s - 1) * TP_NACC + ((lane >> 2) & 7)] = r;
-                }
-                if (s < TP_CHUNK) {
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) vprev[k] = as.v[k].x + as.v[k].y;
-                }
+            for (int s = 0; s < TP_CHUNK; s += 2) {
+                src_step_pp<Q, KU, NP>(tp, at, ra, pa, rb, pb, cb + (s + 1) * TP_SRCW, true, s > 0, vprev,
+                                         wacc + (s - 1) * TP_NACC, lane);
+                src_step_pp<Q, KU, NP>(tp, at, rb, pb, ra, pa, cb + (s + 2) * TP_SRCW, s + 2 < TP_CHUNK, true,
+                                         vprev, wacc + s * TP_NACC, lane);
             }
+            } else if constexpr (PF == 1) {
+            load_src<LOU>(cb, ra);
+#pragma unroll 1
+            for (int s = 0; s < TP_CHUNK; s += 2) {
+                src_step<Q, KU, NP>(tp, at, ra, rb, cb + (s + 1) * TP_SRCW, true, s > 0, vprev,
+                                      wacc + (s - 1) * TP_NACC, lane);
+                src_step<Q, KU, NP>(tp, at, rb, ra, cb + (s + 2) * TP_SRCW, s + 2 < TP_CHUNK, true, vprev,
+                                      wacc + s * TP_NACC, lane);
+            }
+            } else {
+#pragma unroll 1
+            for (int s = 0; s < TP_CHUNK; ++s) {
+                load_src<LOU>(cb + s * TP_SRCW, ra);
+                src_step<Q, KU, NP>(tp, at, ra, rb, nullptr, false, s > 0, vprev, wacc + (s - 1) * TP_NACC,
+                                      lane);
+            }
+            }
+            const float r = warp_transpose_reduce8(vprev, lane);
+            if ((lane & 3) == 0) wacc[(TP_CHUNK - 1) * TP_NACC + ((lane >> 2) & 7)] = r;
         } else {
-            for (int i = lane; i < TP_CHUNK * TP_NACC; i += 32) sacc[warp * TP_CHUNK * TP_NACC + i] = 0.f;
+            for (int i = lane; i < TP_CHUNK * TP_NACC; i += 32) wacc[i] = 0.f;
         }
         __syncthreads();
-        // sum the warps' source partials of this chunk and promote to FP64
-        for (int i = threadIdx.x; i < TP_CHUNK * TP_NACC; i += THREADS) {
+        // sum the warps' source partials of this chunk, undo the sign convention of
+        // slots 1 and 5..7 (see pair_grad) and promote to FP64
+        for (int i = threadIdx.x; i < TP_CHUNK * TP_NACC; i += 32 * W) {
             float ssum = 0.f;
 #pragma unroll
-            for (int w = 0; w < WARPS; ++w) ssum += sacc[w * TP_CHUNK * TP_NACC + i];
+            for (int w = 0; w < W; ++w) ssum += sacc[w * TP_CHUNK * TP_NACC + i];
             const int s = i / TP_NACC, comp = i % TP_NACC;
+            if (comp == 1 || comp >= 5) ssum = -ssum;
             if (ssum != 0.f) atomicAdd(&A.acc[comp * ntp + sbase + s], (double)ssum);
         }
         __syncthreads();
@@ -476,15 +617,17 @@ __device__ __forceinline__ bool grad_item(const DirectArgs& A, ChunkPipe& pipe, 
 // ------------------------------------------------------------ gradient kernel
 // Persistent: every block takes items from the queue until it is empty.  Two
 // instantiations: MASKQ = true serves the masked items (per-pair exclusion
-// test), MASKQ = false the precise and fast items (each has its own register
-// budget).
+// test), MASKQ = false the precise and fast items (each has its own block
+// shape and register budget, see GradShape).
 template <int Q, bool MASKQ>
-__global__ void __launch_bounds__(THREADS, 1) k_pairs_grad(DirectArgs A) {
+__global__ void __launch_bounds__(GradShape<MASKQ>::THREADS, 1) k_pairs_grad(DirectArgs A) {
+    constexpr int W = GradShape<MASKQ>::W, NP = GradShape<MASKQ>::NP;
     extern __shared__ __align__(128) unsigned char smem[];
-    float* sacc = reinterpret_cast<float*>(smem);                                 // [WARPS][CHUNK][8]
-    float* chunk = reinterpret_cast<float*>(smem + SMEM_SACC);                    // [2][CHUNK][SRCW]
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + SMEM_SACC + 2 * CHUNK_BYTES);
-    int* s_item = reinterpret_cast<int*>(smem + SMEM_SACC + 2 * CHUNK_BYTES + 16);
+    constexpr int SACC_BYTES = W * TP_CHUNK * TP_NACC * 4;
+    float* sacc = reinterpret_cast<float*>(smem);                                 // [W][CHUNK][8]
+    float* chunk = reinterpret_cast<float*>(smem + SACC_BYTES);                   // [2][CHUNK][SRCW]
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + SACC_BYTES + 2 * CHUNK_BYTES);
+    int* s_item = reinterpret_cast<int*>(smem + SACC_BYTES + 2 * CHUNK_BYTES + 16);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t ntp = A.ntp;
@@ -499,9 +642,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_pairs_grad(DirectArgs A) {
     pipe.mbar = mbar;
     pipe.phases = 0u;
 
-    TgtPair tp[2];
+    TgtPair tp[NP];
     int rowI = -1;
-    const int pbase = warp * 64 + lane;  // pair index within the super-tile: pbase, pbase+32
+    const int pbase = warp * 32 * NP + lane;  // pair index within the super-tile: pbase + 32 P
     while (true) {
         const Item it = fetch_item(A, s_item);
         if (it.kind < 0) break;
@@ -509,25 +652,28 @@ __global__ void __launch_bounds__(THREADS, 1) k_pairs_grad(DirectArgs A) {
         if (it.I != rowI) {
             rowI = it.I;
 #pragma unroll
-            for (int P = 0; P < 2; ++P)
+            for (int P = 0; P < NP; ++P)
                 load_tgt<true>(A.soa, ntp, (int64_t)it.I * TP_SUPER + 2 * (pbase + 32 * P), tp[P]);
         }
-        Acc8 at[2];
+        Acc8 at[NP];
 #pragma unroll
-        for (int P = 0; P < 2; ++P)
+        for (int P = 0; P < NP; ++P)
 #pragma unroll
             for (int c = 0; c < TP_NACC; ++c) at[P].v[c] = make_float2(0.f, 0.f);
         bool ok;
-        if (MASKQ) ok = grad_item<Q, K_MASKED>(A, pipe, sacc, it.I, it.J, tp, at, warp, lane, pbase);
-        else if (it.kind == K_FAST) ok = grad_item<Q, K_FAST>(A, pipe, sacc, it.I, it.J, tp, at, warp, lane, pbase);
-        else ok = grad_item<Q, K_PRECISE>(A, pipe, sacc, it.I, it.J, tp, at, warp, lane, pbase);
+        if constexpr (MASKQ) {
+            ok = grad_item<Q, K_MASKED, W, NP, GradShape<MASKQ>::PF>(A, pipe, sacc, it.I, it.J, tp, at, warp, lane, pbase);
+        } else {
+            if (it.kind == K_FAST) ok = grad_item<Q, K_FAST, W, NP, GradShape<MASKQ>::PF>(A, pipe, sacc, it.I, it.J, tp, at, warp, lane, pbase);
+            else ok = grad_item<Q, K_PRECISE, W, NP, GradShape<MASKQ>::PF>(A, pipe, sacc, it.I, it.J, tp, at, warp, lane, pbase);
+        }
         if (!ok) {
             if (tid == 0) tp_dev_error(A.derr, TP_DERR_TIMEOUT);
             return;
         }
         // promote the item's FP32 target partials to FP64
 #pragma unroll
-        for (int P = 0; P < 2; ++P) {
+        for (int P = 0; P < NP; ++P) {
             const int64_t t0 = (int64_t)it.I * TP_SUPER + 2 * (pbase + 32 * P);
 #pragma unroll
             for (int k = 0; k < TP_NACC; ++k) {
@@ -713,8 +859,10 @@ template <int Q>
 tp_status launch_grad_q(tp_ctx* ctx, DirectArgs A) {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_pairs_grad<Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_GRAD);
-        cudaFuncSetAttribute(k_pairs_grad<Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_GRAD);
+        cudaFuncSetAttribute(k_pairs_grad<Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             GradShape<false>::SMEM);
+        cudaFuncSetAttribute(k_pairs_grad<Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             GradShape<true>::SMEM);
         attr = true;
     }
     TP_CU(cudaMemsetAsync(ctx->work, 0, 2 * sizeof(unsigned), ctx->stream));
@@ -724,7 +872,7 @@ tp_status launch_grad_q(tp_ctx* ctx, DirectArgs A) {
         M.np = M.nf = 0;
         M.work = ctx->work + 1;
         const int grid = (int)std::min<int64_t>(ctx->num_sms, ctx->n_masked);
-        k_pairs_grad<Q, true><<<grid, THREADS, SMEM_GRAD, ctx->stream>>>(M);
+        k_pairs_grad<Q, true><<<grid, GradShape<true>::THREADS, GradShape<true>::SMEM, ctx->stream>>>(M);
         ++ctx->nlaunch;
     }
     const int64_t nrest = ctx->n_precise + ctx->n_fast;
@@ -733,7 +881,7 @@ tp_status launch_grad_q(tp_ctx* ctx, DirectArgs A) {
         DirectArgs R = A;
         R.nm = 0;
         const int grid = (int)std::min<int64_t>(ctx->num_sms, nrest);
-        k_pairs_grad<Q, false><<<grid, THREADS, SMEM_GRAD, ctx->stream>>>(R);
+        k_pairs_grad<Q, false><<<grid, GradShape<false>::THREADS, GradShape<false>::SMEM, ctx->stream>>>(R);
         ++ctx->nlaunch;
     }
     cudaEventRecord(ctx->ev[1], ctx->stream);
@@ -764,6 +912,8 @@ DirectArgs make_args(tp_ctx* ctx, const tp_params* prm) {
     A.mlist = ctx->mlist;
     A.plist = ctx->plist;
     A.flist = ctx->flist;
+    A.bmask = ctx->bmask;
+    A.nsup = (int)ctx->nsup;
     A.nm = (int)ctx->n_masked;
     A.np = (int)ctx->n_precise;
     A.nf = (int)ctx->n_fast;

@@ -29,6 +29,8 @@
 #define TP_CHUNK 128       // sources staged per shared-memory chunk
 #define TP_SRCW 20         // floats per staged source record
 #define TP_NACC 8          // accumulators per triangle
+#define TP_NBLK (TP_SUPER / TP_CHUNK)  // 128-triangle blocks per super-tile side
+#define TP_BMASK_WORDS ((TP_NBLK * TP_NBLK + 31) / 32)  // bits of one super-tile pair's block mask
 #define TP_SPIN_LIMIT (1u << 26)
 // super-tile pairs whose centroid boxes are closer than this fraction of the
 // mesh's centroid-box diagonal form centroid differences from hi + lo parts
@@ -97,6 +99,8 @@ struct tp_ctx {
     unsigned* derr = nullptr;       // device error word
     unsigned* adjbm = nullptr;      // bitmap nsup*nsup: super-tile pairs holding a vertex-sharing pair (or I == J)
     unsigned* flagged = nullptr;    // bitmap nsup*nsup: super-tile pairs not handled by the fast kernel
+    unsigned* bmask = nullptr;      // [nsup*nsup][TP_BMASK_WORDS]: per super-tile pair (I, J), bit i*TP_NBLK+j set
+                                    // when target block i of I and source block j of J hold a vertex-sharing pair
     int32_t* mlist = nullptr;       // compact list of masked super-tile pairs (I,J): a vertex-sharing pair inside
     int32_t* plist = nullptr;       // compact list of unmasked pairs of nearby super-tiles (hi/lo centroids)
     int32_t* flist = nullptr;       // compact list of the remaining (fast) super-tile pairs

@@ -224,22 +224,28 @@ __global__ void k_v2t_sort(const int32_t* __restrict__ off, int64_t nv, int32_t*
     }
 }
 
-// super-tile pairs containing a pair of triangles that share a vertex
+// super-tile pairs containing a pair of triangles that share a vertex, and
+// within each such pair the 128 x 128 blocks holding one.  The pair {T, S}
+// is evaluated as target = the one earlier in Morton order and source = the
+// later one (the item is (I, J) with I <= J), which fixes its block.
 __global__ void k_flag_pairs(const int32_t* __restrict__ F, const int32_t* __restrict__ perm,
                              const int32_t* __restrict__ iperm, const int32_t* __restrict__ off,
-                             const int32_t* __restrict__ v2t, int64_t nt, int nsup, unsigned* __restrict__ bm) {
+                             const int32_t* __restrict__ v2t, int64_t nt, int nsup, unsigned* __restrict__ bm,
+                             unsigned* __restrict__ bmask) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= nt) return;
     int64_t T = perm[k];
-    int I = (int)(k / TP_SUPER);
     for (int c = 0; c < 3; ++c) {
         int32_t v = F[3 * T + c];
         for (int32_t e = off[v]; e < off[v + 1]; ++e) {
             int64_t S = v2t[e] >> 2;
-            int J = iperm[S] / TP_SUPER;
-            int a = min(I, J), b = max(I, J);
-            int64_t bit = (int64_t)a * nsup + b;
+            const int64_t ks = iperm[S];
+            const int64_t kt = k < ks ? k : ks, kss = k < ks ? ks : k;  // target, source positions
+            const int a = (int)(kt / TP_SUPER), b = (int)(kss / TP_SUPER);
+            const int64_t bit = (int64_t)a * nsup + b;
             atomicOr(&bm[bit >> 5], 1u << (bit & 31));
+            const int blk = (int)((kt % TP_SUPER) / TP_CHUNK) * TP_NBLK + (int)((kss % TP_SUPER) / TP_CHUNK);
+            atomicOr(&bmask[bit * TP_BMASK_WORDS + (blk >> 5)], 1u << (blk & 31));
         }
     }
 }
@@ -405,8 +411,10 @@ tp_status tp_launch_flagged(tp_ctx* ctx, bool topology) {
     const int64_t nbits = (int64_t)nsup * nsup;
     if (topology) {
         TP_CU(cudaMemsetAsync(ctx->adjbm, 0, sizeof(unsigned) * ((nbits + 31) / 32), ctx->stream));
+        TP_CU(cudaMemsetAsync(ctx->bmask, 0, sizeof(unsigned) * nbits * TP_BMASK_WORDS, ctx->stream));
         k_flag_pairs<<<blocks_for(ctx->nt, 256), 256, 0, ctx->stream>>>(ctx->F, ctx->perm, ctx->iperm, ctx->v2t_off,
-                                                                        ctx->v2t, ctx->nt, nsup, ctx->adjbm);
+                                                                        ctx->v2t, ctx->nt, nsup, ctx->adjbm,
+                                                                        ctx->bmask);
         ++ctx->nlaunch;
         k_flag_diag<<<blocks_for(nsup, 256), 256, 0, ctx->stream>>>(nsup, ctx->adjbm);
         ++ctx->nlaunch;
