@@ -110,6 +110,19 @@ tp_status tp_energy(tp_ctx* ctx, const tp_params* params, double* energy_out);
 tp_status tp_gradient(tp_ctx* ctx, const tp_params* params, double* energy_out, void* grad_out, int g_dtype,
                       uint32_t flags);
 
+/* Energy (energy_out may be NULL) and the per-triangle derivatives that the
+ * vertex gradient is assembled from: for every triangle T, in the caller's
+ * order, dPhi/dw_T (area) into fw[nt], dPhi/dnu_T (unit normal, taken as a
+ * free vector) into fnu[nt][3] and dPhi/dx_T (centroid) into fx[nt][3], all
+ * FP64 and including the prefactor c.  These are the one-point counterparts
+ * of the fields f_K, f_nu and f of Eq. (dTP_reordered), Sec. 3.2, which the
+ * surface finite-element assembly consumes.  Every mode (direct, Barnes-Hut,
+ * learned) and precision of tp_gradient is supported.  The outputs are device
+ * pointers when flags has TP_DEVICE_PTR, else host memory; any of them may be
+ * NULL.  Errors as tp_gradient. */
+tp_status tp_fields(tp_ctx* ctx, const tp_params* params, double* energy_out, double* fw, double* fnu, double* fx,
+                    uint32_t flags);
+
 /* Load the far-field network used by TP_LEARNED from a file written by
  * tp_far_model_save: header {"TPFM", version 1, 24, 64, 7, nparam, theta,
  * q, p, step}, then the feature mean/std/min/max [4][24] f32 and the FP32
@@ -150,8 +163,10 @@ tp_status tp_far_fit_normalisation(tp_ctx* ctx);
 tp_status tp_far_train(tp_ctx* ctx, int64_t steps, int64_t batch, double lr, double wd, uint64_t seed,
                        double* last_loss);
 /* Network on given rows X[n][24] (raw, or normalised if normalised != 0):
- * outputs Y[n][7]; with targets/masks [n][8] also the loss and the parameter
- * gradient grad[10375] (each output may be NULL).  For tests. */
+ * outputs Y[n][7].  With targets or masks [n][8] the training kernel runs and
+ * also returns the loss and the parameter gradient grad[10375]; with neither,
+ * the inference kernel of TP_LEARNED evaluations runs (grad and loss are
+ * zeroed).  Each output may be NULL.  For tests. */
 tp_status tp_far_eval(tp_ctx* ctx, const float* X, int64_t n, int normalised, const float* tgt, const float* mask,
                       float* Y, float* grad, double* loss);
 /* One AdamW step with the given gradient [10375].  For tests. */

@@ -33,7 +33,7 @@ _u8 = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
 
 def build(force: bool = False) -> str:
     """Compile ``oracle.c`` (and the MLP reference) into ``liboracle.so``."""
-    srcs = [os.path.join(_HERE, f) for f in ("oracle.c", "oracle_mlp.c") if os.path.exists(os.path.join(_HERE, f))]
+    srcs = [os.path.join(_HERE, f) for f in ("oracle.c", "oracle_mlp.c", "oracle_conf.c") if os.path.exists(os.path.join(_HERE, f))]
     if not force and os.path.exists(_SO) and all(os.path.getmtime(_SO) >= os.path.getmtime(s) for s in srcs + [os.path.join(_HERE, "oracle.h")]):
         return _SO
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared", "-std=c11",
@@ -62,6 +62,9 @@ def _load():
     lib.or_moments.argtypes = [_d, _i32, _d, _d, _d, i64, _i32, _i32, _i32, _d, _d]
     lib.or_bh_accum.argtypes = [_d, _d, _d, _i32, i64, _i32, _i32, _i32, _i32, _i32, _i32, i64, _d, _d, dbl, i32,
                                 dbl, dbl, i32, _d, _d, _d, C.POINTER(C.c_int64), C.POINTER(C.c_int64), i32]
+    lib.or_conf_energy.argtypes = [_d, _d, _d, i64, _d, _d, i64, dbl, dbl, dbl, i32]
+    lib.or_conf_energy.restype = dbl
+    lib.or_conf_accum.argtypes = [_d, _d, _d, i64, _d, _d, i64, dbl, dbl, _d, _d, _d, i32]
     if hasattr(lib, "or_mlp_forward"):
         _bind_mlp(lib)
     _lib = lib
@@ -322,3 +325,40 @@ def far_channels(x, nu, w, targets, members, momC, q=6.0, p=12.0):
                         np.ascontiguousarray(w, dtype=np.float64), tl, tl.size, sc, sc.size,
                         np.ascontiguousarray(momC, dtype=np.float64), q, p, mono, exact)
     return mono, exact
+
+
+# ---------------------------------------------------------------- confinement (Eq. TPConf)
+def conf_data(Vc, Fc):
+    """Centroids y [nk,3] and areas a [nk] of the confining surface's triangles."""
+    y, _, a = tri_data(Vc, Fc)
+    return y, a
+
+
+def conf_energy(V, F, Vc, Fc, q=6.0, p=12.0, c=1.0, soa=None, conf=None, nthreads=None):
+    """Phi_conf = c sum_T sum_K w_T a_K |nu_T.(x_T - y_K)|^q / |x_T - y_K|^p (Eq. TPConf)."""
+    lib = _load()
+    x, nu, w = soa if soa is not None else tri_data(V, F)
+    y, a = conf if conf is not None else conf_data(Vc, Fc)
+    x, nu, w, y, a = (np.ascontiguousarray(t, dtype=np.float64) for t in (x, nu, w, y, a))
+    return lib.or_conf_energy(x, nu, w, x.shape[0], y, a, y.shape[0], q, p, c, nthreads or nthreads_default())
+
+
+def conf_accum(V, F, Vc, Fc, q=6.0, p=12.0, soa=None, conf=None, nthreads=None):
+    """Per-triangle dPhi_conf/dw_T, dPhi_conf/dnu_T [.,3], dPhi_conf/dx_T [.,3] (without c)."""
+    lib = _load()
+    x, nu, w = soa if soa is not None else tri_data(V, F)
+    y, a = conf if conf is not None else conf_data(Vc, Fc)
+    x, nu, w, y, a = (np.ascontiguousarray(t, dtype=np.float64) for t in (x, nu, w, y, a))
+    nt = x.shape[0]
+    gw, gnu, gx = np.zeros(nt), np.zeros((nt, 3)), np.zeros((nt, 3))
+    lib.or_conf_accum(x, nu, w, nt, y, a, y.shape[0], q, p, gw, gnu, gx, nthreads or nthreads_default())
+    return gw, gnu, gx
+
+
+def conf_gradient(V, F, Vc, Fc, q=6.0, p=12.0, c=1.0, nthreads=None):
+    """(Phi_conf, dPhi_conf/dV [nv,3]): only the evolving surface moves."""
+    x, nu, w = tri_data(V, F)
+    conf = conf_data(Vc, Fc)
+    E = conf_energy(V, F, Vc, Fc, q, p, c, soa=(x, nu, w), conf=conf, nthreads=nthreads)
+    gw, gnu, gx = conf_accum(V, F, Vc, Fc, q, p, soa=(x, nu, w), conf=conf, nthreads=nthreads)
+    return E, adjoint(V, F, gw, gnu, gx, c)

@@ -56,6 +56,14 @@ void or_bh_accum(const double* x, const double* nu, const double* w, const int32
                  double q, double p, int adj, double* gw, double* gnu, double* gx,
                  int64_t* n_near_pairs, int64_t* n_far_terms, int nthreads);
 
+/* Confinement energy, Eq. (TPConf), Sec. 2.2 (oracle_conf.c): evolving surface
+ * (x, nu, w)[nt], fixed confining surface (centroids y, areas a)[nk]. */
+double or_conf_energy(const double* x, const double* nu, const double* w, int64_t nt, const double* y,
+                      const double* a, int64_t nk, double q, double p, double c, int nthreads);
+
+void or_conf_accum(const double* x, const double* nu, const double* w, int64_t nt, const double* y, const double* a,
+                   int64_t nk, double q, double p, double* gw, double* gnu, double* gx, int nthreads);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,6 +30,7 @@ from ._tp import (  # noqa: F401
     tp_destroy,
     tp_energy,
     tp_far_model_load,
+    tp_fields,
     tp_get_stats,
     tp_gradient,
     tp_last_error,
@@ -49,6 +50,7 @@ __all__ = [
     "tp_energy",
     "tp_gradient",
     "tp_far_model_load",
+    "tp_fields",
     "tp_get_stats",
     "tp_params_default",
 ]

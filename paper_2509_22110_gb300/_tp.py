@@ -77,6 +77,8 @@ def lib():
     L.tp_energy.restype = i32
     L.tp_gradient.argtypes = [vp, C.POINTER(tp_params), C.POINTER(C.c_double), vp, i32, u32]
     L.tp_gradient.restype = i32
+    L.tp_fields.argtypes = [vp, C.POINTER(tp_params), C.POINTER(C.c_double), vp, vp, vp, u32]
+    L.tp_fields.restype = i32
     L.tp_far_model_load.argtypes = [vp, C.c_char_p]
     L.tp_far_model_load.restype = i32
     L.tp_get_stats.argtypes = [vp, C.POINTER(tp_stats)]
@@ -214,6 +216,26 @@ def tp_gradient(ctx, grad_out, params=None, want_energy=True):
     _check(ctx, lib().tp_gradient(ctx, C.byref(p), C.byref(e) if want_energy else None, pg, gd,
                                   TP_DEVICE_PTR if dg else 0))
     return e.value if want_energy else None
+
+
+def tp_fields(ctx, nt, params=None, fw=None, fnu=None, fx=None):
+    """Per-triangle dPhi/dw [nt], dPhi/dnu [nt,3], dPhi/dx [nt,3] (float64, caller's
+    triangle order).  Outputs may be given (all host numpy or all CUDA tensors);
+    missing ones are allocated on the host.  Returns (energy, fw, fnu, fx)."""
+    p = params or tp_params_default()
+    given = [a for a in (fw, fnu, fx) if a is not None]
+    dev = bool(given) and _ptr(given[0])[1]
+    if not dev:
+        fw = np.zeros(nt) if fw is None else fw
+        fnu = np.zeros((nt, 3)) if fnu is None else fnu
+        fx = np.zeros((nt, 3)) if fx is None else fx
+    for a in (fw, fnu, fx):
+        if a is not None and (not str(a.dtype).endswith("float64") or _ptr(a)[1] != dev):
+            raise ValueError("outputs must be float64 and all on the host or all on the device")
+    e = C.c_double(0.0)
+    _check(ctx, lib().tp_fields(ctx, C.byref(p), C.byref(e), _ptr(fw)[0], _ptr(fnu)[0], _ptr(fx)[0],
+                                TP_DEVICE_PTR if dev else 0))
+    return e.value, fw, fnu, fx
 
 
 def tp_far_model_load(ctx, path):

@@ -78,6 +78,24 @@ __global__ void k_adjoint(const double* __restrict__ V, const int32_t* __restric
     for (int a = 0; a < 3; ++a) grad[3 * v + a] = (OutT)(scale * g[a]);
 }
 
+// Per-triangle derivatives in the caller's order, with w, nu and x taken as
+// independent variables (the one-point counterparts of f_K, f_nu and f of
+// Eq. (dTP_reordered), Sec. 3.2): fw [nt], fnu [nt][3], fx [nt][3].
+__global__ void k_fields(const int32_t* __restrict__ iperm, const double* __restrict__ nu64,
+                         const double* __restrict__ w64, const double* __restrict__ acc, int64_t nt, int64_t ntp,
+                         double q, double pq, double scale, double* __restrict__ fw, double* __restrict__ fnu,
+                         double* __restrict__ fx) {
+    const int64_t T = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (T >= nt) return;
+    const int64_t k = iperm[T];
+    const double U = acc[1 * ntp + k];
+    if (fw) fw[T] = scale * acc[0 * ntp + k] / (pq * w64[T]);
+    for (int a = 0; a < 3; ++a) {
+        if (fnu) fnu[3 * T + a] = scale * q * acc[(2 + a) * ntp + k] / pq;
+        if (fx) fx[3 * T + a] = scale * q * (acc[(5 + a) * ntp + k] + U * nu64[a * nt + T]) / pq;
+    }
+}
+
 // deterministic two-pass sum of n doubles: fixed per-thread strides, fixed tree
 __global__ void k_sum_partial(const double* __restrict__ in, int64_t n, int64_t stride, double* __restrict__ part) {
     __shared__ double sh[256];
@@ -120,6 +138,16 @@ tp_status tp_launch_adjoint(tp_ctx* ctx, const tp_params* prm, void* grad, int g
         k_adjoint<float><<<blocks, 256, 0, ctx->stream>>>(ctx->V64, ctx->F, ctx->v2t_off, ctx->v2t, ctx->iperm,
                                                           ctx->nu64, ctx->w64, ctx->acc, nv, ctx->nt, ctx->ntp, q,
                                                           pq, prm->scale, static_cast<float*>(grad));
+    ++ctx->nlaunch;
+    TP_CU(cudaGetLastError());
+    return TP_OK;
+}
+
+tp_status tp_launch_fields(tp_ctx* ctx, const tp_params* prm, double* fw, double* fnu, double* fx) {
+    const int64_t nt = ctx->nt;
+    const double q = prm->q, pq = (double)prm->p / prm->q;
+    k_fields<<<(unsigned)((nt + 255) / 256), 256, 0, ctx->stream>>>(ctx->iperm, ctx->nu64, ctx->w64, ctx->acc, nt,
+                                                                    ctx->ntp, q, pq, prm->scale, fw, fnu, fx);
     ++ctx->nlaunch;
     TP_CU(cudaGetLastError());
     return TP_OK;

@@ -26,6 +26,11 @@
 // list flush and FP64 across flushes; each target is owned by one warp, so
 // results are stored without atomics in the same accumulator layout as the
 // direct kernels (see tp_direct.cu), and the same adjoint applies.
+//
+// Learned correction (TP_LEARNED).  The Barnes-Hut pass also lists the far
+// nodes of every leaf (runs of up to 256 nodes, reserved with one atomic per
+// run); a second kernel runs the network on the listed (leaf, cluster) pairs
+// in batches of 32 and adds the change of the far terms to the targets.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -67,6 +72,10 @@ struct BHArgs {
     const __nv_bfloat16* wb;     // network weights (BF16 block)
     const float* mbias;          // network biases
     const float* mnorm;          // [4][24] feature mean, std, lo, hi
+    int32_t* far_list;           // M_LIST: far node ids, in runs of one leaf
+    tp_far_run* far_runs;        // M_LIST: the runs
+    unsigned long long* far_count;  // [2] rows and runs listed (counted past the capacities)
+    int64_t far_cap, run_cap;
     // sampling of far pairs (RECORD mode)
     uint32_t keep_u;
     uint64_t seed;
@@ -75,11 +84,9 @@ struct BHArgs {
     int32_t* rec_count;
 };
 
-enum { M_BH = 0, M_LEARNED = 1, M_RECORD = 2 };
-constexpr int LW_X = 32 * MLP_NIP;       // per-warp BF16 input rows
-constexpr int LW_H = 32 * MLP_NH;        // per-warp BF16 hidden rows (two buffers)
-constexpr size_t LEARN_WARP_BYTES = (size_t)(LW_X + 2 * LW_H) * 2 + 32 * MLP_NOP * 4 + 32 * 8 * 4 + 32 * 4;
-constexpr size_t LEARN_SMEM = (size_t)MLPB_N * 2 + MLPF_N * 4 + 4 * MLP_NI * 4 + 4 * LEARN_WARP_BYTES;
+// M_BH: evaluate; M_LIST: evaluate and list the far nodes of every leaf for
+// the learned correction; M_RECORD: sample far pairs for training only.
+enum { M_BH = 0, M_LIST = 1, M_RECORD = 2 };
 
 __device__ __forceinline__ float bh_rcp(float x) {
     float y;
@@ -257,7 +264,6 @@ __device__ __forceinline__ bool adjacent(int3 a, int3 b, int edge_only) {
 
 template <int Q, int MODE>
 __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
-    extern __shared__ __align__(16) unsigned char lsm[];  // LEARNED: network and per-warp scratch
     __shared__ int32_t s_stack[BH_WARPS][BH_STACK];
     __shared__ int32_t s_far[BH_WARPS][BH_FAR];
     __shared__ int32_t s_near[BH_WARPS][BH_NEAR];
@@ -266,16 +272,6 @@ __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
     __shared__ int4 s_stg_f[BH_WARPS][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t li = (int64_t)blockIdx.x * BH_WARPS + warp;
-    __nv_bfloat16* s_wb = reinterpret_cast<__nv_bfloat16*>(lsm);
-    float* s_bias = reinterpret_cast<float*>(lsm + MLPB_N * 2);
-    float* s_norm = s_bias + MLPF_N;
-    unsigned char* wscr = lsm + MLPB_N * 2 + MLPF_N * 4 + 4 * MLP_NI * 4 + warp * LEARN_WARP_BYTES;
-    if (MODE == M_LEARNED) {
-        for (int i = threadIdx.x; i < MLPB_N; i += blockDim.x) s_wb[i] = A.wb[i];
-        for (int i = threadIdx.x; i < MLPF_N; i += blockDim.x) s_bias[i] = A.mbias[i];
-        for (int i = threadIdx.x; i < 4 * MLP_NI; i += blockDim.x) s_norm[i] = A.mnorm[i];
-        __syncthreads();
-    }
     if (li >= A.nleaves) return;
     int32_t* st = s_stack[warp];
     int32_t* far = s_far[warp];
@@ -309,12 +305,33 @@ __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
         tg.w = 0.f;
     }
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    unsigned long long n_near = 0, n_far = 0, n_farp = 0, n_learn = 0;
+    unsigned long long n_near = 0, n_far = 0, n_farp = 0;
     const unsigned lt = (1u << lane) - 1u;
 
     // far list: stage 32 node records at a time in shared memory, then every
     // half-warp sweeps them (half h takes records h, h+2, ...)
     auto flush_far = [&](int nf) {
+        if (MODE == M_LIST && nf > 0) {
+            // one run of this leaf: reserve rows and a run record, store the node ids
+            unsigned long long pos = 0, run = 0;
+            if (lane == 0) {
+                pos = atomicAdd(&A.far_count[0], (unsigned long long)nf);
+                run = atomicAdd(&A.far_count[1], 1ull);
+            }
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            run = __shfl_sync(0xffffffffu, run, 0);
+            if (pos + (unsigned long long)nf <= (unsigned long long)A.far_cap &&
+                run < (unsigned long long)A.run_cap) {
+                for (int i = lane; i < nf; i += 32) A.far_list[pos + i] = far[i];
+                if (lane == 0) {
+                    tp_far_run fr;
+                    fr.start = (int64_t)pos;
+                    fr.li = (int32_t)li;
+                    fr.len = nf;
+                    A.far_runs[run] = fr;
+                }
+            }
+        }
         float a32[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int b0 = 0; b0 < nf; b0 += 32) {
             const int nb = nf - b0 < 32 ? nf - b0 : 32;
@@ -329,60 +346,12 @@ __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
                 stg_cnt[lane] = A.last[C] - A.first[C] + 1;
             }
             __syncwarp();
-            if (MODE == M_LEARNED) {
-                // features of (L, C) for this lane's node, the network on the 32 rows, factors
-                __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(wscr);
-                __nv_bfloat16* ha = X + LW_X;
-                __nv_bfloat16* hb = ha + LW_H;
-                float* y = reinterpret_cast<float*>(hb + LW_H);
-                float* kf = y + 32 * MLP_NOP;
-                int* ind = reinterpret_cast<int*>(kf + 32 * 8);
-                int in_dist = 0;
-                if (lane < nb) {
-                    float f[MLP_NI];
-                    far_features(A.nodeft + 16 * L, A.nodeft + 16 * (int64_t)far[b0 + lane], f);
-                    in_dist = 1;
-#pragma unroll
-                    for (int c = 0; c < MLP_NI; ++c) {
-                        const float lo = s_norm[2 * MLP_NI + c], hi = s_norm[3 * MLP_NI + c];
-                        const float pad = 0.05f * (hi - lo);
-                        if (!(f[c] >= lo - pad && f[c] <= hi + pad)) in_dist = 0;
-                        X[lane * MLP_NIP + c] = __float2bfloat16_rn((f[c] - s_norm[c]) / s_norm[MLP_NI + c]);
-                    }
-                } else {
-#pragma unroll
-                    for (int c = 0; c < MLP_NI; ++c) X[lane * MLP_NIP + c] = __float2bfloat16_rn(0.f);
-                }
-#pragma unroll
-                for (int c = MLP_NI; c < MLP_NIP; ++c) X[lane * MLP_NIP + c] = __float2bfloat16_rn(0.f);
-                ind[lane] = in_dist;
-                __syncwarp();
-                warp_mlp_forward(s_wb, s_bias, X, ha, hb, ha, nullptr, nullptr, nullptr, y, 0);
-                warp_mlp_forward(s_wb, s_bias, X, ha, hb, ha, nullptr, nullptr, nullptr, y, 16);
-                if (lane < nb) {
-#pragma unroll
-                    for (int c = 0; c < MLP_NO; ++c)
-                        kf[lane * 8 + c] = ind[lane] ? __expf(fminf(4.f, fmaxf(-4.f, y[lane * MLP_NOP + c]))) : 1.f;
-                }
-                __syncwarp();
-                for (int i = half; i < nb; i += 2) {
-                    const float* r = stg + i * 16;
-                    if (active) {
-                        gather_pair_learned<Q>(tg, r, r + 3, r + 6, r[9], kf + i * 8, a32);
-                        n_far += 1;
-                        n_farp += (unsigned long long)stg_cnt[i];
-                        n_learn += (unsigned long long)ind[i];
-                    }
-                }
-                __syncwarp();
-            } else {
-                for (int i = half; i < nb; i += 2) {
-                    const float* r = stg + i * 16;
-                    if (active) {
-                        gather_pair<Q>(tg, r, r + 3, r + 6, r[9], a32);
-                        n_far += 1;
-                        n_farp += (unsigned long long)stg_cnt[i];
-                    }
+            for (int i = half; i < nb; i += 2) {
+                const float* r = stg + i * 16;
+                if (active) {
+                    gather_pair<Q>(tg, r, r + 3, r + 6, r[9], a32);
+                    n_far += 1;
+                    n_farp += (unsigned long long)stg_cnt[i];
                 }
             }
         }
@@ -511,14 +480,129 @@ __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
         n_near += __shfl_xor_sync(0xffffffffu, n_near, o);
         n_far += __shfl_xor_sync(0xffffffffu, n_far, o);
         n_farp += __shfl_xor_sync(0xffffffffu, n_farp, o);
-        n_learn += __shfl_xor_sync(0xffffffffu, n_learn, o);
     }
     if (lane == 0) {
         atomicAdd(&A.counts[0], n_near);
         atomicAdd(&A.counts[1], n_far);
         atomicAdd(&A.counts[2], n_farp);
-        atomicAdd(&A.counts[3], n_learn);
     }
+}
+
+// ------------------------------------------------------------ learned correction
+// The far terms evaluated by the Barnes-Hut pass carry factor 1 in every
+// channel; the network's factors kf replace them, so each listed (leaf L,
+// cluster C) pair adds (kf - 1) x channel to the targets of L.  One warp per
+// run (up to 256 far nodes of one leaf): per 32 nodes the lanes build the
+// features of their (L, C) pair, the warp runs the network on the tensor
+// cores with activations in registers (two 16-row tiles), and the half-warps
+// sweep the nodes for the 16 targets.  Pairs outside the training ranges
+// keep factor 1 (no correction).  Runs of one leaf may be processed by
+// different warps at once, so the FP32 run sums are added to the FP64
+// accumulators atomically.
+constexpr int FL_WARPS = 8;
+struct FarWarpSmem {
+    __nv_bfloat16 X[32 * MLP_NIP];  // normalised features, BF16
+    float y[32 * MLP_NOP];          // network outputs
+    float kf[32 * 8];               // factors - 1
+    float stg[32 * 16];             // node records
+    int ind[32];                    // in the training ranges
+};
+constexpr size_t FL_SMEM = (size_t)MLPB_N * 2 + MLPF_N * 4 + 4 * MLP_NI * 4 + FL_WARPS * sizeof(FarWarpSmem);
+
+template <int Q>
+__global__ void __launch_bounds__(FL_WARPS * 32) k_far_learned(BHArgs A) {
+    extern __shared__ __align__(16) unsigned char fsm[];
+    __nv_bfloat16* s_wb = reinterpret_cast<__nv_bfloat16*>(fsm);
+    float* s_bias = reinterpret_cast<float*>(fsm + MLPB_N * 2);
+    float* s_norm = s_bias + MLPF_N;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    FarWarpSmem* ws = reinterpret_cast<FarWarpSmem*>(fsm + MLPB_N * 2 + MLPF_N * 4 + 4 * MLP_NI * 4) + warp;
+    for (int i = threadIdx.x; i < MLPB_N; i += blockDim.x) s_wb[i] = A.wb[i];
+    for (int i = threadIdx.x; i < MLPF_N; i += blockDim.x) s_bias[i] = A.mbias[i];
+    for (int i = threadIdx.x; i < 4 * MLP_NI; i += blockDim.x) s_norm[i] = A.mnorm[i];
+    __syncthreads();
+    const unsigned long long nr = A.far_count[1];
+    const int64_t nruns = nr < (unsigned long long)A.run_cap ? (int64_t)nr : A.run_cap;
+    const int t = lane & 15, half = lane >> 4;
+    unsigned long long n_learn = 0;
+    for (int64_t run = (int64_t)blockIdx.x * FL_WARPS + warp; run < nruns; run += (int64_t)gridDim.x * FL_WARPS) {
+        const tp_far_run R = A.far_runs[run];
+        const int64_t L = A.leaves[R.li];
+        const int64_t fL = A.first[L];
+        const int cnt = A.last[L] - A.first[L] + 1;
+        const bool active = t < cnt;
+        const int64_t k = fL + t;
+        Tgt tg;
+        if (active) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                tg.h[c] = A.soa[c * A.ntp + k];
+                tg.l[c] = A.soa[(3 + c) * A.ntp + k];
+                tg.n[c] = A.soa[(6 + c) * A.ntp + k];
+            }
+            tg.w = A.soa[9 * A.ntp + k];
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) tg.h[c] = tg.l[c] = tg.n[c] = 0.f;
+            tg.w = 0.f;
+        }
+        float a32[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int b0 = 0; b0 < R.len; b0 += 32) {
+            const int nb = R.len - b0 < 32 ? R.len - b0 : 32;
+            __syncwarp();
+            int in_dist = 0;
+            if (lane < nb) {
+                const int64_t C = A.far_list[R.start + b0 + lane];
+                const float4* r = reinterpret_cast<const float4*>(A.nodef + 16 * C);
+                float4* d = reinterpret_cast<float4*>(ws->stg + lane * 16);
+                d[0] = r[0];
+                d[1] = r[1];
+                d[2] = r[2];
+                float f[MLP_NI];
+                far_features(A.nodeft + 16 * L, A.nodeft + 16 * C, f);
+                in_dist = 1;
+#pragma unroll
+                for (int c = 0; c < MLP_NI; ++c) {
+                    const float lo = s_norm[2 * MLP_NI + c], hi = s_norm[3 * MLP_NI + c];
+                    const float pad = 0.05f * (hi - lo);
+                    if (!(f[c] >= lo - pad && f[c] <= hi + pad)) in_dist = 0;
+                    ws->X[lane * MLP_NIP + c] = __float2bfloat16_rn((f[c] - s_norm[c]) / s_norm[MLP_NI + c]);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < MLP_NI; ++c) ws->X[lane * MLP_NIP + c] = __float2bfloat16_rn(0.f);
+            }
+#pragma unroll
+            for (int c = MLP_NI; c < MLP_NIP; ++c) ws->X[lane * MLP_NIP + c] = __float2bfloat16_rn(0.f);
+            ws->ind[lane] = in_dist;
+            __syncwarp();
+            warp_mlp_forward_regs(s_wb, s_bias, ws->X, ws->y, 0);
+            if (nb > 16) warp_mlp_forward_regs(s_wb, s_bias, ws->X, ws->y, 16);
+            __syncwarp();
+            if (lane < nb) {
+#pragma unroll
+                for (int c = 0; c < MLP_NO; ++c)
+                    ws->kf[lane * 8 + c] = in_dist ? __expf(fminf(4.f, fmaxf(-4.f, ws->y[lane * MLP_NOP + c]))) - 1.f : 0.f;
+            }
+            __syncwarp();
+            for (int i = half; i < nb; i += 2) {
+                if (active && ws->ind[i]) {
+                    const float* r = ws->stg + i * 16;
+                    gather_pair_learned<Q>(tg, r, r + 3, r + 6, r[9], ws->kf + i * 8, a32);
+                    n_learn += 1;
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a32[c] += __shfl_xor_sync(0xffffffffu, a32[c], 16);
+        if (half == 0 && active) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (a32[c] != 0.f) atomicAdd(&A.acc[c * A.ntp + k], (double)a32[c]);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) n_learn += __shfl_xor_sync(0xffffffffu, n_learn, o);
+    if (lane == 0 && n_learn) atomicAdd(&A.counts[3], n_learn);
 }
 
 BHArgs make_bh_args(tp_ctx* ctx, double theta, int edge_only) {
@@ -562,19 +646,59 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
     const unsigned blocks = (unsigned)((t.nleaves + BH_WARPS - 1) / BH_WARPS);
     cudaEventRecord(ctx->ev[0], ctx->stream);
     if (learned) {
+        // Barnes-Hut pass that also lists the far nodes of every leaf, then the
+        // network's correction of those far terms
         A.wb = static_cast<const __nv_bfloat16*>(tp_mlp_weights(ctx));
         A.mbias = tp_mlp_bias(ctx);
         A.mnorm = tp_mlp_norm(ctx);
+        if (!ctx->far_count) TP_TRY(tp_alloc_t(ctx, &ctx->far_count, 2));
+        if (!ctx->far_list) {
+            const int64_t rows = std::max<int64_t>(1 << 20, t.nleaves * 1024);
+            TP_TRY(tp_alloc_t(ctx, &ctx->far_list, rows));
+            TP_TRY(tp_alloc_t(ctx, &ctx->far_runs, rows / 32 + t.nleaves + 1024));
+            ctx->far_cap = rows;
+            ctx->run_cap = rows / 32 + t.nleaves + 1024;
+        }
+        for (int attempt = 0;; ++attempt) {
+            TP_CU(cudaMemsetAsync(ctx->far_count, 0, 2 * sizeof(unsigned long long), ctx->stream));
+            A.far_list = ctx->far_list;
+            A.far_runs = ctx->far_runs;
+            A.far_count = ctx->far_count;
+            A.far_cap = ctx->far_cap;
+            A.run_cap = ctx->run_cap;
+            if (prm->q == 6)
+                k_bh<6, M_LIST><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
+            else
+                k_bh<8, M_LIST><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
+            ++ctx->nlaunch;
+            unsigned long long fc[2] = {0, 0};
+            TP_CU(cudaMemcpyAsync(fc, ctx->far_count, sizeof(fc), cudaMemcpyDeviceToHost, ctx->stream));
+            TP_CU(cudaStreamSynchronize(ctx->stream));
+            if ((int64_t)fc[0] <= ctx->far_cap && (int64_t)fc[1] <= ctx->run_cap) break;
+            if (attempt > 0) return tp_set_err(ctx, TP_E_OOM, "far-pair list overflow");
+            // enlarge to the counted need (with slack) and repeat the pass
+            tp_free(ctx, ctx->far_list);
+            tp_free(ctx, ctx->far_runs);
+            ctx->far_list = nullptr;
+            ctx->far_runs = nullptr;
+            const int64_t rows = (int64_t)(fc[0] + fc[0] / 4 + 1024), runs = (int64_t)(fc[1] + fc[1] / 4 + 1024);
+            TP_TRY(tp_alloc_t(ctx, &ctx->far_list, rows));
+            TP_TRY(tp_alloc_t(ctx, &ctx->far_runs, runs));
+            ctx->far_cap = rows;
+            ctx->run_cap = runs;
+            TP_CU(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), ctx->stream));
+        }
         static bool attr = false;
         if (!attr) {
-            cudaFuncSetAttribute(k_bh<6, M_LEARNED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LEARN_SMEM);
-            cudaFuncSetAttribute(k_bh<8, M_LEARNED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LEARN_SMEM);
+            cudaFuncSetAttribute(k_far_learned<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FL_SMEM);
+            cudaFuncSetAttribute(k_far_learned<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FL_SMEM);
             attr = true;
         }
+        const unsigned lblocks = (unsigned)std::max(1, ctx->num_sms * 3);
         if (prm->q == 6)
-            k_bh<6, M_LEARNED><<<blocks, BH_WARPS * 32, LEARN_SMEM, ctx->stream>>>(A);
+            k_far_learned<6><<<lblocks, FL_WARPS * 32, FL_SMEM, ctx->stream>>>(A);
         else
-            k_bh<8, M_LEARNED><<<blocks, BH_WARPS * 32, LEARN_SMEM, ctx->stream>>>(A);
+            k_far_learned<8><<<lblocks, FL_WARPS * 32, FL_SMEM, ctx->stream>>>(A);
     } else {
         if (prm->q == 6)
             k_bh<6, M_BH><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);

@@ -152,6 +152,7 @@ void release_mesh(tp_ctx* ctx) {
     free_ptr(ctx, ctx->flist);
     free_ptr(ctx, ctx->tbox);
     free_ptr(ctx, ctx->gradbuf);
+    free_ptr(ctx, ctx->fieldbuf);
     free_ptr(ctx, ctx->vtmp);
     tp_tree& t = ctx->tree;
     free_ptr(ctx, t.codes);
@@ -395,8 +396,13 @@ tp_status tp_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits) {
     return TP_OK;
 }
 
+// Per-triangle outputs of tp_fields (null: tp_energy / tp_gradient).
+struct FieldOut {
+    double *fw, *fnu, *fx;
+};
+
 static tp_status run_eval(tp_ctx* ctx, const tp_params* prm, bool want_grad, void* grad_out, int g_dtype,
-                          uint32_t flags, double* energy_out) {
+                          uint32_t flags, double* energy_out, const FieldOut* fields = nullptr) {
     TP_TRY(check_params(ctx, prm));
     const int64_t nt = ctx->nt, nv = ctx->nv;
     ctx->stats = tp_stats{};
@@ -408,11 +414,11 @@ static tp_status run_eval(tp_ctx* ctx, const tp_params* prm, bool want_grad, voi
     const bool dev = flags & TP_DEVICE_PTR;
     if (want_grad && g_dtype != TP_DTYPE_F32 && g_dtype != TP_DTYPE_F64)
         return tp_set_err(ctx, TP_E_ARG, "bad g_dtype %d", g_dtype);
-    if (want_grad && nv > 0 && !grad_out) return tp_set_err(ctx, TP_E_ARG, "grad_out is NULL");
+    if (want_grad && !fields && nv > 0 && !grad_out) return tp_set_err(ctx, TP_E_ARG, "grad_out is NULL");
     const size_t gbytes = (size_t)(3 * nv) * (g_dtype == TP_DTYPE_F64 ? 8 : 4);
     if (nt == 0) {
         if (energy_out) *energy_out = 0.0;
-        if (want_grad && nv > 0) {
+        if (want_grad && !fields && nv > 0) {
             if (dev) TP_CU(cudaMemsetAsync(grad_out, 0, gbytes, ctx->stream));
             else memset(grad_out, 0, gbytes);
             TP_CU(cudaStreamSynchronize(ctx->stream));
@@ -449,7 +455,16 @@ static tp_status run_eval(tp_ctx* ctx, const tp_params* prm, bool want_grad, voi
         TP_TRY(tp_launch_energy_from_acc(ctx, prm, ctx->scalar));
     }
     void* gdst = nullptr;
-    if (want_grad) {
+    if (fields) {
+        double* st = nullptr;
+        if (!dev) {
+            if (!ctx->fieldbuf) TP_TRY(tp_alloc_t(ctx, &ctx->fieldbuf, 7 * ctx->cap_nt));
+            st = ctx->fieldbuf;
+        }
+        TP_TRY(tp_launch_fields(ctx, prm, dev ? fields->fw : (fields->fw ? st : nullptr),
+                                dev ? fields->fnu : (fields->fnu ? st + nt : nullptr),
+                                dev ? fields->fx : (fields->fx ? st + 4 * nt : nullptr)));
+    } else if (want_grad) {
         gdst = dev ? grad_out : (void*)ctx->gradbuf;
         TP_TRY(tp_launch_adjoint(ctx, prm, gdst, g_dtype));
     }
@@ -460,8 +475,15 @@ static tp_status run_eval(tp_ctx* ctx, const tp_params* prm, bool want_grad, voi
     } else {
         TP_CU(cudaMemcpyAsync(&e, ctx->scalar + 1, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     }
-    if (want_grad && !dev && nv > 0)
+    if (want_grad && !fields && !dev && nv > 0)
         TP_CU(cudaMemcpyAsync(grad_out, ctx->gradbuf, gbytes, cudaMemcpyDeviceToHost, ctx->stream));
+    if (fields && !dev) {
+        if (fields->fw) TP_CU(cudaMemcpyAsync(fields->fw, ctx->fieldbuf, 8 * nt, cudaMemcpyDeviceToHost, ctx->stream));
+        if (fields->fnu)
+            TP_CU(cudaMemcpyAsync(fields->fnu, ctx->fieldbuf + nt, 24 * nt, cudaMemcpyDeviceToHost, ctx->stream));
+        if (fields->fx)
+            TP_CU(cudaMemcpyAsync(fields->fx, ctx->fieldbuf + 4 * nt, 24 * nt, cudaMemcpyDeviceToHost, ctx->stream));
+    }
     TP_CU(cudaStreamSynchronize(ctx->stream));
     TP_TRY(take_device_error(ctx, want_grad ? "tp_gradient" : "tp_energy"));
     if (!energy_from_acc && prm->mode == TP_DIRECT) {
@@ -494,6 +516,15 @@ tp_status tp_gradient(tp_ctx* ctx, const tp_params* params, double* energy_out, 
     DeviceGuard g(ctx->device);
     ctx->err.clear();
     return run_eval(ctx, params, true, grad_out, g_dtype, flags, energy_out);
+}
+
+tp_status tp_fields(tp_ctx* ctx, const tp_params* params, double* energy_out, double* fw, double* fnu, double* fx,
+                    uint32_t flags) {
+    if (!ctx) return TP_E_ARG;
+    DeviceGuard g(ctx->device);
+    ctx->err.clear();
+    const FieldOut fo{fw, fnu, fx};
+    return run_eval(ctx, params, true, nullptr, TP_DTYPE_F64, flags, energy_out, &fo);
 }
 
 tp_status tp_get_stats(const tp_ctx* ctx, tp_stats* out) {

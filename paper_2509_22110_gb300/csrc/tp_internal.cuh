@@ -66,6 +66,14 @@ struct tp_tree {
 
 struct tp_mlp_model;
 
+// A run of the learned far field's pair list: far nodes of one target leaf
+// (leaf index li) at far_list[start, start + len), in traversal order.
+struct tp_far_run {
+    int64_t start;
+    int32_t li;
+    int32_t len;
+};
+
 struct tp_ctx {
     int device = 0;
     int num_sms = 0;
@@ -118,11 +126,17 @@ struct tp_ctx {
     int64_t n_excluded_ordered = 0;  // ordered pairs T != S sharing a vertex
     int64_t cap_nv = 0, cap_nt = 0, cap_ntp = 0, red_cap = 0;
     double* gradbuf = nullptr;      // [3nv] device staging of host gradients
+    double* fieldbuf = nullptr;     // [7nt] device staging of host per-triangle fields (allocated on first use)
     float* vtmp = nullptr;          // [3nv] f32 staging of f32 positions
     double last_q = 6.0, last_pq = 2.0;
     int64_t nlaunch = 0;            // library kernels launched in the current call
     tp_tree tree;
     tp_mlp_model* mlp = nullptr;
+    // far (leaf, cluster) pairs listed by the Barnes-Hut pass for the learned correction
+    int32_t* far_list = nullptr;
+    tp_far_run* far_runs = nullptr;
+    unsigned long long* far_count = nullptr;  // [2] rows and runs listed (may exceed the capacities)
+    int64_t far_cap = 0, run_cap = 0;
 
     tp_stats stats{};
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -158,6 +172,7 @@ tp_status tp_launch_tri_data(tp_ctx* ctx);
 tp_status tp_launch_morton_order(tp_ctx* ctx, int morton_bits);
 tp_status tp_launch_sorted_soa(tp_ctx* ctx);
 tp_status tp_launch_flagged(tp_ctx* ctx, bool topology);
+tp_status tp_launch_fields(tp_ctx* ctx, const tp_params* prm, double* fw, double* fnu, double* fx);
 tp_status tp_build_v2t(tp_ctx* ctx);
 tp_status tp_count_excluded(tp_ctx* ctx);
 // tp_direct.cu

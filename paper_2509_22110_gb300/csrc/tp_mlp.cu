@@ -475,6 +475,39 @@ __global__ void __launch_bounds__(128) k_mlp_train(const __nv_bfloat16* __restri
     if (tid == 0) atomicAdd(&loss[0], S.lsum[0]);
 }
 
+// Forward pass only, with the inference arithmetic of the learned Barnes-Hut
+// correction (warp_mlp_forward_regs): 4 warps x 32 rows per block.
+__global__ void __launch_bounds__(128) k_mlp_infer(const __nv_bfloat16* __restrict__ wb_g,
+                                                   const float* __restrict__ bias_g, const float* __restrict__ norm,
+                                                   const float* __restrict__ X, int64_t n, int normalised,
+                                                   float* __restrict__ Y) {
+    __shared__ __align__(16) __nv_bfloat16 s_wb[MLPB_N];
+    __shared__ float s_bias[MLPF_N];
+    __shared__ __align__(16) __nv_bfloat16 s_x[4][32 * MLP_NIP];
+    __shared__ float s_y[4][32 * MLP_NOP];
+    for (int i = threadIdx.x; i < MLPB_N; i += blockDim.x) s_wb[i] = wb_g[i];
+    for (int i = threadIdx.x; i < MLPF_N; i += blockDim.x) s_bias[i] = bias_g[i];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row = ((int64_t)blockIdx.x * 4 + warp) * 32 + lane;
+    __nv_bfloat16* x = s_x[warp] + lane * MLP_NIP;
+#pragma unroll
+    for (int c = 0; c < MLP_NIP; ++c) {
+        float v = 0.f;
+        if (row < n && c < MLP_NI) {
+            v = X[row * MLP_NI + c];
+            if (!normalised) v = (v - norm[c]) / norm[MLP_NI + c];
+        }
+        x[c] = __float2bfloat16_rn(v);
+    }
+    __syncwarp();
+    warp_mlp_forward_regs(s_wb, s_bias, s_x[warp], s_y[warp], 0);
+    warp_mlp_forward_regs(s_wb, s_bias, s_x[warp], s_y[warp], 16);
+    __syncwarp();
+    if (row < n)
+        for (int c = 0; c < MLP_NO; ++c) Y[row * MLP_NO + c] = s_y[warp][lane * MLP_NOP + c];
+}
+
 // sum of the masks of a batch (the loss normaliser)
 __global__ void k_mask_sum(const float* __restrict__ mask, int64_t ndata, int64_t batch, uint64_t seed,
                            const float* __restrict__ mask_direct, double* __restrict__ out) {
@@ -794,6 +827,22 @@ tp_status tp_far_eval(tp_ctx* ctx, const float* X, int64_t n, int normalised, co
         attr = true;
     }
     float *dX = nullptr, *dT = nullptr, *dM = nullptr, *dY = nullptr;
+    if (!tgt && !mask) {
+        // forward only: the inference kernel of the learned correction
+        TP_TRY(tp_alloc_t(ctx, &dX, n * MLP_NI));
+        TP_TRY(tp_alloc_t(ctx, &dY, n * MLP_NO));
+        TP_CU(cudaMemcpyAsync(dX, X, 4 * MLP_NI * n, cudaMemcpyHostToDevice, ctx->stream));
+        k_mlp_infer<<<(unsigned)((n + 127) / 128), 128, 0, ctx->stream>>>(m->wb, m->bias, m->norm, dX, n,
+                                                                          normalised, dY);
+        TP_CU(cudaGetLastError());
+        if (Y) TP_CU(cudaMemcpyAsync(Y, dY, 4 * MLP_NO * n, cudaMemcpyDeviceToHost, ctx->stream));
+        TP_CU(cudaStreamSynchronize(ctx->stream));
+        if (grad) memset(grad, 0, 4 * MLP_NPARAM);
+        if (loss) *loss = 0.0;
+        tp_free(ctx, dX);
+        tp_free(ctx, dY);
+        return TP_OK;
+    }
     TP_TRY(tp_alloc_t(ctx, &dX, n * MLP_NI));
     TP_TRY(tp_alloc_t(ctx, &dT, n * 8));
     TP_TRY(tp_alloc_t(ctx, &dM, n * 8));

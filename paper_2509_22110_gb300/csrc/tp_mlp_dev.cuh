@@ -157,6 +157,60 @@ __device__ __forceinline__ void warp_mlp_forward(const __nv_bfloat16* wb, const 
     __syncwarp();
 }
 
+// Register-resident variant for inference: the accumulator fragment of a
+// 16 x 8 output tile holds (row g, cols 2t, 2t+1) and (row g+8, same cols)
+// per lane (g = lane/4, t = lane%4), exactly the halves of the A fragment
+// of the next layer's 16 x 16 k-tile, so hidden activations stay in
+// registers (GELU applied, packed to BF16) and only the input X and the
+// output y touch shared memory.
+template <int KT, int NT>
+__device__ __forceinline__ void dense_regs(const uint32_t (&a)[KT][4], const __nv_bfloat16* W, const float* bias,
+                                           uint32_t (&h)[NT / 2][4]) {
+    const int t2 = ((threadIdx.x & 31) & 3) * 2;
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kk = 0; kk < KT; ++kk) {
+            uint32_t b[2];
+            load_b_nk(W, 16 * KT, 16 * kk, 8 * j, b);
+            mma_bf16(d, a[kk], b);
+        }
+        const float b0 = bias[8 * j + t2], b1 = bias[8 * j + t2 + 1];
+        const uint32_t lo = pack_bf16(mlp_gelu(d[0] + b0, nullptr), mlp_gelu(d[1] + b1, nullptr));
+        const uint32_t hi = pack_bf16(mlp_gelu(d[2] + b0, nullptr), mlp_gelu(d[3] + b1, nullptr));
+        h[j >> 1][(j & 1) * 2 + 0] = lo;
+        h[j >> 1][(j & 1) * 2 + 1] = hi;
+    }
+}
+
+// Network forward for 16 rows (m0..m0+15) of X (BF16 [rows][32] in shared
+// memory, normalised features, zero-padded): y (FP32 [rows][8], shared
+// memory, column 7 unused) = the 7 outputs.  Same arithmetic as
+// warp_mlp_forward (BF16 operands, FP32 accumulation, BF16 activations).
+__device__ __forceinline__ void warp_mlp_forward_regs(const __nv_bfloat16* wb, const float* bias,
+                                                      const __nv_bfloat16* X, float* y, int m0) {
+    uint32_t a1[2][4];
+    load_a_rm(X, MLP_NIP, m0, 0, a1[0]);
+    load_a_rm(X, MLP_NIP, m0, 16, a1[1]);
+    uint32_t h1[4][4], h2[4][4];
+    dense_regs<2, 8>(a1, wb + MLPB_W1, bias + MLPF_B1, h1);
+    dense_regs<4, 8>(h1, wb + MLPB_W2, bias + MLPF_B2, h2);
+    dense_regs<4, 8>(h2, wb + MLPB_W3, bias + MLPF_B3, h1);
+    float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        uint32_t b[2];
+        load_b_nk(wb + MLPB_W4, MLP_NH, 16 * kk, 0, b);
+        mma_bf16(d, h1[kk], b);
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int r = m0 + frag_row(v), c = frag_col(v);
+        y[r * MLP_NOP + c] = d[v] + bias[MLPF_B4 + c];
+    }
+}
+
 // ---------------------------------------------------------------- features
 // 24 rotation-invariant features of (leaf L, cluster C) from their f32 node
 // records (A, X[3], nubar[3], M2/A[6], diag):

@@ -286,3 +286,31 @@ def test_full_size_properties(tp, ctx, oracle_mod):
     assert np.abs(grad.sum(0)).max() <= 1e-6 * scale
     assert np.abs(np.cross(V, grad).sum(0)).max() <= 1e-6 * scale
     assert abs(np.sum(V * grad) + 2 * e) <= 1e-5 * e
+
+
+@pytest.mark.parametrize("mesh", ["sphere3", "dish5"])
+def test_triangle_fields(tp, ctx, oracle_mod, mesh, request):
+    """tp_fields: per-triangle dPhi/dw, dPhi/dnu, dPhi/dx (caller's order, with the
+    prefactor) against the oracle's, in the FP32 and FP64 forms, host and device
+    outputs, and through the Barnes-Hut path at theta = 0 (no cluster admitted)."""
+    import torch
+
+    V, F, E, _ = request.getfixturevalue(mesh)
+    c = 0.37
+    gw, gnu, gx = oracle_mod.tri_accum(V, F)
+    gw, gnu, gx = c * gw, c * gnu, c * gx
+    tp.tp_mesh_upload(ctx, V, F)
+    e, fw, fnu, fx = tp.tp_fields(ctx, F.shape[0], tp.tp_params_default(scale=c))
+    assert abs(e - c * E) <= E_TOL * c * E
+    assert rel(fw, gw) <= G_TOL and rel(fnu, gnu) <= G_TOL and rel(fx, gx) <= G_TOL, (rel(fw, gw), rel(fnu, gnu),
+                                                                                   rel(fx, gx))
+    e, fw, fnu, fx = tp.tp_fields(ctx, F.shape[0], tp.tp_params_default(scale=c, prec=tp._tp.TP_F64))
+    assert rel(fw, gw) <= 1e-11 and rel(fnu, gnu) <= 1e-11 and rel(fx, gx) <= 1e-11
+    d = [torch.zeros(F.shape[0], dtype=torch.float64, device="cuda"),
+         torch.zeros((F.shape[0], 3), dtype=torch.float64, device="cuda"), None]
+    tp.tp_fields(ctx, F.shape[0], tp.tp_params_default(scale=c), fw=d[0], fnu=d[1])
+    torch.cuda.synchronize()
+    assert rel(d[0].cpu().numpy(), gw) <= G_TOL and rel(d[1].cpu().numpy(), gnu) <= G_TOL
+    tp.tp_tree_build(ctx, 16, 30)
+    e, fw, fnu, fx = tp.tp_fields(ctx, F.shape[0], tp.tp_params_default(scale=c, mode=tp.TP_BH, theta=0.0))
+    assert rel(fw, gw) <= G_TOL and rel(fnu, gnu) <= G_TOL and rel(fx, gx) <= G_TOL

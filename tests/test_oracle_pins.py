@@ -258,3 +258,42 @@ def test_coincident_centroids_infinite(oracle_mod):
     with np.errstate(all="ignore"):
         E = oracle_mod.energy_soa(x, nu, w, F)
     assert not np.isfinite(E) or E > 1e300
+
+
+# --------------------------------------------------------------- per-triangle fields
+def brute_energy_soa(x, nu, w, F, q=6, p=12):
+    """Separately written Eq. (TP) sum from per-triangle (x, nu, w) taken as free
+    variables (vertex-sharing exclusion from F); analytic in x, nu, w."""
+    sets = [set(int(v) for v in f) for f in np.asarray(F)]
+    nt = len(sets)
+    total = 0
+    for T in range(nt):
+        keep = np.array([S for S in range(nt) if S != T and not (sets[T] & sets[S])], dtype=np.int64)
+        d = x[T][None, :] - x[keep]
+        n = d @ nu[T]
+        r2 = np.sum(d * d, axis=1)
+        total = total + w[T] * np.sum(w[keep] * n**q / r2 ** (p // 2))
+    return total
+
+
+def test_triangle_fields_complex_step(oracle_mod):
+    """dPhi/dw_T, dPhi/dnu_T and dPhi/dx_T of the oracle (the one-point counterparts
+    of f_K, f_nu, f of Eq. (dTP_reordered)) against complex-step derivatives of an
+    independently written sum, with w, nu and x as independent variables."""
+    V, F = meshgen.sh_deformed_sphere(1, 12, 0.05, 7)
+    x, nu, w = oracle_mod.tri_data(V, F)
+    gw, gnu, gx = oracle_mod.tri_accum(V, F, soa=(x, nu, w))
+    h = 1e-30
+    for T in (0, 17, 43, 79):
+        wc = w.astype(np.complex128)
+        wc[T] += 1j * h
+        assert abs(brute_energy_soa(x, nu, wc, F).imag / h - gw[T]) <= 1e-12 * abs(gw[T])
+        for a in range(3):
+            nc = nu.astype(np.complex128)
+            nc[T, a] += 1j * h
+            ref = brute_energy_soa(x, nc, w, F).imag / h
+            assert abs(ref - gnu[T, a]) <= 1e-12 * np.linalg.norm(gnu[T]), (T, a, ref, gnu[T, a])
+            xc = x.astype(np.complex128)
+            xc[T, a] += 1j * h
+            ref = brute_energy_soa(xc, nu, w, F).imag / h
+            assert abs(ref - gx[T, a]) <= 1e-12 * np.linalg.norm(gx[T]), (T, a, ref, gx[T, a])
