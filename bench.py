@@ -40,6 +40,10 @@ UNIT = "pair-interactions/s"
 # its expression DAG with an FMA as 2 flops: 24 FMA + 28 FMUL/FADD = 76 flops
 # (the hi/lo cancellation correction and the reduction overhead not counted).
 FLOPS_PER_UNORDERED_PAIR = 76
+# The same count for one (target, confining triangle) pair of the confinement
+# energy+gradient (one ordering, target side only): 11 FMA + 16 FMUL/FADD = 38
+# flops (the hi/lo cancellation correction, 6 FADD, not counted).
+FLOPS_PER_CONF_PAIR = 38
 FP32_LANES_PER_SM = 128
 # DRAM bytes per launch of the dominant kernel from the committed ncu
 # capture (profiles/); None until a capture of the current kernel exists.
@@ -50,6 +54,8 @@ WORKLOADS = {
     "dish_l5": "icosphere level 5 (20,480 triangles) mapped to a double-walled dish, gap 0.02, jitter N(0,0.002^2)",
     "sh_l6_s2": "icosphere level 6 (81,920 triangles) with seeded SH deformation l<=12, a_lm~N(0,(0.05/l)^2), seed 2",
     "folds_l8": "icosphere level 8 (1,310,720 triangles) with 40 seeded radial folds of depth 0.1",
+    "conf_l7": "unit icosphere level 7 (327,680 triangles), radial jitter N(0,0.005^2), seed 13, inside the "
+               "concentric icosphere level 7 of radius 1.1 (327,680 confining triangles)",
 }
 
 
@@ -60,7 +66,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sh_l7", choices=sorted(WORKLOADS))
-    ap.add_argument("--mode", default="direct", choices=["direct", "bh", "learned"])
+    ap.add_argument("--mode", default="direct", choices=["direct", "bh", "learned", "conf"],
+                    help="conf: the confinement energy (Eq. TPConf) of the conf_l7 workload")
     ap.add_argument("--far-model", default=None, help="trained far-field model (learned mode)")
     ap.add_argument("--theta", type=float, default=0.25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -264,12 +271,105 @@ def inloop(args):
     return 0
 
 
+def conf_bench(args):
+    """Confinement energy + gradient of a sphere inside a confining sphere (one GPU)."""
+    import torch
+
+    import paper_2509_22110_gb300 as tp
+    from paper_2509_22110_gb300 import _tp, build as _b, meshgen
+
+    _b.build()
+    V, F, Vc, Fc = meshgen.sphere_in_sphere(7, 1.1, 0.005, 13)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    ctx = tp.tp_create(0, stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        Vd = torch.tensor(V, device=dev)
+        Fd = torch.tensor(F, device=dev)
+        gd = torch.zeros_like(Vd)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream.synchronize()
+    tp.tp_mesh_upload(ctx, Vd, Fd)
+    tp.tp_conf_upload(ctx, Vc, Fc)
+    prm = tp.tp_params_default()
+    launches, kern_ms = [0], []
+
+    def step():
+        tp.tp_mesh_upload(ctx, Vd, None, flags=_tp.TP_POSITIONS_ONLY)
+        launches[0] += tp.tp_get_stats(ctx)["kernel_launches"]
+        e = tp.tp_conf_gradient(ctx, gd, prm)
+        st = tp.tp_get_stats(ctx)
+        launches[0] += st["kernel_launches"]
+        kern_ms.append(st["ms_kernel"])
+        return e, st
+
+    for _ in range(args.warmup):
+        step()
+    launches[0] = 0
+    kern_ms.clear()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(0)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+        starts[k].record(stream)
+        energy, st = step()
+        ends[k].record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    pairs = st["pairs_exact"]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = float(measured_peaks().get("sm_max_mhz", 2070.0))
+    peak = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    kms = statistics.mean(kern_ms)
+    achieved = FLOPS_PER_CONF_PAIR * pairs / (kms / 1e3) / 1e12
+    line = {"metric": "TP confinement energy+grad pair-interactions/s (Eq. TPConf)", "value": args.steps * pairs /
+            (total_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (seeded meshes)",
+            "config": {"workload": WORKLOADS["conf_l7"], "nt": int(F.shape[0]), "nt_conf": int(Fc.shape[0]),
+                       "q": 6, "p": 12, "accumulation": "f64",
+                       "l2": "flushed (256 MB write) before every timed step", "parallelism": "single GPU"},
+            "energy": energy, "gpu_launches": launches[0], "clocks": clk,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_conf_grad<6>", "kernel_ms": kms,
+                         "flops_per_pair": FLOPS_PER_CONF_PAIR, "pairs_per_launch": pairs,
+                         "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz"}}
+    if not args.no_accuracy:
+        g64 = torch.zeros_like(Vd)
+        e64 = tp.tp_conf_gradient(ctx, g64, tp.tp_params_default(prec=tp.TP_F64))
+        line["accuracy"] = {"energy_rel_err_vs_f64": abs(energy - e64) / abs(e64),
+                            "grad_rel_l2_vs_f64": float(torch.linalg.norm(gd - g64) / torch.linalg.norm(g64))}
+    if not args.no_e2e:
+        Vh = torch.tensor(V).pin_memory()
+        gh = torch.zeros(V.shape, dtype=torch.float64).pin_memory()
+        tp.tp_mesh_upload(ctx, Vh, None, flags=_tp.TP_POSITIONS_ONLY)
+        tp.tp_conf_gradient(ctx, gh, prm)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            tp.tp_mesh_upload(ctx, Vh, None, flags=_tp.TP_POSITIONS_ONLY)
+            tp.tp_conf_gradient(ctx, gh, prm)
+        torch.cuda.synchronize(dev)
+        line["e2e"] = {"value": args.steps * pairs / (time.perf_counter() - t0), "unit": UNIT,
+                       "h2d_bytes_per_step": int(Vh.numel() * 8), "d2h_bytes_per_step": int(gh.numel() * 8 + 8)}
+    tp.tp_destroy(ctx)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
     if args.inloop:
         return inloop(args)
+    if args.mode == "conf":
+        return conf_bench(args)
     import torch
     import torch.distributed as tdist
 

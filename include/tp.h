@@ -123,6 +123,28 @@ tp_status tp_gradient(tp_ctx* ctx, const tp_params* params, double* energy_out, 
 tp_status tp_fields(tp_ctx* ctx, const tp_params* params, double* energy_out, double* fw, double* fnu, double* fx,
                     uint32_t flags);
 
+/* Upload the fixed confining surface S_conf of the confinement energy,
+ * Eq. (TPConf), Sec. 2.2 (Confinement): vertices V[nv][3] (v_dtype f32/f64)
+ * and faces F[nt][3], host memory or device memory with TP_DEVICE_PTR; the
+ * library copies them.  Only the centroids and areas of its triangles enter
+ * (its normal never does, so orientation does not matter and the surface may
+ * be non-smooth).  Face indices outside [0, nv) give TP_E_ARG, non-finite
+ * coordinates TP_E_NONFINITE.  It stays until the next tp_conf_upload and is
+ * independent of tp_mesh_upload. */
+tp_status tp_conf_upload(tp_ctx* ctx, const void* V, int64_t nv, int v_dtype, const int32_t* F, int64_t nt,
+                         uint32_t flags);
+
+/* Confinement energy of the uploaded (evolving) mesh S against S_conf,
+ *   Phi_conf = c sum_{T in S} sum_{K in S_conf} w_T a_K |nu_T.(x_T - y_K)|^q / |x_T - y_K|^p
+ * (one centroid point per flat triangle on both surfaces; c = rho_conf/alpha is
+ * params->scale), and optionally its gradient with respect to the vertices of
+ * S (S_conf does not move): grad_out as in tp_gradient, or NULL for the energy
+ * only.  params->mode must be TP_DIRECT; prec TP_F32_F64ACC (FP32 pair terms,
+ * FP64 accumulation) or TP_F64.  Touching surfaces give TP_E_NONFINITE with
+ * energy +inf; no confining surface gives TP_E_STATE. */
+tp_status tp_conf_gradient(tp_ctx* ctx, const tp_params* params, double* energy_out, void* grad_out, int g_dtype,
+                           uint32_t flags);
+
 /* Load the far-field network used by TP_LEARNED from a file written by
  * tp_far_model_save: header {"TPFM", version 1, 24, 64, 7, nparam, theta,
  * q, p, step}, then the feature mean/std/min/max [4][24] f32 and the FP32

@@ -362,3 +362,12 @@ def conf_gradient(V, F, Vc, Fc, q=6.0, p=12.0, c=1.0, nthreads=None):
     E = conf_energy(V, F, Vc, Fc, q, p, c, soa=(x, nu, w), conf=conf, nthreads=nthreads)
     gw, gnu, gx = conf_accum(V, F, Vc, Fc, q, p, soa=(x, nu, w), conf=conf, nthreads=nthreads)
     return E, adjoint(V, F, gw, gnu, gx, c)
+
+
+def conf_vertex_gradient_sample(V, F, Vc, Fc, verts, q=6.0, p=12.0, c=1.0, nthreads=None):
+    """Exact dPhi_conf/dv for the listed vertices of the evolving surface only."""
+    tris = incident_triangles(F, verts)
+    x, nu, w = tri_data(V, F)
+    gw, gnu, gx = conf_accum(V, F, Vc, Fc, q, p, soa=(x[tris], nu[tris], w[tris]), nthreads=nthreads)
+    grad = adjoint(V, F, gw, gnu, gx, c, tris=tris)
+    return grad[np.asarray(verts)]

@@ -23,6 +23,8 @@ from ._tp import (  # noqa: F401
     TP_F64,
     TP_LEARNED,
     TPError,
+    tp_conf_gradient,
+    tp_conf_upload,
     tp_create,
     tp_debug_accum,
     tp_debug_tree,
@@ -42,6 +44,8 @@ from ._tp import (  # noqa: F401
 
 __all__ = [
     "TPEnergy",
+    "tp_conf_upload",
+    "tp_conf_gradient",
     "TangentPointEnergy",
     "tp_create",
     "tp_destroy",

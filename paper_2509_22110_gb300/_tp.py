@@ -79,6 +79,10 @@ def lib():
     L.tp_gradient.restype = i32
     L.tp_fields.argtypes = [vp, C.POINTER(tp_params), C.POINTER(C.c_double), vp, vp, vp, u32]
     L.tp_fields.restype = i32
+    L.tp_conf_upload.argtypes = [vp, vp, i64, i32, vp, i64, u32]
+    L.tp_conf_upload.restype = i32
+    L.tp_conf_gradient.argtypes = [vp, C.POINTER(tp_params), C.POINTER(C.c_double), vp, i32, u32]
+    L.tp_conf_gradient.restype = i32
     L.tp_far_model_load.argtypes = [vp, C.c_char_p]
     L.tp_far_model_load.restype = i32
     L.tp_get_stats.argtypes = [vp, C.POINTER(tp_stats)]
@@ -236,6 +240,30 @@ def tp_fields(ctx, nt, params=None, fw=None, fnu=None, fx=None):
     _check(ctx, lib().tp_fields(ctx, C.byref(p), C.byref(e), _ptr(fw)[0], _ptr(fnu)[0], _ptr(fx)[0],
                                 TP_DEVICE_PTR if dev else 0))
     return e.value, fw, fnu, fx
+
+
+def tp_conf_upload(ctx, V, F):
+    """Upload the fixed confining surface (numpy arrays or CUDA tensors; V f32/f64 [nv,3], F int32 [nt,3])."""
+    pv, dv = _ptr(V)
+    pf, df = _ptr(F)
+    if dv != df:
+        raise ValueError("V and F must both be on the host or both on the device")
+    vd = TP_DTYPE_F64 if str(V.dtype).endswith("float64") else TP_DTYPE_F32
+    _check(ctx, lib().tp_conf_upload(ctx, pv, V.shape[0], vd, pf, F.shape[0], TP_DEVICE_PTR if dv else 0))
+
+
+def tp_conf_gradient(ctx, grad_out=None, params=None):
+    """Confinement energy of the uploaded mesh against the confining surface; fills
+    ``grad_out`` ([nv,3] float32/float64, host numpy or CUDA tensor) when given."""
+    p = params or tp_params_default()
+    e = C.c_double(0.0)
+    if grad_out is None:
+        _check(ctx, lib().tp_conf_gradient(ctx, C.byref(p), C.byref(e), None, TP_DTYPE_F64, 0))
+    else:
+        pg, dg = _ptr(grad_out)
+        gd = TP_DTYPE_F64 if str(grad_out.dtype).endswith("float64") else TP_DTYPE_F32
+        _check(ctx, lib().tp_conf_gradient(ctx, C.byref(p), C.byref(e), pg, gd, TP_DEVICE_PTR if dg else 0))
+    return e.value
 
 
 def tp_far_model_load(ctx, path):

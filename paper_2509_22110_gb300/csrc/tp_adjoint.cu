@@ -170,6 +170,11 @@ tp_status tp_launch_energy_from_acc(tp_ctx* ctx, const tp_params* prm, double* d
     return reduce_strided(ctx, ctx->acc, ctx->ntp, 1, prm->scale / (2.0 * pq), d_out);
 }
 
+// mul * sum over triangles of the accumulator Ew
+tp_status tp_launch_energy_scaled(tp_ctx* ctx, double mul, double* d_out) {
+    return reduce_strided(ctx, ctx->acc, ctx->ntp, 1, mul, d_out);
+}
+
 tp_status tp_launch_reduce_sum(tp_ctx* ctx, const double* in, int64_t n, double* d_out) {
     return reduce_strided(ctx, in, n, 1, 1.0, d_out);
 }

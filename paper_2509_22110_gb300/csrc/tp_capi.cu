@@ -527,6 +527,113 @@ tp_status tp_fields(tp_ctx* ctx, const tp_params* params, double* energy_out, do
     return run_eval(ctx, params, true, nullptr, TP_DTYPE_F64, flags, energy_out, &fo);
 }
 
+tp_status tp_conf_upload(tp_ctx* ctx, const void* V, int64_t nv, int v_dtype, const int32_t* F, int64_t nt,
+                         uint32_t flags) {
+    if (!ctx) return TP_E_ARG;
+    DeviceGuard g(ctx->device);
+    ctx->err.clear();
+    ctx->nlaunch = 0;
+    const bool dev = flags & TP_DEVICE_PTR;
+    if (v_dtype != TP_DTYPE_F32 && v_dtype != TP_DTYPE_F64) return tp_set_err(ctx, TP_E_ARG, "bad v_dtype %d", v_dtype);
+    if (nv < 0 || nt < 0) return tp_set_err(ctx, TP_E_ARG, "negative size");
+    if (nt >= (int64_t)1 << 30 || nv >= (int64_t)1 << 30) return tp_set_err(ctx, TP_E_ARG, "mesh too large");
+    if ((nv > 0 && !V) || (nt > 0 && !F)) return tp_set_err(ctx, TP_E_ARG, "V or F is NULL");
+    ctx->have_conf = false;
+    const int64_t ntp = ((nt + TP_SUPER - 1) / TP_SUPER) * TP_SUPER;
+    if (nv > ctx->conf_cap_nv || nt > ctx->conf_cap_nt || !ctx->conf_src) {
+        free_ptr(ctx, ctx->conf_V64);
+        free_ptr(ctx, ctx->conf_F);
+        free_ptr(ctx, ctx->conf_vtmp);
+        free_ptr(ctx, ctx->conf_y64);
+        free_ptr(ctx, ctx->conf_a64);
+        free_ptr(ctx, ctx->conf_src);
+        const int64_t cnv = std::max<int64_t>(nv, 1), cnt = std::max<int64_t>(nt, 1);
+        const int64_t cntp = std::max<int64_t>(ntp, TP_SUPER);
+        TP_TRY(tp_alloc_t(ctx, &ctx->conf_V64, 3 * cnv));
+        TP_TRY(tp_alloc_t(ctx, &ctx->conf_F, 3 * cnt));
+        TP_TRY(tp_alloc_t(ctx, &ctx->conf_vtmp, 3 * cnv));
+        TP_TRY(tp_alloc_t(ctx, &ctx->conf_y64, 3 * cnt));
+        TP_TRY(tp_alloc_t(ctx, &ctx->conf_a64, cnt));
+        TP_TRY(tp_alloc_t(ctx, &ctx->conf_src, (int64_t)TP_SRCW * cntp));
+        ctx->conf_cap_nv = cnv;
+        ctx->conf_cap_nt = cnt;
+    }
+    ctx->conf_nv = nv;
+    ctx->conf_nt = nt;
+    ctx->conf_ntp = ntp;
+    const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (nv > 0) {
+        if (v_dtype == TP_DTYPE_F64) {
+            TP_CU(cudaMemcpyAsync(ctx->conf_V64, V, 24 * nv, kind, ctx->stream));
+        } else {
+            TP_CU(cudaMemcpyAsync(ctx->conf_vtmp, V, 12 * nv, kind, ctx->stream));
+            k_f32_to_f64<<<(unsigned)((3 * nv + 255) / 256), 256, 0, ctx->stream>>>(ctx->conf_vtmp, ctx->conf_V64,
+                                                                                  3 * nv);
+            ++ctx->nlaunch;
+        }
+    }
+    if (nt > 0) {
+        TP_CU(cudaMemcpyAsync(ctx->conf_F, F, 12 * nt, kind, ctx->stream));
+        TP_TRY(tp_launch_conf_tri(ctx));
+    }
+    TP_TRY(take_device_error(ctx, "tp_conf_upload"));
+    ctx->have_conf = true;
+    return TP_OK;
+}
+
+tp_status tp_conf_gradient(tp_ctx* ctx, const tp_params* params, double* energy_out, void* grad_out, int g_dtype,
+                           uint32_t flags) {
+    if (!ctx) return TP_E_ARG;
+    DeviceGuard g(ctx->device);
+    ctx->err.clear();
+    const tp_params* prm = params;
+    TP_TRY(check_params(ctx, prm));
+    if (prm->mode != TP_DIRECT) return tp_set_err(ctx, TP_E_ARG, "the confinement energy is evaluated directly");
+    if (!ctx->have_conf) return tp_set_err(ctx, TP_E_STATE, "no confining surface uploaded (tp_conf_upload)");
+    const bool want_grad = grad_out != nullptr;
+    if (want_grad && g_dtype != TP_DTYPE_F32 && g_dtype != TP_DTYPE_F64)
+        return tp_set_err(ctx, TP_E_ARG, "bad g_dtype %d", g_dtype);
+    const int64_t nt = ctx->nt, nv = ctx->nv;
+    const bool dev = flags & TP_DEVICE_PTR;
+    const size_t gbytes = (size_t)(3 * nv) * (g_dtype == TP_DTYPE_F64 ? 8 : 4);
+    ctx->stats = tp_stats{};
+    ctx->stats.nt = nt;
+    ctx->stats.nv = nv;
+    ctx->nlaunch = 0;
+    if (nt == 0 || ctx->conf_nt == 0) {
+        if (energy_out) *energy_out = 0.0;
+        if (want_grad && nv > 0) {
+            if (dev) TP_CU(cudaMemsetAsync(grad_out, 0, gbytes, ctx->stream));
+            else memset(grad_out, 0, gbytes);
+            TP_CU(cudaStreamSynchronize(ctx->stream));
+        }
+        return TP_OK;
+    }
+    cudaEventRecord(ctx->ev[2], ctx->stream);
+    TP_TRY(tp_launch_conf(ctx, prm));
+    const double pq = (double)prm->p / prm->q;
+    TP_TRY(tp_launch_energy_scaled(ctx, prm->scale / pq, ctx->scalar));
+    if (want_grad) TP_TRY(tp_launch_adjoint(ctx, prm, dev ? grad_out : (void*)ctx->gradbuf, g_dtype));
+    cudaEventRecord(ctx->ev[3], ctx->stream);
+    double e = 0.0;
+    TP_CU(cudaMemcpyAsync(&e, ctx->scalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (want_grad && !dev && nv > 0)
+        TP_CU(cudaMemcpyAsync(grad_out, ctx->gradbuf, gbytes, cudaMemcpyDeviceToHost, ctx->stream));
+    TP_CU(cudaStreamSynchronize(ctx->stream));
+    TP_TRY(take_device_error(ctx, "tp_conf_gradient"));
+    ctx->stats.pairs_exact = nt * ctx->conf_nt;
+    ctx->stats.kernel_pairs = nt * ctx->conf_nt;
+    ctx->stats.ms_kernel = elapsed(ctx->ev[0], ctx->ev[1]);
+    ctx->stats.ms_total = elapsed(ctx->ev[2], ctx->ev[3]);
+    ctx->stats.kernel_launches = ctx->nlaunch;
+    if (energy_out) *energy_out = e;
+    if (!std::isfinite(e)) {
+        if (energy_out) *energy_out = INFINITY;
+        return tp_set_err(ctx, TP_E_NONFINITE, "confinement energy is not finite: the surfaces touch");
+    }
+    return TP_OK;
+}
+
 tp_status tp_get_stats(const tp_ctx* ctx, tp_stats* out) {
     if (!ctx || !out) return TP_E_ARG;
     *out = ctx->stats;

@@ -493,10 +493,25 @@ __device__ __forceinline__ void src_step_pp(const TgtPair (&tp)[NP], Acc8 (&at)[
     for (int k = 0; k < 8; ++k) vprev[k] = as.v[k].x + as.v[k].y;
 }
 
+// Fold the FP32 energy partials of the targets into FP64.  A target's energy
+// terms can span many orders of magnitude (the nearest sources dominate), and
+// a long FP32 running sum drops the small terms that follow a large one, so
+// the FP32 partials cover at most 32 sources (or one chunk) before the fold.
+template <int NP>
+__device__ __forceinline__ void fold_energy(Acc8 (&at)[NP], double (&e64)[NP][2]) {
+#pragma unroll
+    for (int P = 0; P < NP; ++P) {
+        e64[P][0] += (double)at[P].v[0].x;
+        e64[P][1] += (double)at[P].v[0].y;
+        at[P].v[0] = make_float2(0.f, 0.f);
+    }
+}
+
 // The 12 chunks of one item for one item kind; target partials in `at`.
 template <int Q, int KIND, int W, int NP, int PF>
 __device__ __forceinline__ bool grad_item(const DirectArgs& A, ChunkPipe& pipe, float* sacc, int I, int J,
-                                          const TgtPair (&tp)[NP], Acc8 (&at)[NP], int warp, int lane, int pbase) {
+                                          const TgtPair (&tp)[NP], Acc8 (&at)[NP], double (&e64)[NP][2], int warp,
+                                          int lane, int pbase) {
     constexpr bool LO = KIND != K_FAST;
     const int64_t ntp = A.ntp;
     int3 tf[NP][2];
@@ -557,6 +572,7 @@ __device__ __forceinline__ bool grad_item(const DirectArgs& A, ChunkPipe& pipe, 
                 const float r = warp_transpose_reduce8(v, lane);
                 if ((lane & 3) == 0) wacc[s * TP_NACC + ((lane >> 2) & 7)] = r;
             }
+            fold_energy<NP>(at, e64);
         } else if (!skip) {
             // two sources per trip with alternating record registers: the next
             // source's record is loaded while the current one is evaluated
@@ -575,6 +591,7 @@ __device__ __forceinline__ bool grad_item(const DirectArgs& A, ChunkPipe& pipe, 
                                          wacc + (s - 1) * TP_NACC, lane);
                 src_step_pp<Q, KU, NP>(tp, at, rb, pb, ra, pa, cb + (s + 2) * TP_SRCW, s + 2 < TP_CHUNK, true,
                                          vprev, wacc + s * TP_NACC, lane);
+                if ((s & 30) == 30) fold_energy<NP>(at, e64);
             }
             } else if constexpr (PF == 1) {
             load_src<LOU>(cb, ra);
@@ -584,6 +601,7 @@ __device__ __forceinline__ bool grad_item(const DirectArgs& A, ChunkPipe& pipe, 
                                       wacc + (s - 1) * TP_NACC, lane);
                 src_step<Q, KU, NP>(tp, at, rb, ra, cb + (s + 2) * TP_SRCW, s + 2 < TP_CHUNK, true, vprev,
                                       wacc + s * TP_NACC, lane);
+                if ((s & 30) == 30) fold_energy<NP>(at, e64);
             }
             } else {
 #pragma unroll 1
@@ -591,6 +609,7 @@ __device__ __forceinline__ bool grad_item(const DirectArgs& A, ChunkPipe& pipe, 
                 load_src<LOU>(cb + s * TP_SRCW, ra);
                 src_step<Q, KU, NP>(tp, at, ra, rb, nullptr, false, s > 0, vprev, wacc + (s - 1) * TP_NACC,
                                       lane);
+                if ((s & 31) == 31) fold_energy<NP>(at, e64);
             }
             }
             const float r = warp_transpose_reduce8(vprev, lane);
@@ -656,27 +675,33 @@ __global__ void __launch_bounds__(GradShape<MASKQ>::THREADS, 1) k_pairs_grad(Dir
                 load_tgt<true>(A.soa, ntp, (int64_t)it.I * TP_SUPER + 2 * (pbase + 32 * P), tp[P]);
         }
         Acc8 at[NP];
+        double e64[NP][2];
 #pragma unroll
-        for (int P = 0; P < NP; ++P)
+        for (int P = 0; P < NP; ++P) {
+            e64[P][0] = e64[P][1] = 0.0;
 #pragma unroll
             for (int c = 0; c < TP_NACC; ++c) at[P].v[c] = make_float2(0.f, 0.f);
+        }
         bool ok;
         if constexpr (MASKQ) {
-            ok = grad_item<Q, K_MASKED, W, NP, GradShape<MASKQ>::PF>(A, pipe, sacc, it.I, it.J, tp, at, warp, lane, pbase);
+            ok = grad_item<Q, K_MASKED, W, NP, GradShape<MASKQ>::PF>(A, pipe, sacc, it.I, it.J, tp, at, e64, warp, lane, pbase);
         } else {
-            if (it.kind == K_FAST) ok = grad_item<Q, K_FAST, W, NP, GradShape<MASKQ>::PF>(A, pipe, sacc, it.I, it.J, tp, at, warp, lane, pbase);
-            else ok = grad_item<Q, K_PRECISE, W, NP, GradShape<MASKQ>::PF>(A, pipe, sacc, it.I, it.J, tp, at, warp, lane, pbase);
+            if (it.kind == K_FAST) ok = grad_item<Q, K_FAST, W, NP, GradShape<MASKQ>::PF>(A, pipe, sacc, it.I, it.J, tp, at, e64, warp, lane, pbase);
+            else ok = grad_item<Q, K_PRECISE, W, NP, GradShape<MASKQ>::PF>(A, pipe, sacc, it.I, it.J, tp, at, e64, warp, lane, pbase);
         }
         if (!ok) {
             if (tid == 0) tp_dev_error(A.derr, TP_DERR_TIMEOUT);
             return;
         }
-        // promote the item's FP32 target partials to FP64
+        // promote the item's target partials to FP64 (the energy already folded)
+        fold_energy<NP>(at, e64);
 #pragma unroll
         for (int P = 0; P < NP; ++P) {
             const int64_t t0 = (int64_t)it.I * TP_SUPER + 2 * (pbase + 32 * P);
+            if (e64[P][0] != 0.0) atomicAdd(&A.acc[t0], e64[P][0]);
+            if (e64[P][1] != 0.0) atomicAdd(&A.acc[t0 + 1], e64[P][1]);
 #pragma unroll
-            for (int k = 0; k < TP_NACC; ++k) {
+            for (int k = 1; k < TP_NACC; ++k) {
                 if (at[P].v[k].x != 0.f) atomicAdd(&A.acc[k * ntp + t0], (double)at[P].v[k].x);
                 if (at[P].v[k].y != 0.f) atomicAdd(&A.acc[k * ntp + t0 + 1], (double)at[P].v[k].y);
             }
@@ -903,6 +928,237 @@ tp_status launch_energy_q(tp_ctx* ctx, DirectArgs A, int* nparts) {
     return TP_OK;
 }
 
+// ------------------------------------------------------------ confinement (Eq. TPConf)
+// Phi_conf = c sum_{T in S} sum_{K in S_conf} w_T a_K |nu_T.(x_T - y_K)|^q / |x_T - y_K|^p
+// (Sec. 2.2, Confinement): the target side of the pair kernel with only the
+// al^q ordering, because the confining surface's normal never enters and it
+// does not move.  With wts = w~_T w~_K (w~ = sqrt(p/q) area), inv = 1/|d|^2,
+// al = nu_T.d inv:
+//   Ew += wts al^q, U += A5 = wts inv al^(q-1), Gn += A5 d, Gx += -(p/q) wts inv al^q d,
+// the direct kernel's accumulator convention, so the same adjoint gives the
+// vertex gradient; Phi_conf = c sum_T Ew_T / (p/q).  No pair is excluded (the
+// surfaces share no vertex); d always takes the hi/lo parts.
+
+// FP64 centroid and area of each confining triangle (its normal is not needed)
+__global__ void k_conf_tri(const double* __restrict__ V, const int32_t* __restrict__ F, int64_t nt, int64_t nv,
+                           double* __restrict__ y64, double* __restrict__ a64, unsigned* derr) {
+    const int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (K >= nt) return;
+    const int32_t i0 = F[3 * K], i1 = F[3 * K + 1], i2 = F[3 * K + 2];
+    if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= nv || i1 >= nv || i2 >= nv) {
+        tp_dev_error(derr, TP_DERR_INDEX);
+        for (int a = 0; a < 3; ++a) y64[a * nt + K] = 0.0;
+        a64[K] = 0.0;
+        return;
+    }
+    const double *pa = V + 3 * (int64_t)i0, *pb = V + 3 * (int64_t)i1, *pc = V + 3 * (int64_t)i2;
+    double e1[3], e2[3];
+    for (int k = 0; k < 3; ++k) {
+        y64[k * nt + K] = __ddiv_rn(__dadd_rn(__dadd_rn(pa[k], pb[k]), pc[k]), 3.0);
+        e1[k] = __dsub_rn(pb[k], pa[k]);
+        e2[k] = __dsub_rn(pc[k], pa[k]);
+    }
+    const double N0 = e1[1] * e2[2] - e1[2] * e2[1], N1 = e1[2] * e2[0] - e1[0] * e2[2],
+                 N2 = e1[0] * e2[1] - e1[1] * e2[0];
+    const double area = 0.5 * sqrt(N0 * N0 + N1 * N1 + N2 * N2);
+    if (!isfinite(area) || !isfinite(y64[K]) || !isfinite(y64[nt + K]) || !isfinite(y64[2 * nt + K]))
+        tp_dev_error(derr, TP_DERR_NONFINITE);
+    a64[K] = area;
+}
+
+// staged source records (the direct kernel's layout, normal zero) relative to
+// the evolving mesh's centre; padding: zero area, far away
+__global__ void k_conf_records(const double* __restrict__ y64, const double* __restrict__ a64,
+                               const double* __restrict__ center, int64_t nt, int64_t ntp, float* __restrict__ src) {
+    const int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (K >= ntp) return;
+    float v[10];
+    if (K < nt) {
+        for (int a = 0; a < 3; ++a) {
+            const double yc = y64[a * nt + K] - center[a];
+            const float hi = (float)yc;
+            v[a] = hi;
+            v[3 + a] = (float)(yc - (double)hi);
+            v[6 + a] = 0.f;
+        }
+        v[9] = (float)(1.4142135623730951 * a64[K]);  // sqrt(p/q) a, p = 2q
+    } else {
+        v[0] = 8192.0f + 8.0f * (float)(K - nt);
+        v[1] = v[2] = 8192.0f;
+        for (int a = 3; a < 10; ++a) v[a] = 0.f;
+    }
+    for (int a = 0; a < 10; ++a) {
+        src[K * TP_SRCW + 2 * a] = v[a];
+        src[K * TP_SRCW + 2 * a + 1] = v[a];
+    }
+}
+
+// centroid hi/lo and weight of a staged record (the normal is not read)
+__device__ __forceinline__ void load_src_pos(const float* rec, SrcRec& s) {
+    const float4* r = reinterpret_cast<const float4*>(rec);
+    const float4 a = r[0], b = r[1], c = r[2], e = r[4];
+    s.h[0] = make_float2(a.x, a.y);
+    s.h[1] = make_float2(a.z, a.w);
+    s.h[2] = make_float2(b.x, b.y);
+    s.l[0] = make_float2(b.z, b.w);
+    s.l[1] = make_float2(c.x, c.y);
+    s.l[2] = make_float2(c.z, c.w);
+    s.w = make_float2(e.z, e.w);
+}
+
+template <int Q>
+__device__ __forceinline__ void conf_pair(const TgtPair& t, const SrcRec& s, Acc8& at) {
+    float2 d[3];
+    pair_diff<true>(t, s, d);
+    float2 r2 = mul2(d[0], d[0]);
+    r2 = fma2(d[1], d[1], r2);
+    r2 = fma2(d[2], d[2], r2);
+    const float2 inv = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+    const float2 wts = mul2(t.w, s.w);
+    float2 a = mul2(t.n[0], d[0]);
+    a = fma2(t.n[1], d[1], a);
+    a = fma2(t.n[2], d[2], a);
+    const float2 al = mul2(a, inv);
+    float2 alq;
+    const float2 al5 = powq_m1<Q>(al, alq);
+    const float2 wi = mul2(wts, inv);
+    const float2 A5 = mul2(wi, al5);
+    const float2 nk = mul2(mul2(wi, alq), f2(-2.0f));  // -(p/q) wts inv al^q, p = 2q
+    at.v[0] = fma2(wts, alq, at.v[0]);
+    at.v[1] = add2(at.v[1], A5);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        at.v[2 + k] = fma2(A5, d[k], at.v[2 + k]);
+        at.v[5 + k] = fma2(nk, d[k], at.v[5 + k]);
+    }
+}
+
+// Persistent: items (target super-tile I, confining super-tile J) for all I, J,
+// from a dynamic queue; block shape of the precise/fast gradient kernel.
+template <int Q>
+__global__ void __launch_bounds__(GradShape<false>::THREADS, 1) k_conf_grad(DirectArgs A) {
+    constexpr int NP = GradShape<false>::NP;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float* chunk = reinterpret_cast<float*>(smem);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * CHUNK_BYTES);
+    int* s_item = reinterpret_cast<int*>(smem + 2 * CHUNK_BYTES + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t ntp = A.ntp;
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    ChunkPipe pipe;
+    pipe.chunk = chunk;
+    pipe.mbar = mbar;
+    pipe.phases = 0u;
+    TgtPair tp[NP];
+    int rowI = -1;
+    const int pbase = warp * 32 * NP + lane;
+    const unsigned nitems = (unsigned)A.nf;  // nsup x nsup_conf
+    while (true) {
+        if (tid == 0) {
+            const unsigned w = atomicAdd(A.work, 1u);
+            s_item[0] = w < nitems ? (int)(w / (unsigned)A.np) : -1;
+            s_item[1] = w < nitems ? (int)(w % (unsigned)A.np) : 0;
+        }
+        __syncthreads();
+        const int I = s_item[0], J = s_item[1];
+        __syncthreads();
+        if (I < 0) break;
+        if (tid == 0) pipe.issue(A, J, 0, 0);
+        if (I != rowI) {
+            rowI = I;
+#pragma unroll
+            for (int P = 0; P < NP; ++P) load_tgt<true>(A.soa, ntp, (int64_t)I * TP_SUPER + 2 * (pbase + 32 * P), tp[P]);
+        }
+        Acc8 at[NP];
+        double e64[NP][2];
+#pragma unroll
+        for (int P = 0; P < NP; ++P) {
+            e64[P][0] = e64[P][1] = 0.0;
+#pragma unroll
+            for (int k = 0; k < TP_NACC; ++k) at[P].v[k] = make_float2(0.f, 0.f);
+        }
+        for (int c = 0; c < NCHUNK; ++c) {
+            const float* cb;
+            if (!pipe.acquire(A, J, c, cb)) {
+                if (tid == 0) tp_dev_error(A.derr, TP_DERR_TIMEOUT);
+                return;
+            }
+            SrcRec ra, rb;
+            load_src_pos(cb, ra);
+#pragma unroll 1
+            for (int s = 0; s < TP_CHUNK; s += 2) {
+                load_src_pos(cb + (s + 1) * TP_SRCW, rb);
+#pragma unroll
+                for (int P = 0; P < NP; ++P) conf_pair<Q>(tp[P], ra, at[P]);
+                if (s + 2 < TP_CHUNK) load_src_pos(cb + (s + 2) * TP_SRCW, ra);
+#pragma unroll
+                for (int P = 0; P < NP; ++P) conf_pair<Q>(tp[P], rb, at[P]);
+                if ((s & 30) == 30) fold_energy<NP>(at, e64);
+            }
+        }
+#pragma unroll
+        for (int P = 0; P < NP; ++P) {
+            const int64_t t0 = (int64_t)I * TP_SUPER + 2 * (pbase + 32 * P);
+            if (e64[P][0] != 0.0) atomicAdd(&A.acc[t0], e64[P][0]);
+            if (e64[P][1] != 0.0) atomicAdd(&A.acc[t0 + 1], e64[P][1]);
+#pragma unroll
+            for (int k = 1; k < TP_NACC; ++k) {
+                if (at[P].v[k].x != 0.f) atomicAdd(&A.acc[k * ntp + t0], (double)at[P].v[k].x);
+                if (at[P].v[k].y != 0.f) atomicAdd(&A.acc[k * ntp + t0 + 1], (double)at[P].v[k].y);
+            }
+        }
+    }
+}
+
+// FP64 reference form: one thread per target (library order), every confining
+// triangle, FP64 arithmetic; same accumulator convention.
+template <int Q>
+__global__ void k_conf_f64(const double* __restrict__ x64, const double* __restrict__ nu64,
+                           const double* __restrict__ w64, const int32_t* __restrict__ perm,
+                           const double* __restrict__ y64, const double* __restrict__ a64, int64_t nt, int64_t nk,
+                           int64_t ntp, double* __restrict__ acc) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= nt) return;
+    const int64_t T = perm[k];
+    double xt[3], nt3[3];
+    for (int a = 0; a < 3; ++a) {
+        xt[a] = x64[a * nt + T];
+        nt3[a] = nu64[a * nt + T];
+    }
+    const double wt = w64[T];
+    double Ew = 0, U = 0, Gn[3] = {0, 0, 0}, Gx[3] = {0, 0, 0};
+    for (int64_t K = 0; K < nk; ++K) {
+        double d[3], r2 = 0, a = 0;
+        for (int c = 0; c < 3; ++c) {
+            d[c] = xt[c] - y64[c * nk + K];
+            r2 += d[c] * d[c];
+            a += nt3[c] * d[c];
+        }
+        const double inv = 1.0 / r2, al = a * inv, al2 = al * al;
+        const double alq = Q == 6 ? al2 * al2 * al2 : al2 * al2 * al2 * al2;
+        const double al5 = Q == 6 ? al2 * al2 * al : al2 * al2 * al2 * al;
+        const double wts = 2.0 * wt * a64[K];  // (p/q) w_T a_K
+        const double wi = wts * inv, A5 = wi * al5, kk = 2.0 * wi * alq;
+        Ew += wts * alq;
+        U += A5;
+        for (int c = 0; c < 3; ++c) {
+            Gn[c] += A5 * d[c];
+            Gx[c] -= kk * d[c];
+        }
+    }
+    acc[0 * ntp + k] = Ew;
+    acc[1 * ntp + k] = U;
+    for (int c = 0; c < 3; ++c) {
+        acc[(2 + c) * ntp + k] = Gn[c];
+        acc[(5 + c) * ntp + k] = Gx[c];
+    }
+}
+
 DirectArgs make_args(tp_ctx* ctx, const tp_params* prm) {
     DirectArgs A;
     A.soa = ctx->soa;
@@ -932,6 +1188,60 @@ tp_status tp_launch_direct_grad(tp_ctx* ctx, const tp_params* prm) {
     DirectArgs A = make_args(ctx, prm);
     if (prm->q == 6) return launch_grad_q<6>(ctx, A);
     return launch_grad_q<8>(ctx, A);
+}
+
+tp_status tp_launch_conf_tri(tp_ctx* ctx) {
+    k_conf_tri<<<(unsigned)((ctx->conf_nt + 255) / 256), 256, 0, ctx->stream>>>(
+        ctx->conf_V64, ctx->conf_F, ctx->conf_nt, ctx->conf_nv, ctx->conf_y64, ctx->conf_a64, ctx->derr);
+    ++ctx->nlaunch;
+    TP_CU(cudaGetLastError());
+    return TP_OK;
+}
+
+// Confinement accumulators of the evolving mesh's triangles (library order)
+// into ctx->acc; the pair launch is bracketed by ev[0] / ev[1].
+tp_status tp_launch_conf(tp_ctx* ctx, const tp_params* prm) {
+    TP_CU(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * TP_NACC * ctx->ntp, ctx->stream));
+    if (prm->prec == TP_F64) {
+        cudaEventRecord(ctx->ev[0], ctx->stream);
+        const unsigned b = (unsigned)((ctx->nt + 127) / 128);
+        if (prm->q == 6)
+            k_conf_f64<6><<<b, 128, 0, ctx->stream>>>(ctx->x64, ctx->nu64, ctx->w64, ctx->perm, ctx->conf_y64,
+                                                       ctx->conf_a64, ctx->nt, ctx->conf_nt, ctx->ntp, ctx->acc);
+        else
+            k_conf_f64<8><<<b, 128, 0, ctx->stream>>>(ctx->x64, ctx->nu64, ctx->w64, ctx->perm, ctx->conf_y64,
+                                                       ctx->conf_a64, ctx->nt, ctx->conf_nt, ctx->ntp, ctx->acc);
+        ++ctx->nlaunch;
+        cudaEventRecord(ctx->ev[1], ctx->stream);
+        TP_CU(cudaGetLastError());
+        return TP_OK;
+    }
+    k_conf_records<<<(unsigned)((ctx->conf_ntp + 255) / 256), 256, 0, ctx->stream>>>(
+        ctx->conf_y64, ctx->conf_a64, ctx->center, ctx->conf_nt, ctx->conf_ntp, ctx->conf_src);
+    ++ctx->nlaunch;
+    static bool attr = false;
+    constexpr int SMEM = 2 * CHUNK_BYTES + 64;
+    if (!attr) {
+        cudaFuncSetAttribute(k_conf_grad<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        cudaFuncSetAttribute(k_conf_grad<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        attr = true;
+    }
+    DirectArgs A = make_args(ctx, prm);
+    A.src = ctx->conf_src;
+    const int64_t nsupc = ctx->conf_ntp / TP_SUPER;
+    A.np = (int)nsupc;
+    A.nf = (int)(ctx->nsup * nsupc);
+    TP_CU(cudaMemsetAsync(ctx->work, 0, sizeof(unsigned), ctx->stream));
+    const int grid = (int)std::min<int64_t>(ctx->num_sms, ctx->nsup * nsupc);
+    cudaEventRecord(ctx->ev[0], ctx->stream);
+    if (prm->q == 6)
+        k_conf_grad<6><<<grid, GradShape<false>::THREADS, SMEM, ctx->stream>>>(A);
+    else
+        k_conf_grad<8><<<grid, GradShape<false>::THREADS, SMEM, ctx->stream>>>(A);
+    ++ctx->nlaunch;
+    cudaEventRecord(ctx->ev[1], ctx->stream);
+    TP_CU(cudaGetLastError());
+    return TP_OK;
 }
 
 tp_status tp_launch_direct_energy(tp_ctx* ctx, const tp_params* prm, double* partials, int* nparts) {

@@ -132,6 +132,15 @@ struct tp_ctx {
     int64_t nlaunch = 0;            // library kernels launched in the current call
     tp_tree tree;
     tp_mlp_model* mlp = nullptr;
+    // fixed confining surface of the confinement energy (Eq. TPConf)
+    bool have_conf = false;
+    int64_t conf_nv = 0, conf_nt = 0, conf_ntp = 0, conf_cap_nv = 0, conf_cap_nt = 0;
+    double* conf_V64 = nullptr;  // [nv][3]
+    int32_t* conf_F = nullptr;   // [nt][3]
+    float* conf_vtmp = nullptr;  // [3nv] f32 staging
+    double* conf_y64 = nullptr;  // [3][nt] centroids
+    double* conf_a64 = nullptr;  // [nt] areas
+    float* conf_src = nullptr;   // [ntp][TP_SRCW] records relative to the evolving mesh's centre
     // far (leaf, cluster) pairs listed by the Barnes-Hut pass for the learned correction
     int32_t* far_list = nullptr;
     tp_far_run* far_runs = nullptr;
@@ -173,6 +182,9 @@ tp_status tp_launch_morton_order(tp_ctx* ctx, int morton_bits);
 tp_status tp_launch_sorted_soa(tp_ctx* ctx);
 tp_status tp_launch_flagged(tp_ctx* ctx, bool topology);
 tp_status tp_launch_fields(tp_ctx* ctx, const tp_params* prm, double* fw, double* fnu, double* fx);
+tp_status tp_launch_conf_tri(tp_ctx* ctx);
+tp_status tp_launch_conf(tp_ctx* ctx, const tp_params* prm);
+tp_status tp_launch_energy_scaled(tp_ctx* ctx, double mul, double* d_out);
 tp_status tp_build_v2t(tp_ctx* ctx);
 tp_status tp_count_excluded(tp_ctx* ctx);
 // tp_direct.cu

@@ -291,6 +291,15 @@ def nested_spheres(level: int, gap: float):
     return V2, F2
 
 
+def sphere_in_sphere(level: int = 7, radius: float = 1.1, sigma: float = 0.005, seed: int = 13):
+    """Evolving sphere of radius 1 (radial jitter N(0, sigma^2)) and the concentric
+    confining icosphere of the given radius, both at the same subdivision level:
+    the setting of the sphere inversion in a spherical confinement (radius 1.1)."""
+    V, F = perturbed_sphere(level, sigma, seed)
+    Vc, Fc = icosphere(level)
+    return V, F, radius * Vc, Fc
+
+
 def mesh_hash(V, F) -> str:
     """SHA-256 over the little-endian bytes of V (float64) and F (int32)."""
     h = hashlib.sha256()
