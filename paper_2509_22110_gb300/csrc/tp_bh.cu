@@ -491,36 +491,98 @@ __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
 // ------------------------------------------------------------ learned correction
 // The far terms evaluated by the Barnes-Hut pass carry factor 1 in every
 // channel; the network's factors kf replace them, so each listed (leaf L,
-// cluster C) pair adds (kf - 1) x channel to the targets of L.  One warp per
-// run (up to 256 far nodes of one leaf): per 32 nodes the lanes build the
-// features of their (L, C) pair, the warp runs the network on the tensor
-// cores with activations in registers (two 16-row tiles), and the half-warps
-// sweep the nodes for the 16 targets.  Pairs outside the training ranges
-// keep factor 1 (no correction).  Runs of one leaf may be processed by
-// different warps at once, so the FP32 run sums are added to the FP64
-// accumulators atomically.
+// cluster C) pair adds (kf - 1) x channel to the targets of L.  Three passes
+// over the listed pairs:
+//   k_far_feat    - one warp per run: the 24 normalised features of every
+//                   (L, C) pair as a BF16 row (column 31 = 1 when the raw
+//                   features lie in the training ranges, else 0);
+//   k_mlp_rows    - the network on 32 rows per warp on the tensor cores
+//                   (mma.sync m16n8k16, BF16 operands, FP32 accumulation,
+//                   activations in registers, fragment-ordered weights in
+//                   shared memory): kf - 1 per channel (0 outside the ranges);
+//   k_far_correct - one warp per run: (kf - 1) x the far-term channels for
+//                   the 16 targets of the leaf; runs of one leaf may be in
+//                   flight in different warps, so the FP32 run sums are added
+//                   to the FP64 accumulators atomically.
 constexpr int FL_WARPS = 8;
-struct FarWarpSmem {
-    __nv_bfloat16 X[32 * MLP_NIP];  // normalised features, BF16
-    float y[32 * MLP_NOP];          // network outputs
-    float kf[32 * 8];               // factors - 1
-    float stg[32 * 16];             // node records
-    int ind[32];                    // in the training ranges
-};
-constexpr size_t FL_SMEM = (size_t)MLPB_N * 2 + MLPF_N * 4 + 4 * MLP_NI * 4 + FL_WARPS * sizeof(FarWarpSmem);
 
-template <int Q>
-__global__ void __launch_bounds__(FL_WARPS * 32) k_far_learned(BHArgs A) {
-    extern __shared__ __align__(16) unsigned char fsm[];
-    __nv_bfloat16* s_wb = reinterpret_cast<__nv_bfloat16*>(fsm);
-    float* s_bias = reinterpret_cast<float*>(fsm + MLPB_N * 2);
-    float* s_norm = s_bias + MLPF_N;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    FarWarpSmem* ws = reinterpret_cast<FarWarpSmem*>(fsm + MLPB_N * 2 + MLPF_N * 4 + 4 * MLP_NI * 4) + warp;
-    for (int i = threadIdx.x; i < MLPB_N; i += blockDim.x) s_wb[i] = A.wb[i];
-    for (int i = threadIdx.x; i < MLPF_N; i += blockDim.x) s_bias[i] = A.mbias[i];
+__global__ void __launch_bounds__(FL_WARPS * 32) k_far_feat(BHArgs A, __nv_bfloat16* __restrict__ X) {
+    __shared__ float s_norm[4 * MLP_NI];
     for (int i = threadIdx.x; i < 4 * MLP_NI; i += blockDim.x) s_norm[i] = A.mnorm[i];
     __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned long long nr = A.far_count[1];
+    const int64_t nruns = nr < (unsigned long long)A.run_cap ? (int64_t)nr : A.run_cap;
+    for (int64_t run = (int64_t)blockIdx.x * FL_WARPS + warp; run < nruns; run += (int64_t)gridDim.x * FL_WARPS) {
+        const tp_far_run R = A.far_runs[run];
+        const float* fl = A.nodeft + 16 * (int64_t)A.leaves[R.li];
+        for (int i = lane; i < R.len; i += 32) {
+            const int64_t row = R.start + i;
+            float f[MLP_NI];
+            far_features(fl, A.nodeft + 16 * (int64_t)A.far_list[row], f);
+            int in_dist = 1;
+            uint32_t pk[16];
+#pragma unroll
+            for (int c = 0; c < MLP_NI; c += 2) {
+                float v[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float lo = s_norm[2 * MLP_NI + c + h], hi = s_norm[3 * MLP_NI + c + h];
+                    const float pad = 0.05f * (hi - lo);
+                    if (!(f[c + h] >= lo - pad && f[c + h] <= hi + pad)) in_dist = 0;
+                    v[h] = (f[c + h] - s_norm[c + h]) / s_norm[MLP_NI + c + h];
+                }
+                pk[c / 2] = pack_bf16(v[0], v[1]);
+            }
+#pragma unroll
+            for (int c = MLP_NI / 2; c < 15; ++c) pk[c] = 0u;
+            pk[15] = pack_bf16(0.f, in_dist ? 1.f : 0.f);  // column 31: the range flag (zero weight column)
+            uint4* dst = reinterpret_cast<uint4*>(X + row * MLP_NIP);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(FL_WARPS * 32) k_mlp_rows(BHArgs A, const __nv_bfloat16* __restrict__ X,
+                                                           float* __restrict__ kf) {
+    __shared__ __align__(16) uint2 s_wf[MLPW_N];
+    __shared__ float s_bias[MLPF_N];
+    __shared__ float s_y[FL_WARPS][32 * MLP_NOP];
+    mlp_frag_weights(A.wb, s_wf, threadIdx.x, blockDim.x);
+    for (int i = threadIdx.x; i < MLPF_N; i += blockDim.x) s_bias[i] = A.mbias[i];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned long long nrows = A.far_count[0];
+    const int64_t rows = nrows < (unsigned long long)A.far_cap ? (int64_t)nrows : A.far_cap;
+    const int64_t nb = (rows + 31) / 32;  // X has at least nb * 32 rows (capacity rounded up)
+    for (int64_t b = (int64_t)blockIdx.x * FL_WARPS + warp; b < nb; b += (int64_t)gridDim.x * FL_WARPS) {
+        warp_mlp_rows32(s_wf, s_bias, X, 32 * b, s_y[warp]);
+        __syncwarp();
+        const int64_t row = 32 * b + lane;
+        if (row < rows) {
+            const uint32_t flag = *reinterpret_cast<const uint32_t*>(X + row * MLP_NIP + 30);
+            const bool in_dist = (flag >> 16) != 0u;
+            float o[8];
+#pragma unroll
+            for (int c = 0; c < MLP_NO; ++c)
+                o[c] = in_dist ? __expf(fminf(4.f, fmaxf(-4.f, s_y[warp][lane * MLP_NOP + c]))) - 1.f : 0.f;
+            o[7] = in_dist ? 1.f : 0.f;
+            float4* dst = reinterpret_cast<float4*>(kf + row * 8);
+            dst[0] = make_float4(o[0], o[1], o[2], o[3]);
+            dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+        }
+        __syncwarp();
+    }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(FL_WARPS * 32) k_far_correct(BHArgs A, const float* __restrict__ kf) {
+    __shared__ __align__(16) float s_stg[FL_WARPS][32 * 16];
+    __shared__ __align__(16) float s_kf[FL_WARPS][32 * 8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* stg = s_stg[warp];
+    float* skf = s_kf[warp];
     const unsigned long long nr = A.far_count[1];
     const int64_t nruns = nr < (unsigned long long)A.run_cap ? (int64_t)nr : A.run_cap;
     const int t = lane & 15, half = lane >> 4;
@@ -550,45 +612,24 @@ __global__ void __launch_bounds__(FL_WARPS * 32) k_far_learned(BHArgs A) {
         for (int b0 = 0; b0 < R.len; b0 += 32) {
             const int nb = R.len - b0 < 32 ? R.len - b0 : 32;
             __syncwarp();
-            int in_dist = 0;
             if (lane < nb) {
-                const int64_t C = A.far_list[R.start + b0 + lane];
+                const int64_t row = R.start + b0 + lane;
+                const int64_t C = A.far_list[row];
                 const float4* r = reinterpret_cast<const float4*>(A.nodef + 16 * C);
-                float4* d = reinterpret_cast<float4*>(ws->stg + lane * 16);
+                float4* d = reinterpret_cast<float4*>(stg + lane * 16);
                 d[0] = r[0];
                 d[1] = r[1];
                 d[2] = r[2];
-                float f[MLP_NI];
-                far_features(A.nodeft + 16 * L, A.nodeft + 16 * C, f);
-                in_dist = 1;
-#pragma unroll
-                for (int c = 0; c < MLP_NI; ++c) {
-                    const float lo = s_norm[2 * MLP_NI + c], hi = s_norm[3 * MLP_NI + c];
-                    const float pad = 0.05f * (hi - lo);
-                    if (!(f[c] >= lo - pad && f[c] <= hi + pad)) in_dist = 0;
-                    ws->X[lane * MLP_NIP + c] = __float2bfloat16_rn((f[c] - s_norm[c]) / s_norm[MLP_NI + c]);
-                }
-            } else {
-#pragma unroll
-                for (int c = 0; c < MLP_NI; ++c) ws->X[lane * MLP_NIP + c] = __float2bfloat16_rn(0.f);
-            }
-#pragma unroll
-            for (int c = MLP_NI; c < MLP_NIP; ++c) ws->X[lane * MLP_NIP + c] = __float2bfloat16_rn(0.f);
-            ws->ind[lane] = in_dist;
-            __syncwarp();
-            warp_mlp_forward_regs(s_wb, s_bias, ws->X, ws->y, 0);
-            if (nb > 16) warp_mlp_forward_regs(s_wb, s_bias, ws->X, ws->y, 16);
-            __syncwarp();
-            if (lane < nb) {
-#pragma unroll
-                for (int c = 0; c < MLP_NO; ++c)
-                    ws->kf[lane * 8 + c] = in_dist ? __expf(fminf(4.f, fmaxf(-4.f, ws->y[lane * MLP_NOP + c]))) - 1.f : 0.f;
+                const float4* kr = reinterpret_cast<const float4*>(kf + row * 8);
+                float4* kd = reinterpret_cast<float4*>(skf + lane * 8);
+                kd[0] = kr[0];
+                kd[1] = kr[1];
             }
             __syncwarp();
             for (int i = half; i < nb; i += 2) {
-                if (active && ws->ind[i]) {
-                    const float* r = ws->stg + i * 16;
-                    gather_pair_learned<Q>(tg, r, r + 3, r + 6, r[9], ws->kf + i * 8, a32);
+                if (active && skf[i * 8 + 7] != 0.f) {
+                    const float* r = stg + i * 16;
+                    gather_pair_learned<Q>(tg, r, r + 3, r + 6, r[9], skf + i * 8, a32);
                     n_learn += 1;
                 }
             }
@@ -652,12 +693,19 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
         A.mbias = tp_mlp_bias(ctx);
         A.mnorm = tp_mlp_norm(ctx);
         if (!ctx->far_count) TP_TRY(tp_alloc_t(ctx, &ctx->far_count, 2));
+        auto alloc_list = [&](int64_t rows, int64_t runs) -> tp_status {
+            rows = (rows + 31) / 32 * 32;  // whole 32-row network batches
+            TP_TRY(tp_alloc_t(ctx, &ctx->far_list, rows));
+            TP_TRY(tp_alloc_t(ctx, &ctx->far_runs, runs));
+            TP_TRY(tp_alloc_t(ctx, &ctx->far_X, rows * MLP_NIP));
+            TP_TRY(tp_alloc_t(ctx, &ctx->far_kf, rows * 8));
+            ctx->far_cap = rows;
+            ctx->run_cap = runs;
+            return TP_OK;
+        };
         if (!ctx->far_list) {
             const int64_t rows = std::max<int64_t>(1 << 20, t.nleaves * 1024);
-            TP_TRY(tp_alloc_t(ctx, &ctx->far_list, rows));
-            TP_TRY(tp_alloc_t(ctx, &ctx->far_runs, rows / 32 + t.nleaves + 1024));
-            ctx->far_cap = rows;
-            ctx->run_cap = rows / 32 + t.nleaves + 1024;
+            TP_TRY(alloc_list(rows, rows / 32 + t.nleaves + 1024));
         }
         for (int attempt = 0;; ++attempt) {
             TP_CU(cudaMemsetAsync(ctx->far_count, 0, 2 * sizeof(unsigned long long), ctx->stream));
@@ -677,28 +725,23 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
             if ((int64_t)fc[0] <= ctx->far_cap && (int64_t)fc[1] <= ctx->run_cap) break;
             if (attempt > 0) return tp_set_err(ctx, TP_E_OOM, "far-pair list overflow");
             // enlarge to the counted need (with slack) and repeat the pass
-            tp_free(ctx, ctx->far_list);
-            tp_free(ctx, ctx->far_runs);
+            for (void* p : {(void*)ctx->far_list, (void*)ctx->far_runs, (void*)ctx->far_X, (void*)ctx->far_kf})
+                tp_free(ctx, p);
             ctx->far_list = nullptr;
             ctx->far_runs = nullptr;
-            const int64_t rows = (int64_t)(fc[0] + fc[0] / 4 + 1024), runs = (int64_t)(fc[1] + fc[1] / 4 + 1024);
-            TP_TRY(tp_alloc_t(ctx, &ctx->far_list, rows));
-            TP_TRY(tp_alloc_t(ctx, &ctx->far_runs, runs));
-            ctx->far_cap = rows;
-            ctx->run_cap = runs;
+            ctx->far_X = nullptr;
+            ctx->far_kf = nullptr;
+            TP_TRY(alloc_list((int64_t)(fc[0] + fc[0] / 4 + 1024), (int64_t)(fc[1] + fc[1] / 4 + 1024)));
             TP_CU(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), ctx->stream));
         }
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_far_learned<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FL_SMEM);
-            cudaFuncSetAttribute(k_far_learned<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FL_SMEM);
-            attr = true;
-        }
-        const unsigned lblocks = (unsigned)std::max(1, ctx->num_sms * 3);
+        const unsigned lblocks = (unsigned)std::max(1, ctx->num_sms * 4);
+        k_far_feat<<<lblocks, FL_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_X);
+        k_mlp_rows<<<lblocks, FL_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_X, ctx->far_kf);
         if (prm->q == 6)
-            k_far_learned<6><<<lblocks, FL_WARPS * 32, FL_SMEM, ctx->stream>>>(A);
+            k_far_correct<6><<<lblocks, FL_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_kf);
         else
-            k_far_learned<8><<<lblocks, FL_WARPS * 32, FL_SMEM, ctx->stream>>>(A);
+            k_far_correct<8><<<lblocks, FL_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_kf);
+        ctx->nlaunch += 3;
     } else {
         if (prm->q == 6)
             k_bh<6, M_BH><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);

@@ -493,16 +493,25 @@ __device__ __forceinline__ void src_step_pp(const TgtPair (&tp)[NP], Acc8 (&at)[
     for (int k = 0; k < 8; ++k) vprev[k] = as.v[k].x + as.v[k].y;
 }
 
-// Fold the FP32 energy partials of the targets into FP64.  A target's energy
-// terms can span many orders of magnitude (the nearest sources dominate), and
-// a long FP32 running sum drops the small terms that follow a large one, so
-// the FP32 partials cover at most 32 sources (or one chunk) before the fold.
+// Fold the FP32 energy partials of the targets into a compensated sum.  A
+// target's energy terms can span many orders of magnitude (the nearest
+// sources dominate), and a long FP32 running sum drops the small terms that
+// follow a large one, so the plain FP32 partials cover at most 32 sources (or
+// one chunk) and are then added to (s, c) with Kahan's compensated summation
+// in FP32 (FP64 arithmetic is far slower on this part).
+struct EFold {
+    float2 s, c;  // running sum and its compensation, per packed target pair
+};
+
 template <int NP>
-__device__ __forceinline__ void fold_energy(Acc8 (&at)[NP], double (&e64)[NP][2]) {
+__device__ __forceinline__ void fold_energy(Acc8 (&at)[NP], EFold (&ef)[NP]) {
+    const float2 m1 = f2(-1.0f);
 #pragma unroll
     for (int P = 0; P < NP; ++P) {
-        e64[P][0] += (double)at[P].v[0].x;
-        e64[P][1] += (double)at[P].v[0].y;
+        const float2 y = fma2(ef[P].c, m1, at[P].v[0]);       // y = part - c
+        const float2 t = add2(ef[P].s, y);                      // t = s + y
+        ef[P].c = fma2(y, m1, fma2(ef[P].s, m1, t));            // c = (t - s) - y
+        ef[P].s = t;
         at[P].v[0] = make_float2(0.f, 0.f);
     }
 }
@@ -510,7 +519,7 @@ __device__ __forceinline__ void fold_energy(Acc8 (&at)[NP], double (&e64)[NP][2]
 // The 12 chunks of one item for one item kind; target partials in `at`.
 template <int Q, int KIND, int W, int NP, int PF>
 __device__ __forceinline__ bool grad_item(const DirectArgs& A, ChunkPipe& pipe, float* sacc, int I, int J,
-                                          const TgtPair (&tp)[NP], Acc8 (&at)[NP], double (&e64)[NP][2], int warp,
+                                          const TgtPair (&tp)[NP], Acc8 (&at)[NP], EFold (&e64)[NP], int warp,
                                           int lane, int pbase) {
     constexpr bool LO = KIND != K_FAST;
     const int64_t ntp = A.ntp;
@@ -675,10 +684,10 @@ __global__ void __launch_bounds__(GradShape<MASKQ>::THREADS, 1) k_pairs_grad(Dir
                 load_tgt<true>(A.soa, ntp, (int64_t)it.I * TP_SUPER + 2 * (pbase + 32 * P), tp[P]);
         }
         Acc8 at[NP];
-        double e64[NP][2];
+        EFold e64[NP];
 #pragma unroll
         for (int P = 0; P < NP; ++P) {
-            e64[P][0] = e64[P][1] = 0.0;
+            e64[P].s = e64[P].c = make_float2(0.f, 0.f);
 #pragma unroll
             for (int c = 0; c < TP_NACC; ++c) at[P].v[c] = make_float2(0.f, 0.f);
         }
@@ -698,8 +707,9 @@ __global__ void __launch_bounds__(GradShape<MASKQ>::THREADS, 1) k_pairs_grad(Dir
 #pragma unroll
         for (int P = 0; P < NP; ++P) {
             const int64_t t0 = (int64_t)it.I * TP_SUPER + 2 * (pbase + 32 * P);
-            if (e64[P][0] != 0.0) atomicAdd(&A.acc[t0], e64[P][0]);
-            if (e64[P][1] != 0.0) atomicAdd(&A.acc[t0 + 1], e64[P][1]);
+            const double ex = (double)e64[P].s.x - (double)e64[P].c.x, ey = (double)e64[P].s.y - (double)e64[P].c.y;
+            if (ex != 0.0) atomicAdd(&A.acc[t0], ex);
+            if (ey != 0.0) atomicAdd(&A.acc[t0 + 1], ey);
 #pragma unroll
             for (int k = 1; k < TP_NACC; ++k) {
                 if (at[P].v[k].x != 0.f) atomicAdd(&A.acc[k * ntp + t0], (double)at[P].v[k].x);
@@ -1075,10 +1085,10 @@ __global__ void __launch_bounds__(GradShape<false>::THREADS, 1) k_conf_grad(Dire
             for (int P = 0; P < NP; ++P) load_tgt<true>(A.soa, ntp, (int64_t)I * TP_SUPER + 2 * (pbase + 32 * P), tp[P]);
         }
         Acc8 at[NP];
-        double e64[NP][2];
+        EFold e64[NP];
 #pragma unroll
         for (int P = 0; P < NP; ++P) {
-            e64[P][0] = e64[P][1] = 0.0;
+            e64[P].s = e64[P].c = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < TP_NACC; ++k) at[P].v[k] = make_float2(0.f, 0.f);
         }
@@ -1104,8 +1114,9 @@ __global__ void __launch_bounds__(GradShape<false>::THREADS, 1) k_conf_grad(Dire
 #pragma unroll
         for (int P = 0; P < NP; ++P) {
             const int64_t t0 = (int64_t)I * TP_SUPER + 2 * (pbase + 32 * P);
-            if (e64[P][0] != 0.0) atomicAdd(&A.acc[t0], e64[P][0]);
-            if (e64[P][1] != 0.0) atomicAdd(&A.acc[t0 + 1], e64[P][1]);
+            const double ex = (double)e64[P].s.x - (double)e64[P].c.x, ey = (double)e64[P].s.y - (double)e64[P].c.y;
+            if (ex != 0.0) atomicAdd(&A.acc[t0], ex);
+            if (ey != 0.0) atomicAdd(&A.acc[t0 + 1], ey);
 #pragma unroll
             for (int k = 1; k < TP_NACC; ++k) {
                 if (at[P].v[k].x != 0.f) atomicAdd(&A.acc[k * ntp + t0], (double)at[P].v[k].x);

@@ -17,6 +17,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 #include <algorithm>
@@ -145,6 +146,8 @@ struct tp_ctx {
     int32_t* far_list = nullptr;
     tp_far_run* far_runs = nullptr;
     unsigned long long* far_count = nullptr;  // [2] rows and runs listed (may exceed the capacities)
+    __nv_bfloat16* far_X = nullptr;  // [far_cap][32] BF16 network inputs of the listed pairs
+    float* far_kf = nullptr;         // [far_cap][8] factors - 1 (column 7: in the training ranges)
     int64_t far_cap = 0, run_cap = 0;
 
     tp_stats stats{};

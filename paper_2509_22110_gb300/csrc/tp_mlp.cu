@@ -476,16 +476,16 @@ __global__ void __launch_bounds__(128) k_mlp_train(const __nv_bfloat16* __restri
 }
 
 // Forward pass only, with the inference arithmetic of the learned Barnes-Hut
-// correction (warp_mlp_forward_regs): 4 warps x 32 rows per block.
+// correction (warp_mlp_rows32): 4 warps x 32 rows per block.
 __global__ void __launch_bounds__(128) k_mlp_infer(const __nv_bfloat16* __restrict__ wb_g,
                                                    const float* __restrict__ bias_g, const float* __restrict__ norm,
                                                    const float* __restrict__ X, int64_t n, int normalised,
                                                    float* __restrict__ Y) {
-    __shared__ __align__(16) __nv_bfloat16 s_wb[MLPB_N];
+    __shared__ __align__(16) uint2 s_wf[MLPW_N];
     __shared__ float s_bias[MLPF_N];
     __shared__ __align__(16) __nv_bfloat16 s_x[4][32 * MLP_NIP];
     __shared__ float s_y[4][32 * MLP_NOP];
-    for (int i = threadIdx.x; i < MLPB_N; i += blockDim.x) s_wb[i] = wb_g[i];
+    mlp_frag_weights(wb_g, s_wf, threadIdx.x, blockDim.x);
     for (int i = threadIdx.x; i < MLPF_N; i += blockDim.x) s_bias[i] = bias_g[i];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -501,8 +501,7 @@ __global__ void __launch_bounds__(128) k_mlp_infer(const __nv_bfloat16* __restri
         x[c] = __float2bfloat16_rn(v);
     }
     __syncwarp();
-    warp_mlp_forward_regs(s_wb, s_bias, s_x[warp], s_y[warp], 0);
-    warp_mlp_forward_regs(s_wb, s_bias, s_x[warp], s_y[warp], 16);
+    warp_mlp_rows32(s_wf, s_bias, s_x[warp], 0, s_y[warp]);
     __syncwarp();
     if (row < n)
         for (int c = 0; c < MLP_NO; ++c) Y[row * MLP_NO + c] = s_y[warp][lane * MLP_NOP + c];

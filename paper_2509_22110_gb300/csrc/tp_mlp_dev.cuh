@@ -157,57 +157,107 @@ __device__ __forceinline__ void warp_mlp_forward(const __nv_bfloat16* wb, const 
     __syncwarp();
 }
 
-// Register-resident variant for inference: the accumulator fragment of a
-// 16 x 8 output tile holds (row g, cols 2t, 2t+1) and (row g+8, same cols)
-// per lane (g = lane/4, t = lane%4), exactly the halves of the A fragment
-// of the next layer's 16 x 16 k-tile, so hidden activations stay in
-// registers (GELU applied, packed to BF16) and only the input X and the
-// output y touch shared memory.
-template <int KT, int NT>
-__device__ __forceinline__ void dense_regs(const uint32_t (&a)[KT][4], const __nv_bfloat16* W, const float* bias,
-                                           uint32_t (&h)[NT / 2][4]) {
-    const int t2 = ((threadIdx.x & 31) & 3) * 2;
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-        float d[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int kk = 0; kk < KT; ++kk) {
-            uint32_t b[2];
-            load_b_nk(W, 16 * KT, 16 * kk, 8 * j, b);
-            mma_bf16(d, a[kk], b);
+// Inference keeps the hidden activations in registers: the accumulator
+// fragment of a 16 x 8 output tile holds (row g, cols 2t, 2t+1) and (row g+8,
+// same cols) per lane (g = lane/4, t = lane%4), exactly the halves of the A
+// fragment of the next layer's 16 x 16 k-tile, so GELU and the BF16 packing
+// happen in registers and only the input X and the output y touch memory.
+// Fragment-ordered copy of the BF16 weights for the inference kernels: for
+// each layer, n-tile j and k-tile kk, lane l holds the two 32-bit B-fragment
+// registers of mma.m16n8k16 (W[n][k..k+1] and W[n][k+8..k+9], n = 8j + l/4,
+// k = 16kk + 2(l%4)) side by side, so a fragment is one conflict-free 64-bit
+// shared-memory load (the row-major copy puts the 32 lanes in 4 banks).
+#define MLPW_W1 0                       // [8 j][2 kk][32] uint2 (K = 32, padded)
+#define MLPW_W2 (MLPW_W1 + 8 * 2 * 32)  // [8][4][32]
+#define MLPW_W3 (MLPW_W2 + 8 * 4 * 32)  // [8][4][32]
+#define MLPW_W4 (MLPW_W3 + 8 * 4 * 32)  // [1][4][32]
+#define MLPW_N (MLPW_W4 + 1 * 4 * 32)   // 2688 uint2 = 21 KB
+
+// Build the fragment-ordered copy wf[MLPW_N] from the row-major BF16 block wb
+// (threads t of n cooperate).
+__device__ __forceinline__ void mlp_frag_weights(const __nv_bfloat16* wb, uint2* wf, int t, int n) {
+    for (int i = t; i < MLPW_N; i += n) {
+        int base, K, r;
+        const __nv_bfloat16* W;
+        if (i < MLPW_W2) {
+            base = MLPW_W1; K = MLP_NIP; W = wb + MLPB_W1;
+        } else if (i < MLPW_W3) {
+            base = MLPW_W2; K = MLP_NH; W = wb + MLPB_W2;
+        } else if (i < MLPW_W4) {
+            base = MLPW_W3; K = MLP_NH; W = wb + MLPB_W3;
+        } else {
+            base = MLPW_W4; K = MLP_NH; W = wb + MLPB_W4;
         }
-        const float b0 = bias[8 * j + t2], b1 = bias[8 * j + t2 + 1];
-        const uint32_t lo = pack_bf16(mlp_gelu(d[0] + b0, nullptr), mlp_gelu(d[1] + b1, nullptr));
-        const uint32_t hi = pack_bf16(mlp_gelu(d[2] + b0, nullptr), mlp_gelu(d[3] + b1, nullptr));
-        h[j >> 1][(j & 1) * 2 + 0] = lo;
-        h[j >> 1][(j & 1) * 2 + 1] = hi;
+        r = i - base;
+        const int lane = r & 31, kk = (r >> 5) % (K / 16), j = (r >> 5) / (K / 16);
+        const int n0 = 8 * j + (lane >> 2), k = 16 * kk + 2 * (lane & 3);
+        const __nv_bfloat16* p = W + n0 * K + k;
+        wf[i] = make_uint2(pack_bf16_raw(p[0], p[1]), pack_bf16_raw(p[8], p[9]));
     }
 }
 
-// Network forward for 16 rows (m0..m0+15) of X (BF16 [rows][32] in shared
-// memory, normalised features, zero-padded): y (FP32 [rows][8], shared
-// memory, column 7 unused) = the 7 outputs.  Same arithmetic as
-// warp_mlp_forward (BF16 operands, FP32 accumulation, BF16 activations).
-__device__ __forceinline__ void warp_mlp_forward_regs(const __nv_bfloat16* wb, const float* bias,
-                                                      const __nv_bfloat16* X, float* y, int m0) {
-    uint32_t a1[2][4];
-    load_a_rm(X, MLP_NIP, m0, 0, a1[0]);
-    load_a_rm(X, MLP_NIP, m0, 16, a1[1]);
-    uint32_t h1[4][4], h2[4][4];
-    dense_regs<2, 8>(a1, wb + MLPB_W1, bias + MLPF_B1, h1);
-    dense_regs<4, 8>(h1, wb + MLPB_W2, bias + MLPF_B2, h2);
-    dense_regs<4, 8>(h2, wb + MLPB_W3, bias + MLPF_B3, h1);
-    float d[4] = {0.f, 0.f, 0.f, 0.f};
+// One layer for M 16-row tiles with activations in registers: the B fragment
+// of each (n-tile, k-tile) is loaded once and used by every row tile.
+template <int KT, int NT, int M>
+__device__ __forceinline__ void dense_frag(const uint32_t (&a)[M][KT][4], const uint2* wf, const float* bias,
+                                           uint32_t (&h)[M][NT / 2][4]) {
+    const int lane = threadIdx.x & 31, t2 = (lane & 3) * 2;
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+        uint32_t b[KT][2];
+#pragma unroll
+        for (int kk = 0; kk < KT; ++kk) {
+            const uint2 v = wf[(j * KT + kk) * 32 + lane];
+            b[kk][0] = v.x;
+            b[kk][1] = v.y;
+        }
+        const float b0 = bias[8 * j + t2], b1 = bias[8 * j + t2 + 1];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kk = 0; kk < KT; ++kk) mma_bf16(d, a[m][kk], b[kk]);
+            h[m][j >> 1][(j & 1) * 2 + 0] = pack_bf16(mlp_gelu(d[0] + b0, nullptr), mlp_gelu(d[1] + b1, nullptr));
+            h[m][j >> 1][(j & 1) * 2 + 1] = pack_bf16(mlp_gelu(d[2] + b0, nullptr), mlp_gelu(d[3] + b1, nullptr));
+        }
+    }
+}
+
+// Network forward for 32 rows (two 16-row tiles) of X (BF16, row-major with
+// leading dimension 32, any memory space; rows row0..row0+31 must exist):
+// y (FP32 [32][8] in shared memory, row 0 = row0, column 7 unused).  Same
+// arithmetic as warp_mlp_forward (BF16 operands and activations, FP32
+// accumulation).
+__device__ __forceinline__ void warp_mlp_rows32(const uint2* wf, const float* bias, const __nv_bfloat16* X,
+                                                int64_t row0, float* y) {
+    uint32_t a1[2][2][4];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        load_a_rm(X + row0 * MLP_NIP, MLP_NIP, 16 * m, 0, a1[m][0]);
+        load_a_rm(X + row0 * MLP_NIP, MLP_NIP, 16 * m, 16, a1[m][1]);
+    }
+    uint32_t h1[2][4][4], h2[2][4][4];
+    dense_frag<2, 8, 2>(a1, wf + MLPW_W1, bias + MLPF_B1, h1);
+    dense_frag<4, 8, 2>(h1, wf + MLPW_W2, bias + MLPF_B2, h2);
+    dense_frag<4, 8, 2>(h2, wf + MLPW_W3, bias + MLPF_B3, h1);
+    const int lane = threadIdx.x & 31;
+    uint32_t b[4][2];
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
-        uint32_t b[2];
-        load_b_nk(wb + MLPB_W4, MLP_NH, 16 * kk, 0, b);
-        mma_bf16(d, h1[kk], b);
+        const uint2 v = wf[MLPW_W4 + kk * 32 + lane];
+        b[kk][0] = v.x;
+        b[kk][1] = v.y;
     }
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        const int r = m0 + frag_row(v), c = frag_col(v);
-        y[r * MLP_NOP + c] = d[v] + bias[MLPF_B4 + c];
+    for (int m = 0; m < 2; ++m) {
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) mma_bf16(d, h1[m][kk], b[kk]);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int r = 16 * m + frag_row(v), c = frag_col(v);
+            y[r * MLP_NOP + c] = d[v] + bias[MLPF_B4 + c];
+        }
     }
 }
 
