@@ -184,11 +184,13 @@ tp_status tp_far_fit_normalisation(tp_ctx* ctx);
  * batches of `batch` rows; *last_loss: masked mean-square loss of the last batch. */
 tp_status tp_far_train(tp_ctx* ctx, int64_t steps, int64_t batch, double lr, double wd, uint64_t seed,
                        double* last_loss);
-/* Network on given rows X[n][24] (raw, or normalised if normalised != 0):
- * outputs Y[n][7].  With targets or masks [n][8] the training kernel runs and
- * also returns the loss and the parameter gradient grad[10375]; with neither,
- * the inference kernel of TP_LEARNED evaluations runs (grad and loss are
- * zeroed).  Each output may be NULL.  For tests. */
+/* Network on given rows X[n][24] (raw, or normalised if bit 0 of normalised
+ * is set): outputs Y[n][7].  With targets or masks [n][8] the training kernel
+ * runs and also returns the loss and the parameter gradient grad[10375]; with
+ * neither, the inference network of TP_LEARNED evaluations runs (tcgen05 on
+ * the tensor cores; with bit 1 of normalised set, the register-resident
+ * mma.sync variant) and grad and loss are zeroed.  Each output may be NULL.
+ * For tests. */
 tp_status tp_far_eval(tp_ctx* ctx, const float* X, int64_t n, int normalised, const float* tgt, const float* mask,
                       float* Y, float* grad, double* loss);
 /* One AdamW step with the given gradient [10375].  For tests. */
@@ -252,6 +254,13 @@ tp_status tp_debug_tree(tp_ctx* ctx, uint32_t* codes, int32_t* perm, int32_t* le
 tp_status tp_gradient_direct_noalloc(const double* V, int64_t nv, const int32_t* F, int64_t nt,
                                      const tp_params* params, double* energy_out, double* grad_out,
                                      void* cuda_stream, char* errbuf, int64_t errbuf_len);
+
+/* One 128 x N x K tensor-core GEMM D = A B^T (A [128][K], B [N][K] BF16 as
+ * raw 16-bit patterns, D [128][N] FP32; host arrays; K in {16, 32, 64},
+ * N in {16, 64}) through the operand layout, descriptors and accumulator
+ * read-back of the learned far field's network kernel.  Synchronises the
+ * device.  TP_E_ARG on bad sizes.  For tests. */
+tp_status tp_debug_tc_gemm(int device, const uint16_t* A, int K, const uint16_t* B, int N, float* D);
 
 /* Library version string. */
 const char* tp_version(void);

@@ -33,7 +33,7 @@ _u8 = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
 
 def build(force: bool = False) -> str:
     """Compile ``oracle.c`` (and the MLP reference) into ``liboracle.so``."""
-    srcs = [os.path.join(_HERE, f) for f in ("oracle.c", "oracle_mlp.c", "oracle_conf.c") if os.path.exists(os.path.join(_HERE, f))]
+    srcs = [os.path.join(_HERE, f) for f in ("oracle.c", "oracle_mlp.c", "oracle_conf.c", "oracle_quad.c") if os.path.exists(os.path.join(_HERE, f))]
     if not force and os.path.exists(_SO) and all(os.path.getmtime(_SO) >= os.path.getmtime(s) for s in srcs + [os.path.join(_HERE, "oracle.h")]):
         return _SO
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared", "-std=c11",
@@ -65,6 +65,8 @@ def _load():
     lib.or_conf_energy.argtypes = [_d, _d, _d, i64, _d, _d, i64, dbl, dbl, dbl, i32]
     lib.or_conf_energy.restype = dbl
     lib.or_conf_accum.argtypes = [_d, _d, _d, i64, _d, _d, i64, dbl, dbl, _d, _d, _d, i32]
+    lib.or_quad_points.argtypes = [_d, _i32, i64, i32, _d, _d, _d, _d, _d, _i32]
+    lib.or_quad_adjoint.argtypes = [_d, _i32, i64, i32, _d, _d, _d, _d, _d, dbl, _d]
     if hasattr(lib, "or_mlp_forward"):
         _bind_mlp(lib)
     _lib = lib
@@ -371,3 +373,61 @@ def conf_vertex_gradient_sample(V, F, Vc, Fc, verts, q=6.0, p=12.0, c=1.0, nthre
     gw, gnu, gx = conf_accum(V, F, Vc, Fc, q, p, soa=(x[tris], nu[tris], w[tris]), nthreads=nthreads)
     grad = adjoint(V, F, gw, gnu, gx, c, tris=tris)
     return grad[np.asarray(verts)]
+
+
+# ---------------------------------------------------------------- multi-point quadrature (Sec. 3.1, 3.2)
+def quad_rule(k):
+    """Symmetric triangle rules with barycentric points [k,3] and weights [k] (sum 1):
+    k = 1 the centroid (degree 1), k = 3 the points (2/3, 1/6, 1/6) (degree 2), k = 6 the
+    degree-4 rule of Strang and Fix (closed forms of its two orbits)."""
+    if k == 1:
+        return np.array([[1 / 3, 1 / 3, 1 / 3]]), np.array([1.0])
+    if k == 3:
+        a, b = 2.0 / 3.0, 1.0 / 6.0
+        return np.array([[a, b, b], [b, a, b], [b, b, a]]), np.full(3, 1.0 / 3.0)
+    if k == 6:
+        s10, r = np.sqrt(10.0), np.sqrt(38.0 - 44.0 * np.sqrt(2.0 / 5.0))
+        a1, a2 = (8.0 - s10 + r) / 18.0, (8.0 - s10 - r) / 18.0
+        t = np.sqrt(213125.0 - 53320.0 * s10)
+        w1, w2 = (620.0 + t) / 3720.0, (620.0 - t) / 3720.0
+        pts, wts = [], []
+        for a, w in ((a1, w1), (a2, w2)):
+            c = 1.0 - 2.0 * a
+            pts += [[c, a, a], [a, c, a], [a, a, c]]
+            wts += [w, w, w]
+        return np.array(pts), np.array(wts)
+    raise ValueError("quadrature with 1, 3 or 6 points")
+
+
+def quad_points(V, F, k):
+    """Quadrature points of every triangle: x [nt*k,3], nu, w [nt*k], parent faces [nt*k,3]."""
+    lib = _load()
+    V, F = _prep(V, F)
+    bary, om = quad_rule(k)
+    bary = np.ascontiguousarray(bary, dtype=np.float64)
+    om = np.ascontiguousarray(om, dtype=np.float64)
+    n = F.shape[0] * k
+    x, nu, w = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n)
+    Fq = np.zeros((n, 3), dtype=np.int32)
+    lib.or_quad_points(V, F, F.shape[0], k, bary, om, x, nu, w, Fq)
+    return x, nu, w, Fq
+
+
+def quad_energy(V, F, k, q=6.0, p=12.0, c=1.0, nthreads=None):
+    """Phi with k quadrature points per triangle on both integrals (pairs of points of admitted triangles)."""
+    x, nu, w, Fq = quad_points(V, F, k)
+    return energy_soa(x, nu, w, Fq, q, p, c, 0, nthreads)
+
+
+def quad_gradient(V, F, k, q=6.0, p=12.0, c=1.0, nthreads=None):
+    """(Phi, dPhi/dV) of the k-point quadrature form."""
+    lib = _load()
+    V, F = _prep(V, F)
+    x, nu, w, Fq = quad_points(V, F, k)
+    E = energy_soa(x, nu, w, Fq, q, p, c, 0, nthreads)
+    gw, gnu, gx = tri_accum(V, Fq, None, q, p, 0, nthreads, soa=(x, nu, w))
+    bary, om = quad_rule(k)
+    grad = np.zeros_like(V)
+    lib.or_quad_adjoint(V, F, F.shape[0], k, np.ascontiguousarray(bary), np.ascontiguousarray(om),
+                        np.ascontiguousarray(gw), np.ascontiguousarray(gnu), np.ascontiguousarray(gx), c, grad)
+    return E, grad

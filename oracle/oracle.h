@@ -64,6 +64,14 @@ double or_conf_energy(const double* x, const double* nu, const double* w, int64_
 void or_conf_accum(const double* x, const double* nu, const double* w, int64_t nt, const double* y, const double* a,
                    int64_t nk, double q, double p, double* gw, double* gnu, double* gx, int nthreads);
 
+/* Multi-point quadrature form (oracle_quad.c): k points per triangle with
+ * barycentric coordinates bary[k][3] and weights om[k] (summing to 1). */
+void or_quad_points(const double* V, const int32_t* F, int64_t nt, int k, const double* bary, const double* om,
+                    double* x, double* nu, double* w, int32_t* Fq);
+
+void or_quad_adjoint(const double* V, const int32_t* F, int64_t nt, int k, const double* bary, const double* om,
+                     const double* gw, const double* gnu, const double* gx, double c, double* grad);
+
 #ifdef __cplusplus
 }
 #endif

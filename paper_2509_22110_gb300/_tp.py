@@ -111,6 +111,8 @@ def lib():
         getattr(L, n).restype = i32
     L.tp_gradient_direct_noalloc.argtypes = [vp, i64, vp, i64, C.POINTER(tp_params), vp, vp, vp, C.c_char_p, i64]
     L.tp_gradient_direct_noalloc.restype = i32
+    L.tp_debug_tc_gemm.argtypes = [i32, vp, i32, vp, i32, vp]
+    L.tp_debug_tc_gemm.restype = i32
     L.tp_measure_fp32_peak.argtypes = [i32, vp, i32, i32, i32, C.POINTER(C.c_double)]
     L.tp_measure_fp32_peak.restype = i32
     _lib = L
@@ -140,6 +142,18 @@ def _ptr(a):
 
 def tp_version():
     return lib().tp_version().decode()
+
+
+def tp_debug_tc_gemm(A_bits, B_bits, device=0):
+    """D = A B^T through the tensor-core path: A [128,K], B [N,K] uint16 BF16 bit patterns."""
+    A = np.ascontiguousarray(A_bits, dtype=np.uint16)
+    B = np.ascontiguousarray(B_bits, dtype=np.uint16)
+    K, N = A.shape[1], B.shape[0]
+    D = np.zeros((128, N), np.float32)
+    st = lib().tp_debug_tc_gemm(int(device), A.ctypes.data, K, B.ctypes.data, N, D.ctypes.data)
+    if st != TP_OK:
+        raise TPError(st, "tp_debug_tc_gemm failed")
+    return D
 
 
 def tp_measure_fp32_peak(device=0, stream=None, packed=True, warps_per_sm=64, chains=8):
@@ -392,7 +406,7 @@ def tp_far_train(ctx, steps, batch, lr, wd=0.0, seed=0):
     return loss.value
 
 
-def tp_far_eval(ctx, X, normalised=False, tgt=None, mask=None):
+def tp_far_eval(ctx, X, normalised=False, tgt=None, mask=None, mma_sync=False):
     X = _f32(X)
     n = X.shape[0]
     Y = np.zeros((n, 7), np.float32)
@@ -400,7 +414,8 @@ def tp_far_eval(ctx, X, normalised=False, tgt=None, mask=None):
     t = _f32(tgt) if tgt is not None else None
     m = _f32(mask) if mask is not None else None
     loss = C.c_double(0.0)
-    _check(ctx, lib().tp_far_eval(ctx, X.ctypes.data, n, int(bool(normalised)), t.ctypes.data if t is not None else None,
+    _check(ctx, lib().tp_far_eval(ctx, X.ctypes.data, n, int(bool(normalised)) | (2 if mma_sync else 0),
+                                  t.ctypes.data if t is not None else None,
                                   m.ctypes.data if m is not None else None, Y.ctypes.data, g.ctypes.data,
                                   C.byref(loss)))
     return Y, g, loss.value

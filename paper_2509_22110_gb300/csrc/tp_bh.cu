@@ -496,19 +496,25 @@ __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
 //   k_far_feat    - one warp per run: the 24 normalised features of every
 //                   (L, C) pair as a BF16 row (column 31 = 1 when the raw
 //                   features lie in the training ranges, else 0);
-//   k_mlp_rows    - the network on 32 rows per warp on the tensor cores
-//                   (mma.sync m16n8k16, BF16 operands, FP32 accumulation,
-//                   activations in registers, fragment-ordered weights in
-//                   shared memory): kf - 1 per channel (0 outside the ranges);
+//   k_mlp_tc      - the network on 128-row tiles on the 5th-generation
+//                   tensor cores (tcgen05.mma, operands in shared memory,
+//                   FP32 accumulators in tensor memory; tp_tc.cu): kf - 1 per
+//                   channel (0 outside the ranges);
 //   k_far_correct - one warp per run: (kf - 1) x the far-term channels for
 //                   the 16 targets of the leaf; runs of one leaf may be in
 //                   flight in different warps, so the FP32 run sums are added
 //                   to the FP64 accumulators atomically.
 constexpr int FL_WARPS = 8;
 
-__global__ void __launch_bounds__(FL_WARPS * 32) k_far_feat(BHArgs A, __nv_bfloat16* __restrict__ X) {
-    __shared__ float s_norm[4 * MLP_NI];
-    for (int i = threadIdx.x; i < 4 * MLP_NI; i += blockDim.x) s_norm[i] = A.mnorm[i];
+__global__ void __launch_bounds__(FL_WARPS * 32, 2) k_far_feat(BHArgs A, __nv_bfloat16* __restrict__ X) {
+    __shared__ float s_norm[4 * MLP_NI];  // mean, 1/std, lower and upper admitted bound per feature
+    for (int i = threadIdx.x; i < MLP_NI; i += blockDim.x) {
+        const float lo = A.mnorm[2 * MLP_NI + i], hi = A.mnorm[3 * MLP_NI + i], pad = 0.05f * (hi - lo);
+        s_norm[i] = A.mnorm[i];
+        s_norm[MLP_NI + i] = 1.0f / A.mnorm[MLP_NI + i];
+        s_norm[2 * MLP_NI + i] = lo - pad;
+        s_norm[3 * MLP_NI + i] = hi + pad;
+    }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned long long nr = A.far_count[1];
@@ -527,10 +533,9 @@ __global__ void __launch_bounds__(FL_WARPS * 32) k_far_feat(BHArgs A, __nv_bfloa
                 float v[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const float lo = s_norm[2 * MLP_NI + c + h], hi = s_norm[3 * MLP_NI + c + h];
-                    const float pad = 0.05f * (hi - lo);
-                    if (!(f[c + h] >= lo - pad && f[c + h] <= hi + pad)) in_dist = 0;
-                    v[h] = (f[c + h] - s_norm[c + h]) / s_norm[MLP_NI + c + h];
+                    if (!(f[c + h] >= s_norm[2 * MLP_NI + c + h] && f[c + h] <= s_norm[3 * MLP_NI + c + h]))
+                        in_dist = 0;
+                    v[h] = (f[c + h] - s_norm[c + h]) * s_norm[MLP_NI + c + h];
                 }
                 pk[c / 2] = pack_bf16(v[0], v[1]);
             }
@@ -541,38 +546,6 @@ __global__ void __launch_bounds__(FL_WARPS * 32) k_far_feat(BHArgs A, __nv_bfloa
 #pragma unroll
             for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
         }
-    }
-}
-
-__global__ void __launch_bounds__(FL_WARPS * 32) k_mlp_rows(BHArgs A, const __nv_bfloat16* __restrict__ X,
-                                                           float* __restrict__ kf) {
-    __shared__ __align__(16) uint2 s_wf[MLPW_N];
-    __shared__ float s_bias[MLPF_N];
-    __shared__ float s_y[FL_WARPS][32 * MLP_NOP];
-    mlp_frag_weights(A.wb, s_wf, threadIdx.x, blockDim.x);
-    for (int i = threadIdx.x; i < MLPF_N; i += blockDim.x) s_bias[i] = A.mbias[i];
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned long long nrows = A.far_count[0];
-    const int64_t rows = nrows < (unsigned long long)A.far_cap ? (int64_t)nrows : A.far_cap;
-    const int64_t nb = (rows + 31) / 32;  // X has at least nb * 32 rows (capacity rounded up)
-    for (int64_t b = (int64_t)blockIdx.x * FL_WARPS + warp; b < nb; b += (int64_t)gridDim.x * FL_WARPS) {
-        warp_mlp_rows32(s_wf, s_bias, X, 32 * b, s_y[warp]);
-        __syncwarp();
-        const int64_t row = 32 * b + lane;
-        if (row < rows) {
-            const uint32_t flag = *reinterpret_cast<const uint32_t*>(X + row * MLP_NIP + 30);
-            const bool in_dist = (flag >> 16) != 0u;
-            float o[8];
-#pragma unroll
-            for (int c = 0; c < MLP_NO; ++c)
-                o[c] = in_dist ? __expf(fminf(4.f, fmaxf(-4.f, s_y[warp][lane * MLP_NOP + c]))) - 1.f : 0.f;
-            o[7] = in_dist ? 1.f : 0.f;
-            float4* dst = reinterpret_cast<float4*>(kf + row * 8);
-            dst[0] = make_float4(o[0], o[1], o[2], o[3]);
-            dst[1] = make_float4(o[4], o[5], o[6], o[7]);
-        }
-        __syncwarp();
     }
 }
 
@@ -707,6 +680,7 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
             const int64_t rows = std::max<int64_t>(1 << 20, t.nleaves * 1024);
             TP_TRY(alloc_list(rows, rows / 32 + t.nleaves + 1024));
         }
+        int64_t listed_rows = 0;
         for (int attempt = 0;; ++attempt) {
             TP_CU(cudaMemsetAsync(ctx->far_count, 0, 2 * sizeof(unsigned long long), ctx->stream));
             A.far_list = ctx->far_list;
@@ -722,7 +696,10 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
             unsigned long long fc[2] = {0, 0};
             TP_CU(cudaMemcpyAsync(fc, ctx->far_count, sizeof(fc), cudaMemcpyDeviceToHost, ctx->stream));
             TP_CU(cudaStreamSynchronize(ctx->stream));
-            if ((int64_t)fc[0] <= ctx->far_cap && (int64_t)fc[1] <= ctx->run_cap) break;
+            if ((int64_t)fc[0] <= ctx->far_cap && (int64_t)fc[1] <= ctx->run_cap) {
+                listed_rows = (int64_t)fc[0];
+                break;
+            }
             if (attempt > 0) return tp_set_err(ctx, TP_E_OOM, "far-pair list overflow");
             // enlarge to the counted need (with slack) and repeat the pass
             for (void* p : {(void*)ctx->far_list, (void*)ctx->far_runs, (void*)ctx->far_X, (void*)ctx->far_kf})
@@ -736,12 +713,12 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
         }
         const unsigned lblocks = (unsigned)std::max(1, ctx->num_sms * 4);
         k_far_feat<<<lblocks, FL_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_X);
-        k_mlp_rows<<<lblocks, FL_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_X, ctx->far_kf);
+        TP_TRY(tp_launch_mlp_tc(ctx, A.wb, A.mbias, ctx->far_X, listed_rows, ctx->far_kf, 0));
         if (prm->q == 6)
             k_far_correct<6><<<lblocks, FL_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_kf);
         else
             k_far_correct<8><<<lblocks, FL_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_kf);
-        ctx->nlaunch += 3;
+        ctx->nlaunch += 2;  // plus the network launch counted by tp_launch_mlp_tc
     } else {
         if (prm->q == 6)
             k_bh<6, M_BH><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);

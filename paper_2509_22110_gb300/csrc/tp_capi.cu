@@ -111,20 +111,6 @@ tp_status check_params(tp_ctx* ctx, const tp_params* prm) {
     return TP_OK;
 }
 
-// read and clear the device error word; map to a status
-tp_status take_device_error(tp_ctx* ctx, const char* where) {
-    unsigned h = 0;
-    TP_CU(cudaMemcpyAsync(&h, ctx->derr, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
-    TP_CU(cudaStreamSynchronize(ctx->stream));
-    if (!h) return TP_OK;
-    TP_CU(cudaMemsetAsync(ctx->derr, 0, sizeof(unsigned), ctx->stream));
-    if (h & TP_DERR_TIMEOUT) return tp_set_err(ctx, TP_E_TIMEOUT, "%s: a device-side wait timed out", where);
-    if (h & TP_DERR_INDEX) return tp_set_err(ctx, TP_E_ARG, "%s: face index outside [0, nv)", where);
-    if (h & TP_DERR_STACK) return tp_set_err(ctx, TP_E_CUDA, "%s: traversal stack overflow", where);
-    if (h & TP_DERR_NONFINITE)
-        return tp_set_err(ctx, TP_E_NONFINITE, "%s: degenerate triangle or non-finite coordinate", where);
-    return tp_set_err(ctx, TP_E_CUDA, "%s: device error 0x%x", where, h);
-}
 
 void release_mesh(tp_ctx* ctx) {
     free_ptr(ctx, ctx->V64);
@@ -235,6 +221,21 @@ int64_t n_direct_pairs(const tp_ctx* ctx) {
 }
 
 }  // namespace
+
+// read and clear the device error word; map to a status
+tp_status take_device_error(tp_ctx* ctx, const char* where) {
+    unsigned h = 0;
+    TP_CU(cudaMemcpyAsync(&h, ctx->derr, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+    TP_CU(cudaStreamSynchronize(ctx->stream));
+    if (!h) return TP_OK;
+    TP_CU(cudaMemsetAsync(ctx->derr, 0, sizeof(unsigned), ctx->stream));
+    if (h & TP_DERR_TIMEOUT) return tp_set_err(ctx, TP_E_TIMEOUT, "%s: a device-side wait timed out", where);
+    if (h & TP_DERR_INDEX) return tp_set_err(ctx, TP_E_ARG, "%s: face index outside [0, nv)", where);
+    if (h & TP_DERR_STACK) return tp_set_err(ctx, TP_E_CUDA, "%s: traversal stack overflow", where);
+    if (h & TP_DERR_NONFINITE)
+        return tp_set_err(ctx, TP_E_NONFINITE, "%s: degenerate triangle or non-finite coordinate", where);
+    return tp_set_err(ctx, TP_E_CUDA, "%s: device error 0x%x", where, h);
+}
 
 extern "C" {
 

@@ -186,6 +186,9 @@ tp_status tp_launch_sorted_soa(tp_ctx* ctx);
 tp_status tp_launch_flagged(tp_ctx* ctx, bool topology);
 tp_status tp_launch_fields(tp_ctx* ctx, const tp_params* prm, double* fw, double* fnu, double* fx);
 tp_status tp_launch_conf_tri(tp_ctx* ctx);
+tp_status take_device_error(tp_ctx* ctx, const char* where);  // read and clear the device error word
+tp_status tp_launch_mlp_tc(tp_ctx* ctx, const __nv_bfloat16* wb, const float* bias, const __nv_bfloat16* X,
+                           int64_t rows, float* kf, int raw);
 tp_status tp_launch_conf(tp_ctx* ctx, const tp_params* prm);
 tp_status tp_launch_energy_scaled(tp_ctx* ctx, double mul, double* d_out);
 tp_status tp_build_v2t(tp_ctx* ctx);

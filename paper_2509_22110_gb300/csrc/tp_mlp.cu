@@ -475,8 +475,27 @@ __global__ void __launch_bounds__(128) k_mlp_train(const __nv_bfloat16* __restri
     if (tid == 0) atomicAdd(&loss[0], S.lsum[0]);
 }
 
-// Forward pass only, with the inference arithmetic of the learned Barnes-Hut
-// correction (warp_mlp_rows32): 4 warps x 32 rows per block.
+// BF16 network rows [n][32] from host features [n][24] (normalised here
+// unless already normalised); column 31 (the training-range flag) set to 1.
+__global__ void k_rows_bf16(const float* __restrict__ X, int64_t n, int normalised, const float* __restrict__ norm,
+                            __nv_bfloat16* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n * MLP_NIP) return;
+    const int64_t r = i / MLP_NIP;
+    const int c = (int)(i % MLP_NIP);
+    float v = 0.f;
+    if (c < MLP_NI) {
+        v = X[r * MLP_NI + c];
+        if (!normalised) v = (v - norm[c]) / norm[MLP_NI + c];
+    } else if (c == MLP_NIP - 1) {
+        v = 1.f;
+    }
+    out[i] = __float2bfloat16_rn(v);
+}
+
+// Forward pass only, with the arithmetic of the learned Barnes-Hut
+// correction's register-resident mma.sync path (warp_mlp_rows32): 4 warps x
+// 32 rows per block.
 __global__ void __launch_bounds__(128) k_mlp_infer(const __nv_bfloat16* __restrict__ wb_g,
                                                    const float* __restrict__ bias_g, const float* __restrict__ norm,
                                                    const float* __restrict__ X, int64_t n, int normalised,
@@ -819,7 +838,7 @@ tp_status tp_far_eval(tp_ctx* ctx, const float* X, int64_t n, int normalised, co
     if (!ctx || !ctx->mlp || !X || n < 1) return TP_E_ARG;
     cudaSetDevice(ctx->device);
     tp_mlp_model* m = ctx->mlp;
-    if (!normalised && !m->have_norm) return tp_set_err(ctx, TP_E_STATE, "no normalisation");
+    if (!(normalised & 1) && !m->have_norm) return tp_set_err(ctx, TP_E_STATE, "no normalisation");
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem));
@@ -827,15 +846,34 @@ tp_status tp_far_eval(tp_ctx* ctx, const float* X, int64_t n, int normalised, co
     }
     float *dX = nullptr, *dT = nullptr, *dM = nullptr, *dY = nullptr;
     if (!tgt && !mask) {
-        // forward only: the inference kernel of the learned correction
+        // forward only: the inference kernels of the learned correction, the
+        // tensor-core (tcgen05) network, or with normalised = 2 or 3 (bit 1 set)
+        // the register-resident mma.sync one
+        const bool sync_path = normalised >= 2;
+        const int norm_in = normalised & 1;
         TP_TRY(tp_alloc_t(ctx, &dX, n * MLP_NI));
-        TP_TRY(tp_alloc_t(ctx, &dY, n * MLP_NO));
+        TP_TRY(tp_alloc_t(ctx, &dY, n * 8));
         TP_CU(cudaMemcpyAsync(dX, X, 4 * MLP_NI * n, cudaMemcpyHostToDevice, ctx->stream));
-        k_mlp_infer<<<(unsigned)((n + 127) / 128), 128, 0, ctx->stream>>>(m->wb, m->bias, m->norm, dX, n,
-                                                                          normalised, dY);
-        TP_CU(cudaGetLastError());
-        if (Y) TP_CU(cudaMemcpyAsync(Y, dY, 4 * MLP_NO * n, cudaMemcpyDeviceToHost, ctx->stream));
+        if (sync_path) {
+            k_mlp_infer<<<(unsigned)((n + 127) / 128), 128, 0, ctx->stream>>>(m->wb, m->bias, m->norm, dX, n,
+                                                                              norm_in, dY);
+            TP_CU(cudaGetLastError());
+            if (Y) TP_CU(cudaMemcpyAsync(Y, dY, 4 * MLP_NO * n, cudaMemcpyDeviceToHost, ctx->stream));
+        } else {
+            __nv_bfloat16* dR = nullptr;
+            TP_TRY(tp_alloc_t(ctx, &dR, n * MLP_NIP));
+            k_rows_bf16<<<(unsigned)((n * MLP_NIP + 255) / 256), 256, 0, ctx->stream>>>(dX, n, norm_in, m->norm, dR);
+            TP_TRY(tp_launch_mlp_tc(ctx, m->wb, m->bias, dR, n, dY, 1));
+            std::vector<float> y8(8 * n);
+            TP_CU(cudaMemcpyAsync(y8.data(), dY, 32 * n, cudaMemcpyDeviceToHost, ctx->stream));
+            TP_CU(cudaStreamSynchronize(ctx->stream));
+            if (Y)
+                for (int64_t r = 0; r < n; ++r)
+                    for (int c = 0; c < MLP_NO; ++c) Y[r * MLP_NO + c] = y8[r * 8 + c];
+            tp_free(ctx, dR);
+        }
         TP_CU(cudaStreamSynchronize(ctx->stream));
+        TP_TRY(take_device_error(ctx, "tp_far_eval"));
         if (grad) memset(grad, 0, 4 * MLP_NPARAM);
         if (loss) *loss = 0.0;
         tp_free(ctx, dX);
@@ -859,7 +897,7 @@ tp_status tp_far_eval(tp_ctx* ctx, const float* X, int64_t n, int normalised, co
     const float inv_msum = hl[1] > 0.0 ? (float)(1.0 / hl[1]) : 0.f;
     const unsigned blocks = (unsigned)((n + TB - 1) / TB);
     k_mlp_train<<<blocks, 128, sizeof(TrainSmem), ctx->stream>>>(m->wb, m->bias, m->norm, nullptr, dT, dM, n, n, 0,
-                                                                dX, normalised, inv_msum, m->grad, m->red, dY);
+                                                                dX, normalised & 1, inv_msum, m->grad, m->red, dY);
     TP_CU(cudaGetLastError());
     if (Y) TP_CU(cudaMemcpyAsync(Y, dY, 4 * MLP_NO * n, cudaMemcpyDeviceToHost, ctx->stream));
     if (grad) TP_CU(cudaMemcpyAsync(grad, m->grad, 4 * MLP_NPARAM, cudaMemcpyDeviceToHost, ctx->stream));

@@ -197,8 +197,8 @@ def test_model_file_roundtrip_and_errors(tp, ctx, tmp_path):
 
 
 def test_inference_forward_parity(tp, ctx, oracle_mod):
-    """The forward-only path (the inference kernel of TP_LEARNED evaluations,
-    activations kept in registers) against the FP64 oracle on BF16-rounded
+    """The forward-only paths (the tcgen05 network of TP_LEARNED evaluations and the
+    register-resident mma.sync variant) against the FP64 oracle on BF16-rounded
     weights and inputs, and against the training kernel's forward pass."""
     _tp = tp._tp
     rng = np.random.default_rng(4)
@@ -214,5 +214,8 @@ def test_inference_forward_parity(tp, ctx, oracle_mod):
     assert rel(Yi, Yo) <= 1e-2, rel(Yi, Yo)
     Yt, _, _ = _tp.tp_far_eval(ctx, X, normalised=True, tgt=np.zeros((n, 8), np.float32),
                                mask=np.zeros((n, 8), np.float32))
-    # same BF16 arithmetic in both kernels (summation order may differ)
+    # same BF16 arithmetic in all kernels (the order of the FP32 sums differs)
     assert rel(Yi, Yt) <= 2e-3, rel(Yi, Yt)
+    # the register-resident mma.sync variant of the inference network
+    Ys, _, _ = _tp.tp_far_eval(ctx, X, normalised=True, mma_sync=True)
+    assert rel(Ys, Yo) <= 1e-2 and rel(Ys, Yt) <= 2e-3 and rel(Ys, Yi) <= 2e-3, (rel(Ys, Yo), rel(Ys, Yt))
