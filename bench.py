@@ -70,6 +70,8 @@ def parse():
                     help="conf: the confinement energy (Eq. TPConf) of the conf_l7 workload")
     ap.add_argument("--far-model", default=None, help="trained far-field model (learned mode)")
     ap.add_argument("--theta", type=float, default=0.25)
+    ap.add_argument("--quad", type=int, default=1, choices=[1, 3, 6],
+                    help="quadrature points per triangle for both integrals (tp_set_quadrature)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -146,15 +148,19 @@ def measured_peaks():
         return {}
 
 
-def run_cpu_baseline(V, F, seconds):
-    """The FP64 oracle as it stands, on a bounded sample of target triangles."""
+def run_cpu_baseline(V, F, seconds, quad=1):
+    """The FP64 oracle as it stands, on a bounded sample of target elements (triangles,
+    or quadrature points with quad > 1: the oracle's expanded point set)."""
     import oracle
 
     oracle.build()
-    nt = F.shape[0]
     nth = oracle.nthreads_default()
     rng = np.random.default_rng(123)
-    x, nu, w = oracle.tri_data(V, F)
+    if quad == 1:
+        x, nu, w = oracle.tri_data(V, F)
+    else:
+        x, nu, w, F = oracle.quad_points(V, F, quad)
+    nt = F.shape[0]
     oracle.tri_accum(V, F, rng.choice(nt, nth, replace=False), soa=(x, nu, w), nthreads=nth)  # warm the pool
     cal = rng.choice(nt, 4 * nth, replace=False)
     t0 = time.perf_counter()
@@ -169,8 +175,8 @@ def run_cpu_baseline(V, F, seconds):
     dt = time.perf_counter() - t0
     val = m * (nt - 1) / dt
     return {"value": val, "unit": UNIT, "cores": nth, "kind": "oracle",
-            "sample": f"dPhi/d(w,nu,x) of {m} random target triangles against all {nt - 1} others "
-                      f"(both orderings, FP64), {dt:.1f} s; rate = targets*(nt-1)/s"}
+            "sample": f"dPhi/d(w,nu,x) of {m} random target elements against all {nt - 1} others "
+                      f"(both orderings, FP64, {quad} point(s) per triangle), {dt:.1f} s; rate = targets*(nt-1)/s"}
 
 
 def reference_arm(args):
@@ -404,6 +410,8 @@ def main():
         gd = torch.zeros_like(Vd)
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
     stream.synchronize()
+    if args.quad != 1:
+        tp.tp_set_quadrature(ctx, args.quad)
     tp.tp_mesh_upload(ctx, Vd, Fd)
     up_stats = tp.tp_get_stats(ctx)
 
@@ -492,6 +500,7 @@ def main():
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded mesh)",
             "config": {"workload": WORKLOADS[args.workload], "nt": nt, "nv": nv, "mode": args.mode,
+                       "quadrature_points_per_triangle": args.quad,
                        "theta": args.theta if mode != tp.TP_DIRECT else None, "q": 6, "p": 12,
                        "accumulation": "f64", "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
@@ -535,7 +544,7 @@ def main():
 
     tp.tp_destroy(ctx)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = run_cpu_baseline(V, F, args.cpu_seconds)
+        line["cpu_baseline"] = run_cpu_baseline(V, F, args.cpu_seconds, args.quad)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

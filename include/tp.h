@@ -93,6 +93,19 @@ const char* tp_last_error(const tp_ctx* ctx);
 tp_status tp_mesh_upload(tp_ctx* ctx, const void* V, int64_t nv, int v_dtype, const int32_t* F, int64_t nt,
                          uint32_t flags);
 
+/* Quadrature rule per triangle for the next full tp_mesh_upload (Sec. 3.1
+ * and Sec. 3.2 integrate both integrals with a rule per element): npoints = 1
+ * (the centroid, the default), 3 (degree 2: (2/3, 1/6, 1/6) and its
+ * permutations) or 6 (degree 4, Strang and Fix).  Both integrals use the same
+ * rule.  Every point becomes an element with its triangle's normal, the
+ * weight om_q times the area, and its triangle's vertices, so pairs of points
+ * of the same or of vertex-sharing triangles are left out.  With k > 1 points
+ * the element count (tp_stats.nt, the tree, tp_fields) is k times the
+ * triangle count, element i being point i % k of triangle i / k; the vertex
+ * gradient is the exact chain rule through the points.  TP_E_ARG for other
+ * counts.  The allocation-free entry point always uses the centroid. */
+tp_status tp_set_quadrature(tp_ctx* ctx, int npoints);
+
 /* Build the cluster tree used by TP_BH and TP_LEARNED from the current
  * positions: 30-bit Morton codes of the FP64 centroids (morton_bits must be
  * a multiple of 3, at most 30), radix tree of the sorted (code, index) keys,

@@ -38,6 +38,7 @@ from ._tp import (  # noqa: F401
     tp_last_error,
     tp_mesh_upload,
     tp_params_default,
+    tp_set_quadrature,
     tp_tree_build,
     tp_version,
 )
@@ -57,6 +58,7 @@ __all__ = [
     "tp_fields",
     "tp_get_stats",
     "tp_params_default",
+    "tp_set_quadrature",
 ]
 
 

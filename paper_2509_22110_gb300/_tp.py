@@ -79,6 +79,8 @@ def lib():
     L.tp_gradient.restype = i32
     L.tp_fields.argtypes = [vp, C.POINTER(tp_params), C.POINTER(C.c_double), vp, vp, vp, u32]
     L.tp_fields.restype = i32
+    L.tp_set_quadrature.argtypes = [vp, i32]
+    L.tp_set_quadrature.restype = i32
     L.tp_conf_upload.argtypes = [vp, vp, i64, i32, vp, i64, u32]
     L.tp_conf_upload.restype = i32
     L.tp_conf_gradient.argtypes = [vp, C.POINTER(tp_params), C.POINTER(C.c_double), vp, i32, u32]
@@ -254,6 +256,11 @@ def tp_fields(ctx, nt, params=None, fw=None, fnu=None, fx=None):
     _check(ctx, lib().tp_fields(ctx, C.byref(p), C.byref(e), _ptr(fw)[0], _ptr(fnu)[0], _ptr(fx)[0],
                                 TP_DEVICE_PTR if dev else 0))
     return e.value, fw, fnu, fx
+
+
+def tp_set_quadrature(ctx, npoints):
+    """Quadrature points per triangle (1, 3 or 6) for the next full mesh upload."""
+    _check(ctx, lib().tp_set_quadrature(ctx, int(npoints)))
 
 
 def tp_conf_upload(ctx, V, F):

@@ -34,7 +34,8 @@ __global__ void k_adjoint(const double* __restrict__ V, const int32_t* __restric
                           const int32_t* __restrict__ off, const int32_t* __restrict__ v2t,
                           const int32_t* __restrict__ iperm, const double* __restrict__ nu64,
                           const double* __restrict__ w64, const double* __restrict__ acc, int64_t nv, int64_t nt,
-                          int64_t ntp, double q, double pq, double scale, OutT* __restrict__ grad) {
+                          int64_t ntp, double q, double pq, double scale, OutT* __restrict__ grad,
+                          tp_quad_rule rule) {
     int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (v >= nv) return;
     double g[3] = {0.0, 0.0, 0.0};
@@ -60,15 +61,19 @@ __global__ void k_adjoint(const double* __restrict__ V, const int32_t* __restric
             e1[a] = a1[a] - a0[a];
             e2[a] = a2[a] - a0[a];
         }
-        const double len = 2.0 * w;
+        // element weight w = om_q |N| / 2: dPhi/dN gets om_q dPhi/dw nu / 2 (om = 1 for the centroid rule)
+        const int qp = rule.k > 1 ? (int)(T % rule.k) : 0;
+        const double om = rule.k > 1 ? rule.w[qp] : 1.0;
+        const double len = 2.0 * w / om;
         const double ndg = nu[0] * gn[0] + nu[1] * gn[1] + nu[2] * gn[2];
         double G[3];
-        for (int a = 0; a < 3; ++a) G[a] = 0.5 * gw * nu[a] + (gn[a] - nu[a] * ndg) / len;
+        for (int a = 0; a < 3; ++a) G[a] = 0.5 * om * gw * nu[a] + (gn[a] - nu[a] * ndg) / len;
         double c1[3], c2[3];
         cross3(e2, G, c1);  // dPhi/de1
         cross3(G, e1, c2);  // dPhi/de2
         for (int a = 0; a < 3; ++a) {
-            double t = gx[a] / 3.0;
+            // position x = sum_i l_i v_i: dPhi/dv_corner gets l_corner dPhi/dx (1/3 for the centroid)
+            double t = rule.k > 1 ? rule.bary[qp][corner] * gx[a] : gx[a] / 3.0;
             if (corner == 0) t -= c1[a] + c2[a];
             else if (corner == 1) t += c1[a];
             else t += c2[a];
@@ -133,11 +138,11 @@ tp_status tp_launch_adjoint(tp_ctx* ctx, const tp_params* prm, void* grad, int g
     if (g_dtype == TP_DTYPE_F64)
         k_adjoint<double><<<blocks, 256, 0, ctx->stream>>>(ctx->V64, ctx->F, ctx->v2t_off, ctx->v2t, ctx->iperm,
                                                            ctx->nu64, ctx->w64, ctx->acc, nv, ctx->nt, ctx->ntp, q,
-                                                           pq, prm->scale, static_cast<double*>(grad));
+                                                           pq, prm->scale, static_cast<double*>(grad), ctx->quad);
     else
         k_adjoint<float><<<blocks, 256, 0, ctx->stream>>>(ctx->V64, ctx->F, ctx->v2t_off, ctx->v2t, ctx->iperm,
                                                           ctx->nu64, ctx->w64, ctx->acc, nv, ctx->nt, ctx->ntp, q,
-                                                          pq, prm->scale, static_cast<float*>(grad));
+                                                          pq, prm->scale, static_cast<float*>(grad), ctx->quad);
     ++ctx->nlaunch;
     TP_CU(cudaGetLastError());
     return TP_OK;

@@ -139,6 +139,7 @@ void release_mesh(tp_ctx* ctx) {
     free_ptr(ctx, ctx->tbox);
     free_ptr(ctx, ctx->gradbuf);
     free_ptr(ctx, ctx->fieldbuf);
+    free_ptr(ctx, ctx->F_tri);
     free_ptr(ctx, ctx->vtmp);
     tp_tree& t = ctx->tree;
     free_ptr(ctx, t.codes);
@@ -325,10 +326,20 @@ tp_status tp_mesh_upload(tp_ctx* ctx, const void* V, int64_t nv, int v_dtype, co
     }
     if (nv > 0 && !V) return tp_set_err(ctx, TP_E_ARG, "V is NULL");
     if (!posonly && nt > 0 && !F) return tp_set_err(ctx, TP_E_ARG, "F is NULL");
+    int64_t nt_tri = nt;  // caller's triangles; the elements are triangles x quadrature points
     if (!posonly) {
+        const int k = ctx->quad_next.k;
+        if (nt * k >= (int64_t)1 << 30) return tp_set_err(ctx, TP_E_ARG, "mesh too large for the quadrature rule");
+        ctx->quad = ctx->quad_next;
+        nt = nt_tri * k;
         TP_TRY(ensure_buffers(ctx, std::max<int64_t>(nv, 1), std::max<int64_t>(nt, 1)));
+        if (k > 1) {
+            free_ptr(ctx, ctx->F_tri);
+            TP_TRY(tp_alloc_t(ctx, &ctx->F_tri, 3 * std::max<int64_t>(nt_tri, 1)));
+        }
         ctx->nv = nv;
         ctx->nt = nt;
+        ctx->nt_tri = nt_tri;
         ctx->ntp = ((nt + TP_SUPER - 1) / TP_SUPER) * TP_SUPER;
         ctx->nsup = ctx->ntp / TP_SUPER;
         ctx->tree.valid = false;
@@ -350,9 +361,15 @@ tp_status tp_mesh_upload(tp_ctx* ctx, const void* V, int64_t nv, int v_dtype, co
         k_check_finite_v<<<(unsigned)((3 * nv + 255) / 256), 256, 0, ctx->stream>>>(ctx->V64, 3 * nv, ctx->derr);
         ++ctx->nlaunch;
     }
-    if (!posonly && nt > 0)
-        TP_CU(cudaMemcpyAsync(ctx->F, F, (size_t)(3 * nt) * 4, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                              ctx->stream));
+    if (!posonly && nt > 0) {
+        const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        if (ctx->quad.k == 1) {
+            TP_CU(cudaMemcpyAsync(ctx->F, F, (size_t)(3 * nt) * 4, kind, ctx->stream));
+        } else {
+            TP_CU(cudaMemcpyAsync(ctx->F_tri, F, (size_t)(3 * nt_tri) * 4, kind, ctx->stream));
+            TP_TRY(tp_launch_expand_faces(ctx));
+        }
+    }
     if (nt > 0) {
         TP_TRY(tp_launch_tri_data(ctx));
         if (!posonly) {
@@ -526,6 +543,39 @@ tp_status tp_fields(tp_ctx* ctx, const tp_params* params, double* energy_out, do
     ctx->err.clear();
     const FieldOut fo{fw, fnu, fx};
     return run_eval(ctx, params, true, nullptr, TP_DTYPE_F64, flags, energy_out, &fo);
+}
+
+tp_status tp_set_quadrature(tp_ctx* ctx, int npoints) {
+    if (!ctx) return TP_E_ARG;
+    ctx->err.clear();
+    tp_quad_rule r{};
+    r.k = npoints;
+    if (npoints == 1) {
+        r.bary[0][0] = r.bary[0][1] = r.bary[0][2] = 1.0 / 3.0;
+        r.w[0] = 1.0;
+    } else if (npoints == 3) {
+        // degree 2: the points (2/3, 1/6, 1/6) and permutations, equal weights
+        for (int q = 0; q < 3; ++q) {
+            for (int j = 0; j < 3; ++j) r.bary[q][j] = j == q ? 2.0 / 3.0 : 1.0 / 6.0;
+            r.w[q] = 1.0 / 3.0;
+        }
+    } else if (npoints == 6) {
+        // degree 4 (Strang and Fix): two orbits (a, a, 1 - 2a) with closed-form a and weights
+        const double s10 = std::sqrt(10.0), rr = std::sqrt(38.0 - 44.0 * std::sqrt(2.0 / 5.0));
+        const double t = std::sqrt(213125.0 - 53320.0 * s10);
+        const double a[2] = {(8.0 - s10 + rr) / 18.0, (8.0 - s10 - rr) / 18.0};
+        const double w[2] = {(620.0 + t) / 3720.0, (620.0 - t) / 3720.0};
+        for (int o = 0; o < 2; ++o)
+            for (int j = 0; j < 3; ++j) {
+                const int q = 3 * o + j;
+                for (int m = 0; m < 3; ++m) r.bary[q][m] = m == j ? 1.0 - 2.0 * a[o] : a[o];
+                r.w[q] = w[o];
+            }
+    } else {
+        return tp_set_err(ctx, TP_E_ARG, "quadrature with %d points (supported: 1, 3, 6)", npoints);
+    }
+    ctx->quad_next = r;
+    return TP_OK;
 }
 
 tp_status tp_conf_upload(tp_ctx* ctx, const void* V, int64_t nv, int v_dtype, const int32_t* F, int64_t nt,

@@ -67,6 +67,16 @@ struct tp_tree {
 
 struct tp_mlp_model;
 
+// Quadrature rule per triangle (Sec. 3.1, 3.2): k points with barycentric
+// coordinates bary[q][0..2] and weights w[q] (summing to 1).  k = 1 is the
+// centroid rule; every point is then treated as an element carrying its
+// triangle's vertices (for the exclusion) and normal.
+struct tp_quad_rule {
+    int k;
+    double bary[6][3];
+    double w[6];
+};
+
 // A run of the learned far field's pair list: far nodes of one target leaf
 // (leaf index li) at far_list[start, start + len), in traversal order.
 struct tp_far_run {
@@ -81,8 +91,12 @@ struct tp_ctx {
     cudaStream_t stream = nullptr;
     std::string err;
 
-    int64_t nv = 0, nt = 0, ntp = 0, nsup = 0;
+    int64_t nv = 0, nt = 0, ntp = 0, nsup = 0;  // nt: elements = triangles x quadrature points
     bool have_mesh = false;
+    tp_quad_rule quad{1, {{1.0 / 3, 1.0 / 3, 1.0 / 3}}, {1.0}};       // rule of the uploaded mesh
+    tp_quad_rule quad_next{1, {{1.0 / 3, 1.0 / 3, 1.0 / 3}}, {1.0}};  // rule for the next full upload
+    int64_t nt_tri = 0;             // triangles of the uploaded mesh
+    int32_t* F_tri = nullptr;       // [nt_tri][3] caller's faces (quadrature rules with k > 1)
 
     // mesh
     double* V64 = nullptr;
@@ -186,6 +200,7 @@ tp_status tp_launch_sorted_soa(tp_ctx* ctx);
 tp_status tp_launch_flagged(tp_ctx* ctx, bool topology);
 tp_status tp_launch_fields(tp_ctx* ctx, const tp_params* prm, double* fw, double* fnu, double* fx);
 tp_status tp_launch_conf_tri(tp_ctx* ctx);
+tp_status tp_launch_expand_faces(tp_ctx* ctx);
 tp_status take_device_error(tp_ctx* ctx, const char* where);  // read and clear the device error word
 tp_status tp_launch_mlp_tc(tp_ctx* ctx, const __nv_bfloat16* wb, const float* bias, const __nv_bfloat16* X,
                            int64_t rows, float* kf, int raw);

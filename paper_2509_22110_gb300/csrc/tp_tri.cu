@@ -20,9 +20,14 @@
 
 namespace {
 
+// Per element: position, unit normal and weight.  With the centroid rule the
+// element is the triangle, x = ((v0 + v1) + v2) / 3 and w = |N| / 2; with a
+// k-point rule element i is point q = i % k of its triangle (whose vertices
+// F[i] carries), x = (l0 v0 + l1 v1) + l2 v2 and w = om_q |N| / 2; every
+// operation separately rounded (the oracle's order).
 __global__ void k_tri_data(const double* __restrict__ V, const int32_t* __restrict__ F, int64_t nt, int64_t nv,
                            double* __restrict__ x64, double* __restrict__ nu64, double* __restrict__ w64,
-                           unsigned* derr) {
+                           unsigned* derr, tp_quad_rule rule) {
     int64_t T = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (T >= nt) return;
     int32_t i0 = F[3 * T], i1 = F[3 * T + 1], i2 = F[3 * T + 2];
@@ -39,9 +44,14 @@ __global__ void k_tri_data(const double* __restrict__ V, const int32_t* __restri
     const double* b = V + 3 * (int64_t)i1;
     const double* c = V + 3 * (int64_t)i2;
     double e1[3], e2[3];
+    const int q = rule.k > 1 ? (int)(T % rule.k) : 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        x64[k * nt + T] = __ddiv_rn(__dadd_rn(__dadd_rn(a[k], b[k]), c[k]), 3.0);
+        if (rule.k == 1)
+            x64[k * nt + T] = __ddiv_rn(__dadd_rn(__dadd_rn(a[k], b[k]), c[k]), 3.0);
+        else
+            x64[k * nt + T] = __dadd_rn(__dadd_rn(__dmul_rn(rule.bary[q][0], a[k]), __dmul_rn(rule.bary[q][1], b[k])),
+                                        __dmul_rn(rule.bary[q][2], c[k]));
         e1[k] = __dsub_rn(b[k], a[k]);
         e2[k] = __dsub_rn(c[k], a[k]);
     }
@@ -50,10 +60,20 @@ __global__ void k_tri_data(const double* __restrict__ V, const int32_t* __restri
     double N2 = __dsub_rn(__dmul_rn(e1[0], e2[1]), __dmul_rn(e1[1], e2[0]));
     double len = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(N0, N0), __dmul_rn(N1, N1)), __dmul_rn(N2, N2)));
     if (!(len > 0.0) || !isfinite(len)) tp_dev_error(derr, TP_DERR_NONFINITE);
-    w64[T] = __dmul_rn(0.5, len);
+    w64[T] = rule.k == 1 ? __dmul_rn(0.5, len) : __dmul_rn(rule.w[q], __dmul_rn(0.5, len));
     nu64[0 * nt + T] = __ddiv_rn(N0, len);
     nu64[1 * nt + T] = __ddiv_rn(N1, len);
     nu64[2 * nt + T] = __ddiv_rn(N2, len);
+}
+
+// faces of the elements: every quadrature point carries its triangle's vertices
+__global__ void k_expand_faces(const int32_t* __restrict__ Ft, int64_t nt_tri, int k, int32_t* __restrict__ F) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nt_tri * k) return;
+    const int64_t T = i / k;
+    F[3 * i] = Ft[3 * T];
+    F[3 * i + 1] = Ft[3 * T + 1];
+    F[3 * i + 2] = Ft[3 * T + 2];
 }
 
 // per-block min/max of the centroids (6 values), then a final single-block pass
@@ -336,10 +356,18 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 
 }  // namespace
 
+tp_status tp_launch_expand_faces(tp_ctx* ctx) {
+    const int64_t n = ctx->nt_tri * ctx->quad.k;
+    k_expand_faces<<<blocks_for(n, 256), 256, 0, ctx->stream>>>(ctx->F_tri, ctx->nt_tri, ctx->quad.k, ctx->F);
+    ++ctx->nlaunch;
+    TP_CU(cudaGetLastError());
+    return TP_OK;
+}
+
 tp_status tp_launch_tri_data(tp_ctx* ctx) {
     const int64_t nt = ctx->nt;
     k_tri_data<<<blocks_for(nt, 256), 256, 0, ctx->stream>>>(ctx->V64, ctx->F, nt, ctx->nv, ctx->x64, ctx->nu64,
-                                                             ctx->w64, ctx->derr);
+                                                             ctx->w64, ctx->derr, ctx->quad);
     ++ctx->nlaunch;
     int nb = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (nt + 255) / 256));
     k_bounds_partial<<<nb, 256, 0, ctx->stream>>>(ctx->x64, nt, ctx->red);
