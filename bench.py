@@ -82,6 +82,19 @@ def parse():
     return ap.parse_args()
 
 
+def job_throughput(local_ms, ws, steps, units_per_rank, device, tdist=None):
+    """Whole-job time and throughput of replicas: the timed region of every rank
+    ends at a barrier, the job takes the slowest rank's time, and the value is the
+    units all ranks processed divided by it.  Returns (max_ms, units per second)."""
+    import torch
+
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if ws > 1:
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    return max_ms, ws * steps * units_per_rank / (max_ms / 1e3)
+
+
 def dist_info():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -461,14 +474,10 @@ def main():
     if ws > 1:
         tdist.barrier()
     clk = clocks.stop()
-    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    t_local = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        tdist.all_reduce(t_local, op=tdist.ReduceOp.MAX)
-    total_ms = float(t_local.item())
-    ms_step = total_ms / args.steps
     pairs = direct_pairs
-    value = ws * args.steps * pairs / (total_ms / 1e3)
+    total_ms, value = job_throughput(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), ws, args.steps, pairs,
+                                     dev, tdist)
+    ms_step = total_ms / args.steps
 
     # roofline of the dominant kernel (unmasked direct pair kernel)
     roof = None
