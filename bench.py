@@ -45,9 +45,13 @@ FLOPS_PER_UNORDERED_PAIR = 76
 # flops (the hi/lo cancellation correction, 6 FADD, not counted).
 FLOPS_PER_CONF_PAIR = 38
 FP32_LANES_PER_SM = 128
-# DRAM bytes per launch of the dominant kernel from the committed ncu
-# capture (profiles/); None until a capture of the current kernel exists.
-NCU_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) per launch of the dominant kernel on the default
+# workload, from the one-pass ncu capture summarised in
+# profiles/k_pairs_grad_traffic_sh_l7.md (null it when that kernel changes).
+NCU_TRAFFIC_BYTES = 60.04e6
+
+# far-field model trained by paper_2509_22110_gb300.far_train (command in the design notes)
+DEFAULT_FAR_MODEL = os.path.join(ROOT, "paper_2509_22110_gb300", "far_model_l7.bin")
 
 WORKLOADS = {
     "sh_l7": "icosphere level 7 (327,680 triangles) with seeded SH deformation l<=12, a_lm~N(0,(0.05/l)^2), seed 2",
@@ -68,7 +72,8 @@ def parse():
     ap.add_argument("--workload", default="sh_l7", choices=sorted(WORKLOADS))
     ap.add_argument("--mode", default="direct", choices=["direct", "bh", "learned", "conf"],
                     help="conf: the confinement energy (Eq. TPConf) of the conf_l7 workload")
-    ap.add_argument("--far-model", default=None, help="trained far-field model (learned mode)")
+    ap.add_argument("--far-model", default=DEFAULT_FAR_MODEL,
+                    help="trained far-field model (learned mode; default: the packaged level-7 model)")
     ap.add_argument("--theta", type=float, default=0.25)
     ap.add_argument("--quad", type=int, default=1, choices=[1, 3, 6],
                     help="quadrature points per triangle for both integrals (tp_set_quadrature)")
@@ -246,7 +251,7 @@ def inloop(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(dev)
     ctx = tp.tp_create(0, stream.cuda_stream)
-    learned = bool(args.far_model)
+    learned = bool(args.far_model) and os.path.exists(args.far_model)
     if learned:
         tp.tp_far_model_load(ctx, args.far_model)
     Vd = torch.tensor(V, device=dev)
@@ -413,7 +418,7 @@ def main():
     ctx = tp.tp_create(local, stream.cuda_stream)
     mode = {"direct": tp.TP_DIRECT, "bh": tp.TP_BH, "learned": tp.TP_LEARNED}[args.mode]
     if mode == tp.TP_LEARNED:
-        if not args.far_model:
+        if not args.far_model or not os.path.exists(args.far_model):
             raise SystemExit("--mode learned needs --far-model (python -m paper_2509_22110_gb300.far_train)")
         tp.tp_far_model_load(ctx, args.far_model)
     prm = tp.tp_params_default(mode=mode, theta=args.theta)
