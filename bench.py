@@ -48,7 +48,7 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per launch of the dominant kernel on the default
 # workload, from the one-pass ncu capture summarised in
 # profiles/k_pairs_grad_traffic_sh_l7.md (null it when that kernel changes).
-NCU_TRAFFIC_BYTES = 60.04e6
+NCU_TRAFFIC_BYTES = 61.01e6
 
 # far-field model trained by paper_2509_22110_gb300.far_train (command in the design notes)
 DEFAULT_FAR_MODEL = os.path.join(ROOT, "paper_2509_22110_gb300", "far_model_l7.bin")

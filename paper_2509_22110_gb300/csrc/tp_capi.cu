@@ -134,6 +134,13 @@ void release_mesh(tp_ctx* ctx) {
     free_ptr(ctx, ctx->adjbm);
     free_ptr(ctx, ctx->bmask);
     free_ptr(ctx, ctx->mlist);
+    free_ptr(ctx, ctx->item_index);
+    free_ptr(ctx, ctx->xeff);
+    free_ptr(ctx, ctx->xbase);
+    free_ptr(ctx, ctx->xcount);
+    free_ptr(ctx, ctx->xmask);
+    free_ptr(ctx, ctx->xptrs);
+    ctx->x_cap = ctx->x_item_cap = ctx->x_slots = 0;
     free_ptr(ctx, ctx->plist);
     free_ptr(ctx, ctx->flist);
     free_ptr(ctx, ctx->tbox);

@@ -126,7 +126,11 @@ struct DirectArgs {
     int64_t ntp;
     int edge_only;
     unsigned* derr;
-    double* partial;          // per-block energy partials (energy kernel)
+    // energy kernel: per-block energy partials; masked gradient kernel: a device
+    // array of three pointers to the exclusion bits (xmask [slot][128 targets][4
+    // words], xeff per masked item, xbase per masked item).  One field serves
+    // both so that the argument block of the other kernels stays as it is.
+    double* partial;
 };
 
 struct SrcRec {
@@ -359,7 +363,7 @@ __device__ __forceinline__ int3 load_face(const int32_t* Fs, int64_t k) {
 
 // Work item fetched from the dynamic queue: kind and super-tile pair.
 struct Item {
-    int kind, I, J;
+    int kind, I, J, m;  // m: position in the masked list (masked items)
 };
 
 __device__ __forceinline__ Item decode_item(const DirectArgs& A, unsigned w) {
@@ -380,6 +384,7 @@ __device__ __forceinline__ Item decode_item(const DirectArgs& A, unsigned w) {
     }
     it.I = e >> 16;
     it.J = e & 0xffff;
+    it.m = (int)w;
     return it;
 }
 
@@ -405,7 +410,9 @@ struct ChunkPipe {
     }
 };
 
-// block-wide fetch of the next item (thread 0 takes it from the queue)
+// block-wide fetch of the next item (thread 0 takes it from the queue); WITH_M
+// also passes the item's position in the masked list
+template <bool WITH_M>
 __device__ __forceinline__ Item fetch_item(const DirectArgs& A, int* s_item) {
     if (threadIdx.x == 0) {
         const unsigned w = atomicAdd(A.work, 1u);
@@ -413,12 +420,14 @@ __device__ __forceinline__ Item fetch_item(const DirectArgs& A, int* s_item) {
         s_item[0] = it.kind;
         s_item[1] = it.I;
         s_item[2] = it.J;
+        if (WITH_M) s_item[3] = it.m;
     }
     __syncthreads();
     Item it;
     it.kind = s_item[0];
     it.I = s_item[1];
     it.J = s_item[2];
+    it.m = WITH_M ? s_item[3] : 0;
     __syncthreads();  // s_item may be overwritten by the next fetch
     return it;
 }
@@ -518,7 +527,7 @@ __device__ __forceinline__ void fold_energy(Acc8 (&at)[NP], EFold (&ef)[NP]) {
 
 // The 12 chunks of one item for one item kind; target partials in `at`.
 template <int Q, int KIND, int W, int NP, int PF>
-__device__ __forceinline__ bool grad_item(const DirectArgs& A, ChunkPipe& pipe, float* sacc, int I, int J,
+__device__ __forceinline__ bool grad_item(const DirectArgs& A, ChunkPipe& pipe, float* sacc, int I, int J, int m,
                                           const TgtPair (&tp)[NP], Acc8 (&at)[NP], EFold (&e64)[NP], int warp,
                                           int lane, int pbase) {
     constexpr bool LO = KIND != K_FAST;
@@ -556,8 +565,56 @@ __device__ __forceinline__ bool grad_item(const DirectArgs& A, ChunkPipe& pipe, 
             }
         }
         float* wacc = sacc + warp * TP_CHUNK * TP_NACC;
-        if (masked) {
-            // masked items: per-pair exclusion test (no software pipeline: register budget)
+        if (masked && !A.edge_only) {
+            // exclusion bits of this block: 128 bits per target of the lane, bit s set
+            // where (target, source s) is not admitted
+            const uint64_t* xp = reinterpret_cast<const uint64_t*>(A.partial);
+            const uint32_t* xmask = reinterpret_cast<const uint32_t*>(xp[0]);
+            const unsigned* e = reinterpret_cast<const unsigned*>(xp[1]) + (int64_t)m * TP_BMASK_WORDS;
+            const int32_t* xbase = reinterpret_cast<const int32_t*>(xp[2]);
+            const int blk = warp * TP_NBLK + c;
+            int r = 0;
+            for (int wd = 0; wd < (blk >> 5); ++wd) r += __popc(e[wd]);
+            r += __popc(e[blk >> 5] & ((1u << (blk & 31)) - 1u));
+            const int64_t slot = (int64_t)xbase[m] + r;
+            uint4 xb[NP][2];
+#pragma unroll
+            for (int P = 0; P < NP; ++P)
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    xb[P][h] = *reinterpret_cast<const uint4*>(
+                        xmask + (slot * TP_CHUNK + (tl[P][h] - TP_CHUNK * warp)) * 4);
+#pragma unroll
+            for (int wd = 0; wd < 4; ++wd) {
+                uint32_t xw[NP][2];
+#pragma unroll
+                for (int P = 0; P < NP; ++P)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+                        xw[P][h] = wd == 0 ? xb[P][h].x : wd == 1 ? xb[P][h].y : wd == 2 ? xb[P][h].z : xb[P][h].w;
+#pragma unroll 1
+                for (int i = 0; i < 32; ++i) {
+                    const int s = 32 * wd + i;
+                    SrcRec sr;
+                    load_src<LO>(cb + s * TP_SRCW, sr);
+                    Acc8 as;
+                    float2 valid[NP];
+#pragma unroll
+                    for (int P = 0; P < NP; ++P)
+                        valid[P] = make_float2((xw[P][0] >> i) & 1u ? 0.f : 1.f, (xw[P][1] >> i) & 1u ? 0.f : 1.f);
+                    pair_grad<Q, KIND, true>(tp[0], sr, at[0], as, valid[0]);
+#pragma unroll
+                    for (int P = 1; P < NP; ++P) pair_grad<Q, KIND, false>(tp[P], sr, at[P], as, valid[P]);
+                    float v[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) v[k] = as.v[k].x + as.v[k].y;
+                    const float rr = warp_transpose_reduce8(v, lane);
+                    if ((lane & 3) == 0) wacc[s * TP_NACC + ((lane >> 2) & 7)] = rr;
+                }
+            }
+            fold_energy<NP>(at, e64);
+        } else if (masked) {
+            // exclusion by comparing vertex indices (edge-only exclusion)
 #pragma unroll 1
             for (int s = 0; s < TP_CHUNK; ++s) {
                 SrcRec sr;
@@ -674,7 +731,7 @@ __global__ void __launch_bounds__(GradShape<MASKQ>::THREADS, 1) k_pairs_grad(Dir
     int rowI = -1;
     const int pbase = warp * 32 * NP + lane;  // pair index within the super-tile: pbase + 32 P
     while (true) {
-        const Item it = fetch_item(A, s_item);
+        const Item it = fetch_item<MASKQ>(A, s_item);
         if (it.kind < 0) break;
         if (tid == 0) pipe.issue(A, it.J, 0, 0);
         if (it.I != rowI) {
@@ -693,10 +750,10 @@ __global__ void __launch_bounds__(GradShape<MASKQ>::THREADS, 1) k_pairs_grad(Dir
         }
         bool ok;
         if constexpr (MASKQ) {
-            ok = grad_item<Q, K_MASKED, W, NP, GradShape<MASKQ>::PF>(A, pipe, sacc, it.I, it.J, tp, at, e64, warp, lane, pbase);
+            ok = grad_item<Q, K_MASKED, W, NP, GradShape<MASKQ>::PF>(A, pipe, sacc, it.I, it.J, it.m, tp, at, e64, warp, lane, pbase);
         } else {
-            if (it.kind == K_FAST) ok = grad_item<Q, K_FAST, W, NP, GradShape<MASKQ>::PF>(A, pipe, sacc, it.I, it.J, tp, at, e64, warp, lane, pbase);
-            else ok = grad_item<Q, K_PRECISE, W, NP, GradShape<MASKQ>::PF>(A, pipe, sacc, it.I, it.J, tp, at, e64, warp, lane, pbase);
+            if (it.kind == K_FAST) ok = grad_item<Q, K_FAST, W, NP, GradShape<MASKQ>::PF>(A, pipe, sacc, it.I, it.J, it.m, tp, at, e64, warp, lane, pbase);
+            else ok = grad_item<Q, K_PRECISE, W, NP, GradShape<MASKQ>::PF>(A, pipe, sacc, it.I, it.J, it.m, tp, at, e64, warp, lane, pbase);
         }
         if (!ok) {
             if (tid == 0) tp_dev_error(A.derr, TP_DERR_TIMEOUT);
@@ -793,7 +850,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_pairs_energy(DirectArgs A) {
     TgtPair tp[2];
     int rowI = -1;
     while (true) {
-        const Item it = fetch_item(A, s_item);
+        const Item it = fetch_item<false>(A, s_item);
         if (it.kind < 0) break;
         if (tid == 0) pipe.issue(A, it.J, 0, 0);
         if (it.I != rowI) {
@@ -906,6 +963,7 @@ tp_status launch_grad_q(tp_ctx* ctx, DirectArgs A) {
         DirectArgs M = A;
         M.np = M.nf = 0;
         M.work = ctx->work + 1;
+        M.partial = reinterpret_cast<double*>(ctx->xptrs);
         const int grid = (int)std::min<int64_t>(ctx->num_sms, ctx->n_masked);
         k_pairs_grad<Q, true><<<grid, GradShape<true>::THREADS, GradShape<true>::SMEM, ctx->stream>>>(M);
         ++ctx->nlaunch;

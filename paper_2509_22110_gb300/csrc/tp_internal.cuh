@@ -125,6 +125,17 @@ struct tp_ctx {
     unsigned* bmask = nullptr;      // [nsup*nsup][TP_BMASK_WORDS]: per super-tile pair (I, J), bit i*TP_NBLK+j set
                                     // when target block i of I and source block j of J hold a vertex-sharing pair
     int32_t* mlist = nullptr;       // compact list of masked super-tile pairs (I,J): a vertex-sharing pair inside
+                                    // (sorted, so the order does not change between uploads)
+    // exclusion bits of the masked blocks: per masked item m the blocks that need a per-pair test (xeff,
+    // TP_BMASK_WORDS words), their first slot xbase[m]; per slot and target of the block 128 bits, set
+    // where the pair is not admitted (shares a vertex; on diagonal blocks also source <= target)
+    int32_t* item_index = nullptr;  // [nsup*nsup] masked item of (I, J), -1 for others
+    unsigned* xeff = nullptr;       // [n_masked][TP_BMASK_WORDS]
+    int32_t* xbase = nullptr;       // [n_masked + 1]
+    int32_t* xcount = nullptr;      // [n_masked + 1] scratch of the prefix sum
+    uint32_t* xmask = nullptr;      // [slots][128][4]
+    int64_t x_slots = 0, x_cap = 0, x_item_cap = 0;
+    uint64_t* xptrs = nullptr;      // [3] device copy of (xmask, xeff, xbase) for the masked kernel
     int32_t* plist = nullptr;       // compact list of unmasked pairs of nearby super-tiles (hi/lo centroids)
     int32_t* flist = nullptr;       // compact list of the remaining (fast) super-tile pairs
     int32_t* mcount = nullptr;      // [10]: counts of mlist, plist, 3 u64 pair counts (fast, precise, masked), count of flist
@@ -201,6 +212,7 @@ tp_status tp_launch_flagged(tp_ctx* ctx, bool topology);
 tp_status tp_launch_fields(tp_ctx* ctx, const tp_params* prm, double* fw, double* fnu, double* fx);
 tp_status tp_launch_conf_tri(tp_ctx* ctx);
 tp_status tp_launch_expand_faces(tp_ctx* ctx);
+tp_status tp_build_exclusion_bits(tp_ctx* ctx);
 tp_status take_device_error(tp_ctx* ctx, const char* where);  // read and clear the device error word
 tp_status tp_launch_mlp_tc(tp_ctx* ctx, const __nv_bfloat16* wb, const float* bias, const __nv_bfloat16* X,
                            int64_t rows, float* kf, int raw);

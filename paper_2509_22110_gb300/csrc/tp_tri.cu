@@ -434,6 +434,167 @@ tp_status tp_build_v2t(tp_ctx* ctx) {
     return TP_OK;
 }
 
+// ------------------------------------------------------------ exclusion bits of masked blocks
+__global__ void k_item_index(const int32_t* __restrict__ mlist, int n_masked, int nsup, int32_t* __restrict__ idx) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n_masked) return;
+    const int I = mlist[m] >> 16, J = mlist[m] & 0xffff;
+    idx[(int64_t)I * nsup + J] = m;
+}
+
+// blocks of masked item m that take the per-pair test: on a diagonal item the
+// blocks level with the diagonal and those above it holding a vertex-sharing
+// pair (blocks below are skipped), elsewhere the blocks holding one
+__global__ void k_xeff(const int32_t* __restrict__ mlist, int n_masked, int nsup, const unsigned* __restrict__ bmask,
+                       unsigned* __restrict__ xeff, int32_t* __restrict__ xcount) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m > n_masked) return;
+    if (m == n_masked) {
+        xcount[m] = 0;
+        return;
+    }
+    const int I = mlist[m] >> 16, J = mlist[m] & 0xffff;
+    const unsigned* bm = bmask + ((int64_t)I * nsup + J) * TP_BMASK_WORDS;
+    int cnt = 0;
+    for (int wd = 0; wd < TP_BMASK_WORDS; ++wd) {
+        unsigned v = 0;
+        for (int bit = 0; bit < 32; ++bit) {
+            const int blk = 32 * wd + bit;
+            if (blk >= TP_NBLK * TP_NBLK) break;
+            const int w = blk / TP_NBLK, c = blk % TP_NBLK;
+            const bool set = (bm[wd] >> bit) & 1u;
+            const bool use = I == J ? (c == w || (c > w && set)) : set;
+            if (use) v |= 1u << bit;
+        }
+        xeff[(int64_t)m * TP_BMASK_WORDS + wd] = v;
+        cnt += __popc(v);
+    }
+    xcount[m] = cnt;
+}
+
+// slot of block blk of masked item m: its first slot plus the used blocks before blk
+__device__ __forceinline__ int64_t x_slot(const unsigned* xeff, const int32_t* xbase, int m, int blk) {
+    const unsigned* e = xeff + (int64_t)m * TP_BMASK_WORDS;
+    int r = 0;
+    for (int wd = 0; wd < blk >> 5; ++wd) r += __popc(e[wd]);
+    r += __popc(e[blk >> 5] & ((1u << (blk & 31)) - 1u));
+    return (int64_t)xbase[m] + r;
+}
+
+// the vertex-sharing pairs: every element and each element touching one of its
+// vertices (target = the earlier in Morton order)
+__global__ void k_xmask_pairs(const int32_t* __restrict__ F, const int32_t* __restrict__ perm,
+                              const int32_t* __restrict__ iperm, const int32_t* __restrict__ off,
+                              const int32_t* __restrict__ v2t, int64_t nt, int nsup,
+                              const int32_t* __restrict__ item_index, const unsigned* __restrict__ xeff,
+                              const int32_t* __restrict__ xbase, uint32_t* __restrict__ xmask) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= nt) return;
+    const int64_t T = perm[k];
+    for (int c = 0; c < 3; ++c) {
+        const int32_t v = F[3 * T + c];
+        for (int32_t e = off[v]; e < off[v + 1]; ++e) {
+            const int64_t ks = iperm[v2t[e] >> 2];
+            const int64_t kt = k < ks ? k : ks, kss = k < ks ? ks : k;
+            const int a = (int)(kt / TP_SUPER), b = (int)(kss / TP_SUPER);
+            const int m = item_index[(int64_t)a * nsup + b];
+            if (m < 0) continue;  // cannot happen: the pair makes the item masked
+            const int tl = (int)(kt % TP_SUPER), sl = (int)(kss % TP_SUPER);
+            const int blk = (tl / TP_CHUNK) * TP_NBLK + sl / TP_CHUNK;
+            const int64_t slot = x_slot(xeff, xbase, m, blk);
+            const int t = tl % TP_CHUNK, s = sl % TP_CHUNK;
+            atomicOr(&xmask[(slot * TP_CHUNK + t) * 4 + (s >> 5)], 1u << (s & 31));
+        }
+    }
+}
+
+// diagonal blocks of diagonal items: source <= target is not a pair of the item
+__global__ void k_xmask_diag(const int32_t* __restrict__ mlist, int n_masked, const unsigned* __restrict__ xeff,
+                             const int32_t* __restrict__ xbase, uint32_t* __restrict__ xmask) {
+    const int m = blockIdx.x;
+    if (m >= n_masked) return;
+    const int I = mlist[m] >> 16, J = mlist[m] & 0xffff;
+    if (I != J) return;
+    for (int i = threadIdx.x; i < TP_NBLK * TP_CHUNK; i += blockDim.x) {
+        const int w = i / TP_CHUNK, t = i % TP_CHUNK;
+        const int64_t slot = x_slot(xeff, xbase, m, w * TP_NBLK + w);
+        for (int wd = 0; wd < 4; ++wd) {
+            const int lo = 32 * wd;
+            unsigned bits;
+            if (t >= lo + 31) bits = 0xffffffffu;  // every source of this word <= t
+            else if (t < lo) bits = 0u;
+            else bits = (t - lo == 31) ? 0xffffffffu : ((1u << (t - lo + 1)) - 1u);
+            atomicOr(&xmask[(slot * TP_CHUNK + t) * 4 + wd], bits);
+        }
+    }
+}
+
+tp_status tp_build_exclusion_bits(tp_ctx* ctx) {
+    const int nsup = (int)ctx->nsup;
+    const int nm = (int)ctx->n_masked;
+    const int64_t nbits = (int64_t)nsup * nsup;
+    if (nbits > ctx->x_item_cap || !ctx->item_index) {
+        tp_free(ctx, ctx->item_index);
+        ctx->item_index = nullptr;
+        TP_TRY(tp_alloc_t(ctx, &ctx->item_index, nbits));
+    }
+    if (nm + 1 > ctx->x_item_cap || !ctx->xeff) {
+        tp_free(ctx, ctx->xeff);
+        tp_free(ctx, ctx->xbase);
+        tp_free(ctx, ctx->xcount);
+        ctx->xeff = nullptr;
+        ctx->xbase = nullptr;
+        ctx->xcount = nullptr;
+        const int64_t cap = std::max<int64_t>(nbits, nm + 1);
+        TP_TRY(tp_alloc_t(ctx, &ctx->xeff, cap * TP_BMASK_WORDS));
+        TP_TRY(tp_alloc_t(ctx, &ctx->xbase, cap + 1));
+        TP_TRY(tp_alloc_t(ctx, &ctx->xcount, cap + 1));
+        ctx->x_item_cap = cap;
+    }
+    TP_CU(cudaMemsetAsync(ctx->item_index, 0xff, sizeof(int32_t) * nbits, ctx->stream));
+    if (nm == 0) {
+        ctx->x_slots = 0;
+        return TP_OK;
+    }
+    k_item_index<<<blocks_for(nm, 256), 256, 0, ctx->stream>>>(ctx->mlist, nm, nsup, ctx->item_index);
+    int32_t* xcount = ctx->xcount;
+    k_xeff<<<blocks_for(nm + 1, 256), 256, 0, ctx->stream>>>(ctx->mlist, nm, nsup, ctx->bmask, ctx->xeff, xcount);
+    ctx->nlaunch += 2;
+    size_t need = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, need, xcount, ctx->xbase, nm + 1, ctx->stream);
+    if (need > ctx->sort_tmp_bytes) {
+        tp_free(ctx, ctx->sort_tmp);
+        ctx->sort_tmp = nullptr;
+        TP_TRY(tp_alloc(ctx, &ctx->sort_tmp, need));
+        ctx->sort_tmp_bytes = need;
+    }
+    size_t have = ctx->sort_tmp_bytes;
+    TP_CU(cub::DeviceScan::ExclusiveSum(ctx->sort_tmp, have, xcount, ctx->xbase, nm + 1, ctx->stream));
+    int32_t total = 0;
+    TP_CU(cudaMemcpyAsync(&total, ctx->xbase + nm, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    TP_CU(cudaStreamSynchronize(ctx->stream));
+    ctx->x_slots = total;
+    if (total > ctx->x_cap || !ctx->xmask) {
+        tp_free(ctx, ctx->xmask);
+        ctx->xmask = nullptr;
+        TP_TRY(tp_alloc_t(ctx, &ctx->xmask, std::max<int64_t>(total, 1) * TP_CHUNK * 4));
+        ctx->x_cap = std::max<int64_t>(total, 1);
+    }
+    TP_CU(cudaMemsetAsync(ctx->xmask, 0, sizeof(uint32_t) * (size_t)total * TP_CHUNK * 4, ctx->stream));
+    k_xmask_pairs<<<blocks_for(ctx->nt, 256), 256, 0, ctx->stream>>>(ctx->F, ctx->perm, ctx->iperm, ctx->v2t_off,
+                                                                     ctx->v2t, ctx->nt, nsup, ctx->item_index,
+                                                                     ctx->xeff, ctx->xbase, ctx->xmask);
+    k_xmask_diag<<<nm, 256, 0, ctx->stream>>>(ctx->mlist, nm, ctx->xeff, ctx->xbase, ctx->xmask);
+    ctx->nlaunch += 2;
+    if (!ctx->xptrs) TP_TRY(tp_alloc_t(ctx, &ctx->xptrs, 3));
+    const uint64_t hp[3] = {(uint64_t)(uintptr_t)ctx->xmask, (uint64_t)(uintptr_t)ctx->xeff,
+                            (uint64_t)(uintptr_t)ctx->xbase};
+    TP_CU(cudaMemcpyAsync(ctx->xptrs, hp, sizeof(hp), cudaMemcpyHostToDevice, ctx->stream));
+    TP_CU(cudaStreamSynchronize(ctx->stream));  // hp is a host stack array
+    TP_CU(cudaGetLastError());
+    return TP_OK;
+}
+
 tp_status tp_launch_flagged(tp_ctx* ctx, bool topology) {
     const int nsup = (int)ctx->nsup;
     const int64_t nbits = (int64_t)nsup * nsup;
@@ -467,6 +628,23 @@ tp_status tp_launch_flagged(tp_ctx* ctx, bool topology) {
     ctx->pairs_fast = (int64_t)p3[0];
     ctx->pairs_precise = (int64_t)p3[1];
     ctx->pairs_masked_items = (int64_t)p3[2];
+    if (ctx->n_masked > 1) {
+        // a fixed order of the masked items (the exclusion bits are indexed by it)
+        const int nm = (int)ctx->n_masked;
+        int32_t* tmp = ctx->idx_tmp;  // nm <= nt
+        size_t need = 0;
+        cub::DeviceRadixSort::SortKeys(nullptr, need, ctx->mlist, tmp, nm, 0, 32, ctx->stream);
+        if (need > ctx->sort_tmp_bytes) {
+            tp_free(ctx, ctx->sort_tmp);
+            ctx->sort_tmp = nullptr;
+            TP_TRY(tp_alloc(ctx, &ctx->sort_tmp, need));
+            ctx->sort_tmp_bytes = need;
+        }
+        size_t have = ctx->sort_tmp_bytes;
+        TP_CU(cub::DeviceRadixSort::SortKeys(ctx->sort_tmp, have, ctx->mlist, tmp, nm, 0, 32, ctx->stream));
+        TP_CU(cudaMemcpyAsync(ctx->mlist, tmp, sizeof(int32_t) * nm, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    if (topology) TP_TRY(tp_build_exclusion_bits(ctx));
     return TP_OK;
 }
 
