@@ -20,12 +20,18 @@
 // per leaf, 16 by default).  The admissibility test depends on (L, C)
 // only, so the traversal is warp-uniform: the warp pops up to 32 nodes from
 // a shared-memory stack, each lane tests one, and ballots sort them into a
-// far list, a near list and nodes to open.  The lists are evaluated with
-// lanes split as (target = lane % 16, half = lane / 16), each half taking
-// every other far node or near member.  Per-target partials are FP32 per
-// list flush and FP64 across flushes; each target is owned by one warp, so
-// results are stored without atomics in the same accumulator layout as the
-// direct kernels (see tp_direct.cu), and the same adjoint applies.
+// far list, two near lists and nodes to open.  A near cluster whose vertex
+// box is apart from the leaf's can hold no triangle adjacent to a target, so
+// its pairs skip the exclusion test; near clusters whose box touches the
+// leaf's (the leaf itself among them) are listed apart and every pair is
+// tested.  The lists are evaluated in packed FP32x2 arithmetic, one target
+// against two staged sources per instruction, with lanes split as
+// (target = lane % 16, half = lane / 16) for leaves of up to 16 targets
+// (each half taking every other source pair) or one target per lane for
+// larger leaves.  Per-target partials are FP32 per list flush and FP64
+// across flushes; each target is owned by one warp, so results are stored
+// without atomics in the same accumulator layout as the direct kernels (see
+// tp_direct.cu), and the same adjoint applies.
 //
 // Learned correction (TP_LEARNED).  The Barnes-Hut pass also lists the far
 // nodes of every leaf (runs of up to 256 nodes, reserved with one atomic per
@@ -34,6 +40,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
+
+#include <type_traits>
 
 #include "tp_internal.cuh"
 #include "tp_mlp_dev.cuh"
@@ -44,6 +52,9 @@ constexpr int BH_WARPS = 4;
 constexpr int BH_STACK = 1024;
 constexpr int BH_FAR = 256;
 constexpr int BH_NEAR = 128;
+#ifndef TP_BH_MINB
+#define TP_BH_MINB 1  // resident blocks per SM asked of the register allocator
+#endif
 
 struct BHArgs {
     const float* soa;
@@ -98,41 +109,90 @@ struct Tgt {
     float h[3], l[3], n[3], w;
 };
 
-// T-side derivatives of e_TS + e_ST for one source (or cluster) with data
-// (sh, sl, sn, sw), accumulated in the direct kernels' convention.
-template <int Q>
-__device__ __forceinline__ void gather_pair(const Tgt& t, const float* sh, const float* sl, const float* sn, float sw,
-                                            float acc[8]) {
-    float d[3];
+// Packed FP32x2 arithmetic: one lane evaluates one target against two sources
+// at a time (the target's data duplicated in both halves).
+__device__ __forceinline__ float2 bh_f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 bh_neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 bh_fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 bh_mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 bh_add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+struct Tgt2 {
+    float2 h[3], l[3], n[3], w;
+};
+
+// Staged sources (near members or far-node records) are kept in pairs: the
+// ten values (x_hi[3], x_lo[3], nu[3], w~) of sources 2i and 2i+1 interleaved,
+// so that one 16-byte shared load gives two values of both sources.
+constexpr int BH_PAIR = 20;  // floats per staged source pair
+
+__device__ __forceinline__ void stage_put(float* stg, int j, const float v[10]) {
+    float* d = stg + (j >> 1) * BH_PAIR + (j & 1);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) d[k] = (t.h[k] - sh[k]) + (t.l[k] - sl[k]);
-    float inv = bh_rcp(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    float a = t.n[0] * d[0] + t.n[1] * d[1] + t.n[2] * d[2];
-    float b = sn[0] * d[0] + sn[1] * d[1] + sn[2] * d[2];
-    float al = a * inv, be = b * inv;
-    float al2 = al * al, be2 = be * be, al4 = al2 * al2, be4 = be2 * be2;
-    float alq, beq, al5, be5;
-    if (Q == 6) {
-        alq = al4 * al2;
-        beq = be4 * be2;
-        al5 = al4 * al;
-        be5 = be4 * be;
-    } else {
-        alq = al4 * al4;
-        beq = be4 * be4;
-        al5 = al4 * al2 * al;
-        be5 = be4 * be2 * be;
+    for (int c = 0; c < 10; ++c) d[2 * c] = v[c];
+}
+
+// A padding source: zero weight, far from every target, so that its terms
+// vanish without a test (no zero distance, no overflow).
+__device__ __forceinline__ void stage_pad(float* stg, int j) {
+    const float v[10] = {1e18f, 1e18f, 1e18f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    stage_put(stg, j, v);
+}
+
+// T-side derivatives of e_TS + e_ST for the staged source pair p (data at
+// stg + p * BH_PAIR), accumulated in the direct kernels' convention.  SEL:
+// per-half admission (v0, v1); an excluded half gets 1/|d|^2 = 0 and weight
+// 0, so its terms are exact zeros (d itself stays finite: a coincident
+// centroid or the padding source's large offset never reaches a power).
+template <int Q, bool SEL>
+__device__ __forceinline__ void gather_pair2(const Tgt2& t, const float* stg, int p, float2 acc[8], bool v0 = true,
+                                             bool v1 = true) {
+    const float4* r = reinterpret_cast<const float4*>(stg + p * BH_PAIR);
+    const float4 q0 = r[0], q1 = r[1], q2 = r[2], q3 = r[3], q4 = r[4];
+    const float2 sh[3] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y)};
+    const float2 sl[3] = {make_float2(q1.z, q1.w), make_float2(q2.x, q2.y), make_float2(q2.z, q2.w)};
+    const float2 sn[3] = {make_float2(q3.x, q3.y), make_float2(q3.z, q3.w), make_float2(q4.x, q4.y)};
+    const float2 sw = make_float2(q4.z, q4.w);
+    float2 d[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = bh_add2(bh_add2(t.h[k], bh_neg2(sh[k])), bh_add2(t.l[k], bh_neg2(sl[k])));
+    float2 r2 = bh_mul2(d[0], d[0]);
+    r2 = bh_fma2(d[1], d[1], r2);
+    r2 = bh_fma2(d[2], d[2], r2);
+    float2 wts = bh_mul2(t.w, sw);
+    float2 inv = make_float2(bh_rcp(r2.x), bh_rcp(r2.y));
+    if (SEL) {
+        inv = make_float2(v0 ? inv.x : 0.f, v1 ? inv.y : 0.f);
+        wts = make_float2(v0 ? wts.x : 0.f, v1 ? wts.y : 0.f);
     }
-    float wts = t.w * sw;
-    float s6 = alq + beq;
-    float wi = wts * inv;
-    float A5 = wi * al5, B5 = wi * be5, k = 2.0f * wi * s6;  // (p/q) = 2
-    acc[0] += wts * s6;
-    acc[1] += A5;
+    float2 a = bh_mul2(t.n[0], d[0]);
+    a = bh_fma2(t.n[1], d[1], a);
+    a = bh_fma2(t.n[2], d[2], a);
+    float2 b = bh_mul2(sn[0], d[0]);
+    b = bh_fma2(sn[1], d[1], b);
+    b = bh_fma2(sn[2], d[2], b);
+    const float2 al = bh_mul2(a, inv), be = bh_mul2(b, inv);
+    const float2 al2 = bh_mul2(al, al), be2 = bh_mul2(be, be);
+    const float2 al4 = bh_mul2(al2, al2), be4 = bh_mul2(be2, be2);
+    float2 s6, al5, be5;
+    if (Q == 6) {
+        s6 = bh_fma2(be4, be2, bh_mul2(al4, al2));
+        al5 = bh_mul2(al4, al);
+        be5 = bh_mul2(be4, be);
+    } else {
+        s6 = bh_fma2(be4, be4, bh_mul2(al4, al4));
+        al5 = bh_mul2(bh_mul2(al4, al2), al);
+        be5 = bh_mul2(bh_mul2(be4, be2), be);
+    }
+    const float2 wi = bh_mul2(wts, inv);
+    const float2 A5 = bh_mul2(wi, al5), B5 = bh_mul2(wi, be5);
+    const float2 nk = bh_mul2(bh_mul2(wi, s6), bh_f2(-2.0f));  // -(p/q) wts inv s6, p = 2q
+    acc[0] = bh_fma2(wts, s6, acc[0]);
+    acc[1] = bh_add2(acc[1], A5);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        acc[2 + c] += A5 * d[c];
-        acc[5 + c] += B5 * sn[c] - k * d[c];
+    for (int k = 0; k < 3; ++k) {
+        acc[2 + k] = bh_fma2(A5, d[k], acc[2 + k]);
+        acc[5 + k] = bh_fma2(nk, d[k], bh_fma2(B5, sn[k], acc[5 + k]));
     }
 }
 
@@ -262,22 +322,31 @@ __device__ __forceinline__ bool adjacent(int3 a, int3 b, int edge_only) {
     return edge_only ? k >= 2 : k >= 1;
 }
 
+// FP32 outward-rounded vertex boxes strictly apart along some axis.  Two
+// triangles that share a vertex lie in vertex boxes that both hold it, so a
+// near cluster whose box is apart from the target leaf's has no member
+// adjacent to any target and needs no exclusion test.
+__device__ __forceinline__ bool boxes_apart(const LeafAdm& L, const float* c32) {
+    bool apart = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        if (L.out[3 + a] < c32[a] || c32[3 + a] < L.out[a]) apart = true;
+    return apart;
+}
+
 template <int Q, int MODE>
-__global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
+__global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
     __shared__ int32_t s_stack[BH_WARPS][BH_STACK];
     __shared__ int32_t s_far[BH_WARPS][BH_FAR];
-    __shared__ int32_t s_near[BH_WARPS][BH_NEAR];
-    __shared__ __align__(16) float s_stg[BH_WARPS][32 * 16];
-    __shared__ int32_t s_stg_cnt[BH_WARPS][32];
+    __shared__ int2 s_near[BH_WARPS][2][BH_NEAR];  // (first member, count); [0] apart, [1] touching
+    __shared__ __align__(16) float s_stg[BH_WARPS][16 * BH_PAIR];
     __shared__ int4 s_stg_f[BH_WARPS][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t li = (int64_t)blockIdx.x * BH_WARPS + warp;
     if (li >= A.nleaves) return;
     int32_t* st = s_stack[warp];
     int32_t* far = s_far[warp];
-    int32_t* nearl = s_near[warp];
     float* stg = s_stg[warp];
-    int32_t* stg_cnt = s_stg_cnt[warp];
     int4* stg_f = s_stg_f[warp];
     const int64_t L = A.leaves[li];
     const int64_t fL = A.first[L];
@@ -285,31 +354,38 @@ __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
     LeafAdm la;
     leaf_adm(A.box + 6 * L, la);
     const float theta32 = (float)A.theta;
-    const int t = lane & 15, half = lane >> 4;
+    // leaves of up to 16 targets: lanes t and t + 16 share target t and take
+    // alternate source pairs; larger leaves: one target per lane
+    const bool wide = A.leaf_size > 16;
+    const int t = wide ? lane : (lane & 15);
+    const int half = wide ? 0 : (lane >> 4);
+    const int nh = wide ? 1 : 2;
     const int64_t k = fL + t;
     const bool active = t < cnt;
-    Tgt tg;
+    Tgt2 tg;
     int3 tf = make_int3(-2, -2, -2);
     if (active) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            tg.h[c] = A.soa[c * A.ntp + k];
-            tg.l[c] = A.soa[(3 + c) * A.ntp + k];
-            tg.n[c] = A.soa[(6 + c) * A.ntp + k];
+            tg.h[c] = bh_f2(A.soa[c * A.ntp + k]);
+            tg.l[c] = bh_f2(A.soa[(3 + c) * A.ntp + k]);
+            tg.n[c] = bh_f2(A.soa[(6 + c) * A.ntp + k]);
         }
-        tg.w = A.soa[9 * A.ntp + k];
+        tg.w = bh_f2(A.soa[9 * A.ntp + k]);
         tf = make_int3(A.Fs[3 * k], A.Fs[3 * k + 1], A.Fs[3 * k + 2]);
     } else {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) tg.h[c] = tg.l[c] = tg.n[c] = 0.f;
-        tg.w = 0.f;
+        for (int c = 0; c < 3; ++c) tg.h[c] = tg.l[c] = tg.n[c] = bh_f2(0.f);
+        tg.w = bh_f2(0.f);
     }
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // statistics: pair counts of far terms and of near pairs without exclusion
+    // tests are taken per node in the traversal (lane of the node), those of
+    // touching near nodes per admitted pair
     unsigned long long n_near = 0, n_far = 0, n_farp = 0;
     const unsigned lt = (1u << lane) - 1u;
 
-    // far list: stage 32 node records at a time in shared memory, then every
-    // half-warp sweeps them (half h takes records h, h+2, ...)
+    // far list: stage 32 node records at a time, then sweep them in pairs
     auto flush_far = [&](int nf) {
         if (MODE == M_LIST && nf > 0) {
             // one run of this leaf: reserve rows and a run record, store the node ids
@@ -332,80 +408,85 @@ __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
                 }
             }
         }
-        float a32[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        float2 a2[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a2[c] = bh_f2(0.f);
         for (int b0 = 0; b0 < nf; b0 += 32) {
             const int nb = nf - b0 < 32 ? nf - b0 : 32;
             __syncwarp();
             if (lane < nb) {
-                const int32_t C = far[b0 + lane];
-                const float4* r = reinterpret_cast<const float4*>(A.nodef + 16 * (int64_t)C);
-                float4* d = reinterpret_cast<float4*>(stg + lane * 16);
-                d[0] = r[0];
-                d[1] = r[1];
-                d[2] = r[2];
-                stg_cnt[lane] = A.last[C] - A.first[C] + 1;
+                const float4* r = reinterpret_cast<const float4*>(A.nodef + 16 * (int64_t)far[b0 + lane]);
+                const float4 r0 = r[0], r1 = r[1], r2 = r[2];
+                const float v[10] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y};
+                stage_put(stg, lane, v);
+            } else if (lane == nb && (nb & 1)) {
+                stage_pad(stg, lane);
             }
             __syncwarp();
-            for (int i = half; i < nb; i += 2) {
-                const float* r = stg + i * 16;
-                if (active) {
-                    gather_pair<Q>(tg, r, r + 3, r + 6, r[9], a32);
-                    n_far += 1;
-                    n_farp += (unsigned long long)stg_cnt[i];
-                }
-            }
+            const int np = (nb + 1) >> 1;
+            for (int p = half; p < np; p += nh) gather_pair2<Q, false>(tg, stg, p, a2);
         }
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] += (double)a32[c];
+        for (int c = 0; c < 8; ++c) acc[c] += (double)(a2[c].x + a2[c].y);
     };
-    // near list: stage the members of up to 32 sources at a time (whole near
-    // nodes) in shared memory, then every half-warp sweeps them
-    auto flush_near = [&](int nn) {
-        float a32[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // near lists: stage the members of up to 32 sources at a time (whole near
+    // nodes), then sweep them in pairs; TOUCH: nodes whose box meets the
+    // leaf's, where every pair is tested for exclusion
+    auto flush_near = [&](const int2* nl, int nn, auto touch_tag) {
+        constexpr bool TOUCH = decltype(touch_tag)::value;
+        float2 a2[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a2[c] = bh_f2(0.f);
         int i = 0;
         while (i < nn) {
             // take whole nodes while they fit in 32 slots
             int nsrc = 0, i1 = i;
-            while (i1 < nn) {
-                const int m = A.last[nearl[i1]] - A.first[nearl[i1]] + 1;
-                if (nsrc + m > 32) break;
-                nsrc += m;
-                ++i1;
-            }
+            while (i1 < nn && nsrc + nl[i1].y <= 32) nsrc += nl[i1++].y;
             __syncwarp();
             // lane -> (node, member) by walking the taken nodes
             {
                 int base = 0;
                 for (int j = i; j < i1; ++j) {
-                    const int64_t C = nearl[j];
-                    const int64_t f = A.first[C];
-                    const int m = A.last[C] - A.first[C] + 1;
-                    if (lane >= base && lane < base + m) {
-                        const int64_t s = f + (lane - base);
-                        float* d = stg + lane * 16;
+                    const int2 nd = nl[j];
+                    if (lane >= base && lane < base + nd.y) {
+                        const int64_t s = (int64_t)nd.x + (lane - base);
+                        float v[10];
 #pragma unroll
-                        for (int c = 0; c < 10; ++c) d[c] = A.soa[c * A.ntp + s];
-                        stg_f[lane] = make_int4(A.Fs[3 * s], A.Fs[3 * s + 1], A.Fs[3 * s + 2], (int)s);
+                        for (int c = 0; c < 10; ++c) v[c] = A.soa[c * A.ntp + s];
+                        stage_put(stg, lane, v);
+                        if (TOUCH) stg_f[lane] = make_int4(A.Fs[3 * s], A.Fs[3 * s + 1], A.Fs[3 * s + 2], (int)s);
                     }
-                    base += m;
+                    base += nd.y;
+                }
+                if (lane == nsrc && (nsrc & 1)) {
+                    stage_pad(stg, lane);
+                    if (TOUCH) stg_f[lane] = make_int4(-1, -1, -1, -1);
                 }
             }
             __syncwarp();
-            for (int j = half; j < nsrc; j += 2) {
-                const float* r = stg + j * 16;
-                const int4 sf = stg_f[j];
-                if (active && sf.w != (int)k && !adjacent(tf, make_int3(sf.x, sf.y, sf.z), A.edge_only)) {
-                    gather_pair<Q>(tg, r, r + 3, r + 6, r[9], a32);
-                    n_near += 1;
+            const int np = (nsrc + 1) >> 1;
+            for (int p = half; p < np; p += nh) {
+                if (TOUCH) {
+                    const int4 f0 = stg_f[2 * p], f1 = stg_f[2 * p + 1];
+                    const bool v0 = active && f0.w >= 0 && f0.w != (int)k &&
+                                    !adjacent(tf, make_int3(f0.x, f0.y, f0.z), A.edge_only);
+                    const bool v1 = active && f1.w >= 0 && f1.w != (int)k &&
+                                    !adjacent(tf, make_int3(f1.x, f1.y, f1.z), A.edge_only);
+                    gather_pair2<Q, true>(tg, stg, p, a2, v0, v1);
+                    n_near += (unsigned long long)(v0 + v1);
+                } else {
+                    gather_pair2<Q, false>(tg, stg, p, a2);
                 }
             }
             i = i1;
         }
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] += (double)a32[c];
+        for (int c = 0; c < 8; ++c) acc[c] += (double)(a2[c].x + a2[c].y);
     };
+    using Apart = std::false_type;
+    using Touch = std::true_type;
 
-    int sp = 1, nf = 0, nn = 0;
+    int sp = 1, nf = 0, nn[2] = {0, 0};
     if (lane == 0) st[0] = 0;  // root
     __syncwarp();
     bool overflow = false;
@@ -414,17 +495,27 @@ __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
         const int node = lane < m ? st[sp - 1 - lane] : -1;
         __syncwarp();
         sp -= m;
-        bool is_far = false, is_near = false, is_open = false;
+        bool is_far = false, is_near = false, is_open = false, touch = false;
+        int firstc = 0, cntc = 0;
         if (node >= 0) {
-            const int cntc = A.last[node] - A.first[node] + 1;
-            if (admissible(la, A.adm32 + 16 * (int64_t)node, A.box + 6 * (int64_t)node, A.adm64 + 4 * (int64_t)node,
-                           A.theta, theta32))
+            firstc = A.first[node];
+            cntc = A.last[node] - firstc + 1;
+            const float* c32 = A.adm32 + 16 * (int64_t)node;
+            if (admissible(la, c32, A.box + 6 * (int64_t)node, A.adm64 + 4 * (int64_t)node, A.theta, theta32)) {
                 is_far = true;
-            else if (cntc <= A.leaf_size || node >= A.n - 1) is_near = true;
-            else is_open = true;
+                n_far += (unsigned long long)cnt;
+                n_farp += (unsigned long long)cnt * (unsigned long long)cntc;
+            } else if (cntc <= A.leaf_size || node >= A.n - 1) {
+                is_near = true;
+                touch = !boxes_apart(la, c32);
+                if (!touch) n_near += (unsigned long long)cnt * (unsigned long long)cntc;
+            } else {
+                is_open = true;
+            }
         }
         const unsigned bf = __ballot_sync(0xffffffffu, is_far);
-        const unsigned bn = __ballot_sync(0xffffffffu, is_near);
+        const unsigned bn0 = __ballot_sync(0xffffffffu, is_near && !touch);
+        const unsigned bn1 = __ballot_sync(0xffffffffu, is_near && touch);
         const unsigned bo = __ballot_sync(0xffffffffu, is_open);
         if (sp + 2 * __popc(bo) > BH_STACK) {
             overflow = true;
@@ -440,7 +531,8 @@ __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
             }
         } else {
             if (is_far) far[nf + __popc(bf & lt)] = node;
-            if (is_near) nearl[nn + __popc(bn & lt)] = node;
+            if (is_near && !touch) s_near[warp][0][nn[0] + __popc(bn0 & lt)] = make_int2(firstc, cntc);
+            if (is_near && touch) s_near[warp][1][nn[1] + __popc(bn1 & lt)] = make_int2(firstc, cntc);
         }
         if (is_open) {
             const int pos = sp + 2 * __popc(bo & lt);
@@ -449,7 +541,8 @@ __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
         }
         if (MODE != M_RECORD) {
             nf += __popc(bf);
-            nn += __popc(bn);
+            nn[0] += __popc(bn0);
+            nn[1] += __popc(bn1);
         }
         sp += 2 * __popc(bo);
         __syncwarp();
@@ -457,9 +550,13 @@ __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
             flush_far(nf);
             nf = 0;
         }
-        if (nn > BH_NEAR - 32) {
-            flush_near(nn);
-            nn = 0;
+        if (nn[0] > BH_NEAR - 32) {
+            flush_near(s_near[warp][0], nn[0], Apart{});
+            nn[0] = 0;
+        }
+        if (nn[1] > BH_NEAR - 32) {
+            flush_near(s_near[warp][1], nn[1], Touch{});
+            nn[1] = 0;
         }
         __syncwarp();
     }
@@ -469,9 +566,12 @@ __global__ void __launch_bounds__(BH_WARPS * 32) k_bh(BHArgs A) {
     }
     if (MODE == M_RECORD) return;
     flush_far(nf);
-    flush_near(nn);
+    flush_near(s_near[warp][0], nn[0], Apart{});
+    flush_near(s_near[warp][1], nn[1], Touch{});
+    if (!wide) {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 16);
+        for (int c = 0; c < 8; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 16);
+    }
     if (half == 0 && active) {
 #pragma unroll
         for (int c = 0; c < 8; ++c) A.acc[c * A.ntp + k] = acc[c];
@@ -558,7 +658,8 @@ __global__ void __launch_bounds__(FL_WARPS * 32) k_far_correct(BHArgs A, const f
     float* skf = s_kf[warp];
     const unsigned long long nr = A.far_count[1];
     const int64_t nruns = nr < (unsigned long long)A.run_cap ? (int64_t)nr : A.run_cap;
-    const int t = lane & 15, half = lane >> 4;
+    const bool wide = A.leaf_size > 16;  // one target per lane, else two lanes per target
+    const int t = wide ? lane : (lane & 15), half = wide ? 0 : (lane >> 4), nh = wide ? 1 : 2;
     unsigned long long n_learn = 0;
     for (int64_t run = (int64_t)blockIdx.x * FL_WARPS + warp; run < nruns; run += (int64_t)gridDim.x * FL_WARPS) {
         const tp_far_run R = A.far_runs[run];
@@ -599,7 +700,7 @@ __global__ void __launch_bounds__(FL_WARPS * 32) k_far_correct(BHArgs A, const f
                 kd[1] = kr[1];
             }
             __syncwarp();
-            for (int i = half; i < nb; i += 2) {
+            for (int i = half; i < nb; i += nh) {
                 if (active && skf[i * 8 + 7] != 0.f) {
                     const float* r = stg + i * 16;
                     gather_pair_learned<Q>(tg, r, r + 3, r + 6, r[9], skf + i * 8, a32);
@@ -607,8 +708,10 @@ __global__ void __launch_bounds__(FL_WARPS * 32) k_far_correct(BHArgs A, const f
                 }
             }
         }
+        if (!wide) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) a32[c] += __shfl_xor_sync(0xffffffffu, a32[c], 16);
+            for (int c = 0; c < 8; ++c) a32[c] += __shfl_xor_sync(0xffffffffu, a32[c], 16);
+        }
         if (half == 0 && active) {
 #pragma unroll
             for (int c = 0; c < 8; ++c)

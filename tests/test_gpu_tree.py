@@ -101,6 +101,25 @@ def test_bh_parity_with_oracle(tp, ctx, oracle_mod, theta):
     assert abs(tp.tp_energy(ctx, p) - Eo) <= E_TOL * Eo
 
 
+@pytest.mark.parametrize("leaf,q,adj", [(32, 6, 0), (24, 8, 1), (7, 8, 0), (1, 6, 1)])
+def test_bh_parity_leaf_sizes_and_options(tp, ctx, oracle_mod, leaf, q, adj):
+    """Leaves above 16 targets (one target per lane), small leaves, q = 8 and
+    edge-only exclusion against the oracle's Barnes-Hut sums."""
+    V, F = meshgen.sh_deformed_sphere(4, 12, 0.05, 3)
+    Eo, go, info = oracle_mod.bh_gradient(V, F, 0.5, q=q, p=2 * q, adj=adj, leaf_size=leaf)
+    tp.tp_mesh_upload(ctx, V, F)
+    tp.tp_tree_build(ctx, leaf, 30)
+    p = tp.tp_params_default(mode=tp.TP_BH, theta=0.5, q=q, p=2 * q,
+                             flags=tp._tp.TP_EXCLUDE_EDGE if adj else 0)
+    grad = np.zeros_like(V)
+    e = tp.tp_gradient(ctx, grad, p)
+    st = tp.tp_get_stats(ctx)
+    assert st["far_terms"] == info["far_terms"] and info["far_terms"] > 0
+    assert st["pairs_exact"] == info["near_pairs"]
+    assert abs(e - Eo) <= E_TOL * Eo, (e, Eo)
+    assert rel(grad, go) <= G_TOL, rel(grad, go)
+
+
 def test_bh_theta_zero_equals_direct(tp, ctx):
     V, F = meshgen.workload("dish_l5")
     tp.tp_mesh_upload(ctx, V, F)
