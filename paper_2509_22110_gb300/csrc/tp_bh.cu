@@ -53,7 +53,7 @@ constexpr int BH_STACK = 1024;
 constexpr int BH_FAR = 256;
 constexpr int BH_NEAR = 128;
 #ifndef TP_BH_MINB
-#define TP_BH_MINB 1  // resident blocks per SM asked of the register allocator
+#define TP_BH_MINB 5  // resident blocks per SM asked of the register allocator (20 warps)
 #endif
 
 struct BHArgs {
@@ -341,6 +341,7 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
     __shared__ int2 s_near[BH_WARPS][2][BH_NEAR];  // (first member, count); [0] apart, [1] touching
     __shared__ __align__(16) float s_stg[BH_WARPS][16 * BH_PAIR];
     __shared__ int4 s_stg_f[BH_WARPS][32];
+    __shared__ LeafAdm s_la[BH_WARPS];  // the leaf's admissibility constants (read by every test)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t li = (int64_t)blockIdx.x * BH_WARPS + warp;
     if (li >= A.nleaves) return;
@@ -351,8 +352,9 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
     const int64_t L = A.leaves[li];
     const int64_t fL = A.first[L];
     const int cnt = A.last[L] - A.first[L] + 1;
-    LeafAdm la;
-    leaf_adm(A.box + 6 * L, la);
+    if (lane == 0) leaf_adm(A.box + 6 * L, s_la[warp]);
+    __syncwarp();
+    const LeafAdm& la = s_la[warp];
     const float theta32 = (float)A.theta;
     // leaves of up to 16 targets: lanes t and t + 16 share target t and take
     // alternate source pairs; larger leaves: one target per lane
