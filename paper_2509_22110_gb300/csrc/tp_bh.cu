@@ -105,10 +105,6 @@ __device__ __forceinline__ float bh_rcp(float x) {
     return y;
 }
 
-struct Tgt {
-    float h[3], l[3], n[3], w;
-};
-
 // Packed FP32x2 arithmetic: one lane evaluates one target against two sources
 // at a time (the target's data duplicated in both halves).
 __device__ __forceinline__ float2 bh_f2(float a) { return make_float2(a, a); }
@@ -223,49 +219,68 @@ __device__ __forceinline__ void leaf_adm(const double* box, LeafAdm& L) {
     L.dl32 = (float)L.dl;
 }
 
-// Admissibility of cluster C for target leaf L:
-//   boxes strictly disjoint along some axis, and
-//   diag(C) < theta * (|X_C - c_L| - diag(L)/2),
-// with every quantity in FP64, separately rounded, in a fixed order.  An FP32
-// pre-test settles the decision whenever its error bound allows (outward and
-// inward rounded boxes for the strict comparisons; a 1e-5 relative margin for
-// the size test, far above FP32 rounding); otherwise the FP64 test decides.
-// The same far term with the network's per-channel factors (kf[0..6]):
+// The same far term with the network's per-channel factors kf[0..6], for the
+// staged source pair p (records at stg + p * BH_PAIR, factors interleaved at
+// skf + p * 16):
 // E = wts (kf0 al^q + kf1 be^q), U: kf2 A5, Gn: kf3 A5 d, Gx: kf4 B5 nubar - k d,
-// k = (p/q) wts inv (kf5 al^q + kf6 be^q).
+// k = (p/q) wts inv (kf5 al^q + kf6 be^q).  A padding source has zero weight
+// and zero factors.
 template <int Q>
-__device__ __forceinline__ void gather_pair_learned(const Tgt& t, const float* sh, const float* sl, const float* sn,
-                                                    float sw, const float* kf, float acc[8]) {
-    float d[3];
+__device__ __forceinline__ void gather_pair_learned2(const Tgt2& t, const float* stg, const float* skf, int p,
+                                                     float2 acc[8]) {
+    const float4* r = reinterpret_cast<const float4*>(stg + p * BH_PAIR);
+    const float4 q0 = r[0], q1 = r[1], q2 = r[2], q3 = r[3], q4 = r[4];
+    const float4* kq = reinterpret_cast<const float4*>(skf + p * 16);
+    const float4 k01 = kq[0], k23 = kq[1], k45 = kq[2], k6f = kq[3];
+    const float2 sh[3] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y)};
+    const float2 sl[3] = {make_float2(q1.z, q1.w), make_float2(q2.x, q2.y), make_float2(q2.z, q2.w)};
+    const float2 sn[3] = {make_float2(q3.x, q3.y), make_float2(q3.z, q3.w), make_float2(q4.x, q4.y)};
+    const float2 sw = make_float2(q4.z, q4.w);
+    float2 d[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) d[k] = (t.h[k] - sh[k]) + (t.l[k] - sl[k]);
-    float inv = bh_rcp(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    float a = t.n[0] * d[0] + t.n[1] * d[1] + t.n[2] * d[2];
-    float b = sn[0] * d[0] + sn[1] * d[1] + sn[2] * d[2];
-    float al = a * inv, be = b * inv;
-    float al2 = al * al, be2 = be * be, al4 = al2 * al2, be4 = be2 * be2;
-    float alq, beq, al5, be5;
+    for (int k = 0; k < 3; ++k) d[k] = bh_add2(bh_add2(t.h[k], bh_neg2(sh[k])), bh_add2(t.l[k], bh_neg2(sl[k])));
+    float2 r2 = bh_mul2(d[0], d[0]);
+    r2 = bh_fma2(d[1], d[1], r2);
+    r2 = bh_fma2(d[2], d[2], r2);
+    const float2 wts = bh_mul2(t.w, sw);
+    const float2 inv = make_float2(bh_rcp(r2.x), bh_rcp(r2.y));
+    float2 a = bh_mul2(t.n[0], d[0]);
+    a = bh_fma2(t.n[1], d[1], a);
+    a = bh_fma2(t.n[2], d[2], a);
+    float2 b = bh_mul2(sn[0], d[0]);
+    b = bh_fma2(sn[1], d[1], b);
+    b = bh_fma2(sn[2], d[2], b);
+    const float2 al = bh_mul2(a, inv), be = bh_mul2(b, inv);
+    const float2 al2 = bh_mul2(al, al), be2 = bh_mul2(be, be);
+    const float2 al4 = bh_mul2(al2, al2), be4 = bh_mul2(be2, be2);
+    float2 alq, beq, al5, be5;
     if (Q == 6) {
-        alq = al4 * al2;
-        beq = be4 * be2;
-        al5 = al4 * al;
-        be5 = be4 * be;
+        alq = bh_mul2(al4, al2);
+        beq = bh_mul2(be4, be2);
+        al5 = bh_mul2(al4, al);
+        be5 = bh_mul2(be4, be);
     } else {
-        alq = al4 * al4;
-        beq = be4 * be4;
-        al5 = al4 * al2 * al;
-        be5 = be4 * be2 * be;
+        alq = bh_mul2(al4, al4);
+        beq = bh_mul2(be4, be4);
+        al5 = bh_mul2(bh_mul2(al4, al2), al);
+        be5 = bh_mul2(bh_mul2(be4, be2), be);
     }
-    float wts = t.w * sw;
-    float wi = wts * inv;
-    float A5 = wi * al5, B5 = wi * be5;
-    float k = 2.0f * wi * (kf[5] * alq + kf[6] * beq);  // (p/q) = 2
-    acc[0] += wts * (kf[0] * alq + kf[1] * beq);
-    acc[1] += kf[2] * A5;
+    const float2 kf0 = make_float2(k01.x, k01.y), kf1 = make_float2(k01.z, k01.w);
+    const float2 kf2 = make_float2(k23.x, k23.y), kf3 = make_float2(k23.z, k23.w);
+    const float2 kf4 = make_float2(k45.x, k45.y), kf5 = make_float2(k45.z, k45.w);
+    const float2 kf6 = make_float2(k6f.x, k6f.y);
+    const float2 wi = bh_mul2(wts, inv);
+    const float2 A5 = bh_mul2(wi, al5), B5 = bh_mul2(wi, be5);
+    const float2 se = bh_fma2(kf1, beq, bh_mul2(kf0, alq));
+    const float2 sk = bh_fma2(kf6, beq, bh_mul2(kf5, alq));
+    const float2 nk = bh_mul2(bh_mul2(wi, sk), bh_f2(-2.0f));  // -(p/q) wts inv (kf5 al^q + kf6 be^q)
+    const float2 gA = bh_mul2(kf3, A5), gB = bh_mul2(kf4, B5);
+    acc[0] = bh_fma2(wts, se, acc[0]);
+    acc[1] = bh_fma2(kf2, A5, acc[1]);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        acc[2 + c] += kf[3] * A5 * d[c];
-        acc[5 + c] += kf[4] * B5 * sn[c] - k * d[c];
+    for (int k = 0; k < 3; ++k) {
+        acc[2 + k] = bh_fma2(gA, d[k], acc[2 + k]);
+        acc[5 + k] = bh_fma2(nk, d[k], bh_fma2(gB, sn[k], acc[5 + k]));
     }
 }
 
@@ -276,6 +291,13 @@ __device__ __forceinline__ uint64_t bh_mix(uint64_t x) {
     return x ^ (x >> 31);
 }
 
+// Admissibility of cluster C for target leaf L:
+//   boxes strictly disjoint along some axis, and
+//   diag(C) < theta * (|X_C - c_L| - diag(L)/2),
+// with every quantity in FP64, separately rounded, in a fixed order.  An FP32
+// pre-test settles the decision whenever its error bound allows (outward and
+// inward rounded boxes for the strict comparisons; a 1e-5 relative margin for
+// the size test, far above FP32 rounding); otherwise the FP64 test decides.
 __device__ __forceinline__ bool admissible(const LeafAdm& L, const float* c32, const double* bc,
                                            const double* c64, double theta, float theta32) {
     bool sure = false, amb = false;
@@ -653,8 +675,8 @@ __global__ void __launch_bounds__(FL_WARPS * 32, 2) k_far_feat(BHArgs A, __nv_bf
 
 template <int Q>
 __global__ void __launch_bounds__(FL_WARPS * 32) k_far_correct(BHArgs A, const float* __restrict__ kf) {
-    __shared__ __align__(16) float s_stg[FL_WARPS][32 * 16];
-    __shared__ __align__(16) float s_kf[FL_WARPS][32 * 8];
+    __shared__ __align__(16) float s_stg[FL_WARPS][16 * BH_PAIR];
+    __shared__ __align__(16) float s_kf[FL_WARPS][16 * 16];  // factors of source pairs, interleaved
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* stg = s_stg[warp];
     float* skf = s_kf[warp];
@@ -662,7 +684,7 @@ __global__ void __launch_bounds__(FL_WARPS * 32) k_far_correct(BHArgs A, const f
     const int64_t nruns = nr < (unsigned long long)A.run_cap ? (int64_t)nr : A.run_cap;
     const bool wide = A.leaf_size > 16;  // one target per lane, else two lanes per target
     const int t = wide ? lane : (lane & 15), half = wide ? 0 : (lane >> 4), nh = wide ? 1 : 2;
-    unsigned long long n_learn = 0;
+    unsigned long long n_learn = 0;  // (target, row) pairs with the range flag set, counted by lane 0
     for (int64_t run = (int64_t)blockIdx.x * FL_WARPS + warp; run < nruns; run += (int64_t)gridDim.x * FL_WARPS) {
         const tp_far_run R = A.far_runs[run];
         const int64_t L = A.leaves[R.li];
@@ -670,46 +692,54 @@ __global__ void __launch_bounds__(FL_WARPS * 32) k_far_correct(BHArgs A, const f
         const int cnt = A.last[L] - A.first[L] + 1;
         const bool active = t < cnt;
         const int64_t k = fL + t;
-        Tgt tg;
+        Tgt2 tg;
         if (active) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                tg.h[c] = A.soa[c * A.ntp + k];
-                tg.l[c] = A.soa[(3 + c) * A.ntp + k];
-                tg.n[c] = A.soa[(6 + c) * A.ntp + k];
+                tg.h[c] = bh_f2(A.soa[c * A.ntp + k]);
+                tg.l[c] = bh_f2(A.soa[(3 + c) * A.ntp + k]);
+                tg.n[c] = bh_f2(A.soa[(6 + c) * A.ntp + k]);
             }
-            tg.w = A.soa[9 * A.ntp + k];
+            tg.w = bh_f2(A.soa[9 * A.ntp + k]);
         } else {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) tg.h[c] = tg.l[c] = tg.n[c] = 0.f;
-            tg.w = 0.f;
+            for (int c = 0; c < 3; ++c) tg.h[c] = tg.l[c] = tg.n[c] = bh_f2(0.f);
+            tg.w = bh_f2(0.f);
         }
-        float a32[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        float2 a2[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a2[c] = bh_f2(0.f);
         for (int b0 = 0; b0 < R.len; b0 += 32) {
             const int nb = R.len - b0 < 32 ? R.len - b0 : 32;
             __syncwarp();
+            bool flag = false;
+            float* kd = skf + (lane >> 1) * 16 + (lane & 1);
             if (lane < nb) {
                 const int64_t row = R.start + b0 + lane;
-                const int64_t C = A.far_list[row];
-                const float4* r = reinterpret_cast<const float4*>(A.nodef + 16 * C);
-                float4* d = reinterpret_cast<float4*>(stg + lane * 16);
-                d[0] = r[0];
-                d[1] = r[1];
-                d[2] = r[2];
+                const float4* r = reinterpret_cast<const float4*>(A.nodef + 16 * (int64_t)A.far_list[row]);
+                const float4 r0 = r[0], r1 = r[1], r2 = r[2];
+                const float v[10] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y};
+                stage_put(stg, lane, v);
                 const float4* kr = reinterpret_cast<const float4*>(kf + row * 8);
-                float4* kd = reinterpret_cast<float4*>(skf + lane * 8);
-                kd[0] = kr[0];
-                kd[1] = kr[1];
+                const float4 k0 = kr[0], k1 = kr[1];
+                const float kv[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
+#pragma unroll
+                for (int c = 0; c < 8; ++c) kd[2 * c] = kv[c];
+                flag = k1.w != 0.f;
+            } else if (lane == nb && (nb & 1)) {
+                stage_pad(stg, lane);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) kd[2 * c] = 0.f;
             }
+            const unsigned fb = __ballot_sync(0xffffffffu, flag);
+            if (lane == 0) n_learn += (unsigned long long)__popc(fb) * (unsigned long long)cnt;
             __syncwarp();
-            for (int i = half; i < nb; i += nh) {
-                if (active && skf[i * 8 + 7] != 0.f) {
-                    const float* r = stg + i * 16;
-                    gather_pair_learned<Q>(tg, r, r + 3, r + 6, r[9], skf + i * 8, a32);
-                    n_learn += 1;
-                }
-            }
+            const int np = (nb + 1) >> 1;
+            for (int p = half; p < np; p += nh) gather_pair_learned2<Q>(tg, stg, skf, p, a2);
         }
+        float a32[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a32[c] = a2[c].x + a2[c].y;
         if (!wide) {
 #pragma unroll
             for (int c = 0; c < 8; ++c) a32[c] += __shfl_xor_sync(0xffffffffu, a32[c], 16);
@@ -720,7 +750,6 @@ __global__ void __launch_bounds__(FL_WARPS * 32) k_far_correct(BHArgs A, const f
                 if (a32[c] != 0.f) atomicAdd(&A.acc[c * A.ntp + k], (double)a32[c]);
         }
     }
-    for (int o = 16; o > 0; o >>= 1) n_learn += __shfl_xor_sync(0xffffffffu, n_learn, o);
     if (lane == 0 && n_learn) atomicAdd(&A.counts[3], n_learn);
 }
 

@@ -270,51 +270,62 @@ __device__ __forceinline__ void warp_mlp_rows32(const uint2* wf, const float* bi
 //   21 |nubar_L|, 22 |nubar_C|, 23 log(A_C/A_L);
 // frame: e1 = (X_C - X_L)/r, e2 along the part of nubar_C orthogonal to e1
 // (or of the coordinate axis least aligned with e1), e3 = e1 x e2.
+// Single-precision intrinsics throughout (reciprocal square roots, fast
+// logarithms): the features are rounded to BF16 after normalisation, far
+// coarser than their error.
 __device__ __forceinline__ void moment_frame(const float* m6, const float e[3][3], float* out) {
     const float M[3][3] = {{m6[0], m6[1], m6[2]}, {m6[1], m6[3], m6[4]}, {m6[2], m6[4], m6[5]}};
+    float Me[3][3];  // Me[j] = M e_j
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) Me[j][a] = M[a][0] * e[j][0] + M[a][1] * e[j][1] + M[a][2] * e[j][2];
     int o = 0;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = i; j < 3; ++j) {
-            float s = 0.f;
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-                for (int b = 0; b < 3; ++b) s += e[i][a] * M[a][b] * e[j][b];
-            out[o++] = s;
-        }
+        for (int j = i; j < 3; ++j) out[o++] = e[i][0] * Me[j][0] + e[i][1] * Me[j][1] + e[i][2] * Me[j][2];
 }
 
 __device__ __forceinline__ void far_features(const float* L, const float* C, float* f) {
     float D[3], e[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) D[a] = C[1 + a] - L[1 + a];
-    const float r = sqrtf(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+    const float r2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
+    const float rinv = rsqrtf(r2), r = r2 * rinv;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) e[0][a] = D[a] / r;
+    for (int a = 0; a < 3; ++a) e[0][a] = D[a] * rinv;
     float u[3] = {C[4], C[5], C[6]};
     float p = u[0] * e[0][0] + u[1] * e[0][1] + u[2] * e[0][2];
 #pragma unroll
     for (int a = 0; a < 3; ++a) u[a] -= p * e[0][a];
-    float un = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    if (un < 1e-6f) {
+    float un2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    if (un2 < 1e-12f) {  // |u| < 1e-6: use the coordinate axis least aligned with e1
         int k = 0;
-        if (fabsf(e[0][1]) < fabsf(e[0][k])) k = 1;
-        if (fabsf(e[0][2]) < fabsf(e[0][k])) k = 2;
+        float ek = e[0][0];  // selected without indexing, so e stays in registers
+        if (fabsf(e[0][1]) < fabsf(ek)) {
+            k = 1;
+            ek = e[0][1];
+        }
+        if (fabsf(e[0][2]) < fabsf(ek)) {
+            k = 2;
+            ek = e[0][2];
+        }
 #pragma unroll
-        for (int a = 0; a < 3; ++a) u[a] = (a == k ? 1.f : 0.f) - e[0][k] * e[0][a];
-        un = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        for (int a = 0; a < 3; ++a) u[a] = (a == k ? 1.f : 0.f) - ek * e[0][a];
+        un2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     }
+    const float uinv = rsqrtf(un2);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) e[1][a] = u[a] / un;
+    for (int a = 0; a < 3; ++a) e[1][a] = u[a] * uinv;
     e[2][0] = e[0][1] * e[1][2] - e[0][2] * e[1][1];
     e[2][1] = e[0][2] * e[1][0] - e[0][0] * e[1][2];
     e[2][2] = e[0][0] * e[1][1] - e[0][1] * e[1][0];
-    f[0] = logf(r / sqrtf(C[0]));
-    f[1] = logf(r / sqrtf(L[0]));
-    f[2] = C[13] / r;
-    f[3] = L[13] / r;
+    const float lr = __logf(r), lc = __logf(C[0]), ll = __logf(L[0]);
+    f[0] = lr - 0.5f * lc;
+    f[1] = lr - 0.5f * ll;
+    f[2] = C[13] * rinv;
+    f[3] = L[13] * rinv;
 #pragma unroll
     for (int i = 0; i < 3; ++i) f[4 + i] = L[4] * e[i][0] + L[5] * e[i][1] + L[6] * e[i][2];
 #pragma unroll
@@ -323,5 +334,5 @@ __device__ __forceinline__ void far_features(const float* L, const float* C, flo
     moment_frame(L + 7, e, f + 15);
     f[21] = sqrtf(L[4] * L[4] + L[5] * L[5] + L[6] * L[6]);
     f[22] = sqrtf(C[4] * C[4] + C[5] * C[5] + C[6] * C[6]);
-    f[23] = logf(C[0] / L[0]);
+    f[23] = lc - ll;
 }

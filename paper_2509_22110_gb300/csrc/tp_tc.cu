@@ -181,8 +181,10 @@ struct TcSmem {
     unsigned char w2[64 * 64 * 2];       // W2
     unsigned char w3[64 * 64 * 2];       // W3
     unsigned char w4[16 * 64 * 2];       // W4 padded to N = 16
-    unsigned char a[128 * MLP_NIP * 2];  // input tile
-    unsigned char h[2][128 * 64 * 2];    // hidden activations (ping-pong)
+    // activations: the input tile (K = 32) and then each hidden layer's output
+    // (K = 64) in place - a layer's MMAs have completed (mbarrier) before its
+    // epilogue overwrites their A operand
+    unsigned char act[128 * 64 * 2];
     float bias[MLPF_N];
     uint64_t mbar;
     uint32_t tmem;
@@ -245,7 +247,7 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const __nv_bfloat16* __restrict_
     tc_fence_after();
     const uint32_t tmem = S.tmem;
     const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
-    const uint32_t sa = su32(S.a), sh0 = su32(S.h[0]), sh1 = su32(S.h[1]);
+    const uint32_t sact = su32(S.act);
     const uint32_t id64 = umma_idesc(128, 64), id16 = umma_idesc(128, 16);
     uint32_t phase = 0;
     bool failed = false;
@@ -271,7 +273,7 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const __nv_bfloat16* __restrict_
         load_row(t + gridDim.x, vnext);  // in flight during this tile's layers
         const bool in_dist = (v[3].w >> 16) != 0u;  // column 31
 #pragma unroll
-        for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4*>(S.a + tile_off(tid, 8 * q, MLP_NIP)) = v[q];
+        for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4*>(S.act + tile_off(tid, 8 * q, MLP_NIP)) = v[q];
         uint32_t r[64];
         // layers 1..3: GELU epilogues into the hidden tiles
 #pragma unroll 1
@@ -282,11 +284,10 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const __nv_bfloat16* __restrict_
             tc_fence_after();
             if (tid == 0) {
                 const int K = layer == 0 ? MLP_NIP : 64;
-                const uint32_t a0 = layer == 0 ? sa : (layer == 1 ? sh0 : sh1);
                 const uint32_t b0 = su32(layer == 0 ? S.w1 : (layer == 1 ? S.w2 : S.w3));
                 for (int kk = 0; kk < K / 16; ++kk)
-                    tc_mma(tmem, umma_desc(a0 + 256 * kk, 128, 16 * K), umma_desc(b0 + 256 * kk, 128, 16 * K), id64,
-                           kk > 0);
+                    tc_mma(tmem, umma_desc(sact + 256 * kk, 128, 16 * K), umma_desc(b0 + 256 * kk, 128, 16 * K),
+                           id64, kk > 0);
                 tc_commit(&S.mbar);
             }
             if (__syncthreads_or(!mbar_wait(&S.mbar, phase))) {  // the same decision in every thread
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const __nv_bfloat16* __restrict_
             phase ^= 1u;
             tc_fence_after();
             tc_ld64(taddr, r);
-            epi_hidden(r, S.bias + 64 * layer, S.h[layer & 1], tid);  // layer 0 -> h0, 1 -> h1, 2 -> h0
+            epi_hidden(r, S.bias + 64 * layer, S.act, tid);
         }
         if (failed) break;
         // output layer (N = 16, rows 7..15 of W4 zero)
@@ -306,8 +307,8 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const __nv_bfloat16* __restrict_
         tc_fence_after();
         if (tid == 0) {
             for (int kk = 0; kk < 4; ++kk)
-                tc_mma(tmem, umma_desc(sh0 + 256 * kk, 128, 1024), umma_desc(su32(S.w4) + 256 * kk, 128, 1024), id16,
-                       kk > 0);
+                tc_mma(tmem, umma_desc(sact + 256 * kk, 128, 1024), umma_desc(su32(S.w4) + 256 * kk, 128, 1024),
+                       id16, kk > 0);
             tc_commit(&S.mbar);
         }
         if (__syncthreads_or(!mbar_wait(&S.mbar, phase))) {
@@ -357,7 +358,8 @@ tp_status tp_launch_mlp_tc(tp_ctx* ctx, const __nv_bfloat16* wb, const float* bi
     }
     const int64_t ntiles = (rows + 127) / 128;
     if (ntiles == 0) return TP_OK;
-    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * 3);
+    // about 40 KB of shared memory and 64 tensor-memory columns per CTA: 5 CTAs per SM
+    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * 5);
     k_mlp_tc<<<grid, 128, sizeof(TcSmem), ctx->stream>>>(wb, bias, X, rows, kf, raw, ctx->derr);
     ++ctx->nlaunch;
     TP_CU(cudaGetLastError());
