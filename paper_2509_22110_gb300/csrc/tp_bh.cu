@@ -41,8 +41,6 @@
 #include <stdint.h>
 #include <string.h>
 
-#include <type_traits>
-
 #include "tp_internal.cuh"
 #include "tp_mlp_dev.cuh"
 
@@ -83,10 +81,17 @@ struct BHArgs {
     const __nv_bfloat16* wb;     // network weights (BF16 block)
     const float* mbias;          // network biases
     const float* mnorm;          // [4][24] feature mean, std, lo, hi
-    int32_t* far_list;           // M_LIST: far node ids, in runs of one leaf
-    tp_far_run* far_runs;        // M_LIST: the runs
-    unsigned long long* far_count;  // [2] rows and runs listed (counted past the capacities)
+    // far field: far node ids listed for k_far, in runs of one leaf
+    int32_t* far_list;
+    tp_far_run* far_runs;
+    unsigned long long* far_count;  // [0] rows, [1] runs listed (past the capacities), [2] k_far work counter
     int64_t far_cap, run_cap;
+    // near field: clusters apart from the leaf, listed for k_near
+    const float* src;            // [ntp][TP_SRCW] source records (each value twice)
+    int2* near_list;             // (first member, count) per listed cluster
+    tp_far_run* near_runs;       // runs of one leaf
+    unsigned long long* near_count;  // [0] entries, [1] runs listed (past the capacities), [2] k_near work counter
+    int64_t near_cap, nrun_cap;
     // sampling of far pairs (RECORD mode)
     uint32_t keep_u;
     uint64_t seed;
@@ -95,8 +100,11 @@ struct BHArgs {
     int32_t* rec_count;
 };
 
-// M_BH: evaluate; M_LIST: evaluate and list the far nodes of every leaf for
-// the learned correction; M_RECORD: sample far pairs for training only.
+// M_BH: the evaluation pass of the plain form (evaluates the far nodes and
+// the touching near clusters, lists the near clusters apart from the leaf for
+// k_near); M_LIST: the same for the learned form, with the far nodes listed
+// for the network and k_far instead of evaluated; M_RECORD: sample far pairs
+// for training only.
 enum { M_BH = 0, M_LIST = 1, M_RECORD = 2 };
 
 __device__ __forceinline__ float bh_rcp(float x) {
@@ -135,35 +143,31 @@ __device__ __forceinline__ void stage_pad(float* stg, int j) {
     stage_put(stg, j, v);
 }
 
-// T-side derivatives of e_TS + e_ST for the staged source pair p (data at
-// stg + p * BH_PAIR), accumulated in the direct kernels' convention.  SEL:
-// per-half admission (v0, v1); an excluded half gets 1/|d|^2 = 0 and weight
-// 0, so its terms are exact zeros (d itself stays finite: a coincident
-// centroid or the padding source's large offset never reaches a power).
+// T-side derivatives of e_TS + e_ST for two (target, source) pairs at once,
+// one per half of the float2 operands (targets th..tw, sources sh..sw),
+// accumulated in the direct kernels' convention.  SEL: per-half admission
+// (v0, v1); an excluded half gets 1/|d|^2 = 0 and weight 0, so its terms are
+// exact zeros (d itself stays finite: a coincident centroid or a padding
+// source's large offset never reaches a power).
 template <int Q, bool SEL>
-__device__ __forceinline__ void gather_pair2(const Tgt2& t, const float* stg, int p, float2 acc[8], bool v0 = true,
-                                             bool v1 = true) {
-    const float4* r = reinterpret_cast<const float4*>(stg + p * BH_PAIR);
-    const float4 q0 = r[0], q1 = r[1], q2 = r[2], q3 = r[3], q4 = r[4];
-    const float2 sh[3] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y)};
-    const float2 sl[3] = {make_float2(q1.z, q1.w), make_float2(q2.x, q2.y), make_float2(q2.z, q2.w)};
-    const float2 sn[3] = {make_float2(q3.x, q3.y), make_float2(q3.z, q3.w), make_float2(q4.x, q4.y)};
-    const float2 sw = make_float2(q4.z, q4.w);
+__device__ __forceinline__ void pair_core(const float2 (&th)[3], const float2 (&tl)[3], const float2 (&tn)[3],
+                                          float2 tw, const float2 (&sh)[3], const float2 (&sl)[3],
+                                          const float2 (&sn)[3], float2 sw, float2 acc[8], bool v0, bool v1) {
     float2 d[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) d[k] = bh_add2(bh_add2(t.h[k], bh_neg2(sh[k])), bh_add2(t.l[k], bh_neg2(sl[k])));
+    for (int k = 0; k < 3; ++k) d[k] = bh_add2(bh_add2(th[k], bh_neg2(sh[k])), bh_add2(tl[k], bh_neg2(sl[k])));
     float2 r2 = bh_mul2(d[0], d[0]);
     r2 = bh_fma2(d[1], d[1], r2);
     r2 = bh_fma2(d[2], d[2], r2);
-    float2 wts = bh_mul2(t.w, sw);
+    float2 wts = bh_mul2(tw, sw);
     float2 inv = make_float2(bh_rcp(r2.x), bh_rcp(r2.y));
     if (SEL) {
         inv = make_float2(v0 ? inv.x : 0.f, v1 ? inv.y : 0.f);
         wts = make_float2(v0 ? wts.x : 0.f, v1 ? wts.y : 0.f);
     }
-    float2 a = bh_mul2(t.n[0], d[0]);
-    a = bh_fma2(t.n[1], d[1], a);
-    a = bh_fma2(t.n[2], d[2], a);
+    float2 a = bh_mul2(tn[0], d[0]);
+    a = bh_fma2(tn[1], d[1], a);
+    a = bh_fma2(tn[2], d[2], a);
     float2 b = bh_mul2(sn[0], d[0]);
     b = bh_fma2(sn[1], d[1], b);
     b = bh_fma2(sn[2], d[2], b);
@@ -192,6 +196,31 @@ __device__ __forceinline__ void gather_pair2(const Tgt2& t, const float* stg, in
     }
 }
 
+// One target (duplicated in both halves of t) against the staged source pair
+// p (data at stg + p * BH_PAIR).
+template <int Q, bool SEL>
+__device__ __forceinline__ void gather_pair2(const Tgt2& t, const float* stg, int p, float2 acc[8], bool v0 = true,
+                                             bool v1 = true) {
+    const float4* r = reinterpret_cast<const float4*>(stg + p * BH_PAIR);
+    const float4 q0 = r[0], q1 = r[1], q2 = r[2], q3 = r[3], q4 = r[4];
+    const float2 sh[3] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y)};
+    const float2 sl[3] = {make_float2(q1.z, q1.w), make_float2(q2.x, q2.y), make_float2(q2.z, q2.w)};
+    const float2 sn[3] = {make_float2(q3.x, q3.y), make_float2(q3.z, q3.w), make_float2(q4.x, q4.y)};
+    pair_core<Q, SEL>(t.h, t.l, t.n, t.w, sh, sl, sn, make_float2(q4.z, q4.w), acc, v0, v1);
+}
+
+// A pair of targets (one per half of t) against one source record of the
+// direct kernels' layout (each value stored twice: x_hi[3], x_lo[3], nu[3], w~).
+template <int Q>
+__device__ __forceinline__ void near_pair2(const Tgt2& t, const float* rec, float2 acc[8]) {
+    const float4* r = reinterpret_cast<const float4*>(rec);
+    const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4];
+    const float2 sh[3] = {make_float2(r0.x, r0.y), make_float2(r0.z, r0.w), make_float2(r1.x, r1.y)};
+    const float2 sl[3] = {make_float2(r1.z, r1.w), make_float2(r2.x, r2.y), make_float2(r2.z, r2.w)};
+    const float2 sn[3] = {make_float2(r3.x, r3.y), make_float2(r3.z, r3.w), make_float2(r4.x, r4.y)};
+    pair_core<Q, false>(t.h, t.l, t.n, t.w, sh, sl, sn, make_float2(r4.z, r4.w), acc, true, true);
+}
+
 // Target-leaf constants of the admissibility test.
 struct LeafAdm {
     double bl[6];      // FP64 vertex box
@@ -217,71 +246,6 @@ __device__ __forceinline__ void leaf_adm(const double* box, LeafAdm& L) {
     }
     L.dl = __dsqrt_rn(dl2);
     L.dl32 = (float)L.dl;
-}
-
-// The same far term with the network's per-channel factors kf[0..6], for the
-// staged source pair p (records at stg + p * BH_PAIR, factors interleaved at
-// skf + p * 16):
-// E = wts (kf0 al^q + kf1 be^q), U: kf2 A5, Gn: kf3 A5 d, Gx: kf4 B5 nubar - k d,
-// k = (p/q) wts inv (kf5 al^q + kf6 be^q).  A padding source has zero weight
-// and zero factors.
-template <int Q>
-__device__ __forceinline__ void gather_pair_learned2(const Tgt2& t, const float* stg, const float* skf, int p,
-                                                     float2 acc[8]) {
-    const float4* r = reinterpret_cast<const float4*>(stg + p * BH_PAIR);
-    const float4 q0 = r[0], q1 = r[1], q2 = r[2], q3 = r[3], q4 = r[4];
-    const float4* kq = reinterpret_cast<const float4*>(skf + p * 16);
-    const float4 k01 = kq[0], k23 = kq[1], k45 = kq[2], k6f = kq[3];
-    const float2 sh[3] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y)};
-    const float2 sl[3] = {make_float2(q1.z, q1.w), make_float2(q2.x, q2.y), make_float2(q2.z, q2.w)};
-    const float2 sn[3] = {make_float2(q3.x, q3.y), make_float2(q3.z, q3.w), make_float2(q4.x, q4.y)};
-    const float2 sw = make_float2(q4.z, q4.w);
-    float2 d[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) d[k] = bh_add2(bh_add2(t.h[k], bh_neg2(sh[k])), bh_add2(t.l[k], bh_neg2(sl[k])));
-    float2 r2 = bh_mul2(d[0], d[0]);
-    r2 = bh_fma2(d[1], d[1], r2);
-    r2 = bh_fma2(d[2], d[2], r2);
-    const float2 wts = bh_mul2(t.w, sw);
-    const float2 inv = make_float2(bh_rcp(r2.x), bh_rcp(r2.y));
-    float2 a = bh_mul2(t.n[0], d[0]);
-    a = bh_fma2(t.n[1], d[1], a);
-    a = bh_fma2(t.n[2], d[2], a);
-    float2 b = bh_mul2(sn[0], d[0]);
-    b = bh_fma2(sn[1], d[1], b);
-    b = bh_fma2(sn[2], d[2], b);
-    const float2 al = bh_mul2(a, inv), be = bh_mul2(b, inv);
-    const float2 al2 = bh_mul2(al, al), be2 = bh_mul2(be, be);
-    const float2 al4 = bh_mul2(al2, al2), be4 = bh_mul2(be2, be2);
-    float2 alq, beq, al5, be5;
-    if (Q == 6) {
-        alq = bh_mul2(al4, al2);
-        beq = bh_mul2(be4, be2);
-        al5 = bh_mul2(al4, al);
-        be5 = bh_mul2(be4, be);
-    } else {
-        alq = bh_mul2(al4, al4);
-        beq = bh_mul2(be4, be4);
-        al5 = bh_mul2(bh_mul2(al4, al2), al);
-        be5 = bh_mul2(bh_mul2(be4, be2), be);
-    }
-    const float2 kf0 = make_float2(k01.x, k01.y), kf1 = make_float2(k01.z, k01.w);
-    const float2 kf2 = make_float2(k23.x, k23.y), kf3 = make_float2(k23.z, k23.w);
-    const float2 kf4 = make_float2(k45.x, k45.y), kf5 = make_float2(k45.z, k45.w);
-    const float2 kf6 = make_float2(k6f.x, k6f.y);
-    const float2 wi = bh_mul2(wts, inv);
-    const float2 A5 = bh_mul2(wi, al5), B5 = bh_mul2(wi, be5);
-    const float2 se = bh_fma2(kf1, beq, bh_mul2(kf0, alq));
-    const float2 sk = bh_fma2(kf6, beq, bh_mul2(kf5, alq));
-    const float2 nk = bh_mul2(bh_mul2(wi, sk), bh_f2(-2.0f));  // -(p/q) wts inv (kf5 al^q + kf6 be^q)
-    const float2 gA = bh_mul2(kf3, A5), gB = bh_mul2(kf4, B5);
-    acc[0] = bh_fma2(wts, se, acc[0]);
-    acc[1] = bh_fma2(kf2, A5, acc[1]);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        acc[2 + k] = bh_fma2(gA, d[k], acc[2 + k]);
-        acc[5 + k] = bh_fma2(nk, d[k], bh_fma2(gB, sn[k], acc[5 + k]));
-    }
 }
 
 __device__ __forceinline__ uint64_t bh_mix(uint64_t x) {
@@ -409,55 +373,87 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
     unsigned long long n_near = 0, n_far = 0, n_farp = 0;
     const unsigned lt = (1u << lane) - 1u;
 
-    // far list: stage 32 node records at a time, then sweep them in pairs
-    auto flush_far = [&](int nf) {
-        if (MODE == M_LIST && nf > 0) {
-            // one run of this leaf: reserve rows and a run record, store the node ids
-            unsigned long long pos = 0, run = 0;
-            if (lane == 0) {
-                pos = atomicAdd(&A.far_count[0], (unsigned long long)nf);
-                run = atomicAdd(&A.far_count[1], 1ull);
-            }
-            pos = __shfl_sync(0xffffffffu, pos, 0);
-            run = __shfl_sync(0xffffffffu, run, 0);
-            if (pos + (unsigned long long)nf <= (unsigned long long)A.far_cap &&
-                run < (unsigned long long)A.run_cap) {
-                for (int i = lane; i < nf; i += 32) A.far_list[pos + i] = far[i];
-                if (lane == 0) {
-                    tp_far_run fr;
-                    fr.start = (int64_t)pos;
-                    fr.li = (int32_t)li;
-                    fr.len = nf;
-                    A.far_runs[run] = fr;
-                }
-            }
+    // far nodes of the learned form: one run of node ids for the network and
+    // the far-field kernel (k_far),
+    // reserved with one atomic per run; a run whose ids do not fit is recorded
+    // with no rows (the host sees the overflow in the counts and repeats the
+    // evaluation)
+    auto emit_far = [&](int nf) {
+        if (nf == 0) return;
+        unsigned long long pos = 0, run = 0;
+        if (lane == 0) {
+            pos = atomicAdd(&A.far_count[0], (unsigned long long)nf);
+            run = atomicAdd(&A.far_count[1], 1ull);
         }
-        float2 a2[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) a2[c] = bh_f2(0.f);
-        for (int b0 = 0; b0 < nf; b0 += 32) {
-            const int nb = nf - b0 < 32 ? nf - b0 : 32;
-            __syncwarp();
-            if (lane < nb) {
-                const float4* r = reinterpret_cast<const float4*>(A.nodef + 16 * (int64_t)far[b0 + lane]);
-                const float4 r0 = r[0], r1 = r[1], r2 = r[2];
-                const float v[10] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y};
-                stage_put(stg, lane, v);
-            } else if (lane == nb && (nb & 1)) {
-                stage_pad(stg, lane);
-            }
-            __syncwarp();
-            const int np = (nb + 1) >> 1;
-            for (int p = half; p < np; p += nh) gather_pair2<Q, false>(tg, stg, p, a2);
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        run = __shfl_sync(0xffffffffu, run, 0);
+        const bool fits = pos + (unsigned long long)nf <= (unsigned long long)A.far_cap;
+        if (fits)
+            for (int i = lane; i < nf; i += 32) A.far_list[pos + i] = far[i];
+        if (lane == 0 && run < (unsigned long long)A.run_cap) {
+            tp_far_run fr;
+            fr.start = fits ? (int64_t)pos : 0;
+            fr.li = (int32_t)li;
+            fr.len = fits ? nf : 0;
+            A.far_runs[run] = fr;
         }
-#pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] += (double)(a2[c].x + a2[c].y);
     };
-    // near lists: stage the members of up to 32 sources at a time (whole near
-    // nodes), then sweep them in pairs; TOUCH: nodes whose box meets the
-    // leaf's, where every pair is tested for exclusion
-    auto flush_near = [&](const int2* nl, int nn, auto touch_tag) {
-        constexpr bool TOUCH = decltype(touch_tag)::value;
+    // far nodes of the plain form: stage 32 node records at a time, then
+    // sweep them in pairs (one target against two records per packed step)
+    auto flush_far = [&](int nf) {
+        if constexpr (MODE == M_LIST) {
+            emit_far(nf);
+        } else {
+            float2 a2[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) a2[c] = bh_f2(0.f);
+            for (int b0 = 0; b0 < nf; b0 += 32) {
+                const int nb = nf - b0 < 32 ? nf - b0 : 32;
+                __syncwarp();
+                if (lane < nb) {
+                    const float4* r = reinterpret_cast<const float4*>(A.nodef + 16 * (int64_t)far[b0 + lane]);
+                    const float4 r0 = r[0], r1 = r[1], r2 = r[2];
+                    const float v[10] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y};
+                    stage_put(stg, lane, v);
+                } else if (lane == nb && (nb & 1)) {
+                    stage_pad(stg, lane);
+                }
+                __syncwarp();
+                const int np = (nb + 1) >> 1;
+                for (int p = half; p < np; p += nh) gather_pair2<Q, false>(tg, stg, p, a2);
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] += (double)(a2[c].x + a2[c].y);
+        }
+    };
+    // near clusters apart from the leaf: one run of (first member, count)
+    // entries for the near-field kernel (k_near), reserved with one atomic per
+    // run; a run whose entries do not fit is recorded with no entries (the
+    // host sees the overflow in the counts and repeats the evaluation)
+    auto emit_near = [&](int nn) {
+        if (nn == 0) return;
+        unsigned long long pos = 0, run = 0;
+        if (lane == 0) {
+            pos = atomicAdd(&A.near_count[0], (unsigned long long)nn);
+            run = atomicAdd(&A.near_count[1], 1ull);
+        }
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        run = __shfl_sync(0xffffffffu, run, 0);
+        const bool fits = pos + (unsigned long long)nn <= (unsigned long long)A.near_cap;
+        if (fits)
+            for (int i = lane; i < nn; i += 32) A.near_list[pos + i] = s_near[warp][0][i];
+        if (lane == 0 && run < (unsigned long long)A.nrun_cap) {
+            tp_far_run nr;
+            nr.start = fits ? (int64_t)pos : 0;
+            nr.li = (int32_t)li;
+            nr.len = fits ? nn : 0;
+            A.near_runs[run] = nr;
+        }
+    };
+    // near clusters whose box touches the leaf's: stage the members of up to
+    // 32 sources at a time (whole clusters), then sweep them in pairs with the
+    // exclusion test on every pair
+    auto flush_touch = [&](const int2* nl, int nn) {
         float2 a2[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) a2[c] = bh_f2(0.f);
@@ -478,37 +474,31 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
 #pragma unroll
                         for (int c = 0; c < 10; ++c) v[c] = A.soa[c * A.ntp + s];
                         stage_put(stg, lane, v);
-                        if (TOUCH) stg_f[lane] = make_int4(A.Fs[3 * s], A.Fs[3 * s + 1], A.Fs[3 * s + 2], (int)s);
+                        stg_f[lane] = make_int4(A.Fs[3 * s], A.Fs[3 * s + 1], A.Fs[3 * s + 2], (int)s);
                     }
                     base += nd.y;
                 }
                 if (lane == nsrc && (nsrc & 1)) {
                     stage_pad(stg, lane);
-                    if (TOUCH) stg_f[lane] = make_int4(-1, -1, -1, -1);
+                    stg_f[lane] = make_int4(-1, -1, -1, -1);
                 }
             }
             __syncwarp();
             const int np = (nsrc + 1) >> 1;
             for (int p = half; p < np; p += nh) {
-                if (TOUCH) {
-                    const int4 f0 = stg_f[2 * p], f1 = stg_f[2 * p + 1];
-                    const bool v0 = active && f0.w >= 0 && f0.w != (int)k &&
-                                    !adjacent(tf, make_int3(f0.x, f0.y, f0.z), A.edge_only);
-                    const bool v1 = active && f1.w >= 0 && f1.w != (int)k &&
-                                    !adjacent(tf, make_int3(f1.x, f1.y, f1.z), A.edge_only);
-                    gather_pair2<Q, true>(tg, stg, p, a2, v0, v1);
-                    n_near += (unsigned long long)(v0 + v1);
-                } else {
-                    gather_pair2<Q, false>(tg, stg, p, a2);
-                }
+                const int4 f0 = stg_f[2 * p], f1 = stg_f[2 * p + 1];
+                const bool v0 = active && f0.w >= 0 && f0.w != (int)k &&
+                                !adjacent(tf, make_int3(f0.x, f0.y, f0.z), A.edge_only);
+                const bool v1 = active && f1.w >= 0 && f1.w != (int)k &&
+                                !adjacent(tf, make_int3(f1.x, f1.y, f1.z), A.edge_only);
+                gather_pair2<Q, true>(tg, stg, p, a2, v0, v1);
+                n_near += (unsigned long long)(v0 + v1);
             }
             i = i1;
         }
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[c] += (double)(a2[c].x + a2[c].y);
     };
-    using Apart = std::false_type;
-    using Touch = std::true_type;
 
     int sp = 1, nf = 0, nn[2] = {0, 0};
     if (lane == 0) st[0] = 0;  // root
@@ -575,11 +565,11 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
             nf = 0;
         }
         if (nn[0] > BH_NEAR - 32) {
-            flush_near(s_near[warp][0], nn[0], Apart{});
+            emit_near(nn[0]);
             nn[0] = 0;
         }
         if (nn[1] > BH_NEAR - 32) {
-            flush_near(s_near[warp][1], nn[1], Touch{});
+            flush_touch(s_near[warp][1], nn[1]);
             nn[1] = 0;
         }
         __syncwarp();
@@ -590,8 +580,8 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
     }
     if (MODE == M_RECORD) return;
     flush_far(nf);
-    flush_near(s_near[warp][0], nn[0], Apart{});
-    flush_near(s_near[warp][1], nn[1], Touch{});
+    emit_near(nn[0]);
+    flush_touch(s_near[warp][1], nn[1]);
     if (!wide) {
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 16);
@@ -612,22 +602,394 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
     }
 }
 
+// ------------------------------------------------------------ near field
+// The near clusters apart from a leaf (listed by k_bh in runs of up to
+// BH_NEAR clusters) are summed by k_near, one warp per run (taken from a work
+// counter).  Lanes are (target pair, source stream), sized to the leaf: its
+// cnt targets make np = ceil(cnt / 2) pairs and the warp runs 32 / np streams
+// (a leaf of 11 triangles: 6 pairs x 5 streams), so few lanes idle; each lane
+// evaluates its two targets against every ns-th source in packed FP32x2
+// arithmetic.  Sources are the direct kernels' records (80 B, each value
+// twice, so one record feeds both halves): whole clusters are copied into a
+// two-slot ring of NR_SLOT records per warp with cp.async.bulk, completion on
+// an mbarrier per slot (bounded waits), so the next slot's copies run while
+// this one is evaluated.  The energy channel is folded into FP64 after every
+// slot; at the end of the run the streams are summed through shared memory
+// (the ring, free by then) and the targets' FP64 accumulators are updated
+// atomically (runs of one leaf may be
+// in flight in several warps, after k_bh has stored its own part).
+#ifndef TP_NR_SLOT
+#define TP_NR_SLOT 64
+#endif
+constexpr int NR_WARPS = 4;
+constexpr int NR_SLOT = TP_NR_SLOT;  // source records per ring slot
+static_assert(NR_SLOT >= 32, "a slot must hold the largest cluster leaf (32 triangles)");
+
+struct NearWarpSmem {
+    float rec[2][NR_SLOT * TP_SRCW];
+    int2 ent[BH_NEAR];
+    uint64_t bar[2];
+};
+
+template <int Q>
+__global__ void __launch_bounds__(NR_WARPS * 32) k_near(BHArgs A) {
+    __shared__ __align__(128) NearWarpSmem s_w[NR_WARPS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    NearWarpSmem& S = s_w[warp];
+    if (lane == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncwarp();
+    uint32_t ph0 = 0u, ph1 = 0u;  // phase parities of the two slots' mbarriers (scalars: no local memory)
+    const unsigned long long nr = A.near_count[1];
+    const int64_t nruns = nr < (unsigned long long)A.nrun_cap ? (int64_t)nr : A.nrun_cap;
+    bool failed = false;
+    while (!failed) {
+        int64_t run = 0;
+        if (lane == 0) run = (int64_t)atomicAdd(&A.near_count[2], 1ull);
+        run = __shfl_sync(0xffffffffu, run, 0);
+        if (run >= nruns) break;
+        const tp_far_run R = A.near_runs[run];
+        if (R.len <= 0 || R.len > BH_NEAR || R.li < 0 || (int64_t)R.li >= A.nleaves || R.start < 0 ||
+            R.start + R.len > A.near_cap)
+            continue;  // a run whose entries overflowed the list (the evaluation is repeated)
+        const int64_t L = A.leaves[R.li];
+        const int64_t fL = A.first[L];
+        const int cnt = A.last[L] - A.first[L] + 1;
+        const int npair = (cnt + 1) >> 1;           // target pairs
+        const int ng = 32 / npair;                  // source streams
+        const int tpl = lane % npair, g = lane / npair;  // this lane's pair and stream (g >= ng: idle)
+        for (int i = lane; i < R.len; i += 32) S.ent[i] = A.near_list[R.start + i];
+        // this lane's two targets, fL + 2 tpl + h (h = 0, 1); absent ones have zero weight
+        Tgt2 tg;
+        bool act[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int t = 2 * tpl + h;
+            act[h] = t < cnt && g < ng;
+            const int64_t k = fL + (act[h] ? t : 0);
+            float v[10];
+#pragma unroll
+            for (int c = 0; c < 10; ++c) v[c] = act[h] ? A.soa[c * A.ntp + k] : 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                (h ? tg.h[c].y : tg.h[c].x) = v[c];
+                (h ? tg.l[c].y : tg.l[c].x) = v[3 + c];
+                (h ? tg.n[c].y : tg.n[c].x) = v[6 + c];
+            }
+            (h ? tg.w.y : tg.w.x) = v[9];
+        }
+        __syncwarp();
+        // slot planning: whole clusters while they fit; lane 0 issues the copies
+        int next = 0, ns0 = 0, ns1 = 0;  // records planned into slot 0 / 1 and not yet consumed
+        auto plan = [&](int b) {
+            int n = 0;
+            const int i0 = next;
+            while (next < R.len && n + S.ent[next].y <= NR_SLOT) n += S.ent[next++].y;
+            if (b) ns1 = n;
+            else ns0 = n;
+            if (n == 0) {
+                // a cluster larger than a slot cannot occur (leaves hold at most 32)
+                if (next < R.len && lane == 0) tp_dev_error(A.derr, TP_DERR_INDEX);
+                return;
+            }
+            if (lane == 0) {
+                mbar_expect_tx(&S.bar[b], (uint32_t)(n * TP_SRCW * 4));
+                int o = 0;
+                for (int e = i0; e < next; ++e) {
+                    const int2 en = S.ent[e];
+                    tma_load_1d(S.rec[b] + o * TP_SRCW, A.src + (int64_t)en.x * TP_SRCW,
+                                (uint32_t)(en.y * TP_SRCW * 4), &S.bar[b]);
+                    o += en.y;
+                }
+            }
+        };
+        plan(0);
+        plan(1);
+        float2 a2[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a2[c] = bh_f2(0.f);
+        double e64[2] = {0.0, 0.0};
+        for (int slot = 0;; ++slot) {
+            const int b = slot & 1;
+            const int n = b ? ns1 : ns0;
+            if (n == 0) break;  // nothing planned (an empty run)
+            const bool ok = mbar_wait_bounded(&S.bar[b], b ? ph1 : ph0);
+            if (!__all_sync(0xffffffffu, ok)) {  // the same decision in every lane
+                failed = true;
+                break;
+            }
+            if (b) {
+                ph1 ^= 1u;
+                ns1 = 0;  // consumed (planned again below)
+            } else {
+                ph0 ^= 1u;
+                ns0 = 0;
+            }
+            const float* rb = S.rec[b];
+            if (g < ng)
+                for (int j = g; j < n; j += ng) near_pair2<Q>(tg, rb + j * TP_SRCW, a2);
+            e64[0] += (double)a2[0].x;
+            e64[1] += (double)a2[0].y;
+            a2[0] = bh_f2(0.f);
+            __syncwarp();  // every lane is done with slot b before it is refilled
+            plan(b);
+            if (ns0 == 0 && ns1 == 0) break;
+        }
+        if (failed) {
+            // copies of either slot may still be in flight: wait for them (bounded,
+            // the phases of slots not yet consumed) before this warp stops using
+            // its shared memory
+            if (lane == 0) tp_dev_error(A.derr, TP_DERR_TIMEOUT);
+            if (ns0 > 0) mbar_wait_bounded(&S.bar[0], ph0);
+            if (ns1 > 0) mbar_wait_bounded(&S.bar[1], ph1);
+            break;
+        }
+        // sum the source streams through shared memory (the ring is free: every
+        // planned slot has been consumed) and add to the targets
+        float* red = S.rec[0];  // [32 lanes][16] channel partials of both targets
+        double* ered = reinterpret_cast<double*>(S.rec[1]);  // [32 lanes][2] energies
+#pragma unroll
+        for (int c = 1; c < 8; ++c) {
+            red[lane * 16 + 2 * c] = a2[c].x;
+            red[lane * 16 + 2 * c + 1] = a2[c].y;
+        }
+        ered[2 * lane] = e64[0];
+        ered[2 * lane + 1] = e64[1];
+        __syncwarp();
+        if (lane < npair) {
+            for (int gg = 1; gg < ng; ++gg) {
+                const int o = gg * npair + lane;
+#pragma unroll
+                for (int c = 1; c < 8; ++c) {
+                    a2[c].x += red[o * 16 + 2 * c];
+                    a2[c].y += red[o * 16 + 2 * c + 1];
+                }
+                e64[0] += ered[2 * o];
+                e64[1] += ered[2 * o + 1];
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (!act[h]) continue;
+                const int64_t k = fL + 2 * tpl + h;
+                atomicAdd(&A.acc[k], e64[h]);
+#pragma unroll
+                for (int c = 1; c < 8; ++c) atomicAdd(&A.acc[c * A.ntp + k], (double)(h ? a2[c].y : a2[c].x));
+            }
+        }
+        __syncwarp();  // the entry list is reused by the next run
+    }
+}
+
+// ------------------------------------------------------------ learned far field
+// In the learned form the far nodes of every leaf (listed by k_bh in runs of
+// up to BH_FAR nodes) are evaluated by k_far after the network, one warp per
+// run (taken from a work counter), with the same leaf-sized lanes as k_near:
+// (target pair, record stream).  Each batch of 32 listed nodes is staged in
+// shared memory in the duplicated record layout with the network's channel
+// factors; the next batch's records are loaded into registers while this one
+// is evaluated.  Every channel c of the far term is scaled by the factor
+// exp(y_c) of its (leaf, cluster) row (1 outside the training ranges):
+// E = wts (f0 al^q + f1 be^q), U: f2 A5, Gn: f3 A5 d, Gx: f4 B5 nubar - k d,
+// k = (p/q) wts inv (f5 al^q + f6 be^q).  (The plain form evaluates its far
+// nodes inside k_bh, straight from the traversal's staged list.)
+template <int Q>
+__device__ __forceinline__ void far_pair2_learned(const Tgt2& t, const float* rec, const float* fk, float2 acc[8]) {
+    const float4* r = reinterpret_cast<const float4*>(rec);
+    const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4];
+    const float2 sh[3] = {make_float2(r0.x, r0.y), make_float2(r0.z, r0.w), make_float2(r1.x, r1.y)};
+    const float2 sl[3] = {make_float2(r1.z, r1.w), make_float2(r2.x, r2.y), make_float2(r2.z, r2.w)};
+    const float2 sn[3] = {make_float2(r3.x, r3.y), make_float2(r3.z, r3.w), make_float2(r4.x, r4.y)};
+    const float2 sw = make_float2(r4.z, r4.w);
+    const float4 f03 = reinterpret_cast<const float4*>(fk)[0], f47 = reinterpret_cast<const float4*>(fk)[1];
+    float2 d[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = bh_add2(bh_add2(t.h[k], bh_neg2(sh[k])), bh_add2(t.l[k], bh_neg2(sl[k])));
+    float2 r2s = bh_mul2(d[0], d[0]);
+    r2s = bh_fma2(d[1], d[1], r2s);
+    r2s = bh_fma2(d[2], d[2], r2s);
+    const float2 wts = bh_mul2(t.w, sw);
+    const float2 inv = make_float2(bh_rcp(r2s.x), bh_rcp(r2s.y));
+    float2 a = bh_mul2(t.n[0], d[0]);
+    a = bh_fma2(t.n[1], d[1], a);
+    a = bh_fma2(t.n[2], d[2], a);
+    float2 b = bh_mul2(sn[0], d[0]);
+    b = bh_fma2(sn[1], d[1], b);
+    b = bh_fma2(sn[2], d[2], b);
+    const float2 al = bh_mul2(a, inv), be = bh_mul2(b, inv);
+    const float2 al2 = bh_mul2(al, al), be2 = bh_mul2(be, be);
+    const float2 al4 = bh_mul2(al2, al2), be4 = bh_mul2(be2, be2);
+    float2 alq, beq, al5, be5;
+    if (Q == 6) {
+        alq = bh_mul2(al4, al2);
+        beq = bh_mul2(be4, be2);
+        al5 = bh_mul2(al4, al);
+        be5 = bh_mul2(be4, be);
+    } else {
+        alq = bh_mul2(al4, al4);
+        beq = bh_mul2(be4, be4);
+        al5 = bh_mul2(bh_mul2(al4, al2), al);
+        be5 = bh_mul2(bh_mul2(be4, be2), be);
+    }
+    const float2 wi = bh_mul2(wts, inv);
+    const float2 A5 = bh_mul2(wi, al5), B5 = bh_mul2(wi, be5);
+    const float2 se = bh_fma2(bh_f2(f03.y), beq, bh_mul2(bh_f2(f03.x), alq));
+    const float2 sk = bh_fma2(bh_f2(f47.z), beq, bh_mul2(bh_f2(f47.y), alq));
+    const float2 nk = bh_mul2(bh_mul2(wi, sk), bh_f2(-2.0f));  // -(p/q) wts inv (f5 al^q + f6 be^q)
+    const float2 gA = bh_mul2(bh_f2(f03.w), A5), gB = bh_mul2(bh_f2(f47.x), B5);
+    acc[0] = bh_fma2(wts, se, acc[0]);
+    acc[1] = bh_fma2(bh_f2(f03.z), A5, acc[1]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        acc[2 + k] = bh_fma2(gA, d[k], acc[2 + k]);
+        acc[5 + k] = bh_fma2(nk, d[k], bh_fma2(gB, sn[k], acc[5 + k]));
+    }
+}
+
+constexpr int FAR_WARPS = 8;
+
+template <int Q>
+__global__ void __launch_bounds__(FAR_WARPS * 32) k_far(BHArgs A, const float* __restrict__ kf) {
+    __shared__ __align__(16) float s_rec[FAR_WARPS][32 * TP_SRCW];  // duplicated records of a batch
+    __shared__ __align__(16) float s_fk[FAR_WARPS][32 * 8];         // channel factors of a batch
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* rec = s_rec[warp];
+    float* fk = s_fk[warp];
+    const unsigned long long nr = A.far_count[1];
+    const int64_t nruns = nr < (unsigned long long)A.run_cap ? (int64_t)nr : A.run_cap;
+    unsigned long long n_learn = 0;  // (target, row) pairs with the range flag set, counted by lane 0
+    while (true) {
+        int64_t run = 0;
+        if (lane == 0) run = (int64_t)atomicAdd(&A.far_count[2], 1ull);
+        run = __shfl_sync(0xffffffffu, run, 0);
+        if (run >= nruns) break;
+        const tp_far_run R = A.far_runs[run];
+        if (R.len <= 0 || R.len > BH_FAR || R.li < 0 || (int64_t)R.li >= A.nleaves || R.start < 0 ||
+            R.start + R.len > A.far_cap)
+            continue;  // a run whose rows overflowed the list (the evaluation is repeated)
+        const int64_t L = A.leaves[R.li];
+        const int64_t fL = A.first[L];
+        const int cnt = A.last[L] - A.first[L] + 1;
+        const int npair = (cnt + 1) >> 1;
+        const int ng = 32 / npair;
+        const int tpl = lane % npair, g = lane / npair;
+        Tgt2 tg;
+        bool act[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int t = 2 * tpl + h;
+            act[h] = t < cnt && g < ng;
+            const int64_t k = fL + (act[h] ? t : 0);
+            float v[10];
+#pragma unroll
+            for (int c = 0; c < 10; ++c) v[c] = act[h] ? A.soa[c * A.ntp + k] : 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                (h ? tg.h[c].y : tg.h[c].x) = v[c];
+                (h ? tg.l[c].y : tg.l[c].x) = v[3 + c];
+                (h ? tg.n[c].y : tg.n[c].x) = v[6 + c];
+            }
+            (h ? tg.w.y : tg.w.x) = v[9];
+        }
+        float2 a2[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a2[c] = bh_f2(0.f);
+        double e64[2] = {0.0, 0.0};
+        // this lane's row of a batch, loaded one batch ahead
+        float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0, q2 = q0, k0 = q0, k1 = q0;
+        auto load_row = [&](int b0, int nb) {
+            if (lane < nb) {
+                const int64_t row = R.start + b0 + lane;
+                const float4* r = reinterpret_cast<const float4*>(A.nodef + 16 * (int64_t)A.far_list[row]);
+                q0 = r[0];
+                q1 = r[1];
+                q2 = r[2];
+                const float4* kr = reinterpret_cast<const float4*>(kf + row * 8);
+                k0 = kr[0];
+                k1 = kr[1];
+            }
+        };
+        int nb = R.len < 32 ? R.len : 32;
+        load_row(0, nb);
+        for (int b0 = 0; b0 < R.len; b0 += 32) {
+            __syncwarp();  // the previous batch has been evaluated
+            if (lane < nb) {
+                float4* d = reinterpret_cast<float4*>(rec + lane * TP_SRCW);
+                d[0] = make_float4(q0.x, q0.x, q0.y, q0.y);  // x_hi
+                d[1] = make_float4(q0.z, q0.z, q0.w, q0.w);  // x_hi[2], x_lo[0]
+                d[2] = make_float4(q1.x, q1.x, q1.y, q1.y);  // x_lo[1..2]
+                d[3] = make_float4(q1.z, q1.z, q1.w, q1.w);  // nubar[0..1]
+                d[4] = make_float4(q2.x, q2.x, q2.y, q2.y);  // nubar[2], area
+                // factors exp(y_c) = 1 + (exp(y_c) - 1); the network wrote exp(y_c) - 1
+                float4* f = reinterpret_cast<float4*>(fk + lane * 8);
+                f[0] = make_float4(1.f + k0.x, 1.f + k0.y, 1.f + k0.z, 1.f + k0.w);
+                f[1] = make_float4(1.f + k1.x, 1.f + k1.y, 1.f + k1.z, k1.w);
+            }
+            const unsigned fb = __ballot_sync(0xffffffffu, lane < nb && k1.w != 0.f);
+            if (lane == 0) n_learn += (unsigned long long)__popc(fb) * (unsigned long long)cnt;
+            __syncwarp();
+            const int n = nb;
+            if (b0 + 32 < R.len) {
+                nb = R.len - (b0 + 32) < 32 ? R.len - (b0 + 32) : 32;
+                load_row(b0 + 32, nb);
+            }
+            if (g < ng) {
+                for (int j = g; j < n; j += ng) far_pair2_learned<Q>(tg, rec + j * TP_SRCW, fk + j * 8, a2);
+            }
+            e64[0] += (double)a2[0].x;
+            e64[1] += (double)a2[0].y;
+            a2[0] = bh_f2(0.f);
+        }
+        // sum the streams through shared memory and add to the targets
+        __syncwarp();
+        float* red = rec;                                // [32 lanes][16]
+        double* ered = reinterpret_cast<double*>(fk);    // [32 lanes][2]
+#pragma unroll
+        for (int c = 1; c < 8; ++c) {
+            red[lane * 16 + 2 * c] = a2[c].x;
+            red[lane * 16 + 2 * c + 1] = a2[c].y;
+        }
+        ered[2 * lane] = e64[0];
+        ered[2 * lane + 1] = e64[1];
+        __syncwarp();
+        if (lane < npair) {
+            for (int gg = 1; gg < ng; ++gg) {
+                const int o = gg * npair + lane;
+#pragma unroll
+                for (int c = 1; c < 8; ++c) {
+                    a2[c].x += red[o * 16 + 2 * c];
+                    a2[c].y += red[o * 16 + 2 * c + 1];
+                }
+                e64[0] += ered[2 * o];
+                e64[1] += ered[2 * o + 1];
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (!act[h]) continue;
+                const int64_t k = fL + 2 * tpl + h;
+                atomicAdd(&A.acc[k], e64[h]);
+#pragma unroll
+                for (int c = 1; c < 8; ++c) atomicAdd(&A.acc[c * A.ntp + k], (double)(h ? a2[c].y : a2[c].x));
+            }
+        }
+        __syncwarp();  // the staging buffers are reused by the next run
+    }
+    if (lane == 0 && n_learn) atomicAdd(&A.counts[3], n_learn);
+}
+
 // ------------------------------------------------------------ learned correction
-// The far terms evaluated by the Barnes-Hut pass carry factor 1 in every
-// channel; the network's factors kf replace them, so each listed (leaf L,
-// cluster C) pair adds (kf - 1) x channel to the targets of L.  Three passes
-// over the listed pairs:
-//   k_far_feat    - one warp per run: the 24 normalised features of every
-//                   (L, C) pair as a BF16 row (column 31 = 1 when the raw
-//                   features lie in the training ranges, else 0);
-//   k_mlp_tc      - the network on 128-row tiles on the 5th-generation
-//                   tensor cores (tcgen05.mma, operands in shared memory,
-//                   FP32 accumulators in tensor memory; tp_tc.cu): kf - 1 per
-//                   channel (0 outside the ranges);
-//   k_far_correct - one warp per run: (kf - 1) x the far-term channels for
-//                   the 16 targets of the leaf; runs of one leaf may be in
-//                   flight in different warps, so the FP32 run sums are added
-//                   to the FP64 accumulators atomically.
+// The network scales each channel of the far term of a listed (leaf L,
+// cluster C) pair by a factor.  Two passes over the listed pairs come before
+// k_far applies the factors:
+//   k_far_feat - one warp per run: the 24 normalised features of every
+//                (L, C) pair as a BF16 row (column 31 = 1 when the raw
+//                features lie in the training ranges, else 0);
+//   k_mlp_tc   - the network on 128-row tiles on the 5th-generation tensor
+//                cores (tcgen05.mma, operands in shared memory, FP32
+//                accumulators in tensor memory; tp_tc.cu): exp(y_c) - 1 per
+//                channel (0 outside the ranges).
 constexpr int FL_WARPS = 8;
 
 __global__ void __launch_bounds__(FL_WARPS * 32, 2) k_far_feat(BHArgs A, __nv_bfloat16* __restrict__ X) {
@@ -673,86 +1035,6 @@ __global__ void __launch_bounds__(FL_WARPS * 32, 2) k_far_feat(BHArgs A, __nv_bf
     }
 }
 
-template <int Q>
-__global__ void __launch_bounds__(FL_WARPS * 32) k_far_correct(BHArgs A, const float* __restrict__ kf) {
-    __shared__ __align__(16) float s_stg[FL_WARPS][16 * BH_PAIR];
-    __shared__ __align__(16) float s_kf[FL_WARPS][16 * 16];  // factors of source pairs, interleaved
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* stg = s_stg[warp];
-    float* skf = s_kf[warp];
-    const unsigned long long nr = A.far_count[1];
-    const int64_t nruns = nr < (unsigned long long)A.run_cap ? (int64_t)nr : A.run_cap;
-    const bool wide = A.leaf_size > 16;  // one target per lane, else two lanes per target
-    const int t = wide ? lane : (lane & 15), half = wide ? 0 : (lane >> 4), nh = wide ? 1 : 2;
-    unsigned long long n_learn = 0;  // (target, row) pairs with the range flag set, counted by lane 0
-    for (int64_t run = (int64_t)blockIdx.x * FL_WARPS + warp; run < nruns; run += (int64_t)gridDim.x * FL_WARPS) {
-        const tp_far_run R = A.far_runs[run];
-        const int64_t L = A.leaves[R.li];
-        const int64_t fL = A.first[L];
-        const int cnt = A.last[L] - A.first[L] + 1;
-        const bool active = t < cnt;
-        const int64_t k = fL + t;
-        Tgt2 tg;
-        if (active) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                tg.h[c] = bh_f2(A.soa[c * A.ntp + k]);
-                tg.l[c] = bh_f2(A.soa[(3 + c) * A.ntp + k]);
-                tg.n[c] = bh_f2(A.soa[(6 + c) * A.ntp + k]);
-            }
-            tg.w = bh_f2(A.soa[9 * A.ntp + k]);
-        } else {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) tg.h[c] = tg.l[c] = tg.n[c] = bh_f2(0.f);
-            tg.w = bh_f2(0.f);
-        }
-        float2 a2[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) a2[c] = bh_f2(0.f);
-        for (int b0 = 0; b0 < R.len; b0 += 32) {
-            const int nb = R.len - b0 < 32 ? R.len - b0 : 32;
-            __syncwarp();
-            bool flag = false;
-            float* kd = skf + (lane >> 1) * 16 + (lane & 1);
-            if (lane < nb) {
-                const int64_t row = R.start + b0 + lane;
-                const float4* r = reinterpret_cast<const float4*>(A.nodef + 16 * (int64_t)A.far_list[row]);
-                const float4 r0 = r[0], r1 = r[1], r2 = r[2];
-                const float v[10] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y};
-                stage_put(stg, lane, v);
-                const float4* kr = reinterpret_cast<const float4*>(kf + row * 8);
-                const float4 k0 = kr[0], k1 = kr[1];
-                const float kv[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
-#pragma unroll
-                for (int c = 0; c < 8; ++c) kd[2 * c] = kv[c];
-                flag = k1.w != 0.f;
-            } else if (lane == nb && (nb & 1)) {
-                stage_pad(stg, lane);
-#pragma unroll
-                for (int c = 0; c < 8; ++c) kd[2 * c] = 0.f;
-            }
-            const unsigned fb = __ballot_sync(0xffffffffu, flag);
-            if (lane == 0) n_learn += (unsigned long long)__popc(fb) * (unsigned long long)cnt;
-            __syncwarp();
-            const int np = (nb + 1) >> 1;
-            for (int p = half; p < np; p += nh) gather_pair_learned2<Q>(tg, stg, skf, p, a2);
-        }
-        float a32[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) a32[c] = a2[c].x + a2[c].y;
-        if (!wide) {
-#pragma unroll
-            for (int c = 0; c < 8; ++c) a32[c] += __shfl_xor_sync(0xffffffffu, a32[c], 16);
-        }
-        if (half == 0 && active) {
-#pragma unroll
-            for (int c = 0; c < 8; ++c)
-                if (a32[c] != 0.f) atomicAdd(&A.acc[c * A.ntp + k], (double)a32[c]);
-        }
-    }
-    if (lane == 0 && n_learn) atomicAdd(&A.counts[3], n_learn);
-}
-
 BHArgs make_bh_args(tp_ctx* ctx, double theta, int edge_only) {
     tp_tree& t = ctx->tree;
     BHArgs A;
@@ -786,84 +1068,127 @@ BHArgs make_bh_args(tp_ctx* ctx, double theta, int edge_only) {
 tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
     tp_tree& t = ctx->tree;
     if (t.leaf_size > 32) return tp_set_err(ctx, TP_E_ARG, "leaf_size above 32");
-    TP_CU(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * TP_NACC * ctx->ntp, ctx->stream));
     unsigned long long* counts = reinterpret_cast<unsigned long long*>(ctx->scalar + 2);
-    TP_CU(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), ctx->stream));
     BHArgs A = make_bh_args(ctx, prm->theta, (prm->flags & TP_EXCLUDE_EDGE) ? 1 : 0);
     A.counts = counts;
     const unsigned blocks = (unsigned)((t.nleaves + BH_WARPS - 1) / BH_WARPS);
+    // pair lists, first sized for about 256 near clusters and 1024 far nodes per
+    // leaf, then to the counted need
+    if (!ctx->near_count) TP_TRY(tp_alloc_t(ctx, &ctx->near_count, 3));
+    if (!ctx->far_count) TP_TRY(tp_alloc_t(ctx, &ctx->far_count, 3));
+    auto alloc_near = [&](int64_t ents, int64_t runs) -> tp_status {
+        TP_TRY(tp_alloc_t(ctx, &ctx->near_list, ents));
+        TP_TRY(tp_alloc_t(ctx, &ctx->near_runs, runs));
+        ctx->near_cap = ents;
+        ctx->nrun_cap = runs;
+        return TP_OK;
+    };
+    auto alloc_far = [&](int64_t rows, int64_t runs) -> tp_status {
+        rows = (rows + 31) / 32 * 32;  // whole 32-row network batches
+        TP_TRY(tp_alloc_t(ctx, &ctx->far_list, rows));
+        TP_TRY(tp_alloc_t(ctx, &ctx->far_runs, runs));
+        ctx->far_cap = rows;
+        ctx->run_cap = runs;
+        return TP_OK;
+    };
+    if (!ctx->near_list) {
+        const int64_t ents = std::max<int64_t>(1 << 20, t.nleaves * 256);
+        TP_TRY(alloc_near(ents, ents / 32 + t.nleaves + 1024));
+    }
+    if (!ctx->far_list) {
+        const int64_t rows = std::max<int64_t>(1 << 20, t.nleaves * 1024);
+        TP_TRY(alloc_far(rows, rows / 32 + t.nleaves + 1024));
+    }
+    const unsigned nblocks = (unsigned)std::max(1, ctx->num_sms * 4);
+    const unsigned fblocks = (unsigned)std::max(1, ctx->num_sms * 4);
     cudaEventRecord(ctx->ev[0], ctx->stream);
+    int64_t listed_rows = 0;
+    unsigned long long h[4] = {0, 0, 0, 0};
+    for (int attempt = 0;; ++attempt) {
+        TP_CU(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * TP_NACC * ctx->ntp, ctx->stream));
+        TP_CU(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), ctx->stream));
+        TP_CU(cudaMemsetAsync(ctx->near_count, 0, 3 * sizeof(unsigned long long), ctx->stream));
+        TP_CU(cudaMemsetAsync(ctx->far_count, 0, 3 * sizeof(unsigned long long), ctx->stream));
+        A.src = ctx->src;
+        A.near_list = ctx->near_list;
+        A.near_runs = ctx->near_runs;
+        A.near_count = ctx->near_count;
+        A.near_cap = ctx->near_cap;
+        A.nrun_cap = ctx->nrun_cap;
+        A.far_list = ctx->far_list;
+        A.far_runs = ctx->far_runs;
+        A.far_count = ctx->far_count;
+        A.far_cap = ctx->far_cap;
+        A.run_cap = ctx->run_cap;
+        // the traversal (far nodes evaluated or listed, touching near clusters
+        // evaluated, the other near clusters listed), then the listed near clusters
+        if (prm->q == 6) {
+            if (learned) k_bh<6, M_LIST><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
+            else k_bh<6, M_BH><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
+            k_near<6><<<nblocks, NR_WARPS * 32, 0, ctx->stream>>>(A);
+        } else {
+            if (learned) k_bh<8, M_LIST><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
+            else k_bh<8, M_BH><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
+            k_near<8><<<nblocks, NR_WARPS * 32, 0, ctx->stream>>>(A);
+        }
+        ctx->nlaunch += 2;
+        TP_CU(cudaGetLastError());
+        unsigned long long nc[2] = {0, 0}, fc[2] = {0, 0};
+        TP_CU(cudaMemcpyAsync(nc, ctx->near_count, sizeof(nc), cudaMemcpyDeviceToHost, ctx->stream));
+        TP_CU(cudaMemcpyAsync(fc, ctx->far_count, sizeof(fc), cudaMemcpyDeviceToHost, ctx->stream));
+        TP_CU(cudaMemcpyAsync(h, counts, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+        TP_CU(cudaStreamSynchronize(ctx->stream));
+        const bool near_ok = (int64_t)nc[0] <= ctx->near_cap && (int64_t)nc[1] <= ctx->nrun_cap;
+        const bool far_ok = (int64_t)fc[0] <= ctx->far_cap && (int64_t)fc[1] <= ctx->run_cap;
+        if (near_ok && far_ok) {
+            listed_rows = (int64_t)fc[0];
+            break;
+        }
+        if (attempt > 0) return tp_set_err(ctx, TP_E_OOM, "Barnes-Hut pair list overflow");
+        // enlarge the lists that overflowed to the counted need (with slack) and repeat
+        if (!near_ok) {
+            tp_free(ctx, ctx->near_list);
+            tp_free(ctx, ctx->near_runs);
+            ctx->near_list = nullptr;
+            ctx->near_runs = nullptr;
+            TP_TRY(alloc_near((int64_t)(nc[0] + nc[0] / 4 + 1024), (int64_t)(nc[1] + nc[1] / 4 + 1024)));
+        }
+        if (!far_ok) {
+            tp_free(ctx, ctx->far_list);
+            tp_free(ctx, ctx->far_runs);
+            ctx->far_list = nullptr;
+            ctx->far_runs = nullptr;
+            TP_TRY(alloc_far((int64_t)(fc[0] + fc[0] / 4 + 1024), (int64_t)(fc[1] + fc[1] / 4 + 1024)));
+        }
+    }
     if (learned) {
-        // Barnes-Hut pass that also lists the far nodes of every leaf, then the
-        // network's correction of those far terms
+        // network rows and factors of the listed (leaf, cluster) pairs
+        if (ctx->far_xcap < ctx->far_cap) {
+            tp_free(ctx, ctx->far_X);
+            tp_free(ctx, ctx->far_kf);
+            ctx->far_X = nullptr;
+            ctx->far_kf = nullptr;
+            ctx->far_xcap = 0;
+            TP_TRY(tp_alloc_t(ctx, &ctx->far_X, ctx->far_cap * MLP_NIP));
+            TP_TRY(tp_alloc_t(ctx, &ctx->far_kf, ctx->far_cap * 8));
+            ctx->far_xcap = ctx->far_cap;
+        }
         A.wb = static_cast<const __nv_bfloat16*>(tp_mlp_weights(ctx));
         A.mbias = tp_mlp_bias(ctx);
         A.mnorm = tp_mlp_norm(ctx);
-        if (!ctx->far_count) TP_TRY(tp_alloc_t(ctx, &ctx->far_count, 2));
-        auto alloc_list = [&](int64_t rows, int64_t runs) -> tp_status {
-            rows = (rows + 31) / 32 * 32;  // whole 32-row network batches
-            TP_TRY(tp_alloc_t(ctx, &ctx->far_list, rows));
-            TP_TRY(tp_alloc_t(ctx, &ctx->far_runs, runs));
-            TP_TRY(tp_alloc_t(ctx, &ctx->far_X, rows * MLP_NIP));
-            TP_TRY(tp_alloc_t(ctx, &ctx->far_kf, rows * 8));
-            ctx->far_cap = rows;
-            ctx->run_cap = runs;
-            return TP_OK;
-        };
-        if (!ctx->far_list) {
-            const int64_t rows = std::max<int64_t>(1 << 20, t.nleaves * 1024);
-            TP_TRY(alloc_list(rows, rows / 32 + t.nleaves + 1024));
-        }
-        int64_t listed_rows = 0;
-        for (int attempt = 0;; ++attempt) {
-            TP_CU(cudaMemsetAsync(ctx->far_count, 0, 2 * sizeof(unsigned long long), ctx->stream));
-            A.far_list = ctx->far_list;
-            A.far_runs = ctx->far_runs;
-            A.far_count = ctx->far_count;
-            A.far_cap = ctx->far_cap;
-            A.run_cap = ctx->run_cap;
-            if (prm->q == 6)
-                k_bh<6, M_LIST><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
-            else
-                k_bh<8, M_LIST><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
-            ++ctx->nlaunch;
-            unsigned long long fc[2] = {0, 0};
-            TP_CU(cudaMemcpyAsync(fc, ctx->far_count, sizeof(fc), cudaMemcpyDeviceToHost, ctx->stream));
-            TP_CU(cudaStreamSynchronize(ctx->stream));
-            if ((int64_t)fc[0] <= ctx->far_cap && (int64_t)fc[1] <= ctx->run_cap) {
-                listed_rows = (int64_t)fc[0];
-                break;
-            }
-            if (attempt > 0) return tp_set_err(ctx, TP_E_OOM, "far-pair list overflow");
-            // enlarge to the counted need (with slack) and repeat the pass
-            for (void* p : {(void*)ctx->far_list, (void*)ctx->far_runs, (void*)ctx->far_X, (void*)ctx->far_kf})
-                tp_free(ctx, p);
-            ctx->far_list = nullptr;
-            ctx->far_runs = nullptr;
-            ctx->far_X = nullptr;
-            ctx->far_kf = nullptr;
-            TP_TRY(alloc_list((int64_t)(fc[0] + fc[0] / 4 + 1024), (int64_t)(fc[1] + fc[1] / 4 + 1024)));
-            TP_CU(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), ctx->stream));
-        }
+        // the network's factors of the listed far terms, then the far terms with them
         const unsigned lblocks = (unsigned)std::max(1, ctx->num_sms * 4);
         k_far_feat<<<lblocks, FL_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_X);
         TP_TRY(tp_launch_mlp_tc(ctx, A.wb, A.mbias, ctx->far_X, listed_rows, ctx->far_kf, 0));
         if (prm->q == 6)
-            k_far_correct<6><<<lblocks, FL_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_kf);
+            k_far<6><<<fblocks, FAR_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_kf);
         else
-            k_far_correct<8><<<lblocks, FL_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_kf);
+            k_far<8><<<fblocks, FAR_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_kf);
         ctx->nlaunch += 2;  // plus the network launch counted by tp_launch_mlp_tc
-    } else {
-        if (prm->q == 6)
-            k_bh<6, M_BH><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
-        else
-            k_bh<8, M_BH><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
+        TP_CU(cudaGetLastError());
+        TP_CU(cudaMemcpyAsync(h + 3, counts + 3, sizeof(h[3]), cudaMemcpyDeviceToHost, ctx->stream));
     }
-    ++ctx->nlaunch;
     cudaEventRecord(ctx->ev[1], ctx->stream);
-    TP_CU(cudaGetLastError());
-    unsigned long long h[4] = {0, 0, 0, 0};
-    TP_CU(cudaMemcpyAsync(h, counts, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
     TP_CU(cudaStreamSynchronize(ctx->stream));
     ctx->stats.pairs_exact = (int64_t)h[0];
     ctx->stats.far_terms = (int64_t)h[1];

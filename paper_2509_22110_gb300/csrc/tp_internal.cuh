@@ -77,8 +77,9 @@ struct tp_quad_rule {
     double w[6];
 };
 
-// A run of the learned far field's pair list: far nodes of one target leaf
-// (leaf index li) at far_list[start, start + len), in traversal order.
+// A run of a Barnes-Hut pair list: the far nodes (learned far field) or the
+// near clusters apart from the leaf (near field) of one target leaf (leaf
+// index li) at list[start, start + len), in traversal order.
 struct tp_far_run {
     int64_t start;
     int32_t li;
@@ -170,10 +171,17 @@ struct tp_ctx {
     // far (leaf, cluster) pairs listed by the Barnes-Hut pass for the learned correction
     int32_t* far_list = nullptr;
     tp_far_run* far_runs = nullptr;
-    unsigned long long* far_count = nullptr;  // [2] rows and runs listed (may exceed the capacities)
+    unsigned long long* far_count = nullptr;  // [0] rows, [1] runs listed (may exceed the capacities), [2] work counter
     __nv_bfloat16* far_X = nullptr;  // [far_cap][32] BF16 network inputs of the listed pairs
     float* far_kf = nullptr;         // [far_cap][8] factors - 1 (column 7: in the training ranges)
     int64_t far_cap = 0, run_cap = 0;
+    int64_t far_xcap = 0;             // rows of far_X and far_kf
+    // Barnes-Hut near field: (first member, count) of every near cluster whose
+    // vertex box is apart from the target leaf's, in runs of one leaf
+    int2* near_list = nullptr;
+    tp_far_run* near_runs = nullptr;
+    unsigned long long* near_count = nullptr;  // [0] entries, [1] runs listed (may exceed the capacities), [2] work counter
+    int64_t near_cap = 0, nrun_cap = 0;
 
     tp_stats stats{};
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -245,3 +253,44 @@ const float* tp_mlp_norm(const tp_ctx* ctx);
 
 // ---------------------------------------------------------------- device helpers
 __device__ __forceinline__ void tp_dev_error(unsigned* derr, unsigned bit) { atomicOr(derr, bit); }
+
+// Bulk copies (cp.async.bulk, completion counted in bytes on an mbarrier) and
+// bounded mbarrier waits, shared by the pair kernels.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: true when the phase completed, false after TP_SPIN_LIMIT polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < TP_SPIN_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
