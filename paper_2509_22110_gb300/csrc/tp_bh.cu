@@ -510,11 +510,21 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
         __syncwarp();
         sp -= m;
         bool is_far = false, is_near = false, is_open = false, touch = false;
-        int firstc = 0, cntc = 0;
+        int firstc = 0, cntc = 0, lc = 0, rc = 0;
         if (node >= 0) {
+            // everything the test and the push need, loaded in one round: the
+            // node's FP32 record, its member range and (internal nodes) its children
+            const float4* c4 = reinterpret_cast<const float4*>(A.adm32 + 16 * (int64_t)node);
+            const float4 q0 = c4[0], q1 = c4[1], q2 = c4[2], q3 = c4[3];
             firstc = A.first[node];
-            cntc = A.last[node] - firstc + 1;
-            const float* c32 = A.adm32 + 16 * (int64_t)node;
+            const int lastc = A.last[node];
+            if (node < A.n - 1) {
+                lc = A.left[node];
+                rc = A.right[node];
+            }
+            cntc = lastc - firstc + 1;
+            const float c32[16] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w,
+                                   q2.x, q2.y, q2.z, q2.w, q3.x, q3.y, q3.z, q3.w};
             if (admissible(la, c32, A.box + 6 * (int64_t)node, A.adm64 + 4 * (int64_t)node, A.theta, theta32)) {
                 is_far = true;
                 n_far += (unsigned long long)cnt;
@@ -550,8 +560,8 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
         }
         if (is_open) {
             const int pos = sp + 2 * __popc(bo & lt);
-            st[pos] = A.right[node];
-            st[pos + 1] = A.left[node];
+            st[pos] = rc;
+            st[pos + 1] = lc;
         }
         if (MODE != M_RECORD) {
             nf += __popc(bf);
