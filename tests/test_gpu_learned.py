@@ -219,3 +219,43 @@ def test_inference_forward_parity(tp, ctx, oracle_mod):
     # the register-resident mma.sync variant of the inference network
     Ys, _, _ = _tp.tp_far_eval(ctx, X, normalised=True, mma_sync=True)
     assert rel(Ys, Yo) <= 1e-2 and rel(Ys, Yt) <= 2e-3 and rel(Ys, Yi) <= 2e-3, (rel(Ys, Yo), rel(Ys, Yt))
+
+
+def test_learned_evaluation_with_constant_factors(tp, ctx):
+    """End to end through the learned passes (listing, features, tensor-core
+    network, far terms with factors) on a level-6 mesh at theta = 0.25: a
+    network whose output layer is zero except a bias b scales every far
+    channel by exp(b), with ranges wide enough that every row is in range.
+    b = 0 must reproduce plain Barnes-Hut (both are within 1e-6 / 1e-5 of the
+    exact sums, so they agree to twice that), and (learned - plain) / (e^b - 1)
+    is the same far part for b = 0.1 and b = -0.2."""
+    _tp = tp._tp
+    V, F = meshgen.sh_deformed_sphere(6, 12, 0.05, 3)
+    tp.tp_mesh_upload(ctx, V, F)
+    tp.tp_tree_build(ctx, 16, 30)
+    gb = np.zeros_like(V)
+    eb = tp.tp_gradient(ctx, gb, tp.tp_params_default(mode=tp.TP_BH, theta=0.25))
+    far_terms = tp.tp_get_stats(ctx)["far_terms"]
+    assert far_terms > 0
+    _tp.tp_far_model_init(ctx, 3)
+    P, _ = _tp.tp_far_get_params(ctx)
+    norm = np.stack([np.zeros(24), np.ones(24), np.full(24, -1e30), np.full(24, 1e30)]).astype(np.float32)
+    w4, b4 = 64 * 24 + 64 + 2 * (64 * 64 + 64), 64 * 24 + 64 + 2 * (64 * 64 + 64) + 7 * 64
+    res = {}
+    for b in (0.0, 0.1, -0.2):
+        Q = P.copy()
+        Q[w4:b4] = 0.0
+        Q[b4:b4 + 7] = b
+        _tp.tp_far_set_params(ctx, Q, norm)
+        g = np.zeros_like(V)
+        e = tp.tp_gradient(ctx, g, tp.tp_params_default(mode=tp.TP_LEARNED, theta=0.25))
+        st = tp.tp_get_stats(ctx)
+        assert st["far_terms"] == far_terms and st["learned_terms"] == far_terms
+        res[b] = (e, g)
+    e0, g0 = res[0.0]
+    assert abs(e0 - eb) <= 2e-6 * eb, (e0, eb)
+    assert rel(g0, gb) <= 2e-5, rel(g0, gb)
+    fe = {b: (res[b][0] - eb) / np.expm1(b) for b in (0.1, -0.2)}
+    fg = {b: (res[b][1] - gb) / np.expm1(b) for b in (0.1, -0.2)}
+    assert fe[0.1] > 0 and abs(fe[0.1] - fe[-0.2]) <= 1e-4 * fe[0.1], fe
+    assert rel(fg[0.1], fg[-0.2]) <= 1e-3, rel(fg[0.1], fg[-0.2])
