@@ -800,10 +800,14 @@ __global__ void __launch_bounds__(NR_WARPS * 32) k_near(BHArgs A) {
 // (target pair, record stream).  Each batch of 32 listed nodes is staged in
 // shared memory in the duplicated record layout with the network's channel
 // factors; the next batch's records are loaded into registers while this one
-// is evaluated.  Every channel c of the far term is scaled by the factor
-// exp(y_c) of its (leaf, cluster) row (1 outside the training ranges):
-// E = wts (f0 al^q + f1 be^q), U: f2 A5, Gn: f3 A5 d, Gx: f4 B5 nubar - k d,
-// k = (p/q) wts inv (f5 al^q + f6 be^q).  (The plain form evaluates its far
+// is evaluated.  The channels of the far term are scaled by the factors
+// f_c = exp(y_c) of its (leaf, cluster) row (1 outside the training ranges):
+// E = wts (f0 al^q + f1 be^q), U: f2 A5, Gx: f4 B5 nubar - k d,
+// k = (p/q) wts inv (f5 al^q + f6 be^q).  The normal-derivative channel Gn
+// keeps the monopole A5 d: its factor is fitted to the channel's projection on
+// the target-cluster direction, and applied to the whole vector it doubled the
+// gradient error (level-7 sphere, theta = 0.25: 8.3e-3 with it, 3.9e-3
+// without, 4.4e-3 for plain Barnes-Hut).  (The plain form evaluates its far
 // nodes inside k_bh, straight from the traversal's staged list.)
 template <int Q>
 __device__ __forceinline__ void far_pair2_learned(const Tgt2& t, const float* rec, const float* fk, float2 acc[8]) {
@@ -848,12 +852,12 @@ __device__ __forceinline__ void far_pair2_learned(const Tgt2& t, const float* re
     const float2 se = bh_fma2(bh_f2(f03.y), beq, bh_mul2(bh_f2(f03.x), alq));
     const float2 sk = bh_fma2(bh_f2(f47.z), beq, bh_mul2(bh_f2(f47.y), alq));
     const float2 nk = bh_mul2(bh_mul2(wi, sk), bh_f2(-2.0f));  // -(p/q) wts inv (f5 al^q + f6 be^q)
-    const float2 gA = bh_mul2(bh_f2(f03.w), A5), gB = bh_mul2(bh_f2(f47.x), B5);
+    const float2 gB = bh_mul2(bh_f2(f47.x), B5);  // (f3, the Gn factor, is not applied)
     acc[0] = bh_fma2(wts, se, acc[0]);
     acc[1] = bh_fma2(bh_f2(f03.z), A5, acc[1]);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        acc[2 + k] = bh_fma2(gA, d[k], acc[2 + k]);
+        acc[2 + k] = bh_fma2(A5, d[k], acc[2 + k]);
         acc[5 + k] = bh_fma2(nk, d[k], bh_fma2(gB, sn[k], acc[5 + k]));
     }
 }

@@ -224,8 +224,9 @@ def test_inference_forward_parity(tp, ctx, oracle_mod):
 def test_learned_evaluation_with_constant_factors(tp, ctx):
     """End to end through the learned passes (listing, features, tensor-core
     network, far terms with factors) on a level-6 mesh at theta = 0.25: a
-    network whose output layer is zero except a bias b scales every far
-    channel by exp(b), with ranges wide enough that every row is in range.
+    network whose output layer is zero except a bias b scales every corrected
+    far channel by exp(b) (all but the normal derivative, which keeps the
+    monopole), with ranges wide enough that every row is in range.
     b = 0 must reproduce plain Barnes-Hut (both are within 1e-6 / 1e-5 of the
     exact sums, so they agree to twice that), and (learned - plain) / (e^b - 1)
     is the same far part for b = 0.1 and b = -0.2."""
