@@ -702,7 +702,7 @@ __global__ void __launch_bounds__(NR_WARPS * 32) k_near(BHArgs A) {
             else ns0 = n;
             if (n == 0) {
                 // a cluster larger than a slot cannot occur (leaves hold at most 32)
-                if (next < R.len && lane == 0) tp_dev_error(A.derr, TP_DERR_INDEX);
+                if (next < R.len && lane == 0) tp_dev_error(A.derr, TP_DERR_INTERNAL);
                 return;
             }
             if (lane == 0) {

@@ -42,6 +42,7 @@
 #define TP_DERR_STACK 0x2u
 #define TP_DERR_INDEX 0x4u
 #define TP_DERR_NONFINITE 0x8u
+#define TP_DERR_INTERNAL 0x10u  // a consistency check of a kernel's own work lists failed
 
 struct tp_tree {
     bool valid = false;
