@@ -806,8 +806,8 @@ __global__ void __launch_bounds__(NR_WARPS * 32) k_near(BHArgs A) {
 // k = (p/q) wts inv (f5 al^q + f6 be^q).  The normal-derivative channel Gn
 // keeps the monopole A5 d: its factor is fitted to the channel's projection on
 // the target-cluster direction, and applied to the whole vector it doubled the
-// gradient error (level-7 sphere, theta = 0.25: 8.3e-3 with it, 3.9e-3
-// without, 4.4e-3 for plain Barnes-Hut).  (The plain form evaluates its far
+// gradient error (level-7 sphere, theta = 0.25, a model trained at theta =
+// 0.25 and 0.5: 8.3e-3 with it, 3.9e-3 without, 4.4e-3 for plain Barnes-Hut).  (The plain form evaluates its far
 // nodes inside k_bh, straight from the traversal's staged list.)
 template <int Q>
 __device__ __forceinline__ void far_pair2_learned(const Tgt2& t, const float* rec, const float* fk, float2 acc[8]) {
