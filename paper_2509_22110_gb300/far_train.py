@@ -122,10 +122,31 @@ def main():
     ap.add_argument("--eval-seeds", type=int, nargs=2, default=None)
     ap.add_argument("--eval-thetas", type=float, nargs="+", default=[0.25, 0.5])
     ap.add_argument("--summary", default=None, help="write the evaluation rows as JSON here")
+    ap.add_argument("--eval-only", default=None, metavar="MODEL",
+                    help="skip training: load this model file and evaluate it on --eval-seeds")
     args = ap.parse_args()
     import torch
 
     ctx = _tp.tp_create(0, torch.cuda.current_stream().cuda_stream)
+    if args.eval_only:
+        if not args.eval_seeds:
+            ap.error("--eval-only needs --eval-seeds")
+        _tp.tp_far_model_load(ctx, args.eval_only)
+        rows = evaluate(ctx, range(*args.eval_seeds), args.level, args.eval_thetas, log=None)
+        summ = {}
+        for th in args.eval_thetas:
+            for mode in ("bh", "learned"):
+                rs = [r for r in rows if r["theta"] == th and r["mode"] == mode]
+                summ[f"{mode}@{th}"] = {k: {"min": float(np.min([r[k] for r in rs])),
+                                            "mean": float(np.mean([r[k] for r in rs])),
+                                            "max": float(np.max([r[k] for r in rs]))}
+                                        for k in ("energy_err", "grad_err", "ms_eval")}
+        print(json.dumps(summ))
+        if args.summary:
+            with open(args.summary, "w") as f:
+                json.dump({"model": args.eval_only, "eval": summ, "rows": rows}, f, indent=1)
+        _tp.tp_destroy(ctx)
+        return
     t0 = time.time()
     _tp.tp_far_model_init(ctx, 1234)
     _tp.tp_far_dataset_reset(ctx)
