@@ -386,7 +386,13 @@ tp_status tp_mesh_upload(tp_ctx* ctx, const void* V, int64_t nv, int v_dtype, co
             TP_TRY(tp_launch_morton_order(ctx, 30));
         }
         TP_TRY(tp_launch_sorted_soa(ctx));
-        TP_TRY(tp_launch_flagged(ctx, !posonly));
+        if (posonly) {
+            // the direct kernels' item lists are refreshed when a direct evaluation needs them
+            if (ctx->flags_stale < 1) ctx->flags_stale = 1;
+        } else {
+            TP_TRY(tp_launch_flagged(ctx, true));
+            ctx->flags_stale = 0;
+        }
         if (!posonly) TP_TRY(tp_count_excluded(ctx));
     }
     cudaEventRecord(ctx->ev[3], ctx->stream);

@@ -1214,6 +1214,7 @@ DirectArgs make_args(tp_ctx* ctx, const tp_params* prm) {
 }  // namespace
 
 tp_status tp_launch_direct_grad(tp_ctx* ctx, const tp_params* prm) {
+    TP_TRY(tp_ensure_flagged(ctx));
     TP_CU(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * TP_NACC * ctx->ntp, ctx->stream));
     DirectArgs A = make_args(ctx, prm);
     if (prm->q == 6) return launch_grad_q<6>(ctx, A);
@@ -1275,6 +1276,7 @@ tp_status tp_launch_conf(tp_ctx* ctx, const tp_params* prm) {
 }
 
 tp_status tp_launch_direct_energy(tp_ctx* ctx, const tp_params* prm, double* partials, int* nparts) {
+    TP_TRY(tp_ensure_flagged(ctx));
     DirectArgs A = make_args(ctx, prm);
     A.partial = partials;
     if (prm->q == 6) return launch_energy_q<6>(ctx, A, nparts);

@@ -148,6 +148,10 @@ struct tp_ctx {
     double* host_pinned = nullptr;  // small pinned staging
 
     int64_t n_masked = 0;
+    // the item lists above are refreshed on the next direct evaluation: 1 after a
+    // positions-only upload (classification), 2 after a tree build re-sorted the
+    // triangles (also the vertex-sharing blocks and exclusion bits)
+    int flags_stale = 0;
     int64_t n_precise = 0;
     int64_t n_fast = 0;
     int64_t pairs_fast = 0, pairs_precise = 0, pairs_masked_items = 0;  // unordered real pairs per item kind
@@ -218,6 +222,7 @@ tp_status tp_launch_tri_data(tp_ctx* ctx);
 tp_status tp_launch_morton_order(tp_ctx* ctx, int morton_bits);
 tp_status tp_launch_sorted_soa(tp_ctx* ctx);
 tp_status tp_launch_flagged(tp_ctx* ctx, bool topology);
+tp_status tp_ensure_flagged(tp_ctx* ctx);
 tp_status tp_launch_fields(tp_ctx* ctx, const tp_params* prm, double* fw, double* fnu, double* fx);
 tp_status tp_launch_conf_tri(tp_ctx* ctx);
 tp_status tp_launch_expand_faces(tp_ctx* ctx);

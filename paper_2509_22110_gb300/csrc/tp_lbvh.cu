@@ -261,7 +261,7 @@ tp_status tp_launch_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits) {
     // 1. Morton order of the current centroids; refresh the library-order data
     TP_TRY(tp_launch_morton_order(ctx, morton_bits));
     TP_TRY(tp_launch_sorted_soa(ctx));
-    TP_TRY(tp_launch_flagged(ctx, true));
+    ctx->flags_stale = 2;  // the direct kernels' item lists follow the new order when next needed
     // 2. radix tree
     if (n > 1) {
         k_radix_tree<<<nblk(n - 1, 256), 256, 0, ctx->stream>>>(ctx->codes_sorted, ctx->perm, n, t.left, t.right,

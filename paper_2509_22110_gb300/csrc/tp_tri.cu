@@ -648,6 +648,13 @@ tp_status tp_launch_flagged(tp_ctx* ctx, bool topology) {
     return TP_OK;
 }
 
+tp_status tp_ensure_flagged(tp_ctx* ctx) {
+    if (ctx->flags_stale == 0) return TP_OK;
+    TP_TRY(tp_launch_flagged(ctx, ctx->flags_stale >= 2));
+    ctx->flags_stale = 0;
+    return TP_OK;
+}
+
 namespace {
 // number of distinct S != T sharing a vertex with T (ordered excluded pairs)
 __global__ void k_count_excluded(const int32_t* __restrict__ F, const int32_t* __restrict__ off,

@@ -120,6 +120,43 @@ def test_bh_parity_leaf_sizes_and_options(tp, ctx, oracle_mod, leaf, q, adj):
     assert rel(grad, go) <= G_TOL, rel(grad, go)
 
 
+def test_direct_after_tree_build_and_position_updates(tp, ctx):
+    """The direct kernels' item lists follow a tree build (which re-sorts the
+    triangles) and positions-only uploads: the direct sums then match a fresh
+    context on the same positions."""
+    import torch
+
+    V, F = meshgen.sh_deformed_sphere(5, 12, 0.05, 7)
+    V2 = V + 0.03 * np.sin(3.0 * V[:, [1, 2, 0]])  # smooth, changes the Morton order
+    V3 = V2 + 0.01 * np.cos(2.0 * V2[:, [2, 0, 1]])
+    tp.tp_mesh_upload(ctx, V, F)
+    tp.tp_tree_build(ctx, 16, 30)
+    tp.tp_mesh_upload(ctx, V2, None, flags=tp._tp.TP_POSITIONS_ONLY)
+    tp.tp_tree_build(ctx, 16, 30)
+    g2 = np.zeros_like(V2)
+    e2 = tp.tp_gradient(ctx, g2)
+    e2e = tp.tp_energy(ctx)
+    tp.tp_mesh_upload(ctx, V3, None, flags=tp._tp.TP_POSITIONS_ONLY)
+    g3 = np.zeros_like(V3)
+    e3 = tp.tp_gradient(ctx, g3)
+    c2 = tp.tp_create(0, torch.cuda.current_stream().cuda_stream)
+    try:
+        # same positions and the same Morton order (computed from V2 in both): equal up to summation order
+        tp.tp_mesh_upload(c2, V2, F)
+        gf = np.zeros_like(V2)
+        ef = tp.tp_gradient(c2, gf)
+        assert abs(e2 - ef) <= 1e-12 * ef and abs(e2e - ef) <= 1e-6 * ef
+        assert rel(g2, gf) <= 1e-12, rel(g2, gf)
+        # V3 in the order of V2 against a fresh order of V3: both within the direct-form bars of the exact sums
+        tp.tp_mesh_upload(c2, V3, F)
+        gf = np.zeros_like(V3)
+        ef = tp.tp_gradient(c2, gf)
+        assert abs(e3 - ef) <= 2 * E_TOL * ef, (e3, ef)
+        assert rel(g3, gf) <= 2 * G_TOL, rel(g3, gf)
+    finally:
+        tp.tp_destroy(c2)
+
+
 def test_bh_theta_zero_equals_direct(tp, ctx):
     V, F = meshgen.workload("dish_l5")
     tp.tp_mesh_upload(ctx, V, F)
