@@ -1176,6 +1176,7 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
         }
     }
     if (learned) {
+        TP_TRY(tp_ensure_node_features(ctx));
         // network rows and factors of the listed (leaf, cluster) pairs
         if (ctx->far_xcap < ctx->far_cap) {
             tp_free(ctx, ctx->far_X);

@@ -46,6 +46,7 @@
 
 struct tp_tree {
     bool valid = false;
+    bool feat_stale = true;  // nodeft is computed when the learned form first needs it after a build
     int leaf_size = 16, morton_bits = 30;
     int64_t nleaves = 0;
     uint32_t* codes = nullptr;   // [nt] by caller's index
@@ -252,6 +253,7 @@ tp_status tp_launch_bh_sample(tp_ctx* ctx, double theta, uint32_t keep_u, uint64
 // tp_mlp.cu
 void tp_mlp_release(tp_ctx* ctx);
 tp_status tp_mlp_node_features(tp_ctx* ctx);
+tp_status tp_ensure_node_features(tp_ctx* ctx);
 bool tp_mlp_ready(const tp_ctx* ctx);
 const void* tp_mlp_weights(const tp_ctx* ctx);
 const float* tp_mlp_bias(const tp_ctx* ctx);

@@ -297,7 +297,7 @@ tp_status tp_launch_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits) {
     ++ctx->nlaunch;
     k_node_adm<<<nblk(nn, 256), 256, 0, ctx->stream>>>(t.mom, t.box, nn, t.adm64, t.adm32);
     ++ctx->nlaunch;
-    TP_TRY(tp_mlp_node_features(ctx));
+    t.feat_stale = true;  // the network's node features are computed when the learned form needs them
     int32_t h = 0;
     TP_CU(cudaMemcpyAsync(&h, t.nleaves_d, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
     TP_CU(cudaStreamSynchronize(ctx->stream));

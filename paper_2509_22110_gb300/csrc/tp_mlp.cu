@@ -636,6 +636,13 @@ tp_status tp_mlp_node_features(tp_ctx* ctx) {
     return TP_OK;
 }
 
+tp_status tp_ensure_node_features(tp_ctx* ctx) {
+    if (!ctx->tree.feat_stale) return TP_OK;
+    TP_TRY(tp_mlp_node_features(ctx));
+    ctx->tree.feat_stale = false;
+    return TP_OK;
+}
+
 const void* tp_mlp_weights(const tp_ctx* ctx) { return ctx->mlp ? ctx->mlp->wb : nullptr; }
 const float* tp_mlp_bias(const tp_ctx* ctx) { return ctx->mlp ? ctx->mlp->bias : nullptr; }
 const float* tp_mlp_norm(const tp_ctx* ctx) { return ctx->mlp ? ctx->mlp->norm : nullptr; }
@@ -747,6 +754,7 @@ tp_status tp_far_sample_pairs(tp_ctx* ctx, double theta, double keep, uint64_t s
     const int64_t np = std::min<int64_t>(h, max_pairs);
     TP_TRY(ensure_dataset(ctx, m->dcount + np));
     if (np > 0) {
+        TP_TRY(tp_ensure_node_features(ctx));
         tp_tree& t = ctx->tree;
         k_far_label<<<(unsigned)np, 128, 0, ctx->stream>>>(m->dpairs, m->dcount, np, t.leaves, t.first, t.last, t.mom,
                                                            t.nodeft, ctx->soa, ctx->ntp, ctx->center, 6, m->dfeat,
