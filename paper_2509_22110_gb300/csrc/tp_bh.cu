@@ -16,27 +16,28 @@
 // Derivatives are not propagated into the cluster moments.  theta = 0
 // admits no cluster and reproduces the direct sum.
 //
-// GPU organisation.  One warp per target cluster leaf (at most 32 targets
-// per leaf, 16 by default).  The admissibility test depends on (L, C)
-// only, so the traversal is warp-uniform: the warp pops up to 32 nodes from
-// a shared-memory stack, each lane tests one, and ballots sort them into a
-// far list, two near lists and nodes to open.  A near cluster whose vertex
-// box is apart from the leaf's can hold no triangle adjacent to a target, so
-// its pairs skip the exclusion test; near clusters whose box touches the
-// leaf's (the leaf itself among them) are listed apart and every pair is
-// tested.  The lists are evaluated in packed FP32x2 arithmetic, one target
-// against two staged sources per instruction, with lanes split as
-// (target = lane % 16, half = lane / 16) for leaves of up to 16 targets
-// (each half taking every other source pair) or one target per lane for
-// larger leaves.  Per-target partials are FP32 per list flush and FP64
-// across flushes; each target is owned by one warp, so results are stored
-// without atomics in the same accumulator layout as the direct kernels (see
-// tp_direct.cu), and the same adjoint applies.
+// GPU organisation.  k_bh: one warp per target cluster leaf (at most 32
+// targets per leaf, 16 by default).  The admissibility test depends on (L, C)
+// only, so the traversal is warp-uniform: the warp pops up to 32 nodes from a
+// shared-memory stack, each lane tests one, and ballots sort them into a far
+// list, two near lists and nodes to open.  A near cluster whose vertex box is
+// apart from the leaf's can hold no triangle adjacent to a target: those are
+// listed for k_near, which sums them without exclusion tests.  Near clusters
+// whose box touches the leaf's (the leaf itself among them) are evaluated in
+// k_bh with the test on every pair, and so are the far terms of the plain
+// form.  These sweeps run in packed FP32x2 arithmetic, one target against two
+// staged sources per instruction, with lanes split as (target = lane % 16,
+// half = lane / 16) for leaves of up to 16 targets (each half taking every
+// other source pair) or one target per lane for larger leaves.  Per-target
+// partials are FP32 per list flush and FP64 across flushes; each target is
+// owned by one warp, so k_bh stores its results without atomics in the
+// accumulator layout of the direct kernels (see tp_direct.cu); k_near (and
+// k_far) add to them, and the same adjoint applies.
 //
-// Learned correction (TP_LEARNED).  The Barnes-Hut pass also lists the far
-// nodes of every leaf (runs of up to 256 nodes, reserved with one atomic per
-// run); a second kernel runs the network on the listed (leaf, cluster) pairs
-// in batches of 32 and adds the change of the far terms to the targets.
+// Learned form (TP_LEARNED).  The traversal lists the far nodes of every leaf
+// (runs of up to 256 nodes, reserved with one atomic per run) instead of
+// evaluating them; the network runs on the listed (leaf, cluster) pairs, and
+// k_far evaluates each far term once with the network's channel factors.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
