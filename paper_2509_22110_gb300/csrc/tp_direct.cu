@@ -910,14 +910,11 @@ __global__ void k_pairs_f64(const double* x64, const double* nu64, const double*
 
 template <int Q>
 tp_status launch_grad_q(tp_ctx* ctx, DirectArgs A) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_pairs_grad<Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             GradShape<false>::SMEM);
-        cudaFuncSetAttribute(k_pairs_grad<Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             GradShape<true>::SMEM);
-        attr = true;
-    }
+    // the shared-memory limit is a per-device attribute: set it on the current device at every launch
+    TP_CU(cudaFuncSetAttribute(k_pairs_grad<Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               GradShape<false>::SMEM));
+    TP_CU(cudaFuncSetAttribute(k_pairs_grad<Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               GradShape<true>::SMEM));
     TP_CU(cudaMemsetAsync(ctx->work, 0, 2 * sizeof(unsigned), ctx->stream));
     // masked items first (their own queue), then the precise and fast items
     if (ctx->n_masked > 0) {
@@ -1250,13 +1247,10 @@ tp_status tp_launch_conf(tp_ctx* ctx, const tp_params* prm) {
     k_conf_records<<<(unsigned)((ctx->conf_ntp + 255) / 256), 256, 0, ctx->stream>>>(
         ctx->conf_y64, ctx->conf_a64, ctx->center, ctx->conf_nt, ctx->conf_ntp, ctx->conf_src);
     ++ctx->nlaunch;
-    static bool attr = false;
     constexpr int SMEM = 2 * CHUNK_BYTES + 64;
-    if (!attr) {
-        cudaFuncSetAttribute(k_conf_grad<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-        cudaFuncSetAttribute(k_conf_grad<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-        attr = true;
-    }
+    // per-device attribute: set on the current device at every launch
+    TP_CU(cudaFuncSetAttribute(k_conf_grad<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
+    TP_CU(cudaFuncSetAttribute(k_conf_grad<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
     DirectArgs A = make_args(ctx, prm);
     A.src = ctx->conf_src;
     const int64_t nsupc = ctx->conf_ntp / TP_SUPER;

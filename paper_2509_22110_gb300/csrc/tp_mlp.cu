@@ -805,11 +805,8 @@ tp_status tp_far_train(tp_ctx* ctx, int64_t steps, int64_t batch, double lr, dou
     tp_mlp_model* m = ctx->mlp;
     if (m->dcount < 1 || !m->have_norm) return tp_set_err(ctx, TP_E_STATE, "empty dataset or no normalisation");
     if (steps < 1 || batch < 1) return tp_set_err(ctx, TP_E_ARG, "steps and batch must be positive");
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem));
-        attr = true;
-    }
+    // per-device attribute: set on the current device at every call
+    TP_CU(cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem)));
     const unsigned blocks = (unsigned)((batch + TB - 1) / TB);
     double hl[2] = {0, 0};
     for (int64_t s = 0; s < steps; ++s) {
@@ -847,11 +844,8 @@ tp_status tp_far_eval(tp_ctx* ctx, const float* X, int64_t n, int normalised, co
     cudaSetDevice(ctx->device);
     tp_mlp_model* m = ctx->mlp;
     if (!(normalised & 1) && !m->have_norm) return tp_set_err(ctx, TP_E_STATE, "no normalisation");
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem));
-        attr = true;
-    }
+    // per-device attribute: set on the current device at every call
+    TP_CU(cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem)));
     float *dX = nullptr, *dT = nullptr, *dM = nullptr, *dY = nullptr;
     if (!tgt && !mask) {
         // forward only: the inference kernels of the learned correction, the

@@ -221,9 +221,11 @@ def test_inference_forward_parity(tp, ctx, oracle_mod):
     assert rel(Ys, Yo) <= 1e-2 and rel(Ys, Yt) <= 2e-3 and rel(Ys, Yi) <= 2e-3, (rel(Ys, Yo), rel(Ys, Yt))
 
 
-def test_learned_evaluation_with_constant_factors(tp, ctx):
+@pytest.mark.parametrize("leaf", [16, 32])
+def test_learned_evaluation_with_constant_factors(tp, ctx, leaf):
     """End to end through the learned passes (listing, features, tensor-core
-    network, far terms with factors) on a level-6 mesh at theta = 0.25: a
+    network, far terms with factors) on a level-6 mesh at theta = 0.25, with
+    leaves of up to 16 and of up to 32 triangles: a
     network whose output layer is zero except a bias b scales every corrected
     far channel by exp(b) (all but the normal derivative, which keeps the
     monopole), with ranges wide enough that every row is in range.
@@ -233,7 +235,7 @@ def test_learned_evaluation_with_constant_factors(tp, ctx):
     _tp = tp._tp
     V, F = meshgen.sh_deformed_sphere(6, 12, 0.05, 3)
     tp.tp_mesh_upload(ctx, V, F)
-    tp.tp_tree_build(ctx, 16, 30)
+    tp.tp_tree_build(ctx, leaf, 30)
     gb = np.zeros_like(V)
     eb = tp.tp_gradient(ctx, gb, tp.tp_params_default(mode=tp.TP_BH, theta=0.25))
     far_terms = tp.tp_get_stats(ctx)["far_terms"]
