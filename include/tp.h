@@ -238,6 +238,16 @@ tp_status tp_debug_tri_data(tp_ctx* ctx, int32_t* perm, double* x, double* nu, d
  * order (without scale): gw[nt] = dPhi/dw_T, gnu[nt*3], gx[nt*3]. */
 tp_status tp_debug_accum(tp_ctx* ctx, double* gw, double* gnu, double* gx);
 
+/* Rows of the learned far field processed at a time.  A TP_LEARNED
+ * evaluation lists its (leaf, cluster) far pairs, then computes features,
+ * runs the network and applies its factors in windows of at most `rows`
+ * listed pairs; the network rows and factors take 100 B per row of the
+ * window.  rows = 0 restores the default of 32 Mi rows (about 3.4 GB).
+ * Results do not depend on the window beyond FP32 rounding of partial sums.
+ * An implementation control with no counterpart in the paper.  TP_E_ARG for
+ * rows in 1..31. */
+tp_status tp_set_learned_window(tp_ctx* ctx, int64_t rows);
+
 /* The tree of the last tp_tree_build: codes[nt] (by original index),
  * perm[nt], left/right[nt-1], first/last[2nt-1], leaves[*nleaves] (capacity nt),
  * mom[(2nt-1)*13], box[(2nt-1)*6].  Any pointer may be NULL. */

@@ -38,6 +38,7 @@ from ._tp import (  # noqa: F401
     tp_last_error,
     tp_mesh_upload,
     tp_params_default,
+    tp_set_learned_window,
     tp_set_quadrature,
     tp_tree_build,
     tp_version,

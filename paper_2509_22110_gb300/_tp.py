@@ -94,6 +94,8 @@ def lib():
     L.tp_debug_accum.argtypes = [vp, vp, vp, vp]
     L.tp_debug_accum.restype = i32
     L.tp_debug_tree.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, C.POINTER(C.c_int64), vp, vp]
+    L.tp_set_learned_window.argtypes = [vp, C.c_int64]
+    L.tp_set_learned_window.restype = i32
     L.tp_debug_tree.restype = i32
     L.tp_far_model_init.argtypes = [vp, C.c_uint64]
     L.tp_far_model_save.argtypes = [vp, C.c_char_p]
@@ -312,6 +314,11 @@ def tp_debug_accum(ctx, nt):
     gx = np.zeros((nt, 3))
     _check(ctx, lib().tp_debug_accum(ctx, gw.ctypes.data, gnu.ctypes.data, gx.ctypes.data))
     return gw, gnu, gx
+
+
+def tp_set_learned_window(ctx, rows=0):
+    """Listed far pairs per window of the learned passes (0: the default, 32 Mi rows)."""
+    _check(ctx, lib().tp_set_learned_window(ctx, int(rows)))
 
 
 def tp_debug_tree(ctx, nt):

@@ -42,6 +42,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <cub/cub.cuh>
+
 #include "tp_internal.cuh"
 #include "tp_mlp_dev.cuh"
 
@@ -865,8 +867,40 @@ __device__ __forceinline__ void far_pair2_learned(const Tgt2& t, const float* re
 
 constexpr int FAR_WARPS = 8;
 
+// first index i in the sorted a[0, n) with a[i] >= v
+__device__ __forceinline__ int64_t bh_lower_bound(const int64_t* a, int64_t n, int64_t v) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// The runs (in first-row order) that hold rows of the window [w0, w1): the runs
+// tile the listed rows, so they are the run holding w0 up to the last one
+// starting below w1.
+__device__ __forceinline__ void window_runs(const int64_t* skey, int64_t nruns, int64_t w0, int64_t w1, int64_t& lo,
+                                            int64_t& hi) {
+    lo = bh_lower_bound(skey, nruns, w0 + 1) - 1;
+    if (lo < 0) lo = 0;
+    hi = bh_lower_bound(skey, nruns, w1);
+}
+
+__global__ void k_run_keys(const tp_far_run* __restrict__ runs, int64_t nruns, int64_t* __restrict__ key,
+                           int32_t* __restrict__ ord) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nruns) return;
+    key[i] = runs[i].start;
+    ord[i] = (int32_t)i;
+}
+
+
 template <int Q>
-__global__ void __launch_bounds__(FAR_WARPS * 32) k_far(BHArgs A, const float* __restrict__ kf) {
+__global__ void __launch_bounds__(FAR_WARPS * 32) k_far(BHArgs A, const float* __restrict__ kf, int64_t w0,
+                                                         int64_t w1, const int64_t* __restrict__ skey,
+                                                         const int32_t* __restrict__ sord) {
     __shared__ __align__(16) float s_rec[FAR_WARPS][32 * TP_SRCW];  // duplicated records of a batch
     __shared__ __align__(16) float s_fk[FAR_WARPS][32 * 8];         // channel factors of a batch
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -874,16 +908,23 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) k_far(BHArgs A, const float* _
     float* fk = s_fk[warp];
     const unsigned long long nr = A.far_count[1];
     const int64_t nruns = nr < (unsigned long long)A.run_cap ? (int64_t)nr : A.run_cap;
+    int64_t rlo, rhi;
+    window_runs(skey, nruns, w0, w1, rlo, rhi);
     unsigned long long n_learn = 0;  // (target, row) pairs with the range flag set, counted by lane 0
     while (true) {
         int64_t run = 0;
-        if (lane == 0) run = (int64_t)atomicAdd(&A.far_count[2], 1ull);
+        if (lane == 0) run = rlo + (int64_t)atomicAdd(&A.far_count[2], 1ull);
         run = __shfl_sync(0xffffffffu, run, 0);
-        if (run >= nruns) break;
-        const tp_far_run R = A.far_runs[run];
+        if (run >= rhi) break;
+        const tp_far_run R = A.far_runs[sord[run]];
         if (R.len <= 0 || R.len > BH_FAR || R.li < 0 || (int64_t)R.li >= A.nleaves || R.start < 0 ||
             R.start + R.len > A.far_cap)
             continue;  // a run whose rows overflowed the list (the evaluation is repeated)
+        // the run's rows inside this window of rows [w0, w1); kf holds the window's rows
+        const int64_t r0 = R.start > w0 ? R.start : w0;
+        const int64_t r1 = R.start + R.len < w1 ? R.start + R.len : w1;
+        if (r0 >= r1) continue;
+        const int rlen = (int)(r1 - r0);
         const int64_t L = A.leaves[R.li];
         const int64_t fL = A.first[L];
         const int cnt = A.last[L] - A.first[L] + 1;
@@ -916,19 +957,19 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) k_far(BHArgs A, const float* _
         float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0, q2 = q0, k0 = q0, k1 = q0;
         auto load_row = [&](int b0, int nb) {
             if (lane < nb) {
-                const int64_t row = R.start + b0 + lane;
+                const int64_t row = r0 + b0 + lane;
                 const float4* r = reinterpret_cast<const float4*>(A.nodef + 16 * (int64_t)A.far_list[row]);
                 q0 = r[0];
                 q1 = r[1];
                 q2 = r[2];
-                const float4* kr = reinterpret_cast<const float4*>(kf + row * 8);
+                const float4* kr = reinterpret_cast<const float4*>(kf + (row - w0) * 8);
                 k0 = kr[0];
                 k1 = kr[1];
             }
         };
-        int nb = R.len < 32 ? R.len : 32;
+        int nb = rlen < 32 ? rlen : 32;
         load_row(0, nb);
-        for (int b0 = 0; b0 < R.len; b0 += 32) {
+        for (int b0 = 0; b0 < rlen; b0 += 32) {
             __syncwarp();  // the previous batch has been evaluated
             if (lane < nb) {
                 float4* d = reinterpret_cast<float4*>(rec + lane * TP_SRCW);
@@ -946,8 +987,8 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) k_far(BHArgs A, const float* _
             if (lane == 0) n_learn += (unsigned long long)__popc(fb) * (unsigned long long)cnt;
             __syncwarp();
             const int n = nb;
-            if (b0 + 32 < R.len) {
-                nb = R.len - (b0 + 32) < 32 ? R.len - (b0 + 32) : 32;
+            if (b0 + 32 < rlen) {
+                nb = rlen - (b0 + 32) < 32 ? rlen - (b0 + 32) : 32;
                 load_row(b0 + 32, nb);
             }
             if (g < ng) {
@@ -1007,7 +1048,9 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) k_far(BHArgs A, const float* _
 //                channel (0 outside the ranges).
 constexpr int FL_WARPS = 8;
 
-__global__ void __launch_bounds__(FL_WARPS * 32, 2) k_far_feat(BHArgs A, __nv_bfloat16* __restrict__ X) {
+__global__ void __launch_bounds__(FL_WARPS * 32, 2) k_far_feat(BHArgs A, __nv_bfloat16* __restrict__ X, int64_t w0,
+                                                                int64_t w1, const int64_t* __restrict__ skey,
+                                                                const int32_t* __restrict__ sord) {
     __shared__ float s_norm[4 * MLP_NI];  // mean, 1/std, lower and upper admitted bound per feature
     for (int i = threadIdx.x; i < MLP_NI; i += blockDim.x) {
         const float lo = A.mnorm[2 * MLP_NI + i], hi = A.mnorm[3 * MLP_NI + i], pad = 0.05f * (hi - lo);
@@ -1020,22 +1063,29 @@ __global__ void __launch_bounds__(FL_WARPS * 32, 2) k_far_feat(BHArgs A, __nv_bf
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned long long nr = A.far_count[1];
     const int64_t nruns = nr < (unsigned long long)A.run_cap ? (int64_t)nr : A.run_cap;
-    for (int64_t run = (int64_t)blockIdx.x * FL_WARPS + warp; run < nruns; run += (int64_t)gridDim.x * FL_WARPS) {
-        const tp_far_run R = A.far_runs[run];
+    int64_t rlo, rhi;
+    window_runs(skey, nruns, w0, w1, rlo, rhi);
+    for (int64_t run = rlo + (int64_t)blockIdx.x * FL_WARPS + warp; run < rhi; run += (int64_t)gridDim.x * FL_WARPS) {
+        const tp_far_run R = A.far_runs[sord[run]];
+        // the run's rows inside this window of rows [w0, w1); X holds the window's rows
+        const int64_t r0 = R.start > w0 ? R.start : w0;
+        const int64_t r1 = R.start + R.len < w1 ? R.start + R.len : w1;
+        if (r0 >= r1) continue;
+        const int rlen = (int)(r1 - r0);
         const float* fl = A.nodeft + 16 * (int64_t)A.leaves[R.li];
         // the cluster record of this lane's next row is loaded while this row is
         // computed (the rows' records are random accesses: 6 % less learned time)
         float4 cq[4];
         auto load_c = [&](int i) {
-            if (i < R.len) {
-                const float4* p = reinterpret_cast<const float4*>(A.nodeft + 16 * (int64_t)A.far_list[R.start + i]);
+            if (i < rlen) {
+                const float4* p = reinterpret_cast<const float4*>(A.nodeft + 16 * (int64_t)A.far_list[r0 + i]);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) cq[q] = p[q];
             }
         };
         load_c(lane);
-        for (int i = lane; i < R.len; i += 32) {
-            const int64_t row = R.start + i;
+        for (int i = lane; i < rlen; i += 32) {
+            const int64_t row = r0 + i;
             float f[MLP_NI];
             const float cr[16] = {cq[0].x, cq[0].y, cq[0].z, cq[0].w, cq[1].x, cq[1].y, cq[1].z, cq[1].w,
                                   cq[2].x, cq[2].y, cq[2].z, cq[2].w, cq[3].x, cq[3].y, cq[3].z, cq[3].w};
@@ -1057,7 +1107,7 @@ __global__ void __launch_bounds__(FL_WARPS * 32, 2) k_far_feat(BHArgs A, __nv_bf
 #pragma unroll
             for (int c = MLP_NI / 2; c < 15; ++c) pk[c] = 0u;
             pk[15] = pack_bf16(0.f, in_dist ? 1.f : 0.f);  // column 31: the range flag (zero weight column)
-            uint4* dst = reinterpret_cast<uint4*>(X + row * MLP_NIP);
+            uint4* dst = reinterpret_cast<uint4*>(X + (row - w0) * MLP_NIP);
 #pragma unroll
             for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
         }
@@ -1116,6 +1166,14 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
         rows = (rows + 31) / 32 * 32;  // whole 32-row network batches
         TP_TRY(tp_alloc_t(ctx, &ctx->far_list, rows));
         TP_TRY(tp_alloc_t(ctx, &ctx->far_runs, runs));
+        for (void* p : {(void*)ctx->run_key, (void*)ctx->run_key_s, (void*)ctx->run_ord, (void*)ctx->run_ord_s})
+            tp_free(ctx, p);
+        ctx->run_key = ctx->run_key_s = nullptr;
+        ctx->run_ord = ctx->run_ord_s = nullptr;
+        TP_TRY(tp_alloc_t(ctx, &ctx->run_key, runs));
+        TP_TRY(tp_alloc_t(ctx, &ctx->run_key_s, runs));
+        TP_TRY(tp_alloc_t(ctx, &ctx->run_ord, runs));
+        TP_TRY(tp_alloc_t(ctx, &ctx->run_ord_s, runs));
         ctx->far_cap = rows;
         ctx->run_cap = runs;
         return TP_OK;
@@ -1131,7 +1189,7 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
     const unsigned nblocks = (unsigned)std::max(1, ctx->num_sms * 4);
     const unsigned fblocks = (unsigned)std::max(1, ctx->num_sms * 4);
     cudaEventRecord(ctx->ev[0], ctx->stream);
-    int64_t listed_rows = 0;
+    int64_t listed_rows = 0, listed_runs = 0;
     unsigned long long h[4] = {0, 0, 0, 0};
     for (int attempt = 0;; ++attempt) {
         TP_CU(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * TP_NACC * ctx->ntp, ctx->stream));
@@ -1171,6 +1229,7 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
         const bool far_ok = (int64_t)fc[0] <= ctx->far_cap && (int64_t)fc[1] <= ctx->run_cap;
         if (near_ok && far_ok) {
             listed_rows = (int64_t)fc[0];
+            listed_runs = (int64_t)fc[1];
             break;
         }
         if (attempt > 0) return tp_set_err(ctx, TP_E_OOM, "Barnes-Hut pair list overflow");
@@ -1192,29 +1251,58 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
     }
     if (learned) {
         TP_TRY(tp_ensure_node_features(ctx));
-        // network rows and factors of the listed (leaf, cluster) pairs
-        if (ctx->far_xcap < ctx->far_cap) {
+        // network rows and factors of the listed (leaf, cluster) pairs, for one
+        // window of at most ctx->learned_window rows at a time
+        const int64_t win = std::min<int64_t>(std::max<int64_t>(listed_rows, 32), ctx->learned_window);
+        if (ctx->far_xcap < win) {
             tp_free(ctx, ctx->far_X);
             tp_free(ctx, ctx->far_kf);
             ctx->far_X = nullptr;
             ctx->far_kf = nullptr;
             ctx->far_xcap = 0;
-            TP_TRY(tp_alloc_t(ctx, &ctx->far_X, ctx->far_cap * MLP_NIP));
-            TP_TRY(tp_alloc_t(ctx, &ctx->far_kf, ctx->far_cap * 8));
-            ctx->far_xcap = ctx->far_cap;
+            TP_TRY(tp_alloc_t(ctx, &ctx->far_X, win * MLP_NIP));
+            TP_TRY(tp_alloc_t(ctx, &ctx->far_kf, win * 8));
+            ctx->far_xcap = win;
         }
         A.wb = static_cast<const __nv_bfloat16*>(tp_mlp_weights(ctx));
         A.mbias = tp_mlp_bias(ctx);
         A.mnorm = tp_mlp_norm(ctx);
-        // the network's factors of the listed far terms, then the far terms with them
+        // the runs in first-row order, so that a window visits only its own runs
+        if (listed_runs > 0) {
+            k_run_keys<<<(unsigned)((listed_runs + 255) / 256), 256, 0, ctx->stream>>>(
+                ctx->far_runs, listed_runs, ctx->run_key, ctx->run_ord);
+            ++ctx->nlaunch;
+            int end_bit = 1;
+            while (end_bit < 63 && ((int64_t)1 << end_bit) <= listed_rows) ++end_bit;
+            size_t need = 0;
+            TP_CU(cub::DeviceRadixSort::SortPairs(nullptr, need, ctx->run_key, ctx->run_key_s, ctx->run_ord,
+                                                  ctx->run_ord_s, (int)listed_runs, 0, end_bit, ctx->stream));
+            if (need > ctx->sort_tmp_bytes) {
+                tp_free(ctx, ctx->sort_tmp);
+                ctx->sort_tmp = nullptr;
+                TP_TRY(tp_alloc(ctx, &ctx->sort_tmp, need));
+                ctx->sort_tmp_bytes = need;
+            }
+            size_t have = ctx->sort_tmp_bytes;
+            TP_CU(cub::DeviceRadixSort::SortPairs(ctx->sort_tmp, have, ctx->run_key, ctx->run_key_s, ctx->run_ord,
+                                                  ctx->run_ord_s, (int)listed_runs, 0, end_bit, ctx->stream));
+        }
+        // per window: the network's factors of the listed far terms, then the far terms with them
         const unsigned lblocks = (unsigned)std::max(1, ctx->num_sms * 4);
-        k_far_feat<<<lblocks, FL_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_X);
-        TP_TRY(tp_launch_mlp_tc(ctx, A.wb, A.mbias, ctx->far_X, listed_rows, ctx->far_kf, 0));
-        if (prm->q == 6)
-            k_far<6><<<fblocks, FAR_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_kf);
-        else
-            k_far<8><<<fblocks, FAR_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_kf);
-        ctx->nlaunch += 2;  // plus the network launch counted by tp_launch_mlp_tc
+        for (int64_t w0 = 0; w0 < listed_rows; w0 += win) {
+            const int64_t w1 = std::min<int64_t>(w0 + win, listed_rows);
+            k_far_feat<<<lblocks, FL_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_X, w0, w1, ctx->run_key_s,
+                                                                ctx->run_ord_s);
+            TP_TRY(tp_launch_mlp_tc(ctx, A.wb, A.mbias, ctx->far_X, w1 - w0, ctx->far_kf, 0));
+            TP_CU(cudaMemsetAsync(ctx->far_count + 2, 0, sizeof(unsigned long long), ctx->stream));
+            if (prm->q == 6)
+                k_far<6><<<fblocks, FAR_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_kf, w0, w1, ctx->run_key_s,
+                                                                   ctx->run_ord_s);
+            else
+                k_far<8><<<fblocks, FAR_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_kf, w0, w1, ctx->run_key_s,
+                                                                   ctx->run_ord_s);
+            ctx->nlaunch += 2;
+        }
         TP_CU(cudaGetLastError());
         TP_CU(cudaMemcpyAsync(h + 3, counts + 3, sizeof(h[3]), cudaMemcpyDeviceToHost, ctx->stream));
     }

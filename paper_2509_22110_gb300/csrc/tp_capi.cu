@@ -755,6 +755,14 @@ tp_status tp_debug_accum(tp_ctx* ctx, double* gw, double* gnu, double* gx) {
     return TP_OK;
 }
 
+tp_status tp_set_learned_window(tp_ctx* ctx, int64_t rows) {
+    if (!ctx) return TP_E_ARG;
+    ctx->err.clear();
+    if (rows != 0 && rows < 32) return tp_set_err(ctx, TP_E_ARG, "learned window of %lld rows (minimum 32)", (long long)rows);
+    ctx->learned_window = rows == 0 ? TP_LEARNED_WINDOW : rows;
+    return TP_OK;
+}
+
 tp_status tp_debug_tree(tp_ctx* ctx, uint32_t* codes, int32_t* perm, int32_t* left, int32_t* right, int32_t* first,
                         int32_t* last, int32_t* leaves, int64_t* nleaves, double* mom, double* box) {
     if (!ctx) return TP_E_ARG;

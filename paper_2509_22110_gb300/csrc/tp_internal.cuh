@@ -38,6 +38,10 @@
 #define TP_PRECISE_GAP_REL 0.02f
 
 // device error bits
+// listed far rows per window of the learned passes: 32 Mi rows, about 3.4 GB
+// of network rows and factors (tp_set_learned_window changes it)
+#define TP_LEARNED_WINDOW ((int64_t)1 << 25)
+
 #define TP_DERR_TIMEOUT 0x1u
 #define TP_DERR_STACK 0x2u
 #define TP_DERR_INDEX 0x4u
@@ -182,6 +186,11 @@ struct tp_ctx {
     float* far_kf = nullptr;         // [far_cap][8] factors - 1 (column 7: in the training ranges)
     int64_t far_cap = 0, run_cap = 0;
     int64_t far_xcap = 0;             // rows of far_X and far_kf
+    // the far runs sorted by first row (keys, run indices; unsorted inputs too), so
+    // that each window of the learned passes visits only its own runs
+    int64_t *run_key = nullptr, *run_key_s = nullptr;
+    int32_t *run_ord = nullptr, *run_ord_s = nullptr;
+    int64_t learned_window = TP_LEARNED_WINDOW;  // listed far rows per window of the learned passes
     // Barnes-Hut near field: (first member, count) of every near cluster whose
     // vertex box is apart from the target leaf's, in runs of one leaf
     int2* near_list = nullptr;

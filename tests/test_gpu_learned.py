@@ -11,7 +11,11 @@ energy error on a held-out mesh.
 import numpy as np
 import pytest
 
+import pathlib
+
 from paper_2509_22110_gb300 import meshgen
+
+ROOT = pathlib.Path(__file__).resolve().parents[1]
 
 pytestmark = pytest.mark.gpu
 
@@ -262,3 +266,30 @@ def test_learned_evaluation_with_constant_factors(tp, ctx, leaf):
     fg = {b: (res[b][1] - gb) / np.expm1(b) for b in (0.1, -0.2)}
     assert fe[0.1] > 0 and abs(fe[0.1] - fe[-0.2]) <= 1e-4 * fe[0.1], fe
     assert rel(fg[0.1], fg[-0.2]) <= 1e-3, rel(fg[0.1], fg[-0.2])
+
+
+def test_learned_windows_match_one_pass(tp, ctx):
+    """The learned passes over the listed far pairs in windows of 2^17 rows (many
+    windows, runs split across them) give the same sums as one window, within
+    FP32 rounding of the per-window partial sums."""
+    V, F = meshgen.sh_deformed_sphere(6, 12, 0.05, 4)
+    tp.tp_mesh_upload(ctx, V, F)
+    tp.tp_tree_build(ctx, 16, 30)
+    tp.tp_far_model_load(ctx, str(ROOT / "paper_2509_22110_gb300" / "far_model_l7.bin"))
+    prm = tp.tp_params_default(mode=tp.TP_LEARNED, theta=0.25)
+    g1 = np.zeros_like(V)
+    e1 = tp.tp_gradient(ctx, g1, prm)
+    st1 = tp.tp_get_stats(ctx)
+    assert st1["far_terms"] > 16 * (1 << 17)  # several windows below
+    tp.tp_set_learned_window(ctx, 1 << 17)
+    try:
+        g2 = np.zeros_like(V)
+        e2 = tp.tp_gradient(ctx, g2, prm)
+        st2 = tp.tp_get_stats(ctx)
+    finally:
+        tp.tp_set_learned_window(ctx, 0)
+    assert st2["learned_terms"] == st1["learned_terms"]
+    assert abs(e2 - e1) <= 1e-6 * abs(e1), (e1, e2)
+    assert rel(g2, g1) <= 1e-5, rel(g2, g1)
+    with pytest.raises(tp.TPError):
+        tp.tp_set_learned_window(ctx, 5)
