@@ -226,6 +226,9 @@ typedef struct {
     int64_t kernel_pairs;    /* unordered triangle pairs evaluated by the dominant kernel
                                 launch of the last call (direct mode: the far-apart
                                 super-tile pairs), for throughput accounting          */
+    int64_t far_rows;        /* (target leaf, cluster) far pairs of the last Barnes-Hut
+                                or learned call: in the learned form, the rows the
+                                network evaluated                                     */
 } tp_stats;
 
 tp_status tp_get_stats(const tp_ctx* ctx, tp_stats* out);

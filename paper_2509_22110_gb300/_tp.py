@@ -47,7 +47,7 @@ class tp_stats(C.Structure):
                 ("far_pairs", C.c_int64), ("learned_terms", C.c_int64), ("tile_pairs", C.c_int64),
                 ("tile_pairs_masked", C.c_int64), ("tile_pairs_precise", C.c_int64), ("ms_kernel", C.c_float),
                 ("ms_total", C.c_float), ("kernel_launches", C.c_int64),
-                ("kernel_pairs", C.c_int64)]
+                ("kernel_pairs", C.c_int64), ("far_rows", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

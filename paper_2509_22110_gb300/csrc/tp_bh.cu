@@ -79,6 +79,7 @@ struct BHArgs {
     double* acc;
     unsigned* derr;
     unsigned long long* counts;  // [0] near pairs, [1] far terms, [2] far pairs, [3] learned terms
+    unsigned long long* far_rows;  // (leaf, cluster) far pairs
     // learned far field
     const float* nodeft;         // [nn][16] f32 feature records
     const __nv_bfloat16* wb;     // network weights (BF16 block)
@@ -612,6 +613,7 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
         atomicAdd(&A.counts[0], n_near);
         atomicAdd(&A.counts[1], n_far);
         atomicAdd(&A.counts[2], n_farp);
+        atomicAdd(A.far_rows, n_far / (unsigned long long)cnt);  // far terms = cnt x far nodes of this leaf
     }
 }
 
@@ -1148,8 +1150,10 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
     tp_tree& t = ctx->tree;
     if (t.leaf_size > 32) return tp_set_err(ctx, TP_E_ARG, "leaf_size above 32");
     unsigned long long* counts = reinterpret_cast<unsigned long long*>(ctx->scalar + 2);
+    unsigned long long* far_rows = reinterpret_cast<unsigned long long*>(ctx->scalar + 7);
     BHArgs A = make_bh_args(ctx, prm->theta, (prm->flags & TP_EXCLUDE_EDGE) ? 1 : 0);
     A.counts = counts;
+    A.far_rows = far_rows;
     const unsigned blocks = (unsigned)((t.nleaves + BH_WARPS - 1) / BH_WARPS);
     // pair lists, first sized for about 256 near clusters and 1024 far nodes per
     // leaf, then to the counted need
@@ -1190,10 +1194,11 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
     const unsigned fblocks = (unsigned)std::max(1, ctx->num_sms * 4);
     cudaEventRecord(ctx->ev[0], ctx->stream);
     int64_t listed_rows = 0, listed_runs = 0;
-    unsigned long long h[4] = {0, 0, 0, 0};
+    unsigned long long h[4] = {0, 0, 0, 0}, h_rows = 0;
     for (int attempt = 0;; ++attempt) {
         TP_CU(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * TP_NACC * ctx->ntp, ctx->stream));
         TP_CU(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), ctx->stream));
+        TP_CU(cudaMemsetAsync(far_rows, 0, sizeof(unsigned long long), ctx->stream));
         TP_CU(cudaMemsetAsync(ctx->near_count, 0, 3 * sizeof(unsigned long long), ctx->stream));
         TP_CU(cudaMemsetAsync(ctx->far_count, 0, 3 * sizeof(unsigned long long), ctx->stream));
         A.src = ctx->src;
@@ -1224,6 +1229,7 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
         TP_CU(cudaMemcpyAsync(nc, ctx->near_count, sizeof(nc), cudaMemcpyDeviceToHost, ctx->stream));
         TP_CU(cudaMemcpyAsync(fc, ctx->far_count, sizeof(fc), cudaMemcpyDeviceToHost, ctx->stream));
         TP_CU(cudaMemcpyAsync(h, counts, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+        TP_CU(cudaMemcpyAsync(&h_rows, far_rows, sizeof(h_rows), cudaMemcpyDeviceToHost, ctx->stream));
         TP_CU(cudaStreamSynchronize(ctx->stream));
         const bool near_ok = (int64_t)nc[0] <= ctx->near_cap && (int64_t)nc[1] <= ctx->nrun_cap;
         const bool far_ok = (int64_t)fc[0] <= ctx->far_cap && (int64_t)fc[1] <= ctx->run_cap;
@@ -1312,6 +1318,7 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
     ctx->stats.far_terms = (int64_t)h[1];
     ctx->stats.far_pairs = (int64_t)h[2];
     ctx->stats.learned_terms = (int64_t)h[3];
+    ctx->stats.far_rows = (int64_t)h_rows;
     return TP_OK;
 }
 

@@ -258,6 +258,8 @@ def test_learned_evaluation_with_constant_factors(tp, ctx, leaf):
         e = tp.tp_gradient(ctx, g, tp.tp_params_default(mode=tp.TP_LEARNED, theta=0.25))
         st = tp.tp_get_stats(ctx)
         assert st["far_terms"] == far_terms and st["learned_terms"] == far_terms
+        # far terms are (target, cluster) pairs: each (leaf, cluster) row serves 1..leaf targets
+        assert st["far_rows"] <= far_terms <= leaf * st["far_rows"]
         res[b] = (e, g)
     e0, g0 = res[0.0]
     assert abs(e0 - eb) <= 2e-6 * eb, (e0, eb)
