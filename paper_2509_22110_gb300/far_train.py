@@ -119,6 +119,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--init-seed", type=int, default=1234, help="seed of the network's initial weights")
+    ap.add_argument("--train-seed", type=int, default=0, help="seed of the minibatch order")
     ap.add_argument("--eval-seeds", type=int, nargs=2, default=None)
     ap.add_argument("--eval-thetas", type=float, nargs="+", default=[0.25, 0.5])
     ap.add_argument("--summary", default=None, help="write the evaluation rows as JSON here")
@@ -148,14 +150,14 @@ def main():
         _tp.tp_destroy(ctx)
         return
     t0 = time.time()
-    _tp.tp_far_model_init(ctx, 1234)
+    _tp.tp_far_model_init(ctx, args.init_seed)
     _tp.tp_far_dataset_reset(ctx)
     n = 0
     for th in args.theta:
         n += sample_meshes(ctx, range(*args.seeds), args.level, th, args.pairs_per_mesh, seed=int(th * 1000))
     t1 = time.time()
     _tp.tp_far_fit_normalisation(ctx)
-    hist = train(ctx, args.steps, args.batch, args.lr)
+    hist = train(ctx, args.steps, args.batch, args.lr, seed=args.train_seed)
     t2 = time.time()
     if sorted(args.channels) != list(range(7)):
         keep_channels(ctx, args.channels)
