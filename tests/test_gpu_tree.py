@@ -157,6 +157,27 @@ def test_direct_after_tree_build_and_position_updates(tp, ctx):
         tp.tp_destroy(c2)
 
 
+@pytest.mark.parametrize("nt_keep", [2, 17, 33, 777, 2000])
+def test_bh_ragged_sizes(tp, ctx, oracle_mod, nt_keep):
+    """Open sub-meshes of sizes that fill no leaf, run or list evenly (two
+    triangles that share a vertex give an empty sum), against the oracle's
+    Barnes-Hut sums at theta = 0.5."""
+    V, F = meshgen.perturbed_sphere(4, 0.01, 3)
+    F = np.ascontiguousarray(F[:nt_keep])
+    Eo, go, info = oracle_mod.bh_gradient(V, F, 0.5)
+    tp.tp_mesh_upload(ctx, V, F)
+    tp.tp_tree_build(ctx, 16, 30)
+    grad = np.zeros_like(V)
+    e = tp.tp_gradient(ctx, grad, tp.tp_params_default(mode=tp.TP_BH, theta=0.5))
+    st = tp.tp_get_stats(ctx)
+    assert st["far_terms"] == info["far_terms"] and st["pairs_exact"] == info["near_pairs"]
+    if Eo == 0.0:
+        assert e == 0.0 and not grad.any()
+        return
+    assert abs(e - Eo) <= E_TOL * Eo, (e, Eo)
+    assert rel(grad, go) <= G_TOL, rel(grad, go)
+
+
 def test_bh_theta_zero_equals_direct(tp, ctx):
     V, F = meshgen.workload("dish_l5")
     tp.tp_mesh_upload(ctx, V, F)
