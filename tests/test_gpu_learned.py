@@ -8,10 +8,10 @@ of the oracle's FP64 channel sums; a trained network lowers the Barnes-Hut
 energy error on a held-out mesh.
 """
 
+import pathlib
+
 import numpy as np
 import pytest
-
-import pathlib
 
 from paper_2509_22110_gb300 import meshgen
 

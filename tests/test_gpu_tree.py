@@ -8,10 +8,14 @@ admissibility decisions, FP32 pair terms on the GPU); theta = 0 equals the
 direct sum.
 """
 
+import pathlib
+
 import numpy as np
 import pytest
 
 from paper_2509_22110_gb300 import meshgen
+
+ROOT = pathlib.Path(__file__).resolve().parents[1]
 
 pytestmark = pytest.mark.gpu
 
@@ -171,6 +175,15 @@ def test_bh_ragged_sizes(tp, ctx, oracle_mod, nt_keep):
     e = tp.tp_gradient(ctx, grad, tp.tp_params_default(mode=tp.TP_BH, theta=0.5))
     st = tp.tp_get_stats(ctx)
     assert st["far_terms"] == info["far_terms"] and st["pairs_exact"] == info["near_pairs"]
+    # the learned form on the same tree: empty or tiny far lists, windows and runs
+    tp.tp_far_model_load(ctx, str(ROOT / "paper_2509_22110_gb300" / "far_model_l7.bin"))
+    gl = np.zeros_like(V)
+    el = tp.tp_gradient(ctx, gl, tp.tp_params_default(mode=tp.TP_LEARNED, theta=0.5))
+    stl = tp.tp_get_stats(ctx)
+    assert stl["far_terms"] == info["far_terms"] and stl["learned_terms"] <= stl["far_terms"]
+    assert np.isfinite(el) and np.all(np.isfinite(gl))
+    if info["far_terms"] == 0:
+        assert el == e and np.array_equal(gl, grad)
     if Eo == 0.0:
         assert e == 0.0 and not grad.any()
         return
