@@ -29,56 +29,67 @@ __device__ __forceinline__ void cross3(const double* a, const double* b, double*
     c[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-template <typename OutT>
-__global__ void k_adjoint(const double* __restrict__ V, const int32_t* __restrict__ F,
-                          const int32_t* __restrict__ off, const int32_t* __restrict__ v2t,
-                          const int32_t* __restrict__ iperm, const double* __restrict__ nu64,
-                          const double* __restrict__ w64, const double* __restrict__ acc, int64_t nv, int64_t nt,
-                          int64_t ntp, double q, double pq, double scale, OutT* __restrict__ grad,
-                          tp_quad_rule rule) {
-    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (v >= nv) return;
-    double g[3] = {0.0, 0.0, 0.0};
-    for (int32_t e = off[v]; e < off[v + 1]; ++e) {
-        const int32_t ent = v2t[e];
-        const int64_t T = ent >> 2;
-        const int corner = ent & 3;
-        const int64_t k = iperm[T];
-        const double w = w64[T];
-        double nu[3], gn[3], gx[3];
-        for (int a = 0; a < 3; ++a) nu[a] = nu64[a * nt + T];
-        const double Ew = acc[0 * ntp + k], U = acc[1 * ntp + k];
-        const double gw = Ew / (pq * w);
-        for (int a = 0; a < 3; ++a) {
-            gn[a] = q * acc[(2 + a) * ntp + k] / pq;
-            gx[a] = q * (acc[(5 + a) * ntp + k] + U * nu[a]) / pq;
-        }
-        const double* a0 = V + 3 * (int64_t)F[3 * T];
-        const double* a1 = V + 3 * (int64_t)F[3 * T + 1];
-        const double* a2 = V + 3 * (int64_t)F[3 * T + 2];
-        double e1[3], e2[3];
-        for (int a = 0; a < 3; ++a) {
-            e1[a] = a1[a] - a0[a];
-            e2[a] = a2[a] - a0[a];
-        }
-        // element weight w = om_q |N| / 2: dPhi/dN gets om_q dPhi/dw nu / 2 (om = 1 for the centroid rule)
-        const int qp = rule.k > 1 ? (int)(T % rule.k) : 0;
-        const double om = rule.k > 1 ? rule.w[qp] : 1.0;
-        const double len = 2.0 * w / om;
-        const double ndg = nu[0] * gn[0] + nu[1] * gn[1] + nu[2] * gn[2];
-        double G[3];
-        for (int a = 0; a < 3; ++a) G[a] = 0.5 * om * gw * nu[a] + (gn[a] - nu[a] * ndg) / len;
-        double c1[3], c2[3];
-        cross3(e2, G, c1);  // dPhi/de1
-        cross3(G, e1, c2);  // dPhi/de2
+// The chain rule of one element: its three corner contributions to dPhi/dV
+// (corner c of element T at adjc[9 T + 3 c + a]), computed once per element.
+__global__ void k_adjoint_tri(const double* __restrict__ V, const int32_t* __restrict__ F,
+                              const int32_t* __restrict__ iperm, const double* __restrict__ nu64,
+                              const double* __restrict__ w64, const double* __restrict__ acc, int64_t nt,
+                              int64_t ntp, double q, double pq, double* __restrict__ adjc, tp_quad_rule rule) {
+    const int64_t T = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (T >= nt) return;
+    const int64_t k = iperm[T];
+    const double w = w64[T];
+    double nu[3], gn[3], gx[3];
+    for (int a = 0; a < 3; ++a) nu[a] = nu64[a * nt + T];
+    const double Ew = acc[0 * ntp + k], U = acc[1 * ntp + k];
+    const double gw = Ew / (pq * w);
+    for (int a = 0; a < 3; ++a) {
+        gn[a] = q * acc[(2 + a) * ntp + k] / pq;
+        gx[a] = q * (acc[(5 + a) * ntp + k] + U * nu[a]) / pq;
+    }
+    const double* a0 = V + 3 * (int64_t)F[3 * T];
+    const double* a1 = V + 3 * (int64_t)F[3 * T + 1];
+    const double* a2 = V + 3 * (int64_t)F[3 * T + 2];
+    double e1[3], e2[3];
+    for (int a = 0; a < 3; ++a) {
+        e1[a] = a1[a] - a0[a];
+        e2[a] = a2[a] - a0[a];
+    }
+    // element weight w = om_q |N| / 2: dPhi/dN gets om_q dPhi/dw nu / 2 (om = 1 for the centroid rule)
+    const int qp = rule.k > 1 ? (int)(T % rule.k) : 0;
+    const double om = rule.k > 1 ? rule.w[qp] : 1.0;
+    const double len = 2.0 * w / om;
+    const double ndg = nu[0] * gn[0] + nu[1] * gn[1] + nu[2] * gn[2];
+    double G[3];
+    for (int a = 0; a < 3; ++a) G[a] = 0.5 * om * gw * nu[a] + (gn[a] - nu[a] * ndg) / len;
+    double c1[3], c2[3];
+    cross3(e2, G, c1);  // dPhi/de1
+    cross3(G, e1, c2);  // dPhi/de2
+    double* out = adjc + 9 * T;
+    for (int corner = 0; corner < 3; ++corner)
         for (int a = 0; a < 3; ++a) {
             // position x = sum_i l_i v_i: dPhi/dv_corner gets l_corner dPhi/dx (1/3 for the centroid)
             double t = rule.k > 1 ? rule.bary[qp][corner] * gx[a] : gx[a] / 3.0;
             if (corner == 0) t -= c1[a] + c2[a];
             else if (corner == 1) t += c1[a];
             else t += c2[a];
-            g[a] += t;
+            out[3 * corner + a] = t;
         }
+}
+
+// dPhi/dV: per vertex, the corner contributions of its elements in the fixed
+// order of the vertex -> element CSR (deterministic).
+template <typename OutT>
+__global__ void k_adjoint_gather(const int32_t* __restrict__ off, const int32_t* __restrict__ v2t,
+                                 const double* __restrict__ adjc, int64_t nv, double scale,
+                                 OutT* __restrict__ grad) {
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    double g[3] = {0.0, 0.0, 0.0};
+    for (int32_t e = off[v]; e < off[v + 1]; ++e) {
+        const int32_t ent = v2t[e];
+        const double* c = adjc + 9 * (int64_t)(ent >> 2) + 3 * (ent & 3);
+        for (int a = 0; a < 3; ++a) g[a] += c[a];
     }
     for (int a = 0; a < 3; ++a) grad[3 * v + a] = (OutT)(scale * g[a]);
 }
@@ -132,17 +143,20 @@ __global__ void k_sum_final(const double* __restrict__ part, int nb, double mul,
 }  // namespace
 
 tp_status tp_launch_adjoint(tp_ctx* ctx, const tp_params* prm, void* grad, int g_dtype) {
-    const int64_t nv = ctx->nv;
-    unsigned blocks = (unsigned)((nv + 255) / 256);
+    const int64_t nv = ctx->nv, nt = ctx->nt;
     const double q = prm->q, pq = (double)prm->p / prm->q;
+    if (nt > 0) {
+        k_adjoint_tri<<<(unsigned)((nt + 255) / 256), 256, 0, ctx->stream>>>(
+            ctx->V64, ctx->F, ctx->iperm, ctx->nu64, ctx->w64, ctx->acc, nt, ctx->ntp, q, pq, ctx->adjc, ctx->quad);
+        ++ctx->nlaunch;
+    }
+    const unsigned blocks = (unsigned)((nv + 255) / 256);
     if (g_dtype == TP_DTYPE_F64)
-        k_adjoint<double><<<blocks, 256, 0, ctx->stream>>>(ctx->V64, ctx->F, ctx->v2t_off, ctx->v2t, ctx->iperm,
-                                                           ctx->nu64, ctx->w64, ctx->acc, nv, ctx->nt, ctx->ntp, q,
-                                                           pq, prm->scale, static_cast<double*>(grad), ctx->quad);
+        k_adjoint_gather<double><<<blocks, 256, 0, ctx->stream>>>(ctx->v2t_off, ctx->v2t, ctx->adjc, nv, prm->scale,
+                                                                  static_cast<double*>(grad));
     else
-        k_adjoint<float><<<blocks, 256, 0, ctx->stream>>>(ctx->V64, ctx->F, ctx->v2t_off, ctx->v2t, ctx->iperm,
-                                                          ctx->nu64, ctx->w64, ctx->acc, nv, ctx->nt, ctx->ntp, q,
-                                                          pq, prm->scale, static_cast<float*>(grad), ctx->quad);
+        k_adjoint_gather<float><<<blocks, 256, 0, ctx->stream>>>(ctx->v2t_off, ctx->v2t, ctx->adjc, nv, prm->scale,
+                                                                 static_cast<float*>(grad));
     ++ctx->nlaunch;
     TP_CU(cudaGetLastError());
     return TP_OK;

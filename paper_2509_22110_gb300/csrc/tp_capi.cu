@@ -129,6 +129,7 @@ void release_mesh(tp_ctx* ctx) {
     free_ptr(ctx, ctx->src);
     free_ptr(ctx, ctx->Fs);
     free_ptr(ctx, ctx->acc);
+    free_ptr(ctx, ctx->adjc);
     free_ptr(ctx, ctx->red);
     free_ptr(ctx, ctx->flagged);
     free_ptr(ctx, ctx->adjbm);
@@ -196,6 +197,7 @@ tp_status ensure_buffers(tp_ctx* ctx, int64_t nv, int64_t nt) {
     TP_TRY(tp_alloc_t(ctx, &ctx->src, (int64_t)TP_SRCW * ntp));
     TP_TRY(tp_alloc_t(ctx, &ctx->Fs, 3 * ntp));
     TP_TRY(tp_alloc_t(ctx, &ctx->acc, (int64_t)TP_NACC * ntp));
+    TP_TRY(tp_alloc_t(ctx, &ctx->adjc, 9 * nt));
     ctx->red_cap = std::max<int64_t>(nt, 6 * 1024) + 4096;
     TP_TRY(tp_alloc_t(ctx, &ctx->red, ctx->red_cap));
     const int64_t nbits = nsup * nsup;

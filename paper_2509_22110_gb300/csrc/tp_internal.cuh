@@ -122,6 +122,7 @@ struct tp_ctx {
     float* src = nullptr;           // [ntp][TP_SRCW]
     int32_t* Fs = nullptr;          // [ntp][3]
     double* acc = nullptr;          // [TP_NACC][ntp]
+    double* adjc = nullptr;         // [nt][3][3]: per element, its corners' contributions to dPhi/dV
     double* center = nullptr;       // [3] f64 centre subtracted before the f32 split
     double* bounds = nullptr;       // [6] min/max of centroids
     double* red = nullptr;          // reduction scratch
