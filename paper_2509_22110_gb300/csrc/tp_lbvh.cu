@@ -18,10 +18,12 @@
 //      has more, listed in ascending order of their first triangle;
 //   4. moments bottom-up: a primitive holds w, w x (3), w nu (3),
 //      (w nu_a) nu_b (6) and its vertex box; an internal node holds
-//      left + right (left first), added by the second thread to reach it
-//      (atomic visit counter, no waiting).  Every FP64 operation is
-//      separately rounded in a fixed order, so the moments are bit-exact
-//      with the oracle.
+//      left + right, added by the second thread to reach it (atomic visit
+//      counter, no waiting: in shared memory while the node's range lies in
+//      the block's slice of primitives, in global memory above that).  Every
+//      FP64 operation is separately rounded in a fixed order, so the moments
+//      are bit-exact with the oracle.  A second pass writes each node's
+//      far-field and admissibility records.
 #include <cub/cub.cuh>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -102,116 +104,186 @@ struct NonNeg {
     __device__ __forceinline__ bool operator()(const int32_t& a) const { return a >= 0; }
 };
 
-// primitive moments and the bottom-up pass
-__global__ void k_moments(const double* __restrict__ V, const int32_t* __restrict__ F,
-                          const double* __restrict__ x64, const double* __restrict__ nu64,
-                          const double* __restrict__ w64, const int32_t* __restrict__ perm,
-                          const int32_t* __restrict__ left, const int32_t* __restrict__ right,
-                          const int32_t* __restrict__ parent, int64_t n, int32_t* __restrict__ counter,
-                          double* __restrict__ mom, double* __restrict__ box) {
-    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+constexpr int MOM_B = 64;   // primitives per block of the bottom-up pass
+constexpr int MOM_W = 19;   // values per node: 13 moments + 6 box bounds
+
+// The records derived from a node's moments and box:
+//   nodef[v] = X - centre split hi/lo (6), nubar = sum(w nu)/A (3), sqrt(p/q) A (1)
+//              in FP32 for the far-field terms;
+//   adm64[v] = (X_C[3] = sum(w x)/A, diag_C = |box extent|) in FP64, with exactly
+//              the operations and order of the oracle's admissibility test;
+//   adm32[v] = box rounded outward (min down, max up) [6], box rounded inward
+//              (min up, max down) [6], X_C [3], diag_C [1] in FP32 for the
+//              pre-test that settles all but borderline cases (tp_bh.cu).
+__device__ __forceinline__ void node_records(int64_t v, const double* __restrict__ m, const double* __restrict__ b,
+                                             const double* __restrict__ c3, float* __restrict__ nodef,
+                                             double* __restrict__ adm64, float* __restrict__ adm32) {
+    double dc2 = 0.0;
+    double X[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double ec = __dsub_rn(b[3 + a], b[a]);
+        dc2 = __dadd_rn(dc2, __dmul_rn(ec, ec));
+        X[a] = __ddiv_rn(m[1 + a], m[0]);
+    }
+    const double dc = __dsqrt_rn(dc2);
+    double2* a64 = reinterpret_cast<double2*>(adm64 + 4 * v);
+    a64[0] = make_double2(X[0], X[1]);
+    a64[1] = make_double2(X[2], dc);
+    float4* a32 = reinterpret_cast<float4*>(adm32 + 16 * v);
+    a32[0] = make_float4(__double2float_rd(b[0]), __double2float_rd(b[1]), __double2float_rd(b[2]),
+                         __double2float_ru(b[3]));
+    a32[1] = make_float4(__double2float_ru(b[4]), __double2float_ru(b[5]), __double2float_ru(b[0]),
+                         __double2float_ru(b[1]));
+    a32[2] = make_float4(__double2float_ru(b[2]), __double2float_rd(b[3]), __double2float_rd(b[4]),
+                         __double2float_rd(b[5]));
+    a32[3] = make_float4((float)X[0], (float)X[1], (float)X[2], (float)dc);
+    float hi[3], lo[3], nb[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double Xc = X[a] - c3[a];
+        hi[a] = (float)Xc;
+        lo[a] = (float)(Xc - (double)hi[a]);
+        nb[a] = (float)(__ddiv_rn(m[4 + a], m[0]));
+    }
+    float4* r = reinterpret_cast<float4*>(nodef + 16 * v);
+    r[0] = make_float4(hi[0], hi[1], hi[2], lo[0]);
+    r[1] = make_float4(lo[1], lo[2], nb[0], nb[1]);
+    r[2] = make_float4(nb[2], (float)(1.4142135623730951 * m[0]), 0.0f, 0.0f);
+    r[3] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+__device__ __forceinline__ void node_store(int64_t v, const double* __restrict__ m, double* __restrict__ mom,
+                                           double* __restrict__ box) {
+    double* mo = mom + 13 * v;
+#pragma unroll
+    for (int c = 0; c < 13; ++c) mo[c] = m[c];
+    double2* bo = reinterpret_cast<double2*>(box + 6 * v);
+    bo[0] = make_double2(m[13], m[14]);
+    bo[1] = make_double2(m[15], m[16]);
+    bo[2] = make_double2(m[17], m[18]);
+}
+
+// parent = left + right (moments), box = union with the left child's value
+// kept on ties, as in the oracle
+__device__ __forceinline__ void node_combine(double* __restrict__ own, const double* __restrict__ sib, int stride,
+                                             bool own_left) {
+#pragma unroll
+    for (int c = 0; c < 13; ++c) own[c] = __dadd_rn(own[c], sib[c * stride]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double o0 = own[13 + a], s0 = sib[(13 + a) * stride];
+        const double o1 = own[16 + a], s1 = sib[(16 + a) * stride];
+        const double l0 = own_left ? o0 : s0, r0 = own_left ? s0 : o0;
+        const double l1 = own_left ? o1 : s1, r1 = own_left ? s1 : o1;
+        own[13 + a] = l0 < r0 ? l0 : r0;
+        own[16 + a] = l1 > r1 ? l1 : r1;
+    }
+}
+
+// Primitive moments and the bottom-up pass.
+// Block b owns primitives [b MOM_B, (b+1) MOM_B): a node whose key range lies
+// inside that slice is added up in shared memory (CTA counters), one whose
+// range spans slices through global memory (device counters); in both the
+// second thread to reach a node adds its children and carries on.
+__global__ void __launch_bounds__(MOM_B) k_moments(
+    const double* __restrict__ V, const int32_t* __restrict__ F, const double* __restrict__ x64,
+    const double* __restrict__ nu64, const double* __restrict__ w64, const int32_t* __restrict__ perm,
+    const int32_t* __restrict__ left, const int32_t* __restrict__ right, const int32_t* __restrict__ parent,
+    const int32_t* __restrict__ first, const int32_t* __restrict__ last, int64_t n, int32_t* __restrict__ counter,
+    double* __restrict__ mom, double* __restrict__ box) {
+    __shared__ double vs[MOM_W][2 * MOM_B];  // slot t: primitive base+t; slot MOM_B+i: internal node base+i
+    __shared__ int cnt_s[MOM_B];
+    const int t = threadIdx.x;
+    const int64_t base = blockIdx.x * (int64_t)MOM_B;
+    cnt_s[t] = 0;
+    __syncthreads();
+    const int64_t k = base + t;
     if (k >= n) return;
-    const int64_t T = perm[k];
-    int64_t v = n - 1 + k;
+    double own[MOM_W];
     {
-        double* m = mom + 13 * v;
+        const int64_t T = perm[k];
         const double w = w64[T];
         double nu[3];
         for (int a = 0; a < 3; ++a) nu[a] = nu64[a * n + T];
-        m[0] = w;
-        for (int a = 0; a < 3; ++a) m[1 + a] = __dmul_rn(w, x64[a * n + T]);
-        for (int a = 0; a < 3; ++a) m[4 + a] = __dmul_rn(w, nu[a]);
+        own[0] = w;
+        for (int a = 0; a < 3; ++a) own[1 + a] = __dmul_rn(w, x64[a * n + T]);
+        for (int a = 0; a < 3; ++a) own[4 + a] = __dmul_rn(w, nu[a]);
         int o = 7;
         for (int a = 0; a < 3; ++a)
-            for (int c = a; c < 3; ++c) m[o++] = __dmul_rn(__dmul_rn(w, nu[a]), nu[c]);
-        double* b = box + 6 * v;
+            for (int c = a; c < 3; ++c) own[o++] = __dmul_rn(__dmul_rn(w, nu[a]), nu[c]);
+        const int64_t f0 = 3 * (int64_t)F[3 * T], f1 = 3 * (int64_t)F[3 * T + 1], f2 = 3 * (int64_t)F[3 * T + 2];
         for (int a = 0; a < 3; ++a) {
-            double p0 = V[3 * (int64_t)F[3 * T] + a], p1 = V[3 * (int64_t)F[3 * T + 1] + a],
-                   p2 = V[3 * (int64_t)F[3 * T + 2] + a];
+            const double p0 = V[f0 + a], p1 = V[f1 + a], p2 = V[f2 + a];
             double lo = p0, hi = p0;
             if (p1 < lo) lo = p1;
             if (p1 > hi) hi = p1;
             if (p2 < lo) lo = p2;
             if (p2 > hi) hi = p2;
-            b[a] = lo;
-            b[3 + a] = hi;
+            own[13 + a] = lo;
+            own[16 + a] = hi;
         }
     }
+    int64_t v = n - 1 + k;
+    node_store(v, own, mom, box);
     if (n == 1) return;
-    // climb: the second thread to reach a node adds its children
+    int slot = t;
+    bool local = true;
     while (true) {
         const int64_t p = parent[v];
         if (p < 0) break;
-        __threadfence();
-        if (atomicAdd(&counter[p], 1) == 0) break;
-        __threadfence();
-        const int64_t l = left[p], r = right[p];
-        const double* ml = mom + 13 * l;
-        const double* mr = mom + 13 * r;
-        double* m = mom + 13 * p;
-        for (int c = 0; c < 13; ++c) m[c] = __dadd_rn(__ldcg(ml + c), __ldcg(mr + c));
-        const double* bl = box + 6 * l;
-        const double* br = box + 6 * r;
-        double* b = box + 6 * p;
-        for (int a = 0; a < 3; ++a) {
-            double l0 = __ldcg(bl + a), r0 = __ldcg(br + a), l1 = __ldcg(bl + 3 + a), r1 = __ldcg(br + 3 + a);
-            b[a] = l0 < r0 ? l0 : r0;
-            b[3 + a] = l1 > r1 ? l1 : r1;
+        const int64_t lc = left[p], rc = right[p];
+        const bool own_left = lc == v;
+        const int64_t sib = own_left ? rc : lc;
+        if (local && first[p] >= base && last[p] < base + MOM_B) {
+#pragma unroll
+            for (int c = 0; c < MOM_W; ++c) vs[c][slot] = own[c];
+            __threadfence_block();
+            if (atomicAdd(&cnt_s[p - base], 1) == 0) break;
+            __threadfence_block();
+            const int ss = sib >= n - 1 ? (int)(sib - (n - 1) - base) : MOM_B + (int)(sib - base);
+            node_combine(own, &vs[0][ss], 2 * MOM_B, own_left);
+            slot = MOM_B + (int)(p - base);
+        } else {
+            local = false;
+            __threadfence();
+            if (atomicAdd(&counter[p], 1) == 0) break;
+            __threadfence();
+            double sv[MOM_W];
+            const double* ms = mom + 13 * sib;
+            const double* bs = box + 6 * sib;
+#pragma unroll
+            for (int c = 0; c < 13; ++c) sv[c] = __ldcg(ms + c);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                sv[13 + a] = __ldcg(bs + a);
+                sv[16 + a] = __ldcg(bs + 3 + a);
+            }
+            node_combine(own, sv, 1, own_left);
         }
         v = p;
+        node_store(v, own, mom, box);
     }
 }
 
-// f32 node record for the far-field evaluation: X - centre split hi/lo (6),
-// nubar = sum(w nu)/A (3), sqrt(p/q) A (1)
-__global__ void k_node_records(const double* __restrict__ mom, const double* __restrict__ center, int64_t nn,
-                               float* __restrict__ rec) {
-    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (v >= nn) return;
-    const double* m = mom + 13 * v;
-    float* r = rec + 16 * v;
-    for (int a = 0; a < 3; ++a) {
-        double X = m[1 + a] / m[0] - center[a];
-        float hi = (float)X;
-        r[a] = hi;
-        r[3 + a] = (float)(X - (double)hi);
-        r[6 + a] = (float)(m[4 + a] / m[0]);
-    }
-    r[9] = (float)(1.4142135623730951 * m[0]);
-    for (int a = 10; a < 16; ++a) r[a] = 0.0f;
-}
-
-// Per-node constants of the admissibility test (Barnes-Hut, tp_bh.cu):
-//   adm64[v] = (X_C[3] = sum(w x)/A, diag_C = |box extent|) in FP64, computed
-//              with exactly the operations and order of the oracle's test;
-//   adm32[v] = box rounded outward (min down, max up) [6], box rounded inward
-//              (min up, max down) [6], X_C [3], diag_C [1] in FP32 for the
-//              pre-test that settles all but borderline cases.
-__global__ void k_node_adm(const double* __restrict__ mom, const double* __restrict__ box, int64_t nn,
+// far-field and admissibility records of every node (one thread per node)
+__global__ void k_node_out(const double* __restrict__ mom, const double* __restrict__ box,
+                           const double* __restrict__ center, int64_t nn, float* __restrict__ nodef,
                            double* __restrict__ adm64, float* __restrict__ adm32) {
-    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (v >= nn) return;
-    const double* m = mom + 13 * v;
-    const double* b = box + 6 * v;
-    double dc2 = 0.0;
-    double X[3];
-    for (int a = 0; a < 3; ++a) {
-        const double ec = __dsub_rn(b[3 + a], b[a]);
-        dc2 = __dadd_rn(dc2, __dmul_rn(ec, ec));
-        X[a] = __ddiv_rn(m[1 + a], m[0]);
-        adm64[4 * v + a] = X[a];
+    double m[13], b[6];
+#pragma unroll
+    for (int c = 0; c < 13; ++c) m[c] = mom[13 * v + c];
+    const double2* bi = reinterpret_cast<const double2*>(box + 6 * v);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double2 x = bi[c];
+        b[2 * c] = x.x;
+        b[2 * c + 1] = x.y;
     }
-    const double dc = __dsqrt_rn(dc2);
-    adm64[4 * v + 3] = dc;
-    float* r = adm32 + 16 * v;
-    for (int a = 0; a < 3; ++a) {
-        r[a] = __double2float_rd(b[a]);
-        r[3 + a] = __double2float_ru(b[3 + a]);
-        r[6 + a] = __double2float_ru(b[a]);
-        r[9 + a] = __double2float_rd(b[3 + a]);
-        r[12 + a] = (float)X[a];
-    }
-    r[15] = (float)dc;
+    const double c3[3] = {center[0], center[1], center[2]};
+    node_records(v, m, b, c3, nodef, adm64, adm32);
 }
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -290,12 +362,11 @@ tp_status tp_launch_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits) {
                                 ctx->stream));
     // 4. moments
     if (n > 1) TP_CU(cudaMemsetAsync(t.counter, 0, sizeof(int32_t) * (n - 1), ctx->stream));
-    k_moments<<<nblk(n, 256), 256, 0, ctx->stream>>>(ctx->V64, ctx->F, ctx->x64, ctx->nu64, ctx->w64, ctx->perm,
-                                                     t.left, t.right, t.parent, n, t.counter, t.mom, t.box);
+    k_moments<<<nblk(n, MOM_B), MOM_B, 0, ctx->stream>>>(ctx->V64, ctx->F, ctx->x64, ctx->nu64, ctx->w64, ctx->perm,
+                                                         t.left, t.right, t.parent, t.first, t.last, n, t.counter,
+                                                         t.mom, t.box);
     ++ctx->nlaunch;
-    k_node_records<<<nblk(nn, 256), 256, 0, ctx->stream>>>(t.mom, ctx->center, nn, t.nodef);
-    ++ctx->nlaunch;
-    k_node_adm<<<nblk(nn, 256), 256, 0, ctx->stream>>>(t.mom, t.box, nn, t.adm64, t.adm32);
+    k_node_out<<<nblk(nn, 256), 256, 0, ctx->stream>>>(t.mom, t.box, ctx->center, nn, t.nodef, t.adm64, t.adm32);
     ++ctx->nlaunch;
     t.feat_stale = true;  // the network's node features are computed when the learned form needs them
     int32_t h = 0;
