@@ -250,6 +250,16 @@ tp_status tp_launch_direct_grad(tp_ctx* ctx, const tp_params* prm);
 tp_status tp_launch_direct_energy(tp_ctx* ctx, const tp_params* prm, double* partials, int* nparts);
 tp_status tp_launch_direct_f64(tp_ctx* ctx, const tp_params* prm, bool grad);
 // tp_adjoint.cu
+// A node the Barnes-Hut traversal can reach: the root, or a child of a node
+// with more than leaf_size members (a node of at most leaf_size members is
+// never opened, tp_bh.cu).  Per-node records are written for these only.
+__device__ __forceinline__ bool tp_node_reachable(const int32_t* __restrict__ parent,
+                                                  const int32_t* __restrict__ first,
+                                                  const int32_t* __restrict__ last, int64_t v, int leaf_size) {
+    const int32_t p = parent[v];
+    return p < 0 || last[p] - first[p] + 1 > leaf_size;
+}
+
 tp_status tp_launch_adjoint(tp_ctx* ctx, const tp_params* prm, void* grad, int g_dtype);
 tp_status tp_launch_energy_from_acc(tp_ctx* ctx, const tp_params* prm, double* d_out);
 tp_status tp_launch_reduce_sum(tp_ctx* ctx, const double* in, int64_t n, double* d_out);

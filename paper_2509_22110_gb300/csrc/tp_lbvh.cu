@@ -22,8 +22,8 @@
 //      counter, no waiting: in shared memory while the node's range lies in
 //      the block's slice of primitives, in global memory above that).  Every
 //      FP64 operation is separately rounded in a fixed order, so the moments
-//      are bit-exact with the oracle.  A second pass writes each node's
-//      far-field and admissibility records.
+//      are bit-exact with the oracle.  A second pass writes the far-field
+//      and admissibility records of the nodes the traversal can reach.
 #include <cub/cub.cuh>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -266,12 +266,15 @@ __global__ void __launch_bounds__(MOM_B) k_moments(
     }
 }
 
-// far-field and admissibility records of every node (one thread per node)
+// far-field and admissibility records of every node the traversal can reach
+// (one thread per node)
 __global__ void k_node_out(const double* __restrict__ mom, const double* __restrict__ box,
-                           const double* __restrict__ center, int64_t nn, float* __restrict__ nodef,
-                           double* __restrict__ adm64, float* __restrict__ adm32) {
+                           const int32_t* __restrict__ parent, const int32_t* __restrict__ first,
+                           const int32_t* __restrict__ last, int leaf_size, const double* __restrict__ center,
+                           int64_t nn, float* __restrict__ nodef, double* __restrict__ adm64,
+                           float* __restrict__ adm32) {
     const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (v >= nn) return;
+    if (v >= nn || !tp_node_reachable(parent, first, last, v, leaf_size)) return;
     double m[13], b[6];
 #pragma unroll
     for (int c = 0; c < 13; ++c) m[c] = mom[13 * v + c];
@@ -366,7 +369,8 @@ tp_status tp_launch_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits) {
                                                          t.left, t.right, t.parent, t.first, t.last, n, t.counter,
                                                          t.mom, t.box);
     ++ctx->nlaunch;
-    k_node_out<<<nblk(nn, 256), 256, 0, ctx->stream>>>(t.mom, t.box, ctx->center, nn, t.nodef, t.adm64, t.adm32);
+    k_node_out<<<nblk(nn, 256), 256, 0, ctx->stream>>>(t.mom, t.box, t.parent, t.first, t.last, leaf_size,
+                                                       ctx->center, nn, t.nodef, t.adm64, t.adm32);
     ++ctx->nlaunch;
     t.feat_stale = true;  // the network's node features are computed when the learned form needs them
     int32_t h = 0;

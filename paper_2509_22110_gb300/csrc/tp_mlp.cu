@@ -58,11 +58,13 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
     return x ^ (x >> 31);
 }
 
-// FP32 feature record of every node: A, X[3], nubar[3], M2/A (6), diag
-__global__ void k_node_feat(const double* __restrict__ mom, const double* __restrict__ box, int64_t nn,
-                            float* __restrict__ rec) {
+// FP32 feature record of every node the traversal can reach: A, X[3],
+// nubar[3], M2/A (6), diag
+__global__ void k_node_feat(const double* __restrict__ mom, const double* __restrict__ box,
+                            const int32_t* __restrict__ parent, const int32_t* __restrict__ first,
+                            const int32_t* __restrict__ last, int leaf_size, int64_t nn, float* __restrict__ rec) {
     int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (v >= nn) return;
+    if (v >= nn || !tp_node_reachable(parent, first, last, v, leaf_size)) return;
     const double* m = mom + 13 * v;
     const double* b = box + 6 * v;
     float* r = rec + FEAT_REC * v;
@@ -630,7 +632,8 @@ void tp_mlp_release(tp_ctx* ctx) {
 tp_status tp_mlp_node_features(tp_ctx* ctx) {
     tp_tree& t = ctx->tree;
     const int64_t nn = 2 * ctx->nt - 1;
-    k_node_feat<<<(unsigned)((nn + 255) / 256), 256, 0, ctx->stream>>>(t.mom, t.box, nn, t.nodeft);
+    k_node_feat<<<(unsigned)((nn + 255) / 256), 256, 0, ctx->stream>>>(t.mom, t.box, t.parent, t.first, t.last,
+                                                                      t.leaf_size, nn, t.nodeft);
     ++ctx->nlaunch;
     TP_CU(cudaGetLastError());
     return TP_OK;
