@@ -164,6 +164,18 @@ __device__ __forceinline__ void node_store(int64_t v, const double* __restrict__
     bo[2] = make_double2(m[17], m[18]);
 }
 
+// Order-preserving integer key of a finite double, with -0 and +0 equal:
+// key(l) < key(r) exactly when l < r.  The boxes' min/max selections below
+// keep the FP64 comparison's result (ties pick the same operand) but run on
+// the integer pipe instead of the narrow FP64 pipe.  Positions are finite
+// (checked at upload).
+__device__ __forceinline__ long long ord_key(double x) {
+    const long long b = __double_as_longlong(x);
+    return b >= 0 ? b : (long long)(0x8000000000000000ULL - (unsigned long long)b);
+}
+__device__ __forceinline__ double lo_of(double l, double r) { return ord_key(l) < ord_key(r) ? l : r; }
+__device__ __forceinline__ double hi_of(double l, double r) { return ord_key(l) > ord_key(r) ? l : r; }
+
 // parent = left + right (moments), box = union with the left child's value
 // kept on ties, as in the oracle
 __device__ __forceinline__ void node_combine(double* __restrict__ own, const double* __restrict__ sib, int stride,
@@ -176,8 +188,8 @@ __device__ __forceinline__ void node_combine(double* __restrict__ own, const dou
         const double o1 = own[16 + a], s1 = sib[(16 + a) * stride];
         const double l0 = own_left ? o0 : s0, r0 = own_left ? s0 : o0;
         const double l1 = own_left ? o1 : s1, r1 = own_left ? s1 : o1;
-        own[13 + a] = l0 < r0 ? l0 : r0;
-        own[16 + a] = l1 > r1 ? l1 : r1;
+        own[13 + a] = lo_of(l0, r0);
+        own[16 + a] = hi_of(l1, r1);
     }
 }
 
@@ -215,13 +227,9 @@ __global__ void __launch_bounds__(MOM_B) k_moments(
         const int64_t f0 = 3 * (int64_t)F[3 * T], f1 = 3 * (int64_t)F[3 * T + 1], f2 = 3 * (int64_t)F[3 * T + 2];
         for (int a = 0; a < 3; ++a) {
             const double p0 = V[f0 + a], p1 = V[f1 + a], p2 = V[f2 + a];
-            double lo = p0, hi = p0;
-            if (p1 < lo) lo = p1;
-            if (p1 > hi) hi = p1;
-            if (p2 < lo) lo = p2;
-            if (p2 > hi) hi = p2;
-            own[13 + a] = lo;
-            own[16 + a] = hi;
+            // lo = p0, then p1 and p2 replace it when smaller (hi: larger)
+            own[13 + a] = lo_of(p2, lo_of(p1, p0));
+            own[16 + a] = hi_of(p2, hi_of(p1, p0));
         }
     }
     int64_t v = n - 1 + k;

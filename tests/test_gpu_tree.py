@@ -161,6 +161,45 @@ def test_direct_after_tree_build_and_position_updates(tp, ctx):
         tp.tp_destroy(c2)
 
 
+def test_bh_and_learned_after_rebuilds_match_fresh_context(tp, ctx):
+    """Node records and network features are written only for nodes the
+    traversal can reach (the root and children of nodes above the leaf
+    size); the other nodes keep what an earlier build left.  After builds
+    with smaller and larger leaf sizes on other positions, the Barnes-Hut and
+    learned results equal those of a fresh context (up to summation order)."""
+    import torch
+
+    model = str(ROOT / "paper_2509_22110_gb300" / "far_model_l7.bin")
+    V, F = meshgen.sh_deformed_sphere(5, 12, 0.05, 9)
+    V2 = V + 0.03 * np.sin(3.0 * V[:, [1, 2, 0]])  # smooth, changes the Morton order
+    tp.tp_far_model_load(ctx, model)
+    tp.tp_mesh_upload(ctx, V, F)
+    g = np.zeros_like(V)
+    for leaf in (4, 32):
+        tp.tp_tree_build(ctx, leaf, 30)
+        tp.tp_gradient(ctx, g, tp.tp_params_default(mode=tp.TP_BH, theta=0.5))
+        tp.tp_gradient(ctx, g, tp.tp_params_default(mode=tp.TP_LEARNED, theta=0.5))
+    tp.tp_mesh_upload(ctx, V2, None, flags=tp._tp.TP_POSITIONS_ONLY)
+    tp.tp_tree_build(ctx, 16, 30)
+    got = {}
+    for mode in (tp.TP_BH, tp.TP_LEARNED):
+        gm = np.zeros_like(V2)
+        got[mode] = (tp.tp_gradient(ctx, gm, tp.tp_params_default(mode=mode, theta=0.5)), gm)
+    c2 = tp.tp_create(0, torch.cuda.current_stream().cuda_stream)
+    try:
+        tp.tp_far_model_load(c2, model)
+        tp.tp_mesh_upload(c2, V2, F)
+        tp.tp_tree_build(c2, 16, 30)
+        for mode, tol in ((tp.TP_BH, 1e-12), (tp.TP_LEARNED, 1e-7)):
+            gf = np.zeros_like(V2)
+            ef = tp.tp_gradient(c2, gf, tp.tp_params_default(mode=mode, theta=0.5))
+            e, gm = got[mode]
+            assert abs(e - ef) <= tol * abs(ef), (mode, e, ef)
+            assert rel(gm, gf) <= tol, (mode, rel(gm, gf))
+    finally:
+        tp.tp_destroy(c2)
+
+
 @pytest.mark.parametrize("nt_keep", [2, 17, 33, 777, 2000])
 def test_bh_ragged_sizes(tp, ctx, oracle_mod, nt_keep):
     """Open sub-meshes of sizes that fill no leaf, run or list evenly (two
