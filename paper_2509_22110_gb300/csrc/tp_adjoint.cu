@@ -34,18 +34,21 @@ __device__ __forceinline__ void cross3(const double* a, const double* b, double*
 __global__ void k_adjoint_tri(const double* __restrict__ V, const int32_t* __restrict__ F,
                               const int32_t* __restrict__ iperm, const double* __restrict__ nu64,
                               const double* __restrict__ w64, const double* __restrict__ acc, int64_t nt,
-                              int64_t ntp, double q, double pq, double* __restrict__ adjc, tp_quad_rule rule) {
+                              int64_t ntp, double qp, double ipq, double* __restrict__ adjc, tp_quad_rule rule) {
     const int64_t T = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (T >= nt) return;
     const int64_t k = iperm[T];
     const double w = w64[T];
     double nu[3], gn[3], gx[3];
     for (int a = 0; a < 3; ++a) nu[a] = nu64[a * nt + T];
+    // one division per element: the FP64 pipe is narrow, and reciprocals
+    // change the result only in the last bits
+    const double iw = 1.0 / w;
     const double Ew = acc[0 * ntp + k], U = acc[1 * ntp + k];
-    const double gw = Ew / (pq * w);
+    const double gw = Ew * iw * ipq;  // Ew / (pq w)
     for (int a = 0; a < 3; ++a) {
-        gn[a] = q * acc[(2 + a) * ntp + k] / pq;
-        gx[a] = q * (acc[(5 + a) * ntp + k] + U * nu[a]) / pq;
+        gn[a] = qp * acc[(2 + a) * ntp + k];
+        gx[a] = qp * (acc[(5 + a) * ntp + k] + U * nu[a]);
     }
     const double* a0 = V + 3 * (int64_t)F[3 * T];
     const double* a1 = V + 3 * (int64_t)F[3 * T + 1];
@@ -56,12 +59,12 @@ __global__ void k_adjoint_tri(const double* __restrict__ V, const int32_t* __res
         e2[a] = a2[a] - a0[a];
     }
     // element weight w = om_q |N| / 2: dPhi/dN gets om_q dPhi/dw nu / 2 (om = 1 for the centroid rule)
-    const int qp = rule.k > 1 ? (int)(T % rule.k) : 0;
-    const double om = rule.k > 1 ? rule.w[qp] : 1.0;
-    const double len = 2.0 * w / om;
+    const int qi = rule.k > 1 ? (int)(T % rule.k) : 0;
+    const double om = rule.k > 1 ? rule.w[qi] : 1.0;
+    const double ilen = 0.5 * om * iw;  // 1 / |N|, |N| = 2 w / om
     const double ndg = nu[0] * gn[0] + nu[1] * gn[1] + nu[2] * gn[2];
     double G[3];
-    for (int a = 0; a < 3; ++a) G[a] = 0.5 * om * gw * nu[a] + (gn[a] - nu[a] * ndg) / len;
+    for (int a = 0; a < 3; ++a) G[a] = 0.5 * om * gw * nu[a] + (gn[a] - nu[a] * ndg) * ilen;
     double c1[3], c2[3];
     cross3(e2, G, c1);  // dPhi/de1
     cross3(G, e1, c2);  // dPhi/de2
@@ -69,7 +72,7 @@ __global__ void k_adjoint_tri(const double* __restrict__ V, const int32_t* __res
     for (int corner = 0; corner < 3; ++corner)
         for (int a = 0; a < 3; ++a) {
             // position x = sum_i l_i v_i: dPhi/dv_corner gets l_corner dPhi/dx (1/3 for the centroid)
-            double t = rule.k > 1 ? rule.bary[qp][corner] * gx[a] : gx[a] / 3.0;
+            double t = rule.k > 1 ? rule.bary[qi][corner] * gx[a] : gx[a] * (1.0 / 3.0);
             if (corner == 0) t -= c1[a] + c2[a];
             else if (corner == 1) t += c1[a];
             else t += c2[a];
@@ -147,7 +150,8 @@ tp_status tp_launch_adjoint(tp_ctx* ctx, const tp_params* prm, void* grad, int g
     const double q = prm->q, pq = (double)prm->p / prm->q;
     if (nt > 0) {
         k_adjoint_tri<<<(unsigned)((nt + 255) / 256), 256, 0, ctx->stream>>>(
-            ctx->V64, ctx->F, ctx->iperm, ctx->nu64, ctx->w64, ctx->acc, nt, ctx->ntp, q, pq, ctx->adjc, ctx->quad);
+            ctx->V64, ctx->F, ctx->iperm, ctx->nu64, ctx->w64, ctx->acc, nt, ctx->ntp, q / pq, 1.0 / pq, ctx->adjc,
+            ctx->quad);
         ++ctx->nlaunch;
     }
     const unsigned blocks = (unsigned)((nv + 255) / 256);
