@@ -246,9 +246,10 @@ tp_status tp_debug_accum(tp_ctx* ctx, double* gw, double* gnu, double* gx);
  * runs the network and applies its factors in windows of at most `rows`
  * listed pairs; the network rows and factors take 100 B per row of the
  * window.  rows = 0 restores the default of 32 Mi rows (about 3.4 GB).
- * Results do not depend on the window beyond FP32 rounding of partial sums.
- * An implementation control with no counterpart in the paper.  TP_E_ARG for
- * rows in 1..31. */
+ * Windows end on the first row of a run of one leaf's pairs, so they may
+ * hold up to 255 rows more, and no run is split: results do not depend on
+ * the window beyond the order of the FP64 atomic sums.  An implementation
+ * control with no counterpart in the paper.  TP_E_ARG for rows in 1..31. */
 tp_status tp_set_learned_window(tp_ctx* ctx, int64_t rows);
 
 /* The tree of the last tp_tree_build: codes[nt] (by original index),

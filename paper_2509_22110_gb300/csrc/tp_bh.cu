@@ -890,6 +890,23 @@ __device__ __forceinline__ void window_runs(const int64_t* skey, int64_t nruns, 
     hi = bh_lower_bound(skey, nruns, w1);
 }
 
+// Window boundaries of the learned passes, moved onto run starts: bnd[k] is
+// the first row of the first run starting at or after row k win (the listed
+// rows if none).  No run is then split between windows, so its FP32 sums do
+// not depend on where the listing placed its rows.  A window holds fewer
+// than win + BH_FAR rows.
+__global__ void k_window_bounds(const int64_t* __restrict__ skey, int64_t nruns, int64_t win, int64_t nwin,
+                                int64_t rows, int64_t* __restrict__ bnd) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k > nwin) return;
+    if (k == 0 || k == nwin) {
+        bnd[k] = k == 0 ? 0 : rows;
+        return;
+    }
+    const int64_t i = bh_lower_bound(skey, nruns, k * win);
+    bnd[k] = i < nruns ? skey[i] : rows;
+}
+
 __global__ void k_run_keys(const tp_far_run* __restrict__ runs, int64_t nruns, int64_t* __restrict__ key,
                            int32_t* __restrict__ ord) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1260,15 +1277,16 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
         // network rows and factors of the listed (leaf, cluster) pairs, for one
         // window of at most ctx->learned_window rows at a time
         const int64_t win = std::min<int64_t>(std::max<int64_t>(listed_rows, 32), ctx->learned_window);
-        if (ctx->far_xcap < win) {
+        const int64_t xcap = win + BH_FAR;  // a window ends on a run start, at most BH_FAR - 1 rows late
+        if (ctx->far_xcap < xcap) {
             tp_free(ctx, ctx->far_X);
             tp_free(ctx, ctx->far_kf);
             ctx->far_X = nullptr;
             ctx->far_kf = nullptr;
             ctx->far_xcap = 0;
-            TP_TRY(tp_alloc_t(ctx, &ctx->far_X, win * MLP_NIP));
-            TP_TRY(tp_alloc_t(ctx, &ctx->far_kf, win * 8));
-            ctx->far_xcap = win;
+            TP_TRY(tp_alloc_t(ctx, &ctx->far_X, xcap * MLP_NIP));
+            TP_TRY(tp_alloc_t(ctx, &ctx->far_kf, xcap * 8));
+            ctx->far_xcap = xcap;
         }
         A.wb = static_cast<const __nv_bfloat16*>(tp_mlp_weights(ctx));
         A.mbias = tp_mlp_bias(ctx);
@@ -1293,10 +1311,33 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
             TP_CU(cub::DeviceRadixSort::SortPairs(ctx->sort_tmp, have, ctx->run_key, ctx->run_key_s, ctx->run_ord,
                                                   ctx->run_ord_s, (int)listed_runs, 0, end_bit, ctx->stream));
         }
+        // window boundaries on run starts (read back once when there are several windows)
+        const int64_t nwin = (listed_rows + win - 1) / win;
+        std::vector<int64_t> bnd = {0, listed_rows};
+        if (nwin > 1) {
+            if (ctx->win_bnd_cap < nwin + 1) {
+                tp_free(ctx, ctx->win_bnd);
+                ctx->win_bnd = nullptr;
+                ctx->win_bnd_cap = 0;
+                TP_TRY(tp_alloc_t(ctx, &ctx->win_bnd, nwin + 1));
+                ctx->win_bnd_cap = nwin + 1;
+            }
+            k_window_bounds<<<(unsigned)((nwin + 256) / 256), 256, 0, ctx->stream>>>(
+                ctx->run_key_s, listed_runs, win, nwin, listed_rows, ctx->win_bnd);
+            ++ctx->nlaunch;
+            bnd.resize(nwin + 1);
+            TP_CU(cudaMemcpyAsync(bnd.data(), ctx->win_bnd, sizeof(int64_t) * (nwin + 1), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+            TP_CU(cudaStreamSynchronize(ctx->stream));
+        }
         // per window: the network's factors of the listed far terms, then the far terms with them
         const unsigned lblocks = (unsigned)std::max(1, ctx->num_sms * 4);
-        for (int64_t w0 = 0; w0 < listed_rows; w0 += win) {
-            const int64_t w1 = std::min<int64_t>(w0 + win, listed_rows);
+        for (size_t wi = 0; wi + 1 < bnd.size(); ++wi) {
+            const int64_t w0 = bnd[wi], w1 = bnd[wi + 1];
+            if (w1 <= w0) continue;
+            if (w1 - w0 > ctx->far_xcap)  // cannot happen while runs hold at most BH_FAR rows
+                return tp_set_err(ctx, TP_E_STATE, "internal: learned window of %lld rows above %lld",
+                                  (long long)(w1 - w0), (long long)ctx->far_xcap);
             k_far_feat<<<lblocks, FL_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_X, w0, w1, ctx->run_key_s,
                                                                 ctx->run_ord_s);
             TP_TRY(tp_launch_mlp_tc(ctx, A.wb, A.mbias, ctx->far_X, w1 - w0, ctx->far_kf, 0));

@@ -192,6 +192,8 @@ struct tp_ctx {
     int64_t *run_key = nullptr, *run_key_s = nullptr;
     int32_t *run_ord = nullptr, *run_ord_s = nullptr;
     int64_t learned_window = TP_LEARNED_WINDOW;  // listed far rows per window of the learned passes
+    int64_t* win_bnd = nullptr;  // first row of each window of the learned passes (a run's first row)
+    int64_t win_bnd_cap = 0;
     // Barnes-Hut near field: (first member, count) of every near cluster whose
     // vertex box is apart from the target leaf's, in runs of one leaf
     int2* near_list = nullptr;
