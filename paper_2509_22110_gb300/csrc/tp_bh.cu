@@ -1164,6 +1164,7 @@ BHArgs make_bh_args(tp_ctx* ctx, double theta, int edge_only) {
 }  // namespace
 
 tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
+    TP_TRY(tp_ensure_sorted(ctx));
     tp_tree& t = ctx->tree;
     if (t.leaf_size > 32) return tp_set_err(ctx, TP_E_ARG, "leaf_size above 32");
     unsigned long long* counts = reinterpret_cast<unsigned long long*>(ctx->scalar + 2);
@@ -1365,6 +1366,7 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
 
 tp_status tp_launch_bh_sample(tp_ctx* ctx, double theta, uint32_t keep_u, uint64_t seed, int2* out, int64_t cap,
                               int32_t* counter) {
+    TP_TRY(tp_ensure_sorted(ctx));
     tp_tree& t = ctx->tree;
     BHArgs A = make_bh_args(ctx, theta, 0);
     A.keep_u = keep_u;

@@ -387,11 +387,13 @@ tp_status tp_mesh_upload(tp_ctx* ctx, const void* V, int64_t nv, int v_dtype, co
             TP_TRY(tp_build_v2t(ctx));
             TP_TRY(tp_launch_morton_order(ctx, 30));
         }
-        TP_TRY(tp_launch_sorted_soa(ctx));
         if (posonly) {
-            // the direct kernels' item lists are refreshed when a direct evaluation needs them
+            // the Morton-order records and the direct kernels' item lists are
+            // refreshed when a kernel needs them (a tree build redoes both)
+            ctx->soa_stale = true;
             if (ctx->flags_stale < 1) ctx->flags_stale = 1;
         } else {
+            TP_TRY(tp_launch_sorted_soa(ctx));
             TP_TRY(tp_launch_flagged(ctx, true));
             ctx->flags_stale = 0;
         }

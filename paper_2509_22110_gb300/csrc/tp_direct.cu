@@ -1229,6 +1229,7 @@ tp_status tp_launch_conf_tri(tp_ctx* ctx) {
 // Confinement accumulators of the evolving mesh's triangles (library order)
 // into ctx->acc; the pair launch is bracketed by ev[0] / ev[1].
 tp_status tp_launch_conf(tp_ctx* ctx, const tp_params* prm) {
+    TP_TRY(tp_ensure_sorted(ctx));
     TP_CU(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * TP_NACC * ctx->ntp, ctx->stream));
     if (prm->prec == TP_F64) {
         cudaEventRecord(ctx->ev[0], ctx->stream);

@@ -157,6 +157,7 @@ struct tp_ctx {
     // the item lists above are refreshed on the next direct evaluation: 1 after a
     // positions-only upload (classification), 2 after a tree build re-sorted the
     // triangles (also the vertex-sharing blocks and exclusion bits)
+    bool soa_stale = false;  // soa/src/Fs lag the positions (positions-only upload since the last refresh)
     int flags_stale = 0;
     int64_t n_precise = 0;
     int64_t n_fast = 0;
@@ -236,6 +237,8 @@ tp_status tp_launch_morton_order(tp_ctx* ctx, int morton_bits);
 tp_status tp_launch_sorted_soa(tp_ctx* ctx);
 tp_status tp_launch_flagged(tp_ctx* ctx, bool topology);
 tp_status tp_ensure_flagged(tp_ctx* ctx);
+// refreshes soa/src/Fs after a positions-only upload, when a kernel first needs them
+tp_status tp_ensure_sorted(tp_ctx* ctx);
 tp_status tp_launch_fields(tp_ctx* ctx, const tp_params* prm, double* fw, double* fnu, double* fx);
 tp_status tp_launch_conf_tri(tp_ctx* ctx);
 tp_status tp_launch_expand_faces(tp_ctx* ctx);
@@ -260,6 +263,29 @@ __device__ __forceinline__ bool tp_node_reachable(const int32_t* __restrict__ pa
                                                   const int32_t* __restrict__ last, int64_t v, int leaf_size) {
     const int32_t p = parent[v];
     return p < 0 || last[p] - first[p] + 1 > leaf_size;
+}
+
+// Per-node passes cover TP_NODE_BLK consecutive nodes per block and first
+// gather the reachable ones (under a tenth at leaf size 16) into shared
+// memory, so that their FP64 work runs on dense lanes rather than on a few
+// lanes of every warp.
+constexpr int TP_NODE_THREADS = 256;
+constexpr int TP_NODE_BLK = 1024;
+
+// Compacts the reachable nodes of [v0, v0 + TP_NODE_BLK) into list (order
+// unspecified) and returns their count; every thread of the block calls it.
+__device__ __forceinline__ int tp_reachable_list(const int32_t* __restrict__ parent,
+                                                 const int32_t* __restrict__ first,
+                                                 const int32_t* __restrict__ last, int leaf_size, int64_t v0,
+                                                 int64_t nn, int32_t* list, int* cnt) {
+    if (threadIdx.x == 0) *cnt = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < TP_NODE_BLK; j += blockDim.x) {
+        const int64_t v = v0 + j;
+        if (v < nn && tp_node_reachable(parent, first, last, v, leaf_size)) list[atomicAdd(cnt, 1)] = (int32_t)v;
+    }
+    __syncthreads();
+    return *cnt;
 }
 
 tp_status tp_launch_adjoint(tp_ctx* ctx, const tp_params* prm, void* grad, int g_dtype);

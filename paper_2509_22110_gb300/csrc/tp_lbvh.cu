@@ -275,26 +275,30 @@ __global__ void __launch_bounds__(MOM_B) k_moments(
 }
 
 // far-field and admissibility records of every node the traversal can reach
-// (one thread per node)
-__global__ void k_node_out(const double* __restrict__ mom, const double* __restrict__ box,
-                           const int32_t* __restrict__ parent, const int32_t* __restrict__ first,
-                           const int32_t* __restrict__ last, int leaf_size, const double* __restrict__ center,
-                           int64_t nn, float* __restrict__ nodef, double* __restrict__ adm64,
-                           float* __restrict__ adm32) {
-    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (v >= nn || !tp_node_reachable(parent, first, last, v, leaf_size)) return;
-    double m[13], b[6];
-#pragma unroll
-    for (int c = 0; c < 13; ++c) m[c] = mom[13 * v + c];
-    const double2* bi = reinterpret_cast<const double2*>(box + 6 * v);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const double2 x = bi[c];
-        b[2 * c] = x.x;
-        b[2 * c + 1] = x.y;
-    }
+__global__ void __launch_bounds__(TP_NODE_THREADS) k_node_out(
+    const double* __restrict__ mom, const double* __restrict__ box, const int32_t* __restrict__ parent,
+    const int32_t* __restrict__ first, const int32_t* __restrict__ last, int leaf_size,
+    const double* __restrict__ center, int64_t nn, float* __restrict__ nodef, double* __restrict__ adm64,
+    float* __restrict__ adm32) {
+    __shared__ int32_t list[TP_NODE_BLK];
+    __shared__ int cnt;
+    const int n = tp_reachable_list(parent, first, last, leaf_size, blockIdx.x * (int64_t)TP_NODE_BLK, nn, list,
+                                    &cnt);
     const double c3[3] = {center[0], center[1], center[2]};
-    node_records(v, m, b, c3, nodef, adm64, adm32);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int64_t v = list[i];
+        double m[13], b[6];
+#pragma unroll
+        for (int c = 0; c < 13; ++c) m[c] = mom[13 * v + c];
+        const double2* bi = reinterpret_cast<const double2*>(box + 6 * v);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double2 x = bi[c];
+            b[2 * c] = x.x;
+            b[2 * c + 1] = x.y;
+        }
+        node_records(v, m, b, c3, nodef, adm64, adm32);
+    }
 }
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -377,8 +381,8 @@ tp_status tp_launch_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits) {
                                                          t.left, t.right, t.parent, t.first, t.last, n, t.counter,
                                                          t.mom, t.box);
     ++ctx->nlaunch;
-    k_node_out<<<nblk(nn, 256), 256, 0, ctx->stream>>>(t.mom, t.box, t.parent, t.first, t.last, leaf_size,
-                                                       ctx->center, nn, t.nodef, t.adm64, t.adm32);
+    k_node_out<<<nblk(nn, TP_NODE_BLK), TP_NODE_THREADS, 0, ctx->stream>>>(
+        t.mom, t.box, t.parent, t.first, t.last, leaf_size, ctx->center, nn, t.nodef, t.adm64, t.adm32);
     ++ctx->nlaunch;
     t.feat_stale = true;  // the network's node features are computed when the learned form needs them
     int32_t h = 0;

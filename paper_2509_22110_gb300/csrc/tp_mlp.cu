@@ -60,25 +60,33 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 
 // FP32 feature record of every node the traversal can reach: A, X[3],
 // nubar[3], M2/A (6), diag
-__global__ void k_node_feat(const double* __restrict__ mom, const double* __restrict__ box,
-                            const int32_t* __restrict__ parent, const int32_t* __restrict__ first,
-                            const int32_t* __restrict__ last, int leaf_size, int64_t nn, float* __restrict__ rec) {
-    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (v >= nn || !tp_node_reachable(parent, first, last, v, leaf_size)) return;
-    const double* m = mom + 13 * v;
-    const double* b = box + 6 * v;
-    float* r = rec + FEAT_REC * v;
-    const double A = m[0];
-    r[0] = (float)A;
-    for (int a = 0; a < 3; ++a) {
-        r[1 + a] = (float)(m[1 + a] / A);
-        r[4 + a] = (float)(m[4 + a] / A);
+__global__ void __launch_bounds__(TP_NODE_THREADS) k_node_feat(const double* __restrict__ mom,
+                                                               const double* __restrict__ box,
+                                                               const int32_t* __restrict__ parent,
+                                                               const int32_t* __restrict__ first,
+                                                               const int32_t* __restrict__ last, int leaf_size,
+                                                               int64_t nn, float* __restrict__ rec) {
+    __shared__ int32_t list[TP_NODE_BLK];
+    __shared__ int cnt;
+    const int n = tp_reachable_list(parent, first, last, leaf_size, blockIdx.x * (int64_t)TP_NODE_BLK, nn, list,
+                                    &cnt);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int64_t v = list[i];
+        const double* m = mom + 13 * v;
+        const double* b = box + 6 * v;
+        float* r = rec + FEAT_REC * v;
+        const double A = m[0];
+        r[0] = (float)A;
+        for (int a = 0; a < 3; ++a) {
+            r[1 + a] = (float)(m[1 + a] / A);
+            r[4 + a] = (float)(m[4 + a] / A);
+        }
+        for (int c = 0; c < 6; ++c) r[7 + c] = (float)(m[7 + c] / A);
+        double d2 = 0.0;
+        for (int a = 0; a < 3; ++a) d2 += (b[3 + a] - b[a]) * (b[3 + a] - b[a]);
+        r[13] = (float)sqrt(d2);
+        r[14] = r[15] = 0.f;
     }
-    for (int c = 0; c < 6; ++c) r[7 + c] = (float)(m[7 + c] / A);
-    double d2 = 0.0;
-    for (int a = 0; a < 3; ++a) d2 += (b[3 + a] - b[a]) * (b[3 + a] - b[a]);
-    r[13] = (float)sqrt(d2);
-    r[14] = r[15] = 0.f;
 }
 
 // Features and labels of sampled (leaf, cluster) pairs; one block per pair.
@@ -632,8 +640,8 @@ void tp_mlp_release(tp_ctx* ctx) {
 tp_status tp_mlp_node_features(tp_ctx* ctx) {
     tp_tree& t = ctx->tree;
     const int64_t nn = 2 * ctx->nt - 1;
-    k_node_feat<<<(unsigned)((nn + 255) / 256), 256, 0, ctx->stream>>>(t.mom, t.box, t.parent, t.first, t.last,
-                                                                      t.leaf_size, nn, t.nodeft);
+    k_node_feat<<<(unsigned)((nn + TP_NODE_BLK - 1) / TP_NODE_BLK), TP_NODE_THREADS, 0, ctx->stream>>>(
+        t.mom, t.box, t.parent, t.first, t.last, t.leaf_size, nn, t.nodeft);
     ++ctx->nlaunch;
     TP_CU(cudaGetLastError());
     return TP_OK;

@@ -405,7 +405,12 @@ tp_status tp_launch_sorted_soa(tp_ctx* ctx) {
         ctx->src, ctx->Fs);
     ++ctx->nlaunch;
     TP_CU(cudaGetLastError());
+    ctx->soa_stale = false;
     return TP_OK;
+}
+
+tp_status tp_ensure_sorted(tp_ctx* ctx) {
+    return ctx->soa_stale ? tp_launch_sorted_soa(ctx) : TP_OK;
 }
 
 tp_status tp_build_v2t(tp_ctx* ctx) {
@@ -649,6 +654,7 @@ tp_status tp_launch_flagged(tp_ctx* ctx, bool topology) {
 }
 
 tp_status tp_ensure_flagged(tp_ctx* ctx) {
+    TP_TRY(tp_ensure_sorted(ctx));
     if (ctx->flags_stale == 0) return TP_OK;
     TP_TRY(tp_launch_flagged(ctx, ctx->flags_stale >= 2));
     ctx->flags_stale = 0;
