@@ -620,6 +620,26 @@ __device__ __forceinline__ bool grad_item(const DirectArgs& A, ChunkPipe& pipe, 
                                          vprev, wacc + s * TP_NACC, lane);
                 if ((s & 30) == 30) fold_energy<NP>(at, e64);
             }
+            } else if constexpr (PF == 1 && KIND == K_MASKED) {
+            // Unmasked blocks of masked items, with a branch-free loop body: the
+            // first step reduces zeros into source 0's slots (overwritten by source
+            // 0's own sums one step later, same lanes, program order), and the last
+            // prefetch re-reads record TP_CHUNK - 1.  In the masked kernel this
+            // form compiles without spills (161 registers against 168 and a spilled
+            // stack frame) and takes about 0.25 ms less per evaluation at 327,680
+            // triangles; in the precise/fast kernel the guarded form below is
+            // faster (89.5 against 90.1 ms).
+            load_src<LOU>(cb, ra);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) vprev[k] = 0.f;
+#pragma unroll 1
+            for (int s = 0; s < TP_CHUNK; s += 2) {
+                src_step<Q, KU, NP>(tp, at, ra, rb, cb + (s + 1) * TP_SRCW, true, true, vprev,
+                                      wacc + (s > 0 ? s - 1 : 0) * TP_NACC, lane);
+                src_step<Q, KU, NP>(tp, at, rb, ra, cb + min(s + 2, TP_CHUNK - 1) * TP_SRCW, true, true, vprev,
+                                      wacc + s * TP_NACC, lane);
+                if ((s & 30) == 30) fold_energy<NP>(at, e64);
+            }
             } else if constexpr (PF == 1) {
             load_src<LOU>(cb, ra);
 #pragma unroll 1
