@@ -778,7 +778,25 @@ __device__ __forceinline__ bool energy_item(const DirectArgs& A, ChunkPipe& pipe
         if (!pipe.acquire(A, J, c, cb)) return false;
         const int64_t sbase = (int64_t)J * TP_SUPER + (int64_t)c * TP_CHUNK;
         const bool skip = (KIND == K_MASKED) && (I == J) && (c < warp);
-        if (!skip) {
+        // As in the gradient kernel, only the diagonal block and the 128 x 128
+        // blocks that hold a vertex-sharing pair take the per-pair test; the
+        // other blocks of a masked item run the unmasked arithmetic.
+        bool masked = KIND == K_MASKED && !skip;
+        if (KIND == K_MASKED && !skip && !(I == J && c == warp)) {
+            const int blk = warp * TP_NBLK + c;
+            const unsigned wd = __ldg(&A.bmask[((int64_t)I * A.nsup + J) * TP_BMASK_WORDS + (blk >> 5)]);
+            masked = (wd >> (blk & 31)) & 1u;
+        }
+        if (KIND == K_MASKED && !skip && !masked) {
+            const float2 one = make_float2(1.f, 1.f);
+#pragma unroll 2
+            for (int s = 0; s < TP_CHUNK; ++s) {
+                SrcRec sr;
+                load_src<true>(cb + s * TP_SRCW, sr);
+#pragma unroll
+                for (int P = 0; P < 2; ++P) ea[P] = add2(ea[P], pair_energy<Q, K_PRECISE>(tp[P], sr, one));
+            }
+        } else if (!skip) {
 #pragma unroll 2
             for (int s = 0; s < TP_CHUNK; ++s) {
                 SrcRec sr;
