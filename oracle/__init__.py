@@ -53,6 +53,8 @@ def _load():
     lib.or_tri_data.argtypes = [_d, _i32, i64, _d, _d, _d]
     lib.or_energy.argtypes = [_d, _d, _d, _i32, i64, dbl, dbl, dbl, i32, i32]
     lib.or_energy.restype = dbl
+    lib.or_admitted_pairs.argtypes = [_i32, i64, i32, i32]
+    lib.or_admitted_pairs.restype = i64
     lib.or_energy_touching.argtypes = [_d, _d, _d, _i32, i64, _u8, dbl, dbl, dbl, i32, i32]
     lib.or_energy_touching.restype = dbl
     lib.or_tri_accum.argtypes = [_d, _d, _d, _i32, i64, C.c_void_p, i64, dbl, dbl, i32, _d, _d, _d, i32]
@@ -124,6 +126,13 @@ def energy(V, F, q=6.0, p=12.0, c=1.0, adj=0, nthreads=None):
     """Phi = c * sum over admitted ordered pairs (Eq. TP, one centroid point per triangle)."""
     x, nu, w = tri_data(V, F)
     return energy_soa(x, nu, w, F, q, p, c, adj, nthreads)
+
+
+def admitted_pairs(F, adj=0, nthreads=None):
+    """Ordered pairs (T, S), T != S, that the sum of Eq. TP keeps (brute force over all nt^2 pairs)."""
+    lib = _load()
+    F = np.ascontiguousarray(F, dtype=np.int32)
+    return int(lib.or_admitted_pairs(F, F.shape[0], adj, nthreads or nthreads_default()))
 
 
 def energy_touching(V, F, tris, q=6.0, p=12.0, c=1.0, adj=0, nthreads=None):

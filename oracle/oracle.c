@@ -116,6 +116,21 @@ double or_energy(const double* x, const double* nu, const double* w, const int32
     return c * E;
 }
 
+/* Number of ordered pairs (T, S) the double sum of or_energy runs over: every
+ * T != S that the exclusion rule (adj) keeps.  Brute force over all nt^2
+ * ordered pairs with the same test as the energy. */
+int64_t or_admitted_pairs(const int32_t* F, int64_t nt, int adj, int nthreads) {
+    int64_t total = 0;
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads) reduction(+ : total)
+    for (int64_t T = 0; T < nt; ++T) {
+        int64_t k = 0;
+        for (int64_t S = 0; S < nt; ++S) k += excluded(F, T, S, adj) ? 0 : 1;
+        total += k;
+    }
+    return total;
+}
+
 /* Energy of the ordered pairs (T,S) with T or S in the set: the part of Phi
  * that changes when only vertices of triangles in the set move. */
 double or_energy_touching(const double* x, const double* nu, const double* w, const int32_t* F, int64_t nt,

@@ -31,6 +31,8 @@ void or_tri_data(const double* V, const int32_t* F, int64_t nt, double* x, doubl
 double or_energy(const double* x, const double* nu, const double* w, const int32_t* F, int64_t nt,
                  double q, double p, double c, int adj, int nthreads);
 
+int64_t or_admitted_pairs(const int32_t* F, int64_t nt, int adj, int nthreads);
+
 double or_energy_touching(const double* x, const double* nu, const double* w, const int32_t* F, int64_t nt,
                           const uint8_t* in_set, double q, double p, double c, int adj, int nthreads);
 

@@ -158,3 +158,81 @@ def test_bh_no_excluded_pair_is_far(oracle_mod):
                 bs = box[t["n"] - 1 + np.where(t["perm"] == S)[0][0]]
                 overlap = all(bt[a] <= bs[3 + a] and bs[a] <= bt[3 + a] for a in range(3))
                 assert overlap
+
+
+def _bh_target_energy(xT, nuT, wT, T, near, far, x, nu, w, mom, q=6, p=12):
+    """The Barnes-Hut energy seen by target T as a function of its own (x, nu, w): exact
+    pairs (both orderings) with its near triangles plus, for every admissible cluster C,
+    the monopole of both orderings with C's moments held fixed (only the inner integral
+    is clustered, Sec. 3.2; area-weighted centroid and unnormalised area-averaged normal).
+    Analytic in xT, nuT for even q, so complex steps give its exact derivatives."""
+    f = 0
+    if len(near):
+        d = xT[None, :] - x[near]
+        r2 = np.sum(d * d, axis=1)
+        a = d @ nuT
+        b = np.sum(nu[near] * d, axis=1)
+        f = f + wT * np.sum(w[near] * (a**q + b**q) / r2 ** (p // 2))
+    for C in far:
+        A = mom[C, 0]
+        X = mom[C, 1:4] / A
+        nb = mom[C, 4:7] / A
+        d = xT - X
+        r2 = np.sum(d * d)
+        f = f + wT * A * ((d @ nuT) ** q + (nb @ (-d)) ** q) / r2 ** (p // 2)
+    return f
+
+
+def test_bh_far_term_complex_step(oracle_mod):
+    """Every target's Barnes-Hut derivatives dPhi/dw, dPhi/dnu, dPhi/dx (or_bh_accum) equal
+    the complex-step derivatives of the target's energy written above, with the near/far
+    split found by a traversal written here from the admissibility rule (vertex boxes
+    strictly apart on some axis and diag_C < theta (|X_C - c_L| - diag_L / 2))."""
+    V, F = meshgen.sh_deformed_sphere(3, 12, 0.05, 2)
+    x, nu, w = oracle_mod.tri_data(V, F)
+    leaf = 4
+    t = oracle_mod.lbvh(x, 30, leaf)
+    mom, box = oracle_mod.moments(V, F, t, soa=(x, nu, w))
+    theta = 0.5
+    gw, gnu, gx, nn, nf = oracle_mod.bh_accum(V, F, t, mom, box, theta, soa=(x, nu, w))
+    n = t["n"]
+    left, right, first, last, perm = t["left"], t["right"], t["first"], t["last"], t["perm"]
+    sets = [set(int(v) for v in f) for f in F]
+    rng = np.random.default_rng(5)
+    far_total = near_total = 0
+    leaves = list(t["leaves"])
+    checked = 0
+    for L in rng.choice(leaves, 24, replace=False):
+        bl = box[L]
+        cl = 0.5 * (bl[:3] + bl[3:])
+        dl = np.linalg.norm(bl[3:] - bl[:3])
+        near, far = [], []
+        stack = [0]
+        while stack:
+            C = stack.pop()
+            bc = box[C]
+            apart = any(bl[3 + a] < bc[a] or bc[3 + a] < bl[a] for a in range(3))
+            X = mom[C, 1:4] / mom[C, 0]
+            if apart and np.linalg.norm(bc[3:] - bc[:3]) < theta * (np.linalg.norm(X - cl) - 0.5 * dl):
+                far.append(C)
+            elif last[C] - first[C] + 1 <= leaf:
+                near.extend(int(perm[m]) for m in range(first[C], last[C] + 1))
+            else:
+                stack += [right[C], left[C]]
+        for k in range(first[L], last[L] + 1):
+            T = int(perm[k])
+            nearT = np.array([S for S in near if S != T and not (sets[T] & sets[S])], dtype=np.int64)
+            far_total += len(far)
+            near_total += len(nearT)
+            h = 1e-30
+            f0 = _bh_target_energy(x[T], nu[T], w[T], T, nearT, far, x, nu, w, mom)
+            assert abs(gw[T] - f0 / w[T]) <= 1e-12 * abs(gw[T])
+            for a in range(3):
+                e = np.zeros(3, dtype=complex)
+                e[a] = 1j * h
+                dx = _bh_target_energy(x[T] + e, nu[T], w[T], T, nearT, far, x, nu, w, mom).imag / h
+                dn = _bh_target_energy(x[T], nu[T] + e, w[T], T, nearT, far, x, nu, w, mom).imag / h
+                assert abs(gx[T, a] - dx) <= 1e-11 * np.abs(gx[T]).max(), (T, a, gx[T, a], dx)
+                assert abs(gnu[T, a] - dn) <= 1e-11 * np.abs(gnu[T]).max(), (T, a, gnu[T, a], dn)
+            checked += 1
+    assert checked > 50 and far_total > 10 * checked and near_total > 0
