@@ -46,8 +46,8 @@ typedef enum {
     TP_E_NONFINITE = 4, /* degenerate triangle, non-finite vertex or coincident admitted
                            centroids: the energy is +inf (finite only if embedded,
                            Sec. 2.2.2)                                                   */
-    TP_E_TIMEOUT = 5,   /* a device-side bounded wait gave up                            */
-    TP_E_OOM = 6,       /* device allocation failed                                      */
+    TP_E_TIMEOUT = 5,   /* a device-side bounded wait gave up (1 s)                      */
+    TP_E_OOM = 6,       /* device allocation failed (the mesh must be uploaded again)    */
     TP_E_MODEL = 7      /* malformed far-field model file                                */
 } tp_status;
 
@@ -268,16 +268,23 @@ tp_status tp_debug_tree(tp_ctx* ctx, uint32_t* codes, int32_t* perm, int32_t* le
  * FP64 accumulation).
  *   V [nv][3] f64, F [nt][3] i32: device inputs on the current device.
  *   energy_out (1 f64) and grad_out ([nv][3] f64): device outputs, caller-owned.
- *   params: q/p as tp_gradient, mode must be TP_DIRECT; scale and
+ *   params: q/p as tp_gradient, mode must be TP_DIRECT and prec
+ *   TP_F32_F64ACC (other modes and precisions give TP_E_ARG); scale and
  *   TP_EXCLUDE_EDGE are honoured.  cuda_stream orders the work; the call
  *   does not synchronise.  errbuf (may be NULL) receives a message on failure.
  * All scratch is one fixed __device__ array sized for at most 65536
  * triangles (about 7 MB, kept by every GPU that loads the library until the
  * process exits); larger meshes give TP_E_ARG.  The first call on a device
- * looks up that array's address and should be made before any stream
- * capture.  Calls share the array: calls that overlap on the GPU race.
- * Non-finite results (coincident admitted centroids) show as inf/NaN in the
- * outputs instead of a status. */
+ * looks up that array's address (cudaGetSymbolAddress) and keeps it for the
+ * life of the process; make that first call before any stream capture.  The
+ * kept address assumes the device's primary context is never reset
+ * (cudaDeviceReset) and that callers use the primary context.  Calls share
+ * the array: calls that overlap on the GPU race.
+ * The inputs are not validated on the device, since the call does not
+ * synchronise: a face index outside [0, nv) (the triangle is skipped by the
+ * pull-back and its data set to NaN), a degenerate (zero-area) triangle and
+ * coincident admitted centroids all show as NaN or inf in energy_out and
+ * grad_out, with status TP_OK. */
 tp_status tp_gradient_direct_noalloc(const double* V, int64_t nv, const int32_t* F, int64_t nt,
                                      const tp_params* params, double* energy_out, double* grad_out,
                                      void* cuda_stream, char* errbuf, int64_t errbuf_len);
@@ -288,6 +295,29 @@ tp_status tp_gradient_direct_noalloc(const double* V, int64_t nv, const int32_t*
  * read-back of the learned far field's network kernel.  Synchronises the
  * device.  TP_E_ARG on bad sizes.  For tests. */
 tp_status tp_debug_tc_gemm(int device, const uint16_t* A, int K, const uint16_t* B, int N, float* D);
+
+/* Failure paths, for tests (no GPU fault is involved in either):
+ * tp_debug_wait_timeout launches one block that arms an mbarrier for bytes no
+ * copy delivers and waits on it with the pair kernels' bounded wait, limited
+ * to limit_ms (0 < limit_ms <= 1000); the wait gives up, the kernel sets the
+ * device error word and returns, and the call reports TP_E_TIMEOUT (the
+ * context stays usable).  tp_debug_fail_alloc makes the allocation after
+ * `after` more successful ones fail once as if the device were out of memory
+ * (after < 0 disarms it).  Any TP_E_OOM, simulated or real, releases the
+ * mesh, tree, pair lists and confining surface of the context (the model,
+ * stream and settings stay): upload the mesh again to continue. */
+tp_status tp_debug_wait_timeout(tp_ctx* ctx, double limit_ms);
+tp_status tp_debug_fail_alloc(tp_ctx* ctx, int64_t after);
+
+/* The cluster-tree build's own stable key sort and compaction on a host
+ * array, for tests: keys[n] are sorted by their low `bits` bits (1..32) with
+ * ties in input order; keys_out receives the sorted keys and perm_out the
+ * input position of each.  With compact_out and ncompact not NULL, the keys
+ * read as int32 are also compacted: the entries >= 0, in order, to
+ * compact_out (capacity n) and their number to *ncompact.  Host buffers;
+ * synchronises the context stream; allocates and frees its own buffers. */
+tp_status tp_debug_sort(tp_ctx* ctx, const uint32_t* keys, int64_t n, int bits, uint32_t* keys_out,
+                        int32_t* perm_out, int32_t* compact_out, int32_t* ncompact);
 
 /* Library version string. */
 const char* tp_version(void);

@@ -7,9 +7,12 @@ exact vertex gradient, evaluated by hand-written CUDA kernels behind the C ABI
 of ``include/tp.h``.
 
 ``_tp`` is the ctypes binding (same names as the C entry points);
-:class:`TPEnergy` is the ``torch.autograd.Function`` whose backward calls
-``tp_gradient`` (which recomputes the pair geometry; nothing per pair is
-stored); :class:`TangentPointEnergy` owns a context for one mesh topology.
+:class:`TPEnergy` is the ``torch.autograd.Function``: when the positions
+require a gradient its forward makes one ``tp_gradient`` call (energy and
+vertex gradient from a single pass over the pairs, which recomputes the pair
+geometry; nothing per pair is stored) and keeps the [nv, 3] gradient for the
+backward, which only scales it; otherwise the forward calls ``tp_energy``.
+:class:`TangentPointEnergy` owns a context for one mesh topology.
 ``meshgen`` builds the seeded synthetic meshes.
 """
 
@@ -87,6 +90,7 @@ class TangentPointEnergy:
         self.params = tp_params_default(**params)
         self._uploaded = False
         self._tree = None
+        self.calls = {"energy": 0, "gradient": 0}  # library evaluations made through this object
 
     def close(self):
         if self.ctx:
@@ -111,12 +115,14 @@ class TangentPointEnergy:
 
     def energy(self, V):
         self.upload(V)
+        self.calls["energy"] += 1
         return tp_energy(self.ctx, self.params)
 
     def gradient(self, V, out=None):
         self.upload(V)
         torch = _torch()
         g = out if out is not None else torch.empty_like(V)
+        self.calls["gradient"] += 1
         e = tp_gradient(self.ctx, g, self.params)
         return e, g
 
@@ -132,15 +138,17 @@ def _make_function():
 
         @staticmethod
         def forward(ctx, V, tpe):
-            e = tpe.energy(V)
-            ctx.tpe = tpe
-            ctx.save_for_backward(V)
+            if ctx.needs_input_grad[0]:
+                # one pass over the pairs gives both; only the vertex gradient is kept
+                e, grad = tpe.gradient(V.detach())
+                ctx.save_for_backward(grad)
+            else:
+                e = tpe.energy(V)
             return V.new_tensor(e)
 
         @staticmethod
         def backward(ctx, g):
-            (V,) = ctx.saved_tensors
-            _, grad = ctx.tpe.gradient(V)
+            (grad,) = ctx.saved_tensors
             return grad * g, None
 
     return _TPEnergy

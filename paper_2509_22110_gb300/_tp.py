@@ -115,6 +115,12 @@ def lib():
         getattr(L, n).restype = i32
     L.tp_gradient_direct_noalloc.argtypes = [vp, i64, vp, i64, C.POINTER(tp_params), vp, vp, vp, C.c_char_p, i64]
     L.tp_gradient_direct_noalloc.restype = i32
+    L.tp_debug_wait_timeout.argtypes = [vp, C.c_double]
+    L.tp_debug_wait_timeout.restype = i32
+    L.tp_debug_sort.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp]
+    L.tp_debug_sort.restype = i32
+    L.tp_debug_fail_alloc.argtypes = [vp, i64]
+    L.tp_debug_fail_alloc.restype = i32
     L.tp_debug_tc_gemm.argtypes = [i32, vp, i32, vp, i32, vp]
     L.tp_debug_tc_gemm.restype = i32
     L.tp_measure_fp32_peak.argtypes = [i32, vp, i32, i32, i32, C.POINTER(C.c_double)]
@@ -337,14 +343,54 @@ def tp_debug_tree(ctx, nt):
     return out
 
 
+def tp_debug_wait_timeout(ctx, limit_ms):
+    """Make a device-side bounded wait run out (raises TPError with TP_E_TIMEOUT)."""
+    _check(ctx, lib().tp_debug_wait_timeout(ctx, float(limit_ms)))
+
+
+def tp_debug_sort(ctx, keys, bits=32, compact=False):
+    """Stable sort of uint32 keys by their low ``bits`` bits with the library's own kernels:
+    (sorted keys, input positions) and, with ``compact``, the entries >= 0 of the keys
+    read as int32, in order."""
+    k = np.ascontiguousarray(keys, dtype=np.uint32)
+    n = k.shape[0]
+    ko = np.zeros(n, dtype=np.uint32)
+    po = np.zeros(n, dtype=np.int32)
+    co = np.zeros(max(n, 1), dtype=np.int32)
+    nc = C.c_int32(0)
+    _check(ctx, lib().tp_debug_sort(ctx, k.ctypes.data, n, bits, ko.ctypes.data, po.ctypes.data,
+                                    co.ctypes.data if compact else None, C.byref(nc) if compact else None))
+    return (ko, po, co[: nc.value]) if compact else (ko, po)
+
+
+def tp_debug_fail_alloc(ctx, after):
+    """Fail the allocation after ``after`` more successful ones (negative: disarm)."""
+    _check(ctx, lib().tp_debug_fail_alloc(ctx, int(after)))
+
+
 def tp_gradient_direct_noalloc(V, F, energy_out, grad_out, params=None, stream=None):
     """Allocation-free direct energy + gradient: V [nv,3] f64, F [nt,3] int32,
     energy_out [1] f64 and grad_out [nv,3] f64, all CUDA tensors on the
     current device; ``stream`` a cudaStream_t integer (None: legacy default)."""
+    import torch
+
     p = params or tp_params_default()
+    for name, a in (("V", V), ("F", F), ("energy_out", energy_out), ("grad_out", grad_out)):
+        if not isinstance(a, torch.Tensor):
+            raise TypeError(f"{name} must be a torch tensor")
+    if V.dtype != torch.float64 or energy_out.dtype != torch.float64 or grad_out.dtype != torch.float64:
+        raise TypeError("V, energy_out and grad_out must be float64")
+    if F.dtype != torch.int32:
+        raise TypeError("F must be int32")
+    if V.dim() != 2 or V.shape[1] != 3 or F.dim() != 2 or F.shape[1] != 3:
+        raise ValueError("V must be [nv, 3] and F [nt, 3]")
+    if tuple(grad_out.shape) != tuple(V.shape) or energy_out.numel() < 1:
+        raise ValueError("grad_out must have V's shape and energy_out at least one element")
     for a in (V, F, energy_out, grad_out):
-        if not (hasattr(a, "is_cuda") and a.is_cuda and a.is_contiguous()):
+        if not (a.is_cuda and a.is_contiguous()):
             raise ValueError("all arguments must be contiguous CUDA tensors")
+        if a.device.index != torch.cuda.current_device():
+            raise ValueError("all arguments must be on the current CUDA device")
     buf = C.create_string_buffer(256)
     st = lib().tp_gradient_direct_noalloc(V.data_ptr(), V.shape[0], F.data_ptr(), F.shape[0], C.byref(p),
                                           energy_out.data_ptr(), grad_out.data_ptr(), C.c_void_p(stream or 0),

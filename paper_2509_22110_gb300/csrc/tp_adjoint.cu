@@ -146,6 +146,7 @@ __global__ void k_sum_final(const double* __restrict__ part, int nb, double mul,
 }  // namespace
 
 tp_status tp_launch_adjoint(tp_ctx* ctx, const tp_params* prm, void* grad, int g_dtype) {
+    TpRange nvtx_range("tp_launch_adjoint");
     const int64_t nv = ctx->nv, nt = ctx->nt;
     const double q = prm->q, pq = (double)prm->p / prm->q;
     if (nt > 0) {
@@ -167,6 +168,7 @@ tp_status tp_launch_adjoint(tp_ctx* ctx, const tp_params* prm, void* grad, int g
 }
 
 tp_status tp_launch_fields(tp_ctx* ctx, const tp_params* prm, double* fw, double* fnu, double* fx) {
+    TpRange nvtx_range("tp_launch_fields");
     const int64_t nt = ctx->nt;
     const double q = prm->q, pq = (double)prm->p / prm->q;
     k_fields<<<(unsigned)((nt + 255) / 256), 256, 0, ctx->stream>>>(ctx->iperm, ctx->nu64, ctx->w64, ctx->acc, nt,

@@ -42,7 +42,6 @@
 #include <stdint.h>
 #include <string.h>
 
-#include <cub/cub.cuh>
 
 #include "tp_internal.cuh"
 #include "tp_mlp_dev.cuh"
@@ -178,20 +177,26 @@ __device__ __forceinline__ void pair_core(const float2 (&th)[3], const float2 (&
     const float2 al = bh_mul2(a, inv), be = bh_mul2(b, inv);
     const float2 al2 = bh_mul2(al, al), be2 = bh_mul2(be, be);
     const float2 al4 = bh_mul2(al2, al2), be4 = bh_mul2(be2, be2);
-    float2 s6, al5, be5;
+    float2 al5, be5;
     if (Q == 6) {
-        s6 = bh_fma2(be4, be2, bh_mul2(al4, al2));
         al5 = bh_mul2(al4, al);
         be5 = bh_mul2(be4, be);
     } else {
-        s6 = bh_fma2(be4, be4, bh_mul2(al4, al4));
         al5 = bh_mul2(bh_mul2(al4, al2), al);
         be5 = bh_mul2(bh_mul2(be4, be2), be);
     }
     const float2 wi = bh_mul2(wts, inv);
     const float2 A5 = bh_mul2(wi, al5), B5 = bh_mul2(wi, be5);
+#if TP_PAIR_T
+    // wi s6 = A5 al + B5 be, and the pair energy wts s6 = (wi s6) |d|^2
+    const float2 ws6 = bh_fma2(A5, al, bh_mul2(B5, be));
+    const float2 nk = bh_mul2(ws6, bh_f2(-2.0f));  // -(p/q) wts inv s6, p = 2q
+    acc[0] = bh_fma2(ws6, r2, acc[0]);
+#else
+    const float2 s6 = Q == 6 ? bh_fma2(be4, be2, bh_mul2(al4, al2)) : bh_fma2(be4, be4, bh_mul2(al4, al4));
     const float2 nk = bh_mul2(bh_mul2(wi, s6), bh_f2(-2.0f));  // -(p/q) wts inv s6, p = 2q
     acc[0] = bh_fma2(wts, s6, acc[0]);
+#endif
     acc[1] = bh_add2(acc[1], A5);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -1164,6 +1169,7 @@ BHArgs make_bh_args(tp_ctx* ctx, double theta, int edge_only) {
 }  // namespace
 
 tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
+    TpRange nvtx_range("tp_launch_bh");
     TP_TRY(tp_ensure_sorted(ctx));
     tp_tree& t = ctx->tree;
     if (t.leaf_size > 32) return tp_set_err(ctx, TP_E_ARG, "leaf_size above 32");
@@ -1299,18 +1305,9 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
             ++ctx->nlaunch;
             int end_bit = 1;
             while (end_bit < 63 && ((int64_t)1 << end_bit) <= listed_rows) ++end_bit;
-            size_t need = 0;
-            TP_CU(cub::DeviceRadixSort::SortPairs(nullptr, need, ctx->run_key, ctx->run_key_s, ctx->run_ord,
-                                                  ctx->run_ord_s, (int)listed_runs, 0, end_bit, ctx->stream));
-            if (need > ctx->sort_tmp_bytes) {
-                tp_free(ctx, ctx->sort_tmp);
-                ctx->sort_tmp = nullptr;
-                TP_TRY(tp_alloc(ctx, &ctx->sort_tmp, need));
-                ctx->sort_tmp_bytes = need;
-            }
-            size_t have = ctx->sort_tmp_bytes;
-            TP_CU(cub::DeviceRadixSort::SortPairs(ctx->sort_tmp, have, ctx->run_key, ctx->run_key_s, ctx->run_ord,
-                                                  ctx->run_ord_s, (int)listed_runs, 0, end_bit, ctx->stream));
+            TP_TRY(tp_sort_pairs_u64(ctx, reinterpret_cast<const uint64_t*>(ctx->run_key), ctx->run_ord,
+                                     reinterpret_cast<uint64_t*>(ctx->run_key_s), ctx->run_ord_s, listed_runs,
+                                     end_bit));
         }
         // window boundaries on run starts (read back once when there are several windows)
         const int64_t nwin = (listed_rows + win - 1) / win;
@@ -1366,6 +1363,7 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
 
 tp_status tp_launch_bh_sample(tp_ctx* ctx, double theta, uint32_t keep_u, uint64_t seed, int2* out, int64_t cap,
                               int32_t* counter) {
+    TpRange nvtx_range("tp_launch_bh_sample");
     TP_TRY(tp_ensure_sorted(ctx));
     tp_tree& t = ctx->tree;
     BHArgs A = make_bh_args(ctx, theta, 0);

@@ -42,9 +42,19 @@ tp_status tp_cuda_check(tp_ctx* c, cudaError_t e, const char* what) {
 tp_status tp_alloc(tp_ctx* ctx, void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    if (ctx->fail_alloc_after >= 0) {
+        if (ctx->fail_alloc_after == 0) {
+            ctx->fail_alloc_after = -1;
+            tp_drop_mesh_state(ctx);
+            *p = nullptr;
+            return tp_set_err(ctx, TP_E_OOM, "allocation of %zu bytes failed (simulated by tp_debug_fail_alloc)", bytes);
+        }
+        --ctx->fail_alloc_after;
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        tp_drop_mesh_state(ctx);
         *p = nullptr;
         return tp_set_err(ctx, TP_E_OOM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
     }
@@ -103,6 +113,9 @@ tp_status check_params(tp_ctx* ctx, const tp_params* prm) {
     if (!std::isfinite(prm->scale)) return tp_set_err(ctx, TP_E_ARG, "scale is not finite");
     if (prm->mode != TP_DIRECT && !(prm->theta >= 0.0 && std::isfinite(prm->theta)))
         return tp_set_err(ctx, TP_E_ARG, "theta must be finite and >= 0");
+    if (prm->mode != TP_DIRECT && prm->prec != TP_F32_F64ACC)
+        return tp_set_err(ctx, TP_E_ARG, "the clustered forms evaluate FP32 terms with FP64 sums only (prec %d)",
+                          prm->prec);
     if (!ctx->have_mesh) return tp_set_err(ctx, TP_E_STATE, "no mesh uploaded");
     if (prm->mode != TP_DIRECT && !ctx->tree.valid && ctx->nt > 0)
         return tp_set_err(ctx, TP_E_STATE, "mode %d needs tp_tree_build first", prm->mode);
@@ -170,6 +183,43 @@ void release_mesh(tp_ctx* ctx) {
     ctx->have_mesh = false;
 }
 
+}  // namespace
+
+void tp_drop_mesh_state(tp_ctx* ctx) {
+    release_mesh(ctx);
+    free_ptr(ctx, ctx->near_list);
+    free_ptr(ctx, ctx->near_runs);
+    ctx->near_cap = ctx->nrun_cap = 0;
+    free_ptr(ctx, ctx->far_list);
+    free_ptr(ctx, ctx->far_runs);
+    free_ptr(ctx, ctx->run_key);
+    free_ptr(ctx, ctx->run_key_s);
+    free_ptr(ctx, ctx->run_ord);
+    free_ptr(ctx, ctx->run_ord_s);
+    ctx->far_cap = ctx->run_cap = 0;
+    free_ptr(ctx, ctx->far_X);
+    free_ptr(ctx, ctx->far_kf);
+    ctx->far_xcap = 0;
+    free_ptr(ctx, ctx->win_bnd);
+    ctx->win_bnd_cap = 0;
+    free_ptr(ctx, ctx->sort_hist);
+    free_ptr(ctx, ctx->sort_ktmp);
+    free_ptr(ctx, ctx->sort_vtmp);
+    ctx->sort_hist_cap = ctx->sort_kv_cap = 0;
+    free_ptr(ctx, ctx->conf_V64);
+    free_ptr(ctx, ctx->conf_F);
+    free_ptr(ctx, ctx->conf_vtmp);
+    free_ptr(ctx, ctx->conf_y64);
+    free_ptr(ctx, ctx->conf_a64);
+    free_ptr(ctx, ctx->conf_src);
+    ctx->conf_cap_nv = ctx->conf_cap_nt = 0;
+    ctx->have_conf = false;
+    ctx->have_mesh = false;
+    ctx->tree.valid = false;
+}
+
+namespace {
+
 tp_status ensure_buffers(tp_ctx* ctx, int64_t nv, int64_t nt) {
     const int64_t ntp = ((nt + TP_SUPER - 1) / TP_SUPER) * TP_SUPER;
     const int64_t nsup = ntp / TP_SUPER;
@@ -225,9 +275,9 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
     return ms;
 }
 
-int64_t n_direct_pairs(const tp_ctx* ctx) {
-    // ordered pairs: nt (nt - 1) minus the excluded ones (computed on upload)
-    return ctx->nt * (ctx->nt - 1) - ctx->n_excluded_ordered;
+int64_t n_direct_pairs(const tp_ctx* ctx, bool edge_only) {
+    // ordered pairs: nt (nt - 1) minus the excluded ones (counted on upload)
+    return ctx->nt * (ctx->nt - 1) - (edge_only ? ctx->n_excluded_edge_ordered : ctx->n_excluded_ordered);
 }
 
 }  // namespace
@@ -248,7 +298,88 @@ tp_status take_device_error(tp_ctx* ctx, const char* where) {
     return tp_set_err(ctx, TP_E_CUDA, "%s: device error 0x%x", where, h);
 }
 
+namespace {
+// Test kernel of the bounded waits: one mbarrier armed for 16 bytes that no
+// copy will deliver, waited on with mbar_wait_bounded and the given limit; on
+// expiry the device error word gets the timeout bit.  No copy is in flight
+// when the block exits.
+__global__ void k_debug_wait(uint64_t limit_ns, unsigned* derr) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_expect_tx(&bar, 16);
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0u, limit_ns);
+    if (!ok && threadIdx.x == 0) tp_dev_error(derr, TP_DERR_TIMEOUT);
+}
+}  // namespace
+
 extern "C" {
+
+tp_status tp_debug_wait_timeout(tp_ctx* ctx, double limit_ms) {
+    if (!ctx) return TP_E_ARG;
+    DeviceGuard g(ctx->device);
+    ctx->err.clear();
+    if (!(limit_ms > 0.0 && limit_ms <= 1000.0)) return tp_set_err(ctx, TP_E_ARG, "limit_ms must be in (0, 1000]");
+    k_debug_wait<<<1, 32, 0, ctx->stream>>>((uint64_t)(limit_ms * 1e6), ctx->derr);
+    TP_CU(cudaGetLastError());
+    return take_device_error(ctx, "tp_debug_wait_timeout");
+}
+
+tp_status tp_debug_sort(tp_ctx* ctx, const uint32_t* keys, int64_t n, int bits, uint32_t* keys_out,
+                        int32_t* perm_out, int32_t* compact_out, int32_t* ncompact) {
+    if (!ctx || n < 0 || (n > 0 && (!keys || !keys_out || !perm_out))) return TP_E_ARG;
+    DeviceGuard g(ctx->device);
+    ctx->err.clear();
+    if (bits < 1 || bits > 32) return tp_set_err(ctx, TP_E_ARG, "bits must be in [1, 32]");
+    if (n == 0) {
+        if (ncompact) *ncompact = 0;
+        return TP_OK;
+    }
+    uint32_t *kin = nullptr, *kout = nullptr;
+    int32_t *vin = nullptr, *vout = nullptr, *cnt = nullptr;
+    tp_status st = TP_OK;
+    auto done = [&](tp_status s) {
+        tp_free(ctx, kin);
+        tp_free(ctx, kout);
+        tp_free(ctx, vin);
+        tp_free(ctx, vout);
+        tp_free(ctx, cnt);
+        return s;
+    };
+    if ((st = tp_alloc_t(ctx, &kin, n)) != TP_OK || (st = tp_alloc_t(ctx, &kout, n)) != TP_OK ||
+        (st = tp_alloc_t(ctx, &vin, n)) != TP_OK || (st = tp_alloc_t(ctx, &vout, n)) != TP_OK ||
+        (st = tp_alloc_t(ctx, &cnt, 1)) != TP_OK)
+        return done(st);
+    std::vector<int32_t> iota((size_t)n);
+    for (int64_t i = 0; i < n; ++i) iota[(size_t)i] = (int32_t)i;
+    if (cudaMemcpyAsync(kin, keys, 4 * (size_t)n, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+        cudaMemcpyAsync(vin, iota.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+        return done(tp_cuda_check(ctx, cudaGetLastError(), "tp_debug_sort upload"));
+    if ((st = tp_sort_pairs_u32(ctx, kin, vin, kout, vout, n, bits)) != TP_OK) return done(st);
+    if (compact_out && ncompact) {
+        // compaction of the keys read as int32 (the entries >= 0 in order)
+        if ((st = tp_compact_nonneg(ctx, reinterpret_cast<const int32_t*>(kin), n, vin, cnt)) != TP_OK) return done(st);
+    }
+    cudaMemcpyAsync(keys_out, kout, 4 * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream);
+    cudaMemcpyAsync(perm_out, vout, 4 * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (compact_out && ncompact) {
+        cudaMemcpyAsync(ncompact, cnt, 4, cudaMemcpyDeviceToHost, ctx->stream);
+        cudaMemcpyAsync(compact_out, vin, 4 * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return done(tp_cuda_check(ctx, e, "tp_debug_sort"));
+    return done(TP_OK);
+}
+
+tp_status tp_debug_fail_alloc(tp_ctx* ctx, int64_t after) {
+    if (!ctx) return TP_E_ARG;
+    ctx->fail_alloc_after = after < 0 ? -1 : after;
+    return TP_OK;
+}
 
 void tp_params_default(tp_params* p) {
     if (!p) return;
@@ -287,7 +418,7 @@ tp_status tp_create(tp_ctx** out, int device, void* cuda_stream) {
     }
     ctx->num_sms = prop.multiProcessorCount;
     for (int i = 0; i < 4; ++i) cudaEventCreate(&ctx->ev[i]);
-    if (tp_alloc_t(ctx, &ctx->derr, 4) != TP_OK || tp_alloc_t(ctx, &ctx->scalar, 8) != TP_OK ||
+    if (tp_alloc_t(ctx, &ctx->derr, 4) != TP_OK || tp_alloc_t(ctx, &ctx->scalar, 10) != TP_OK ||
         tp_alloc_t(ctx, &ctx->center, 3) != TP_OK || tp_alloc_t(ctx, &ctx->bounds, 6) != TP_OK ||
         tp_alloc_t(ctx, &ctx->mcount, 16) != TP_OK || tp_alloc_t(ctx, &ctx->work, 4) != TP_OK) {
         tp_destroy(ctx);
@@ -319,6 +450,7 @@ const char* tp_last_error(const tp_ctx* ctx) { return ctx ? ctx->err.c_str() : "
 
 tp_status tp_mesh_upload(tp_ctx* ctx, const void* V, int64_t nv, int v_dtype, const int32_t* F, int64_t nt,
                          uint32_t flags) {
+    TpRange nvtx_range("tp_mesh_upload");
     if (!ctx) return TP_E_ARG;
     DeviceGuard g(ctx->device);
     ctx->err.clear();
@@ -411,6 +543,7 @@ tp_status tp_mesh_upload(tp_ctx* ctx, const void* V, int64_t nv, int v_dtype, co
 }
 
 tp_status tp_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits) {
+    TpRange nvtx_range("tp_tree_build");
     if (!ctx) return TP_E_ARG;
     DeviceGuard g(ctx->device);
     ctx->err.clear();
@@ -470,6 +603,8 @@ static tp_status run_eval(tp_ctx* ctx, const tp_params* prm, bool want_grad, voi
                 energy_from_acc = false;
                 TP_TRY(tp_launch_reduce_sum(ctx, ctx->red, nt, ctx->scalar + 1));
             }
+        } else if (prm->prec == TP_F32_KAHAN) {
+            TP_TRY(tp_launch_direct_kahan(ctx, prm));
         } else if (want_grad) {
             TP_TRY(tp_launch_direct_grad(ctx, prm));
         } else {
@@ -478,11 +613,11 @@ static tp_status run_eval(tp_ctx* ctx, const tp_params* prm, bool want_grad, voi
             TP_TRY(tp_launch_reduce_sum(ctx, ctx->red, nparts, ctx->scalar + 1));
             energy_from_acc = false;
         }
-        ctx->stats.pairs_exact = n_direct_pairs(ctx);
+        ctx->stats.pairs_exact = n_direct_pairs(ctx, (prm->flags & TP_EXCLUDE_EDGE) != 0);
         ctx->stats.tile_pairs = ctx->nsup * (ctx->nsup + 1) / 2;
         ctx->stats.tile_pairs_masked = ctx->n_masked;
         ctx->stats.tile_pairs_precise = ctx->n_precise;
-        ctx->stats.kernel_pairs = ctx->pairs_fast + ctx->pairs_precise;  // the timed (non-masked) launch
+        ctx->stats.kernel_pairs = tp_direct_timed_pairs(ctx);  // the timed (non-masked) launch
     } else {
         TP_TRY(tp_launch_bh(ctx, prm, prm->mode == TP_LEARNED));
     }
@@ -539,6 +674,7 @@ static tp_status run_eval(tp_ctx* ctx, const tp_params* prm, bool want_grad, voi
 }
 
 tp_status tp_energy(tp_ctx* ctx, const tp_params* params, double* energy_out) {
+    TpRange nvtx_range("tp_energy");
     if (!ctx) return TP_E_ARG;
     DeviceGuard g(ctx->device);
     ctx->err.clear();
@@ -548,6 +684,7 @@ tp_status tp_energy(tp_ctx* ctx, const tp_params* params, double* energy_out) {
 
 tp_status tp_gradient(tp_ctx* ctx, const tp_params* params, double* energy_out, void* grad_out, int g_dtype,
                       uint32_t flags) {
+    TpRange nvtx_range("tp_gradient");
     if (!ctx) return TP_E_ARG;
     DeviceGuard g(ctx->device);
     ctx->err.clear();
@@ -556,6 +693,7 @@ tp_status tp_gradient(tp_ctx* ctx, const tp_params* params, double* energy_out, 
 
 tp_status tp_fields(tp_ctx* ctx, const tp_params* params, double* energy_out, double* fw, double* fnu, double* fx,
                     uint32_t flags) {
+    TpRange nvtx_range("tp_fields");
     if (!ctx) return TP_E_ARG;
     DeviceGuard g(ctx->device);
     ctx->err.clear();
@@ -598,6 +736,7 @@ tp_status tp_set_quadrature(tp_ctx* ctx, int npoints) {
 
 tp_status tp_conf_upload(tp_ctx* ctx, const void* V, int64_t nv, int v_dtype, const int32_t* F, int64_t nt,
                          uint32_t flags) {
+    TpRange nvtx_range("tp_conf_upload");
     if (!ctx) return TP_E_ARG;
     DeviceGuard g(ctx->device);
     ctx->err.clear();
@@ -652,12 +791,15 @@ tp_status tp_conf_upload(tp_ctx* ctx, const void* V, int64_t nv, int v_dtype, co
 
 tp_status tp_conf_gradient(tp_ctx* ctx, const tp_params* params, double* energy_out, void* grad_out, int g_dtype,
                            uint32_t flags) {
+    TpRange nvtx_range("tp_conf_gradient");
     if (!ctx) return TP_E_ARG;
     DeviceGuard g(ctx->device);
     ctx->err.clear();
     const tp_params* prm = params;
     TP_TRY(check_params(ctx, prm));
     if (prm->mode != TP_DIRECT) return tp_set_err(ctx, TP_E_ARG, "the confinement energy is evaluated directly");
+    if (prm->prec == TP_F32_KAHAN)
+        return tp_set_err(ctx, TP_E_ARG, "the confinement energy has FP32 terms with FP64 sums or the FP64 form only");
     if (!ctx->have_conf) return tp_set_err(ctx, TP_E_STATE, "no confining surface uploaded (tp_conf_upload)");
     const bool want_grad = grad_out != nullptr;
     if (want_grad && g_dtype != TP_DTYPE_F32 && g_dtype != TP_DTYPE_F64)

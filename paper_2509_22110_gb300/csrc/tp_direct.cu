@@ -152,14 +152,33 @@ __device__ __forceinline__ float2 powq_m1(float2 x, float2& xq) {
     }
 }
 
+#ifndef TP_DIFF_FMA
+#define TP_DIFF_FMA 0
+#endif
 template <bool LO>
 __device__ __forceinline__ void pair_diff(const TgtPair& t, const SrcRec& s, float2 d[3]) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
+#if TP_DIFF_FMA
+        const float2 m1 = f2(-1.0f);
+        if (LO) d[k] = add2(fma2(s.h[k], m1, t.h[k]), fma2(s.l[k], m1, t.l[k]));
+        else d[k] = fma2(s.h[k], m1, t.h[k]);
+#else
         if (LO) d[k] = add2(add2(t.h[k], neg2(s.h[k])), add2(t.l[k], neg2(s.l[k])));
         else d[k] = add2(t.h[k], neg2(s.h[k]));
+#endif
     }
 }
+
+// x^(Q-1) (Q even: 6 or 8)
+template <int Q>
+__device__ __forceinline__ float2 powm1(float2 x) {
+    float2 x2 = mul2(x, x);
+    float2 x4 = mul2(x2, x2);
+    if (Q == 6) return mul2(x4, x);
+    return mul2(mul2(x4, x2), x);
+}
+
 
 // x^(Q-1) into xm1 and x^Q + addend into sum (the last product fused with the add)
 template <int Q>
@@ -181,6 +200,7 @@ __device__ __forceinline__ void powq_m1_fma(float2 x, float2 addend, float2& xm1
 struct PairPre {
     float2 d[3];
     float2 inv;
+    float2 r2;
 };
 
 template <int KIND>
@@ -189,6 +209,7 @@ __device__ __forceinline__ void pair_pre(const TgtPair& t, const SrcRec& s, Pair
     float2 r2 = mul2(p.d[0], p.d[0]);
     r2 = fma2(p.d[1], p.d[1], r2);
     r2 = fma2(p.d[2], p.d[2], r2);
+    p.r2 = r2;
     p.inv = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
 }
 
@@ -216,6 +237,17 @@ __device__ __forceinline__ void pair_post(const TgtPair& t, const SrcRec& s, con
     b = fma2(s.n[1], d[1], b);
     b = fma2(s.n[2], d[2], b);
     float2 al = mul2(a, inv), be = mul2(b, inv);
+#if TP_PAIR_T
+    // wi s6 = wi (al^q + be^q) = A5 al + B5 be: no al^q, be^q or s6 of their own;
+    // the pair energy E = wts s6 = (wi s6) |d|^2 is fused into both energy sums
+    float2 al5 = powm1<Q>(al), be5 = powm1<Q>(be);
+    float2 wi = mul2(wts, inv);
+    float2 A5 = mul2(wi, al5);
+    float2 B5 = mul2(wi, be5);
+    const float2 tt = fma2(A5, al, mul2(B5, be));
+    float2 nk = mul2(tt, f2(-2.0f));  // -(p/q) wts inv s6, p = 2q
+    const float2 ew = tt, ewm = p.r2;
+#else
     float2 alq;
     float2 al5 = powq_m1<Q>(al, alq);
     float2 be5, s6;
@@ -224,8 +256,10 @@ __device__ __forceinline__ void pair_post(const TgtPair& t, const SrcRec& s, con
     float2 A5 = mul2(wi, al5);
     float2 B5 = mul2(wi, be5);
     float2 nk = mul2(mul2(wi, s6), f2(-2.0f));  // -(p/q) wts inv s6, p = 2q
+    const float2 ew = wts, ewm = s6;
+#endif
     // target side (E = wts s6 is fused into both energy accumulations)
-    at.v[0] = fma2(wts, s6, at.v[0]);
+    at.v[0] = fma2(ew, ewm, at.v[0]);
     at.v[1] = add2(at.v[1], A5);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -234,7 +268,7 @@ __device__ __forceinline__ void pair_post(const TgtPair& t, const SrcRec& s, con
     }
     // source side (slots 1 and 5..7 negated, see above)
     if (FIRST) {
-        as.v[0] = mul2(wts, s6);
+        as.v[0] = mul2(ew, ewm);
         as.v[1] = B5;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -242,7 +276,7 @@ __device__ __forceinline__ void pair_post(const TgtPair& t, const SrcRec& s, con
             as.v[5 + k] = fma2(nk, d[k], mul2(A5, t.n[k]));
         }
     } else {
-        as.v[0] = fma2(wts, s6, as.v[0]);
+        as.v[0] = fma2(ew, ewm, as.v[0]);
         as.v[1] = add2(as.v[1], B5);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -405,13 +439,30 @@ __device__ __forceinline__ Item fetch_item(const DirectArgs& A, int* s_item) {
 #ifndef TP_GRAD_PREFETCH
 #define TP_GRAD_PREFETCH 1  // 1: prefetch the next source record; 2: also its geometry
 #endif
+#ifndef TP_EFOLD_SMEM
+#define TP_EFOLD_SMEM 0  // compensated energy sums of the gradient kernels: 0 registers, 1 shared memory
+#endif
+#ifndef TP_FAST_ONLY
+#define TP_FAST_ONLY 0  // 1: the precise/fast launch takes the fast items only; precise items run in the masked launch
+#endif
+#ifndef TP_GRAD_RED
+#define TP_GRAD_RED 1  // per-source warp reduction: 0 shuffle butterfly, 1 transposed through shared memory
+#endif
+// Transposed reduction of the source partials (TP_GRAD_RED 1): per warp two
+// slabs of 16 rows x 32 floats (row = component + 8 x source of a 2-source
+// step, column = lane), swizzled so that both the row-wise stores and the
+// column-wise 16-byte loads are free of bank conflicts.
+constexpr int SLAB_FLOATS = 16 * 32;
 template <bool MASKQ>
 struct GradShape {
     static constexpr int W = MASKQ ? 12 : TP_GRAD_W;
     static constexpr int NP = TP_SUPER / (64 * W);
     static constexpr int PF = MASKQ ? 1 : TP_GRAD_PREFETCH;  // source pipeline depth (register budget)
+    static constexpr int RED = MASKQ ? 0 : TP_GRAD_RED;
     static constexpr int THREADS = 32 * W;
-    static constexpr int SMEM = W * TP_CHUNK * TP_NACC * 4 + 2 * CHUNK_BYTES + 64;
+    static constexpr int SLAB_BYTES = RED == 1 ? W * 2 * SLAB_FLOATS * 4 : 0;
+    static constexpr int EFOLD_BYTES = TP_EFOLD_SMEM ? W * NP * 32 * 16 : 0;
+    static constexpr int SMEM = W * TP_CHUNK * TP_NACC * 4 + SLAB_BYTES + EFOLD_BYTES + 2 * CHUNK_BYTES + 64;
     static_assert(W * 32 * NP * 2 == TP_SUPER, "a block owns one super-tile of targets");
 };
 
@@ -435,6 +486,46 @@ __device__ __forceinline__ void src_step(const TgtPair (&tp)[NP], Acc8 (&at)[NP]
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) vprev[k] = as.v[k].x + as.v[k].y;
+}
+
+// One source of a precise/fast item with the transposed reduction: prefetch
+// the next source record, the NP packed evaluations, then the lane's 8 source
+// partials (both halves added) stored into rows row0..row0+7 of the slab.
+// Row r, lane l is stored at r * 32 + (l ^ ((r & 7) << 2)): each store of a row
+// covers the 32 banks once, and a load of 16 bytes by 8 lanes reading rows
+// r..r+7 at one logical column covers them once as well.
+template <int Q, int KIND, int NP>
+__device__ __forceinline__ void src_step_slab(const TgtPair (&tp)[NP], Acc8 (&at)[NP], const SrcRec& cur,
+                                              SrcRec& nxt, const float* nrec, bool has_next, float* slab_row0,
+                                              int lane) {
+    constexpr bool LO = KIND != K_FAST;
+    if (has_next) load_src<LO>(nrec, nxt);
+    const float2 one = make_float2(1.f, 1.f);
+    Acc8 as;
+    pair_grad<Q, KIND, true>(tp[0], cur, at[0], as, one);
+#pragma unroll
+    for (int P = 1; P < NP; ++P) pair_grad<Q, KIND, false>(tp[P], cur, at[P], as, one);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) slab_row0[k * 32 + (lane ^ (k << 2))] = as.v[k].x + as.v[k].y;
+}
+
+// Column sums of one slab (16 rows: 8 components x 2 sources) over the 32
+// lanes that stored them: lane l sums half a row (row l & 15, logical columns
+// 16 (l >> 4) .. + 15) with four 16-byte loads, the two halves meet by one
+// shuffle, and lanes 0..15 write the 16 totals (source-major, component-minor:
+// the order of the warp's partial array) to out[0..15].
+__device__ __forceinline__ void slab_reduce(const float* slab, float* out, int lane) {
+    const int r = lane & 15, h = lane >> 4;
+    const float* row = slab + r * 32;
+    const int xr = (r & 7) << 2;
+    float v = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 q = *reinterpret_cast<const float4*>(row + (((h << 4) | (k << 2)) ^ xr));
+        v += (q.x + q.y) + (q.z + q.w);
+    }
+    v += __shfl_xor_sync(0xffffffffu, v, 16);
+    if (lane < 16) out[lane] = v;
 }
 
 // Pipelined variant of src_step: the normal-independent geometry of the next
@@ -473,6 +564,27 @@ struct EFold {
     float2 s, c;  // running sum and its compensation, per packed target pair
 };
 
+// The same compensated sums kept in shared memory instead of registers: this
+// lane's (s.x, s.y, c.x, c.y) per packed target pair at p[32 P].
+struct EFoldSmem {
+    float4* p;
+};
+
+template <int NP>
+__device__ __forceinline__ void fold_energy(Acc8 (&at)[NP], EFoldSmem ef) {
+    const float2 m1 = f2(-1.0f);
+#pragma unroll
+    for (int P = 0; P < NP; ++P) {
+        const float4 q = ef.p[32 * P];
+        const float2 s0 = make_float2(q.x, q.y), c0 = make_float2(q.z, q.w);
+        const float2 y = fma2(c0, m1, at[P].v[0]);
+        const float2 t = add2(s0, y);
+        const float2 c = fma2(y, m1, fma2(s0, m1, t));
+        ef.p[32 * P] = make_float4(t.x, t.y, c.x, c.y);
+        at[P].v[0] = make_float2(0.f, 0.f);
+    }
+}
+
 template <int NP>
 __device__ __forceinline__ void fold_energy(Acc8 (&at)[NP], EFold (&ef)[NP]) {
     const float2 m1 = f2(-1.0f);
@@ -487,11 +599,13 @@ __device__ __forceinline__ void fold_energy(Acc8 (&at)[NP], EFold (&ef)[NP]) {
 }
 
 // The 12 chunks of one item for one item kind; target partials in `at`.
-template <int Q, int KIND, int W, int NP, int PF>
+template <int Q, int KIND, int W, int NP, int PF, class EF>
 __device__ __forceinline__ bool grad_item(const DirectArgs& A, ChunkPipe& pipe, float* sacc, int I, int J, int m,
-                                          const TgtPair (&tp)[NP], Acc8 (&at)[NP], EFold (&e64)[NP], int warp,
+                                          const TgtPair (&tp)[NP], Acc8 (&at)[NP], EF& e64, int warp,
                                           int lane, int pbase) {
     constexpr bool LO = KIND != K_FAST;
+    constexpr bool SLABRED = KIND != K_MASKED && PF == 1 && TP_GRAD_RED == 1 && W == GradShape<false>::W &&
+                             !(TP_FAST_ONLY && KIND == K_PRECISE);
     const int64_t ntp = A.ntp;
     int3 tf[NP][2];
     int tl[NP][2];  // target positions within the super-tile
@@ -640,6 +754,25 @@ __device__ __forceinline__ bool grad_item(const DirectArgs& A, ChunkPipe& pipe, 
                                       wacc + s * TP_NACC, lane);
                 if ((s & 30) == 30) fold_energy<NP>(at, e64);
             }
+            } else if constexpr (PF == 1 && SLABRED) {
+            // Two sources per trip; their 16 partials go to one slab, and the
+            // previous trip's slab is summed first (its loads and adds overlap
+            // this trip's arithmetic).  The __syncwarp at the end of a trip
+            // orders a slab's stores before its loads one trip later, and those
+            // loads before the stores into it two trips later.
+            float* slab = sacc + W * TP_CHUNK * TP_NACC + warp * 2 * SLAB_FLOATS;
+            load_src<LOU>(cb, ra);
+#pragma unroll 1
+            for (int s = 0; s < TP_CHUNK; s += 2) {
+                float* sw = slab + ((s >> 1) & 1) * SLAB_FLOATS;
+                if (s > 0) slab_reduce(slab + (((s >> 1) - 1) & 1) * SLAB_FLOATS, wacc + (s - 2) * TP_NACC, lane);
+                src_step_slab<Q, KU, NP>(tp, at, ra, rb, cb + (s + 1) * TP_SRCW, true, sw, lane);
+                src_step_slab<Q, KU, NP>(tp, at, rb, ra, cb + (s + 2) * TP_SRCW, s + 2 < TP_CHUNK, sw + 8 * 32,
+                                         lane);
+                if ((s & 30) == 30) fold_energy<NP>(at, e64);
+                __syncwarp();
+            }
+            slab_reduce(slab + ((TP_CHUNK / 2 - 1) & 1) * SLAB_FLOATS, wacc + (TP_CHUNK - 2) * TP_NACC, lane);
             } else if constexpr (PF == 1) {
             load_src<LOU>(cb, ra);
 #pragma unroll 1
@@ -659,8 +792,10 @@ __device__ __forceinline__ bool grad_item(const DirectArgs& A, ChunkPipe& pipe, 
                 if ((s & 31) == 31) fold_energy<NP>(at, e64);
             }
             }
-            const float r = warp_transpose_reduce8(vprev, lane);
-            if ((lane & 3) == 0) wacc[(TP_CHUNK - 1) * TP_NACC + ((lane >> 2) & 7)] = r;
+            if constexpr (!SLABRED) {
+                const float r = warp_transpose_reduce8(vprev, lane);
+                if ((lane & 3) == 0) wacc[(TP_CHUNK - 1) * TP_NACC + ((lane >> 2) & 7)] = r;
+            }
         } else {
             for (int i = lane; i < TP_CHUNK * TP_NACC; i += 32) wacc[i] = 0.f;
         }
@@ -689,8 +824,9 @@ template <int Q, bool MASKQ>
 __global__ void __launch_bounds__(GradShape<MASKQ>::THREADS, 1) k_pairs_grad(DirectArgs A) {
     constexpr int W = GradShape<MASKQ>::W, NP = GradShape<MASKQ>::NP;
     extern __shared__ __align__(128) unsigned char smem[];
-    constexpr int SACC_BYTES = W * TP_CHUNK * TP_NACC * 4;
-    float* sacc = reinterpret_cast<float*>(smem);                                 // [W][CHUNK][8]
+    constexpr int SACC_BYTES =
+        W * TP_CHUNK * TP_NACC * 4 + GradShape<MASKQ>::SLAB_BYTES + GradShape<MASKQ>::EFOLD_BYTES;
+    float* sacc = reinterpret_cast<float*>(smem);  // [W][CHUNK][8], then slabs, then energy folds
     float* chunk = reinterpret_cast<float*>(smem + SACC_BYTES);                   // [2][CHUNK][SRCW]
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + SACC_BYTES + 2 * CHUNK_BYTES);
     int* s_item = reinterpret_cast<int*>(smem + SACC_BYTES + 2 * CHUNK_BYTES + 16);
@@ -719,19 +855,33 @@ __global__ void __launch_bounds__(GradShape<MASKQ>::THREADS, 1) k_pairs_grad(Dir
             rowI = it.I;
 #pragma unroll
             for (int P = 0; P < NP; ++P)
-                load_tgt<true>(A.soa, ntp, (int64_t)it.I * TP_SUPER + 2 * (pbase + 32 * P), tp[P]);
+                load_tgt<!(TP_FAST_ONLY && !MASKQ)>(A.soa, ntp, (int64_t)it.I * TP_SUPER + 2 * (pbase + 32 * P), tp[P]);
         }
         Acc8 at[NP];
+#if TP_EFOLD_SMEM
+        EFoldSmem e64;
+        e64.p = reinterpret_cast<float4*>(smem + W * TP_CHUNK * TP_NACC * 4 + GradShape<MASKQ>::SLAB_BYTES) +
+                warp * NP * 32 + lane;
+#pragma unroll
+        for (int P = 0; P < NP; ++P) e64.p[32 * P] = make_float4(0.f, 0.f, 0.f, 0.f);
+#else
         EFold e64[NP];
 #pragma unroll
+        for (int P = 0; P < NP; ++P) e64[P].s = e64[P].c = make_float2(0.f, 0.f);
+#endif
+#pragma unroll
         for (int P = 0; P < NP; ++P) {
-            e64[P].s = e64[P].c = make_float2(0.f, 0.f);
 #pragma unroll
             for (int c = 0; c < TP_NACC; ++c) at[P].v[c] = make_float2(0.f, 0.f);
         }
         bool ok;
         if constexpr (MASKQ) {
-            ok = grad_item<Q, K_MASKED, W, NP, GradShape<MASKQ>::PF>(A, pipe, sacc, it.I, it.J, it.m, tp, at, e64, warp, lane, pbase);
+            if (TP_FAST_ONLY && it.kind == K_PRECISE)
+                ok = grad_item<Q, K_PRECISE, W, NP, GradShape<MASKQ>::PF>(A, pipe, sacc, it.I, it.J, it.m, tp, at, e64, warp, lane, pbase);
+            else
+                ok = grad_item<Q, K_MASKED, W, NP, GradShape<MASKQ>::PF>(A, pipe, sacc, it.I, it.J, it.m, tp, at, e64, warp, lane, pbase);
+        } else if constexpr (TP_FAST_ONLY) {
+            ok = grad_item<Q, K_FAST, W, NP, GradShape<MASKQ>::PF>(A, pipe, sacc, it.I, it.J, it.m, tp, at, e64, warp, lane, pbase);
         } else {
             if (it.kind == K_FAST) ok = grad_item<Q, K_FAST, W, NP, GradShape<MASKQ>::PF>(A, pipe, sacc, it.I, it.J, it.m, tp, at, e64, warp, lane, pbase);
             else ok = grad_item<Q, K_PRECISE, W, NP, GradShape<MASKQ>::PF>(A, pipe, sacc, it.I, it.J, it.m, tp, at, e64, warp, lane, pbase);
@@ -745,7 +895,12 @@ __global__ void __launch_bounds__(GradShape<MASKQ>::THREADS, 1) k_pairs_grad(Dir
 #pragma unroll
         for (int P = 0; P < NP; ++P) {
             const int64_t t0 = (int64_t)it.I * TP_SUPER + 2 * (pbase + 32 * P);
+#if TP_EFOLD_SMEM
+            const float4 q = e64.p[32 * P];
+            const double ex = (double)q.x - (double)q.z, ey = (double)q.y - (double)q.w;
+#else
             const double ex = (double)e64[P].s.x - (double)e64[P].c.x, ey = (double)e64[P].s.y - (double)e64[P].c.y;
+#endif
             if (ex != 0.0) atomicAdd(&A.acc[t0], ex);
             if (ey != 0.0) atomicAdd(&A.acc[t0 + 1], ey);
 #pragma unroll
@@ -946,6 +1101,95 @@ __global__ void k_pairs_f64(const double* x64, const double* nu64, const double*
     eper[k] = es;
 }
 
+// ------------------------------------------------------------ compensated FP32 kernel (TP_F32_KAHAN)
+// One thread per target (library order), gathering over every source: the
+// pair terms in FP32 (centroid differences from hi + lo parts, as in the
+// precise items of the symmetric kernel) and every one of the target's eight
+// sums (Ew, U, Gn[3], Gx[3], both orderings) accumulated with Kahan's
+// compensated summation in FP32, so that no sum is carried in FP64: FP64
+// enters only when the finished sums are stored for the pull-back and the
+// final energy reduction.  Each unordered pair is evaluated twice (once from
+// each end), which the symmetric kernel avoids; this form trades that for
+// sums whose error does not grow with the number of sources.
+struct Kahan {
+    float s, c;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+constexpr int KAHAN_TILE = 128;
+
+template <int Q>
+__global__ void __launch_bounds__(KAHAN_TILE) k_pairs_kahan(const float* __restrict__ soa, const int32_t* __restrict__ Fs,
+                                                          int64_t nt, int64_t ntp, int edge_only,
+                                                          double* __restrict__ acc) {
+    __shared__ float sd[10][KAHAN_TILE];
+    __shared__ int sf[3][KAHAN_TILE];
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool active = k < nt;
+    float t[10];
+#pragma unroll
+    for (int c = 0; c < 10; ++c) t[c] = active ? soa[c * ntp + k] : 0.f;
+    const int3 ft = active ? make_int3(Fs[3 * k], Fs[3 * k + 1], Fs[3 * k + 2]) : make_int3(-1, -1, -1);
+    Kahan K[TP_NACC];
+#pragma unroll
+    for (int c = 0; c < TP_NACC; ++c) K[c].s = K[c].c = 0.f;
+    for (int64_t s0 = 0; s0 < nt; s0 += KAHAN_TILE) {
+        __syncthreads();
+        const int64_t S = s0 + threadIdx.x;
+#pragma unroll
+        for (int c = 0; c < 10; ++c) sd[c][threadIdx.x] = S < nt ? soa[c * ntp + S] : 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sf[c][threadIdx.x] = S < nt ? Fs[3 * S + c] : -1;
+        __syncthreads();
+        if (!active) continue;
+        const int m = (nt - s0) < KAHAN_TILE ? (int)(nt - s0) : KAHAN_TILE;
+        for (int j = 0; j < m; ++j) {
+            if (s0 + j == k) continue;
+            if (share_vertex(ft, make_int3(sf[0][j], sf[1][j], sf[2][j]), edge_only)) continue;
+            float d[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) d[c] = (t[c] - sd[c][j]) + (t[3 + c] - sd[3 + c][j]);
+            const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            const float inv = rcp_approx(r2);
+            const float a = t[6] * d[0] + t[7] * d[1] + t[8] * d[2];
+            const float b = sd[6][j] * d[0] + sd[7][j] * d[1] + sd[8][j] * d[2];
+            const float al = a * inv, be = b * inv;
+            const float al2 = al * al, be2 = be * be, al4 = al2 * al2, be4 = be2 * be2;
+            float al5, be5, alq, beq;
+            if (Q == 6) {
+                al5 = al4 * al;
+                be5 = be4 * be;
+                alq = al4 * al2;
+                beq = be4 * be2;
+            } else {
+                al5 = al4 * al2 * al;
+                be5 = be4 * be2 * be;
+                alq = al4 * al4;
+                beq = be4 * be4;
+            }
+            const float wts = t[9] * sd[9][j];  // w~_T w~_S = (p/q) w_T w_S
+            const float s6 = alq + beq, wi = wts * inv;
+            const float A5 = wi * al5, B5 = wi * be5, kk = 2.0f * wi * s6;  // p = 2q
+            K[0].add(wts * s6);
+            K[1].add(A5);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                K[2 + c].add(A5 * d[c]);
+                K[5 + c].add(B5 * sd[6 + c][j] - kk * d[c]);
+            }
+        }
+    }
+    if (!active) return;
+#pragma unroll
+    for (int c = 0; c < TP_NACC; ++c) acc[c * ntp + k] = (double)K[c].s - (double)K[c].c;
+}
+
+
 template <int Q>
 tp_status launch_grad_q(tp_ctx* ctx, DirectArgs A) {
     // the shared-memory limit is a per-device attribute: set it on the current device at every launch
@@ -955,20 +1199,23 @@ tp_status launch_grad_q(tp_ctx* ctx, DirectArgs A) {
                                GradShape<true>::SMEM));
     TP_CU(cudaMemsetAsync(ctx->work, 0, 2 * sizeof(unsigned), ctx->stream));
     // masked items first (their own queue), then the precise and fast items
-    if (ctx->n_masked > 0) {
+    const int64_t nmq = ctx->n_masked + (TP_FAST_ONLY ? ctx->n_precise : 0);
+    if (nmq > 0) {
         DirectArgs M = A;
-        M.np = M.nf = 0;
+        if (!TP_FAST_ONLY) M.np = 0;
+        M.nf = 0;
         M.work = ctx->work + 1;
         M.partial = reinterpret_cast<double*>(ctx->xptrs);
-        const int grid = (int)std::min<int64_t>(ctx->num_sms, ctx->n_masked);
+        const int grid = (int)std::min<int64_t>(ctx->num_sms, nmq);
         k_pairs_grad<Q, true><<<grid, GradShape<true>::THREADS, GradShape<true>::SMEM, ctx->stream>>>(M);
         ++ctx->nlaunch;
     }
-    const int64_t nrest = ctx->n_precise + ctx->n_fast;
+    const int64_t nrest = (TP_FAST_ONLY ? 0 : ctx->n_precise) + ctx->n_fast;
     cudaEventRecord(ctx->ev[0], ctx->stream);
     if (nrest > 0) {
         DirectArgs R = A;
         R.nm = 0;
+        if (TP_FAST_ONLY) R.np = 0;
         const int grid = (int)std::min<int64_t>(ctx->num_sms, nrest);
         k_pairs_grad<Q, false><<<grid, GradShape<false>::THREADS, GradShape<false>::SMEM, ctx->stream>>>(R);
         ++ctx->nlaunch;
@@ -1083,6 +1330,21 @@ __device__ __forceinline__ void conf_pair(const TgtPair& t, const SrcRec& s, Acc
     a = fma2(t.n[1], d[1], a);
     a = fma2(t.n[2], d[2], a);
     const float2 al = mul2(a, inv);
+#if TP_PAIR_T
+    // wi al^q = A5 al; the pair energy wts al^q = (wi al^q) |d|^2; Gx collects
+    // (wi al^q) d, and its factor -(p/q) = -2 is applied once per item
+    const float2 al5 = powm1<Q>(al);
+    const float2 wi = mul2(wts, inv);
+    const float2 A5 = mul2(wi, al5);
+    const float2 tt = mul2(A5, al);
+    at.v[0] = fma2(tt, r2, at.v[0]);
+    at.v[1] = add2(at.v[1], A5);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        at.v[2 + k] = fma2(A5, d[k], at.v[2 + k]);
+        at.v[5 + k] = fma2(tt, d[k], at.v[5 + k]);
+    }
+#else
     float2 alq;
     const float2 al5 = powq_m1<Q>(al, alq);
     const float2 wi = mul2(wts, inv);
@@ -1095,7 +1357,10 @@ __device__ __forceinline__ void conf_pair(const TgtPair& t, const SrcRec& s, Acc
         at.v[2 + k] = fma2(A5, d[k], at.v[2 + k]);
         at.v[5 + k] = fma2(nk, d[k], at.v[5 + k]);
     }
+#endif
 }
+// factor of the Gx partials of conf_pair at the end of an item
+constexpr float CONF_GX_SCALE = TP_PAIR_T ? -2.0f : 1.0f;
 
 // Persistent: items (target super-tile I, confining super-tile J) for all I, J,
 // from a dynamic queue; block shape of the precise/fast gradient kernel.
@@ -1175,8 +1440,9 @@ __global__ void __launch_bounds__(GradShape<false>::THREADS, 1) k_conf_grad(Dire
             if (ey != 0.0) atomicAdd(&A.acc[t0 + 1], ey);
 #pragma unroll
             for (int k = 1; k < TP_NACC; ++k) {
-                if (at[P].v[k].x != 0.f) atomicAdd(&A.acc[k * ntp + t0], (double)at[P].v[k].x);
-                if (at[P].v[k].y != 0.f) atomicAdd(&A.acc[k * ntp + t0 + 1], (double)at[P].v[k].y);
+                const float sc = k >= 5 ? CONF_GX_SCALE : 1.0f;
+                if (at[P].v[k].x != 0.f) atomicAdd(&A.acc[k * ntp + t0], (double)(sc * at[P].v[k].x));
+                if (at[P].v[k].y != 0.f) atomicAdd(&A.acc[k * ntp + t0 + 1], (double)(sc * at[P].v[k].y));
             }
         }
     }
@@ -1251,6 +1517,7 @@ DirectArgs make_args(tp_ctx* ctx, const tp_params* prm) {
 }  // namespace
 
 tp_status tp_launch_direct_grad(tp_ctx* ctx, const tp_params* prm) {
+    TpRange nvtx_range("tp_launch_direct_grad");
     TP_TRY(tp_ensure_flagged(ctx));
     TP_CU(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * TP_NACC * ctx->ntp, ctx->stream));
     DirectArgs A = make_args(ctx, prm);
@@ -1269,6 +1536,7 @@ tp_status tp_launch_conf_tri(tp_ctx* ctx) {
 // Confinement accumulators of the evolving mesh's triangles (library order)
 // into ctx->acc; the pair launch is bracketed by ev[0] / ev[1].
 tp_status tp_launch_conf(tp_ctx* ctx, const tp_params* prm) {
+    TpRange nvtx_range("tp_launch_conf");
     TP_TRY(tp_ensure_sorted(ctx));
     TP_CU(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * TP_NACC * ctx->ntp, ctx->stream));
     if (prm->prec == TP_F64) {
@@ -1311,6 +1579,7 @@ tp_status tp_launch_conf(tp_ctx* ctx, const tp_params* prm) {
 }
 
 tp_status tp_launch_direct_energy(tp_ctx* ctx, const tp_params* prm, double* partials, int* nparts) {
+    TpRange nvtx_range("tp_launch_direct_energy");
     TP_TRY(tp_ensure_flagged(ctx));
     DirectArgs A = make_args(ctx, prm);
     A.partial = partials;
@@ -1318,7 +1587,30 @@ tp_status tp_launch_direct_energy(tp_ctx* ctx, const tp_params* prm, double* par
     return launch_energy_q<8>(ctx, A, nparts);
 }
 
+// unordered pairs of the launch that ev[0] / ev[1] bracket in the direct gradient
+int64_t tp_direct_timed_pairs(const tp_ctx* ctx) {
+    return ctx->pairs_fast + (TP_FAST_ONLY ? 0 : ctx->pairs_precise);
+}
+
+tp_status tp_launch_direct_kahan(tp_ctx* ctx, const tp_params* prm) {
+    TpRange nvtx_range("tp_launch_direct_kahan");
+    TP_TRY(tp_ensure_sorted(ctx));
+    TP_CU(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * TP_NACC * ctx->ntp, ctx->stream));
+    const int edge = (prm->flags & TP_EXCLUDE_EDGE) ? 1 : 0;
+    const unsigned blocks = (unsigned)((ctx->nt + KAHAN_TILE - 1) / KAHAN_TILE);
+    cudaEventRecord(ctx->ev[0], ctx->stream);
+    if (prm->q == 6)
+        k_pairs_kahan<6><<<blocks, KAHAN_TILE, 0, ctx->stream>>>(ctx->soa, ctx->Fs, ctx->nt, ctx->ntp, edge, ctx->acc);
+    else
+        k_pairs_kahan<8><<<blocks, KAHAN_TILE, 0, ctx->stream>>>(ctx->soa, ctx->Fs, ctx->nt, ctx->ntp, edge, ctx->acc);
+    ++ctx->nlaunch;
+    cudaEventRecord(ctx->ev[1], ctx->stream);
+    TP_CU(cudaGetLastError());
+    return TP_OK;
+}
+
 tp_status tp_launch_direct_f64(tp_ctx* ctx, const tp_params* prm, bool grad) {
+    TpRange nvtx_range("tp_launch_direct_f64");
     (void)grad;
     TP_CU(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * TP_NACC * ctx->ntp, ctx->stream));
     const int edge = (prm->flags & TP_EXCLUDE_EDGE) ? 1 : 0;

@@ -26,6 +26,19 @@
 
 #include "../../include/tp.h"
 
+#include <nvtx3/nvToolsExt.h>
+
+// NVTX range over the lifetime of the object: every C-ABI call and every
+// launch phase (one or a few kernels) is marked on the host timeline of a
+// profiler (nsys, ncu --nvtx).  Header-only NVTX costs a predictable branch
+// when no tool is attached.
+struct TpRange {
+    explicit TpRange(const char* name) { nvtxRangePushA(name); }
+    ~TpRange() { nvtxRangePop(); }
+    TpRange(const TpRange&) = delete;
+    TpRange& operator=(const TpRange&) = delete;
+};
+
 #define TP_SUPER 1536      // triangles per super-tile (one block's target set)
 #define TP_CHUNK 128       // sources staged per shared-memory chunk
 #define TP_SRCW 20         // floats per staged source record
@@ -33,6 +46,15 @@
 #define TP_NBLK (TP_SUPER / TP_CHUNK)  // 128-triangle blocks per super-tile side
 #define TP_BMASK_WORDS ((TP_NBLK * TP_NBLK + 31) / 32)  // bits of one super-tile pair's block mask
 #define TP_SPIN_LIMIT (1u << 26)
+// Pair arithmetic of the gradient kernels: 1 forms wi s6 = wi (al^q + be^q) as
+// A5 al + B5 be and the pair energy as that times |d|^2 (one packed operation
+// fewer per pair), 0 forms al^q, be^q and s6 explicitly.
+#ifndef TP_PAIR_T
+#define TP_PAIR_T 1
+#endif
+// a bounded device wait gives up after this much wall-clock time (ns), or
+// after TP_SPIN_LIMIT polls, whichever comes first
+#define TP_WAIT_NS 1000000000ull
 // super-tile pairs whose centroid boxes are closer than this fraction of the
 // mesh's centroid-box diagonal form centroid differences from hi + lo parts
 #define TP_PRECISE_GAP_REL 0.02f
@@ -126,7 +148,7 @@ struct tp_ctx {
     double* center = nullptr;       // [3] f64 centre subtracted before the f32 split
     double* bounds = nullptr;       // [6] min/max of centroids
     double* red = nullptr;          // reduction scratch
-    double* scalar = nullptr;       // [4] device scalars (energy ...)
+    double* scalar = nullptr;       // [10] device scalars (energies, counters)
     unsigned* derr = nullptr;       // device error word
     unsigned* adjbm = nullptr;      // bitmap nsup*nsup: super-tile pairs holding a vertex-sharing pair (or I == J)
     unsigned* flagged = nullptr;    // bitmap nsup*nsup: super-tile pairs not handled by the fast kernel
@@ -149,8 +171,11 @@ struct tp_ctx {
     int32_t* mcount = nullptr;      // [10]: counts of mlist, plist, 3 u64 pair counts (fast, precise, masked), count of flist
     unsigned* work = nullptr;       // [2] dynamic work counters of the persistent pair kernels
     float* tbox = nullptr;          // [nsup][6] f32 centroid boxes of the super-tiles
-    void* sort_tmp = nullptr;
-    size_t sort_tmp_bytes = 0;
+    // scratch of the hand-written key sort and compaction (tp_sort.cu)
+    uint32_t* sort_hist = nullptr;  // per-tile digit counts and digit totals
+    uint32_t* sort_ktmp = nullptr;  // ping-pong keys (32- or 64-bit)
+    int32_t* sort_vtmp = nullptr;   // ping-pong values
+    int64_t sort_hist_cap = 0, sort_kv_cap = 0;  // sort_kv_cap in 32-bit words
     double* host_pinned = nullptr;  // small pinned staging
 
     int64_t n_masked = 0;
@@ -162,7 +187,8 @@ struct tp_ctx {
     int64_t n_precise = 0;
     int64_t n_fast = 0;
     int64_t pairs_fast = 0, pairs_precise = 0, pairs_masked_items = 0;  // unordered real pairs per item kind
-    int64_t n_excluded_ordered = 0;  // ordered pairs T != S sharing a vertex
+    int64_t n_excluded_ordered = 0;       // ordered pairs T != S sharing a vertex
+    int64_t n_excluded_edge_ordered = 0;  // ordered pairs T != S sharing an edge
     int64_t cap_nv = 0, cap_nt = 0, cap_ntp = 0, red_cap = 0;
     double* gradbuf = nullptr;      // [3nv] device staging of host gradients
     double* fieldbuf = nullptr;     // [7nt] device staging of host per-triangle fields (allocated on first use)
@@ -207,6 +233,9 @@ struct tp_ctx {
 
     // allocation bookkeeping
     std::vector<void*> allocs;
+    // test hook (tp_debug_fail_alloc): the allocation after this many more
+    // successful ones fails as if the device were out of memory; -1 = never
+    int64_t fail_alloc_after = -1;
 };
 
 // ---------------------------------------------------------------- host helpers
@@ -225,6 +254,11 @@ tp_status tp_cuda_check(tp_ctx* c, cudaError_t e, const char* what);
 
 tp_status tp_alloc(tp_ctx* ctx, void** p, size_t bytes);
 void tp_free(tp_ctx* ctx, void* p);
+// After a failed allocation: release every buffer derived from the mesh
+// (mesh, tree, item lists, Barnes-Hut lists, sort scratch, confining surface)
+// and zero their capacities, so that no later call sees a buffer that a
+// half-finished resize left missing.  The model, stream and settings stay.
+void tp_drop_mesh_state(tp_ctx* ctx);
 template <typename T>
 inline tp_status tp_alloc_t(tp_ctx* ctx, T** p, size_t n) {
     return tp_alloc(ctx, reinterpret_cast<void**>(p), n * sizeof(T) + 16);
@@ -254,6 +288,20 @@ tp_status tp_count_excluded(tp_ctx* ctx);
 tp_status tp_launch_direct_grad(tp_ctx* ctx, const tp_params* prm);
 tp_status tp_launch_direct_energy(tp_ctx* ctx, const tp_params* prm, double* partials, int* nparts);
 tp_status tp_launch_direct_f64(tp_ctx* ctx, const tp_params* prm, bool grad);
+// unordered pairs of the direct gradient's timed launch (ev[0] / ev[1])
+int64_t tp_direct_timed_pairs(const tp_ctx* ctx);
+// compensated FP32 sums (TP_F32_KAHAN): per-target gather into ctx->acc
+tp_status tp_launch_direct_kahan(tp_ctx* ctx, const tp_params* prm);
+// Stable sort of n (32-bit key, 32-bit value) pairs by the low `bits` bits of
+// the key (LSD radix, tp_sort.cu); inputs are left unchanged.
+tp_status tp_sort_pairs_u32(tp_ctx* ctx, const uint32_t* keys_in, const int32_t* vals_in, uint32_t* keys_out,
+                            int32_t* vals_out, int64_t n, int bits);
+tp_status tp_sort_pairs_u64(tp_ctx* ctx, const uint64_t* keys_in, const int32_t* vals_in, uint64_t* keys_out,
+                            int32_t* vals_out, int64_t n, int bits);
+// The entries >= 0 of in[0..n) in order to out, their number to *count_d (device).
+tp_status tp_compact_nonneg(tp_ctx* ctx, const int32_t* in, int64_t n, int32_t* out, int32_t* count_d);
+// Prefix sum of m counts (exclusive or inclusive, out may be in), total to *total_d if not null.
+tp_status tp_scan_u32(tp_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t m, bool inclusive, int32_t* total_d);
 // tp_adjoint.cu
 // A node the Barnes-Hut traversal can reach: the root, or a child of a node
 // with more than leaf_size members (a node of at most leaf_size members is
@@ -343,10 +391,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: true when the phase completed, false after TP_SPIN_LIMIT polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (uint32_t i = 0; i < TP_SPIN_LIMIT; ++i)
+__device__ __forceinline__ uint64_t tp_globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait: true when the phase completed; false once limit_ns of
+// wall-clock time has passed (the clock is read every 32 polls, and only
+// after the first poll failed) or after TP_SPIN_LIMIT polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns = TP_WAIT_NS) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = tp_globaltimer_ns();
+    for (uint32_t i = 1; i < TP_SPIN_LIMIT; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 31u) == 0u && tp_globaltimer_ns() - t0 > limit_ns) return false;
+    }
     return false;
 }
 

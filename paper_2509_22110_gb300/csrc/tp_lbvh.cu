@@ -24,7 +24,6 @@
 //      FP64 operation is separately rounded in a fixed order, so the moments
 //      are bit-exact with the oracle.  A second pass writes the far-field
 //      and admissibility records of the nodes the traversal can reach.
-#include <cub/cub.cuh>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -100,9 +99,6 @@ __global__ void k_mark_leaves(int64_t n, int leaf_size, const int32_t* __restric
     start_node[first[v]] = (int32_t)v;
 }
 
-struct NonNeg {
-    __device__ __forceinline__ bool operator()(const int32_t& a) const { return a >= 0; }
-};
 
 constexpr int MOM_B = 64;   // primitives per block of the bottom-up pass
 constexpr int MOM_W = 19;   // values per node: 13 moments + 6 box bounds
@@ -306,6 +302,7 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 }  // namespace
 
 tp_status tp_launch_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits) {
+    TpRange nvtx_range("tp_launch_tree_build");
     const int64_t n = ctx->nt;
     const int64_t nn = 2 * n - 1;
     tp_tree& t = ctx->tree;
@@ -364,17 +361,7 @@ tp_status tp_launch_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits) {
     TP_CU(cudaMemsetAsync(start_node, 0xff, sizeof(int32_t) * n, ctx->stream));
     k_mark_leaves<<<nblk(nn, 256), 256, 0, ctx->stream>>>(n, leaf_size, t.first, t.last, t.parent, start_node);
     ++ctx->nlaunch;
-    size_t need = 0;
-    cub::DeviceSelect::If(nullptr, need, start_node, t.leaves, t.nleaves_d, (int)n, NonNeg(), ctx->stream);
-    if (need > ctx->sort_tmp_bytes) {
-        tp_free(ctx, ctx->sort_tmp);
-        ctx->sort_tmp = nullptr;
-        TP_TRY(tp_alloc(ctx, &ctx->sort_tmp, need));
-        ctx->sort_tmp_bytes = need;
-    }
-    size_t have = ctx->sort_tmp_bytes;
-    TP_CU(cub::DeviceSelect::If(ctx->sort_tmp, have, start_node, t.leaves, t.nleaves_d, (int)n, NonNeg(),
-                                ctx->stream));
+    TP_TRY(tp_compact_nonneg(ctx, start_node, n, t.leaves, t.nleaves_d));
     // 4. moments
     if (n > 1) TP_CU(cudaMemsetAsync(t.counter, 0, sizeof(int32_t) * (n - 1), ctx->stream));
     k_moments<<<nblk(n, MOM_B), MOM_B, 0, ctx->stream>>>(ctx->V64, ctx->F, ctx->x64, ctx->nu64, ctx->w64, ctx->perm,

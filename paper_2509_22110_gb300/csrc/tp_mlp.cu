@@ -648,6 +648,7 @@ tp_status tp_mlp_node_features(tp_ctx* ctx) {
 }
 
 tp_status tp_ensure_node_features(tp_ctx* ctx) {
+    TpRange nvtx_range("tp_ensure_node_features");
     if (!ctx->tree.feat_stale) return TP_OK;
     TP_TRY(tp_mlp_node_features(ctx));
     ctx->tree.feat_stale = false;
@@ -741,6 +742,7 @@ tp_status tp_far_dataset_size(tp_ctx* ctx, int64_t* n) {
 // pair and seed), up to max_pairs; append their features and labels.
 tp_status tp_far_sample_pairs(tp_ctx* ctx, double theta, double keep, uint64_t seed, int64_t max_pairs,
                               int64_t* n_added) {
+    TpRange nvtx_range("tp_far_sample_pairs");
     if (!ctx) return TP_E_ARG;
     cudaSetDevice(ctx->device);
     ctx->err.clear();
@@ -797,6 +799,7 @@ tp_status tp_far_dataset_get(tp_ctx* ctx, int64_t i0, int64_t n, float* feat, fl
 
 // Feature normalisation (mean, std) and in-distribution ranges from the dataset.
 tp_status tp_far_fit_normalisation(tp_ctx* ctx) {
+    TpRange nvtx_range("tp_far_fit_normalisation");
     if (!ctx || !ctx->mlp || ctx->mlp->dcount < 2) return TP_E_STATE;
     cudaSetDevice(ctx->device);
     k_feat_stats<<<MLP_NI, 256, 0, ctx->stream>>>(ctx->mlp->dfeat, ctx->mlp->dcount, ctx->mlp->norm);
@@ -811,6 +814,7 @@ tp_status tp_far_fit_normalisation(tp_ctx* ctx) {
 // *mean_loss receives the mean batch loss of the last step.
 tp_status tp_far_train(tp_ctx* ctx, int64_t steps, int64_t batch, double lr, double wd, uint64_t seed,
                        double* last_loss) {
+    TpRange nvtx_range("tp_far_train");
     if (!ctx || !ctx->mlp) return TP_E_STATE;
     cudaSetDevice(ctx->device);
     tp_mlp_model* m = ctx->mlp;
@@ -851,6 +855,7 @@ tp_status tp_far_train(tp_ctx* ctx, int64_t steps, int64_t batch, double lr, dou
 // != 0), Y [n][7] out; grad [MLP_NPARAM] out (may be null).  For tests.
 tp_status tp_far_eval(tp_ctx* ctx, const float* X, int64_t n, int normalised, const float* tgt, const float* mask,
                       float* Y, float* grad, double* loss) {
+    TpRange nvtx_range("tp_far_eval");
     if (!ctx || !ctx->mlp || !X || n < 1) return TP_E_ARG;
     cudaSetDevice(ctx->device);
     tp_mlp_model* m = ctx->mlp;
@@ -926,6 +931,7 @@ tp_status tp_far_eval(tp_ctx* ctx, const float* X, int64_t n, int normalised, co
 
 // One AdamW step with a given gradient (host, [MLP_NPARAM]); for tests.
 tp_status tp_far_adamw_step(tp_ctx* ctx, const float* grad, double lr, double wd) {
+    TpRange nvtx_range("tp_far_adamw_step");
     if (!ctx || !ctx->mlp || !grad) return TP_E_ARG;
     cudaSetDevice(ctx->device);
     tp_mlp_model* m = ctx->mlp;
@@ -965,6 +971,7 @@ tp_status tp_far_model_save(tp_ctx* ctx, const char* path) {
 }
 
 tp_status tp_far_model_load(tp_ctx* ctx, const char* path) {
+    TpRange nvtx_range("tp_far_model_load");
     if (!ctx || !path) return TP_E_ARG;
     cudaSetDevice(ctx->device);
     FILE* f = fopen(path, "rb");

@@ -12,9 +12,12 @@
 //
 // The scratch address is looked up once per device with
 // cudaGetSymbolAddress, on the first call made with that device current;
-// make that first call before any stream capture starts.  Every call uses
-// the same array: two calls whose work overlaps on the GPU (different
-// streams, or different host threads) race on it and give wrong results.
+// make that first call before any stream capture starts.  The address is
+// kept for the life of the process, which assumes the device's primary
+// context is never reset (cudaDeviceReset) and is the context in use.
+// Every call uses the same array: two calls whose work overlaps on the GPU
+// (different streams, or different host threads) race on it and give wrong
+// results.
 // Every scratch entry a call reads is written by that call first, so the
 // contents left by an earlier call do not matter.
 //
@@ -258,6 +261,8 @@ extern "C" tp_status tp_gradient_direct_noalloc(const double* V, int64_t nv, con
     if (!((params->q == 6 && params->p == 12) || (params->q == 8 && params->p == 16)))
         return na_err(errbuf, errbuf_len, TP_E_ARG, "unsupported exponents (supported: q=6 p=12, q=8 p=16)");
     if (params->mode != TP_DIRECT) return na_err(errbuf, errbuf_len, TP_E_ARG, "only TP_DIRECT is available here");
+    if (params->prec != TP_F32_F64ACC)
+        return na_err(errbuf, errbuf_len, TP_E_ARG, "only TP_F32_F64ACC (FP32 pair terms, FP64 sums) is available here");
     if (nv < 0 || nt < 0) return na_err(errbuf, errbuf_len, TP_E_ARG, "negative size");
     if (nt > TP_NOALLOC_MAX_TRIS) {
         char msg[160];

@@ -351,6 +351,7 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const __nv_bfloat16* __restrict_
 
 tp_status tp_launch_mlp_tc(tp_ctx* ctx, const __nv_bfloat16* wb, const float* bias, const __nv_bfloat16* X,
                            int64_t rows, float* kf, int raw) {
+    TpRange nvtx_range("tp_launch_mlp_tc");
     // per-device attribute: set on the current device at every launch
     TP_CU(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem)));
     const int64_t ntiles = (rows + 127) / 128;

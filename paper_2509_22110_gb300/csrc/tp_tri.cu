@@ -11,7 +11,6 @@
 // products then differences, |N| = sqrt((Nx^2 + Ny^2) + Nz^2), w = |N|/2,
 // nu = N/|N| - so the Morton codes and cluster moments built from it are
 // reproducible bit for bit.
-#include <cub/cub.cuh>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -357,6 +356,7 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 }  // namespace
 
 tp_status tp_launch_expand_faces(tp_ctx* ctx) {
+    TpRange nvtx_range("tp_launch_expand_faces");
     const int64_t n = ctx->nt_tri * ctx->quad.k;
     k_expand_faces<<<blocks_for(n, 256), 256, 0, ctx->stream>>>(ctx->F_tri, ctx->nt_tri, ctx->quad.k, ctx->F);
     ++ctx->nlaunch;
@@ -365,6 +365,7 @@ tp_status tp_launch_expand_faces(tp_ctx* ctx) {
 }
 
 tp_status tp_launch_tri_data(tp_ctx* ctx) {
+    TpRange nvtx_range("tp_launch_tri_data");
     const int64_t nt = ctx->nt;
     k_tri_data<<<blocks_for(nt, 256), 256, 0, ctx->stream>>>(ctx->V64, ctx->F, nt, ctx->nv, ctx->x64, ctx->nu64,
                                                              ctx->w64, ctx->derr, ctx->quad);
@@ -379,27 +380,19 @@ tp_status tp_launch_tri_data(tp_ctx* ctx) {
 }
 
 tp_status tp_launch_morton_order(tp_ctx* ctx, int morton_bits) {
+    TpRange nvtx_range("tp_launch_morton_order");
     const int64_t nt = ctx->nt;
     k_morton<<<blocks_for(nt, 256), 256, 0, ctx->stream>>>(ctx->x64, nt, ctx->bounds, morton_bits / 3, ctx->codes,
                                                            ctx->idx_tmp);
     ++ctx->nlaunch;
-    size_t need = 0;
-    cub::DeviceRadixSort::SortPairs(nullptr, need, ctx->codes, ctx->codes_sorted, ctx->idx_tmp, ctx->perm, (int)nt, 0,
-                                    morton_bits, ctx->stream);
-    if (need > ctx->sort_tmp_bytes) {
-        tp_free(ctx, ctx->sort_tmp);
-        ctx->sort_tmp = nullptr;
-        TP_TRY(tp_alloc(ctx, &ctx->sort_tmp, need));
-        ctx->sort_tmp_bytes = need;
-    }
-    size_t have = ctx->sort_tmp_bytes;
-    TP_CU(cub::DeviceRadixSort::SortPairs(ctx->sort_tmp, have, ctx->codes, ctx->codes_sorted, ctx->idx_tmp, ctx->perm,
-                                          (int)nt, 0, morton_bits, ctx->stream));
+    // stable sort of (code, T) by code: ties keep ascending T, i.e. the order of key = code << 32 | T
+    TP_TRY(tp_sort_pairs_u32(ctx, ctx->codes, ctx->idx_tmp, ctx->codes_sorted, ctx->perm, nt, morton_bits));
     TP_CU(cudaGetLastError());
     return TP_OK;
 }
 
 tp_status tp_launch_sorted_soa(tp_ctx* ctx) {
+    TpRange nvtx_range("tp_launch_sorted_soa");
     k_sorted_soa<<<blocks_for(ctx->ntp, 256), 256, 0, ctx->stream>>>(
         ctx->x64, ctx->nu64, ctx->w64, ctx->F, ctx->perm, ctx->center, ctx->nt, ctx->ntp, ctx->iperm, ctx->soa,
         ctx->src, ctx->Fs);
@@ -414,22 +407,14 @@ tp_status tp_ensure_sorted(tp_ctx* ctx) {
 }
 
 tp_status tp_build_v2t(tp_ctx* ctx) {
+    TpRange nvtx_range("tp_build_v2t");
     const int64_t nt = ctx->nt, nv = ctx->nv;
     int32_t* cnt = ctx->idx_tmp;  // reuse as counter scratch (nt >= nv/2 for closed meshes; sized max)
     TP_CU(cudaMemsetAsync(ctx->v2t_off, 0, sizeof(int32_t) * (nv + 1), ctx->stream));
     k_v2t_count<<<blocks_for(3 * nt, 256), 256, 0, ctx->stream>>>(ctx->F, nt, nv, ctx->v2t_off + 1, ctx->derr);
     ++ctx->nlaunch;
-    size_t need = 0;
-    cub::DeviceScan::InclusiveSum(nullptr, need, ctx->v2t_off + 1, ctx->v2t_off + 1, (int)nv, ctx->stream);
-    if (need > ctx->sort_tmp_bytes) {
-        tp_free(ctx, ctx->sort_tmp);
-        ctx->sort_tmp = nullptr;
-        TP_TRY(tp_alloc(ctx, &ctx->sort_tmp, need));
-        ctx->sort_tmp_bytes = need;
-    }
-    size_t have = ctx->sort_tmp_bytes;
-    TP_CU(cub::DeviceScan::InclusiveSum(ctx->sort_tmp, have, ctx->v2t_off + 1, ctx->v2t_off + 1, (int)nv,
-                                        ctx->stream));
+    uint32_t* off = reinterpret_cast<uint32_t*>(ctx->v2t_off + 1);
+    TP_TRY(tp_scan_u32(ctx, off, off, nv, true, nullptr));
     TP_CU(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nv, ctx->stream));
     k_v2t_fill<<<blocks_for(3 * nt, 256), 256, 0, ctx->stream>>>(ctx->F, nt, nv, ctx->v2t_off, cnt, ctx->v2t);
     ++ctx->nlaunch;
@@ -535,6 +520,7 @@ __global__ void k_xmask_diag(const int32_t* __restrict__ mlist, int n_masked, co
 }
 
 tp_status tp_build_exclusion_bits(tp_ctx* ctx) {
+    TpRange nvtx_range("tp_build_exclusion_bits");
     const int nsup = (int)ctx->nsup;
     const int nm = (int)ctx->n_masked;
     const int64_t nbits = (int64_t)nsup * nsup;
@@ -565,16 +551,8 @@ tp_status tp_build_exclusion_bits(tp_ctx* ctx) {
     int32_t* xcount = ctx->xcount;
     k_xeff<<<blocks_for(nm + 1, 256), 256, 0, ctx->stream>>>(ctx->mlist, nm, nsup, ctx->bmask, ctx->xeff, xcount);
     ctx->nlaunch += 2;
-    size_t need = 0;
-    cub::DeviceScan::ExclusiveSum(nullptr, need, xcount, ctx->xbase, nm + 1, ctx->stream);
-    if (need > ctx->sort_tmp_bytes) {
-        tp_free(ctx, ctx->sort_tmp);
-        ctx->sort_tmp = nullptr;
-        TP_TRY(tp_alloc(ctx, &ctx->sort_tmp, need));
-        ctx->sort_tmp_bytes = need;
-    }
-    size_t have = ctx->sort_tmp_bytes;
-    TP_CU(cub::DeviceScan::ExclusiveSum(ctx->sort_tmp, have, xcount, ctx->xbase, nm + 1, ctx->stream));
+    TP_TRY(tp_scan_u32(ctx, reinterpret_cast<const uint32_t*>(xcount), reinterpret_cast<uint32_t*>(ctx->xbase),
+                       nm + 1, false, nullptr));
     int32_t total = 0;
     TP_CU(cudaMemcpyAsync(&total, ctx->xbase + nm, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
     TP_CU(cudaStreamSynchronize(ctx->stream));
@@ -601,6 +579,7 @@ tp_status tp_build_exclusion_bits(tp_ctx* ctx) {
 }
 
 tp_status tp_launch_flagged(tp_ctx* ctx, bool topology) {
+    TpRange nvtx_range("tp_launch_flagged");
     const int nsup = (int)ctx->nsup;
     const int64_t nbits = (int64_t)nsup * nsup;
     if (topology) {
@@ -637,16 +616,9 @@ tp_status tp_launch_flagged(tp_ctx* ctx, bool topology) {
         // a fixed order of the masked items (the exclusion bits are indexed by it)
         const int nm = (int)ctx->n_masked;
         int32_t* tmp = ctx->idx_tmp;  // nm <= nt
-        size_t need = 0;
-        cub::DeviceRadixSort::SortKeys(nullptr, need, ctx->mlist, tmp, nm, 0, 32, ctx->stream);
-        if (need > ctx->sort_tmp_bytes) {
-            tp_free(ctx, ctx->sort_tmp);
-            ctx->sort_tmp = nullptr;
-            TP_TRY(tp_alloc(ctx, &ctx->sort_tmp, need));
-            ctx->sort_tmp_bytes = need;
-        }
-        size_t have = ctx->sort_tmp_bytes;
-        TP_CU(cub::DeviceRadixSort::SortKeys(ctx->sort_tmp, have, ctx->mlist, tmp, nm, 0, 32, ctx->stream));
+        // entries are I << 16 | J with I, J < 2^15: non-negative, so their unsigned order is theirs
+        TP_TRY(tp_sort_pairs_u32(ctx, reinterpret_cast<const uint32_t*>(ctx->mlist), nullptr,
+                                 reinterpret_cast<uint32_t*>(tmp), nullptr, nm, 31));
         TP_CU(cudaMemcpyAsync(ctx->mlist, tmp, sizeof(int32_t) * nm, cudaMemcpyDeviceToDevice, ctx->stream));
     }
     if (topology) TP_TRY(tp_build_exclusion_bits(ctx));
@@ -662,11 +634,12 @@ tp_status tp_ensure_flagged(tp_ctx* ctx) {
 }
 
 namespace {
-// number of distinct S != T sharing a vertex with T (ordered excluded pairs)
+// Ordered excluded pairs: out[0] counts the distinct S != T sharing a vertex
+// with T, out[1] those sharing an edge (two or more vertices), summed over T.
 __global__ void k_count_excluded(const int32_t* __restrict__ F, const int32_t* __restrict__ off,
                                  const int32_t* __restrict__ v2t, int64_t nt, unsigned long long* __restrict__ out) {
     int64_t T = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    unsigned long long cnt = 0;
+    unsigned long long cnt = 0, cnt_edge = 0;
     if (T < nt) {
         for (int c = 0; c < 3; ++c) {
             int32_t v = F[3 * T + c];
@@ -679,23 +652,36 @@ __global__ void k_count_excluded(const int32_t* __restrict__ F, const int32_t* _
                     int32_t v2 = F[3 * T + c2];
                     seen = (F[3 * S] == v2) || (F[3 * S + 1] == v2) || (F[3 * S + 2] == v2);
                 }
-                if (!seen) ++cnt;
+                if (seen) continue;
+                ++cnt;
+                int k = 0;
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) k += F[3 * T + i] == F[3 * S + j];
+                if (k >= 2) ++cnt_edge;
             }
         }
     }
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, cnt);
+    for (int o = 16; o > 0; o >>= 1) {
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        cnt_edge += __shfl_xor_sync(0xffffffffu, cnt_edge, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (cnt) atomicAdd(out, cnt);
+        if (cnt_edge) atomicAdd(out + 1, cnt_edge);
+    }
 }
 }  // namespace
 
 tp_status tp_count_excluded(tp_ctx* ctx) {
-    unsigned long long* d = reinterpret_cast<unsigned long long*>(ctx->scalar + 6);
-    TP_CU(cudaMemsetAsync(d, 0, 8, ctx->stream));
+    TpRange nvtx_range("tp_count_excluded");
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(ctx->scalar + 8);
+    TP_CU(cudaMemsetAsync(d, 0, 16, ctx->stream));
     k_count_excluded<<<blocks_for(ctx->nt, 256), 256, 0, ctx->stream>>>(ctx->F, ctx->v2t_off, ctx->v2t, ctx->nt, d);
     ++ctx->nlaunch;
-    unsigned long long h = 0;
-    TP_CU(cudaMemcpyAsync(&h, d, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    unsigned long long h[2] = {0, 0};
+    TP_CU(cudaMemcpyAsync(h, d, 16, cudaMemcpyDeviceToHost, ctx->stream));
     TP_CU(cudaStreamSynchronize(ctx->stream));
-    ctx->n_excluded_ordered = (int64_t)h;
+    ctx->n_excluded_ordered = (int64_t)h[0];
+    ctx->n_excluded_edge_ordered = (int64_t)h[1];
     return TP_OK;
 }

@@ -59,3 +59,27 @@ def test_oracle_library_loads(oracle_mod):
 
     lib = ctypes.CDLL(oracle_mod._SO)
     assert hasattr(lib, "or_energy")
+
+
+def test_noalloc_binding_rejects_wrong_dtypes_on_the_host():
+    """The allocation-free entry point reads V as [nv][3] FP64 and F as [nt][3] int32 on
+    the device; the binding must refuse other dtypes and shapes before any call."""
+    torch = pytest.importorskip("torch")
+    from paper_2509_22110_gb300 import _tp
+
+    V = torch.zeros((4, 3), dtype=torch.float64)
+    F = torch.zeros((2, 3), dtype=torch.int32)
+    e = torch.zeros(1, dtype=torch.float64)
+    g = torch.zeros((4, 3), dtype=torch.float64)
+    with pytest.raises(TypeError):
+        _tp.tp_gradient_direct_noalloc(V.float(), F, e, g)
+    with pytest.raises(TypeError):
+        _tp.tp_gradient_direct_noalloc(V, F.long(), e, g)
+    with pytest.raises(TypeError):
+        _tp.tp_gradient_direct_noalloc(V, F, e, g.float())
+    with pytest.raises(ValueError):
+        _tp.tp_gradient_direct_noalloc(V, F, e, g[:3])
+    with pytest.raises(ValueError):
+        _tp.tp_gradient_direct_noalloc(V[:, :2].contiguous(), F, e, g)
+    with pytest.raises(ValueError):  # host tensors: the entry point takes device pointers only
+        _tp.tp_gradient_direct_noalloc(V, F, e, g)

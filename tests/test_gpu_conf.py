@@ -98,6 +98,9 @@ def test_conf_errors(tp, ctx):
     with pytest.raises(tp.TPError) as ei:
         tp.tp_conf_gradient(ctx, np.zeros_like(V), tp.tp_params_default(mode=tp.TP_BH, theta=0.5))
     assert ei.value.status == tp._tp.TP_E_ARG
+    with pytest.raises(tp.TPError) as ei:  # compensated FP32 sums exist for the direct self-energy only
+        tp.tp_conf_gradient(ctx, np.zeros_like(V), tp.tp_params_default(prec=tp._tp.TP_F32_KAHAN))
+    assert ei.value.status == tp._tp.TP_E_ARG
     bad = F.copy()
     bad[3, 1] = V.shape[0] + 5
     with pytest.raises(tp.TPError) as ei:

@@ -77,6 +77,29 @@ def test_tree_bitexact(tp, ctx, oracle_mod, name, leaf, bits):
     assert np.array_equal(g["box"], box)
 
 
+def _sort_cases():
+    rng = np.random.default_rng(21)
+    for n in (1, 2, 31, 2047, 2048, 2049, 100003):
+        for bits in (30, 8, 6, 31, 32):
+            hi = 1 << bits
+            yield n, bits, rng.integers(0, hi, n, dtype=np.uint64).astype(np.uint32)  # mostly distinct
+            yield n, bits, rng.integers(0, min(hi, 37), n, dtype=np.uint64).astype(np.uint32)  # many ties
+    yield 5000, 30, np.full(5000, 12345, dtype=np.uint32)  # all equal
+    yield 5000, 30, np.arange(5000, 0, -1, dtype=np.uint32)  # reversed
+
+
+def test_key_sort_and_compaction(tp, ctx):
+    """The tree build's own stable radix sort (ties keep input order: the order of the
+    keys code << 32 | index) and leaf compaction against numpy on adversarial inputs."""
+    for n, bits, keys in _sort_cases():
+        ko, po, co = tp._tp.tp_debug_sort(ctx, keys, bits, compact=True)
+        want = np.argsort(keys, kind="stable")
+        assert np.array_equal(po, want), (n, bits)
+        assert np.array_equal(ko, keys[want]), (n, bits)
+        k32 = keys.view(np.int32)
+        assert np.array_equal(co, k32[k32 >= 0]), (n, bits)
+
+
 def test_tree_single_triangle(tp, ctx, oracle_mod):
     V, F = meshgen.icosahedron()
     F = np.ascontiguousarray(F[:1])
