@@ -33,7 +33,8 @@ _u8 = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
 
 def build(force: bool = False) -> str:
     """Compile ``oracle.c`` (and the MLP reference) into ``liboracle.so``."""
-    srcs = [os.path.join(_HERE, f) for f in ("oracle.c", "oracle_mlp.c", "oracle_conf.c", "oracle_quad.c") if os.path.exists(os.path.join(_HERE, f))]
+    srcs = [os.path.join(_HERE, f) for f in ("oracle.c", "oracle_mlp.c", "oracle_conf.c", "oracle_quad.c",
+                                              "oracle_dt.c") if os.path.exists(os.path.join(_HERE, f))]
     if not force and os.path.exists(_SO) and all(os.path.getmtime(_SO) >= os.path.getmtime(s) for s in srcs + [os.path.join(_HERE, "oracle.h")]):
         return _SO
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared", "-std=c11",
@@ -64,6 +65,10 @@ def _load():
     lib.or_moments.argtypes = [_d, _i32, _d, _d, _d, i64, _i32, _i32, _i32, _d, _d]
     lib.or_bh_accum.argtypes = [_d, _d, _d, _i32, i64, _i32, _i32, _i32, _i32, _i32, _i32, i64, _d, _d, dbl, i32,
                                 dbl, dbl, i32, _d, _d, _d, C.POINTER(C.c_int64), C.POINTER(C.c_int64), i32]
+    lib.or_dt_accum.argtypes = [_d, _d, _d, _i32, i64, _i32, _i32, _i32, _i32, _i32, _i32, _d, _d, dbl, i32, dbl,
+                                dbl, i32, _d, _d, _d, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                C.POINTER(C.c_int64)]
+    lib.or_dt_accum.restype = dbl
     lib.or_conf_energy.argtypes = [_d, _d, _d, i64, _d, _d, i64, dbl, dbl, dbl, i32]
     lib.or_conf_energy.restype = dbl
     lib.or_conf_accum.argtypes = [_d, _d, _d, i64, _d, _d, i64, dbl, dbl, _d, _d, _d, i32]
@@ -278,6 +283,37 @@ def bh_gradient(V, F, theta, q=6.0, p=12.0, c=1.0, adj=0, morton_bits=30, leaf_s
 
 # ---------------------------------------------------------------- learned far field
 MLP_NI, MLP_NH, MLP_NO = 24, 64, 7
+
+
+def dt_accum(V, F, tree, mom, box, theta, q=6.0, p=12.0, adj=0, soa=None):
+    """Cluster-cluster (dual-tree) Barnes-Hut form (see or_dt_accum): per-triangle
+    derivatives (without c), the energy (without c) and the pair counts."""
+    lib = _load()
+    V, F = _prep(V, F)
+    x, nu, w = soa if soa is not None else tri_data(V, F)
+    n = tree["n"]
+    gw = np.zeros(n)
+    gnu = np.zeros((n, 3))
+    gx = np.zeros((n, 3))
+    nn, nf, nr = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+    left = np.ascontiguousarray(np.concatenate([tree["left"], [-1]]).astype(np.int32))
+    right = np.ascontiguousarray(np.concatenate([tree["right"], [-1]]).astype(np.int32))
+    E = lib.or_dt_accum(np.ascontiguousarray(x), np.ascontiguousarray(nu), np.ascontiguousarray(w), F, n,
+                        tree["perm"], left, right, tree["parent"], tree["first"], tree["last"],
+                        np.ascontiguousarray(mom), np.ascontiguousarray(box), theta, tree["leaf_size"], q, p, adj,
+                        gw, gnu, gx, C.byref(nn), C.byref(nf), C.byref(nr))
+    return E, gw, gnu, gx, {"near_pairs": nn.value, "far_pairs": nf.value, "far_represented": nr.value}
+
+
+def dt_gradient(V, F, theta, q=6.0, p=12.0, c=1.0, adj=0, morton_bits=30, leaf_size=16):
+    """(Phi_DT, grad_DT, info) of the cluster-cluster form with prefactor c."""
+    x, nu, w = tri_data(V, F)
+    tree = lbvh(x, morton_bits, leaf_size)
+    mom, box = moments(V, F, tree, soa=(x, nu, w))
+    E, gw, gnu, gx, info = dt_accum(V, F, tree, mom, box, theta, q, p, adj, soa=(x, nu, w))
+    grad = adjoint(V, F, gw, gnu, gx, c)
+    info["phi_from_weights"] = 0.5 * c * float(np.sum(w * gw))
+    return c * E, grad, info
 
 
 def mlp_nparam():

@@ -58,6 +58,16 @@ void or_bh_accum(const double* x, const double* nu, const double* w, const int32
                  double q, double p, int adj, double* gw, double* gnu, double* gx,
                  int64_t* n_near_pairs, int64_t* n_far_terms, int nthreads);
 
+/* Cluster-cluster (dual-tree) Barnes-Hut form (oracle_dt.c): returns the
+ * energy without c; gw/gnu/gx are overwritten with the per-triangle
+ * derivatives (without c).  parent[2n-1] from or_lbvh. */
+int or_dt_admissible(const double* bA, const double* mA, const double* bB, const double* mB, double theta);
+double or_dt_accum(const double* x, const double* nu, const double* w, const int32_t* F, int64_t n,
+                   const int32_t* perm, const int32_t* left, const int32_t* right, const int32_t* parent,
+                   const int32_t* first, const int32_t* last, const double* mom, const double* box, double theta,
+                   int leaf_size, double q, double p, int adj, double* gw, double* gnu, double* gx,
+                   int64_t* n_near_pairs, int64_t* n_far_pairs, int64_t* n_far_represented);
+
 /* Confinement energy, Eq. (TPConf), Sec. 2.2 (oracle_conf.c): evolving surface
  * (x, nu, w)[nt], fixed confining surface (centroids y, areas a)[nk]. */
 double or_conf_energy(const double* x, const double* nu, const double* w, int64_t nt, const double* y,
