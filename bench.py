@@ -70,8 +70,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sh_l7", choices=sorted(WORKLOADS))
-    ap.add_argument("--mode", default="direct", choices=["direct", "bh", "learned", "conf"],
-                    help="conf: the confinement energy (Eq. TPConf) of the conf_l7 workload")
+    ap.add_argument("--mode", default="direct", choices=["direct", "bh", "learned", "dual", "conf"],
+                    help="bh: inner integral clustered (Barnes-Hut); dual: both integrals clustered (cluster-cluster); "
+                         "conf: the confinement energy (Eq. TPConf) of the conf_l7 workload")
     ap.add_argument("--far-model", default=DEFAULT_FAR_MODEL,
                     help="trained far-field model (learned mode; default: the packaged level-7 model)")
     ap.add_argument("--theta", type=float, default=0.25)
@@ -423,7 +424,7 @@ def main():
     nt, nv = F.shape[0], V.shape[0]
     stream = torch.cuda.Stream(dev)
     ctx = tp.tp_create(local, stream.cuda_stream)
-    mode = {"direct": tp.TP_DIRECT, "bh": tp.TP_BH, "learned": tp.TP_LEARNED}[args.mode]
+    mode = {"direct": tp.TP_DIRECT, "bh": tp.TP_BH, "learned": tp.TP_LEARNED, "dual": tp.TP_BH_DUAL}[args.mode]
     if mode == tp.TP_LEARNED:
         if not args.far_model or not os.path.exists(args.far_model):
             raise SystemExit("--mode learned needs --far-model (python -m paper_2509_22110_gb300.far_train)")

@@ -51,7 +51,14 @@ typedef enum {
     TP_E_MODEL = 7      /* malformed far-field model file                                */
 } tp_status;
 
-typedef enum { TP_DIRECT = 0, TP_BH = 1, TP_LEARNED = 2 } tp_mode;
+/* TP_DIRECT: every admitted pair exactly.  TP_BH: the inner integral
+ * clustered (Sec. 3.2), cluster monopoles per target.  TP_LEARNED: TP_BH with
+ * the network's correction of the far terms.  TP_BH_DUAL: both integrals
+ * clustered (the cluster-cluster scheme Sec. 3.2 compares with): node pairs
+ * with vertex boxes apart and max(diag_A, diag_B) < theta |X_A - X_B| take
+ * the monopole of both orderings, the gradient includes the derivatives
+ * through the cluster moments.  The clustered forms need tp_tree_build. */
+typedef enum { TP_DIRECT = 0, TP_BH = 1, TP_LEARNED = 2, TP_BH_DUAL = 3 } tp_mode;
 typedef enum { TP_F32_F64ACC = 0, TP_F32_KAHAN = 1, TP_F64 = 2 } tp_prec;
 enum { TP_DTYPE_F32 = 0, TP_DTYPE_F64 = 1 };
 

@@ -21,6 +21,7 @@ from __future__ import annotations
 from . import _tp
 from ._tp import (  # noqa: F401
     TP_BH,
+    TP_BH_DUAL,
     TP_DIRECT,
     TP_F32_F64ACC,
     TP_F64,

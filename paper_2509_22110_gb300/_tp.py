@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libtp.so")
 _lib = None
 
 TP_OK, TP_E_ARG, TP_E_CUDA, TP_E_STATE, TP_E_NONFINITE, TP_E_TIMEOUT, TP_E_OOM, TP_E_MODEL = range(8)
-TP_DIRECT, TP_BH, TP_LEARNED = 0, 1, 2
+TP_DIRECT, TP_BH, TP_LEARNED, TP_BH_DUAL = 0, 1, 2, 3
 TP_F32_F64ACC, TP_F32_KAHAN, TP_F64 = 0, 1, 2
 TP_DTYPE_F32, TP_DTYPE_F64 = 0, 1
 TP_DEVICE_PTR = 0x1

@@ -108,7 +108,7 @@ tp_status check_params(tp_ctx* ctx, const tp_params* prm) {
     if (!prm) return tp_set_err(ctx, TP_E_ARG, "params is NULL");
     if (!((prm->q == 6 && prm->p == 12) || (prm->q == 8 && prm->p == 16)))
         return tp_set_err(ctx, TP_E_ARG, "unsupported exponents q=%d p=%d (supported: 6/12, 8/16)", prm->q, prm->p);
-    if (prm->mode < TP_DIRECT || prm->mode > TP_LEARNED) return tp_set_err(ctx, TP_E_ARG, "bad mode %d", prm->mode);
+    if (prm->mode < TP_DIRECT || prm->mode > TP_BH_DUAL) return tp_set_err(ctx, TP_E_ARG, "bad mode %d", prm->mode);
     if (prm->prec < TP_F32_F64ACC || prm->prec > TP_F64) return tp_set_err(ctx, TP_E_ARG, "bad prec %d", prm->prec);
     if (!std::isfinite(prm->scale)) return tp_set_err(ctx, TP_E_ARG, "scale is not finite");
     if (prm->mode != TP_DIRECT && !(prm->theta >= 0.0 && std::isfinite(prm->theta)))
@@ -202,6 +202,18 @@ void tp_drop_mesh_state(tp_ctx* ctx) {
     ctx->far_xcap = 0;
     free_ptr(ctx, ctx->win_bnd);
     ctx->win_bnd_cap = 0;
+    free_ptr(ctx, ctx->dt_front[0]);
+    free_ptr(ctx, ctx->dt_front[1]);
+    free_ptr(ctx, ctx->dt_far);
+    free_ptr(ctx, ctx->dt_near);
+    ctx->dt_cap = ctx->dt_far_cap = ctx->dt_near_cap = 0;
+    free_ptr(ctx, ctx->dt_off);
+    free_ptr(ctx, ctx->dt_cursor);
+    free_ptr(ctx, ctx->dt_node2leaf);
+    free_ptr(ctx, ctx->dt_G);
+    free_ptr(ctx, ctx->dt_P);
+    free_ptr(ctx, ctx->dt_list);
+    ctx->dt_leaf_cap = ctx->dt_node_cap = ctx->dt_list_cap = 0;
     free_ptr(ctx, ctx->sort_hist);
     free_ptr(ctx, ctx->sort_ktmp);
     free_ptr(ctx, ctx->sort_vtmp);
@@ -618,6 +630,8 @@ static tp_status run_eval(tp_ctx* ctx, const tp_params* prm, bool want_grad, voi
         ctx->stats.tile_pairs_masked = ctx->n_masked;
         ctx->stats.tile_pairs_precise = ctx->n_precise;
         ctx->stats.kernel_pairs = tp_direct_timed_pairs(ctx);  // the timed (non-masked) launch
+    } else if (prm->mode == TP_BH_DUAL) {
+        TP_TRY(tp_launch_dual(ctx, prm));
     } else {
         TP_TRY(tp_launch_bh(ctx, prm, prm->mode == TP_LEARNED));
     }

@@ -449,10 +449,17 @@ __device__ __forceinline__ Item fetch_item(const DirectArgs& A, int* s_item) {
 #define TP_GRAD_RED 1  // per-source warp reduction: 0 shuffle butterfly, 1 transposed through shared memory
 #endif
 // Transposed reduction of the source partials (TP_GRAD_RED 1): per warp two
-// slabs of 16 rows x 32 floats (row = component + 8 x source of a 2-source
-// step, column = lane), swizzled so that both the row-wise stores and the
-// column-wise 16-byte loads are free of bank conflicts.
-constexpr int SLAB_FLOATS = 16 * 32;
+// slabs of 16 rows (row = component + 8 x source of a 2-source step) of 32
+// lanes' values.  TP_SLAB_PAD 1: rows padded to 36 floats, so that row r's
+// 16-byte groups fall on banks 4r + 4j (mod 32): the stores of one row by 32
+// lanes and the 16-byte loads of 8 lanes reading rows r..r+7 are free of bank
+// conflicts, and the store addresses are one base plus immediates.
+// TP_SLAB_PAD 0: unpadded rows with the column XOR-swizzled by the row.
+#ifndef TP_SLAB_PAD
+#define TP_SLAB_PAD 0
+#endif
+constexpr int SLAB_ROW = TP_SLAB_PAD ? 36 : 32;
+constexpr int SLAB_FLOATS = 16 * SLAB_ROW;
 template <bool MASKQ>
 struct GradShape {
     static constexpr int W = MASKQ ? 12 : TP_GRAD_W;
@@ -491,9 +498,10 @@ __device__ __forceinline__ void src_step(const TgtPair (&tp)[NP], Acc8 (&at)[NP]
 // One source of a precise/fast item with the transposed reduction: prefetch
 // the next source record, the NP packed evaluations, then the lane's 8 source
 // partials (both halves added) stored into rows row0..row0+7 of the slab.
-// Row r, lane l is stored at r * 32 + (l ^ ((r & 7) << 2)): each store of a row
-// covers the 32 banks once, and a load of 16 bytes by 8 lanes reading rows
-// r..r+7 at one logical column covers them once as well.
+// Row r, lane l is stored at r * 36 + l (padded rows) or r * 32 + (l ^ ((r & 7)
+// << 2)) (swizzled rows): either way each store of a row covers the 32 banks
+// once, and a load of 16 bytes by 8 lanes reading rows r..r+7 at one logical
+// column covers them once as well.
 template <int Q, int KIND, int NP>
 __device__ __forceinline__ void src_step_slab(const TgtPair (&tp)[NP], Acc8 (&at)[NP], const SrcRec& cur,
                                               SrcRec& nxt, const float* nrec, bool has_next, float* slab_row0,
@@ -506,7 +514,10 @@ __device__ __forceinline__ void src_step_slab(const TgtPair (&tp)[NP], Acc8 (&at
 #pragma unroll
     for (int P = 1; P < NP; ++P) pair_grad<Q, KIND, false>(tp[P], cur, at[P], as, one);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) slab_row0[k * 32 + (lane ^ (k << 2))] = as.v[k].x + as.v[k].y;
+    for (int k = 0; k < 8; ++k) {
+        if (TP_SLAB_PAD) slab_row0[k * SLAB_ROW + lane] = as.v[k].x + as.v[k].y;
+        else slab_row0[k * 32 + (lane ^ (k << 2))] = as.v[k].x + as.v[k].y;
+    }
 }
 
 // Column sums of one slab (16 rows: 8 components x 2 sources) over the 32
@@ -516,8 +527,8 @@ __device__ __forceinline__ void src_step_slab(const TgtPair (&tp)[NP], Acc8 (&at
 // the order of the warp's partial array) to out[0..15].
 __device__ __forceinline__ void slab_reduce(const float* slab, float* out, int lane) {
     const int r = lane & 15, h = lane >> 4;
-    const float* row = slab + r * 32;
-    const int xr = (r & 7) << 2;
+    const float* row = slab + r * SLAB_ROW;
+    const int xr = TP_SLAB_PAD ? 0 : (r & 7) << 2;
     float v = 0.f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -767,8 +778,8 @@ __device__ __forceinline__ bool grad_item(const DirectArgs& A, ChunkPipe& pipe, 
                 float* sw = slab + ((s >> 1) & 1) * SLAB_FLOATS;
                 if (s > 0) slab_reduce(slab + (((s >> 1) - 1) & 1) * SLAB_FLOATS, wacc + (s - 2) * TP_NACC, lane);
                 src_step_slab<Q, KU, NP>(tp, at, ra, rb, cb + (s + 1) * TP_SRCW, true, sw, lane);
-                src_step_slab<Q, KU, NP>(tp, at, rb, ra, cb + (s + 2) * TP_SRCW, s + 2 < TP_CHUNK, sw + 8 * 32,
-                                         lane);
+                src_step_slab<Q, KU, NP>(tp, at, rb, ra, cb + (s + 2) * TP_SRCW, s + 2 < TP_CHUNK,
+                                         sw + 8 * SLAB_ROW, lane);
                 if ((s & 30) == 30) fold_energy<NP>(at, e64);
                 __syncwarp();
             }

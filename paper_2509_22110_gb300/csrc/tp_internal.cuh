@@ -227,6 +227,20 @@ struct tp_ctx {
     tp_far_run* near_runs = nullptr;
     unsigned long long* near_count = nullptr;  // [0] entries, [1] runs listed (may exceed the capacities), [2] work counter
     int64_t near_cap = 0, nrun_cap = 0;
+    // cluster-cluster form (tp_dual.cu): traversal frontier, far and near node
+    // pairs, per-leaf partner lists, per-node derivative sums
+    unsigned long long* dt_cnt = nullptr;  // [8] counters of the traversal and the passes
+    int2* dt_front[2] = {nullptr, nullptr};
+    int2* dt_far = nullptr;
+    int2* dt_near = nullptr;
+    int64_t dt_cap = 0, dt_far_cap = 0, dt_near_cap = 0;
+    uint32_t* dt_off = nullptr;     // [nleaves + 1] partner-list offsets
+    uint32_t* dt_cursor = nullptr;  // [nleaves + 1]
+    int32_t* dt_node2leaf = nullptr;  // [2n - 1]
+    double* dt_G = nullptr;         // [2n - 1][7] far-field derivatives per node
+    double* dt_P = nullptr;         // [2n - 1][7] the same divided by the node area, weight term
+    int2* dt_list = nullptr;        // partner leaves as (first member, count)
+    int64_t dt_leaf_cap = 0, dt_node_cap = 0, dt_list_cap = 0;
 
     tp_stats stats{};
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -344,6 +358,10 @@ tp_status tp_launch_check_finite(tp_ctx* ctx);
 tp_status tp_launch_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits);
 // tp_bh.cu
 tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned);
+// cluster-cluster (dual-tree) form into ctx->acc (tp_dual.cu)
+tp_status tp_launch_dual(tp_ctx* ctx, const tp_params* prm);
+tp_status tp_dual_lists(tp_ctx* ctx, int64_t cap_front, int64_t cap_far, int64_t cap_near);
+tp_status tp_dual_leaf_buffers(tp_ctx* ctx, int64_t nleaves, int64_t nn, int64_t entries);
 tp_status tp_launch_bh_sample(tp_ctx* ctx, double theta, uint32_t keep_u, uint64_t seed, int2* out, int64_t cap,
                               int32_t* counter);
 // tp_mlp.cu
