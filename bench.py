@@ -37,18 +37,20 @@ METRIC = "TP energy+grad ms/eval & pair-interactions/s at 327k tris; rel err vs 
 UNIT = "pair-interactions/s"
 # Algorithmic FP32 work per unordered admitted pair of the energy+gradient
 # pair function (both orderings, shared subexpressions once), counted from
-# its expression DAG with an FMA as 2 flops: 24 FMA + 28 FMUL/FADD = 76 flops
-# (the hi/lo cancellation correction and the reduction overhead not counted).
+# its expression DAG with an FMA as 2 flops: 27 FMA + 22 FMUL/FADD = 76 flops
+# in 49 operations (the hi/lo cancellation correction and the reduction
+# overhead not counted).
 FLOPS_PER_UNORDERED_PAIR = 76
 # The same count for one (target, confining triangle) pair of the confinement
-# energy+gradient (one ordering, target side only): 11 FMA + 16 FMUL/FADD = 38
-# flops (the hi/lo cancellation correction, 6 FADD, not counted).
-FLOPS_PER_CONF_PAIR = 38
+# energy+gradient (one ordering, target side only): 11 FMA + 14 FMUL/FADD = 36
+# flops in 25 operations (the hi/lo cancellation correction, 6 FADD, not
+# counted; the -p/q factor of Gx is applied once per item, not per pair).
+FLOPS_PER_CONF_PAIR = 36
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per launch of the dominant kernel on the default
 # workload, from the one-pass ncu capture summarised in
 # profiles/k_pairs_grad_traffic_sh_l7.md (null it when that kernel changes).
-NCU_TRAFFIC_BYTES = 61.01e6
+NCU_TRAFFIC_BYTES = 60.61e6
 
 # far-field model trained by paper_2509_22110_gb300.far_train (command in the design notes)
 DEFAULT_FAR_MODEL = os.path.join(ROOT, "paper_2509_22110_gb300", "far_model_l7.bin")

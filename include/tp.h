@@ -67,6 +67,8 @@ enum { TP_DTYPE_F32 = 0, TP_DTYPE_F64 = 1 };
 #define TP_POSITIONS_ONLY 0x2u  /* re-upload V only; keep faces and derived topology   */
 /* flags of tp_params */
 #define TP_EXCLUDE_EDGE 0x4u    /* exclude only pairs sharing an edge (default: a vertex) */
+#define TP_LEARNED_ENERGY 0x8u  /* TP_LEARNED: the network corrects the two energy channels only; U and
+                                   the force channels keep the monopole, so the gradient is TP_BH's */
 
 typedef struct {
     int32_t q, p;   /* exponents: q even, p even; supported (6,12) and (8,16)       */
@@ -74,7 +76,7 @@ typedef struct {
     int32_t mode;   /* tp_mode                                                      */
     double theta;   /* opening parameter of TP_BH / TP_LEARNED (Sec. 3.2)           */
     int32_t prec;   /* tp_prec                                                      */
-    uint32_t flags; /* TP_EXCLUDE_EDGE                                              */
+    uint32_t flags; /* TP_EXCLUDE_EDGE, TP_LEARNED_ENERGY                           */
 } tp_params;
 
 /* Fill *p with the defaults: q=6, p=12, scale=1, DIRECT, theta=0.25, F32_F64ACC. */

@@ -24,6 +24,7 @@ TP_DTYPE_F32, TP_DTYPE_F64 = 0, 1
 TP_DEVICE_PTR = 0x1
 TP_POSITIONS_ONLY = 0x2
 TP_EXCLUDE_EDGE = 0x4
+TP_LEARNED_ENERGY = 0x8
 
 STATUS_NAMES = {
     0: "TP_OK", 1: "TP_E_ARG", 2: "TP_E_CUDA", 3: "TP_E_STATE", 4: "TP_E_NONFINITE",

@@ -809,10 +809,13 @@ __global__ void k_run_keys(const tp_far_run* __restrict__ runs, int64_t nruns, i
 }
 
 
+// energy_only: the network's factors are applied to the two energy channels
+// only; U and the force channels keep the monopole (the gradient is then that
+// of plain Barnes-Hut).
 template <int Q>
 __global__ void __launch_bounds__(FAR_WARPS * 32) k_far(BHArgs A, const float* __restrict__ kf, int64_t w0,
                                                          int64_t w1, const int64_t* __restrict__ skey,
-                                                         const int32_t* __restrict__ sord) {
+                                                         const int32_t* __restrict__ sord, int energy_only) {
     __shared__ __align__(16) float s_rec[FAR_WARPS][32 * TP_SRCW];  // duplicated records of a batch
     __shared__ __align__(16) float s_fk[FAR_WARPS][32 * 8];         // channel factors of a batch
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -892,8 +895,13 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) k_far(BHArgs A, const float* _
                 d[4] = make_float4(q2.x, q2.x, q2.y, q2.y);  // nubar[2], area
                 // factors exp(y_c) = 1 + (exp(y_c) - 1); the network wrote exp(y_c) - 1
                 float4* f = reinterpret_cast<float4*>(fk + lane * 8);
-                f[0] = make_float4(1.f + k0.x, 1.f + k0.y, 1.f + k0.z, 1.f + k0.w);
-                f[1] = make_float4(1.f + k1.x, 1.f + k1.y, 1.f + k1.z, k1.w);
+                if (energy_only) {
+                    f[0] = make_float4(1.f + k0.x, 1.f + k0.y, 1.f, 1.f);
+                    f[1] = make_float4(1.f, 1.f, 1.f, k1.w);
+                } else {
+                    f[0] = make_float4(1.f + k0.x, 1.f + k0.y, 1.f + k0.z, 1.f + k0.w);
+                    f[1] = make_float4(1.f + k1.x, 1.f + k1.y, 1.f + k1.z, k1.w);
+                }
             }
             const unsigned fb = __ballot_sync(0xffffffffu, lane < nb && k1.w != 0.f);
             if (lane == 0) n_learn += (unsigned long long)__popc(fb) * (unsigned long long)cnt;
@@ -1228,12 +1236,13 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
                                                                 ctx->run_ord_s);
             TP_TRY(tp_launch_mlp_tc(ctx, A.wb, A.mbias, ctx->far_X, w1 - w0, ctx->far_kf, 0));
             TP_CU(cudaMemsetAsync(ctx->far_count + 2, 0, sizeof(unsigned long long), ctx->stream));
+            const int eonly = (prm->flags & TP_LEARNED_ENERGY) ? 1 : 0;
             if (prm->q == 6)
                 k_far<6><<<fblocks, FAR_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_kf, w0, w1, ctx->run_key_s,
-                                                                   ctx->run_ord_s);
+                                                                   ctx->run_ord_s, eonly);
             else
                 k_far<8><<<fblocks, FAR_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_kf, w0, w1, ctx->run_key_s,
-                                                                   ctx->run_ord_s);
+                                                                   ctx->run_ord_s, eonly);
             ctx->nlaunch += 2;
         }
         TP_CU(cudaGetLastError());
@@ -1246,6 +1255,28 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
     ctx->stats.far_pairs = (int64_t)h[2];
     ctx->stats.learned_terms = (int64_t)h[3];
     ctx->stats.far_rows = (int64_t)h_rows;
+    return TP_OK;
+}
+
+// The Barnes-Hut near-field kernel on given runs of (first member, count)
+// entries whose clusters have vertex boxes apart from their run's leaf (so no
+// exclusion test is needed): adds to ctx->acc with FP64 atomics.  counters[1]
+// holds the number of runs, counters[2] is the work counter (zeroed here).
+tp_status tp_launch_near_runs(tp_ctx* ctx, int q, const int2* list, int64_t list_len, const tp_far_run* runs,
+                              int64_t run_cap, unsigned long long* counters) {
+    BHArgs A = make_bh_args(ctx, 0.0, 0);
+    A.src = ctx->src;
+    A.near_list = const_cast<int2*>(list);
+    A.near_runs = const_cast<tp_far_run*>(runs);
+    A.near_count = counters;
+    A.near_cap = list_len;
+    A.nrun_cap = run_cap;
+    TP_CU(cudaMemsetAsync(counters + 2, 0, sizeof(unsigned long long), ctx->stream));
+    const unsigned nblocks = (unsigned)std::max(1, ctx->num_sms * 4);
+    if (q == 6) k_near<6><<<nblocks, NR_WARPS * 32, 0, ctx->stream>>>(A);
+    else k_near<8><<<nblocks, NR_WARPS * 32, 0, ctx->stream>>>(A);
+    ++ctx->nlaunch;
+    TP_CU(cudaGetLastError());
     return TP_OK;
 }
 

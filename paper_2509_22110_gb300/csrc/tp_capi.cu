@@ -213,7 +213,8 @@ void tp_drop_mesh_state(tp_ctx* ctx) {
     free_ptr(ctx, ctx->dt_G);
     free_ptr(ctx, ctx->dt_P);
     free_ptr(ctx, ctx->dt_list);
-    ctx->dt_leaf_cap = ctx->dt_node_cap = ctx->dt_list_cap = 0;
+    free_ptr(ctx, ctx->dt_runs);
+    ctx->dt_leaf_cap = ctx->dt_node_cap = ctx->dt_list_cap = ctx->dt_run_cap = 0;
     free_ptr(ctx, ctx->sort_hist);
     free_ptr(ctx, ctx->sort_ktmp);
     free_ptr(ctx, ctx->sort_vtmp);

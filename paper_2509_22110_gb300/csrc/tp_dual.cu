@@ -27,15 +27,27 @@
 //   k_dt_expand   one level of the recursion: every node pair of the
 //                 frontier is classified (far, near, or split into the next
 //                 frontier); lists grow by warp-aggregated atomics and the
-//                 host repeats the traversal with larger lists on overflow;
-//   k_dt_far      FP64 far terms, one thread per far pair, node derivatives
-//                 summed with FP64 atomics;
-//   k_dt_count/k_dt_fill  per cluster leaf, the list of its near partners
-//                 (both directions of each near pair) as (first member, count);
+//                 host repeats the traversal with larger lists on overflow.
+//                 The test reads the tree build's node records (FP64 centroid
+//                 quotients and diagonals, outward/inward-rounded FP32 boxes):
+//                 an FP32 test with a safety margin decides unless the case
+//                 is close, which goes to FP64 on the same quantities as the
+//                 oracle.  Several levels run per host synchronisation (each
+//                 launch reads its frontier size from device memory);
+//   k_dt_far      far terms in FP32 from the records (no division), one
+//                 thread per far pair, node derivatives summed with FP64
+//                 atomics;
+//   k_dt_count/k_dt_fill/k_dt_runs  per cluster leaf, its near partners
+//                 (both directions of each near pair) as (first member,
+//                 count) in two lists: partners whose FP32 outward vertex box
+//                 touches the leaf's (the leaf itself among them) and the
+//                 others, the latter cut into runs of at most 128;
 //   k_dt_near     one warp per cluster leaf gathers both orderings of every
-//                 admitted pair with its partners' members (packed FP32x2,
-//                 FP64 per partner batch), exclusion test on every pair, and
-//                 stores the leaf's accumulators (direct kernels' layout);
+//                 admitted pair with its touching partners' members (packed
+//                 FP32x2, exclusion test on every pair) and stores the leaf's
+//                 accumulators (direct kernels' layout); the apart partners
+//                 go to the Barnes-Hut near-field kernel (k_near, tp_bh.cu),
+//                 which needs no exclusion test and adds with atomics;
 //   k_dt_node     per node, the derivatives divided by A and the weight term;
 //   k_dt_down     per triangle, the sum over its ancestors added to its
 //                 accumulators (Ew += (p/q) w gw, Gn += (p/q)/q gnu,
@@ -60,8 +72,11 @@ struct DTTree {
     const int32_t* first;
     const int32_t* last;
     const int32_t* perm;
-    const double* mom;  // [nn][13]
-    const double* box;  // [nn][6]
+    const double* mom;    // [nn][13]
+    const double* box;    // [nn][6]
+    const double* adm64;  // [nn][4] X (FP64 quotients), diagonal
+    const float* adm32;   // [nn][16] outward box, inward box, X, diagonal (FP32)
+    const float* nodef;   // [nn][16] FP32 far-field record (nubar at 6..8)
     int64_t n;
     int leaf;
 };
@@ -80,21 +95,67 @@ __device__ __forceinline__ double dt_diag2(const double* b) {
     return s;
 }
 
-__device__ bool dt_admissible(const double* bA, const double* mA, const double* bB, const double* mB, double theta) {
-    bool disjoint = false;
+// Admissibility of {A, B}: vertex boxes strictly apart along some axis and
+// max(diag_A, diag_B) < theta |X_A - X_B|.  The FP32 records decide when they
+// can: outward-rounded boxes apart -> apart, inward-rounded boxes overlapping
+// on every axis -> not apart, the size test outside a 1e-5 relative margin
+// (far above the FP32 rounding of the records and of the distance); the other
+// cases use FP64 boxes, centroid quotients and diagonals (the oracle's values
+// and operations: sqrt(max(dA2, dB2)) = max(sqrt dA2, sqrt dB2) exactly).
+__device__ bool dt_admissible(const DTTree& T, int A, int B, double theta, float theta32) {
+    const float* cA = T.adm32 + 16 * (int64_t)A;
+    const float* cB = T.adm32 + 16 * (int64_t)B;
+    bool sure = false, amb = false;
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-        if (bA[3 + a] < bB[a] || bB[3 + a] < bA[a]) disjoint = true;
-    if (!disjoint) return false;
-    const double dA2 = dt_diag2(bA), dB2 = dt_diag2(bB);
+    for (int a = 0; a < 3; ++a) {
+        if (cA[3 + a] < cB[a] || cB[3 + a] < cA[a]) sure = true;
+        else if (!(cA[9 + a] >= cB[6 + a] && cB[9 + a] >= cA[6 + a])) amb = true;
+    }
+    if (!sure) {
+        if (!amb) return false;
+        const double* bA = T.box + 6 * (int64_t)A;
+        const double* bB = T.box + 6 * (int64_t)B;
+        bool disjoint = false;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (bA[3 + a] < bB[a] || bB[3 + a] < bA[a]) disjoint = true;
+        if (!disjoint) return false;
+    }
+    float r2f = 0.f, M = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float t = cA[12 + a] - cB[12 + a];
+        r2f = fmaf(t, t, r2f);
+        M += fabsf(cA[12 + a]) + fabsf(cB[12 + a]);
+    }
+    const float distf = sqrtf(r2f);
+    const float lhsf = fmaxf(cA[15], cB[15]);
+    const float rhsf = theta32 * distf;
+    const float margin = 1e-5f * (lhsf + theta32 * (distf + M));
+    if (lhsf < rhsf - margin) return true;
+    if (lhsf > rhsf + margin) return false;
+    const double* aA = T.adm64 + 4 * (int64_t)A;
+    const double* aB = T.adm64 + 4 * (int64_t)B;
     double r2 = 0.0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const double t = __dsub_rn(__ddiv_rn(mA[1 + a], mA[0]), __ddiv_rn(mB[1 + a], mB[0]));
+        const double t = __dsub_rn(aA[a], aB[a]);
         r2 = __dadd_rn(r2, __dmul_rn(t, t));
     }
-    const double diag = __dsqrt_rn(dA2 > dB2 ? dA2 : dB2);
+    const double diag = aA[3] > aB[3] ? aA[3] : aB[3];
     return diag < __dmul_rn(theta, __dsqrt_rn(r2));
+}
+
+// FP32 outward-rounded vertex boxes strictly apart along some axis: no member
+// of A shares a vertex with a member of B
+__device__ __forceinline__ bool dt_boxes_apart(const DTTree& T, int A, int B) {
+    const float* cA = T.adm32 + 16 * (int64_t)A;
+    const float* cB = T.adm32 + 16 * (int64_t)B;
+    bool apart = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        if (cA[3 + a] < cB[a] || cB[3 + a] < cA[a]) apart = true;
+    return apart;
 }
 
 // Reserve cnt (>= 0) slots of a list for every lane of a warp with one atomic;
@@ -116,11 +177,18 @@ __device__ __forceinline__ unsigned long long warp_reserve(unsigned cnt, unsigne
 
 // One level of the pair recursion.  cnt[0] frontier in, cnt[1] frontier out,
 // cnt[2] far, cnt[3] near; an append past a capacity sets cnt[4].
+// The frontier size is read from n_in_p (the previous level's output count);
+// a level whose input overflowed its list (cnt[4] set) does nothing.
 __global__ void __launch_bounds__(DT_THREADS) k_dt_expand(DTTree T, double theta, const int2* __restrict__ fin,
-                                                          int64_t n_in, int2* __restrict__ fout, int64_t cap_out,
+                                                          const unsigned long long* __restrict__ n_in_p,
+                                                          int64_t cap_in, int2* __restrict__ fout,
+                                                          unsigned long long* __restrict__ n_out_p, int64_t cap_out,
                                                           int2* __restrict__ far, int64_t cap_far,
                                                           int2* __restrict__ near, int64_t cap_near,
                                                           unsigned long long* __restrict__ cnt) {
+    if (cnt[4]) return;
+    const int64_t n_in = (int64_t)*n_in_p < cap_in ? (int64_t)*n_in_p : cap_in;
+    const float theta32 = (float)theta;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t rounds = (n_in + stride - 1) / stride;
     for (int64_t r = 0; r < rounds; ++r) {  // uniform trip count: every lane reaches the warp reservations
@@ -134,8 +202,7 @@ __global__ void __launch_bounds__(DT_THREADS) k_dt_expand(DTTree T, double theta
             const bool sA = dt_small(T, A), sB = dt_small(T, B);
             if (A == B) {
                 kind = sA ? 0 : 4;
-            } else if (dt_admissible(T.box + 6 * (int64_t)A, T.mom + 13 * (int64_t)A, T.box + 6 * (int64_t)B,
-                                     T.mom + 13 * (int64_t)B, theta)) {
+            } else if (dt_admissible(T, A, B, theta, theta32)) {
                 kind = 1;
             } else if (sA && sB) {
                 kind = 0;
@@ -145,7 +212,7 @@ __global__ void __launch_bounds__(DT_THREADS) k_dt_expand(DTTree T, double theta
             }
         }
         const unsigned n_out = kind == 4 ? 3u : (kind == 2 || kind == 3) ? 2u : 0u;
-        const unsigned long long po = warp_reserve(n_out, &cnt[1]);
+        const unsigned long long po = warp_reserve(n_out, n_out_p);
         const unsigned long long pf = warp_reserve(kind == 1 ? 1u : 0u, &cnt[2]);
         const unsigned long long pn = warp_reserve(kind == 0 ? 1u : 0u, &cnt[3]);
         if (kind == 1) {
@@ -175,51 +242,55 @@ __global__ void __launch_bounds__(DT_THREADS) k_dt_expand(DTTree T, double theta
     }
 }
 
-// Far pairs in FP64: the node derivatives dE/d(A, X[3], nubar[3]) of both
-// nodes into G[node][7]; the represented ordered pairs into *rep.
+// Far pairs: the monopole of both orderings in FP32 from the records (X_A -
+// X_B formed in FP64 from the centroid quotients, then rounded; nubar from the
+// far-field record), the node derivatives dE/d(A, X[3], nubar[3]) of both
+// nodes summed into G[node][7] with FP64 atomics; the represented ordered
+// pairs into *rep.
 __global__ void __launch_bounds__(DT_THREADS) k_dt_far(DTTree T, const int2* __restrict__ far, int64_t nfar, int q,
-                                                       double p, double* __restrict__ G,
-                                                       unsigned long long* __restrict__ rep) {
+                                                       double* __restrict__ G, unsigned long long* __restrict__ rep) {
     unsigned long long my_rep = 0;
+    const float pf = 2.0f * (float)q;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nfar; i += (int64_t)gridDim.x * blockDim.x) {
         const int2 pr = far[i];
-        const double* mA = T.mom + 13 * (int64_t)pr.x;
-        const double* mB = T.mom + 13 * (int64_t)pr.y;
-        const double AA = mA[0], AB = mB[0];
-        double d[3], nA[3], nB[3], r2 = 0.0, n1 = 0.0, n2 = 0.0;
+        const double* xA = T.adm64 + 4 * (int64_t)pr.x;
+        const double* xB = T.adm64 + 4 * (int64_t)pr.y;
+        const float* fA = T.nodef + 16 * (int64_t)pr.x;
+        const float* fB = T.nodef + 16 * (int64_t)pr.y;
+        const float AA = (float)T.mom[13 * (int64_t)pr.x], AB = (float)T.mom[13 * (int64_t)pr.y];
+        const float nA[3] = {fA[6], fA[7], fA[8]}, nB[3] = {fB[6], fB[7], fB[8]};
+        float d[3], r2 = 0.f, n1 = 0.f, n2 = 0.f;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            d[a] = mA[1 + a] / AA - mB[1 + a] / AB;
-            nA[a] = mA[4 + a] / AA;
-            nB[a] = mB[4 + a] / AB;
-            r2 += d[a] * d[a];
+            d[a] = (float)(xA[a] - xB[a]);
+            r2 = fmaf(d[a], d[a], r2);
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            n1 += nA[a] * d[a];
-            n2 -= nB[a] * d[a];
+            n1 = fmaf(nA[a], d[a], n1);
+            n2 = fmaf(-nB[a], d[a], n2);
         }
-        const double inv = 1.0 / r2;
-        double rp = 1.0;  // |d|^-p, p even
-        for (int e = 0; e < (int)(p / 2); ++e) rp *= inv;
-        double b1 = (double)q, b2 = (double)q;  // q n^(q-1)
+        // with al = n1 / |d|^2 and be = n2 / |d|^2, n^q |d|^-p = al^q (p = 2q): no
+        // power of |d| alone, so nothing overflows for small clusters at large theta
+        const float inv = 1.0f / r2, al = n1 * inv, be = n2 * inv;
+        float al1 = 1.f, be1 = 1.f;  // al^(q-1), be^(q-1)
         for (int e = 0; e < q - 1; ++e) {
-            b1 *= n1;
-            b2 *= n2;
+            al1 *= al;
+            be1 *= be;
         }
-        const double a1 = b1 * n1 / q, a2 = b2 * n2 / q;  // n^q
-        const double AAB = AA * AB, s = a1 + a2;
+        const float AAB = AA * AB, s = al1 * al + be1 * be;  // al^q + be^q
+        const float qa = (float)q * al1 * inv, qb = (float)q * be1 * inv;
         double* GA = G + 7 * (int64_t)pr.x;
         double* GB = G + 7 * (int64_t)pr.y;
-        atomicAdd(&GA[0], AB * s * rp);
-        atomicAdd(&GB[0], AA * s * rp);
+        atomicAdd(&GA[0], (double)(AB * s));
+        atomicAdd(&GB[0], (double)(AA * s));
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const double gX = AAB * rp * (b1 * nA[k] - b2 * nB[k] - p * s * inv * d[k]);
-            atomicAdd(&GA[1 + k], gX);
-            atomicAdd(&GB[1 + k], -gX);
-            atomicAdd(&GA[4 + k], AAB * b1 * rp * d[k]);
-            atomicAdd(&GB[4 + k], -AAB * b2 * rp * d[k]);
+            const float gX = AAB * (qa * nA[k] - qb * nB[k] - pf * s * inv * d[k]);
+            atomicAdd(&GA[1 + k], (double)gX);
+            atomicAdd(&GB[1 + k], (double)-gX);
+            atomicAdd(&GA[4 + k], (double)(AAB * qa * d[k]));
+            atomicAdd(&GB[4 + k], (double)(-AAB * qb * d[k]));
         }
         my_rep += 2ull * (unsigned long long)(T.last[pr.x] - T.first[pr.x] + 1) *
                   (unsigned long long)(T.last[pr.y] - T.first[pr.y] + 1);
@@ -233,35 +304,86 @@ __global__ void k_dt_leaf_index(const int32_t* __restrict__ leaves, int64_t nlea
     if (i < nleaves) node2leaf[leaves[i]] = (int32_t)i;
 }
 
-// partners per cluster leaf: both directions of every near pair (a self pair once)
-__global__ void k_dt_count(const int2* __restrict__ near, int64_t nnear, const int32_t* __restrict__ node2leaf,
-                           uint32_t* __restrict__ count, unsigned* derr) {
+// partners per cluster leaf, both directions of every near pair (a self pair
+// once): touching partners counted in ct[leaf], apart ones in ca[leaf]
+// (the ordered member pairs of the apart node pairs, all admitted, into *apart_pairs)
+__global__ void k_dt_count(DTTree T, const int2* __restrict__ near, int64_t nnear,
+                           const int32_t* __restrict__ node2leaf, uint32_t* __restrict__ ct,
+                           uint32_t* __restrict__ ca, unsigned long long* __restrict__ apart_pairs, unsigned* derr) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= nnear) return;
-    const int2 pr = near[i];
-    const int la = node2leaf[pr.x], lb = node2leaf[pr.y];
-    if (la < 0 || lb < 0) {  // a near node that is not a cluster leaf: the recursion's invariant failed
-        tp_dev_error(derr, TP_DERR_INTERNAL);
-        return;
+    unsigned long long np = 0;
+    if (i < nnear) {
+        const int2 pr = near[i];
+        const int la = node2leaf[pr.x], lb = node2leaf[pr.y];
+        if (la < 0 || lb < 0) {  // a near node that is not a cluster leaf: the recursion's invariant failed
+            tp_dev_error(derr, TP_DERR_INTERNAL);
+        } else if (pr.x == pr.y) {
+            atomicAdd(&ct[la], 1u);
+        } else if (dt_boxes_apart(T, pr.x, pr.y)) {
+            atomicAdd(&ca[la], 1u);
+            atomicAdd(&ca[lb], 1u);
+            np = 2ull * (unsigned long long)(T.last[pr.x] - T.first[pr.x] + 1) *
+                 (unsigned long long)(T.last[pr.y] - T.first[pr.y] + 1);
+        } else {
+            atomicAdd(&ct[la], 1u);
+            atomicAdd(&ct[lb], 1u);
+        }
     }
-    atomicAdd(&count[la], 1u);
-    if (pr.x != pr.y) atomicAdd(&count[lb], 1u);
+    for (int o = 16; o > 0; o >>= 1) np += __shfl_xor_sync(0xffffffffu, np, o);
+    if ((threadIdx.x & 31) == 0 && np) atomicAdd(apart_pairs, np);
 }
 
-__global__ void k_dt_fill(const int2* __restrict__ near, int64_t nnear, const int32_t* __restrict__ node2leaf,
-                          const int32_t* __restrict__ first, const int32_t* __restrict__ last,
-                          const uint32_t* __restrict__ off, uint32_t* __restrict__ cursor, int2* __restrict__ list) {
+__global__ void k_dt_fill(DTTree T, const int2* __restrict__ near, int64_t nnear,
+                          const int32_t* __restrict__ node2leaf, const uint32_t* __restrict__ ot,
+                          const uint32_t* __restrict__ oa, uint32_t* __restrict__ kt, uint32_t* __restrict__ ka,
+                          int2* __restrict__ lt, int2* __restrict__ lap) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= nnear) return;
     const int2 pr = near[i];
     const int la = node2leaf[pr.x], lb = node2leaf[pr.y];
     if (la < 0 || lb < 0) return;
-    list[off[la] + atomicAdd(&cursor[la], 1u)] = make_int2(first[pr.y], last[pr.y] - first[pr.y] + 1);
-    if (pr.x != pr.y) list[off[lb] + atomicAdd(&cursor[lb], 1u)] = make_int2(first[pr.x], last[pr.x] - first[pr.x] + 1);
+    const int2 eB = make_int2(T.first[pr.y], T.last[pr.y] - T.first[pr.y] + 1);
+    if (pr.x == pr.y) {
+        lt[ot[la] + atomicAdd(&kt[la], 1u)] = eB;
+        return;
+    }
+    const int2 eA = make_int2(T.first[pr.x], T.last[pr.x] - T.first[pr.x] + 1);
+    if (dt_boxes_apart(T, pr.x, pr.y)) {
+        lap[oa[la] + atomicAdd(&ka[la], 1u)] = eB;
+        lap[oa[lb] + atomicAdd(&ka[lb], 1u)] = eA;
+    } else {
+        lt[ot[la] + atomicAdd(&kt[la], 1u)] = eB;
+        lt[ot[lb] + atomicAdd(&kt[lb], 1u)] = eA;
+    }
+}
+
+constexpr int DT_RUN = 128;  // apart partners per run of the near-field kernel
+
+__global__ void k_dt_runcount(const uint32_t* __restrict__ ca, int64_t nl, uint32_t* __restrict__ nr) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < nl) nr[i] = (ca[i] + DT_RUN - 1) / DT_RUN;
+}
+
+__global__ void k_dt_runs(const uint32_t* __restrict__ ca, const uint32_t* __restrict__ oa,
+                          const uint32_t* __restrict__ orr, int64_t nl, tp_far_run* __restrict__ runs) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nl) return;
+    const uint32_t n = ca[i];
+    for (uint32_t j = 0; j * DT_RUN < n; ++j) {
+        tp_far_run r;
+        r.start = (int64_t)oa[i] + (int64_t)j * DT_RUN;
+        r.li = (int32_t)i;
+        r.len = (int32_t)min((uint32_t)DT_RUN, n - j * DT_RUN);
+        runs[orr[i] + j] = r;
+    }
+}
+
+__global__ void k_dt_setcount(const int32_t* __restrict__ total, unsigned long long* __restrict__ counter) {
+    *counter = (unsigned long long)*total;
 }
 
 // One warp per cluster leaf: both orderings of every admitted pair of its
-// targets with its near partners' members, gathered on the target side.
+// targets with its touching partners' members, gathered on the target side.
 template <int Q>
 __global__ void __launch_bounds__(DT_NEAR_WARPS * 32) k_dt_near(const float* __restrict__ soa, int64_t ntp,
                                                                 const int32_t* __restrict__ Fs,
@@ -356,14 +478,26 @@ __global__ void k_dt_node(const double* __restrict__ G, const double* __restrict
     const int64_t N = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (N >= nn) return;
     const double* g = G + 7 * N;
+    double gv[7];
+    bool any = false;
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+        gv[c] = g[c];
+        any = any || gv[c] != 0.0;
+    }
+    if (!any) {  // a node in no far pair (most of them): nothing to pass down
+#pragma unroll
+        for (int c = 0; c < 7; ++c) P[7 * N + c] = 0.0;
+        return;
+    }
     const double* m = mom + 13 * N;
-    const double A = m[0];
-    double s = g[0];
+    const double ia = 1.0 / m[0];
+    double s = gv[0];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        P[7 * N + 1 + a] = g[1 + a] / A;
-        P[7 * N + 4 + a] = g[4 + a] / A;
-        s -= (g[1 + a] * (m[1 + a] / A) + g[4 + a] * (m[4 + a] / A)) / A;
+        P[7 * N + 1 + a] = gv[1 + a] * ia;
+        P[7 * N + 4 + a] = gv[4 + a] * ia;
+        s -= (gv[1 + a] * (m[1 + a] * ia) + gv[4 + a] * (m[4 + a] * ia)) * ia;
     }
     P[7 * N] = s;
 }
@@ -417,66 +551,93 @@ tp_status tp_launch_dual(tp_ctx* ctx, const tp_params* prm) {
     T.perm = ctx->perm;
     T.mom = t.mom;
     T.box = t.box;
+    T.adm64 = t.adm64;
+    T.adm32 = t.adm32;
+    T.nodef = t.nodef;
     T.n = n;
     T.leaf = t.leaf_size;
-    if (!ctx->dt_cnt) TP_TRY(tp_alloc_t(ctx, &ctx->dt_cnt, 8));
+    // counters: [2] far pairs, [3] near pairs, [4] overflow, [5] admitted pairs of the
+    // touching pass, [6] represented far pairs, [7] pairs of the apart node pairs,
+    // [9] runs and [10] work counter of the near-field kernel; from [16] the frontier
+    // sizes of DT_LEVELS levels
+    constexpr int DT_LEVELS = 4096, DT_SYNC = 8;
+    if (!ctx->dt_cnt) TP_TRY(tp_alloc_t(ctx, &ctx->dt_cnt, 16 + DT_LEVELS));
     unsigned long long* cnt = ctx->dt_cnt;
+    unsigned long long* fsize = cnt + 16;
     if (ctx->dt_cap == 0) {
         const int64_t c0 = std::max<int64_t>(1 << 16, 64 * t.nleaves);
         TP_TRY(tp_dual_lists(ctx, c0, c0, c0));
     }
     cudaEventRecord(ctx->ev[0], ctx->stream);
     int64_t n_far = 0, n_near = 0;
+    const unsigned eblocks = (unsigned)std::max(1, 8 * ctx->num_sms);
     for (int attempt = 0;; ++attempt) {
-        // the traversal, level by level from (root, root)
+        // the traversal from (root, root), DT_SYNC levels per host synchronisation
         const int2 root = make_int2(0, 0);
+        const unsigned long long one = 1ull;
         TP_CU(cudaMemcpyAsync(ctx->dt_front[0], &root, sizeof(int2), cudaMemcpyHostToDevice, ctx->stream));
-        TP_CU(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), ctx->stream));
-        int64_t n_in = 1;
-        int cur = 0;
-        bool overflow = false;
-        unsigned long long h[5] = {0, 0, 0, 0, 0};
-        for (int level = 0; n_in > 0 && level < 4096; ++level) {
-            TP_CU(cudaMemsetAsync(cnt + 1, 0, sizeof(unsigned long long), ctx->stream));
-            const unsigned blocks = (unsigned)std::min<int64_t>(dt_blocks(n_in, DT_THREADS), 8 * ctx->num_sms);
-            k_dt_expand<<<blocks, DT_THREADS, 0, ctx->stream>>>(T, prm->theta, ctx->dt_front[cur], n_in,
-                                                                 ctx->dt_front[cur ^ 1], ctx->dt_cap, ctx->dt_far,
-                                                                 ctx->dt_far_cap, ctx->dt_near, ctx->dt_near_cap, cnt);
-            ++ctx->nlaunch;
+        TP_CU(cudaMemsetAsync(cnt, 0, (16 + DT_LEVELS) * sizeof(unsigned long long), ctx->stream));
+        TP_CU(cudaMemcpyAsync(fsize, &one, sizeof(one), cudaMemcpyHostToDevice, ctx->stream));
+        unsigned long long h[5] = {0, 0, 0, 0, 0}, last = 1;
+        bool done = false;
+        for (int level = 0; level < DT_LEVELS - 1 && !done;) {
+            for (int k = 0; k < DT_SYNC && level < DT_LEVELS - 1; ++k, ++level)
+                k_dt_expand<<<eblocks, DT_THREADS, 0, ctx->stream>>>(
+                    T, prm->theta, ctx->dt_front[level & 1], fsize + level, ctx->dt_cap, ctx->dt_front[(level + 1) & 1],
+                    fsize + level + 1, ctx->dt_cap, ctx->dt_far, ctx->dt_far_cap, ctx->dt_near, ctx->dt_near_cap, cnt);
+            ctx->nlaunch += DT_SYNC;
             TP_CU(cudaMemcpyAsync(h, cnt, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
+            TP_CU(cudaMemcpyAsync(&last, fsize + level, sizeof(last), cudaMemcpyDeviceToHost, ctx->stream));
             TP_CU(cudaStreamSynchronize(ctx->stream));
-            if (h[4]) {
-                overflow = true;
-                break;
-            }
-            n_in = (int64_t)h[1];
-            cur ^= 1;
+            done = h[4] != 0 || last == 0;
         }
-        if (!overflow) {
+        if (!h[4] && last == 0) {
             n_far = (int64_t)h[2];
             n_near = (int64_t)h[3];
             break;
         }
-        if (attempt > 3) return tp_set_err(ctx, TP_E_OOM, "dual-tree pair lists keep overflowing");
-        // grow the list that overflowed (the counters passed the capacities) and repeat
-        TP_TRY(tp_dual_lists(ctx, std::max<int64_t>(ctx->dt_cap, (int64_t)h[1]) * 2,
+        if (attempt > 3 || !h[4]) return tp_set_err(ctx, TP_E_OOM, "dual-tree pair lists keep overflowing");
+        // grow every list to twice its size and repeat (an overflowing level stops the traversal,
+        // so its count is a lower bound of the need)
+        unsigned long long fmax = 0, hf[DT_LEVELS];
+        TP_CU(cudaMemcpyAsync(hf, fsize, sizeof(hf), cudaMemcpyDeviceToHost, ctx->stream));
+        TP_CU(cudaStreamSynchronize(ctx->stream));
+        for (int l = 0; l < DT_LEVELS; ++l) fmax = std::max(fmax, hf[l]);
+        TP_TRY(tp_dual_lists(ctx, std::max<int64_t>(ctx->dt_cap, (int64_t)fmax) * 2,
                              std::max<int64_t>(ctx->dt_far_cap, (int64_t)h[2]) * 2,
                              std::max<int64_t>(ctx->dt_near_cap, (int64_t)h[3]) * 2));
     }
-    // per-leaf partner lists
-    const int64_t nl = t.nleaves;
-    TP_TRY(tp_dual_leaf_buffers(ctx, nl, nn, 2 * n_near));
+    // per-leaf partner lists: touching ones, apart ones cut into runs
+    const int64_t nl = t.nleaves, L1 = nl + 1;
+    TP_TRY(tp_dual_leaf_buffers(ctx, nl, nn, 4 * n_near, 2 * n_near / 128 + nl + 1));
+    uint32_t* ct = ctx->dt_off;  // counts, then offsets, of the touching lists
+    uint32_t* ca = ct + L1;      // ... of the apart lists
+    uint32_t* cr = ca + L1;      // ... of the runs
+    uint32_t* kt = ctx->dt_cursor;
+    uint32_t* ka = kt + L1;
+    uint32_t* cat = cr + L1;     // apart counts kept for the runs
+    int32_t* tot = reinterpret_cast<int32_t*>(cat + L1);  // [0] apart entries, [1] runs
     TP_CU(cudaMemsetAsync(ctx->dt_node2leaf, 0xff, sizeof(int32_t) * nn, ctx->stream));
-    TP_CU(cudaMemsetAsync(ctx->dt_off, 0, sizeof(uint32_t) * (nl + 1), ctx->stream));
-    TP_CU(cudaMemsetAsync(ctx->dt_cursor, 0, sizeof(uint32_t) * nl, ctx->stream));
+    TP_CU(cudaMemsetAsync(ctx->dt_off, 0, sizeof(uint32_t) * (4 * L1 + 2), ctx->stream));
+    TP_CU(cudaMemsetAsync(ctx->dt_cursor, 0, sizeof(uint32_t) * 2 * L1, ctx->stream));
     k_dt_leaf_index<<<dt_blocks(nl, 256), 256, 0, ctx->stream>>>(t.leaves, nl, ctx->dt_node2leaf);
-    k_dt_count<<<dt_blocks(n_near, 256), 256, 0, ctx->stream>>>(ctx->dt_near, n_near, ctx->dt_node2leaf, ctx->dt_off,
-                                                                ctx->derr);
-    TP_TRY(tp_scan_u32(ctx, ctx->dt_off, ctx->dt_off, nl + 1, false, nullptr));
-    k_dt_fill<<<dt_blocks(n_near, 256), 256, 0, ctx->stream>>>(ctx->dt_near, n_near, ctx->dt_node2leaf, t.first,
-                                                               t.last, ctx->dt_off, ctx->dt_cursor, ctx->dt_list);
+    k_dt_count<<<dt_blocks(n_near, 256), 256, 0, ctx->stream>>>(T, ctx->dt_near, n_near, ctx->dt_node2leaf, ct, ca,
+                                                                cnt + 7, ctx->derr);
+    TP_CU(cudaMemcpyAsync(cat, ca, sizeof(uint32_t) * L1, cudaMemcpyDeviceToDevice, ctx->stream));
+    k_dt_runcount<<<dt_blocks(nl, 256), 256, 0, ctx->stream>>>(ca, nl, cr);
     ctx->nlaunch += 3;
-    // near field: every target owned by one warp, stored without atomics
+    TP_TRY(tp_scan_u32(ctx, ct, ct, L1, false, nullptr));
+    TP_TRY(tp_scan_u32(ctx, ca, ca, L1, false, tot));
+    TP_TRY(tp_scan_u32(ctx, cr, cr, L1, false, tot + 1));
+    int2* list_t = ctx->dt_list;               // at most 2 n_near touching entries
+    int2* list_a = ctx->dt_list + 2 * n_near;  // at most 2 n_near apart entries
+    k_dt_fill<<<dt_blocks(n_near, 256), 256, 0, ctx->stream>>>(T, ctx->dt_near, n_near, ctx->dt_node2leaf, ct, ca, kt,
+                                                               ka, list_t, list_a);
+    k_dt_runs<<<dt_blocks(nl, 256), 256, 0, ctx->stream>>>(cat, ca, cr, nl, ctx->dt_runs);
+    k_dt_setcount<<<1, 1, 0, ctx->stream>>>(tot + 1, cnt + 8 + 1);
+    ctx->nlaunch += 3;
+    // near field: touching partners with the exclusion test (each target owned by one warp, stored),
+    // then the apart partners in the Barnes-Hut near-field kernel (added)
     TP_CU(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * TP_NACC * ctx->ntp, ctx->stream));
     unsigned long long* npairs = cnt + 5;
     unsigned long long* rep = cnt + 6;
@@ -484,18 +645,17 @@ tp_status tp_launch_dual(tp_ctx* ctx, const tp_params* prm) {
     const int edge = (prm->flags & TP_EXCLUDE_EDGE) ? 1 : 0;
     if (prm->q == 6)
         k_dt_near<6><<<dt_blocks(nl, DT_NEAR_WARPS), DT_NEAR_WARPS * 32, 0, ctx->stream>>>(
-            ctx->soa, ctx->ntp, ctx->Fs, t.leaves, nl, t.first, t.last, wide, ctx->dt_off, ctx->dt_list, edge,
-            ctx->acc, npairs);
+            ctx->soa, ctx->ntp, ctx->Fs, t.leaves, nl, t.first, t.last, wide, ct, list_t, edge, ctx->acc, npairs);
     else
         k_dt_near<8><<<dt_blocks(nl, DT_NEAR_WARPS), DT_NEAR_WARPS * 32, 0, ctx->stream>>>(
-            ctx->soa, ctx->ntp, ctx->Fs, t.leaves, nl, t.first, t.last, wide, ctx->dt_off, ctx->dt_list, edge,
-            ctx->acc, npairs);
+            ctx->soa, ctx->ntp, ctx->Fs, t.leaves, nl, t.first, t.last, wide, ct, list_t, edge, ctx->acc, npairs);
     ++ctx->nlaunch;
+    TP_TRY(tp_launch_near_runs(ctx, prm->q, list_a, 2 * n_near, ctx->dt_runs, ctx->dt_run_cap, cnt + 8));
     // far field: node derivatives, then down to the triangles
     TP_CU(cudaMemsetAsync(ctx->dt_G, 0, sizeof(double) * 7 * nn, ctx->stream));
     if (n_far > 0) {
         k_dt_far<<<(unsigned)std::min<int64_t>(dt_blocks(n_far, DT_THREADS), 16 * ctx->num_sms), DT_THREADS, 0,
-                   ctx->stream>>>(T, ctx->dt_far, n_far, prm->q, (double)prm->p, ctx->dt_G, rep);
+                   ctx->stream>>>(T, ctx->dt_far, n_far, prm->q, ctx->dt_G, rep);
         k_dt_node<<<dt_blocks(nn, 256), 256, 0, ctx->stream>>>(ctx->dt_G, t.mom, nn, ctx->dt_P);
         k_dt_down<<<dt_blocks(n, 256), 256, 0, ctx->stream>>>(t.parent, ctx->perm, n, ctx->dt_P, ctx->x64, ctx->nu64,
                                                              ctx->w64, ctx->ntp, (double)prm->p / prm->q,
@@ -504,10 +664,11 @@ tp_status tp_launch_dual(tp_ctx* ctx, const tp_params* prm) {
     }
     cudaEventRecord(ctx->ev[1], ctx->stream);
     TP_CU(cudaGetLastError());
-    unsigned long long h2[2] = {0, 0};
+    unsigned long long h2[3] = {0, 0, 0};
     TP_CU(cudaMemcpyAsync(h2, cnt + 5, sizeof(h2), cudaMemcpyDeviceToHost, ctx->stream));
     TP_CU(cudaStreamSynchronize(ctx->stream));
-    ctx->stats.pairs_exact = (int64_t)h2[0];
+    // admitted near pairs: those of the touching pass plus every pair of the apart node pairs
+    ctx->stats.pairs_exact = (int64_t)(h2[0] + h2[2]);
     ctx->stats.far_terms = n_far;
     ctx->stats.far_pairs = (int64_t)h2[1];
     ctx->stats.far_rows = n_far;
@@ -543,7 +704,7 @@ tp_status tp_dual_lists(tp_ctx* ctx, int64_t cap_front, int64_t cap_far, int64_t
 }
 
 // per-leaf partner lists and per-node derivative buffers
-tp_status tp_dual_leaf_buffers(tp_ctx* ctx, int64_t nleaves, int64_t nn, int64_t entries) {
+tp_status tp_dual_leaf_buffers(tp_ctx* ctx, int64_t nleaves, int64_t nn, int64_t entries, int64_t runs) {
     if (ctx->dt_leaf_cap < nleaves + 1 || ctx->dt_node_cap < nn) {
         for (void* p : {(void*)ctx->dt_off, (void*)ctx->dt_cursor, (void*)ctx->dt_node2leaf, (void*)ctx->dt_G,
                         (void*)ctx->dt_P})
@@ -552,8 +713,8 @@ tp_status tp_dual_leaf_buffers(tp_ctx* ctx, int64_t nleaves, int64_t nn, int64_t
         ctx->dt_node2leaf = nullptr;
         ctx->dt_G = ctx->dt_P = nullptr;
         ctx->dt_leaf_cap = ctx->dt_node_cap = 0;
-        TP_TRY(tp_alloc_t(ctx, &ctx->dt_off, nleaves + 1));
-        TP_TRY(tp_alloc_t(ctx, &ctx->dt_cursor, nleaves + 1));
+        TP_TRY(tp_alloc_t(ctx, &ctx->dt_off, 4 * (nleaves + 1) + 2));
+        TP_TRY(tp_alloc_t(ctx, &ctx->dt_cursor, 2 * (nleaves + 1)));
         TP_TRY(tp_alloc_t(ctx, &ctx->dt_node2leaf, nn));
         TP_TRY(tp_alloc_t(ctx, &ctx->dt_G, 7 * nn));
         TP_TRY(tp_alloc_t(ctx, &ctx->dt_P, 7 * nn));
@@ -566,6 +727,13 @@ tp_status tp_dual_leaf_buffers(tp_ctx* ctx, int64_t nleaves, int64_t nn, int64_t
         ctx->dt_list_cap = 0;
         TP_TRY(tp_alloc_t(ctx, &ctx->dt_list, std::max<int64_t>(entries, 1)));
         ctx->dt_list_cap = entries;
+    }
+    if (ctx->dt_run_cap < runs) {
+        tp_free(ctx, ctx->dt_runs);
+        ctx->dt_runs = nullptr;
+        ctx->dt_run_cap = 0;
+        TP_TRY(tp_alloc_t(ctx, &ctx->dt_runs, std::max<int64_t>(runs, 1)));
+        ctx->dt_run_cap = runs;
     }
     return TP_OK;
 }

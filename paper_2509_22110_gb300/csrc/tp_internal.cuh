@@ -239,8 +239,9 @@ struct tp_ctx {
     int32_t* dt_node2leaf = nullptr;  // [2n - 1]
     double* dt_G = nullptr;         // [2n - 1][7] far-field derivatives per node
     double* dt_P = nullptr;         // [2n - 1][7] the same divided by the node area, weight term
-    int2* dt_list = nullptr;        // partner leaves as (first member, count)
-    int64_t dt_leaf_cap = 0, dt_node_cap = 0, dt_list_cap = 0;
+    int2* dt_list = nullptr;        // partner leaves as (first member, count): touching, then apart
+    tp_far_run* dt_runs = nullptr;  // runs of at most 128 apart partners of one leaf, for the near-field kernel
+    int64_t dt_leaf_cap = 0, dt_node_cap = 0, dt_list_cap = 0, dt_run_cap = 0;
 
     tp_stats stats{};
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -358,10 +359,13 @@ tp_status tp_launch_check_finite(tp_ctx* ctx);
 tp_status tp_launch_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits);
 // tp_bh.cu
 tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned);
+// Barnes-Hut near-field kernel on runs of clusters apart from their leaf (tp_bh.cu)
+tp_status tp_launch_near_runs(tp_ctx* ctx, int q, const int2* list, int64_t list_len, const tp_far_run* runs,
+                              int64_t run_cap, unsigned long long* counters);
 // cluster-cluster (dual-tree) form into ctx->acc (tp_dual.cu)
 tp_status tp_launch_dual(tp_ctx* ctx, const tp_params* prm);
 tp_status tp_dual_lists(tp_ctx* ctx, int64_t cap_front, int64_t cap_far, int64_t cap_near);
-tp_status tp_dual_leaf_buffers(tp_ctx* ctx, int64_t nleaves, int64_t nn, int64_t entries);
+tp_status tp_dual_leaf_buffers(tp_ctx* ctx, int64_t nleaves, int64_t nn, int64_t entries, int64_t runs);
 tp_status tp_launch_bh_sample(tp_ctx* ctx, double theta, uint32_t keep_u, uint64_t seed, int2* out, int64_t cap,
                               int32_t* counter);
 // tp_mlp.cu

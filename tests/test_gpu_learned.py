@@ -145,10 +145,12 @@ def test_training_lowers_the_far_field_error(tp, ctx, tmp_path):
     _tp.tp_far_dataset_reset(ctx)
     far_train.sample_meshes(ctx, range(1000, 1008), 5, 0.5, 20000, log=None)
     _tp.tp_far_fit_normalisation(ctx)
+    # the loss of the initial network on one batch: a step with learning rate 0 leaves the
+    # weights as they are (the first logged loss of train() is taken after 50 steps, when
+    # most of the decrease has already happened)
+    loss0 = _tp.tp_far_train(ctx, 1, 2048, 0.0, 0.0, 99)
     hist = far_train.train(ctx, 800, 2048, 2e-3, log=None)
-    # the first logged loss is already after 50 steps; training is not bit-reproducible
-    # (FP32 atomic gradient sums), so ask for a clear but not a fixed-factor decrease
-    assert hist[-1][1] < 0.7 * hist[0][1], hist[:3] + hist[-3:]
+    assert hist[-1][1] < 0.5 * loss0, (loss0, hist[:3], hist[-3:])
     path = str(tmp_path / "m.bin")
     _tp.tp_far_model_save(ctx, path)
     V, F = meshgen.sh_deformed_sphere(5, 12, 0.05, 2000)
@@ -165,11 +167,18 @@ def test_training_lowers_the_far_field_error(tp, ctx, tmp_path):
         el = tp.tp_gradient(ctx2, gl, tp.tp_params_default(mode=tp.TP_LEARNED, theta=0.5))
         st = tp.tp_get_stats(ctx2)
         assert st["learned_terms"] > 0.5 * st["far_terms"]
+        ge = np.zeros_like(V)
+        ee = tp.tp_gradient(ctx2, ge, tp.tp_params_default(mode=tp.TP_LEARNED, theta=0.5,
+                                                           flags=_tp.TP_LEARNED_ENERGY))
         err_b, err_l = abs(eb - ed) / ed, abs(el - ed) / ed
         gerr_b, gerr_l = rel(gb, gd), rel(gl, gd)
         print(f"energy error BH {err_b:.3e} learned {err_l:.3e}; gradient error BH {gerr_b:.3e} learned {gerr_l:.3e}")
         assert err_l < 0.5 * err_b
-        assert gerr_l < 1.1 * gerr_b
+        # at the trained opening angle the corrected force channels pay as well
+        assert gerr_l <= gerr_b
+        # energy channels only: the same energy, and plain Barnes-Hut's gradient
+        assert abs(ee - el) <= 1e-9 * abs(el)
+        assert rel(ge, gb) <= 1e-9
     finally:
         tp.tp_destroy(ctx2)
 
