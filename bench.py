@@ -78,6 +78,7 @@ def parse():
     ap.add_argument("--far-model", default=DEFAULT_FAR_MODEL,
                     help="trained far-field model (learned mode; default: the packaged level-7 model)")
     ap.add_argument("--theta", type=float, default=0.25)
+    ap.add_argument("--dual-theta", type=float, default=0.25, help="opening angle of the dual form in --inloop runs")
     ap.add_argument("--quad", type=int, default=1, choices=[1, 3, 6],
                     help="quadrature points per triangle for both integrals (tp_set_quadrature)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -87,6 +88,10 @@ def parse():
     ap.add_argument("--inloop", type=int, default=0,
                     help="run N successive evaluations under a seeded smooth displacement (step 1e-3) with the "
                          "tree rebuilt every step, comparing direct, Barnes-Hut and learned forms")
+    ap.add_argument("--inloop-thetas", type=float, nargs="+", default=None,
+                    help="opening angles of the clustered forms in --inloop runs (default: --theta)")
+    ap.add_argument("--inloop-ref-every", type=int, default=10,
+                    help="in --inloop runs, evaluate the FP64 reference every N steps and on the last")
     return ap.parse_args()
 
 
@@ -261,14 +266,22 @@ def inloop(args):
     Fd = torch.tensor(F, device=dev)
     tp.tp_mesh_upload(ctx, Vd, Fd)
     X = V.copy()
-    times = {"direct": [], "bh": [], "learned": []}
+    thetas = args.inloop_thetas or [args.theta]
+    kinds = [("bh", tp.TP_BH, 0), ("dual", tp.TP_BH_DUAL, 0)]
+    if learned:
+        kinds += [("learned", tp.TP_LEARNED, 0), ("learned_energy", tp.TP_LEARNED, _tp.TP_LEARNED_ENERGY)]
+    modes = [(f"{name}@{args.dual_theta if m == tp.TP_BH_DUAL else th:g}", m, fl,
+              args.dual_theta if m == tp.TP_BH_DUAL else th)
+             for th in thetas for name, m, fl in kinds]
+    modes = list({mo[0]: mo for mo in modes}.values())  # the dual form once
+    times = {"direct": []}
+    times.update({mo[0]: [] for mo in modes})
     errs = []
-    modes = [("bh", tp.TP_BH)] + ([("learned", tp.TP_LEARNED)] if learned else [])
     for k in range(args.inloop):
         Vd.copy_(torch.from_numpy(X))
         tp.tp_mesh_upload(ctx, Vd, None, flags=_tp.TP_POSITIONS_ONLY)
         t_up = tp.tp_get_stats(ctx)["ms_total"]
-        ref = k % 10 == 0 or k == args.inloop - 1
+        ref = k % args.inloop_ref_every == 0 or k == args.inloop - 1
         if ref:
             # the FP64 direct sum (FP64 pair terms and sums, the form the tests hold to the
             # oracle) is the reference; the FP32-term direct sum is timed and compared too
@@ -283,9 +296,9 @@ def inloop(args):
         if ref:
             row["direct"] = {"energy_err": abs(e32 - ed) / abs(ed),
                              "grad_err": float(torch.linalg.norm(g32 - gd) / torch.linalg.norm(gd))}
-        for name, m in modes:
+        for name, m, fl, th in modes:
             g = torch.zeros_like(Vd)
-            e = tp.tp_gradient(ctx, g, tp.tp_params_default(mode=m, theta=args.theta))
+            e = tp.tp_gradient(ctx, g, tp.tp_params_default(mode=m, theta=th, flags=fl))
             times[name].append(t_up + t_tree + tp.tp_get_stats(ctx)["ms_total"])
             if ref:
                 row[name] = {"energy_err": abs(e - ed) / abs(ed),
@@ -296,10 +309,11 @@ def inloop(args):
         X = X + 1e-3 * meshgen.smooth_displacement(X, seed=4)
     tp.tp_destroy(ctx)
     out = {"metric": "in-loop TP energy+grad ms/eval", "workload": WORKLOADS[args.workload], "nt": int(F.shape[0]),
-           "steps": args.inloop, "theta": args.theta,
+           "steps": args.inloop, "thetas": thetas, "dual_theta": args.dual_theta,
            "ms_per_eval_median": {k: (statistics.median(v) if v else None) for k, v in times.items()},
            "reference": "direct sum in FP64 (FP64 pair terms and sums; held to the oracle by the tests), evaluated "
-                        "on every 10th step and the last; errors are relative (energy) and relative L2 (gradient)",
+                        f"on every {args.inloop_ref_every}th step and the last; errors are relative (energy) and "
+                        "relative L2 (gradient)",
            "errors": errs}
     print(json.dumps(out), flush=True)
     return 0

@@ -67,8 +67,10 @@ enum { TP_DTYPE_F32 = 0, TP_DTYPE_F64 = 1 };
 #define TP_POSITIONS_ONLY 0x2u  /* re-upload V only; keep faces and derived topology   */
 /* flags of tp_params */
 #define TP_EXCLUDE_EDGE 0x4u    /* exclude only pairs sharing an edge (default: a vertex) */
-#define TP_LEARNED_ENERGY 0x8u  /* TP_LEARNED: the network corrects the two energy channels only; U and
-                                   the force channels keep the monopole, so the gradient is TP_BH's */
+#define TP_LEARNED_ENERGY 0x8u  /* TP_LEARNED: the network's factors correct the energy value only:
+                                   every per-triangle derivative keeps the plain monopole (the gradient
+                                   and tp_fields are TP_BH's) and the correction of the two energy
+                                   channels is added to the returned energy */
 
 typedef struct {
     int32_t q, p;   /* exponents: q even, p even; supported (6,12) and (8,16)       */

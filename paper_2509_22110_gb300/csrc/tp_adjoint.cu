@@ -130,7 +130,9 @@ __global__ void k_sum_partial(const double* __restrict__ in, int64_t n, int64_t 
     if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-__global__ void k_sum_final(const double* __restrict__ part, int nb, double mul, double* __restrict__ out) {
+// out = mul * (sum of the partials + *add), add may be null
+__global__ void k_sum_final(const double* __restrict__ part, int nb, double mul, const double* __restrict__ add,
+                            double* __restrict__ out) {
     __shared__ double sh[256];
     double s = 0.0;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
@@ -140,7 +142,7 @@ __global__ void k_sum_final(const double* __restrict__ part, int nb, double mul,
         if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[0] = mul * sh[0];
+    if (threadIdx.x == 0) out[0] = mul * (sh[0] + (add ? *add : 0.0));
 }
 
 }  // namespace
@@ -178,21 +180,24 @@ tp_status tp_launch_fields(tp_ctx* ctx, const tp_params* prm, double* fw, double
     return TP_OK;
 }
 
-static tp_status reduce_strided(tp_ctx* ctx, const double* in, int64_t n, int64_t stride, double mul, double* d_out) {
+static tp_status reduce_strided(tp_ctx* ctx, const double* in, int64_t n, int64_t stride, double mul, double* d_out,
+                                const double* add = nullptr) {
     const int nb = 512;
     double* part = ctx->red + (ctx->red_cap - nb);
     k_sum_partial<<<nb, 256, 0, ctx->stream>>>(in, n, stride, part);
     ++ctx->nlaunch;
-    k_sum_final<<<1, 256, 0, ctx->stream>>>(part, nb, mul, d_out);
+    k_sum_final<<<1, 256, 0, ctx->stream>>>(part, nb, mul, add, d_out);
     ++ctx->nlaunch;
     TP_CU(cudaGetLastError());
     return TP_OK;
 }
 
 // Phi = c * sum_T Ew_T / (2 p/q): every unordered pair adds (p/q)(e_TS + e_ST) to both ends.
+// The learned form's energy-only correction (TP_LEARNED_ENERGY) is added to the sum.
 tp_status tp_launch_energy_from_acc(tp_ctx* ctx, const tp_params* prm, double* d_out) {
     const double pq = (double)prm->p / prm->q;
-    return reduce_strided(ctx, ctx->acc, ctx->ntp, 1, prm->scale / (2.0 * pq), d_out);
+    const bool eo = prm->mode == TP_LEARNED && (prm->flags & TP_LEARNED_ENERGY);
+    return reduce_strided(ctx, ctx->acc, ctx->ntp, 1, prm->scale / (2.0 * pq), d_out, eo ? ctx->scalar + 6 : nullptr);
 }
 
 // mul * sum over triangles of the accumulator Ew

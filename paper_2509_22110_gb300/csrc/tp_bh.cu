@@ -707,8 +707,12 @@ __global__ void __launch_bounds__(NR_WARPS * 32) k_near(BHArgs A) {
 // gradient error (level-7 sphere, theta = 0.25, a model trained at theta =
 // 0.25 and 0.5: 8.3e-3 with it, 3.9e-3 without, 4.4e-3 for plain Barnes-Hut).  (The plain form evaluates its far
 // nodes inside k_bh, straight from the traversal's staged list.)
-template <int Q>
-__device__ __forceinline__ void far_pair2_learned(const Tgt2& t, const float* rec, const float* fk, float2 acc[8]) {
+// EO (energy only): fk[0], fk[1] hold f0 - 1 and f1 - 1, every accumulator
+// takes the monopole, and the energy correction wts ((f0-1) al^q + (f1-1) be^q)
+// goes to dacc.
+template <int Q, bool EO>
+__device__ __forceinline__ void far_pair2_learned(const Tgt2& t, const float* rec, const float* fk, float2 acc[8],
+                                                  float2& dacc) {
     const float4* r = reinterpret_cast<const float4*>(rec);
     const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4];
     const float2 sh[3] = {make_float2(r0.x, r0.y), make_float2(r0.z, r0.w), make_float2(r1.x, r1.y)};
@@ -747,6 +751,19 @@ __device__ __forceinline__ void far_pair2_learned(const Tgt2& t, const float* re
     }
     const float2 wi = bh_mul2(wts, inv);
     const float2 A5 = bh_mul2(wi, al5), B5 = bh_mul2(wi, be5);
+    if constexpr (EO) {
+        const float2 s6 = bh_add2(alq, beq);
+        const float2 nk = bh_mul2(bh_mul2(wi, s6), bh_f2(-2.0f));
+        acc[0] = bh_fma2(wts, s6, acc[0]);
+        dacc = bh_fma2(wts, bh_fma2(bh_f2(f03.y), beq, bh_mul2(bh_f2(f03.x), alq)), dacc);
+        acc[1] = bh_add2(acc[1], A5);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            acc[2 + k] = bh_fma2(A5, d[k], acc[2 + k]);
+            acc[5 + k] = bh_fma2(nk, d[k], bh_fma2(B5, sn[k], acc[5 + k]));
+        }
+        return;
+    }
     const float2 se = bh_fma2(bh_f2(f03.y), beq, bh_mul2(bh_f2(f03.x), alq));
     const float2 sk = bh_fma2(bh_f2(f47.z), beq, bh_mul2(bh_f2(f47.y), alq));
     const float2 nk = bh_mul2(bh_mul2(wi, sk), bh_f2(-2.0f));  // -(p/q) wts inv (f5 al^q + f6 be^q)
@@ -809,13 +826,14 @@ __global__ void k_run_keys(const tp_far_run* __restrict__ runs, int64_t nruns, i
 }
 
 
-// energy_only: the network's factors are applied to the two energy channels
-// only; U and the force channels keep the monopole (the gradient is then that
-// of plain Barnes-Hut).
-template <int Q>
+// EO (TP_LEARNED_ENERGY): every per-target sum takes the plain monopole (the
+// gradient is that of plain Barnes-Hut) and the network's correction of the
+// two energy channels, sum of wts ((f0-1) al^q + (f1-1) be^q), is added to
+// *de, which the energy reduction adds to the sum of the per-target energies.
+template <int Q, bool EO>
 __global__ void __launch_bounds__(FAR_WARPS * 32) k_far(BHArgs A, const float* __restrict__ kf, int64_t w0,
                                                          int64_t w1, const int64_t* __restrict__ skey,
-                                                         const int32_t* __restrict__ sord, int energy_only) {
+                                                         const int32_t* __restrict__ sord, double* __restrict__ de) {
     __shared__ __align__(16) float s_rec[FAR_WARPS][32 * TP_SRCW];  // duplicated records of a batch
     __shared__ __align__(16) float s_fk[FAR_WARPS][32 * 8];         // channel factors of a batch
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -868,6 +886,7 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) k_far(BHArgs A, const float* _
 #pragma unroll
         for (int c = 0; c < 8; ++c) a2[c] = bh_f2(0.f);
         double e64[2] = {0.0, 0.0};
+        double de_lane = 0.0;
         // this lane's row of a batch, loaded one batch ahead
         float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0, q2 = q0, k0 = q0, k1 = q0;
         auto load_row = [&](int b0, int nb) {
@@ -895,8 +914,8 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) k_far(BHArgs A, const float* _
                 d[4] = make_float4(q2.x, q2.x, q2.y, q2.y);  // nubar[2], area
                 // factors exp(y_c) = 1 + (exp(y_c) - 1); the network wrote exp(y_c) - 1
                 float4* f = reinterpret_cast<float4*>(fk + lane * 8);
-                if (energy_only) {
-                    f[0] = make_float4(1.f + k0.x, 1.f + k0.y, 1.f, 1.f);
+                if (EO) {
+                    f[0] = make_float4(k0.x, k0.y, 1.f, 1.f);  // f0 - 1, f1 - 1
                     f[1] = make_float4(1.f, 1.f, 1.f, k1.w);
                 } else {
                     f[0] = make_float4(1.f + k0.x, 1.f + k0.y, 1.f + k0.z, 1.f + k0.w);
@@ -911,12 +930,14 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) k_far(BHArgs A, const float* _
                 nb = rlen - (b0 + 32) < 32 ? rlen - (b0 + 32) : 32;
                 load_row(b0 + 32, nb);
             }
+            float2 dacc = bh_f2(0.f);
             if (g < ng) {
-                for (int j = g; j < n; j += ng) far_pair2_learned<Q>(tg, rec + j * TP_SRCW, fk + j * 8, a2);
+                for (int j = g; j < n; j += ng) far_pair2_learned<Q, EO>(tg, rec + j * TP_SRCW, fk + j * 8, a2, dacc);
             }
             e64[0] += (double)a2[0].x;
             e64[1] += (double)a2[0].y;
             a2[0] = bh_f2(0.f);
+            if (EO) de_lane += (double)dacc.x + (double)dacc.y;
         }
         // sum the streams through shared memory and add to the targets
         __syncwarp();
@@ -949,6 +970,10 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) k_far(BHArgs A, const float* _
 #pragma unroll
                 for (int c = 1; c < 8; ++c) atomicAdd(&A.acc[c * A.ntp + k], (double)(h ? a2[c].y : a2[c].x));
             }
+        }
+        if (EO) {
+            for (int o = 16; o > 0; o >>= 1) de_lane += __shfl_xor_sync(0xffffffffu, de_lane, o);
+            if (lane == 0 && de_lane != 0.0) atomicAdd(de, de_lane);
         }
         __syncwarp();  // the staging buffers are reused by the next run
     }
@@ -1177,6 +1202,7 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
     }
     if (learned) {
         TP_TRY(tp_ensure_node_features(ctx));
+        TP_CU(cudaMemsetAsync(ctx->scalar + 6, 0, sizeof(double), ctx->stream));
         // network rows and factors of the listed (leaf, cluster) pairs, for one
         // window of at most ctx->learned_window rows at a time
         const int64_t win = std::min<int64_t>(std::max<int64_t>(listed_rows, 32), ctx->learned_window);
@@ -1236,13 +1262,22 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
                                                                 ctx->run_ord_s);
             TP_TRY(tp_launch_mlp_tc(ctx, A.wb, A.mbias, ctx->far_X, w1 - w0, ctx->far_kf, 0));
             TP_CU(cudaMemsetAsync(ctx->far_count + 2, 0, sizeof(unsigned long long), ctx->stream));
-            const int eonly = (prm->flags & TP_LEARNED_ENERGY) ? 1 : 0;
-            if (prm->q == 6)
-                k_far<6><<<fblocks, FAR_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_kf, w0, w1, ctx->run_key_s,
-                                                                   ctx->run_ord_s, eonly);
-            else
-                k_far<8><<<fblocks, FAR_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_kf, w0, w1, ctx->run_key_s,
-                                                                   ctx->run_ord_s, eonly);
+            double* de = ctx->scalar + 6;  // energy correction of TP_LEARNED_ENERGY (zeroed per evaluation)
+            if (prm->flags & TP_LEARNED_ENERGY) {
+                if (prm->q == 6)
+                    k_far<6, true><<<fblocks, FAR_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_kf, w0, w1,
+                                                                              ctx->run_key_s, ctx->run_ord_s, de);
+                else
+                    k_far<8, true><<<fblocks, FAR_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_kf, w0, w1,
+                                                                              ctx->run_key_s, ctx->run_ord_s, de);
+            } else {
+                if (prm->q == 6)
+                    k_far<6, false><<<fblocks, FAR_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_kf, w0, w1,
+                                                                               ctx->run_key_s, ctx->run_ord_s, de);
+                else
+                    k_far<8, false><<<fblocks, FAR_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_kf, w0, w1,
+                                                                               ctx->run_key_s, ctx->run_ord_s, de);
+            }
             ctx->nlaunch += 2;
         }
         TP_CU(cudaGetLastError());

@@ -73,9 +73,10 @@ def keep_channels(ctx, channels):
 
 
 def evaluate(ctx, seeds, level, thetas, log=print):
-    """Energy and gradient errors of plain Barnes-Hut and of the learned
-    correction against the direct sum (FP32 pair terms, FP64 accumulation),
-    with the device time of each evaluation, on held-out meshes."""
+    """Energy and gradient errors of plain Barnes-Hut, of the learned correction
+    and of the learned correction of the energy channels only
+    (TP_LEARNED_ENERGY), against the direct sum (FP32 pair terms, FP64
+    accumulation), with the device time of each evaluation, on held-out meshes."""
     import torch
 
     rows = []
@@ -90,18 +91,19 @@ def evaluate(ctx, seeds, level, thetas, log=print):
         _tp.tp_tree_build(ctx, 16, 30)
         tb_ms = _tp.tp_get_stats(ctx)["ms_total"]
         for th in thetas:
-            for mode in (_tp.TP_BH, _tp.TP_LEARNED):
+            for name, mode, flags in (("bh", _tp.TP_BH, 0), ("learned", _tp.TP_LEARNED, 0),
+                                      ("learned_energy", _tp.TP_LEARNED, _tp.TP_LEARNED_ENERGY)):
                 g = torch.zeros_like(Vd)
-                e = _tp.tp_gradient(ctx, g, _tp.tp_params_default(mode=mode, theta=th))
+                e = _tp.tp_gradient(ctx, g, _tp.tp_params_default(mode=mode, theta=th, flags=flags))
                 st = _tp.tp_get_stats(ctx)
-                rows.append(dict(seed=int(s), theta=th, mode="bh" if mode == _tp.TP_BH else "learned",
+                rows.append(dict(seed=int(s), theta=th, mode=name,
                                  energy_err=abs(e - ed) / abs(ed),
                                  grad_err=float(torch.linalg.norm(g - gd) / torch.linalg.norm(gd)),
                                  ms_eval=st["ms_total"] + tb_ms, ms_direct=td,
                                  far_terms=st["far_terms"], learned_terms=st["learned_terms"]))
                 if log:
                     r = rows[-1]
-                    log(f"seed {s} theta {th} {r['mode']:8s}: energy err {r['energy_err']:.3e} grad err "
+                    log(f"seed {s} theta {th} {r['mode']:14s}: energy err {r['energy_err']:.3e} grad err "
                         f"{r['grad_err']:.3e} {r['ms_eval']:.2f} ms (direct {td:.2f} ms)")
     return rows
 
@@ -137,7 +139,7 @@ def main():
         rows = evaluate(ctx, range(*args.eval_seeds), args.level, args.eval_thetas, log=None)
         summ = {}
         for th in args.eval_thetas:
-            for mode in ("bh", "learned"):
+            for mode in ("bh", "learned", "learned_energy"):
                 rs = [r for r in rows if r["theta"] == th and r["mode"] == mode]
                 summ[f"{mode}@{th}"] = {k: {"min": float(np.min([r[k] for r in rs])),
                                             "mean": float(np.mean([r[k] for r in rs])),
@@ -168,7 +170,7 @@ def main():
         rows = evaluate(ctx, range(*args.eval_seeds), args.level, args.eval_thetas)
         summ = {}
         for th in args.eval_thetas:
-            for mode in ("bh", "learned"):
+            for mode in ("bh", "learned", "learned_energy"):
                 rs = [r for r in rows if r["theta"] == th and r["mode"] == mode]
                 summ[f"{mode}@{th}"] = {k: float(np.mean([r[k] for r in rs])) for k in
                                         ("energy_err", "grad_err", "ms_eval", "ms_direct")}

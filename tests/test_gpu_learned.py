@@ -176,9 +176,10 @@ def test_training_lowers_the_far_field_error(tp, ctx, tmp_path):
         assert err_l < 0.5 * err_b
         # at the trained opening angle the corrected force channels pay as well
         assert gerr_l <= gerr_b
-        # energy channels only: the same energy, and plain Barnes-Hut's gradient
-        assert abs(ee - el) <= 1e-9 * abs(el)
-        assert rel(ge, gb) <= 1e-9
+        # energy channels only: the learned energy (same sums, FP32 rounding aside) and
+        # plain Barnes-Hut's gradient (the same monopole terms, summed in another kernel)
+        assert abs(ee - el) <= 1e-6 * abs(el)
+        assert rel(ge, gb) <= 1e-6
     finally:
         tp.tp_destroy(ctx2)
 
