@@ -78,6 +78,7 @@ def parse():
     ap.add_argument("--far-model", default=DEFAULT_FAR_MODEL,
                     help="trained far-field model (learned mode; default: the packaged level-7 model)")
     ap.add_argument("--theta", type=float, default=0.25)
+    ap.add_argument("--leaf", type=int, default=16, help="cluster leaf size of the tree (1-32) in the clustered modes")
     ap.add_argument("--dual-theta", type=float, default=0.25, help="opening angle of the dual form in --inloop runs")
     ap.add_argument("--quad", type=int, default=1, choices=[1, 3, 6],
                     help="quadrature points per triangle for both integrals (tp_set_quadrature)")
@@ -290,7 +291,7 @@ def inloop(args):
             g32 = torch.zeros_like(Vd)
             e32 = tp.tp_gradient(ctx, g32, tp.tp_params_default())
             times["direct"].append(t_up + tp.tp_get_stats(ctx)["ms_total"])
-        tp.tp_tree_build(ctx, 16, 30)
+        tp.tp_tree_build(ctx, args.leaf, 30)
         t_tree = tp.tp_get_stats(ctx)["ms_total"]
         row = {"step": k}
         if ref:
@@ -465,7 +466,7 @@ def main():
         tp.tp_mesh_upload(ctx, Vd, None, flags=_tp.TP_POSITIONS_ONLY)
         launches[0] += tp.tp_get_stats(ctx)["kernel_launches"]
         if mode != tp.TP_DIRECT:
-            tp.tp_tree_build(ctx, 16, 30)
+            tp.tp_tree_build(ctx, args.leaf, 30)
             tst = tp.tp_get_stats(ctx)
             launches[0] += tst["kernel_launches"]
             tree_ms.append(tst["ms_total"])
@@ -539,7 +540,8 @@ def main():
             "data": "synthetic (seeded mesh)",
             "config": {"workload": WORKLOADS[args.workload], "nt": nt, "nv": nv, "mode": args.mode,
                        "quadrature_points_per_triangle": args.quad,
-                       "theta": args.theta if mode != tp.TP_DIRECT else None, "q": 6, "p": 12,
+                       "theta": args.theta if mode != tp.TP_DIRECT else None,
+                       "leaf_size": args.leaf if mode != tp.TP_DIRECT else None, "q": 6, "p": 12,
                        "accumulation": "f64", "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "energy": energy, "gpu_launches": launches[0], "clocks": clk, "roofline": roof,
@@ -571,7 +573,7 @@ def main():
         for _ in range(args.steps):
             tp.tp_mesh_upload(ctx, Vh, None, flags=_tp.TP_POSITIONS_ONLY)
             if mode != tp.TP_DIRECT:
-                tp.tp_tree_build(ctx, 16, 30)
+                tp.tp_tree_build(ctx, args.leaf, 30)
             tp.tp_gradient(ctx, gh, prm)
         torch.cuda.synchronize(dev)
         t_e2e = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
