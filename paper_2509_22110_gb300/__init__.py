@@ -26,6 +26,7 @@ from ._tp import (  # noqa: F401
     TP_F32_F64ACC,
     TP_F64,
     TP_LEARNED,
+    TP_LEARNED_ENERGY,
     TPError,
     tp_conf_gradient,
     tp_conf_upload,

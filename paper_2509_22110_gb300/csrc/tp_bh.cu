@@ -22,7 +22,9 @@
 // shared-memory stack, each lane tests one, and ballots sort them into a far
 // list, two near lists and nodes to open.  A near cluster whose vertex box is
 // apart from the leaf's can hold no triangle adjacent to a target: those are
-// listed for k_near, which sums them without exclusion tests.  Near clusters
+// listed for k_near, which sums them without exclusion tests (and forms d from
+// the hi parts alone when the boxes are at least TP_PRECISE_GAP_REL of the
+// mesh's box diagonal apart, the direct kernels' FAST rule).  Near clusters
 // whose box touches the leaf's (the leaf itself among them) are evaluated in
 // k_bh with the test on every pair, and so are the far terms of the plain
 // form.  These sweeps run in packed FP32x2 arithmetic, one target against two
@@ -53,6 +55,9 @@ constexpr int BH_WARPS = 4;
 constexpr int BH_STACK = 1024;
 constexpr int BH_FAR = 256;
 constexpr int BH_NEAR = 128;
+#ifndef TP_NEAR_FAST
+#define TP_NEAR_FAST 1  // near clusters far enough apart take the hi-part difference only
+#endif
 #ifndef TP_BH_MINB
 #define TP_BH_MINB 5  // resident blocks per SM asked of the register allocator (20 warps)
 #endif
@@ -73,6 +78,7 @@ struct BHArgs {
     const float* nodef;
     const double* adm64;
     const float* adm32;
+    const double* bounds;        // mesh bounding box (min[3], max[3]) of the tree build
     double theta;
     int leaf_size;
     int edge_only;
@@ -87,6 +93,7 @@ struct BHArgs {
     const float* mnorm;          // [4][24] feature mean, std, lo, hi
     // far field: far node ids listed for k_far, in runs of one leaf
     int32_t* far_list;
+    int32_t* far_leaf;           // the leaf (index into leaves) of each listed row
     tp_far_run* far_runs;
     unsigned long long* far_count;  // [0] rows, [1] runs listed (past the capacities), [2] k_far work counter
     int64_t far_cap, run_cap;
@@ -113,14 +120,14 @@ enum { M_BH = 0, M_LIST = 1, M_RECORD = 2 };
 
 // A pair of targets (one per half of t) against one source record of the
 // direct kernels' layout (each value stored twice: x_hi[3], x_lo[3], nu[3], w~).
-template <int Q>
+template <int Q, bool HILO>
 __device__ __forceinline__ void near_pair2(const Tgt2& t, const float* rec, float2 acc[8]) {
     const float4* r = reinterpret_cast<const float4*>(rec);
     const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4];
     const float2 sh[3] = {make_float2(r0.x, r0.y), make_float2(r0.z, r0.w), make_float2(r1.x, r1.y)};
     const float2 sl[3] = {make_float2(r1.z, r1.w), make_float2(r2.x, r2.y), make_float2(r2.z, r2.w)};
     const float2 sn[3] = {make_float2(r3.x, r3.y), make_float2(r3.z, r3.w), make_float2(r4.x, r4.y)};
-    pair_core<Q, false>(t.h, t.l, t.n, t.w, sh, sl, sn, make_float2(r4.z, r4.w), acc, true, true);
+    pair_core<Q, false, HILO>(t.h, t.l, t.n, t.w, sh, sl, sn, make_float2(r4.z, r4.w), acc, true, true);
 }
 
 // Target-leaf constants of the admissibility test.
@@ -129,10 +136,18 @@ struct LeafAdm {
     double cl[3];      // box centre (bl_min + bl_max) * 0.5
     double dl;         // box diagonal
     float out[6], in[6], cl32[3], dl32;
+    float fast2;       // squared box gap from which a near cluster's pairs take the hi parts only
 };
 
-__device__ __forceinline__ void leaf_adm(const double* box, LeafAdm& L) {
-    double dl2 = 0.0;
+__device__ __forceinline__ void leaf_adm(const double* box, const double* bounds, LeafAdm& L) {
+    double dl2 = 0.0, md2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double e = bounds[3 + a] - bounds[a];
+        md2 += e * e;
+    }
+    const float delta = TP_PRECISE_GAP_REL * (float)sqrt(md2);
+    L.fast2 = TP_NEAR_FAST ? delta * delta : INFINITY;
 #pragma unroll
     for (int a = 0; a < 6; ++a) L.bl[a] = box[a];
 #pragma unroll
@@ -205,6 +220,21 @@ __device__ __forceinline__ bool admissible(const LeafAdm& L, const float* c32, c
 }
 
 
+// Squared gap between the leaf's and a cluster's FP32 outward-rounded vertex
+// boxes (a lower bound of the true gap).  Near clusters at least
+// TP_PRECISE_GAP_REL of the mesh's box diagonal away form d from the hi parts
+// alone, as the direct kernels' FAST items do: the relative error of d is then
+// at most about 2^-24 |x| / gap.
+__device__ __forceinline__ float box_gap2(const LeafAdm& L, const float* c32) {
+    float g2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float g = fmaxf(0.f, fmaxf(c32[a] - L.out[3 + a], L.out[a] - c32[3 + a]));
+        g2 = fmaf(g, g, g2);
+    }
+    return g2;
+}
+
 // FP32 outward-rounded vertex boxes strictly apart along some axis.  Two
 // triangles that share a vertex lie in vertex boxes that both hold it, so a
 // near cluster whose box is apart from the target leaf's has no member
@@ -235,7 +265,7 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
     const int64_t L = A.leaves[li];
     const int64_t fL = A.first[L];
     const int cnt = A.last[L] - A.first[L] + 1;
-    if (lane == 0) leaf_adm(A.box + 6 * L, s_la[warp]);
+    if (lane == 0) leaf_adm(A.box + 6 * L, A.bounds, s_la[warp]);
     __syncwarp();
     const LeafAdm& la = s_la[warp];
     const float theta32 = (float)A.theta;
@@ -245,8 +275,8 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
     const int t = wide ? lane : (lane & 15);
     const int half = wide ? 0 : (lane >> 4);
     const int nh = wide ? 1 : 2;
-    const int64_t k = fL + t;
     const bool active = t < cnt;
+    const int64_t k = fL + t;
     Tgt2 tg;
     int3 tf = make_int3(-2, -2, -2);
     if (active) {
@@ -286,7 +316,10 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
         run = __shfl_sync(0xffffffffu, run, 0);
         const bool fits = pos + (unsigned long long)nf <= (unsigned long long)A.far_cap;
         if (fits)
-            for (int i = lane; i < nf; i += 32) A.far_list[pos + i] = far[i];
+            for (int i = lane; i < nf; i += 32) {
+                A.far_list[pos + i] = far[i];
+                A.far_leaf[pos + i] = (int32_t)li;
+            }
         if (lane == 0 && run < (unsigned long long)A.run_cap) {
             tp_far_run fr;
             fr.start = fits ? (int64_t)pos : 0;
@@ -337,8 +370,20 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
         pos = __shfl_sync(0xffffffffu, pos, 0);
         run = __shfl_sync(0xffffffffu, run, 0);
         const bool fits = pos + (unsigned long long)nn <= (unsigned long long)A.near_cap;
-        if (fits)
-            for (int i = lane; i < nn; i += 32) A.near_list[pos + i] = s_near[warp][0][i];
+        if (fits) {
+            // the clusters with hi/lo differences first, then the hi-only ones, so
+            // that k_near's slots (one kind each) stay full
+            int o = 0;
+            for (int kind = 0; kind < 2; ++kind)
+                for (int i0 = 0; i0 < nn; i0 += 32) {
+                    const int i = i0 + lane;
+                    const int2 e = i < nn ? s_near[warp][0][i] : make_int2(0, 0);
+                    const bool take = i < nn && (e.y < 0) == (kind == 1);
+                    const unsigned bal = __ballot_sync(0xffffffffu, take);
+                    if (take) A.near_list[pos + o + __popc(bal & lt)] = e;
+                    o += __popc(bal);
+                }
+        }
         if (lane == 0 && run < (unsigned long long)A.nrun_cap) {
             tp_far_run nr;
             nr.start = fits ? (int64_t)pos : 0;
@@ -406,7 +451,7 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
         const int node = lane < m ? st[sp - 1 - lane] : -1;
         __syncwarp();
         sp -= m;
-        bool is_far = false, is_near = false, is_open = false, touch = false;
+        bool is_far = false, is_near = false, is_open = false, touch = false, fast = false;
         int firstc = 0, cntc = 0, lc = 0, rc = 0;
         if (node >= 0) {
             // everything the test and the push need, loaded in one round: the
@@ -429,7 +474,10 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
             } else if (cntc <= A.leaf_size || node >= A.n - 1) {
                 is_near = true;
                 touch = !boxes_apart(la, c32);
-                if (!touch) n_near += (unsigned long long)cnt * (unsigned long long)cntc;
+                if (!touch) {
+                    n_near += (unsigned long long)cnt * (unsigned long long)cntc;
+                    fast = box_gap2(la, c32) >= la.fast2;
+                }
             } else {
                 is_open = true;
             }
@@ -452,7 +500,8 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
             }
         } else {
             if (is_far) far[nf + __popc(bf & lt)] = node;
-            if (is_near && !touch) s_near[warp][0][nn[0] + __popc(bn0 & lt)] = make_int2(firstc, cntc);
+            // (first member, count); a negative count marks a cluster whose pairs take the hi parts only
+            if (is_near && !touch) s_near[warp][0][nn[0] + __popc(bn0 & lt)] = make_int2(firstc, fast ? -cntc : cntc);
             if (is_near && touch) s_near[warp][1][nn[1] + __popc(bn1 & lt)] = make_int2(firstc, cntc);
         }
         if (is_open) {
@@ -527,7 +576,10 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
 // atomically (runs of one leaf may be
 // in flight in several warps, after k_bh has stored its own part).
 #ifndef TP_NR_SLOT
-#define TP_NR_SLOT 64
+#define TP_NR_SLOT 56
+#endif
+#ifndef TP_NR_BPS
+#define TP_NR_BPS 5  // k_near blocks per SM: 5 x 40 KB of shared memory, 20 warps
 #endif
 constexpr int NR_WARPS = 4;
 constexpr int NR_SLOT = TP_NR_SLOT;  // source records per ring slot
@@ -590,14 +642,24 @@ __global__ void __launch_bounds__(NR_WARPS * 32) k_near(BHArgs A) {
             (h ? tg.w.y : tg.w.x) = v[9];
         }
         __syncwarp();
-        // slot planning: whole clusters while they fit; lane 0 issues the copies
+        // slot planning: whole clusters of one kind (a negative count marks a
+        // cluster whose pairs take the hi parts only) while they fit; lane 0
+        // issues the copies
         int next = 0, ns0 = 0, ns1 = 0;  // records planned into slot 0 / 1 and not yet consumed
+        bool hi0 = false, hi1 = false;   // the slot's clusters take the hi parts only
         auto plan = [&](int b) {
             int n = 0;
             const int i0 = next;
-            while (next < R.len && n + S.ent[next].y <= NR_SLOT) n += S.ent[next++].y;
-            if (b) ns1 = n;
-            else ns0 = n;
+            const bool hi = next < R.len && S.ent[next].y < 0;
+            while (next < R.len && (S.ent[next].y < 0) == hi && n + abs(S.ent[next].y) <= NR_SLOT)
+                n += abs(S.ent[next++].y);
+            if (b) {
+                ns1 = n;
+                hi1 = hi;
+            } else {
+                ns0 = n;
+                hi0 = hi;
+            }
             if (n == 0) {
                 // a cluster larger than a slot cannot occur (leaves hold at most 32)
                 if (next < R.len && lane == 0) tp_dev_error(A.derr, TP_DERR_INTERNAL);
@@ -608,9 +670,10 @@ __global__ void __launch_bounds__(NR_WARPS * 32) k_near(BHArgs A) {
                 int o = 0;
                 for (int e = i0; e < next; ++e) {
                     const int2 en = S.ent[e];
+                    const int c = abs(en.y);
                     tma_load_1d(S.rec[b] + o * TP_SRCW, A.src + (int64_t)en.x * TP_SRCW,
-                                (uint32_t)(en.y * TP_SRCW * 4), &S.bar[b]);
-                    o += en.y;
+                                (uint32_t)(c * TP_SRCW * 4), &S.bar[b]);
+                    o += c;
                 }
             }
         };
@@ -637,8 +700,12 @@ __global__ void __launch_bounds__(NR_WARPS * 32) k_near(BHArgs A) {
                 ns0 = 0;
             }
             const float* rb = S.rec[b];
-            if (g < ng)
-                for (int j = g; j < n; j += ng) near_pair2<Q>(tg, rb + j * TP_SRCW, a2);
+            if (g < ng) {
+                if (b ? hi1 : hi0)
+                    for (int j = g; j < n; j += ng) near_pair2<Q, false>(tg, rb + j * TP_SRCW, a2);
+                else
+                    for (int j = g; j < n; j += ng) near_pair2<Q, true>(tg, rb + j * TP_SRCW, a2);
+            }
             e64[0] += (double)a2[0].x;
             e64[1] += (double)a2[0].y;
             a2[0] = bh_f2(0.f);
@@ -982,83 +1049,14 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) k_far(BHArgs A, const float* _
 
 // ------------------------------------------------------------ learned correction
 // The network scales each channel of the far term of a listed (leaf L,
-// cluster C) pair by a factor.  Two passes over the listed pairs come before
-// k_far applies the factors:
-//   k_far_feat - one warp per run: the 24 normalised features of every
-//                (L, C) pair as a BF16 row (column 31 = 1 when the raw
-//                features lie in the training ranges, else 0);
-//   k_mlp_tc   - the network on 128-row tiles on the 5th-generation tensor
-//                cores (tcgen05.mma, operands in shared memory, FP32
-//                accumulators in tensor memory; tp_tc.cu): exp(y_c) - 1 per
-//                channel (0 outside the ranges).
-constexpr int FL_WARPS = 8;
-
-__global__ void __launch_bounds__(FL_WARPS * 32, 2) k_far_feat(BHArgs A, __nv_bfloat16* __restrict__ X, int64_t w0,
-                                                                int64_t w1, const int64_t* __restrict__ skey,
-                                                                const int32_t* __restrict__ sord) {
-    __shared__ float s_norm[4 * MLP_NI];  // mean, 1/std, lower and upper admitted bound per feature
-    for (int i = threadIdx.x; i < MLP_NI; i += blockDim.x) {
-        const float lo = A.mnorm[2 * MLP_NI + i], hi = A.mnorm[3 * MLP_NI + i], pad = 0.05f * (hi - lo);
-        s_norm[i] = A.mnorm[i];
-        s_norm[MLP_NI + i] = 1.0f / A.mnorm[MLP_NI + i];
-        s_norm[2 * MLP_NI + i] = lo - pad;
-        s_norm[3 * MLP_NI + i] = hi + pad;
-    }
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned long long nr = A.far_count[1];
-    const int64_t nruns = nr < (unsigned long long)A.run_cap ? (int64_t)nr : A.run_cap;
-    int64_t rlo, rhi;
-    window_runs(skey, nruns, w0, w1, rlo, rhi);
-    for (int64_t run = rlo + (int64_t)blockIdx.x * FL_WARPS + warp; run < rhi; run += (int64_t)gridDim.x * FL_WARPS) {
-        const tp_far_run R = A.far_runs[sord[run]];
-        // the run's rows inside this window of rows [w0, w1); X holds the window's rows
-        const int64_t r0 = R.start > w0 ? R.start : w0;
-        const int64_t r1 = R.start + R.len < w1 ? R.start + R.len : w1;
-        if (r0 >= r1) continue;
-        const int rlen = (int)(r1 - r0);
-        const float* fl = A.nodeft + 16 * (int64_t)A.leaves[R.li];
-        // the cluster record of this lane's next row is loaded while this row is
-        // computed (the rows' records are random accesses: 6 % less learned time)
-        float4 cq[4];
-        auto load_c = [&](int i) {
-            if (i < rlen) {
-                const float4* p = reinterpret_cast<const float4*>(A.nodeft + 16 * (int64_t)A.far_list[r0 + i]);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) cq[q] = p[q];
-            }
-        };
-        load_c(lane);
-        for (int i = lane; i < rlen; i += 32) {
-            const int64_t row = r0 + i;
-            float f[MLP_NI];
-            const float cr[16] = {cq[0].x, cq[0].y, cq[0].z, cq[0].w, cq[1].x, cq[1].y, cq[1].z, cq[1].w,
-                                  cq[2].x, cq[2].y, cq[2].z, cq[2].w, cq[3].x, cq[3].y, cq[3].z, cq[3].w};
-            load_c(i + 32);
-            far_features(fl, cr, f);
-            int in_dist = 1;
-            uint32_t pk[16];
-#pragma unroll
-            for (int c = 0; c < MLP_NI; c += 2) {
-                float v[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (!(f[c + h] >= s_norm[2 * MLP_NI + c + h] && f[c + h] <= s_norm[3 * MLP_NI + c + h]))
-                        in_dist = 0;
-                    v[h] = (f[c + h] - s_norm[c + h]) * s_norm[MLP_NI + c + h];
-                }
-                pk[c / 2] = pack_bf16(v[0], v[1]);
-            }
-#pragma unroll
-            for (int c = MLP_NI / 2; c < 15; ++c) pk[c] = 0u;
-            pk[15] = pack_bf16(0.f, in_dist ? 1.f : 0.f);  // column 31: the range flag (zero weight column)
-            uint4* dst = reinterpret_cast<uint4*>(X + (row - w0) * MLP_NIP);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
-        }
-    }
-}
-
+// cluster C) pair by a factor.  One pass over the listed pairs comes before
+// k_far applies the factors: k_mlp_tc<true> (tp_tc.cu) builds each row's 24
+// normalised features from the feature records of L and C as a BF16 row in
+// shared memory (column 31 = 1 when the raw features lie in the training
+// ranges, else 0) and runs the network on 128-row tiles on the
+// 5th-generation tensor cores (tcgen05.mma, operands in shared memory, FP32
+// accumulators in tensor memory): exp(y_c) - 1 per channel (0 outside the
+// ranges).
 BHArgs make_bh_args(tp_ctx* ctx, double theta, int edge_only) {
     tp_tree& t = ctx->tree;
     BHArgs A;
@@ -1078,6 +1076,7 @@ BHArgs make_bh_args(tp_ctx* ctx, double theta, int edge_only) {
     A.nodef = t.nodef;
     A.adm64 = t.adm64;
     A.adm32 = t.adm32;
+    A.bounds = ctx->bounds;
     A.nodeft = t.nodeft;
     A.theta = theta;
     A.leaf_size = t.leaf_size;
@@ -1114,6 +1113,7 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
     auto alloc_far = [&](int64_t rows, int64_t runs) -> tp_status {
         rows = (rows + 31) / 32 * 32;  // whole 32-row network batches
         TP_TRY(tp_alloc_t(ctx, &ctx->far_list, rows));
+        TP_TRY(tp_alloc_t(ctx, &ctx->far_leaf, rows));
         TP_TRY(tp_alloc_t(ctx, &ctx->far_runs, runs));
         for (void* p : {(void*)ctx->run_key, (void*)ctx->run_key_s, (void*)ctx->run_ord, (void*)ctx->run_ord_s})
             tp_free(ctx, p);
@@ -1135,7 +1135,7 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
         const int64_t rows = std::max<int64_t>(1 << 20, t.nleaves * 1024);
         TP_TRY(alloc_far(rows, rows / 32 + t.nleaves + 1024));
     }
-    const unsigned nblocks = (unsigned)std::max(1, ctx->num_sms * 4);
+    const unsigned nblocks = (unsigned)std::max(1, ctx->num_sms * TP_NR_BPS);
     const unsigned fblocks = (unsigned)std::max(1, ctx->num_sms * 4);
     cudaEventRecord(ctx->ev[0], ctx->stream);
     int64_t listed_rows = 0, listed_runs = 0;
@@ -1153,6 +1153,7 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
         A.near_cap = ctx->near_cap;
         A.nrun_cap = ctx->nrun_cap;
         A.far_list = ctx->far_list;
+        A.far_leaf = ctx->far_leaf;
         A.far_runs = ctx->far_runs;
         A.far_count = ctx->far_count;
         A.far_cap = ctx->far_cap;
@@ -1194,8 +1195,10 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
         }
         if (!far_ok) {
             tp_free(ctx, ctx->far_list);
+            tp_free(ctx, ctx->far_leaf);
             tp_free(ctx, ctx->far_runs);
             ctx->far_list = nullptr;
+            ctx->far_leaf = nullptr;
             ctx->far_runs = nullptr;
             TP_TRY(alloc_far((int64_t)(fc[0] + fc[0] / 4 + 1024), (int64_t)(fc[1] + fc[1] / 4 + 1024)));
         }
@@ -1203,17 +1206,14 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
     if (learned) {
         TP_TRY(tp_ensure_node_features(ctx));
         TP_CU(cudaMemsetAsync(ctx->scalar + 6, 0, sizeof(double), ctx->stream));
-        // network rows and factors of the listed (leaf, cluster) pairs, for one
-        // window of at most ctx->learned_window rows at a time
+        // factors of the listed (leaf, cluster) pairs, for one window of at most
+        // ctx->learned_window rows at a time
         const int64_t win = std::min<int64_t>(std::max<int64_t>(listed_rows, 32), ctx->learned_window);
         const int64_t xcap = win + BH_FAR;  // a window ends on a run start, at most BH_FAR - 1 rows late
         if (ctx->far_xcap < xcap) {
-            tp_free(ctx, ctx->far_X);
             tp_free(ctx, ctx->far_kf);
-            ctx->far_X = nullptr;
             ctx->far_kf = nullptr;
             ctx->far_xcap = 0;
-            TP_TRY(tp_alloc_t(ctx, &ctx->far_X, xcap * MLP_NIP));
             TP_TRY(tp_alloc_t(ctx, &ctx->far_kf, xcap * 8));
             ctx->far_xcap = xcap;
         }
@@ -1251,16 +1251,19 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
             TP_CU(cudaStreamSynchronize(ctx->stream));
         }
         // per window: the network's factors of the listed far terms, then the far terms with them
-        const unsigned lblocks = (unsigned)std::max(1, ctx->num_sms * 4);
+        tp_feat_src fs;
+        fs.nodeft = t.nodeft;
+        fs.far_list = ctx->far_list;
+        fs.far_leaf = ctx->far_leaf;
+        fs.leaves = t.leaves;
+        fs.mnorm = A.mnorm;
         for (size_t wi = 0; wi + 1 < bnd.size(); ++wi) {
             const int64_t w0 = bnd[wi], w1 = bnd[wi + 1];
             if (w1 <= w0) continue;
             if (w1 - w0 > ctx->far_xcap)  // cannot happen while runs hold at most BH_FAR rows
                 return tp_set_err(ctx, TP_E_STATE, "internal: learned window of %lld rows above %lld",
                                   (long long)(w1 - w0), (long long)ctx->far_xcap);
-            k_far_feat<<<lblocks, FL_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_X, w0, w1, ctx->run_key_s,
-                                                                ctx->run_ord_s);
-            TP_TRY(tp_launch_mlp_tc(ctx, A.wb, A.mbias, ctx->far_X, w1 - w0, ctx->far_kf, 0));
+            TP_TRY(tp_launch_mlp_tc_feat(ctx, A.wb, A.mbias, fs, w0, w1, ctx->far_kf));
             TP_CU(cudaMemsetAsync(ctx->far_count + 2, 0, sizeof(unsigned long long), ctx->stream));
             double* de = ctx->scalar + 6;  // energy correction of TP_LEARNED_ENERGY (zeroed per evaluation)
             if (prm->flags & TP_LEARNED_ENERGY) {
@@ -1278,7 +1281,7 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
                     k_far<8, false><<<fblocks, FAR_WARPS * 32, 0, ctx->stream>>>(A, ctx->far_kf, w0, w1,
                                                                                ctx->run_key_s, ctx->run_ord_s, de);
             }
-            ctx->nlaunch += 2;
+            ++ctx->nlaunch;
         }
         TP_CU(cudaGetLastError());
         TP_CU(cudaMemcpyAsync(h + 3, counts + 3, sizeof(h[3]), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1307,7 +1310,7 @@ tp_status tp_launch_near_runs(tp_ctx* ctx, int q, const int2* list, int64_t list
     A.near_cap = list_len;
     A.nrun_cap = run_cap;
     TP_CU(cudaMemsetAsync(counters + 2, 0, sizeof(unsigned long long), ctx->stream));
-    const unsigned nblocks = (unsigned)std::max(1, ctx->num_sms * 4);
+    const unsigned nblocks = (unsigned)std::max(1, ctx->num_sms * TP_NR_BPS);
     if (q == 6) k_near<6><<<nblocks, NR_WARPS * 32, 0, ctx->stream>>>(A);
     else k_near<8><<<nblocks, NR_WARPS * 32, 0, ctx->stream>>>(A);
     ++ctx->nlaunch;

@@ -191,13 +191,13 @@ void tp_drop_mesh_state(tp_ctx* ctx) {
     free_ptr(ctx, ctx->near_runs);
     ctx->near_cap = ctx->nrun_cap = 0;
     free_ptr(ctx, ctx->far_list);
+    free_ptr(ctx, ctx->far_leaf);
     free_ptr(ctx, ctx->far_runs);
     free_ptr(ctx, ctx->run_key);
     free_ptr(ctx, ctx->run_key_s);
     free_ptr(ctx, ctx->run_ord);
     free_ptr(ctx, ctx->run_ord_s);
     ctx->far_cap = ctx->run_cap = 0;
-    free_ptr(ctx, ctx->far_X);
     free_ptr(ctx, ctx->far_kf);
     ctx->far_xcap = 0;
     free_ptr(ctx, ctx->win_bnd);

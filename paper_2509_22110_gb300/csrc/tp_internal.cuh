@@ -208,12 +208,12 @@ struct tp_ctx {
     float* conf_src = nullptr;   // [ntp][TP_SRCW] records relative to the evolving mesh's centre
     // far (leaf, cluster) pairs listed by the Barnes-Hut pass for the learned correction
     int32_t* far_list = nullptr;
+    int32_t* far_leaf = nullptr;  // [far_cap] the leaf (index into the leaf list) of each listed row
     tp_far_run* far_runs = nullptr;
     unsigned long long* far_count = nullptr;  // [0] rows, [1] runs listed (may exceed the capacities), [2] work counter
-    __nv_bfloat16* far_X = nullptr;  // [far_cap][32] BF16 network inputs of the listed pairs
-    float* far_kf = nullptr;         // [far_cap][8] factors - 1 (column 7: in the training ranges)
+    float* far_kf = nullptr;         // [far_xcap][8] factors - 1 of one window (column 7: in the training ranges)
     int64_t far_cap = 0, run_cap = 0;
-    int64_t far_xcap = 0;             // rows of far_X and far_kf
+    int64_t far_xcap = 0;             // rows of far_kf
     // the far runs sorted by first row (keys, run indices; unsorted inputs too), so
     // that each window of the learned passes visits only its own runs
     int64_t *run_key = nullptr, *run_key_s = nullptr;
@@ -295,6 +295,18 @@ tp_status tp_build_exclusion_bits(tp_ctx* ctx);
 tp_status take_device_error(tp_ctx* ctx, const char* where);  // read and clear the device error word
 tp_status tp_launch_mlp_tc(tp_ctx* ctx, const __nv_bfloat16* wb, const float* bias, const __nv_bfloat16* X,
                            int64_t rows, float* kf, int raw);
+// The network on the listed far rows [w0, w1) with their input rows built in
+// the kernel (features of nodeft[leaves[far_leaf[r]]] and nodeft[far_list[r]],
+// normalised with mnorm): kf[r - w0] as tp_launch_mlp_tc with raw = 0.
+struct tp_feat_src {
+    const float* nodeft;
+    const int32_t* far_list;
+    const int32_t* far_leaf;
+    const int32_t* leaves;
+    const float* mnorm;
+};
+tp_status tp_launch_mlp_tc_feat(tp_ctx* ctx, const __nv_bfloat16* wb, const float* bias, const tp_feat_src& fs,
+                                int64_t w0, int64_t w1, float* kf);
 tp_status tp_launch_conf(tp_ctx* ctx, const tp_params* prm);
 tp_status tp_launch_energy_scaled(tp_ctx* ctx, double mul, double* d_out);
 tp_status tp_build_v2t(tp_ctx* ctx);

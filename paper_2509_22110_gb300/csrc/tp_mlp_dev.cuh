@@ -336,3 +336,28 @@ __device__ __forceinline__ void far_features(const float* L, const float* C, flo
     f[22] = sqrtf(C[4] * C[4] + C[5] * C[5] + C[6] * C[6]);
     f[23] = lc - ll;
 }
+
+// Network input row of one listed (leaf, cluster) pair: the 24 features of
+// far_features normalised with the fitted mean and 1/std (norm[0..23],
+// norm[24..47]) and rounded to BF16 pairs in pk[0..11], pk[12..14] zero, and
+// in the high half of pk[15] (column 31) 1 when every raw feature lies in the
+// admitted range [norm[48 + i], norm[72 + i]], else 0 (a zero-weight column).
+__device__ __forceinline__ void feature_row_bf16(const float* fl, const float* cr, const float* norm,
+                                                 uint32_t (&pk)[16]) {
+    float f[MLP_NI];
+    far_features(fl, cr, f);
+    int in_dist = 1;
+#pragma unroll
+    for (int c = 0; c < MLP_NI; c += 2) {
+        float v[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!(f[c + h] >= norm[2 * MLP_NI + c + h] && f[c + h] <= norm[3 * MLP_NI + c + h])) in_dist = 0;
+            v[h] = (f[c + h] - norm[c + h]) * norm[MLP_NI + c + h];
+        }
+        pk[c / 2] = pack_bf16(v[0], v[1]);
+    }
+#pragma unroll
+    for (int c = MLP_NI / 2; c < 15; ++c) pk[c] = 0u;
+    pk[15] = pack_bf16(0.f, in_dist ? 1.f : 0.f);
+}

@@ -52,14 +52,17 @@ __device__ __forceinline__ void stage_pad(float* stg, int j) {
 // accumulated in the direct kernels' convention.  SEL: per-half admission
 // (v0, v1); an excluded half gets 1/|d|^2 = 0 and weight 0, so its terms are
 // exact zeros (d itself stays finite: a coincident centroid or a padding
-// source's large offset never reaches a power).
-template <int Q, bool SEL>
+// source's large offset never reaches a power).  HILO: d = (hi_T - hi_S) +
+// (lo_T - lo_S); without it d = hi_T - hi_S (pairs far enough apart).
+template <int Q, bool SEL, bool HILO = true>
 __device__ __forceinline__ void pair_core(const float2 (&th)[3], const float2 (&tl)[3], const float2 (&tn)[3],
                                           float2 tw, const float2 (&sh)[3], const float2 (&sl)[3],
                                           const float2 (&sn)[3], float2 sw, float2 acc[8], bool v0, bool v1) {
     float2 d[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) d[k] = bh_add2(bh_add2(th[k], bh_neg2(sh[k])), bh_add2(tl[k], bh_neg2(sl[k])));
+    for (int k = 0; k < 3; ++k)
+        d[k] = HILO ? bh_add2(bh_add2(th[k], bh_neg2(sh[k])), bh_add2(tl[k], bh_neg2(sl[k])))
+                    : bh_add2(th[k], bh_neg2(sh[k]));
     float2 r2 = bh_mul2(d[0], d[0]);
     r2 = bh_fma2(d[1], d[1], r2);
     r2 = bh_fma2(d[2], d[2], r2);

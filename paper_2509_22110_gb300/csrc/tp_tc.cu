@@ -26,6 +26,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <string.h>
+
 #include "tp_internal.cuh"
 #include "tp_mlp_dev.cuh"
 
@@ -186,6 +189,7 @@ struct TcSmem {
     // epilogue overwrites their A operand
     unsigned char act[128 * 64 * 2];
     float bias[MLPF_N];
+    float norm[4 * MLP_NI];  // features: mean, 1/std, lower and upper admitted bound (FEAT)
     uint64_t mbar;
     uint32_t tmem;
 };
@@ -224,10 +228,16 @@ __device__ __forceinline__ void epi_hidden(const uint32_t (&r)[64], const float*
 // training-range flag): kf[row][0..6] = exp(clamp(y, -4, 4)) - 1 (0 outside
 // the ranges), kf[row][7] = the flag; with raw != 0 the outputs y themselves
 // (kf[row][0..6]).  Persistent over 128-row tiles.
+// FEAT: no X; the input row of window row r (listed row w0 + r) is built in
+// the kernel from the feature records of its leaf and cluster
+// (feature_row_bf16), so the rows never go through global memory.  The
+// thread of a row loads the row's node indices one tile ahead.
+template <bool FEAT>
 __global__ void __launch_bounds__(128) k_mlp_tc(const __nv_bfloat16* __restrict__ wb,
                                                 const float* __restrict__ bias_g,
                                                 const __nv_bfloat16* __restrict__ X, int64_t rows,
-                                                float* __restrict__ kf, int raw, unsigned* derr) {
+                                                float* __restrict__ kf, int raw, unsigned* derr, tp_feat_src fs,
+                                                int64_t w0) {
     extern __shared__ __align__(128) unsigned char tsm[];
     TcSmem& S = *reinterpret_cast<TcSmem*>(tsm);
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -236,6 +246,15 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const __nv_bfloat16* __restrict_
     load_tile(wb + MLPB_W3, 64, 64, S.w3, tid, 128);
     load_tile(wb + MLPB_W4, 16, 64, S.w4, tid, 128);
     for (int i = tid; i < MLPF_N; i += 128) S.bias[i] = bias_g[i];
+    if (FEAT) {
+        for (int i = tid; i < MLP_NI; i += 128) {
+            const float lo = fs.mnorm[2 * MLP_NI + i], hi = fs.mnorm[3 * MLP_NI + i], pad = 0.05f * (hi - lo);
+            S.norm[i] = fs.mnorm[i];
+            S.norm[MLP_NI + i] = 1.0f / fs.mnorm[MLP_NI + i];
+            S.norm[2 * MLP_NI + i] = lo - pad;
+            S.norm[3 * MLP_NI + i] = hi + pad;
+        }
+    }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(su32(&S.tmem))
                      : "memory");
@@ -263,14 +282,62 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const __nv_bfloat16* __restrict_
             for (int q = 0; q < 4; ++q) v[q] = src[q];
         }
     };
+    // FEAT: the node indices (leaf list index, cluster) of this thread's row of a tile, -1 past the end
+    auto load_idx = [&](int64_t t, int& lf, int& cn) {
+        const int64_t r = 128 * t + tid;
+        lf = cn = -1;
+        if (t < ntiles && r < rows) {
+            lf = fs.far_leaf[w0 + r];
+            cn = fs.far_list[w0 + r];
+        }
+    };
+    auto feat_row = [&](int ln, int cn, uint4 (&v)[4]) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = make_uint4(0, 0, 0, 0);
+        if (cn < 0) return;
+        float fl[16], cr[16];
+        const float4* pl = reinterpret_cast<const float4*>(fs.nodeft + 16 * (int64_t)ln);
+        const float4* pc = reinterpret_cast<const float4*>(fs.nodeft + 16 * (int64_t)cn);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 a = pl[q], b = pc[q];
+            fl[4 * q] = a.x;
+            fl[4 * q + 1] = a.y;
+            fl[4 * q + 2] = a.z;
+            fl[4 * q + 3] = a.w;
+            cr[4 * q] = b.x;
+            cr[4 * q + 1] = b.y;
+            cr[4 * q + 2] = b.z;
+            cr[4 * q + 3] = b.w;
+        }
+        uint32_t pk[16];
+        feature_row_bf16(fl, cr, S.norm, pk);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+    };
+    // FEAT: the node indices of the next tile's row are loaded at the start of
+    // a tile and its leaf after the first layer; the row itself is built at
+    // the start of its tile (building it during the second layer's MMAs needed
+    // 110 registers, and spills at 96: both slower)
+    int lf_next = -1, c_next = -1, l_next = -1;
     uint4 vnext[4];
-    load_row(blockIdx.x, vnext);
+    if (FEAT) {
+        load_idx(blockIdx.x, lf_next, c_next);
+        l_next = c_next >= 0 ? fs.leaves[lf_next] : -1;
+    } else {
+        load_row(blockIdx.x, vnext);
+    }
     for (int64_t t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
         const int64_t row = 128 * t + tid;
         uint4 v[4];
+        if (FEAT) {
+            feat_row(l_next, c_next, v);
+            load_idx(t + gridDim.x, lf_next, c_next);  // in flight during this tile's first layer
+        } else {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = vnext[q];
-        load_row(t + gridDim.x, vnext);  // in flight during this tile's layers
+            for (int q = 0; q < 4; ++q) v[q] = vnext[q];
+            load_row(t + gridDim.x, vnext);  // in flight during this tile's layers
+        }
         const bool in_dist = (v[3].w >> 16) != 0u;  // column 31
 #pragma unroll
         for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4*>(S.act + tile_off(tid, 8 * q, MLP_NIP)) = v[q];
@@ -298,6 +365,7 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const __nv_bfloat16* __restrict_
             tc_fence_after();
             tc_ld64(taddr, r);
             epi_hidden(r, S.bias + 64 * layer, S.act, tid);
+            if (FEAT && layer == 0) l_next = c_next >= 0 ? fs.leaves[lf_next] : -1;  // in flight until the next tile
         }
         if (failed) break;
         // output layer (N = 16, rows 7..15 of W4 zero)
@@ -353,12 +421,28 @@ tp_status tp_launch_mlp_tc(tp_ctx* ctx, const __nv_bfloat16* wb, const float* bi
                            int64_t rows, float* kf, int raw) {
     TpRange nvtx_range("tp_launch_mlp_tc");
     // per-device attribute: set on the current device at every launch
-    TP_CU(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem)));
+    TP_CU(cudaFuncSetAttribute(k_mlp_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem)));
     const int64_t ntiles = (rows + 127) / 128;
     if (ntiles == 0) return TP_OK;
     // about 40 KB of shared memory and 64 tensor-memory columns per CTA: 5 CTAs per SM
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * 5);
-    k_mlp_tc<<<grid, 128, sizeof(TcSmem), ctx->stream>>>(wb, bias, X, rows, kf, raw, ctx->derr);
+    tp_feat_src none;
+    memset(&none, 0, sizeof(none));
+    k_mlp_tc<false><<<grid, 128, sizeof(TcSmem), ctx->stream>>>(wb, bias, X, rows, kf, raw, ctx->derr, none, 0);
+    ++ctx->nlaunch;
+    TP_CU(cudaGetLastError());
+    return TP_OK;
+}
+
+tp_status tp_launch_mlp_tc_feat(tp_ctx* ctx, const __nv_bfloat16* wb, const float* bias, const tp_feat_src& fs,
+                                int64_t w0, int64_t w1, float* kf) {
+    TpRange nvtx_range("tp_launch_mlp_tc_feat");
+    TP_CU(cudaFuncSetAttribute(k_mlp_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem)));
+    const int64_t rows = w1 - w0;
+    const int64_t ntiles = (rows + 127) / 128;
+    if (ntiles <= 0) return TP_OK;
+    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * 5);
+    k_mlp_tc<true><<<grid, 128, sizeof(TcSmem), ctx->stream>>>(wb, bias, nullptr, rows, kf, 0, ctx->derr, fs, w0);
     ++ctx->nlaunch;
     TP_CU(cudaGetLastError());
     return TP_OK;

@@ -24,8 +24,9 @@ import numpy as np
 from . import _tp, meshgen
 
 
-def sample_meshes(ctx, seeds, level, theta, pairs_per_mesh, seed=0, log=print):
-    """Append sampled, labelled pairs of each mesh to the context's training set."""
+def sample_meshes(ctx, seeds, level, theta, pairs_per_mesh, seed=0, log=print, leaf=16):
+    """Append sampled, labelled pairs of each mesh (tree leaves of up to `leaf`
+    triangles) to the context's training set."""
     import torch
 
     total = 0
@@ -34,7 +35,7 @@ def sample_meshes(ctx, seeds, level, theta, pairs_per_mesh, seed=0, log=print):
         Vd = torch.tensor(V, device="cuda")
         Fd = torch.tensor(F, device="cuda")
         _tp.tp_mesh_upload(ctx, Vd, Fd)
-        _tp.tp_tree_build(ctx, 16, 30)
+        _tp.tp_tree_build(ctx, int(leaf), 30)
         n_far = _tp.tp_far_sample_pairs(ctx, theta, 1.0, 0, 0)
         keep = min(1.0, pairs_per_mesh / max(1, n_far))
         added = _tp.tp_far_sample_pairs(ctx, theta, keep, seed * 1000003 + int(s), int(pairs_per_mesh * 1.2) + 16)
@@ -72,11 +73,15 @@ def keep_channels(ctx, channels):
     _tp.tp_far_set_params(ctx, P, N)
 
 
-def evaluate(ctx, seeds, level, thetas, log=print):
+def evaluate(ctx, seeds, level, thetas, log=print, bh_leaves=(), bh_thetas=(), leaf=16):
     """Energy and gradient errors of plain Barnes-Hut, of the learned correction
     and of the learned correction of the energy channels only
     (TP_LEARNED_ENERGY), against the direct sum (FP32 pair terms, FP64
-    accumulation), with the device time of each evaluation, on held-out meshes."""
+    accumulation), with the device time of each evaluation (tree build
+    included), on held-out meshes.  The tree has leaves of up to `leaf`
+    triangles (the size the model was trained with); for every size in bh_leaves plain Barnes-Hut is evaluated again on a tree
+    with leaves of that size, at the opening angles bh_thetas (rows
+    "bh_leaf<size>")."""
     import torch
 
     rows = []
@@ -88,7 +93,7 @@ def evaluate(ctx, seeds, level, thetas, log=print):
         gd = torch.zeros_like(Vd)
         ed = _tp.tp_gradient(ctx, gd, _tp.tp_params_default())
         td = _tp.tp_get_stats(ctx)["ms_total"]
-        _tp.tp_tree_build(ctx, 16, 30)
+        _tp.tp_tree_build(ctx, int(leaf), 30)
         tb_ms = _tp.tp_get_stats(ctx)["ms_total"]
         for th in thetas:
             for name, mode, flags in (("bh", _tp.TP_BH, 0), ("learned", _tp.TP_LEARNED, 0),
@@ -105,6 +110,18 @@ def evaluate(ctx, seeds, level, thetas, log=print):
                     r = rows[-1]
                     log(f"seed {s} theta {th} {r['mode']:14s}: energy err {r['energy_err']:.3e} grad err "
                         f"{r['grad_err']:.3e} {r['ms_eval']:.2f} ms (direct {td:.2f} ms)")
+        for bl in bh_leaves:
+            for th in bh_thetas:
+                _tp.tp_tree_build(ctx, int(bl), 30)
+                tb = _tp.tp_get_stats(ctx)["ms_total"]
+                g = torch.zeros_like(Vd)
+                e = _tp.tp_gradient(ctx, g, _tp.tp_params_default(mode=_tp.TP_BH, theta=th))
+                st = _tp.tp_get_stats(ctx)
+                rows.append(dict(seed=int(s), theta=th, mode=f"bh_leaf{int(bl)}",
+                                 energy_err=abs(e - ed) / abs(ed),
+                                 grad_err=float(torch.linalg.norm(g - gd) / torch.linalg.norm(gd)),
+                                 ms_eval=st["ms_total"] + tb, ms_direct=td,
+                                 far_terms=st["far_terms"], learned_terms=0))
     return rows
 
 
@@ -112,6 +129,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default="far_model.bin")
     ap.add_argument("--level", type=int, default=7)
+    ap.add_argument("--leaf", type=int, default=16, help="cluster leaf size of the trees (training and evaluation)")
     ap.add_argument("--seeds", type=int, nargs=2, default=[1000, 1050])
     ap.add_argument("--pairs-per-mesh", type=int, default=40000)
     ap.add_argument("--theta", type=float, nargs="+", default=[0.25],
@@ -126,6 +144,9 @@ def main():
     ap.add_argument("--eval-seeds", type=int, nargs=2, default=None)
     ap.add_argument("--eval-thetas", type=float, nargs="+", default=[0.25, 0.5])
     ap.add_argument("--summary", default=None, help="write the evaluation rows as JSON here")
+    ap.add_argument("--bh-leaves", type=int, nargs="*", default=[],
+                    help="also evaluate plain Barnes-Hut on trees with these leaf sizes (at --bh-thetas)")
+    ap.add_argument("--bh-thetas", type=float, nargs="*", default=[])
     ap.add_argument("--eval-only", default=None, metavar="MODEL",
                     help="skip training: load this model file and evaluate it on --eval-seeds")
     args = ap.parse_args()
@@ -136,7 +157,8 @@ def main():
         if not args.eval_seeds:
             ap.error("--eval-only needs --eval-seeds")
         _tp.tp_far_model_load(ctx, args.eval_only)
-        rows = evaluate(ctx, range(*args.eval_seeds), args.level, args.eval_thetas, log=None)
+        rows = evaluate(ctx, range(*args.eval_seeds), args.level, args.eval_thetas, log=None,
+                        bh_leaves=args.bh_leaves, bh_thetas=args.bh_thetas, leaf=args.leaf)
         summ = {}
         for th in args.eval_thetas:
             for mode in ("bh", "learned", "learned_energy"):
@@ -145,6 +167,13 @@ def main():
                                             "mean": float(np.mean([r[k] for r in rs])),
                                             "max": float(np.max([r[k] for r in rs]))}
                                         for k in ("energy_err", "grad_err", "ms_eval")}
+        for bl in args.bh_leaves:
+            for th in args.bh_thetas:
+                rs = [r for r in rows if r["theta"] == th and r["mode"] == f"bh_leaf{bl}"]
+                summ[f"bh_leaf{bl}@{th}"] = {k: {"min": float(np.min([r[k] for r in rs])),
+                                                   "mean": float(np.mean([r[k] for r in rs])),
+                                                   "max": float(np.max([r[k] for r in rs]))}
+                                               for k in ("energy_err", "grad_err", "ms_eval")}
         print(json.dumps(summ))
         if args.summary:
             with open(args.summary, "w") as f:
@@ -156,7 +185,8 @@ def main():
     _tp.tp_far_dataset_reset(ctx)
     n = 0
     for th in args.theta:
-        n += sample_meshes(ctx, range(*args.seeds), args.level, th, args.pairs_per_mesh, seed=int(th * 1000))
+        n += sample_meshes(ctx, range(*args.seeds), args.level, th, args.pairs_per_mesh, seed=int(th * 1000),
+                           leaf=args.leaf)
     t1 = time.time()
     _tp.tp_far_fit_normalisation(ctx)
     hist = train(ctx, args.steps, args.batch, args.lr, seed=args.train_seed)
@@ -167,7 +197,7 @@ def main():
     print(f"{n} pairs in {t1 - t0:.1f} s; {args.steps} steps in {t2 - t1:.1f} s; final loss {hist[-1][1]:.5f}; "
           f"saved {args.out}")
     if args.eval_seeds:
-        rows = evaluate(ctx, range(*args.eval_seeds), args.level, args.eval_thetas)
+        rows = evaluate(ctx, range(*args.eval_seeds), args.level, args.eval_thetas, leaf=args.leaf)
         summ = {}
         for th in args.eval_thetas:
             for mode in ("bh", "learned", "learned_energy"):
