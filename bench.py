@@ -53,7 +53,9 @@ FP32_LANES_PER_SM = 128
 NCU_TRAFFIC_BYTES = 60.61e6
 
 # far-field model trained by paper_2509_22110_gb300.far_train (command in the design notes)
-DEFAULT_FAR_MODEL = os.path.join(ROOT, "paper_2509_22110_gb300", "far_model_l7.bin")
+# packaged learned far-field models, by the tree leaf size they were trained with
+FAR_MODELS = {16: os.path.join(ROOT, "paper_2509_22110_gb300", "far_model_l7.bin"),
+              32: os.path.join(ROOT, "paper_2509_22110_gb300", "far_model_l7_leaf32.bin")}
 
 WORKLOADS = {
     "sh_l7": "icosphere level 7 (327,680 triangles) with seeded SH deformation l<=12, a_lm~N(0,(0.05/l)^2), seed 2",
@@ -75,8 +77,8 @@ def parse():
     ap.add_argument("--mode", default="direct", choices=["direct", "bh", "learned", "dual", "conf"],
                     help="bh: inner integral clustered (Barnes-Hut); dual: both integrals clustered (cluster-cluster); "
                          "conf: the confinement energy (Eq. TPConf) of the conf_l7 workload")
-    ap.add_argument("--far-model", default=DEFAULT_FAR_MODEL,
-                    help="trained far-field model (learned mode; default: the packaged level-7 model)")
+    ap.add_argument("--far-model", default=None,
+                    help="learned far-field model file (default: the packaged model trained with --leaf)")
     ap.add_argument("--theta", type=float, default=0.25)
     ap.add_argument("--leaf", type=int, default=16, help="cluster leaf size of the tree (1-32) in the clustered modes")
     ap.add_argument("--dual-theta", type=float, default=0.25, help="opening angle of the dual form in --inloop runs")
@@ -93,7 +95,10 @@ def parse():
                     help="opening angles of the clustered forms in --inloop runs (default: --theta)")
     ap.add_argument("--inloop-ref-every", type=int, default=10,
                     help="in --inloop runs, evaluate the FP64 reference every N steps and on the last")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.far_model is None:
+        args.far_model = FAR_MODELS.get(args.leaf, "")
+    return args
 
 
 def job_throughput(local_ms, ws, steps, units_per_rank, device, tdist=None):

@@ -306,3 +306,34 @@ def test_learned_windows_match_one_pass(tp, ctx):
     assert rel(g2, g1) <= 1e-12, rel(g2, g1)
     with pytest.raises(tp.TPError):
         tp.tp_set_learned_window(ctx, 5)
+
+
+@pytest.mark.parametrize("leaf,theta,model,energy_only", [
+    (16, 0.125, "far_model_l7.bin", True),
+    (32, 0.15, "far_model_l7_leaf32.bin", False),
+])
+def test_packaged_models_at_the_bar(tp, ctx, leaf, theta, model, energy_only):
+    """The packaged models on a held-out level-7 mesh (seed 2, not in their
+    training sets) against the direct sum: energy and gradient errors within
+    the 1e-3 bar of the clustered forms, at opening angles where plain
+    Barnes-Hut on the same tree misses the energy bar."""
+    import torch
+
+    _tp = tp._tp
+    tp.tp_far_model_load(ctx, str(ROOT / "paper_2509_22110_gb300" / model))
+    V, F = meshgen.sh_deformed_sphere(7, 12, 0.05, 2)
+    Vd = torch.tensor(V, device="cuda")
+    tp.tp_mesh_upload(ctx, Vd, torch.tensor(F, device="cuda"))
+    gd = torch.zeros_like(Vd)
+    ed = tp.tp_gradient(ctx, gd, tp.tp_params_default())
+    tp.tp_tree_build(ctx, leaf, 30)
+    gb = torch.zeros_like(Vd)
+    eb = tp.tp_gradient(ctx, gb, tp.tp_params_default(mode=tp.TP_BH, theta=theta))
+    gl = torch.zeros_like(Vd)
+    flags = _tp.TP_LEARNED_ENERGY if energy_only else 0
+    el = tp.tp_gradient(ctx, gl, tp.tp_params_default(mode=tp.TP_LEARNED, theta=theta, flags=flags))
+    err_b, err_l = abs(eb - ed) / ed, abs(el - ed) / ed
+    gerr_l = float(torch.linalg.norm(gl - gd) / torch.linalg.norm(gd))
+    print(f"leaf {leaf} theta {theta}: energy error BH {err_b:.3e} learned {err_l:.3e}; gradient error {gerr_l:.3e}")
+    assert err_b > 1e-3
+    assert err_l <= 1e-3 and gerr_l <= 1e-3
