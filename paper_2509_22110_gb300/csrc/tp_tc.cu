@@ -32,10 +32,6 @@
 #include "tp_internal.cuh"
 #include "tp_mlp_dev.cuh"
 
-#ifndef TP_GELU_F16
-#define TP_GELU_F16 0
-#endif
-
 namespace {
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
@@ -207,18 +203,8 @@ __device__ __forceinline__ uint32_t gelu2_bf16(float z0, float z1) {
     const float2 inner = __ffma2_rn(__fmul2_rn(z, z), make_float2(a, a), make_float2(1.f, 1.f));
     const float2 u = __fmul2_rn(__fmul2_rn(z, inner), make_float2(c, c));
     float2 t;
-#if TP_GELU_F16
-    // one MUFU operation for both: tanh of the FP16 pair (the result is rounded to BF16 below)
-    uint32_t uh, th;
-    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(uh) : "f"(u.y), "f"(u.x));
-    asm("tanh.approx.f16x2 %0, %1;" : "=r"(th) : "r"(uh));
-    asm("{\n\t.reg .f16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\tcvt.f32.f16 %0, lo;\n\tcvt.f32.f16 %1, hi;\n\t}"
-        : "=f"(t.x), "=f"(t.y)
-        : "r"(th));
-#else
     asm("tanh.approx.f32 %0, %1;" : "=f"(t.x) : "f"(u.x));
     asm("tanh.approx.f32 %0, %1;" : "=f"(t.y) : "f"(u.y));
-#endif
     const float2 hz = __fmul2_rn(z, make_float2(0.5f, 0.5f));
     const float2 g = __ffma2_rn(hz, t, hz);
     return pack_bf16(g.x, g.y);
