@@ -119,7 +119,8 @@ struct BHArgs {
 enum { M_BH = 0, M_LIST = 1, M_RECORD = 2 };
 
 // A pair of targets (one per half of t) against one source record of the
-// direct kernels' layout (each value stored twice: x_hi[3], x_lo[3], nu[3], w~).
+// direct kernels' layout (each value stored twice: x_hi[3], x_lo[3], nu[3], w~),
+// without the target weights (k_near multiplies its sums by them).
 template <int Q, bool HILO>
 __device__ __forceinline__ void near_pair2(const Tgt2& t, const float* rec, float2 acc[8]) {
     const float4* r = reinterpret_cast<const float4*>(rec);
@@ -127,7 +128,7 @@ __device__ __forceinline__ void near_pair2(const Tgt2& t, const float* rec, floa
     const float2 sh[3] = {make_float2(r0.x, r0.y), make_float2(r0.z, r0.w), make_float2(r1.x, r1.y)};
     const float2 sl[3] = {make_float2(r1.z, r1.w), make_float2(r2.x, r2.y), make_float2(r2.z, r2.w)};
     const float2 sn[3] = {make_float2(r3.x, r3.y), make_float2(r3.z, r3.w), make_float2(r4.x, r4.y)};
-    pair_core<Q, false, HILO>(t.h, t.l, t.n, t.w, sh, sl, sn, make_float2(r4.z, r4.w), acc, true, true);
+    pair_core<Q, false, HILO, true>(t.h, t.l, t.n, t.w, sh, sl, sn, make_float2(r4.z, r4.w), acc, true, true);
 }
 
 // Target-leaf constants of the admissibility test.
@@ -749,9 +750,11 @@ __global__ void __launch_bounds__(NR_WARPS * 32) k_near(BHArgs A) {
             for (int h = 0; h < 2; ++h) {
                 if (!act[h]) continue;
                 const int64_t k = fL + 2 * tpl + h;
-                atomicAdd(&A.acc[k], e64[h]);
+                const float w = h ? tg.w.y : tg.w.x;  // the target weight left out of the pair terms
+                atomicAdd(&A.acc[k], e64[h] * (double)w);
 #pragma unroll
-                for (int c = 1; c < 8; ++c) atomicAdd(&A.acc[c * A.ntp + k], (double)(h ? a2[c].y : a2[c].x));
+                for (int c = 1; c < 8; ++c)
+                    atomicAdd(&A.acc[c * A.ntp + k], (double)(h ? a2[c].y : a2[c].x) * (double)w);
             }
         }
         __syncwarp();  // the entry list is reused by the next run

@@ -53,8 +53,10 @@ __device__ __forceinline__ void stage_pad(float* stg, int j) {
 // (v0, v1); an excluded half gets 1/|d|^2 = 0 and weight 0, so its terms are
 // exact zeros (d itself stays finite: a coincident centroid or a padding
 // source's large offset never reaches a power).  HILO: d = (hi_T - hi_S) +
-// (lo_T - lo_S); without it d = hi_T - hi_S (pairs far enough apart).
-template <int Q, bool SEL, bool HILO = true>
+// (lo_T - lo_S); without it d = hi_T - hi_S (pairs far enough apart).  TW1:
+// the target weights are left out (every accumulated term carries its
+// target's weight as a factor, which the caller applies to the sums).
+template <int Q, bool SEL, bool HILO = true, bool TW1 = false>
 __device__ __forceinline__ void pair_core(const float2 (&th)[3], const float2 (&tl)[3], const float2 (&tn)[3],
                                           float2 tw, const float2 (&sh)[3], const float2 (&sl)[3],
                                           const float2 (&sn)[3], float2 sw, float2 acc[8], bool v0, bool v1) {
@@ -66,7 +68,7 @@ __device__ __forceinline__ void pair_core(const float2 (&th)[3], const float2 (&
     float2 r2 = bh_mul2(d[0], d[0]);
     r2 = bh_fma2(d[1], d[1], r2);
     r2 = bh_fma2(d[2], d[2], r2);
-    float2 wts = bh_mul2(tw, sw);
+    float2 wts = TW1 ? sw : bh_mul2(tw, sw);
     float2 inv = make_float2(bh_rcp(r2.x), bh_rcp(r2.y));
     if (SEL) {
         inv = make_float2(v0 ? inv.x : 0.f, v1 ? inv.y : 0.f);
