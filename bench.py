@@ -46,14 +46,18 @@ FLOPS_PER_UNORDERED_PAIR = 76
 # flops in 25 operations (the hi/lo cancellation correction, 6 FADD, not
 # counted; the -p/q factor of Gx is applied once per item, not per pair).
 FLOPS_PER_CONF_PAIR = 36
+# The same count for one ordered (target, source) pair of the Barnes-Hut
+# near-field kernel (target side of both orderings, the target weight applied
+# to the sums): 17 FMA + 20 FMUL/FADD = 54 flops in 37 operations (the hi/lo
+# correction of close clusters, 6 FADD, not counted).
+FLOPS_PER_NEAR_PAIR = 54
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per launch of the dominant kernel on the default
 # workload, from the one-pass ncu capture summarised in
 # profiles/k_pairs_grad_traffic_sh_l7.md (null it when that kernel changes).
 NCU_TRAFFIC_BYTES = 60.61e6
 
-# far-field model trained by paper_2509_22110_gb300.far_train (command in the design notes)
-# packaged learned far-field models, by the tree leaf size they were trained with
+# packaged learned far-field models (trained by paper_2509_22110_gb300.far_train), by the tree leaf size they were trained with
 FAR_MODELS = {16: os.path.join(ROOT, "paper_2509_22110_gb300", "far_model_l7.bin"),
               32: os.path.join(ROOT, "paper_2509_22110_gb300", "far_model_l7_leaf32.bin")}
 
@@ -514,8 +518,23 @@ def main():
                                      dev, tdist)
     ms_step = total_ms / args.steps
 
-    # roofline of the dominant kernel (unmasked direct pair kernel)
+    # roofline of the dominant kernel (direct: the unmasked pair kernel; Barnes-Hut and
+    # learned: the near-field kernel)
     roof = None
+    if mode in (tp.TP_BH, tp.TP_LEARNED) and kern_ms and stats["kernel_pairs"] > 0:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        max_mhz = float(measured_peaks().get("sm_max_mhz", 2070.0))
+        peak_tflops = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+        opairs = stats["kernel_pairs"]  # ordered (target, source) pairs of the near-field launch
+        kms = statistics.mean(kern_ms)
+        achieved = FLOPS_PER_NEAR_PAIR * opairs / (kms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "kernel": "k_near<6> (near clusters apart from the target leaf)", "kernel_ms": kms,
+                "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz (max SM clock)",
+                "flops_per_ordered_pair": FLOPS_PER_NEAR_PAIR, "ordered_pairs_per_launch": opairs}
+        if clk and clk.get("sm_mhz"):
+            roof["frac_at_sampled_clock"] = achieved / (sms * FP32_LANES_PER_SM * 2 * clk["sm_mhz"] * 1e6 / 1e12)
     if mode == tp.TP_DIRECT:
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         pk = measured_peaks()

@@ -230,13 +230,17 @@ typedef struct {
     int64_t far_pairs;     /* ordered pairs represented by those far terms            */
     int64_t learned_terms; /* far terms evaluated by the network                       */
     int64_t tile_pairs, tile_pairs_masked, tile_pairs_precise;
-    float ms_kernel;       /* device time of the dominant kernel of the last call      */
+    float ms_kernel;       /* device time of the dominant kernel of the last call
+                              (direct: the pair launch of the PRECISE and FAST items;
+                              Barnes-Hut and learned: the near-field kernel)          */
     float ms_total;        /* device time of the whole last call                       */
     int64_t kernel_launches; /* library kernels launched by the last call (CUDA library
                                 calls such as the radix sort are not counted)        */
-    int64_t kernel_pairs;    /* unordered triangle pairs evaluated by the dominant kernel
-                                launch of the last call (direct mode: the far-apart
-                                super-tile pairs), for throughput accounting          */
+    int64_t kernel_pairs;    /* pairs evaluated by the dominant kernel launch of the
+                                last call, for throughput accounting: direct mode, the
+                                unordered pairs of the PRECISE and FAST items;
+                                Barnes-Hut and learned, the ordered (target, source)
+                                pairs of the near-field kernel                        */
     int64_t far_rows;        /* (target leaf, cluster) far pairs of the last Barnes-Hut
                                 or learned call: in the learned form, the rows the
                                 network evaluated                                     */

@@ -86,6 +86,7 @@ struct BHArgs {
     unsigned* derr;
     unsigned long long* counts;  // [0] near pairs, [1] far terms, [2] far pairs, [3] learned terms
     unsigned long long* far_rows;  // (leaf, cluster) far pairs
+    unsigned long long* near_listed;  // ordered pairs listed for k_near: [0] all, [1] with hi-only differences
     // learned far field
     const float* nodeft;         // [nn][16] f32 feature records
     const __nv_bfloat16* wb;     // network weights (BF16 block)
@@ -371,6 +372,21 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
         pos = __shfl_sync(0xffffffffu, pos, 0);
         run = __shfl_sync(0xffffffffu, run, 0);
         const bool fits = pos + (unsigned long long)nn <= (unsigned long long)A.near_cap;
+        // the run's ordered pairs (all, and those with hi-only differences) for the statistics
+        unsigned int rp = 0, rh = 0;
+        for (int i = lane; i < nn; i += 32) {
+            const int c = s_near[warp][0][i].y;
+            rp += (unsigned)(c < 0 ? -c : c);
+            if (c < 0) rh += (unsigned)-c;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            rp += __shfl_xor_sync(0xffffffffu, rp, o);
+            rh += __shfl_xor_sync(0xffffffffu, rh, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&A.near_listed[0], (unsigned long long)rp * (unsigned long long)cnt);
+            atomicAdd(&A.near_listed[1], (unsigned long long)rh * (unsigned long long)cnt);
+        }
         if (fits) {
             // the clusters with hi/lo differences first, then the hi-only ones, so
             // that k_near's slots (one kind each) stay full
@@ -1140,13 +1156,16 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
     }
     const unsigned nblocks = (unsigned)std::max(1, ctx->num_sms * TP_NR_BPS);
     const unsigned fblocks = (unsigned)std::max(1, ctx->num_sms * 4);
-    cudaEventRecord(ctx->ev[0], ctx->stream);
+    // ordered pairs listed for k_near ([0]) and those of them with hi-only differences ([1])
+    unsigned long long* near_listed = reinterpret_cast<unsigned long long*>(ctx->scalar + 10);
+    A.near_listed = near_listed;
     int64_t listed_rows = 0, listed_runs = 0;
-    unsigned long long h[4] = {0, 0, 0, 0}, h_rows = 0;
+    unsigned long long h[4] = {0, 0, 0, 0}, h_rows = 0, h_lst[2] = {0, 0};
     for (int attempt = 0;; ++attempt) {
         TP_CU(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * TP_NACC * ctx->ntp, ctx->stream));
         TP_CU(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), ctx->stream));
         TP_CU(cudaMemsetAsync(far_rows, 0, sizeof(unsigned long long), ctx->stream));
+        TP_CU(cudaMemsetAsync(near_listed, 0, 2 * sizeof(unsigned long long), ctx->stream));
         TP_CU(cudaMemsetAsync(ctx->near_count, 0, 3 * sizeof(unsigned long long), ctx->stream));
         TP_CU(cudaMemsetAsync(ctx->far_count, 0, 3 * sizeof(unsigned long long), ctx->stream));
         A.src = ctx->src;
@@ -1163,15 +1182,19 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
         A.run_cap = ctx->run_cap;
         // the traversal (far nodes evaluated or listed, touching near clusters
         // evaluated, the other near clusters listed), then the listed near clusters
+        // (the near-field kernel is the timed one: ev[0] .. ev[1])
         if (prm->q == 6) {
             if (learned) k_bh<6, M_LIST><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
             else k_bh<6, M_BH><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
+            cudaEventRecord(ctx->ev[0], ctx->stream);
             k_near<6><<<nblocks, NR_WARPS * 32, 0, ctx->stream>>>(A);
         } else {
             if (learned) k_bh<8, M_LIST><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
             else k_bh<8, M_BH><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
+            cudaEventRecord(ctx->ev[0], ctx->stream);
             k_near<8><<<nblocks, NR_WARPS * 32, 0, ctx->stream>>>(A);
         }
+        cudaEventRecord(ctx->ev[1], ctx->stream);
         ctx->nlaunch += 2;
         TP_CU(cudaGetLastError());
         unsigned long long nc[2] = {0, 0}, fc[2] = {0, 0};
@@ -1179,6 +1202,7 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
         TP_CU(cudaMemcpyAsync(fc, ctx->far_count, sizeof(fc), cudaMemcpyDeviceToHost, ctx->stream));
         TP_CU(cudaMemcpyAsync(h, counts, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
         TP_CU(cudaMemcpyAsync(&h_rows, far_rows, sizeof(h_rows), cudaMemcpyDeviceToHost, ctx->stream));
+        TP_CU(cudaMemcpyAsync(h_lst, near_listed, sizeof(h_lst), cudaMemcpyDeviceToHost, ctx->stream));
         TP_CU(cudaStreamSynchronize(ctx->stream));
         const bool near_ok = (int64_t)nc[0] <= ctx->near_cap && (int64_t)nc[1] <= ctx->nrun_cap;
         const bool far_ok = (int64_t)fc[0] <= ctx->far_cap && (int64_t)fc[1] <= ctx->run_cap;
@@ -1289,9 +1313,9 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
         TP_CU(cudaGetLastError());
         TP_CU(cudaMemcpyAsync(h + 3, counts + 3, sizeof(h[3]), cudaMemcpyDeviceToHost, ctx->stream));
     }
-    cudaEventRecord(ctx->ev[1], ctx->stream);
     TP_CU(cudaStreamSynchronize(ctx->stream));
     ctx->stats.pairs_exact = (int64_t)h[0];
+    ctx->stats.kernel_pairs = (int64_t)h_lst[0];  // ordered pairs of the timed near-field launch
     ctx->stats.far_terms = (int64_t)h[1];
     ctx->stats.far_pairs = (int64_t)h[2];
     ctx->stats.learned_terms = (int64_t)h[3];

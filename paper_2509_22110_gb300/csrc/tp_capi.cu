@@ -431,7 +431,7 @@ tp_status tp_create(tp_ctx** out, int device, void* cuda_stream) {
     }
     ctx->num_sms = prop.multiProcessorCount;
     for (int i = 0; i < 4; ++i) cudaEventCreate(&ctx->ev[i]);
-    if (tp_alloc_t(ctx, &ctx->derr, 4) != TP_OK || tp_alloc_t(ctx, &ctx->scalar, 10) != TP_OK ||
+    if (tp_alloc_t(ctx, &ctx->derr, 4) != TP_OK || tp_alloc_t(ctx, &ctx->scalar, 16) != TP_OK ||
         tp_alloc_t(ctx, &ctx->center, 3) != TP_OK || tp_alloc_t(ctx, &ctx->bounds, 6) != TP_OK ||
         tp_alloc_t(ctx, &ctx->mcount, 16) != TP_OK || tp_alloc_t(ctx, &ctx->work, 4) != TP_OK) {
         tp_destroy(ctx);

@@ -148,7 +148,9 @@ struct tp_ctx {
     double* center = nullptr;       // [3] f64 centre subtracted before the f32 split
     double* bounds = nullptr;       // [6] min/max of centroids
     double* red = nullptr;          // reduction scratch
-    double* scalar = nullptr;       // [10] device scalars (energies, counters)
+    double* scalar = nullptr;       // [16] device scalars: energies [0..1], Barnes-Hut counts [2..5], learned
+                                    // energy correction [6], far rows [7], excluded pairs [8..9], pairs listed
+                                    // for the near-field kernel [10..11]
     unsigned* derr = nullptr;       // device error word
     unsigned* adjbm = nullptr;      // bitmap nsup*nsup: super-tile pairs holding a vertex-sharing pair (or I == J)
     unsigned* flagged = nullptr;    // bitmap nsup*nsup: super-tile pairs not handled by the fast kernel

@@ -123,6 +123,10 @@ def test_bh_parity_with_oracle(tp, ctx, oracle_mod, theta):
     st = tp.tp_get_stats(ctx)
     assert st["far_terms"] == info["far_terms"]
     assert st["pairs_exact"] == info["near_pairs"]
+    # the near-field kernel's pairs (clusters apart from the leaf) are part of the exact pairs,
+    # and its launch is part of the evaluation
+    assert 0 < st["kernel_pairs"] <= st["pairs_exact"]
+    assert 0.0 < st["ms_kernel"] <= st["ms_total"]
     assert abs(e - Eo) <= E_TOL * Eo, (e, Eo)
     assert rel(grad, go) <= G_TOL, rel(grad, go)
     assert abs(tp.tp_energy(ctx, p) - Eo) <= E_TOL * Eo
