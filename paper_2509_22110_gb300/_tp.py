@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libtp.so")
+# the library this binding loads: libtp.so, or the build named by TP_LIB (for
+# instance the checked build libtp_debug.so)
+LIB_PATH = os.environ.get("TP_LIB") or os.path.join(_HERE, "libtp.so")
 _lib = None
 
 TP_OK, TP_E_ARG, TP_E_CUDA, TP_E_STATE, TP_E_NONFINITE, TP_E_TIMEOUT, TP_E_OOM, TP_E_MODEL = range(8)

@@ -85,12 +85,13 @@ __global__ void k_adjoint_tri(const double* __restrict__ V, const int32_t* __res
 template <typename OutT>
 __global__ void k_adjoint_gather(const int32_t* __restrict__ off, const int32_t* __restrict__ v2t,
                                  const double* __restrict__ adjc, int64_t nv, double scale,
-                                 OutT* __restrict__ grad) {
+                                 OutT* __restrict__ grad, int64_t nt, unsigned* __restrict__ derr) {
     const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (v >= nv) return;
     double g[3] = {0.0, 0.0, 0.0};
     for (int32_t e = off[v]; e < off[v + 1]; ++e) {
         const int32_t ent = v2t[e];
+        if (!tp_dbg_ok(ent >= 0 && (ent >> 2) < nt && (ent & 3) < 3, derr)) continue;
         const double* c = adjc + 9 * (int64_t)(ent >> 2) + 3 * (ent & 3);
         for (int a = 0; a < 3; ++a) g[a] += c[a];
     }
@@ -160,10 +161,10 @@ tp_status tp_launch_adjoint(tp_ctx* ctx, const tp_params* prm, void* grad, int g
     const unsigned blocks = (unsigned)((nv + 255) / 256);
     if (g_dtype == TP_DTYPE_F64)
         k_adjoint_gather<double><<<blocks, 256, 0, ctx->stream>>>(ctx->v2t_off, ctx->v2t, ctx->adjc, nv, prm->scale,
-                                                                  static_cast<double*>(grad));
+                                                                  static_cast<double*>(grad), nt, ctx->derr);
     else
         k_adjoint_gather<float><<<blocks, 256, 0, ctx->stream>>>(ctx->v2t_off, ctx->v2t, ctx->adjc, nv, prm->scale,
-                                                                 static_cast<float*>(grad));
+                                                                 static_cast<float*>(grad), nt, ctx->derr);
     ++ctx->nlaunch;
     TP_CU(cudaGetLastError());
     return TP_OK;

@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
         sp -= m;
         bool is_far = false, is_near = false, is_open = false, touch = false, fast = false;
         int firstc = 0, cntc = 0, lc = 0, rc = 0;
-        if (node >= 0) {
+        if (node >= 0 && tp_dbg_ok(node < 2 * A.n - 1, A.derr)) {
             // everything the test and the push need, loaded in one round: the
             // node's FP32 record, its member range and (internal nodes) its children
             const float4* c4 = reinterpret_cast<const float4*>(A.adm32 + 16 * (int64_t)node);
@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
                     fast = box_gap2(la, c32) >= la.fast2;
                 }
             } else {
-                is_open = true;
+                is_open = tp_dbg_ok(lc >= 0 && lc < 2 * A.n - 1 && rc >= 0 && rc < 2 * A.n - 1, A.derr);
             }
         }
         const unsigned bf = __ballot_sync(0xffffffffu, is_far);
@@ -635,6 +635,18 @@ __global__ void __launch_bounds__(NR_WARPS * 32) k_near(BHArgs A) {
         const int64_t L = A.leaves[R.li];
         const int64_t fL = A.first[L];
         const int cnt = A.last[L] - A.first[L] + 1;
+#if TP_DEBUG
+        {
+            // the leaf's targets and every listed member range within the triangles
+            bool ok = fL >= 0 && cnt >= 1 && cnt <= 32 && fL + cnt <= A.ntp;
+            for (int i = lane; i < R.len; i += 32) {
+                const int2 e = A.near_list[R.start + i];
+                const int c = e.y < 0 ? -e.y : e.y;
+                ok = ok && c >= 1 && c <= 32 && e.x >= 0 && (int64_t)e.x + c <= A.ntp;
+            }
+            if (!__all_sync(0xffffffffu, tp_dbg_ok(ok, A.derr))) continue;
+        }
+#endif
         const int npair = (cnt + 1) >> 1;           // target pairs
         const int ng = 32 / npair;                  // source streams
         const int tpl = lane % npair, g = lane / npair;  // this lane's pair and stream (g >= ng: idle)
@@ -947,6 +959,17 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) k_far(BHArgs A, const float* _
         const int64_t L = A.leaves[R.li];
         const int64_t fL = A.first[L];
         const int cnt = A.last[L] - A.first[L] + 1;
+#if TP_DEBUG
+        {
+            // the leaf's targets within the triangles and the run's listed nodes within the tree
+            bool ok = fL >= 0 && cnt >= 1 && cnt <= 32 && fL + cnt <= A.ntp;
+            for (int i = lane; i < rlen; i += 32) {
+                const int nd = A.far_list[r0 + i];
+                ok = ok && nd >= 0 && nd < 2 * A.n - 1;
+            }
+            if (!__all_sync(0xffffffffu, tp_dbg_ok(ok, A.derr))) continue;
+        }
+#endif
         const int npair = (cnt + 1) >> 1;
         const int ng = 32 / npair;
         const int tpl = lane % npair, g = lane / npair;
@@ -1284,6 +1307,8 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
         fs.far_leaf = ctx->far_leaf;
         fs.leaves = t.leaves;
         fs.mnorm = A.mnorm;
+        fs.nleaves = t.nleaves;
+        fs.nnodes = 2 * ctx->nt - 1;
         for (size_t wi = 0; wi + 1 < bnd.size(); ++wi) {
             const int64_t w0 = bnd[wi], w1 = bnd[wi + 1];
             if (w1 <= w0) continue;

@@ -306,6 +306,7 @@ tp_status take_device_error(tp_ctx* ctx, const char* where) {
     if (h & TP_DERR_INDEX) return tp_set_err(ctx, TP_E_ARG, "%s: face index outside [0, nv)", where);
     if (h & TP_DERR_STACK) return tp_set_err(ctx, TP_E_CUDA, "%s: traversal stack overflow", where);
     if (h & TP_DERR_INTERNAL) return tp_set_err(ctx, TP_E_CUDA, "%s: internal work-list check failed", where);
+    if (h & TP_DERR_BOUNDS) return tp_set_err(ctx, TP_E_CUDA, "%s: bounds check of the checked build failed", where);
     if (h & TP_DERR_NONFINITE)
         return tp_set_err(ctx, TP_E_NONFINITE, "%s: degenerate triangle or non-finite coordinate", where);
     return tp_set_err(ctx, TP_E_CUDA, "%s: device error 0x%x", where, h);

@@ -380,6 +380,10 @@ __device__ __forceinline__ Item decode_item(const DirectArgs& A, unsigned w) {
     it.I = e >> 16;
     it.J = e & 0xffff;
     it.m = (int)w;
+#if TP_DEBUG
+    // a listed item names an upper-triangle pair of existing super-tiles
+    if (it.kind >= 0 && !tp_dbg_ok(it.I <= it.J && it.J < A.nsup, A.derr)) it.kind = -1;
+#endif
     return it;
 }
 

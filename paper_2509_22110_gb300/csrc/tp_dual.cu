@@ -79,6 +79,7 @@ struct DTTree {
     const float* nodef;   // [nn][16] FP32 far-field record (nubar at 6..8)
     int64_t n;
     int leaf;
+    unsigned* derr;  // device error word (bounds checks of the TP_DEBUG build)
 };
 
 __device__ __forceinline__ bool dt_small(const DTTree& T, int node) {
@@ -253,6 +254,7 @@ __global__ void __launch_bounds__(DT_THREADS) k_dt_far(DTTree T, const int2* __r
     const float pf = 2.0f * (float)q;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nfar; i += (int64_t)gridDim.x * blockDim.x) {
         const int2 pr = far[i];
+        if (!tp_dbg_ok(pr.x >= 0 && pr.x < 2 * T.n - 1 && pr.y >= 0 && pr.y < 2 * T.n - 1, T.derr)) continue;
         const double* xA = T.adm64 + 4 * (int64_t)pr.x;
         const double* xB = T.adm64 + 4 * (int64_t)pr.y;
         const float* fA = T.nodef + 16 * (int64_t)pr.x;
@@ -393,7 +395,8 @@ __global__ void __launch_bounds__(DT_NEAR_WARPS * 32) k_dt_near(const float* __r
                                                                 const uint32_t* __restrict__ off,
                                                                 const int2* __restrict__ list, int edge_only,
                                                                 double* __restrict__ acc,
-                                                                unsigned long long* __restrict__ npairs) {
+                                                                unsigned long long* __restrict__ npairs,
+                                                                unsigned* __restrict__ derr) {
     __shared__ __align__(16) float s_stg[DT_NEAR_WARPS][16 * BH_PAIR];
     __shared__ int4 s_f[DT_NEAR_WARPS][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -420,6 +423,19 @@ __global__ void __launch_bounds__(DT_NEAR_WARPS * 32) k_dt_near(const float* __r
     double a64[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     unsigned long long n_adm = 0;
     const uint32_t e0 = off[li], e1 = off[li + 1];
+#if TP_DEBUG
+    {
+        // the leaf's targets and every listed partner range within the triangles
+        bool ok = fL >= 0 && cnt >= 1 && cnt <= 32 && fL + cnt <= ntp;
+        for (uint32_t j = e0 + lane; j < e1; j += 32) {
+            const int2 nd = list[j];
+            ok = ok && nd.y >= 1 && nd.y <= 32 && nd.x >= 0 && (int64_t)nd.x + nd.y <= ntp;
+        }
+        if (!__all_sync(0xffffffffu, tp_dbg_ok(ok, derr))) return;
+    }
+#else
+    (void)derr;
+#endif
     uint32_t e = e0;
     while (e < e1) {
         // whole partner leaves while they fit in 32 staging slots
@@ -556,6 +572,7 @@ tp_status tp_launch_dual(tp_ctx* ctx, const tp_params* prm) {
     T.nodef = t.nodef;
     T.n = n;
     T.leaf = t.leaf_size;
+    T.derr = ctx->derr;
     // counters: [2] far pairs, [3] near pairs, [4] overflow, [5] admitted pairs of the
     // touching pass, [6] represented far pairs, [7] pairs of the apart node pairs,
     // [9] runs and [10] work counter of the near-field kernel; from [16] the frontier
@@ -645,10 +662,12 @@ tp_status tp_launch_dual(tp_ctx* ctx, const tp_params* prm) {
     const int edge = (prm->flags & TP_EXCLUDE_EDGE) ? 1 : 0;
     if (prm->q == 6)
         k_dt_near<6><<<dt_blocks(nl, DT_NEAR_WARPS), DT_NEAR_WARPS * 32, 0, ctx->stream>>>(
-            ctx->soa, ctx->ntp, ctx->Fs, t.leaves, nl, t.first, t.last, wide, ct, list_t, edge, ctx->acc, npairs);
+            ctx->soa, ctx->ntp, ctx->Fs, t.leaves, nl, t.first, t.last, wide, ct, list_t, edge, ctx->acc, npairs,
+            ctx->derr);
     else
         k_dt_near<8><<<dt_blocks(nl, DT_NEAR_WARPS), DT_NEAR_WARPS * 32, 0, ctx->stream>>>(
-            ctx->soa, ctx->ntp, ctx->Fs, t.leaves, nl, t.first, t.last, wide, ct, list_t, edge, ctx->acc, npairs);
+            ctx->soa, ctx->ntp, ctx->Fs, t.leaves, nl, t.first, t.last, wide, ct, list_t, edge, ctx->acc, npairs,
+            ctx->derr);
     ++ctx->nlaunch;
     TP_TRY(tp_launch_near_runs(ctx, prm->q, list_a, 2 * n_near, ctx->dt_runs, ctx->dt_run_cap, cnt + 8));
     // far field: node derivatives, then down to the triangles

@@ -59,16 +59,26 @@ struct TpRange {
 // mesh's centroid-box diagonal form centroid differences from hi + lo parts
 #define TP_PRECISE_GAP_REL 0.02f
 
-// device error bits
-// listed far rows per window of the learned passes: 32 Mi rows, about 3.4 GB
-// of network rows and factors (tp_set_learned_window changes it)
+// listed far rows per window of the learned passes: 32 Mi rows, 1 GB of
+// network factors (tp_set_learned_window changes it)
 #define TP_LEARNED_WINDOW ((int64_t)1 << 25)
 
+// device error bits
 #define TP_DERR_TIMEOUT 0x1u
 #define TP_DERR_STACK 0x2u
 #define TP_DERR_INDEX 0x4u
 #define TP_DERR_NONFINITE 0x8u
 #define TP_DERR_INTERNAL 0x10u  // a consistency check of a kernel's own work lists failed
+#define TP_DERR_BOUNDS 0x20u    // a bounds check of the checked build (TP_DEBUG) failed
+
+// TP_DEBUG = 1 builds libtp_debug.so: the list-driven kernels also check every
+// index they read from a work list (node ids, member ranges, listed rows, CSR
+// entries, item tiles) against its array, record a failure in the device
+// error word (TP_DERR_BOUNDS) and skip the access.  The release build checks
+// list capacities only.
+#ifndef TP_DEBUG
+#define TP_DEBUG 0
+#endif
 
 struct tp_tree {
     bool valid = false;
@@ -306,6 +316,7 @@ struct tp_feat_src {
     const int32_t* far_leaf;
     const int32_t* leaves;
     const float* mnorm;
+    int64_t nleaves, nnodes;  // bounds of the indices (checked in TP_DEBUG builds)
 };
 tp_status tp_launch_mlp_tc_feat(tp_ctx* ctx, const __nv_bfloat16* wb, const float* bias, const tp_feat_src& fs,
                                 int64_t w0, int64_t w1, float* kf);
@@ -393,6 +404,21 @@ const float* tp_mlp_norm(const tp_ctx* ctx);
 
 // ---------------------------------------------------------------- device helpers
 __device__ __forceinline__ void tp_dev_error(unsigned* derr, unsigned bit) { atomicOr(derr, bit); }
+
+// The checked build's bounds check: in a TP_DEBUG build, false (with TP_DERR_BOUNDS
+// recorded) when `ok` fails; always true in the release build.
+__device__ __forceinline__ bool tp_dbg_ok(bool ok, unsigned* derr) {
+#if TP_DEBUG
+    if (!ok) {
+        atomicOr(derr, TP_DERR_BOUNDS);
+        return false;
+    }
+#else
+    (void)ok;
+    (void)derr;
+#endif
+    return true;
+}
 
 // Bulk copies (cp.async.bulk, completion counted in bytes on an mbarrier) and
 // bounded mbarrier waits, shared by the pair kernels.

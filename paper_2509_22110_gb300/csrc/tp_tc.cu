@@ -289,6 +289,7 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const __nv_bfloat16* __restrict_
         if (t < ntiles && r < rows) {
             lf = fs.far_leaf[w0 + r];
             cn = fs.far_list[w0 + r];
+            if (!tp_dbg_ok(lf >= 0 && lf < fs.nleaves && cn >= 0 && cn < fs.nnodes, derr)) lf = cn = -1;
         }
     };
     auto feat_row = [&](int ln, int cn, uint4 (&v)[4]) {
@@ -324,6 +325,7 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const __nv_bfloat16* __restrict_
     if (FEAT) {
         load_idx(blockIdx.x, lf_next, c_next);
         l_next = c_next >= 0 ? fs.leaves[lf_next] : -1;
+        if (!tp_dbg_ok(l_next < fs.nnodes, derr)) c_next = -1;
     } else {
         load_row(blockIdx.x, vnext);
     }
@@ -365,7 +367,10 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const __nv_bfloat16* __restrict_
             tc_fence_after();
             tc_ld64(taddr, r);
             epi_hidden(r, S.bias + 64 * layer, S.act, tid);
-            if (FEAT && layer == 0) l_next = c_next >= 0 ? fs.leaves[lf_next] : -1;  // in flight until the next tile
+            if (FEAT && layer == 0) {
+                l_next = c_next >= 0 ? fs.leaves[lf_next] : -1;  // in flight until the next tile
+                if (!tp_dbg_ok(l_next < fs.nnodes, derr)) c_next = -1;
+            }
         }
         if (failed) break;
         // output layer (N = 16, rows 7..15 of W4 zero)

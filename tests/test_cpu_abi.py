@@ -83,3 +83,18 @@ def test_noalloc_binding_rejects_wrong_dtypes_on_the_host():
         _tp.tp_gradient_direct_noalloc(V[:, :2].contiguous(), F, e, g)
     with pytest.raises(ValueError):  # host tensors: the entry point takes device pointers only
         _tp.tp_gradient_direct_noalloc(V, F, e, g)
+
+
+def test_checked_build_exports_the_same_symbols(libpath):
+    """The checked build (device-side bounds checks, -DTP_DEBUG=1) compiles and
+    exports the same entry points as the release library."""
+    from paper_2509_22110_gb300 import build
+
+    dbg = build.build(debug=True)
+    assert os.path.basename(dbg) == "libtp_debug.so"
+
+    def exported(p):
+        out = subprocess.run(["nm", "-D", "--defined-only", p], capture_output=True, text=True, check=True).stdout
+        return set(re.findall(r"\bT (tp_[a-z_0-9]+)$", out, flags=re.M))
+
+    assert exported(dbg) == exported(libpath)
