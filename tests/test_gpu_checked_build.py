@@ -75,6 +75,9 @@ def test_checked_build_matches_release():
         ea, ga = a[key]
         eb, gb = b[key]
         ga, gb = np.asarray(ga), np.asarray(gb)
-        # the same arithmetic; the order of FP64 atomic adds may differ between runs
-        assert abs(ea - eb) <= 1e-12 * abs(ea), (key, ea, eb)
-        assert np.linalg.norm(ga - gb) <= 1e-12 * np.linalg.norm(ga), key
+        # the same arithmetic; the order of FP64 atomic adds may differ between runs. The
+        # cluster-cluster lists are appended with atomics, so their order, and with it the
+        # order of the FP32 partial sums over a leaf's partners, differs between runs too
+        tol = 1e-6 if key.startswith("dual") else 1e-12
+        assert abs(ea - eb) <= tol * abs(ea), (key, ea, eb)
+        assert np.linalg.norm(ga - gb) <= tol * np.linalg.norm(ga), key
