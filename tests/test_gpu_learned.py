@@ -308,6 +308,28 @@ def test_learned_windows_match_one_pass(tp, ctx):
         tp.tp_set_learned_window(ctx, 5)
 
 
+def test_barnes_hut_at_the_bar_with_leaves_of_32(tp, ctx):
+    """Plain Barnes-Hut with leaves of up to 32 at theta = 0.085 on a level-7 mesh
+    (seed 2): energy and gradient within the 1e-3 bar of the clustered forms,
+    where leaves of 16 at the same theta miss the energy bar."""
+    import torch
+
+    V, F = meshgen.sh_deformed_sphere(7, 12, 0.05, 2)
+    Vd = torch.tensor(V, device="cuda")
+    tp.tp_mesh_upload(ctx, Vd, torch.tensor(F, device="cuda"))
+    gd = torch.zeros_like(Vd)
+    ed = tp.tp_gradient(ctx, gd, tp.tp_params_default())
+    errs = {}
+    for leaf in (16, 32):
+        tp.tp_tree_build(ctx, leaf, 30)
+        g = torch.zeros_like(Vd)
+        e = tp.tp_gradient(ctx, g, tp.tp_params_default(mode=tp.TP_BH, theta=0.085))
+        errs[leaf] = (abs(e - ed) / ed, float(torch.linalg.norm(g - gd) / torch.linalg.norm(gd)))
+    print(errs)
+    assert errs[16][0] > 1e-3
+    assert errs[32][0] <= 1e-3 and errs[32][1] <= 1e-3
+
+
 @pytest.mark.parametrize("leaf,theta,model,energy_only", [
     (16, 0.125, "far_model_l7.bin", True),
     (32, 0.15, "far_model_l7_leaf32.bin", False),
