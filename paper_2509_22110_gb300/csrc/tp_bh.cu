@@ -204,7 +204,9 @@ __device__ __forceinline__ bool admissible(const LeafAdm& L, const float* c32, c
         r2f = fmaf(t, t, r2f);
         M += fabsf(c32[12 + a]) + fabsf(L.cl32[a]);
     }
-    const float distf = sqrtf(r2f);
+    // sqrt.approx: the margin below (1e-5 relative) is far above its error
+    float distf;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(distf) : "f"(r2f));
     const float rhsf = theta32 * (distf - 0.5f * L.dl32);
     const float lhsf = c32[15];
     const float margin = 1e-5f * (lhsf + theta32 * (distf + L.dl32 + M));
