@@ -473,16 +473,15 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
         bool is_far = false, is_near = false, is_open = false, touch = false, fast = false;
         int firstc = 0, cntc = 0, lc = 0, rc = 0;
         if (node >= 0 && tp_dbg_ok(node < 2 * A.n - 1, A.derr)) {
-            // everything the test and the push need, loaded in one round: the
-            // node's FP32 record, its member range and (internal nodes) its children
-            const float4* c4 = reinterpret_cast<const float4*>(A.adm32 + 16 * (int64_t)node);
-            const float4 q0 = c4[0], q1 = c4[1], q2 = c4[2], q3 = c4[3];
-            firstc = A.first[node];
-            const int lastc = A.last[node];
-            if (node < A.n - 1) {
-                lc = A.left[node];
-                rc = A.right[node];
-            }
+            // everything the test and the push need, in one round of five 16-byte
+            // loads of the node's record: boxes, centroid, diagonal, member range
+            // and children
+            const float4* c4 = reinterpret_cast<const float4*>(A.adm32 + TP_ADM32_W * (int64_t)node);
+            const float4 q0 = c4[0], q1 = c4[1], q2 = c4[2], q3 = c4[3], q4 = c4[4];
+            firstc = __float_as_int(q4.x);
+            const int lastc = __float_as_int(q4.y);
+            lc = __float_as_int(q4.z);
+            rc = __float_as_int(q4.w);
             cntc = lastc - firstc + 1;
             const float c32[16] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w,
                                    q2.x, q2.y, q2.z, q2.w, q3.x, q3.y, q3.z, q3.w};
@@ -498,7 +497,9 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
                     fast = box_gap2(la, c32) >= la.fast2;
                 }
             } else {
-                is_open = tp_dbg_ok(lc >= 0 && lc < 2 * A.n - 1 && rc >= 0 && rc < 2 * A.n - 1, A.derr);
+                is_open = tp_dbg_ok(lc >= 0 && lc < 2 * A.n - 1 && rc >= 0 && rc < 2 * A.n - 1 &&
+                                        A.first[node] == firstc && A.last[node] == lastc,
+                                    A.derr);
             }
         }
         const unsigned bf = __ballot_sync(0xffffffffu, is_far);

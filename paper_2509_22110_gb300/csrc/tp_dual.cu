@@ -75,7 +75,7 @@ struct DTTree {
     const double* mom;    // [nn][13]
     const double* box;    // [nn][6]
     const double* adm64;  // [nn][4] X (FP64 quotients), diagonal
-    const float* adm32;   // [nn][16] outward box, inward box, X, diagonal (FP32)
+    const float* adm32;   // [nn][TP_ADM32_W] outward box, inward box, X, diagonal (FP32), range, children
     const float* nodef;   // [nn][16] FP32 far-field record (nubar at 6..8)
     int64_t n;
     int leaf;
@@ -86,16 +86,6 @@ __device__ __forceinline__ bool dt_small(const DTTree& T, int node) {
     return node >= T.n - 1 || (T.last[node] - T.first[node] + 1) <= T.leaf;
 }
 
-__device__ __forceinline__ double dt_diag2(const double* b) {
-    double s = 0.0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const double e = __dsub_rn(b[3 + a], b[a]);
-        s = __dadd_rn(s, __dmul_rn(e, e));
-    }
-    return s;
-}
-
 // Admissibility of {A, B}: vertex boxes strictly apart along some axis and
 // max(diag_A, diag_B) < theta |X_A - X_B|.  The FP32 records decide when they
 // can: outward-rounded boxes apart -> apart, inward-rounded boxes overlapping
@@ -104,8 +94,8 @@ __device__ __forceinline__ double dt_diag2(const double* b) {
 // cases use FP64 boxes, centroid quotients and diagonals (the oracle's values
 // and operations: sqrt(max(dA2, dB2)) = max(sqrt dA2, sqrt dB2) exactly).
 __device__ bool dt_admissible(const DTTree& T, int A, int B, double theta, float theta32) {
-    const float* cA = T.adm32 + 16 * (int64_t)A;
-    const float* cB = T.adm32 + 16 * (int64_t)B;
+    const float* cA = T.adm32 + TP_ADM32_W * (int64_t)A;
+    const float* cB = T.adm32 + TP_ADM32_W * (int64_t)B;
     bool sure = false, amb = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -150,8 +140,8 @@ __device__ bool dt_admissible(const DTTree& T, int A, int B, double theta, float
 // FP32 outward-rounded vertex boxes strictly apart along some axis: no member
 // of A shares a vertex with a member of B
 __device__ __forceinline__ bool dt_boxes_apart(const DTTree& T, int A, int B) {
-    const float* cA = T.adm32 + 16 * (int64_t)A;
-    const float* cB = T.adm32 + 16 * (int64_t)B;
+    const float* cA = T.adm32 + TP_ADM32_W * (int64_t)A;
+    const float* cB = T.adm32 + TP_ADM32_W * (int64_t)B;
     bool apart = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a)

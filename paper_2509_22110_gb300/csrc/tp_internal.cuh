@@ -59,6 +59,12 @@ struct TpRange {
 // mesh's centroid-box diagonal form centroid differences from hi + lo parts
 #define TP_PRECISE_GAP_REL 0.02f
 
+// floats per node of the FP32 admissibility record: outward box [6], inward
+// box [6], X_C [3], diag_C [1], then first, last, left, right as int bits
+// (children -1 for single-triangle nodes): 80 bytes, so one round of five
+// 16-byte loads gives a traversal everything it needs about a node
+#define TP_ADM32_W 20
+
 // listed far rows per window of the learned passes: 32 Mi rows, 1 GB of
 // network factors (tp_set_learned_window changes it)
 #define TP_LEARNED_WINDOW ((int64_t)1 << 25)
@@ -97,7 +103,8 @@ struct tp_tree {
     double* box = nullptr;       // [2nt-1][6]
     float* nodef = nullptr;      // [2nt-1][16] f32 node summary used by the far-field terms
     double* adm64 = nullptr;     // [2nt-1][4] f64 X_C, diag_C of the admissibility test
-    float* adm32 = nullptr;      // [2nt-1][16] f32 outward/inward boxes, X_C, diag_C (pre-test)
+    float* adm32 = nullptr;      // [2nt-1][TP_ADM32_W] f32 outward/inward boxes, X_C, diag_C (pre-test),
+                                 // and the member range and children (int bits)
     float* nodeft = nullptr;     // [2nt-1][16] f32 feature record (A, X, nubar, M2/A, diag) of the network
     int32_t* nleaves_d = nullptr;
     int64_t cap = 0;

@@ -110,10 +110,13 @@ constexpr int MOM_W = 19;   // values per node: 13 moments + 6 box bounds
 //              the operations and order of the oracle's admissibility test;
 //   adm32[v] = box rounded outward (min down, max up) [6], box rounded inward
 //              (min up, max down) [6], X_C [3], diag_C [1] in FP32 for the
-//              pre-test that settles all but borderline cases (tp_bh.cu).
+//              pre-test that settles all but borderline cases (tp_bh.cu),
+//              then the member range and the children (int bits, -1 for a
+//              single-triangle node).
 __device__ __forceinline__ void node_records(int64_t v, const double* __restrict__ m, const double* __restrict__ b,
                                              const double* __restrict__ c3, float* __restrict__ nodef,
-                                             double* __restrict__ adm64, float* __restrict__ adm32) {
+                                             double* __restrict__ adm64, float* __restrict__ adm32, int first,
+                                             int last, int left, int right) {
     double dc2 = 0.0;
     double X[3];
 #pragma unroll
@@ -126,7 +129,7 @@ __device__ __forceinline__ void node_records(int64_t v, const double* __restrict
     double2* a64 = reinterpret_cast<double2*>(adm64 + 4 * v);
     a64[0] = make_double2(X[0], X[1]);
     a64[1] = make_double2(X[2], dc);
-    float4* a32 = reinterpret_cast<float4*>(adm32 + 16 * v);
+    float4* a32 = reinterpret_cast<float4*>(adm32 + TP_ADM32_W * v);
     a32[0] = make_float4(__double2float_rd(b[0]), __double2float_rd(b[1]), __double2float_rd(b[2]),
                          __double2float_ru(b[3]));
     a32[1] = make_float4(__double2float_ru(b[4]), __double2float_ru(b[5]), __double2float_ru(b[0]),
@@ -134,6 +137,7 @@ __device__ __forceinline__ void node_records(int64_t v, const double* __restrict
     a32[2] = make_float4(__double2float_ru(b[2]), __double2float_rd(b[3]), __double2float_rd(b[4]),
                          __double2float_rd(b[5]));
     a32[3] = make_float4((float)X[0], (float)X[1], (float)X[2], (float)dc);
+    a32[4] = make_float4(__int_as_float(first), __int_as_float(last), __int_as_float(left), __int_as_float(right));
     float hi[3], lo[3], nb[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -273,9 +277,9 @@ __global__ void __launch_bounds__(MOM_B) k_moments(
 // far-field and admissibility records of every node the traversal can reach
 __global__ void __launch_bounds__(TP_NODE_THREADS) k_node_out(
     const double* __restrict__ mom, const double* __restrict__ box, const int32_t* __restrict__ parent,
-    const int32_t* __restrict__ first, const int32_t* __restrict__ last, int leaf_size,
-    const double* __restrict__ center, int64_t nn, float* __restrict__ nodef, double* __restrict__ adm64,
-    float* __restrict__ adm32) {
+    const int32_t* __restrict__ first, const int32_t* __restrict__ last, const int32_t* __restrict__ left,
+    const int32_t* __restrict__ right, int leaf_size, const double* __restrict__ center, int64_t nn,
+    float* __restrict__ nodef, double* __restrict__ adm64, float* __restrict__ adm32) {
     __shared__ int32_t list[TP_NODE_BLK];
     __shared__ int cnt;
     const int n = tp_reachable_list(parent, first, last, leaf_size, blockIdx.x * (int64_t)TP_NODE_BLK, nn, list,
@@ -293,7 +297,9 @@ __global__ void __launch_bounds__(TP_NODE_THREADS) k_node_out(
             b[2 * c] = x.x;
             b[2 * c + 1] = x.y;
         }
-        node_records(v, m, b, c3, nodef, adm64, adm32);
+        const int64_t n = (nn + 1) / 2;  // triangles; nodes below n - 1 are internal
+        node_records(v, m, b, c3, nodef, adm64, adm32, first[v], last[v], v < n - 1 ? left[v] : -1,
+                     v < n - 1 ? right[v] : -1);
     }
 }
 
@@ -336,7 +342,7 @@ tp_status tp_launch_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits) {
         TP_TRY(tp_alloc_t(ctx, &t.nodef, 16 * nn));
         TP_TRY(tp_alloc_t(ctx, &t.nleaves_d, 4));
         TP_TRY(tp_alloc_t(ctx, &t.adm64, 4 * nn));
-        TP_TRY(tp_alloc_t(ctx, &t.adm32, 16 * nn));
+        TP_TRY(tp_alloc_t(ctx, &t.adm32, TP_ADM32_W * nn));
         TP_TRY(tp_alloc_t(ctx, &t.nodeft, 16 * nn));
         t.cap = n;
     }
@@ -369,7 +375,8 @@ tp_status tp_launch_tree_build(tp_ctx* ctx, int leaf_size, int morton_bits) {
                                                          t.mom, t.box);
     ++ctx->nlaunch;
     k_node_out<<<nblk(nn, TP_NODE_BLK), TP_NODE_THREADS, 0, ctx->stream>>>(
-        t.mom, t.box, t.parent, t.first, t.last, leaf_size, ctx->center, nn, t.nodef, t.adm64, t.adm32);
+        t.mom, t.box, t.parent, t.first, t.last, t.left, t.right, leaf_size, ctx->center, nn, t.nodef, t.adm64,
+        t.adm32);
     ++ctx->nlaunch;
     t.feat_stale = true;  // the network's node features are computed when the learned form needs them
     int32_t h = 0;
