@@ -187,7 +187,7 @@ __device__ __forceinline__ bool admissible(const LeafAdm& L, const float* c32, c
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (L.out[3 + a] < c32[a] || c32[3 + a] < L.out[a]) sure = true;
-        else if (!(L.in[3 + a] >= c32[6 + a] && c32[9 + a] >= L.in[a])) amb = true;
+        else if (!(L.in[3 + a] >= tp_inward_lo(c32[a]) && tp_inward_hi(c32[3 + a]) >= L.in[a])) amb = true;
     }
     if (!sure) {
         if (!amb) return false;
@@ -200,15 +200,15 @@ __device__ __forceinline__ bool admissible(const LeafAdm& L, const float* c32, c
     float r2f = 0.f, M = 0.f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float t = c32[12 + a] - L.cl32[a];
+        const float t = c32[6 + a] - L.cl32[a];
         r2f = fmaf(t, t, r2f);
-        M += fabsf(c32[12 + a]) + fabsf(L.cl32[a]);
+        M += fabsf(c32[6 + a]) + fabsf(L.cl32[a]);
     }
     // sqrt.approx: the margin below (1e-5 relative) is far above its error
     float distf;
     asm("sqrt.approx.f32 %0, %1;" : "=f"(distf) : "f"(r2f));
     const float rhsf = theta32 * (distf - 0.5f * L.dl32);
-    const float lhsf = c32[15];
+    const float lhsf = c32[9];
     const float margin = 1e-5f * (lhsf + theta32 * (distf + L.dl32 + M));
     if (lhsf < rhsf - margin) return true;
     if (lhsf > rhsf + margin) return false;
@@ -473,15 +473,15 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
         bool is_far = false, is_near = false, is_open = false, touch = false, fast = false;
         int firstc = 0, cntc = 0, lc = 0, rc = 0;
         if (node >= 0 && tp_dbg_ok(node < 2 * A.n - 1, A.derr)) {
-            // everything the test and the push need, in one round of five 16-byte
-            // loads of the node's record: boxes, centroid, diagonal, member range
+            // everything the test and the push need, in one round of four 16-byte
+            // loads of the node's record: box, centroid, diagonal, member range
             // and children
             const float4* c4 = reinterpret_cast<const float4*>(A.adm32 + TP_ADM32_W * (int64_t)node);
-            const float4 q0 = c4[0], q1 = c4[1], q2 = c4[2], q3 = c4[3], q4 = c4[4];
-            firstc = __float_as_int(q4.x);
-            const int lastc = __float_as_int(q4.y);
-            lc = __float_as_int(q4.z);
-            rc = __float_as_int(q4.w);
+            const float4 q0 = c4[0], q1 = c4[1], q2 = c4[2], q3 = c4[3];
+            firstc = __float_as_int(q2.z);
+            const int lastc = __float_as_int(q2.w);
+            lc = __float_as_int(q3.x);
+            rc = __float_as_int(q3.y);
             cntc = lastc - firstc + 1;
             const float c32[16] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w,
                                    q2.x, q2.y, q2.z, q2.w, q3.x, q3.y, q3.z, q3.w};

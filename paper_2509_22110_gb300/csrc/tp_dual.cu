@@ -75,7 +75,7 @@ struct DTTree {
     const double* mom;    // [nn][13]
     const double* box;    // [nn][6]
     const double* adm64;  // [nn][4] X (FP64 quotients), diagonal
-    const float* adm32;   // [nn][TP_ADM32_W] outward box, inward box, X, diagonal (FP32), range, children
+    const float* adm32;   // [nn][TP_ADM32_W] outward box, X, diagonal (FP32), range, children
     const float* nodef;   // [nn][16] FP32 far-field record (nubar at 6..8)
     int64_t n;
     int leaf;
@@ -100,7 +100,8 @@ __device__ bool dt_admissible(const DTTree& T, int A, int B, double theta, float
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (cA[3 + a] < cB[a] || cB[3 + a] < cA[a]) sure = true;
-        else if (!(cA[9 + a] >= cB[6 + a] && cB[9 + a] >= cA[6 + a])) amb = true;
+        else if (!(tp_inward_hi(cA[3 + a]) >= tp_inward_lo(cB[a]) && tp_inward_hi(cB[3 + a]) >= tp_inward_lo(cA[a])))
+            amb = true;
     }
     if (!sure) {
         if (!amb) return false;
@@ -115,12 +116,12 @@ __device__ bool dt_admissible(const DTTree& T, int A, int B, double theta, float
     float r2f = 0.f, M = 0.f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float t = cA[12 + a] - cB[12 + a];
+        const float t = cA[6 + a] - cB[6 + a];
         r2f = fmaf(t, t, r2f);
-        M += fabsf(cA[12 + a]) + fabsf(cB[12 + a]);
+        M += fabsf(cA[6 + a]) + fabsf(cB[6 + a]);
     }
     const float distf = sqrtf(r2f);
-    const float lhsf = fmaxf(cA[15], cB[15]);
+    const float lhsf = fmaxf(cA[9], cB[9]);
     const float rhsf = theta32 * distf;
     const float margin = 1e-5f * (lhsf + theta32 * (distf + M));
     if (lhsf < rhsf - margin) return true;

@@ -59,11 +59,12 @@ struct TpRange {
 // mesh's centroid-box diagonal form centroid differences from hi + lo parts
 #define TP_PRECISE_GAP_REL 0.02f
 
-// floats per node of the FP32 admissibility record: outward box [6], inward
-// box [6], X_C [3], diag_C [1], then first, last, left, right as int bits
-// (children -1 for single-triangle nodes): 80 bytes, so one round of five
-// 16-byte loads gives a traversal everything it needs about a node
-#define TP_ADM32_W 20
+// floats per node of the FP32 admissibility record: outward box [6], X_C [3],
+// diag_C [1], first, last, left, right as int bits (children -1 for
+// single-triangle nodes), 2 unused: 64 bytes, so one round of four 16-byte
+// loads gives a traversal everything it needs about a node.  The inward box
+// of the pre-test is derived from the outward one (tp_inward_lo/hi).
+#define TP_ADM32_W 16
 
 // listed far rows per window of the learned passes: 32 Mi rows, 1 GB of
 // network factors (tp_set_learned_window changes it)
@@ -411,6 +412,16 @@ const float* tp_mlp_norm(const tp_ctx* ctx);
 
 // ---------------------------------------------------------------- device helpers
 __device__ __forceinline__ void tp_dev_error(unsigned* derr, unsigned bit) { atomicOr(derr, bit); }
+
+// A bound inside the FP64 interval [lo, hi] whose FP32 outward roundings are
+// olo = rd(lo), ohi = ru(hi): moving olo up (ohi down) by |x| 1.25e-7 + 1e-37
+// passes at least one float spacing (|x| 2^-23 for normal x, below 1e-37
+// otherwise), and the next float above rd(lo) is at least lo.  So
+// tp_inward_lo(olo) >= lo and tp_inward_hi(ohi) <= hi: inward bounds, at most
+// a few spacings tighter than the inward roundings, for a pre-test whose
+// undecided cases go to FP64.
+__device__ __forceinline__ float tp_inward_lo(float olo) { return fmaf(fabsf(olo), 1.25e-7f, olo) + 1e-37f; }
+__device__ __forceinline__ float tp_inward_hi(float ohi) { return fmaf(-fabsf(ohi), 1.25e-7f, ohi) - 1e-37f; }
 
 // The checked build's bounds check: in a TP_DEBUG build, false (with TP_DERR_BOUNDS
 // recorded) when `ok` fails; always true in the release build.

@@ -108,11 +108,10 @@ constexpr int MOM_W = 19;   // values per node: 13 moments + 6 box bounds
 //              in FP32 for the far-field terms;
 //   adm64[v] = (X_C[3] = sum(w x)/A, diag_C = |box extent|) in FP64, with exactly
 //              the operations and order of the oracle's admissibility test;
-//   adm32[v] = box rounded outward (min down, max up) [6], box rounded inward
-//              (min up, max down) [6], X_C [3], diag_C [1] in FP32 for the
-//              pre-test that settles all but borderline cases (tp_bh.cu),
-//              then the member range and the children (int bits, -1 for a
-//              single-triangle node).
+//   adm32[v] = box rounded outward (min down, max up) [6], X_C [3], diag_C [1]
+//              in FP32 for the pre-test that settles all but borderline cases
+//              (tp_bh.cu), then the member range and the children (int bits,
+//              -1 for a single-triangle node).
 __device__ __forceinline__ void node_records(int64_t v, const double* __restrict__ m, const double* __restrict__ b,
                                              const double* __restrict__ c3, float* __restrict__ nodef,
                                              double* __restrict__ adm64, float* __restrict__ adm32, int first,
@@ -132,12 +131,9 @@ __device__ __forceinline__ void node_records(int64_t v, const double* __restrict
     float4* a32 = reinterpret_cast<float4*>(adm32 + TP_ADM32_W * v);
     a32[0] = make_float4(__double2float_rd(b[0]), __double2float_rd(b[1]), __double2float_rd(b[2]),
                          __double2float_ru(b[3]));
-    a32[1] = make_float4(__double2float_ru(b[4]), __double2float_ru(b[5]), __double2float_ru(b[0]),
-                         __double2float_ru(b[1]));
-    a32[2] = make_float4(__double2float_ru(b[2]), __double2float_rd(b[3]), __double2float_rd(b[4]),
-                         __double2float_rd(b[5]));
-    a32[3] = make_float4((float)X[0], (float)X[1], (float)X[2], (float)dc);
-    a32[4] = make_float4(__int_as_float(first), __int_as_float(last), __int_as_float(left), __int_as_float(right));
+    a32[1] = make_float4(__double2float_ru(b[4]), __double2float_ru(b[5]), (float)X[0], (float)X[1]);
+    a32[2] = make_float4((float)X[2], (float)dc, __int_as_float(first), __int_as_float(last));
+    a32[3] = make_float4(__int_as_float(left), __int_as_float(right), 0.f, 0.f);
     float hi[3], lo[3], nb[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
