@@ -44,6 +44,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <type_traits>
 
 #include "tp_internal.cuh"
 #include "tp_mlp_dev.cuh"
@@ -57,6 +58,9 @@ constexpr int BH_FAR = 256;
 constexpr int BH_NEAR = 128;
 #ifndef TP_NEAR_FAST
 #define TP_NEAR_FAST 1  // near clusters far enough apart take the hi-part difference only
+#endif
+#ifndef TP_FAR_FAST
+#define TP_FAR_FAST 1  // the same for the far nodes of the plain form
 #endif
 #ifndef TP_BH_MINB
 #define TP_BH_MINB 5  // resident blocks per SM asked of the register allocator (20 warps)
@@ -333,31 +337,42 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
         }
     };
     // far nodes of the plain form: stage 32 node records at a time, then
-    // sweep them in pairs (one target against two records per packed step)
-    auto flush_far = [&](int nf) {
+    // sweep them in pairs (one target against two records per packed step).
+    // The list holds nodes whose boxes are at least TP_PRECISE_GAP_REL of the
+    // mesh diagonal from the leaf's at its back (far[BH_FAR - 1 - i], i < nff):
+    // their differences take the hi parts alone, as k_near's.  The others sit
+    // at its front (far[i], i < nfp).  The target weight is applied to the sums.
+    auto sweep_far = [&](auto hilo, int nb0, float2 (&a2)[8]) {
+        constexpr bool HILO = decltype(hilo)::value;
+        for (int b0 = 0; b0 < nb0; b0 += 32) {
+            const int nb = nb0 - b0 < 32 ? nb0 - b0 : 32;
+            __syncwarp();
+            if (lane < nb) {
+                const int node = HILO ? far[b0 + lane] : far[BH_FAR - 1 - (b0 + lane)];
+                const float4* r = reinterpret_cast<const float4*>(A.nodef + 16 * (int64_t)node);
+                const float4 r0 = r[0], r1 = r[1], r2 = r[2];
+                const float v[10] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y};
+                stage_put(stg, lane, v);
+            } else if (lane == nb && (nb & 1)) {
+                stage_pad(stg, lane);
+            }
+            __syncwarp();
+            const int np = (nb + 1) >> 1;
+            for (int p = half; p < np; p += nh) gather_pair2<Q, false, HILO, true>(tg, stg, p, a2);
+        }
+    };
+    auto flush_far = [&](int nfp, int nff) {
         if constexpr (MODE == M_LIST) {
-            emit_far(nf);
+            emit_far(nfp);
         } else {
             float2 a2[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c) a2[c] = bh_f2(0.f);
-            for (int b0 = 0; b0 < nf; b0 += 32) {
-                const int nb = nf - b0 < 32 ? nf - b0 : 32;
-                __syncwarp();
-                if (lane < nb) {
-                    const float4* r = reinterpret_cast<const float4*>(A.nodef + 16 * (int64_t)far[b0 + lane]);
-                    const float4 r0 = r[0], r1 = r[1], r2 = r[2];
-                    const float v[10] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y};
-                    stage_put(stg, lane, v);
-                } else if (lane == nb && (nb & 1)) {
-                    stage_pad(stg, lane);
-                }
-                __syncwarp();
-                const int np = (nb + 1) >> 1;
-                for (int p = half; p < np; p += nh) gather_pair2<Q, false>(tg, stg, p, a2);
-            }
+            sweep_far(std::true_type{}, nfp, a2);
+            sweep_far(std::false_type{}, nff, a2);
+            const double tw = (double)tg.w.x;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) acc[c] += (double)(a2[c].x + a2[c].y);
+            for (int c = 0; c < 8; ++c) acc[c] += (double)(a2[c].x + a2[c].y) * tw;
         }
     };
     // near clusters apart from the leaf: one run of (first member, count)
@@ -461,7 +476,7 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
         for (int c = 0; c < 8; ++c) acc[c] += (double)(a2[c].x + a2[c].y);
     };
 
-    int sp = 1, nf = 0, nn[2] = {0, 0};
+    int sp = 1, nfp = 0, nff = 0, nn[2] = {0, 0};
     if (lane == 0) st[0] = 0;  // root
     __syncwarp();
     bool overflow = false;
@@ -470,7 +485,7 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
         const int node = lane < m ? st[sp - 1 - lane] : -1;
         __syncwarp();
         sp -= m;
-        bool is_far = false, is_near = false, is_open = false, touch = false, fast = false;
+        bool is_far = false, is_near = false, is_open = false, touch = false, fast = false, ffast = false;
         int firstc = 0, cntc = 0, lc = 0, rc = 0;
         if (node >= 0 && tp_dbg_ok(node < 2 * A.n - 1, A.derr)) {
             // everything the test and the push need, in one round of four 16-byte
@@ -487,6 +502,7 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
                                    q2.x, q2.y, q2.z, q2.w, q3.x, q3.y, q3.z, q3.w};
             if (admissible(la, c32, A.box + 6 * (int64_t)node, A.adm64 + 4 * (int64_t)node, A.theta, theta32)) {
                 is_far = true;
+                ffast = TP_FAR_FAST && MODE == M_BH && box_gap2(la, c32) >= la.fast2;
                 n_far += (unsigned long long)cnt;
                 n_farp += (unsigned long long)cnt * (unsigned long long)cntc;
             } else if (cntc <= A.leaf_size || node >= A.n - 1) {
@@ -502,7 +518,8 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
                                     A.derr);
             }
         }
-        const unsigned bf = __ballot_sync(0xffffffffu, is_far);
+        const unsigned bfp = __ballot_sync(0xffffffffu, is_far && !ffast);
+        const unsigned bff = __ballot_sync(0xffffffffu, is_far && ffast);
         const unsigned bn0 = __ballot_sync(0xffffffffu, is_near && !touch);
         const unsigned bn1 = __ballot_sync(0xffffffffu, is_near && touch);
         const unsigned bo = __ballot_sync(0xffffffffu, is_open);
@@ -519,7 +536,8 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
                 }
             }
         } else {
-            if (is_far) far[nf + __popc(bf & lt)] = node;
+            if (is_far && !ffast) far[nfp + __popc(bfp & lt)] = node;
+            if (is_far && ffast) far[BH_FAR - 1 - (nff + __popc(bff & lt))] = node;
             // (first member, count); a negative count marks a cluster whose pairs take the hi parts only
             if (is_near && !touch) s_near[warp][0][nn[0] + __popc(bn0 & lt)] = make_int2(firstc, fast ? -cntc : cntc);
             if (is_near && touch) s_near[warp][1][nn[1] + __popc(bn1 & lt)] = make_int2(firstc, cntc);
@@ -530,15 +548,16 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
             st[pos + 1] = lc;
         }
         if (MODE != M_RECORD) {
-            nf += __popc(bf);
+            nfp += __popc(bfp);
+            nff += __popc(bff);
             nn[0] += __popc(bn0);
             nn[1] += __popc(bn1);
         }
         sp += 2 * __popc(bo);
         __syncwarp();
-        if (nf > BH_FAR - 32) {
-            flush_far(nf);
-            nf = 0;
+        if (nfp + nff > BH_FAR - 32) {
+            flush_far(nfp, nff);
+            nfp = nff = 0;
         }
         if (nn[0] > BH_NEAR - 32) {
             emit_near(nn[0]);
@@ -555,7 +574,7 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
         return;
     }
     if (MODE == M_RECORD) return;
-    flush_far(nf);
+    flush_far(nfp, nff);
     emit_near(nn[0]);
     flush_touch(s_near[warp][1], nn[1]);
     if (!wide) {
@@ -675,16 +694,44 @@ __global__ void __launch_bounds__(NR_WARPS * 32) k_near(BHArgs A) {
         }
         __syncwarp();
         // slot planning: whole clusters of one kind (a negative count marks a
-        // cluster whose pairs take the hi parts only) while they fit; lane 0
-        // issues the copies
+        // cluster whose pairs take the hi parts only) while they fit.  The warp
+        // plans up to 32 entries at a time: a ballot finds where the kind
+        // changes, a scan of the counts where the slot is full, and every lane
+        // of the taken prefix issues its own cluster's copy (at most two rounds:
+        // a slot holds at most NR_SLOT <= 64 clusters of one record).
+        static_assert(NR_SLOT <= 64, "two planning rounds of 32 entries fill a slot");
         int next = 0, ns0 = 0, ns1 = 0;  // records planned into slot 0 / 1 and not yet consumed
         bool hi0 = false, hi1 = false;   // the slot's clusters take the hi parts only
         auto plan = [&](int b) {
             int n = 0;
-            const int i0 = next;
             const bool hi = next < R.len && S.ent[next].y < 0;
-            while (next < R.len && (S.ent[next].y < 0) == hi && n + abs(S.ent[next].y) <= NR_SLOT)
-                n += abs(S.ent[next++].y);
+            int my_e[2] = {-1, -1}, my_o[2] = {0, 0};  // this lane's entries and their record offsets
+#pragma unroll
+            for (int round = 0; round < 2; ++round) {
+                if (next >= R.len) break;  // warp-uniform
+                const int e = next + lane;
+                const int2 en = e < R.len ? S.ent[e] : make_int2(0, 0);
+                const int c = abs(en.y);
+                const bool same = e < R.len && (en.y < 0) == hi;
+                const unsigned brk = __ballot_sync(0xffffffffu, !same);
+                const int f = brk ? __ffs(brk) - 1 : 32;  // entries of the slot's kind: lanes < f
+                int incl = lane < f ? c : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                // counts are >= 1, so the entries that fit form a prefix
+                const bool take = lane < f && n + incl <= NR_SLOT;
+                const int m = __popc(__ballot_sync(0xffffffffu, take));
+                if (take) {
+                    my_e[round] = e;
+                    my_o[round] = n + incl - c;
+                }
+                n += m ? __shfl_sync(0xffffffffu, incl, m - 1) : 0;
+                next += m;
+                if (m < 32) break;
+            }
             if (b) {
                 ns1 = n;
                 hi1 = hi;
@@ -697,16 +744,14 @@ __global__ void __launch_bounds__(NR_WARPS * 32) k_near(BHArgs A) {
                 if (next < R.len && lane == 0) tp_dev_error(A.derr, TP_DERR_INTERNAL);
                 return;
             }
-            if (lane == 0) {
-                mbar_expect_tx(&S.bar[b], (uint32_t)(n * TP_SRCW * 4));
-                int o = 0;
-                for (int e = i0; e < next; ++e) {
-                    const int2 en = S.ent[e];
-                    const int c = abs(en.y);
-                    tma_load_1d(S.rec[b] + o * TP_SRCW, A.src + (int64_t)en.x * TP_SRCW,
-                                (uint32_t)(c * TP_SRCW * 4), &S.bar[b]);
-                    o += c;
-                }
+            if (lane == 0) mbar_expect_tx(&S.bar[b], (uint32_t)(n * TP_SRCW * 4));
+            __syncwarp();  // the expected bytes are set before any copy can complete
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                if (my_e[r] < 0) continue;
+                const int2 en = S.ent[my_e[r]];
+                tma_load_1d(S.rec[b] + my_o[r] * TP_SRCW, A.src + (int64_t)en.x * TP_SRCW,
+                            (uint32_t)(abs(en.y) * TP_SRCW * 4), &S.bar[b]);
             }
         };
         plan(0);

@@ -112,8 +112,8 @@ __device__ __forceinline__ void pair_core(const float2 (&th)[3], const float2 (&
 }
 
 // One target (duplicated in both halves of t) against the staged source pair
-// p (data at stg + p * BH_PAIR).
-template <int Q, bool SEL>
+// p (data at stg + p * BH_PAIR); HILO and TW1 as in pair_core.
+template <int Q, bool SEL, bool HILO = true, bool TW1 = false>
 __device__ __forceinline__ void gather_pair2(const Tgt2& t, const float* stg, int p, float2 acc[8], bool v0 = true,
                                              bool v1 = true) {
     const float4* r = reinterpret_cast<const float4*>(stg + p * BH_PAIR);
@@ -121,7 +121,7 @@ __device__ __forceinline__ void gather_pair2(const Tgt2& t, const float* stg, in
     const float2 sh[3] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y)};
     const float2 sl[3] = {make_float2(q1.z, q1.w), make_float2(q2.x, q2.y), make_float2(q2.z, q2.w)};
     const float2 sn[3] = {make_float2(q3.x, q3.y), make_float2(q3.z, q3.w), make_float2(q4.x, q4.y)};
-    pair_core<Q, SEL>(t.h, t.l, t.n, t.w, sh, sl, sn, make_float2(q4.z, q4.w), acc, v0, v1);
+    pair_core<Q, SEL, HILO, TW1>(t.h, t.l, t.n, t.w, sh, sl, sn, make_float2(q4.z, q4.w), acc, v0, v1);
 }
 
 __device__ __forceinline__ bool adjacent(int3 a, int3 b, int edge_only) {
