@@ -301,7 +301,10 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
         for (int c = 0; c < 3; ++c) tg.h[c] = tg.l[c] = tg.n[c] = bh_f2(0.f);
         tg.w = bh_f2(0.f);
     }
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // the target's sums over the flushes: compensated FP32 (value as - ac)
+    float as_[8], ac[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) as_[c] = ac[c] = 0.f;
     // statistics: pair counts of far terms and of near pairs without exclusion
     // tests are taken per node in the traversal (lane of the node), those of
     // touching near nodes per admitted pair
@@ -370,9 +373,9 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
             for (int c = 0; c < 8; ++c) a2[c] = bh_f2(0.f);
             sweep_far(std::true_type{}, nfp, a2);
             sweep_far(std::false_type{}, nff, a2);
-            const double tw = (double)tg.w.x;
+            const float tw = tg.w.x;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) acc[c] += (double)(a2[c].x + a2[c].y) * tw;
+            for (int c = 0; c < 8; ++c) ksum_add(as_[c], ac[c], (a2[c].x + a2[c].y) * tw);
         }
     };
     // near clusters apart from the leaf: one run of (first member, count)
@@ -473,7 +476,7 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
             i = i1;
         }
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] += (double)(a2[c].x + a2[c].y);
+        for (int c = 0; c < 8; ++c) ksum_add(as_[c], ac[c], a2[c].x + a2[c].y);
     };
 
     int sp = 1, nfp = 0, nff = 0, nn[2] = {0, 0};
@@ -577,6 +580,9 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
     flush_far(nfp, nff);
     emit_near(nn[0]);
     flush_touch(s_near[warp][1], nn[1]);
+    double acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = (double)as_[c] - (double)ac[c];
     if (!wide) {
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 16);
@@ -759,7 +765,7 @@ __global__ void __launch_bounds__(NR_WARPS * 32) k_near(BHArgs A) {
         float2 a2[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) a2[c] = bh_f2(0.f);
-        double e64[2] = {0.0, 0.0};
+        KSum2 ek = {bh_f2(0.f), bh_f2(0.f)};  // the energy channel, folded after every slot
         for (int slot = 0;; ++slot) {
             const int b = slot & 1;
             const int n = b ? ns1 : ns0;
@@ -783,8 +789,7 @@ __global__ void __launch_bounds__(NR_WARPS * 32) k_near(BHArgs A) {
                 else
                     for (int j = g; j < n; j += ng) near_pair2<Q, true>(tg, rb + j * TP_SRCW, a2);
             }
-            e64[0] += (double)a2[0].x;
-            e64[1] += (double)a2[0].y;
+            ksum2_add(ek, a2[0]);
             a2[0] = bh_f2(0.f);
             __syncwarp();  // every lane is done with slot b before it is refilled
             plan(b);
@@ -808,6 +813,7 @@ __global__ void __launch_bounds__(NR_WARPS * 32) k_near(BHArgs A) {
             red[lane * 16 + 2 * c] = a2[c].x;
             red[lane * 16 + 2 * c + 1] = a2[c].y;
         }
+        double e64[2] = {(double)ek.s.x - (double)ek.c.x, (double)ek.s.y - (double)ek.c.y};
         ered[2 * lane] = e64[0];
         ered[2 * lane + 1] = e64[1];
         __syncwarp();
@@ -1042,8 +1048,8 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) k_far(BHArgs A, const float* _
         float2 a2[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) a2[c] = bh_f2(0.f);
-        double e64[2] = {0.0, 0.0};
-        double de_lane = 0.0;
+        KSum2 ek = {bh_f2(0.f), bh_f2(0.f)};   // the energy channel, folded after every batch
+        KSum2 kde = {bh_f2(0.f), bh_f2(0.f)};  // EO: the energy correction, likewise
         // this lane's row of a batch, loaded one batch ahead
         float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0, q2 = q0, k0 = q0, k1 = q0;
         auto load_row = [&](int b0, int nb) {
@@ -1091,10 +1097,9 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) k_far(BHArgs A, const float* _
             if (g < ng) {
                 for (int j = g; j < n; j += ng) far_pair2_learned<Q, EO>(tg, rec + j * TP_SRCW, fk + j * 8, a2, dacc);
             }
-            e64[0] += (double)a2[0].x;
-            e64[1] += (double)a2[0].y;
+            ksum2_add(ek, a2[0]);
             a2[0] = bh_f2(0.f);
-            if (EO) de_lane += (double)dacc.x + (double)dacc.y;
+            if (EO) ksum2_add(kde, dacc);
         }
         // sum the streams through shared memory and add to the targets
         __syncwarp();
@@ -1105,6 +1110,7 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) k_far(BHArgs A, const float* _
             red[lane * 16 + 2 * c] = a2[c].x;
             red[lane * 16 + 2 * c + 1] = a2[c].y;
         }
+        double e64[2] = {(double)ek.s.x - (double)ek.c.x, (double)ek.s.y - (double)ek.c.y};
         ered[2 * lane] = e64[0];
         ered[2 * lane + 1] = e64[1];
         __syncwarp();
@@ -1129,6 +1135,7 @@ __global__ void __launch_bounds__(FAR_WARPS * 32) k_far(BHArgs A, const float* _
             }
         }
         if (EO) {
+            double de_lane = ((double)kde.s.x - (double)kde.c.x) + ((double)kde.s.y - (double)kde.c.y);
             for (int o = 16; o > 0; o >>= 1) de_lane += __shfl_xor_sync(0xffffffffu, de_lane, o);
             if (lane == 0 && de_lane != 0.0) atomicAdd(de, de_lane);
         }

@@ -411,7 +411,10 @@ __global__ void __launch_bounds__(DT_NEAR_WARPS * 32) k_dt_near(const float* __r
     }
     tg.w = bh_f2(active ? soa[9 * ntp + k] : 0.f);
     if (active) tf = make_int3(Fs[3 * k], Fs[3 * k + 1], Fs[3 * k + 2]);
-    double a64[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // the target's sums over the batches: compensated FP32 (value as_ - ac)
+    float as_[8], ac[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) as_[c] = ac[c] = 0.f;
     unsigned long long n_adm = 0;
     const uint32_t e0 = off[li], e1 = off[li + 1];
 #if TP_DEBUG
@@ -464,9 +467,12 @@ __global__ void __launch_bounds__(DT_NEAR_WARPS * 32) k_dt_near(const float* __r
             n_adm += (unsigned long long)(v0 + v1);
         }
 #pragma unroll
-        for (int c = 0; c < 8; ++c) a64[c] += (double)(a2[c].x + a2[c].y);
+        for (int c = 0; c < 8; ++c) ksum_add(as_[c], ac[c], a2[c].x + a2[c].y);
         e = e2;
     }
+    double a64[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a64[c] = (double)as_[c] - (double)ac[c];
     if (!wide) {
 #pragma unroll
         for (int c = 0; c < 8; ++c) a64[c] += __shfl_xor_sync(0xffffffffu, a64[c], 16);

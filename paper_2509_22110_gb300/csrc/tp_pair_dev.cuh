@@ -25,6 +25,32 @@ __device__ __forceinline__ float2 bh_fma2(float2 a, float2 b, float2 c) { return
 __device__ __forceinline__ float2 bh_mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 bh_add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
+// Compensated FP32 running sums (Kahan), one per half: the value is s - c.
+// The clustered kernels fold their per-batch FP32 partials into these
+// instead of into FP64 sums: FP64 arithmetic runs at a small fraction of the
+// FP32 rate on this part, and its pipe stalled the warps that issued the
+// folds.  (t - s) - y is formed with FMAs by -1, which no compiler
+// contraction can change.
+struct KSum2 {
+    float2 s, c;
+};
+
+__device__ __forceinline__ void ksum2_add(KSum2& k, float2 x) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 y = __ffma2_rn(k.c, m1, x);
+    const float2 t = __fadd2_rn(k.s, y);
+    k.c = __ffma2_rn(y, m1, __ffma2_rn(k.s, m1, t));
+    k.s = t;
+}
+
+// The same for one scalar sum.
+__device__ __forceinline__ void ksum_add(float& s, float& c, float x) {
+    const float y = __fmaf_rn(c, -1.f, x);
+    const float t = __fadd_rn(s, y);
+    c = __fmaf_rn(y, -1.f, __fmaf_rn(s, -1.f, t));
+    s = t;
+}
+
 struct Tgt2 {
     float2 h[3], l[3], n[3], w;
 };
