@@ -277,9 +277,10 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
     __syncwarp();
     const LeafAdm& la = s_la[warp];
     const float theta32 = (float)A.theta;
-    // leaves of up to 16 targets: lanes t and t + 16 share target t and take
-    // alternate source pairs; larger leaves: one target per lane
-    const bool wide = A.leaf_size > 16;
+    // a leaf of up to 16 targets (in a tree of any leaf size): lanes t and
+    // t + 16 share target t and take alternate source pairs; a larger leaf:
+    // one target per lane
+    const bool wide = cnt > 16;
     const int t = wide ? lane : (lane & 15);
     const int half = wide ? 0 : (lane >> 4);
     const int nh = wide ? 1 : 2;

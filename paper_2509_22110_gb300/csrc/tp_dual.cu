@@ -398,6 +398,7 @@ __global__ void __launch_bounds__(DT_NEAR_WARPS * 32) k_dt_near(const float* __r
     const int64_t L = leaves[li];
     const int64_t fL = first[L];
     const int cnt = last[L] - first[L] + 1;
+    wide = wide && cnt > 16;  // a leaf of up to 16 targets takes two lanes per target in any tree
     const int t = wide ? lane : (lane & 15), half = wide ? 0 : (lane >> 4), nh = wide ? 1 : 2;
     const int64_t k = fL + t;
     const bool active = t < cnt;
