@@ -462,9 +462,6 @@ __device__ __forceinline__ Item fetch_item(const DirectArgs& A, int* s_item) {
 #ifndef TP_SLAB_PAD
 #define TP_SLAB_PAD 0
 #endif
-#ifndef TP_SLAB_ADD2
-#define TP_SLAB_ADD2 0  // 1: the slab's column sums with packed FP32x2 adds (half the add instructions)
-#endif
 constexpr int SLAB_ROW = TP_SLAB_PAD ? 36 : 32;
 constexpr int SLAB_FLOATS = 16 * SLAB_ROW;
 template <bool MASKQ>
@@ -536,25 +533,12 @@ __device__ __forceinline__ void slab_reduce(const float* slab, float* out, int l
     const int r = lane & 15, h = lane >> 4;
     const float* row = slab + r * SLAB_ROW;
     const int xr = TP_SLAB_PAD ? 0 : (r & 7) << 2;
-#if TP_SLAB_ADD2
-    // packed adds: (x + z, y + w) of each 16-byte load, the four pairs summed in
-    // pairs, then the two halves
-    float2 vv;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const float4 q = *reinterpret_cast<const float4*>(row + (((h << 4) | (k << 2)) ^ xr));
-        const float2 u = add2(make_float2(q.x, q.y), make_float2(q.z, q.w));
-        vv = k == 0 ? u : add2(vv, u);
-    }
-    float v = vv.x + vv.y;
-#else
     float v = 0.f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const float4 q = *reinterpret_cast<const float4*>(row + (((h << 4) | (k << 2)) ^ xr));
         v += (q.x + q.y) + (q.z + q.w);
     }
-#endif
     v += __shfl_xor_sync(0xffffffffu, v, 16);
     if (lane < 16) out[lane] = v;
 }
