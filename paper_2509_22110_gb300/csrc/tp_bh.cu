@@ -638,7 +638,7 @@ struct NearWarpSmem {
 };
 
 template <int Q>
-__global__ void __launch_bounds__(NR_WARPS * 32) k_near(BHArgs A) {
+__global__ void __launch_bounds__(NR_WARPS * 32, TP_NR_BPS) k_near(BHArgs A) {
     __shared__ __align__(128) NearWarpSmem s_w[NR_WARPS];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     NearWarpSmem& S = s_w[warp];
