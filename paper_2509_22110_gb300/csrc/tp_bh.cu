@@ -55,7 +55,11 @@ namespace {
 constexpr int BH_WARPS = 4;
 constexpr int BH_STACK = 1024;
 constexpr int BH_FAR = 256;
-constexpr int BH_NEAR = 128;
+#ifndef TP_BH_NEAR
+#define TP_BH_NEAR 128
+#endif
+constexpr int BH_NEAR = TP_BH_NEAR;  // clusters per near-field run (k_bh's list of clusters apart from the leaf)
+constexpr int BH_TOUCH = 128;        // touching clusters gathered before k_bh sweeps them
 #ifndef TP_NEAR_FAST
 #define TP_NEAR_FAST 1  // near clusters far enough apart take the hi-part difference only
 #endif
@@ -259,7 +263,8 @@ template <int Q, int MODE>
 __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
     __shared__ int32_t s_stack[BH_WARPS][BH_STACK];
     __shared__ int32_t s_far[BH_WARPS][BH_FAR];
-    __shared__ int2 s_near[BH_WARPS][2][BH_NEAR];  // (first member, count); [0] apart, [1] touching
+    __shared__ int2 s_near[BH_WARPS][BH_NEAR];    // (first member, count) of clusters apart from the leaf
+    __shared__ int2 s_touch[BH_WARPS][BH_TOUCH];  // (first member, count) of clusters touching it
     __shared__ __align__(16) float s_stg[BH_WARPS][16 * BH_PAIR];
     __shared__ int4 s_stg_f[BH_WARPS][32];
     __shared__ LeafAdm s_la[BH_WARPS];  // the leaf's admissibility constants (read by every test)
@@ -396,7 +401,7 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
         // the run's ordered pairs (all, and those with hi-only differences) for the statistics
         unsigned int rp = 0, rh = 0;
         for (int i = lane; i < nn; i += 32) {
-            const int c = s_near[warp][0][i].y;
+            const int c = s_near[warp][i].y;
             rp += (unsigned)(c < 0 ? -c : c);
             if (c < 0) rh += (unsigned)-c;
         }
@@ -415,7 +420,7 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
             for (int kind = 0; kind < 2; ++kind)
                 for (int i0 = 0; i0 < nn; i0 += 32) {
                     const int i = i0 + lane;
-                    const int2 e = i < nn ? s_near[warp][0][i] : make_int2(0, 0);
+                    const int2 e = i < nn ? s_near[warp][i] : make_int2(0, 0);
                     const bool take = i < nn && (e.y < 0) == (kind == 1);
                     const unsigned bal = __ballot_sync(0xffffffffu, take);
                     if (take) A.near_list[pos + o + __popc(bal & lt)] = e;
@@ -543,8 +548,8 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
             if (is_far && !ffast) far[nfp + __popc(bfp & lt)] = node;
             if (is_far && ffast) far[BH_FAR - 1 - (nff + __popc(bff & lt))] = node;
             // (first member, count); a negative count marks a cluster whose pairs take the hi parts only
-            if (is_near && !touch) s_near[warp][0][nn[0] + __popc(bn0 & lt)] = make_int2(firstc, fast ? -cntc : cntc);
-            if (is_near && touch) s_near[warp][1][nn[1] + __popc(bn1 & lt)] = make_int2(firstc, cntc);
+            if (is_near && !touch) s_near[warp][nn[0] + __popc(bn0 & lt)] = make_int2(firstc, fast ? -cntc : cntc);
+            if (is_near && touch) s_touch[warp][nn[1] + __popc(bn1 & lt)] = make_int2(firstc, cntc);
         }
         if (is_open) {
             const int pos = sp + 2 * __popc(bo & lt);
@@ -567,8 +572,8 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
             emit_near(nn[0]);
             nn[0] = 0;
         }
-        if (nn[1] > BH_NEAR - 32) {
-            flush_touch(s_near[warp][1], nn[1]);
+        if (nn[1] > BH_TOUCH - 32) {
+            flush_touch(s_touch[warp], nn[1]);
             nn[1] = 0;
         }
         __syncwarp();
@@ -580,7 +585,7 @@ __global__ void __launch_bounds__(BH_WARPS * 32, TP_BH_MINB) k_bh(BHArgs A) {
     if (MODE == M_RECORD) return;
     flush_far(nfp, nff);
     emit_near(nn[0]);
-    flush_touch(s_near[warp][1], nn[1]);
+    flush_touch(s_touch[warp], nn[1]);
     double acc[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) acc[c] = (double)as_[c] - (double)ac[c];
