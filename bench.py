@@ -530,7 +530,9 @@ def main():
         achieved = FLOPS_PER_NEAR_PAIR * opairs / (kms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": None,
-                "kernel": "k_near<6> (near clusters apart from the target leaf)", "kernel_ms": kms,
+                "kernel": ("k_near_blk<6> (near clusters apart from the target leaf; one run per block)"
+                           if args.leaf > 16 else "k_near<6> (near clusters apart from the target leaf)"),
+                "kernel_ms": kms,
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz (max SM clock)",
                 "flops_per_ordered_pair": FLOPS_PER_NEAR_PAIR, "ordered_pairs_per_launch": opairs}
         if clk and clk.get("sm_mhz"):

@@ -849,6 +849,231 @@ __global__ void __launch_bounds__(NR_WARPS * 32, TP_NR_BPS) k_near(BHArgs A) {
     }
 }
 
+// Block-wide form of k_near (see TP_NR_BLOCK): one run per block of 128 threads,
+// lanes (target pair, source stream) over the whole block, so a leaf of cnt
+// targets keeps ceil(cnt/2) x floor(128 / pairs) threads busy (22 targets: 121
+// of 128, where a warp keeps 22 of 32); one ring of two slots of NB_SLOT
+// records per block.  Warp 0 plans the slots and issues the copies; a block
+// barrier per slot orders the reuse of a slot.  Numerics as in k_near.
+#ifndef TP_NR_BLOCK
+#define TP_NR_BLOCK 2  // 0: k_near always; 1: k_near_blk always; 2: k_near_blk for trees with leaves of more than 16
+#endif
+// Measured on the level-7 sphere: with leaves of 32 the block-wide form took the
+// near-field launch from 19.2 to 17.4 ms (theta 0.085, six blocks per SM); with
+// leaves of 16, whose runs are shorter and whose warps are already well filled,
+// it was slower (22.2 against 28.3 ms at theta 0.0625).
+__host__ __device__ constexpr bool near_block_form(int leaf_size) {
+    return TP_NR_BLOCK == 1 || (TP_NR_BLOCK == 2 && leaf_size > 16);
+}
+#ifndef TP_NB_BPS
+#define TP_NB_BPS 6  // k_near_blk blocks per SM: 6 x 37 KB of shared memory, at most 85 registers
+#endif
+#ifndef TP_NB_SLOT
+#define TP_NB_SLOT (NR_WARPS * TP_NR_SLOT)
+#endif
+constexpr int NB_THREADS = NR_WARPS * 32;
+constexpr int NB_SLOT = TP_NB_SLOT;  // records per ring slot
+
+struct NearBlockSmem {
+    float rec[2][NB_SLOT * TP_SRCW];
+    int2 ent[BH_NEAR];
+    uint64_t bar[2];
+    int ns[2];  // records planned into each slot and not yet consumed (0: none)
+    int hi[2];  // the slot's clusters take the hi parts only
+    long long work;
+};
+
+template <int Q>
+__global__ void __launch_bounds__(NB_THREADS, TP_NB_BPS) k_near_blk(BHArgs A) {
+    __shared__ __align__(128) NearBlockSmem S;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    uint32_t ph0 = 0u, ph1 = 0u;  // phase parities of the two slots' mbarriers
+    const unsigned long long nr = A.near_count[1];
+    const int64_t nruns = nr < (unsigned long long)A.nrun_cap ? (int64_t)nr : A.nrun_cap;
+    while (true) {
+        if (tid == 0) S.work = (long long)atomicAdd(&A.near_count[2], 1ull);
+        __syncthreads();
+        const int64_t run = S.work;
+        __syncthreads();  // every thread has read the item before thread 0 takes the next
+        if (run >= nruns) break;
+        const tp_far_run R = A.near_runs[run];
+        if (R.len <= 0 || R.len > BH_NEAR || R.li < 0 || (int64_t)R.li >= A.nleaves || R.start < 0 ||
+            R.start + R.len > A.near_cap)
+            continue;  // a run whose entries overflowed the list (the evaluation is repeated)
+        const int64_t L = A.leaves[R.li];
+        const int64_t fL = A.first[L];
+        const int cnt = A.last[L] - A.first[L] + 1;
+#if TP_DEBUG
+        {
+            bool ok = fL >= 0 && cnt >= 1 && cnt <= 32 && fL + cnt <= A.ntp;
+            for (int i = tid; i < R.len; i += NB_THREADS) {
+                const int2 e = A.near_list[R.start + i];
+                const int c = e.y < 0 ? -e.y : e.y;
+                ok = ok && c >= 1 && c <= 32 && e.x >= 0 && (int64_t)e.x + c <= A.ntp;
+            }
+            if (!__syncthreads_and(tp_dbg_ok(ok, A.derr))) continue;
+        }
+#endif
+        const int npair = (cnt + 1) >> 1;                // target pairs
+        const int ng = NB_THREADS / npair;               // source streams
+        const int tpl = tid % npair, g = tid / npair;    // this thread's pair and stream (g >= ng: idle)
+        for (int i = tid; i < R.len; i += NB_THREADS) S.ent[i] = A.near_list[R.start + i];
+        Tgt2 tg;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int t = 2 * tpl + h;
+            const bool act = t < cnt && g < ng;
+            const int64_t k = fL + (act ? t : 0);
+            float v[10];
+#pragma unroll
+            for (int c = 0; c < 10; ++c) v[c] = act ? A.soa[c * A.ntp + k] : 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                (h ? tg.h[c].y : tg.h[c].x) = v[c];
+                (h ? tg.l[c].y : tg.l[c].x) = v[3 + c];
+                (h ? tg.n[c].y : tg.n[c].x) = v[6 + c];
+            }
+            (h ? tg.w.y : tg.w.x) = v[9];
+        }
+        __syncthreads();  // the entries are in shared memory
+        // slot planning by warp 0, as in k_near (at most two rounds of 32
+        // entries per slot); `next` lives in warp 0's registers
+        int next = 0;
+        auto plan = [&](int b) {
+            int n = 0;
+            const bool hi = next < R.len && S.ent[next].y < 0;
+            int my_e[2] = {-1, -1}, my_o[2] = {0, 0};
+#pragma unroll
+            for (int round = 0; round < 2; ++round) {
+                if (next >= R.len) break;
+                const int e = next + lane;
+                const int2 en = e < R.len ? S.ent[e] : make_int2(0, 0);
+                const int c = abs(en.y);
+                const bool same = e < R.len && (en.y < 0) == hi;
+                const unsigned brk = __ballot_sync(0xffffffffu, !same);
+                const int f = brk ? __ffs(brk) - 1 : 32;
+                int incl = lane < f ? c : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const bool take = lane < f && n + incl <= NB_SLOT;
+                const int m = __popc(__ballot_sync(0xffffffffu, take));
+                if (take) {
+                    my_e[round] = e;
+                    my_o[round] = n + incl - c;
+                }
+                n += m ? __shfl_sync(0xffffffffu, incl, m - 1) : 0;
+                next += m;
+                if (m < 32) break;
+            }
+            if (lane == 0) {
+                S.ns[b] = n;
+                S.hi[b] = hi ? 1 : 0;
+            }
+            if (n == 0) {
+                if (next < R.len && lane == 0) tp_dev_error(A.derr, TP_DERR_INTERNAL);
+                return;
+            }
+            if (lane == 0) mbar_expect_tx(&S.bar[b], (uint32_t)(n * TP_SRCW * 4));
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                if (my_e[r] < 0) continue;
+                const int2 en = S.ent[my_e[r]];
+                tma_load_1d(S.rec[b] + my_o[r] * TP_SRCW, A.src + (int64_t)en.x * TP_SRCW,
+                            (uint32_t)(abs(en.y) * TP_SRCW * 4), &S.bar[b]);
+            }
+        };
+        if (warp == 0) {
+            plan(0);
+            plan(1);
+        }
+        __syncthreads();  // the slot sizes are in shared memory
+        float2 a2[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a2[c] = bh_f2(0.f);
+        KSum2 ek = {bh_f2(0.f), bh_f2(0.f)};
+        bool failed = false;
+        for (int slot = 0;; ++slot) {
+            const int b = slot & 1;
+            const int n = S.ns[b];  // planned before the last block barrier
+            if (n == 0) break;
+            const bool ok = mbar_wait_bounded(&S.bar[b], b ? ph1 : ph0);
+            if (__syncthreads_or(!ok)) {  // the same decision in every thread
+                failed = true;
+                break;
+            }
+            if (b) ph1 ^= 1u;
+            else ph0 ^= 1u;
+            const float* rb = S.rec[b];
+            if (g < ng) {
+                if (S.hi[b])
+                    for (int j = g; j < n; j += ng) near_pair2<Q, false>(tg, rb + j * TP_SRCW, a2);
+                else
+                    for (int j = g; j < n; j += ng) near_pair2<Q, true>(tg, rb + j * TP_SRCW, a2);
+            }
+            ksum2_add(ek, a2[0]);
+            a2[0] = bh_f2(0.f);
+            __syncthreads();  // every thread is done with slot b before it is planned again
+            if (warp == 0) plan(b);
+        }
+        if (failed) {
+            // copies of either slot may still be in flight: wait for them (bounded)
+            // before the block leaves its shared memory
+            if (tid == 0) {
+                tp_dev_error(A.derr, TP_DERR_TIMEOUT);
+                if (S.ns[0] > 0) mbar_wait_bounded(&S.bar[0], ph0);
+                if (S.ns[1] > 0) mbar_wait_bounded(&S.bar[1], ph1);
+            }
+            break;
+        }
+        // the streams' sums through shared memory (the ring is free), then one
+        // thread per (target pair, channel) adds both targets' totals
+        float* red = S.rec[0];                               // [128][16] channel partials
+        double* ered = reinterpret_cast<double*>(S.rec[1]);  // [128][2] energies
+#pragma unroll
+        for (int c = 1; c < 8; ++c) {
+            red[tid * 16 + 2 * c] = a2[c].x;
+            red[tid * 16 + 2 * c + 1] = a2[c].y;
+        }
+        ered[2 * tid] = (double)ek.s.x - (double)ek.c.x;
+        ered[2 * tid + 1] = (double)ek.s.y - (double)ek.c.y;
+        __syncthreads();
+        for (int item = tid; item < 8 * npair; item += NB_THREADS) {
+            const int p = item % npair, c = item / npair;
+            double v[2] = {0.0, 0.0};
+            float f[2] = {0.f, 0.f};
+            for (int gg = 0; gg < ng; ++gg) {
+                const int o = gg * npair + p;
+                if (c == 0) {
+                    v[0] += ered[2 * o];
+                    v[1] += ered[2 * o + 1];
+                } else {
+                    f[0] += red[o * 16 + 2 * c];
+                    f[1] += red[o * 16 + 2 * c + 1];
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int t = 2 * p + h;
+                if (t >= cnt) continue;
+                const int64_t k = fL + t;
+                const double w = (double)A.soa[9 * A.ntp + k];  // the target weight left out of the pair terms
+                atomicAdd(&A.acc[c * A.ntp + k], (c == 0 ? v[h] : (double)f[h]) * w);
+            }
+        }
+        __syncthreads();  // the entries and the ring are reused by the next run
+    }
+}
+
 // ------------------------------------------------------------ learned far field
 // In the learned form the far nodes of every leaf (listed by k_bh in runs of
 // up to BH_FAR nodes) are evaluated by k_far after the network, one warp per
@@ -1238,7 +1463,8 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
         const int64_t rows = std::max<int64_t>(1 << 20, t.nleaves * 1024);
         TP_TRY(alloc_far(rows, rows / 32 + t.nleaves + 1024));
     }
-    const unsigned nblocks = (unsigned)std::max(1, ctx->num_sms * TP_NR_BPS);
+    const bool nblk = near_block_form(t.leaf_size);
+    const unsigned nblocks = (unsigned)std::max(1, ctx->num_sms * (nblk ? TP_NB_BPS : TP_NR_BPS));
     const unsigned fblocks = (unsigned)std::max(1, ctx->num_sms * 4);
     // ordered pairs listed for k_near ([0]) and those of them with hi-only differences ([1])
     unsigned long long* near_listed = reinterpret_cast<unsigned long long*>(ctx->scalar + 10);
@@ -1271,12 +1497,14 @@ tp_status tp_launch_bh(tp_ctx* ctx, const tp_params* prm, bool learned) {
             if (learned) k_bh<6, M_LIST><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
             else k_bh<6, M_BH><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
             cudaEventRecord(ctx->ev[0], ctx->stream);
-            k_near<6><<<nblocks, NR_WARPS * 32, 0, ctx->stream>>>(A);
+            if (nblk) k_near_blk<6><<<nblocks, NB_THREADS, 0, ctx->stream>>>(A);
+            else k_near<6><<<nblocks, NR_WARPS * 32, 0, ctx->stream>>>(A);
         } else {
             if (learned) k_bh<8, M_LIST><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
             else k_bh<8, M_BH><<<blocks, BH_WARPS * 32, 0, ctx->stream>>>(A);
             cudaEventRecord(ctx->ev[0], ctx->stream);
-            k_near<8><<<nblocks, NR_WARPS * 32, 0, ctx->stream>>>(A);
+            if (nblk) k_near_blk<8><<<nblocks, NB_THREADS, 0, ctx->stream>>>(A);
+            else k_near<8><<<nblocks, NR_WARPS * 32, 0, ctx->stream>>>(A);
         }
         cudaEventRecord(ctx->ev[1], ctx->stream);
         ctx->nlaunch += 2;
@@ -1423,9 +1651,15 @@ tp_status tp_launch_near_runs(tp_ctx* ctx, int q, const int2* list, int64_t list
     A.near_cap = list_len;
     A.nrun_cap = run_cap;
     TP_CU(cudaMemsetAsync(counters + 2, 0, sizeof(unsigned long long), ctx->stream));
-    const unsigned nblocks = (unsigned)std::max(1, ctx->num_sms * TP_NR_BPS);
-    if (q == 6) k_near<6><<<nblocks, NR_WARPS * 32, 0, ctx->stream>>>(A);
-    else k_near<8><<<nblocks, NR_WARPS * 32, 0, ctx->stream>>>(A);
+    const bool nblk = near_block_form(ctx->tree.leaf_size);
+    const unsigned nblocks = (unsigned)std::max(1, ctx->num_sms * (nblk ? TP_NB_BPS : TP_NR_BPS));
+    if (nblk) {
+        if (q == 6) k_near_blk<6><<<nblocks, NB_THREADS, 0, ctx->stream>>>(A);
+        else k_near_blk<8><<<nblocks, NB_THREADS, 0, ctx->stream>>>(A);
+    } else {
+        if (q == 6) k_near<6><<<nblocks, NR_WARPS * 32, 0, ctx->stream>>>(A);
+        else k_near<8><<<nblocks, NR_WARPS * 32, 0, ctx->stream>>>(A);
+    }
     ++ctx->nlaunch;
     TP_CU(cudaGetLastError());
     return TP_OK;
