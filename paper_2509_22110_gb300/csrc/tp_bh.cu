@@ -56,7 +56,7 @@ constexpr int BH_WARPS = 4;
 constexpr int BH_STACK = 1024;
 constexpr int BH_FAR = 256;
 #ifndef TP_BH_NEAR
-#define TP_BH_NEAR 128
+#define TP_BH_NEAR 256
 #endif
 constexpr int BH_NEAR = TP_BH_NEAR;  // clusters per near-field run (k_bh's list of clusters apart from the leaf)
 constexpr int BH_TOUCH = 128;        // touching clusters gathered before k_bh sweeps them
@@ -869,7 +869,7 @@ __host__ __device__ constexpr bool near_block_form(int leaf_size) {
 #define TP_NB_BPS 6  // k_near_blk blocks per SM: 6 x 37 KB of shared memory, at most 85 registers
 #endif
 #ifndef TP_NB_SLOT
-#define TP_NB_SLOT (NR_WARPS * TP_NR_SLOT)
+#define TP_NB_SLOT 216  // with 256-entry runs: 6 x 37.7 KB of shared memory per SM
 #endif
 constexpr int NB_THREADS = NR_WARPS * 32;
 constexpr int NB_SLOT = TP_NB_SLOT;  // records per ring slot
