@@ -55,9 +55,6 @@ namespace {
 constexpr int BH_WARPS = 4;
 constexpr int BH_STACK = 1024;
 constexpr int BH_FAR = 256;
-#ifndef TP_BH_NEAR
-#define TP_BH_NEAR 256
-#endif
 constexpr int BH_NEAR = TP_BH_NEAR;  // clusters per near-field run (k_bh's list of clusters apart from the leaf)
 constexpr int BH_TOUCH = 128;        // touching clusters gathered before k_bh sweeps them
 #ifndef TP_NEAR_FAST

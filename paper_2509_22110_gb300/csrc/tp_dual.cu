@@ -350,7 +350,7 @@ __global__ void k_dt_fill(DTTree T, const int2* __restrict__ near, int64_t nnear
     }
 }
 
-constexpr int DT_RUN = 128;  // apart partners per run of the near-field kernel
+constexpr int DT_RUN = TP_BH_NEAR;  // apart partners per run of the near-field kernel
 
 __global__ void k_dt_runcount(const uint32_t* __restrict__ ca, int64_t nl, uint32_t* __restrict__ nr) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;

@@ -59,6 +59,12 @@ struct TpRange {
 // mesh's centroid-box diagonal form centroid differences from hi + lo parts
 #define TP_PRECISE_GAP_REL 0.02f
 
+// clusters per run of the near-field kernels' lists (the Barnes-Hut and the
+// cluster-cluster forms write runs of at most this length)
+#ifndef TP_BH_NEAR
+#define TP_BH_NEAR 256
+#endif
+
 // floats per node of the FP32 admissibility record: outward box [6], X_C [3],
 // diag_C [1], first, last, left, right as int bits (children -1 for
 // single-triangle nodes), 2 unused: 64 bytes, so one round of four 16-byte
