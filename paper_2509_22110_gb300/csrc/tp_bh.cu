@@ -1003,13 +1003,10 @@ __global__ void __launch_bounds__(NB_THREADS, TP_NB_BPS) k_near_blk(BHArgs A) {
             const int b = slot & 1;
             const int n = S.ns[b];  // planned before the last block barrier
             if (n == 0) break;
+            // a thread whose wait gave up still reads the slot (in bounds, values
+            // undefined); the barrier below, which also orders the slot's reuse,
+            // makes every thread see the failure, and the run is abandoned
             const bool ok = mbar_wait_bounded(&S.bar[b], b ? ph1 : ph0);
-            if (__syncthreads_or(!ok)) {  // the same decision in every thread
-                failed = true;
-                break;
-            }
-            if (b) ph1 ^= 1u;
-            else ph0 ^= 1u;
             const float* rb = S.rec[b];
             if (g < ng) {
                 if (S.hi[b])
@@ -1019,7 +1016,13 @@ __global__ void __launch_bounds__(NB_THREADS, TP_NB_BPS) k_near_blk(BHArgs A) {
             }
             ksum2_add(ek, a2[0]);
             a2[0] = bh_f2(0.f);
-            __syncthreads();  // every thread is done with slot b before it is planned again
+            // every thread is done with slot b before it is planned again
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            if (b) ph1 ^= 1u;
+            else ph0 ^= 1u;
             if (warp == 0) plan(b);
         }
         if (failed) {
